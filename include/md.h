@@ -1,0 +1,195 @@
+/*
+ * md.h — C ABI of the GB300 short-range Lennard-Jones MD hot path.
+ *
+ * The operations follow tinyMD (Machado et al., arXiv 2009.07400):
+ *   - Sec. 3.2, Eq. 1: positions and velocities are advanced by integrating
+ *     F = m a (here: velocity Verlet, kick-drift-kick);
+ *   - Sec. 3.2, Eq. 2: the 12-6 pair force, in the operation order of the
+ *     potential kernel shown in Sec. 4.2 (sr2 = 1/r^2, sr6 = sr2^3 sigma^6,
+ *     f = 48 eps sr6 (sr6 - 1/2) sr2, F_i += f (x_i - x_j)), strict cutoff
+ *     test r^2 < rc^2;
+ *   - Sec. 3.2, Fig. 1: Verlet lists with a buffer (skin) built from cell
+ *     lists whose side is >= rc + skin; full or half lists (Sec. 3.2 and the
+ *     half_nb specialisation of Sec. 4.2);
+ *   - Sec. 3.2: periodic boundaries in all directions;
+ *   - Sec. 4.2: neighbour-major list layout on GPUs (the k-th neighbours of
+ *     consecutive atoms are contiguous);
+ *   - Sec. 6: cells and lists rebuilt every 20 steps, dt = 0.005, rc = 2.5,
+ *     skin 0.3, FP64.
+ *
+ * Conventions shared by every call:
+ *   - A context owns all device memory it uses; it is created on the CUDA
+ *     device that is current at md_create*, and every later call must be
+ *     made with that device current.  A context is not thread-safe.
+ *   - Host arrays passed in are copied; the caller keeps ownership.  Output
+ *     arrays are caller-allocated.  Positions, velocities and forces cross
+ *     the ABI as n x 3 row-major double arrays in the caller's atom order
+ *     (the library reorders atoms internally by cell and maps back).
+ *   - Work is enqueued on the context's stream.  Calls that return data to
+ *     the host (md_energy, md_get_*) synchronise that stream; md_run
+ *     synchronises once at its end to check the device error word.
+ *   - Every call returns MD_OK (0) or a negative MD_ERR_* code; the text of
+ *     the last error is available from md_last_error.  After MD_ERR_CUDA the
+ *     context should be destroyed.
+ *   - No global state: several contexts may coexist.
+ */
+#ifndef MD_GB300_H
+#define MD_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MD_OK 0
+#define MD_ERR_INVAL (-1)          /* bad argument (null pointer, n <= 0, bad phase ...) */
+#define MD_ERR_BOX_TOO_SMALL (-2)  /* some L < 2 (rc + skin): minimum image would be wrong */
+#define MD_ERR_NOMEM (-3)          /* device or host allocation failed */
+#define MD_ERR_CUDA (-4)           /* a CUDA call failed */
+#define MD_ERR_NL_OVERFLOW (-5)    /* list capacity could not be grown enough */
+#define MD_ERR_TIMEOUT (-6)        /* a bounded device wait gave up */
+#define MD_ERR_NONFINITE (-7)      /* a position/velocity/force is NaN or Inf */
+#define MD_ERR_BADPOS (-8)         /* an atom moved more than one box length since the last wrap */
+#define MD_ERR_STATE (-9)          /* call not valid in the current state */
+
+#define MD_FP64 0   /* every arithmetic step in FP64 */
+#define MD_MIXED 1  /* FP32 pair arithmetic with Kahan sums; FP64 integration and reductions */
+
+/* Orthorhombic periodic box with origin 0: [0,lx) x [0,ly) x [0,lz). */
+typedef struct {
+    double lx, ly, lz;
+} md_box;
+
+/* Physical and algorithmic parameters (LJ reduced units). */
+typedef struct {
+    double epsilon;          /* well depth (V(2^(1/6) sigma) = -epsilon)            */
+    double sigma;            /* distance of the zero of V                           */
+    double mass;             /* atom mass                                           */
+    double cutoff;           /* rc, an absolute length; pairs with r^2 < rc^2 act   */
+    double skin;             /* Verlet buffer; list radius rs = rc + skin (strict)  */
+    double dt;               /* time step                                           */
+    int32_t rebuild_every;   /* rebuild cells + list after the drift of step n when
+                                n % rebuild_every == 0 (plus once at start)          */
+    int32_t precision;       /* MD_FP64 or MD_MIXED                                 */
+    int32_t half_list;       /* 0: full lists; 1: half lists (pair (i,j) stored
+                                with i iff id_j > id_i)                              */
+    int32_t threads_per_atom;/* 0 = tuned default; 1, 2 or 4 lanes per atom in the
+                                full-list force kernels                              */
+} md_params;
+
+/* Read-only facts about a context. */
+typedef struct {
+    int64_t n;               /* total atoms over all replicas                       */
+    int32_t nrep;            /* replicas                                            */
+    int32_t precision, half_list, threads_per_atom;
+    int32_t list_capacity;   /* entries per atom the list can hold                  */
+    int32_t max_neighbors;   /* largest row of the last build                       */
+    int64_t ncells;          /* cells over all replicas                             */
+    int64_t step;            /* steps taken by md_run / md_integrate(2)             */
+    int64_t kernel_launches; /* kernels this context launched (graph nodes counted) */
+    int64_t rebuilds;        /* list builds done                                    */
+} md_info;
+
+typedef struct md_ctx md_ctx;
+
+/* Creates a context for one periodic system of n atoms.
+ *   box, params: copied.  pos, vel: host, n x 3 doubles (caller order).
+ *   stream: a cudaStream_t to enqueue on, or NULL for a stream owned by the
+ *   context.  The initial state is binned, a list is built and forces are
+ *   computed before md_create returns.
+ * Errors: MD_ERR_INVAL, MD_ERR_BOX_TOO_SMALL, MD_ERR_NONFINITE, MD_ERR_NOMEM,
+ *   MD_ERR_CUDA.  On error *out is NULL. */
+int md_create(const md_box *box, const md_params *params, int64_t n, const double *pos,
+              const double *vel, void *stream, md_ctx **out);
+
+/* Creates one context holding nrep independent periodic replicas (same
+ * params, own boxes) that every call advances together: replica r owns
+ * counts[r] atoms, stored consecutively in pos/vel (host, sum(counts) x 3).
+ * Same errors as md_create. */
+int md_create_batch(int32_t nrep, const md_box *boxes, const md_params *params,
+                    const int64_t *counts, const double *pos, const double *vel, void *stream,
+                    md_ctx **out);
+
+void md_destroy(md_ctx *ctx);
+
+/* Text of the last error of ctx (or of the last failed md_create* when ctx is
+ * NULL); never NULL. */
+const char *md_last_error(const md_ctx *ctx);
+
+/* Replaces positions and velocities (host, n x 3, caller order) and
+ * re-establishes cells, list and forces.  Used for restarts. */
+int md_set_state(md_ctx *ctx, const double *pos, const double *vel);
+
+/* Cell binning (Sec. 3.2, Fig. 1): wraps every position into the box with
+ * one conditional +/-L per component, assigns cell (int)(x/s) (clamped to
+ * nc-1) with nc = floor(L/(rc+skin)), s = L/nc, and counting-sorts atoms by
+ * (cell, caller id).  Errors: MD_ERR_BADPOS, MD_ERR_NONFINITE, MD_ERR_CUDA. */
+int md_bin_cells(md_ctx *ctx);
+
+/* Verlet list build (Sec. 3.2, Fig. 1): for every atom, every atom j != i of
+ * the 27 neighbour cells (each periodic image once) with
+ * ((dx*dx + dy*dy) + dz*dz) < (rc+skin)^2 in FP64, dx the minimum-image
+ * difference, each operation rounded.  Bins first if atoms moved since the
+ * last md_bin_cells.  Grows the capacity on overflow.
+ * Errors: MD_ERR_NL_OVERFLOW, MD_ERR_NOMEM, MD_ERR_CUDA. */
+int md_build_neighbors(md_ctx *ctx);
+
+/* LJ forces over the current list (Sec. 3.2 Eq. 2; Sec. 4.2 kernel order). */
+int md_compute_forces(md_ctx *ctx);
+
+/* Velocity Verlet half steps (Sec. 3.2, Eq. 1) with the stored forces:
+ *   phase 1: v += dt/(2m) F; x += dt v      phase 2: v += dt/(2m) F
+ * Errors: MD_ERR_INVAL (phase not 1 or 2). */
+int md_integrate(md_ctx *ctx, int32_t phase);
+
+/* Potential energy (truncated, unshifted 4 eps [(s/r)^12 - (s/r)^6], pairs
+ * with r < rc once), kinetic energy 1/2 m sum v^2 and pair virial
+ * sum_pairs r_ij . F_ij of the current state, reduced in FP64.  Each output
+ * is a host array of nrep doubles (any may be NULL).  Synchronises. */
+int md_energy(md_ctx *ctx, double *pe, double *ke, double *virial);
+
+/* Advances nsteps velocity-Verlet steps with the rebuild schedule; the
+ * per-step work is replayed from CUDA graphs.  When energies is not NULL and
+ * energy_every > 0, (PE, KE, W) of every replica after steps s0 + k *
+ * energy_every (k = 1 .. nsteps / energy_every, s0 = steps taken before this
+ * call) is written to energies (host, (nsteps / energy_every) x nrep x 3
+ * doubles).  Synchronises once at the end.
+ * Errors: MD_ERR_NL_OVERFLOW, MD_ERR_NONFINITE, MD_ERR_BADPOS, MD_ERR_CUDA. */
+int md_run(md_ctx *ctx, int64_t nsteps, int32_t energy_every, double *energies);
+
+/* Copies of the state in caller order (host, n x 3 doubles).  Synchronise. */
+int md_get_positions(md_ctx *ctx, double *pos);
+int md_get_velocities(md_ctx *ctx, double *vel);
+int md_get_forces(md_ctx *ctx, double *force);
+
+/* The cells of the last binning, per replica in order: cell_start (host,
+ * ncells + nrep int32: each replica's exclusive prefix sums including its
+ * end) and cell_atoms (host, n int32 caller ids, ascending within a cell;
+ * ids are local to their replica).  Synchronises. */
+int md_get_cells(md_ctx *ctx, int32_t *cell_start, int32_t *cell_atoms);
+
+/* The current Verlet list in caller ids (local to the replica): counts (host,
+ * n int32) and rows (host, n x cap int32; row i holds counts[i] ids).
+ * Returns MD_ERR_INVAL if some row exceeds cap.  Synchronises. */
+int md_get_neighbors(md_ctx *ctx, int32_t *counts, int32_t *rows, int32_t cap);
+
+int md_get_info(md_ctx *ctx, md_info *info);
+
+/* Reallocates the list for `cap` entries per atom (rounded up to a multiple
+ * of 4) and rebuilds it now, growing past `cap` if the current state needs
+ * more.  Later rebuilds grow it again whenever a row overflows.
+ * Errors: MD_ERR_INVAL (cap < 4), MD_ERR_NOMEM, MD_ERR_NL_OVERFLOW. */
+int md_set_capacity(md_ctx *ctx, int32_t cap);
+
+/* Chooses threads_per_atom and full/half lists by timing each candidate for
+ * `steps` steps on the context's own state (which it restores), keeps the
+ * fastest and reports it in *chosen (may be NULL).  Results are cached per
+ * (precision, atoms-per-replica bucket) for the life of the process. */
+int md_autotune(md_ctx *ctx, int32_t steps, md_params *chosen);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MD_GB300_H */

@@ -198,6 +198,23 @@ def neighbors_cells(x, L, r, half=False, cap=128):
         cap = m + 16
 
 
+def neighbors_cells_raw(x, L, r, half=False, cap=128):
+    """Like neighbors_cells but returns (counts[n], rows[n, cap]) arrays."""
+    x = _f64(x, (-1, 3))
+    n = x.shape[0]
+    L = _box(L)
+    cell_of, start, atoms = bin_cells(x, L, r)
+    nc, _ = cell_grid(L, r)
+    while True:
+        counts = np.zeros(n, np.int32)
+        lst = np.zeros(n * cap, np.int32)
+        m = _load().orc_neighbors_cells(n, _dp(x), _dp(L), _ip(nc), _ip(cell_of), _ip(start),
+                                        _ip(atoms), float(r), int(half), cap, _ip(counts), _ip(lst))
+        if m <= cap:
+            return counts, lst.reshape(n, cap)
+        cap = m + 16
+
+
 def _pack(rows):
     n = len(rows)
     cap = max(1, max((len(r) for r in rows), default=1))

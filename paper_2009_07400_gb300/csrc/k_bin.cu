@@ -1,0 +1,226 @@
+// Cell binning (tinyMD Sec. 3.2, Fig. 1: cells of side >= rc + skin; Sec. 6:
+// "distribution over cells" every 20 steps).
+//
+// GPU design: a counting sort in four passes over HBM-resident SoA data.
+//   1. k_bin_assign   one thread per atom: wrap x into the box (one
+//                     conditional +/-L per component), cell = (int)(x/s)
+//                     clamped to nc-1, histogram with one atomicAdd.
+//   2. scan           exclusive prefix sum of the histogram (three kernels,
+//                     4096 cells per 1024-thread block, warp shuffles).
+//   3. k_bin_scatter  one thread per atom: slot = start + atomicSub(count)-1
+//                     (leaves the histogram at zero for the next binning).
+//   4. k_sort_gather  one warp per cell: rank the cell's members by caller
+//                     id (so the order is the stable (cell, id) order,
+//                     independent of atomic arrival order) and gather x, v,
+//                     id into the reordered buffers; also writes the
+//                     cell-relative FP32 position p = fl32(x - C_cell) and
+//                     the packed cell coordinates used by the mixed path.
+#include <cfloat>
+
+#include "md_internal.cuh"
+
+namespace mdk {
+
+namespace {
+
+__device__ __forceinline__ bool stopped(const DevStatus *st)
+{
+    return *((volatile const int32_t *)&st->flags) != 0;
+}
+
+template <bool BATCHED>
+__global__ void __launch_bounds__(256) k_bin_assign(Dev d)
+{
+    if (stopped(d.status)) return;
+    int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a == 0) d.status->rebuild_count += 1;
+    if (a >= d.n) return;
+    const Rep &R = d.reps[BATCHED ? d.rep_of[a] : 0];
+    dvec4 x = d.x[a];
+    double c[3] = {x.x, x.y, x.z};
+    int32_t k[3];
+    int32_t bad = 0;
+    for (int q = 0; q < 3; q++) {
+        double u = c[q];
+        if (!isfinite(u)) { bad |= FLAG_NONFINITE; u = 0.0; }
+        if (u < 0.0) u = u + R.L[q];
+        else if (u >= R.L[q]) u = u - R.L[q];
+        if (u < 0.0 || u > R.L[q]) { bad |= FLAG_BADPOS; u = 0.0; }
+        c[q] = u;
+        int32_t kk = (int32_t)(u / R.s[q]);
+        k[q] = kk >= R.nc[q] ? R.nc[q] - 1 : kk;
+    }
+    if (bad) atomicOr(&d.status->flags, bad);
+    d.x[a] = mk_dvec4(c[0], c[1], c[2], 0.0);
+    int32_t key = (int32_t)(R.cell_off + ((int64_t)k[0] * R.nc[1] + k[1]) * R.nc[2] + k[2]);
+    d.cell_key[a] = key;
+    atomicAdd(&d.cell_count[key], 1);
+}
+
+// Block-wide exclusive scan of 4 values per thread (1024 threads).
+__device__ __forceinline__ int32_t block_exclusive(int32_t v, int32_t *warp_tot, int32_t *total)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) warp_tot[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        int32_t t = warp_tot[lane];
+        int32_t s = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t u = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += u;
+        }
+        warp_tot[lane] = s - t;
+        if (lane == 31) *total = s;
+    }
+    __syncthreads();
+    return inc - v + warp_tot[w];
+}
+
+constexpr int kScanPer = 4096;  // elements per scan block (1024 threads x 4)
+
+// Phase A: per-block exclusive scan of in[] into out[], block total to tot[b].
+__global__ void __launch_bounds__(1024) k_scan_block(const int32_t *in, int32_t *out,
+                                                      int64_t len, int32_t *tot)
+{
+    __shared__ int32_t wt[32];
+    __shared__ int32_t total;
+    int64_t base = (int64_t)blockIdx.x * kScanPer + threadIdx.x * 4;
+    int32_t v[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) v[q] = (base + q < len) ? in[base + q] : 0;
+    int32_t sum = v[0] + v[1] + v[2] + v[3];
+    int32_t ex = block_exclusive(sum, wt, &total);
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        if (base + q < len) out[base + q] = ex;
+        ex += v[q];
+    }
+    if (threadIdx.x == 0) tot[blockIdx.x] = total;
+}
+
+// Phase B: one block scans the block totals (any count, in chunks of 4096)
+// and writes the grand total to out[len].
+__global__ void __launch_bounds__(1024) k_scan_tops(int32_t *tot, int64_t nb, int32_t *out,
+                                                     int64_t len)
+{
+    __shared__ int32_t wt[32];
+    __shared__ int32_t total;
+    int32_t carry = 0;
+    for (int64_t c0 = 0; c0 < nb; c0 += kScanPer) {
+        int64_t base = c0 + threadIdx.x * 4;
+        int32_t v[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) v[q] = (base + q < nb) ? tot[base + q] : 0;
+        int32_t ex = block_exclusive(v[0] + v[1] + v[2] + v[3], wt, &total);
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            if (base + q < nb) tot[base + q] = carry + ex;
+            ex += v[q];
+        }
+        carry += total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[len] = carry;
+}
+
+// Phase C: add each block's offset.
+__global__ void __launch_bounds__(1024) k_scan_add(int32_t *out, int64_t len, const int32_t *tot)
+{
+    int64_t base = (int64_t)blockIdx.x * kScanPer + threadIdx.x * 4;
+    int32_t off = tot[blockIdx.x];
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+        if (base + q < len) out[base + q] += off;
+}
+
+__global__ void __launch_bounds__(256) k_bin_scatter(Dev d)
+{
+    if (stopped(d.status)) return;
+    int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= d.n) return;
+    int32_t key = d.cell_key[a];
+    int32_t pos = d.cell_start[key] + atomicSub(&d.cell_count[key], 1) - 1;
+    d.perm[pos] = (int32_t)a;
+}
+
+// One warp per cell: rank members by caller id, gather into the new order.
+template <bool BATCHED>
+__global__ void __launch_bounds__(256) k_sort_gather(Dev d, int64_t ncells)
+{
+    if (stopped(d.status)) return;
+    const int lane = threadIdx.x & 31;
+    int64_t cell = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (cell >= ncells) return;
+    const int32_t start = d.cell_start[cell];
+    const int32_t m = d.cell_start[cell + 1] - start;
+    if (m == 0) return;
+    for (int32_t mine = lane; mine - lane < m; mine += 32) {
+        const bool have = mine < m;
+        const int32_t old = have ? d.perm[start + mine] : 0;
+        const int32_t my_id = have ? d.id[old] : INT32_MAX;
+        int32_t rank = 0;
+        for (int32_t c0 = 0; c0 < m; c0 += 32) {
+            int32_t other = (c0 + lane < m) ? d.id[d.perm[start + c0 + lane]] : INT32_MAX;
+#pragma unroll 8
+            for (int t = 0; t < 32; t++) rank += (__shfl_sync(0xffffffffu, other, t) < my_id);
+        }
+        if (!have) continue;
+        const int32_t ns = start + rank;
+        const dvec4 x = d.x[old];
+        d.x_alt[ns] = x;
+        d.v_alt[ns] = d.v[old];
+        d.id_alt[ns] = my_id;
+        const Rep &R = d.reps[BATCHED ? d.rep_of[ns] : 0];
+        int64_t local = cell - R.cell_off;
+        int32_t cz = (int32_t)(local % R.nc[2]);
+        int32_t cy = (int32_t)((local / R.nc[2]) % R.nc[1]);
+        int32_t cx = (int32_t)(local / ((int64_t)R.nc[2] * R.nc[1]));
+        double px = x.x - ((double)cx + 0.5) * R.s[0];
+        double py = x.y - ((double)cy + 0.5) * R.s[1];
+        double pz = x.z - ((double)cz + 0.5) * R.s[2];
+        uint32_t pack = (uint32_t)cx | ((uint32_t)cy << 10) | ((uint32_t)cz << 20);
+        d.p32[ns] = make_float4((float)px, (float)py, (float)pz, __uint_as_float(pack));
+    }
+}
+
+inline unsigned blocks_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
+
+}  // namespace
+
+int64_t scan_tmp_elems(int64_t ncells_total)
+{
+    return (ncells_total + kScanPer - 1) / kScanPer + 1;
+}
+
+// Bins the atoms of d (all replicas).  On return the reordered state is in
+// d.x_alt / d.v_alt / d.id_alt and d.p32 (the caller swaps the pointers).
+int launch_bin(const Dev &d, int64_t ncells, int32_t *tmp, int64_t tmp_len, cudaStream_t st,
+               int *nl)
+{
+    if (d.n <= 0) return 0;
+    const bool batched = d.nrep > 1;
+    unsigned gb = blocks_for(d.n, 256);
+    if (batched) k_bin_assign<true><<<gb, 256, 0, st>>>(d);
+    else k_bin_assign<false><<<gb, 256, 0, st>>>(d);
+    int64_t nb = (ncells + kScanPer - 1) / kScanPer;
+    if (nb + 1 > tmp_len) return -1;
+    k_scan_block<<<(unsigned)nb, 1024, 0, st>>>(d.cell_count, d.cell_start, ncells, tmp);
+    k_scan_tops<<<1, 1024, 0, st>>>(tmp, nb, d.cell_start, ncells);
+    k_scan_add<<<(unsigned)nb, 1024, 0, st>>>(d.cell_start, ncells, tmp);
+    k_bin_scatter<<<gb, 256, 0, st>>>(d);
+    unsigned gs = blocks_for(ncells * 32, 256);
+    if (batched) k_sort_gather<true><<<gs, 256, 0, st>>>(d, ncells);
+    else k_sort_gather<false><<<gs, 256, 0, st>>>(d, ncells);
+    *nl += 6;
+    return (int)cudaGetLastError();
+}
+
+}  // namespace mdk

@@ -1,0 +1,159 @@
+// Verlet-list build (tinyMD Sec. 3.2, Fig. 1: scan the neighbour cells, keep
+// every j within r = rc + skin; half lists store each pair once; Sec. 4.2:
+// neighbour-major layout on GPUs).
+//
+// The list criterion is exact FP64: r^2 = ((dx*dx + dy*dy) + dz*dz) with dx
+// the minimum-image difference, each operation rounded, compared strictly
+// with (rc+skin)^2.  GB300's FP64 rate is a small fraction of its FP32 rate,
+// so every candidate is first classified in FP32 from the cell-relative
+// positions p = fl32(x - C_cell):
+//     d = (p_i - p_j) + o * (-s)        (o = stencil offset of j's image)
+// The FP32 r^2 of a candidate differs from the FP64 one by far less than
+// 2.5e-4 rs^2 (a few FP32 ulps of |p| <= s/2 and |o s| <= s propagated
+// through the three squares), so only candidates inside that band are
+// decided by the FP64 test: about 3 % of the atoms meet one.  The FP64 test
+// applies the image shift the way the minimum-image branch does,
+// (x_i - x_j) -/+ L, with __dmul_rn/__dadd_rn so nothing is contracted.
+//
+// Each periodic image of each neighbour cell is visited once (all 27
+// offsets, each with its own image shift), so boxes with fewer than three
+// cells per dimension need no de-duplication: at most one image of an atom
+// lies within rs < L/2.
+//
+// Layout: entries of atom i are int4 chunks, chunk q at int4 index q*n + i;
+// the last chunk of a row is padded with self entries in slot 27.  Rows
+// longer than the capacity are counted but not stored (overflow flag).
+#include "md_internal.cuh"
+
+namespace mdk {
+
+namespace {
+
+__device__ __forceinline__ bool stopped(const DevStatus *st)
+{
+    return *((volatile const int32_t *)&st->flags) != 0;
+}
+
+__device__ __forceinline__ double image_diff(double xi, double xj, int k, double L)
+{
+    double t = __dsub_rn(xi, xj);
+    if (k > 0) t = __dsub_rn(t, L);
+    else if (k < 0) t = __dadd_rn(t, L);
+    return t;
+}
+
+// Builds row i; returns its length (rows longer than the capacity are
+// counted in full but stored only up to the capacity).
+template <bool BATCHED, bool HALF>
+__device__ __forceinline__ int32_t build_row(const Dev &d, const LJ &lj, int64_t i)
+{
+    const Rep &R = d.reps[BATCHED ? d.rep_of[i] : 0];
+    const float4 pi = d.p32[i];
+    const uint32_t pack = __float_as_uint(pi.w);
+    const int ci[3] = {(int)(pack & 1023u), (int)((pack >> 10) & 1023u), (int)((pack >> 20) & 1023u)};
+    const int32_t idi = HALF ? d.id[i] : 0;
+    const int64_t n = d.n;
+    int4 *nb4 = reinterpret_cast<int4 *>(d.nb);
+    const int cap4 = d.cap >> 2;
+
+    int32_t cnt = 0;
+    int4 buf = make_int4(0, 0, 0, 0);
+    bool have_xi = false;
+    dvec4 xi = mk_dvec4(0, 0, 0, 0);
+
+    for (int ox = -1; ox <= 1; ox++) {
+        int ux = ci[0] + ox, kx = 0;
+        if (ux < 0) { ux += R.nc[0]; kx = -1; } else if (ux >= R.nc[0]) { ux -= R.nc[0]; kx = 1; }
+        for (int oy = -1; oy <= 1; oy++) {
+            int uy = ci[1] + oy, ky = 0;
+            if (uy < 0) { uy += R.nc[1]; ky = -1; } else if (uy >= R.nc[1]) { uy -= R.nc[1]; ky = 1; }
+            for (int oz = -1; oz <= 1; oz++) {
+                int uz = ci[2] + oz, kz = 0;
+                if (uz < 0) { uz += R.nc[2]; kz = -1; } else if (uz >= R.nc[2]) { uz -= R.nc[2]; kz = 1; }
+                const int64_t cell = R.cell_off + ((int64_t)ux * R.nc[1] + uy) * R.nc[2] + uz;
+                const int32_t j0 = d.cell_start[cell], j1 = d.cell_start[cell + 1];
+                const uint32_t slot = (uint32_t)((ox + 1) * 9 + (oy + 1) * 3 + (oz + 1));
+                const float offx = (float)ox * R.nsf[0];
+                const float offy = (float)oy * R.nsf[1];
+                const float offz = (float)oz * R.nsf[2];
+                for (int32_t j = j0; j < j1; j++) {
+                    if (j == i) continue;
+                    if (HALF && d.id[j] <= idi) continue;
+                    const float4 pj = d.p32[j];
+                    const float dx = (pi.x - pj.x) + offx;
+                    const float dy = (pi.y - pj.y) + offy;
+                    const float dz = (pi.z - pj.z) + offz;
+                    const float r2f = dx * dx + dy * dy + dz * dz;
+                    bool keep;
+                    if (r2f < lj.rs2f_lo) keep = true;
+                    else if (r2f > lj.rs2f_hi) keep = false;
+                    else {
+                        if (!have_xi) { xi = d.x[i]; have_xi = true; }
+                        const dvec4 xj = d.x[j];
+                        const double tx = image_diff(xi.x, xj.x, kx, R.L[0]);
+                        const double ty = image_diff(xi.y, xj.y, ky, R.L[1]);
+                        const double tz = image_diff(xi.z, xj.z, kz, R.L[2]);
+                        const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(tx, tx), __dmul_rn(ty, ty)),
+                                                    __dmul_rn(tz, tz));
+                        keep = r2 < lj.rs2;
+                    }
+                    if (keep) {
+                        const int32_t e = (int32_t)((uint32_t)j | (slot << kJBits));
+                        switch (cnt & 3) {
+                            case 0: buf.x = e; break;
+                            case 1: buf.y = e; break;
+                            case 2: buf.z = e; break;
+                            default:
+                                buf.w = e;
+                                if ((cnt >> 2) < cap4) nb4[(int64_t)(cnt >> 2) * n + i] = buf;
+                        }
+                        cnt++;
+                    }
+                }
+            }
+        }
+    }
+    if ((cnt & 3) != 0 && (cnt >> 2) < cap4) {
+        const int32_t pad = (int32_t)((uint32_t)i | ((uint32_t)kPadSlot << kJBits));
+        const int r = cnt & 3;
+        if (r <= 1) buf.y = pad;
+        if (r <= 2) buf.z = pad;
+        buf.w = pad;
+        nb4[(int64_t)(cnt >> 2) * n + i] = buf;
+    }
+    d.nb_count[i] = cnt;
+    return cnt;
+}
+
+
+template <bool BATCHED, bool HALF>
+__global__ void __launch_bounds__(128) k_build(Dev d, LJ lj)
+{
+    if (stopped(d.status)) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t cnt = i < d.n ? build_row<BATCHED, HALF>(d, lj, i) : 0;
+    // every lane of the warp reaches this point: reduce the row lengths
+    const int32_t wmax = __reduce_max_sync(0xffffffffu, cnt);
+    if ((threadIdx.x & 31) == 0) atomicMax(&d.status->max_count, wmax);
+    if (cnt > d.cap) {
+        atomicOr(&d.status->flags, FLAG_NL_OVERFLOW);
+        d.status->overflow_at = d.status->rebuild_count;
+    }
+}
+
+}  // namespace
+
+int launch_build(const Dev &d, const LJ &lj, bool half, cudaStream_t st, int *nl)
+{
+    if (d.n <= 0) return 0;
+    unsigned g = (unsigned)((d.n + 127) / 128);
+    const bool b = d.nrep > 1;
+    if (b && half) k_build<true, true><<<g, 128, 0, st>>>(d, lj);
+    else if (b) k_build<true, false><<<g, 128, 0, st>>>(d, lj);
+    else if (half) k_build<false, true><<<g, 128, 0, st>>>(d, lj);
+    else k_build<false, false><<<g, 128, 0, st>>>(d, lj);
+    *nl += 1;
+    return (int)cudaGetLastError();
+}
+
+}  // namespace mdk

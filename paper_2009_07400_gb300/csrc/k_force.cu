@@ -1,0 +1,446 @@
+// LJ 12-6 forces over the Verlet list (tinyMD Sec. 3.2, Eq. 2) in the
+// operation order of the potential kernel of Sec. 4.2:
+//     sr2 = 1/rsq; sr6 = sr2*sr2*sr2*sigma^6; f = 48 eps sr6 (sr6 - 1/2) sr2
+//     F_i += f * del,  del = x_i - x_j,  only if rsq < rc^2.
+//
+// GPU mapping (Sec. 3.1/4.1: one thread per particle; here TPA = 1, 2 or 4
+// lanes per atom): the neighbour-major list is streamed from HBM as int4
+// chunks (ld.global.cs: evict-first, it is read once per step), neighbour
+// positions are gathered through the read-only L1 path (16 B float4 in the
+// mixed path, so the whole position array stays L2-resident), and the
+// per-atom sum stays in registers.  No tensor cores: the pair gather is not a
+// dense contraction.
+//
+// Mixed path: positions are FP32 offsets from the centre of the atom's cell
+// at the last binning; a neighbour's displacement is
+//     d = (p_i - p_j) + o * (-s)
+// with o its stencil offset (decoded from the entry's 5-bit slot through a
+// 27-entry shared table), so |d|'s FP32 rounding error is that of numbers of
+// size ~s rather than of the box length.  Per-atom sums are Kahan
+// compensated.  Positions and velocities are integrated in FP64.
+//
+// Epilogues (velocity Verlet, Sec. 3.2 Eq. 1, kick-drift-kick, c = dt/(2m)):
+//   EPI_F    store F
+//   EPI_FK   store F; v += c F                          (last step of a run)
+//   EPI_FKKD v += c F (full step n); v += c F; x += dt v; write the FP32
+//            position of step n+1 into the other p32 buffer (other atoms are
+//            still gathering this step's positions).
+#include "md_internal.cuh"
+
+namespace mdk {
+
+namespace {
+
+__device__ __forceinline__ bool stopped(const DevStatus *st)
+{
+    return *((volatile const int32_t *)&st->flags) != 0;
+}
+
+__device__ __forceinline__ int4 ld_stream(const int4 *p) { return __ldcs(p); }
+
+// Kahan (compensated) accumulation: s + c tracks the exact running sum.
+__device__ __forceinline__ void kahan_add(float &s, float &c, float term)
+{
+    const float y = term - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// FP64 reciprocal: FP32 seed refined by two Newton-Raphson steps
+// r <- r + r (1 - a r); each squares the relative error (2^-24 -> 2^-48 ->
+// below FP64 rounding).  Cheaper than an IEEE FP64 division on GB300.
+__device__ __forceinline__ double rcp_nr(double a)
+{
+    double r = (double)__frcp_rn((float)a);
+    double e = fma(-a, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-a, r, 1.0);
+    return fma(r, e, r);
+}
+
+__device__ __forceinline__ float4 stencil_entry(int s)
+{
+    // slot 27 (padding) sits 4096 cells away: far outside rc, masked.
+    return s < 27 ? make_float4((float)(s / 9 - 1), (float)((s / 3) % 3 - 1), (float)(s % 3 - 1), 0.f)
+                  : make_float4(4096.f, 0.f, 0.f, 0.f);
+}
+
+// FP64 epilogue shared by both precisions.  fx..fz: force on atom i.
+template <int EPI, bool ENERGY>
+__device__ __forceinline__ void epilogue(const Dev &d, const LJ &lj, const Rep &R, int64_t i,
+                                         double fx, double fy, double fz, uint32_t pack,
+                                         bool mixed)
+{
+    if (EPI == EPI_F || EPI == EPI_FK) {
+        if (mixed) d.f32[i] = make_float4((float)fx, (float)fy, (float)fz, 0.f);
+        else d.f64[i] = mk_dvec4(fx, fy, fz, 0.0);
+    }
+    if (EPI == EPI_F) return;
+    dvec4 v = d.v[i];
+    v.x = fma(lj.half_dt_m, fx, v.x);
+    v.y = fma(lj.half_dt_m, fy, v.y);
+    v.z = fma(lj.half_dt_m, fz, v.z);
+    if (ENERGY) d.ke_atom64[i] = 0.5 * lj.mass * fma(v.x, v.x, fma(v.y, v.y, v.z * v.z));
+    if (EPI == EPI_FKKD) {
+        v.x = fma(lj.half_dt_m, fx, v.x);
+        v.y = fma(lj.half_dt_m, fy, v.y);
+        v.z = fma(lj.half_dt_m, fz, v.z);
+        dvec4 x = d.x[i];
+        x.x = fma(lj.dt, v.x, x.x);
+        x.y = fma(lj.dt, v.y, x.y);
+        x.z = fma(lj.dt, v.z, x.z);
+        d.x[i] = x;
+        const double cx = ((double)(pack & 1023u) + 0.5) * R.s[0];
+        const double cy = ((double)((pack >> 10) & 1023u) + 0.5) * R.s[1];
+        const double cz = ((double)((pack >> 20) & 1023u) + 0.5) * R.s[2];
+        d.p32_nxt[i] = make_float4((float)(x.x - cx), (float)(x.y - cy), (float)(x.z - cz),
+                                   __uint_as_float(pack));
+    }
+    d.v[i] = v;
+}
+
+// ---------------------------------------------------------------------------
+// Mixed precision, full list.
+// ---------------------------------------------------------------------------
+template <int TPA, bool BATCHED, int EPI, bool ENERGY>
+__global__ void __launch_bounds__(256) k_force_mixed_full(Dev d, LJ lj)
+{
+    __shared__ float4 otab[32];
+    if (threadIdx.x < 32) otab[threadIdx.x] = stencil_entry(threadIdx.x);
+    __syncthreads();
+    if (stopped(d.status)) return;
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i0 = gt / TPA;
+    const int sub = (int)(gt % TPA);
+    const bool valid = i0 < d.n;
+    if (TPA == 1 && !valid) return;
+    const int64_t i = valid ? i0 : d.n - 1;
+    const int64_t n = d.n;
+    const Rep &R = d.reps[BATCHED ? d.rep_of[i] : 0];
+    const float nsx = R.nsf[0], nsy = R.nsf[1], nsz = R.nsf[2];
+    const float4 pi = d.p32[i];
+    const int cnt = valid ? d.nb_count[i] : 0;
+    const int nq = (cnt + 3) >> 2;
+    const int4 *nb4 = reinterpret_cast<const int4 *>(d.nb);
+
+    float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
+    float pe = 0.f, w = 0.f;
+
+    auto pair = [&](int32_t e) {
+        const int32_t j = (int32_t)((uint32_t)e & kJMask);
+        const float4 o = otab[(uint32_t)e >> kJBits];
+        const float4 pj = __ldg(&d.p32[j]);
+        const float dx = fmaf(o.x, nsx, pi.x - pj.x);
+        const float dy = fmaf(o.y, nsy, pi.y - pj.y);
+        const float dz = fmaf(o.z, nsz, pi.z - pj.z);
+        const float rsq = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        const float sr2 = __frcp_rn(rsq);
+        const float sr6 = sr2 * sr2 * sr2 * lj.sigma6f;
+        float f = lj.c48ef * sr6 * (sr6 - 0.5f) * sr2;
+        const bool in = rsq < lj.rc2f;
+        f = in ? f : 0.f;
+        kahan_add(sx, cx, f * dx);
+        kahan_add(sy, cy, f * dy);
+        kahan_add(sz, cz, f * dz);
+        if (ENERGY) {
+            pe += in ? lj.c4ef * sr6 * (sr6 - 1.f) : 0.f;
+            w += f * rsq;
+        }
+    };
+
+    int q = sub;
+    int4 nxt = q < nq ? ld_stream(nb4 + (int64_t)q * n + i) : make_int4(0, 0, 0, 0);
+    for (; q < nq; q += TPA) {
+        const int4 e = nxt;
+        if (q + TPA < nq) nxt = ld_stream(nb4 + (int64_t)(q + TPA) * n + i);
+        pair(e.x);
+        pair(e.y);
+        pair(e.z);
+        pair(e.w);
+    }
+    float fx = sx - cx, fy = sy - cy, fz = sz - cz;
+    if (TPA > 1) {
+#pragma unroll
+        for (int o = TPA / 2; o > 0; o >>= 1) {
+            fx += __shfl_xor_sync(0xffffffffu, fx, o);
+            fy += __shfl_xor_sync(0xffffffffu, fy, o);
+            fz += __shfl_xor_sync(0xffffffffu, fz, o);
+            if (ENERGY) {
+                pe += __shfl_xor_sync(0xffffffffu, pe, o);
+                w += __shfl_xor_sync(0xffffffffu, w, o);
+            }
+        }
+        if (sub != 0 || !valid) return;
+    }
+    if (ENERGY) {
+        d.pe_atom[i] = 0.5f * pe;
+        d.w_atom[i] = 0.5f * w;
+    }
+    epilogue<EPI, ENERGY>(d, lj, R, i, (double)fx, (double)fy, (double)fz,
+                          __float_as_uint(pi.w), true);
+}
+
+// ---------------------------------------------------------------------------
+// Mixed precision, half list: i-side Kahan sum in registers, j-side through
+// vector FP32 atomics (red.global.add.v4.f32); f32 must be zero on entry.
+// ---------------------------------------------------------------------------
+template <bool BATCHED, bool ENERGY>
+__global__ void __launch_bounds__(256) k_force_mixed_half(Dev d, LJ lj)
+{
+    __shared__ float4 otab[32];
+    if (threadIdx.x < 32) otab[threadIdx.x] = stencil_entry(threadIdx.x);
+    __syncthreads();
+    if (stopped(d.status)) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.n) return;
+    const int64_t n = d.n;
+    const Rep &R = d.reps[BATCHED ? d.rep_of[i] : 0];
+    const float nsx = R.nsf[0], nsy = R.nsf[1], nsz = R.nsf[2];
+    const float4 pi = d.p32[i];
+    const int cnt = d.nb_count[i];
+    const int nq = (cnt + 3) >> 2;
+    const int4 *nb4 = reinterpret_cast<const int4 *>(d.nb);
+    float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
+    float pe = 0.f, w = 0.f;
+
+    auto pair = [&](int32_t e) {
+        const uint32_t slot = (uint32_t)e >> kJBits;
+        if (slot >= 27) return;
+        const int32_t j = (int32_t)((uint32_t)e & kJMask);
+        const float4 o = otab[slot];
+        const float4 pj = __ldg(&d.p32[j]);
+        const float dx = fmaf(o.x, nsx, pi.x - pj.x);
+        const float dy = fmaf(o.y, nsy, pi.y - pj.y);
+        const float dz = fmaf(o.z, nsz, pi.z - pj.z);
+        const float rsq = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        if (!(rsq < lj.rc2f)) return;
+        const float sr2 = __frcp_rn(rsq);
+        const float sr6 = sr2 * sr2 * sr2 * lj.sigma6f;
+        const float f = lj.c48ef * sr6 * (sr6 - 0.5f) * sr2;
+        const float tx = f * dx, ty = f * dy, tz = f * dz;
+        kahan_add(sx, cx, tx);
+        kahan_add(sy, cy, ty);
+        kahan_add(sz, cz, tz);
+        atomicAdd(&d.f32[j], make_float4(-tx, -ty, -tz, 0.f));
+        if (ENERGY) {
+            pe += lj.c4ef * sr6 * (sr6 - 1.f);
+            w += f * rsq;
+        }
+    };
+    for (int q = 0; q < nq; q++) {
+        const int4 e = ld_stream(nb4 + (int64_t)q * n + i);
+        pair(e.x);
+        pair(e.y);
+        pair(e.z);
+        pair(e.w);
+    }
+    atomicAdd(&d.f32[i], make_float4(sx - cx, sy - cy, sz - cz, 0.f));
+    if (ENERGY) {
+        d.pe_atom[i] = pe;
+        d.w_atom[i] = w;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64, full list.  The image shift of a neighbour is added to (x_i - x_j)
+// exactly as the minimum-image branch would; atoms in interior cells never
+// need one, so the per-pair shift is only applied in warps that have an atom
+// on a box face.
+// ---------------------------------------------------------------------------
+struct Shift {
+    double lo[3], hi[3];  // added for o = -1 / o = +1 (0 unless on a face)
+};
+
+template <bool EDGE>
+__device__ __forceinline__ void f64_pair(const Dev &d, const LJ &lj, const dvec4 &xi,
+                                         const Shift &sh, int32_t e, double &fx, double &fy,
+                                         double &fz, double &pe, double &w, bool energy)
+{
+    const uint32_t slot = (uint32_t)e >> kJBits;
+    const int32_t j = (int32_t)((uint32_t)e & kJMask);
+    const dvec4 xj = ldg_dvec4(&d.x[j]);
+    double dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+    if (EDGE) {
+        const int ox = (int)(slot / 9) - 1, oy = (int)((slot / 3) % 3) - 1, oz = (int)(slot % 3) - 1;
+        if (ox) dx = dx + (ox < 0 ? sh.lo[0] : sh.hi[0]);
+        if (oy) dy = dy + (oy < 0 ? sh.lo[1] : sh.hi[1]);
+        if (oz) dz = dz + (oz < 0 ? sh.lo[2] : sh.hi[2]);
+    }
+    const double rsq = fma(dz, dz, fma(dy, dy, dx * dx));
+    const bool in = (rsq < lj.rc2) && (slot < 27);
+    const double sr2 = rcp_nr(rsq);
+    const double sr6 = sr2 * sr2 * sr2 * lj.sigma6;
+    double f = lj.c48e * sr6 * (sr6 - 0.5) * sr2;
+    f = in ? f : 0.0;
+    fx = fma(f, dx, fx);
+    fy = fma(f, dy, fy);
+    fz = fma(f, dz, fz);
+    if (energy) {
+        pe += in ? lj.c4e * sr6 * (sr6 - 1.0) : 0.0;
+        w = fma(f, rsq, w);
+    }
+}
+
+__device__ __forceinline__ Shift make_shift(const Rep &R, uint32_t pack, bool &edge)
+{
+    const int c[3] = {(int)(pack & 1023u), (int)((pack >> 10) & 1023u), (int)((pack >> 20) & 1023u)};
+    Shift sh;
+    edge = false;
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+        sh.lo[q] = c[q] == 0 ? R.L[q] : 0.0;            // image of cell -1 sits at x - L
+        sh.hi[q] = c[q] == R.nc[q] - 1 ? -R.L[q] : 0.0;  // image of cell nc sits at x + L
+        edge |= (c[q] == 0) || (c[q] == R.nc[q] - 1);
+    }
+    return sh;
+}
+
+template <int TPA, bool BATCHED, int EPI, bool ENERGY>
+__global__ void __launch_bounds__(256) k_force_f64_full(Dev d, LJ lj)
+{
+    if (stopped(d.status)) return;
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i0 = gt / TPA;
+    const int sub = (int)(gt % TPA);
+    const bool valid = i0 < d.n;
+    if (TPA == 1 && !valid) return;
+    const int64_t i = valid ? i0 : d.n - 1;
+    const int64_t n = d.n;
+    const Rep &R = d.reps[BATCHED ? d.rep_of[i] : 0];
+    const dvec4 xi = d.x[i];
+    const uint32_t pack = __float_as_uint(d.p32[i].w);
+    bool edge;
+    const Shift sh = make_shift(R, pack, edge);
+    const int cnt = valid ? d.nb_count[i] : 0;
+    const int nq = (cnt + 3) >> 2;
+    const int4 *nb4 = reinterpret_cast<const int4 *>(d.nb);
+    double fx = 0, fy = 0, fz = 0, pe = 0, w = 0;
+    const bool any_edge = __any_sync(__activemask(), edge);
+    for (int q = sub; q < nq; q += TPA) {
+        const int4 e = ld_stream(nb4 + (int64_t)q * n + i);
+        if (any_edge) {
+            f64_pair<true>(d, lj, xi, sh, e.x, fx, fy, fz, pe, w, ENERGY);
+            f64_pair<true>(d, lj, xi, sh, e.y, fx, fy, fz, pe, w, ENERGY);
+            f64_pair<true>(d, lj, xi, sh, e.z, fx, fy, fz, pe, w, ENERGY);
+            f64_pair<true>(d, lj, xi, sh, e.w, fx, fy, fz, pe, w, ENERGY);
+        } else {
+            f64_pair<false>(d, lj, xi, sh, e.x, fx, fy, fz, pe, w, ENERGY);
+            f64_pair<false>(d, lj, xi, sh, e.y, fx, fy, fz, pe, w, ENERGY);
+            f64_pair<false>(d, lj, xi, sh, e.z, fx, fy, fz, pe, w, ENERGY);
+            f64_pair<false>(d, lj, xi, sh, e.w, fx, fy, fz, pe, w, ENERGY);
+        }
+    }
+    if (TPA > 1) {
+#pragma unroll
+        for (int o = TPA / 2; o > 0; o >>= 1) {
+            fx += __shfl_xor_sync(0xffffffffu, fx, o);
+            fy += __shfl_xor_sync(0xffffffffu, fy, o);
+            fz += __shfl_xor_sync(0xffffffffu, fz, o);
+            if (ENERGY) {
+                pe += __shfl_xor_sync(0xffffffffu, pe, o);
+                w += __shfl_xor_sync(0xffffffffu, w, o);
+            }
+        }
+        if (sub != 0 || !valid) return;
+    }
+    if (ENERGY) {
+        d.pe_atom64[i] = 0.5 * pe;
+        d.w_atom64[i] = 0.5 * w;
+    }
+    epilogue<EPI, ENERGY>(d, lj, R, i, fx, fy, fz, pack, false);
+}
+
+// FP64, half list: j-side through FP64 atomics; f64 must be zero on entry.
+template <bool BATCHED, bool ENERGY>
+__global__ void __launch_bounds__(256) k_force_f64_half(Dev d, LJ lj)
+{
+    if (stopped(d.status)) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.n) return;
+    const int64_t n = d.n;
+    const Rep &R = d.reps[BATCHED ? d.rep_of[i] : 0];
+    const dvec4 xi = d.x[i];
+    const uint32_t pack = __float_as_uint(d.p32[i].w);
+    bool edge;
+    const Shift sh = make_shift(R, pack, edge);
+    const int cnt = d.nb_count[i];
+    const int nq = (cnt + 3) >> 2;
+    const int4 *nb4 = reinterpret_cast<const int4 *>(d.nb);
+    double fx = 0, fy = 0, fz = 0, pe = 0, w = 0;
+    for (int q = 0; q < nq; q++) {
+        const int4 e4 = ld_stream(nb4 + (int64_t)q * n + i);
+        const int32_t es[4] = {e4.x, e4.y, e4.z, e4.w};
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            double gx = 0, gy = 0, gz = 0, pp = 0, ww = 0;
+            f64_pair<true>(d, lj, xi, sh, es[t], gx, gy, gz, pp, ww, ENERGY);
+            if (gx != 0.0 || gy != 0.0 || gz != 0.0) {
+                const int32_t j = (int32_t)((uint32_t)es[t] & kJMask);
+                atomicAdd(&d.f64[j].x, -gx);
+                atomicAdd(&d.f64[j].y, -gy);
+                atomicAdd(&d.f64[j].z, -gz);
+            }
+            fx += gx; fy += gy; fz += gz; pe += pp; w += ww;
+        }
+    }
+    atomicAdd(&d.f64[i].x, fx);
+    atomicAdd(&d.f64[i].y, fy);
+    atomicAdd(&d.f64[i].z, fz);
+    if (ENERGY) {
+        d.pe_atom64[i] = pe;
+        d.w_atom64[i] = w;
+    }
+}
+
+template <int TPA, bool B>
+int launch_full(const Dev &d, const LJ &lj, bool mixed, int epi, bool energy, cudaStream_t st)
+{
+    const int64_t threads = d.n * TPA;
+    const unsigned g = (unsigned)((threads + 255) / 256);
+#define MD_FULL(EP, EN)                                                                    \
+    do {                                                                                   \
+        if (mixed) k_force_mixed_full<TPA, B, EP, EN><<<g, 256, 0, st>>>(d, lj);           \
+        else k_force_f64_full<TPA, B, EP, EN><<<g, 256, 0, st>>>(d, lj);                   \
+    } while (0)
+    if (epi == EPI_F) { if (energy) MD_FULL(EPI_F, true); else MD_FULL(EPI_F, false); }
+    else if (epi == EPI_FK) { if (energy) MD_FULL(EPI_FK, true); else MD_FULL(EPI_FK, false); }
+    else { if (energy) MD_FULL(EPI_FKKD, true); else MD_FULL(EPI_FKKD, false); }
+#undef MD_FULL
+    return 0;
+}
+
+}  // namespace
+
+// Half lists only support EPI_F (the caller zeroes the force array first and
+// integrates in a separate kernel).
+int launch_force(const Dev &d, const LJ &lj, int precision, bool half, int tpa, int epi,
+                 bool energy, bool batched, cudaStream_t st, int *nl)
+{
+    if (d.n <= 0) return 0;
+    const bool mixed = precision == 1;
+    if (half) {
+        if (epi != EPI_F) return -1;
+        const unsigned g = (unsigned)((d.n + 255) / 256);
+#define MD_HALF(B, EN)                                                   \
+    do {                                                                 \
+        if (mixed) k_force_mixed_half<B, EN><<<g, 256, 0, st>>>(d, lj);  \
+        else k_force_f64_half<B, EN><<<g, 256, 0, st>>>(d, lj);          \
+    } while (0)
+        if (batched) { if (energy) MD_HALF(true, true); else MD_HALF(true, false); }
+        else { if (energy) MD_HALF(false, true); else MD_HALF(false, false); }
+#undef MD_HALF
+    } else if (batched) {
+        if (tpa == 4) launch_full<4, true>(d, lj, mixed, epi, energy, st);
+        else if (tpa == 2) launch_full<2, true>(d, lj, mixed, epi, energy, st);
+        else launch_full<1, true>(d, lj, mixed, epi, energy, st);
+    } else {
+        if (tpa == 4) launch_full<4, false>(d, lj, mixed, epi, energy, st);
+        else if (tpa == 2) launch_full<2, false>(d, lj, mixed, epi, energy, st);
+        else launch_full<1, false>(d, lj, mixed, epi, energy, st);
+    }
+    *nl += 1;
+    return (int)cudaGetLastError();
+}
+
+}  // namespace mdk

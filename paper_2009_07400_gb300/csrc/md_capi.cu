@@ -1,0 +1,911 @@
+// Host runtime and C ABI (include/md.h) of the GB300 LJ MD hot path.
+//
+// A context owns the device state of one or more periodic replicas laid out
+// back to back (structure of arrays, atoms sorted by (replica, cell, id) at
+// every binning).  md_run turns a span of steps into a list of operations --
+//     KD                 first half-kick + drift (from stored forces)
+//     REBUILD            bin + build, after the drift of step n % every == 0
+//     F(n)               forces at x_n fused with the rest of velocity Verlet
+// -- cut at every rebuild into segments, and replays each segment from a
+// CUDA graph cached under (buffer parities, operation string).  A steady
+// 20-step cycle is one graph launch.
+//
+// Failure handling: kernels set bits in a device error word and every later
+// kernel returns at once while it is set, so the state freezes at the first
+// failure.  md_run synchronises once at its end; a list overflow is repaired
+// by growing the capacity and resuming at the rebuild that overflowed.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/md.h"
+#include "md_internal.cuh"
+
+using namespace mdk;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct Op {
+    enum Kind { KD, REBUILD, FORCE } kind;
+    int64_t step;   // step n the op belongs to
+    bool last;      // FORCE: last step of the run (store F, no next drift)
+    bool energy;    // FORCE: log (PE, KE, W) of step n
+};
+
+struct GraphRec {
+    cudaGraphExec_t exec;
+    int launches;
+    int xb_after, pb_after;
+};
+
+}  // namespace
+
+struct md_ctx {
+    int64_t n = 0;
+    int32_t nrep = 0;
+    md_params p{};
+    LJ lj{};
+    std::vector<Rep> reps_h;
+    std::vector<int64_t> counts_h;
+    int64_t ncells = 0;
+    int64_t nchunks = 0;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    int tpa = 1;
+
+    Rep *reps_d = nullptr;
+    int32_t *rep_of_d = nullptr;
+    dvec4 *x[2] = {nullptr, nullptr}, *v[2] = {nullptr, nullptr};
+    int32_t *id[2] = {nullptr, nullptr};
+    float4 *p32[2] = {nullptr, nullptr};
+    float4 *f32 = nullptr;
+    dvec4 *f64 = nullptr;
+    int32_t *cell_key = nullptr, *cell_count = nullptr, *cell_start = nullptr, *perm = nullptr;
+    int32_t *scan_tmp = nullptr;
+    int64_t scan_len = 0;
+    int32_t *nb = nullptr, *nb_count = nullptr;
+    int32_t cap = 0;
+    float *pe_atom = nullptr, *w_atom = nullptr;
+    double *pe64 = nullptr, *w64 = nullptr, *ke64 = nullptr;
+    DevStatus *status = nullptr;
+    int64_t *chunk_rep_d = nullptr, *chunk_first_d = nullptr;
+    double *partials_d = nullptr, *eout_d = nullptr;
+    double *elog_d = nullptr;
+    int64_t elog_cap = 0;
+    double *io_d = nullptr;
+
+    int xb = 0, pb = 0;
+    bool moved_since_bin = true, list_valid = false, forces_valid = false;
+    int64_t step = 0, launches = 0, rebuilds = 0, builds_enqueued = 0;
+    int32_t last_max = 0;
+    std::string err;
+    std::map<std::string, GraphRec> graphs;
+};
+
+namespace {
+
+int fail(md_ctx *c, int code, const std::string &msg)
+{
+    if (c) c->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(c, MD_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+Dev view(const md_ctx *c)
+{
+    Dev d{};
+    d.n = c->n;
+    d.nrep = c->nrep;
+    d.cap = c->cap;
+    d.reps = c->reps_d;
+    d.rep_of = c->rep_of_d;
+    d.x = c->x[c->xb];
+    d.v = c->v[c->xb];
+    d.x_alt = c->x[1 - c->xb];
+    d.v_alt = c->v[1 - c->xb];
+    d.id = c->id[c->xb];
+    d.id_alt = c->id[1 - c->xb];
+    d.p32 = c->p32[c->pb];
+    d.p32_nxt = c->p32[1 - c->pb];
+    d.f32 = c->f32;
+    d.f64 = c->f64;
+    d.cell_key = c->cell_key;
+    d.cell_count = c->cell_count;
+    d.cell_start = c->cell_start;
+    d.perm = c->perm;
+    d.nb = c->nb;
+    d.nb_count = c->nb_count;
+    d.pe_atom = c->pe_atom;
+    d.w_atom = c->w_atom;
+    d.pe_atom64 = c->pe64;
+    d.w_atom64 = c->w64;
+    d.ke_atom64 = c->ke64;
+    d.status = c->status;
+    return d;
+}
+
+template <typename T>
+int dalloc(md_ctx *c, T **p, size_t count)
+{
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * count);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(c, MD_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    return MD_OK;
+}
+
+void free_all(md_ctx *c)
+{
+    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+    c->graphs.clear();
+    void *ptrs[] = {c->reps_d, c->rep_of_d, c->x[0], c->x[1], c->v[0], c->v[1], c->id[0],
+                    c->id[1], c->p32[0], c->p32[1], c->f32, c->f64, c->cell_key, c->cell_count,
+                    c->cell_start, c->perm, c->scan_tmp, c->nb, c->nb_count, c->pe_atom,
+                    c->w_atom, c->pe64, c->w64, c->ke64, c->status, c->chunk_rep_d,
+                    c->chunk_first_d, c->partials_d, c->eout_d, c->elog_d, c->io_d};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (c->own_stream && c->st) cudaStreamDestroy(c->st);
+}
+
+bool is_mixed(const md_ctx *c) { return c->p.precision == MD_MIXED; }
+bool is_half(const md_ctx *c) { return c->p.half_list != 0; }
+bool batched(const md_ctx *c) { return c->nrep > 1; }
+
+int32_t round4(int64_t v) { return (int32_t)((v + 3) / 4 * 4); }
+
+int alloc_list(md_ctx *c, int32_t cap)
+{
+    if (c->nb) cudaFree(c->nb);
+    c->nb = nullptr;
+    c->cap = round4(cap);
+    int rc = dalloc(c, &c->nb, (size_t)c->n * (size_t)c->cap);
+    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+    c->graphs.clear();
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Enqueue helpers (used both directly and under stream capture).
+// ---------------------------------------------------------------------------
+int enq_bin(md_ctx *c, int *nl)
+{
+    Dev d = view(c);
+    if (launch_bin(d, c->ncells, c->scan_tmp, c->scan_len, c->st, nl) != 0)
+        return fail(c, MD_ERR_CUDA, "binning launch failed");
+    c->xb = 1 - c->xb;  // reordered state now lives in the other buffers
+    c->moved_since_bin = false;
+    c->list_valid = false;
+    c->forces_valid = false;
+    return MD_OK;
+}
+
+int enq_build(md_ctx *c, int *nl)
+{
+    CK(cudaMemsetAsync(&c->status->max_count, 0, sizeof(int32_t), c->st));
+    Dev d = view(c);
+    if (launch_build(d, c->lj, is_half(c), c->st, nl) != 0)
+        return fail(c, MD_ERR_CUDA, "list build launch failed");
+    c->list_valid = true;
+    c->builds_enqueued++;
+    return MD_OK;
+}
+
+int enq_energy(md_ctx *c, bool ke_from_v, double *out3, int *nl)
+{
+    Dev d = view(c);
+    if (launch_energy(d, c->lj, c->p.precision, ke_from_v, c->chunk_rep_d, c->chunk_first_d,
+                      c->nchunks, c->partials_d, out3, out3 ? nullptr : c->elog_d, c->st,
+                      nl) != 0)
+        return fail(c, MD_ERR_CUDA, "energy launch failed");
+    return MD_OK;
+}
+
+// Forces at the current positions followed by `epi` (EPI_F / EPI_FK /
+// EPI_FKKD); with `energy`, per-atom PE/W (and KE of the full-step v).
+int enq_force(md_ctx *c, int epi, bool energy, int *nl)
+{
+    Dev d = view(c);
+    if (is_half(c)) {
+        if (is_mixed(c)) CK(cudaMemsetAsync(c->f32, 0, sizeof(float4) * c->n, c->st));
+        else CK(cudaMemsetAsync(c->f64, 0, sizeof(dvec4) * c->n, c->st));
+        if (launch_force(d, c->lj, c->p.precision, true, 1, EPI_F, energy, batched(c), c->st, nl))
+            return fail(c, MD_ERR_CUDA, "force launch failed");
+        if (epi == EPI_FK) {
+            if (launch_integrate(d, c->lj, c->p.precision, 2, batched(c), c->st, nl))
+                return fail(c, MD_ERR_CUDA, "integrate launch failed");
+        } else if (epi == EPI_FKKD) {
+            if (launch_integrate(d, c->lj, c->p.precision, energy ? 4 : 3, batched(c), c->st, nl))
+                return fail(c, MD_ERR_CUDA, "integrate launch failed");
+        }
+    } else {
+        if (launch_force(d, c->lj, c->p.precision, false, c->tpa, epi, energy, batched(c), c->st,
+                         nl))
+            return fail(c, MD_ERR_CUDA, "force launch failed");
+        if (epi == EPI_FKKD) c->pb = 1 - c->pb;
+    }
+    if (epi == EPI_FKKD) c->moved_since_bin = true;
+    c->forces_valid = (epi != EPI_FKKD);
+    return MD_OK;
+}
+
+int enq_op(md_ctx *c, const Op &op, int *nl)
+{
+    int rc = MD_OK;
+    if (op.kind == Op::KD) {
+        Dev d = view(c);
+        if (launch_integrate(d, c->lj, c->p.precision, 1, batched(c), c->st, nl))
+            return fail(c, MD_ERR_CUDA, "integrate launch failed");
+        c->moved_since_bin = true;
+        c->forces_valid = false;
+    } else if (op.kind == Op::REBUILD) {
+        if ((rc = enq_bin(c, nl))) return rc;
+        if ((rc = enq_build(c, nl))) return rc;
+    } else {
+        const int epi = op.last ? EPI_FK : EPI_FKKD;
+        // For FK with energy on half lists the KE is of the final v: the
+        // phase-2 kick then the energy pass reading v (ke_from_v).
+        if ((rc = enq_force(c, epi, op.energy, nl))) return rc;
+        if (op.energy) {
+            if ((rc = enq_energy(c, op.last, nullptr, nl))) return rc;
+        }
+    }
+    return rc;
+}
+
+std::string key_of(const md_ctx *c, const std::vector<Op> &ops)
+{
+    std::string k = std::to_string(c->xb) + std::to_string(c->pb) + ":";
+    for (const Op &o : ops) {
+        if (o.kind == Op::KD) k += 'K';
+        else if (o.kind == Op::REBUILD) k += 'R';
+        else k += o.last ? (o.energy ? 'L' : 'l') : (o.energy ? 'E' : 'e');
+    }
+    return k;
+}
+
+// Runs one segment of ops through a cached CUDA graph.
+int run_segment(md_ctx *c, const std::vector<Op> &ops)
+{
+    const std::string key = key_of(c, ops);
+    auto it = c->graphs.find(key);
+    if (it == c->graphs.end()) {
+        const int xb0 = c->xb, pb0 = c->pb;
+        const bool mv = c->moved_since_bin, lv = c->list_valid, fv = c->forces_valid;
+        const int64_t be = c->builds_enqueued;
+        CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+        int nl = 0, rc = MD_OK;
+        for (const Op &op : ops)
+            if ((rc = enq_op(c, op, &nl))) break;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->st, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return fail(c, MD_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+        GraphRec rec{};
+        e = cudaGraphInstantiate(&rec.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(c, MD_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+        rec.launches = nl;
+        rec.xb_after = c->xb;
+        rec.pb_after = c->pb;
+        it = c->graphs.emplace(key, rec).first;
+        // capture changed the host bookkeeping; rewind, the replay re-applies it
+        c->xb = xb0; c->pb = pb0;
+        c->moved_since_bin = mv; c->list_valid = lv; c->forces_valid = fv;
+        c->builds_enqueued = be;
+    }
+    CK(cudaGraphLaunch(it->second.exec, c->st));
+    c->launches += it->second.launches;
+    c->xb = it->second.xb_after;
+    c->pb = it->second.pb_after;
+    for (const Op &op : ops) {
+        if (op.kind == Op::REBUILD) {
+            c->builds_enqueued++;
+            c->rebuilds++;
+            c->moved_since_bin = false;
+            c->list_valid = true;
+        } else if (op.kind == Op::KD) {
+            c->moved_since_bin = true;
+            c->forces_valid = false;
+        } else {
+            c->forces_valid = op.last;
+            if (!op.last) c->moved_since_bin = true;
+        }
+    }
+    return MD_OK;
+}
+
+int read_status(md_ctx *c, DevStatus *s)
+{
+    CK(cudaMemcpyAsync(s, c->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return MD_OK;
+}
+
+int check_flags(md_ctx *c, const DevStatus &s)
+{
+    if (s.flags & FLAG_NONFINITE) return fail(c, MD_ERR_NONFINITE, "non-finite position found at binning");
+    if (s.flags & FLAG_BADPOS) return fail(c, MD_ERR_BADPOS, "an atom moved more than one box length between wraps");
+    return MD_OK;
+}
+
+int grow_list(md_ctx *c, int32_t seen_max)
+{
+    int64_t want = std::max<int64_t>((int64_t)(seen_max * 1.2) + 8, (int64_t)c->cap * 3 / 2);
+    if (want > (int64_t)1 << 16) return fail(c, MD_ERR_NL_OVERFLOW, "neighbour list capacity limit reached");
+    int rc = alloc_list(c, (int32_t)want);
+    if (rc) return fail(c, MD_ERR_NL_OVERFLOW, "cannot grow the neighbour list: " + c->err);
+    return MD_OK;
+}
+
+// Bin + build with overflow repair (direct launches, synchronising).
+int rebuild_now(md_ctx *c, bool bin)
+{
+    for (int attempt = 0; attempt < 8; attempt++) {
+        int nl = 0, rc;
+        if (bin && (rc = enq_bin(c, &nl))) return rc;
+        bin = false;
+        if ((rc = enq_build(c, &nl))) return rc;
+        c->launches += nl;
+        c->rebuilds++;
+        DevStatus s;
+        if ((rc = read_status(c, &s))) return rc;
+        if ((rc = check_flags(c, s))) return rc;
+        c->last_max = s.max_count;
+        if (!(s.flags & FLAG_NL_OVERFLOW)) return MD_OK;
+        CK(cudaMemsetAsync(&c->status->flags, 0, sizeof(int32_t), c->st));
+        if ((rc = grow_list(c, s.max_count))) return rc;
+    }
+    return fail(c, MD_ERR_NL_OVERFLOW, "neighbour list kept overflowing");
+}
+
+int ensure_list(md_ctx *c)
+{
+    if (c->list_valid && !c->moved_since_bin) return MD_OK;
+    return rebuild_now(c, true);
+}
+
+int ensure_forces(md_ctx *c)
+{
+    if (c->forces_valid) return MD_OK;
+    int rc = ensure_list(c);
+    if (rc) return rc;
+    int nl = 0;
+    if ((rc = enq_force(c, EPI_F, false, &nl))) return rc;
+    c->launches += nl;
+    return MD_OK;
+}
+
+// A rebuild planned by run_span: its step and the buffer parities right
+// after its binning (the state a resume after an overflow starts from).
+struct PlannedRebuild {
+    int64_t step;
+    int xb_after_bin, pb;
+};
+
+// Plans steps (first .. last) and executes them; `kd` = the drift to x_first
+// is still to be done.
+int run_span(md_ctx *c, int64_t s0, int64_t first, int64_t last, bool kd, int32_t energy_every,
+             std::vector<PlannedRebuild> *rebuilds)
+{
+    const int64_t every = c->p.rebuild_every;
+    std::vector<Op> seg;
+    if (kd) seg.push_back({Op::KD, first, false, false});
+    for (int64_t nstep = first; nstep <= last; nstep++) {
+        const bool rebuild = (nstep % every) == 0;
+        if (rebuild) {
+            if (!seg.empty()) {
+                int rc = run_segment(c, seg);
+                if (rc) return rc;
+                seg.clear();
+            }
+            seg.push_back({Op::REBUILD, nstep, false, false});
+            rebuilds->push_back({nstep, 1 - c->xb, c->pb});
+        }
+        // energies are logged every energy_every steps counted from the run's start
+        const bool en = energy_every > 0 && ((nstep - s0) % energy_every) == 0;
+        seg.push_back({Op::FORCE, nstep, nstep == last, en});
+    }
+    if (!seg.empty()) return run_segment(c, seg);
+    return MD_OK;
+}
+
+int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64_t *counts,
+                 int32_t nrep, const double *pos, const double *vel, void *stream);
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Public ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *md_last_error(const md_ctx *c)
+{
+    return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+int md_create_batch(int32_t nrep, const md_box *boxes, const md_params *p, const int64_t *counts,
+                    const double *pos, const double *vel, void *stream, md_ctx **out)
+{
+    if (!out) return fail(nullptr, MD_ERR_INVAL, "out is NULL");
+    *out = nullptr;
+    md_ctx *c = new (std::nothrow) md_ctx();
+    if (!c) return fail(nullptr, MD_ERR_NOMEM, "host allocation failed");
+    int rc = make_context(c, boxes, p, counts, nrep, pos, vel, stream);
+    if (rc) {
+        g_create_error = c->err;
+        free_all(c);
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return MD_OK;
+}
+
+int md_create(const md_box *box, const md_params *p, int64_t n, const double *pos,
+              const double *vel, void *stream, md_ctx **out)
+{
+    return md_create_batch(1, box, p, &n, pos, vel, stream, out);
+}
+
+void md_destroy(md_ctx *c)
+{
+    if (!c) return;
+    if (c->st) cudaStreamSynchronize(c->st);
+    free_all(c);
+    delete c;
+}
+
+int md_set_state(md_ctx *c, const double *pos, const double *vel)
+{
+    if (!c || !pos || !vel) return fail(c, MD_ERR_INVAL, "null argument");
+    for (int64_t t = 0; t < 3 * c->n; t++)
+        if (!std::isfinite(pos[t]) || !std::isfinite(vel[t]))
+            return fail(c, MD_ERR_NONFINITE, "non-finite input");
+    const size_t bytes = sizeof(double) * 3 * (size_t)c->n;
+    CK(cudaMemcpyAsync(c->io_d, pos, bytes, cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->io_d + 3 * c->n, vel, bytes, cudaMemcpyHostToDevice, c->st));
+    c->xb = 0;
+    c->pb = 0;
+    int nl = 0;
+    Dev d = view(c);
+    if (launch_scatter_in(d, c->io_d, c->io_d + 3 * c->n, c->st, &nl))
+        return fail(c, MD_ERR_CUDA, "upload launch failed");
+    c->launches += nl;
+    CK(cudaMemsetAsync(c->status, 0, sizeof(DevStatus), c->st));
+    c->moved_since_bin = true;
+    c->list_valid = false;
+    c->forces_valid = false;
+    int rc = rebuild_now(c, true);
+    if (rc) return rc;
+    return ensure_forces(c);
+}
+
+int md_bin_cells(md_ctx *c)
+{
+    if (!c) return fail(c, MD_ERR_INVAL, "null context");
+    int nl = 0;
+    int rc = enq_bin(c, &nl);
+    c->launches += nl;
+    if (rc) return rc;
+    DevStatus s;
+    if ((rc = read_status(c, &s))) return rc;
+    return check_flags(c, s);
+}
+
+int md_build_neighbors(md_ctx *c)
+{
+    if (!c) return fail(c, MD_ERR_INVAL, "null context");
+    return rebuild_now(c, c->moved_since_bin);
+}
+
+int md_compute_forces(md_ctx *c)
+{
+    if (!c) return fail(c, MD_ERR_INVAL, "null context");
+    int rc = ensure_list(c);
+    if (rc) return rc;
+    int nl = 0;
+    rc = enq_force(c, EPI_F, false, &nl);
+    c->launches += nl;
+    return rc;
+}
+
+int md_integrate(md_ctx *c, int32_t phase)
+{
+    if (!c) return fail(c, MD_ERR_INVAL, "null context");
+    if (phase != 1 && phase != 2) return fail(c, MD_ERR_INVAL, "phase must be 1 or 2");
+    int rc = ensure_forces(c);
+    if (rc) return rc;
+    int nl = 0;
+    Dev d = view(c);
+    if (launch_integrate(d, c->lj, c->p.precision, phase, batched(c), c->st, &nl))
+        return fail(c, MD_ERR_CUDA, "integrate launch failed");
+    c->launches += nl;
+    if (phase == 1) {
+        c->moved_since_bin = true;
+        c->forces_valid = false;
+    } else {
+        c->step++;
+    }
+    return MD_OK;
+}
+
+int md_energy(md_ctx *c, double *pe, double *ke, double *w)
+{
+    if (!c) return fail(c, MD_ERR_INVAL, "null context");
+    int rc = ensure_list(c);
+    if (rc) return rc;
+    int nl = 0;
+    if ((rc = enq_force(c, EPI_F, true, &nl))) return rc;
+    if ((rc = enq_energy(c, true, c->eout_d, &nl))) return rc;
+    c->launches += nl;
+    std::vector<double> h(3 * (size_t)c->nrep);
+    CK(cudaMemcpyAsync(h.data(), c->eout_d, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    for (int32_t r = 0; r < c->nrep; r++) {
+        if (pe) pe[r] = h[3 * r + 0];
+        if (ke) ke[r] = h[3 * r + 1];
+        if (w) w[r] = h[3 * r + 2];
+    }
+    return MD_OK;
+}
+
+int md_run(md_ctx *c, int64_t nsteps, int32_t energy_every, double *energies)
+{
+    if (!c || nsteps < 0) return fail(c, MD_ERR_INVAL, "bad argument");
+    if (nsteps == 0) return MD_OK;
+    const bool log = energies && energy_every > 0;
+    const int32_t ev = log ? energy_every : 0;
+    int rc = ensure_forces(c);
+    if (rc) return rc;
+    const int64_t nlog = log ? nsteps / energy_every : 0;
+    if (log) {
+        if (nlog > c->elog_cap) {
+            if (c->elog_d) cudaFree(c->elog_d);
+            c->elog_d = nullptr;
+            if ((rc = dalloc(c, &c->elog_d, (size_t)nlog * 3 * c->nrep))) return rc;
+            c->elog_cap = nlog;
+            for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+            c->graphs.clear();
+        }
+        CK(cudaMemsetAsync(&c->status->elog_cursor, 0, sizeof(int64_t), c->st));
+    }
+    const int64_t s0 = c->step;
+    int64_t first = s0 + 1;
+    const int64_t last = s0 + nsteps;
+    bool kd = true;
+    for (int attempt = 0; attempt < 8; attempt++) {
+        std::vector<PlannedRebuild> planned;
+        CK(cudaMemsetAsync(&c->status->rebuild_count, 0, sizeof(int64_t), c->st));
+        if ((rc = run_span(c, s0, first, last, kd, ev, &planned))) return rc;
+        DevStatus s;
+        if ((rc = read_status(c, &s))) return rc;
+        if ((rc = check_flags(c, s))) return rc;
+        if (!(s.flags & FLAG_NL_OVERFLOW)) {
+            if (!planned.empty()) c->last_max = s.max_count;
+            c->step = last;
+            if (log) {
+                CK(cudaMemcpyAsync(energies, c->elog_d, sizeof(double) * 3 * c->nrep * nlog,
+                                   cudaMemcpyDeviceToHost, c->st));
+                CK(cudaStreamSynchronize(c->st));
+            }
+            return MD_OK;
+        }
+        // The k-th rebuild of this span overflowed and every kernel after it
+        // returned at once: the device state is x_n (drifted, binned), v at
+        // the half step.  Grow the list and resume at that rebuild.
+        const int64_t k = s.overflow_at;
+        if (k < 1 || k > (int64_t)planned.size())
+            return fail(c, MD_ERR_NL_OVERFLOW, "list overflow at an unknown rebuild");
+        const PlannedRebuild &pr = planned[(size_t)k - 1];
+        c->xb = pr.xb_after_bin;
+        c->pb = pr.pb;
+        c->moved_since_bin = false;
+        c->list_valid = false;
+        c->forces_valid = false;
+        CK(cudaMemsetAsync(&c->status->flags, 0, sizeof(int32_t), c->st));
+        if ((rc = grow_list(c, s.max_count))) return rc;
+        if (log) {
+            int64_t before = 0;
+            for (int64_t t = s0 + 1; t < pr.step; t++) before += ((t - s0) % ev) == 0;
+            CK(cudaMemcpyAsync(&c->status->elog_cursor, &before, sizeof(int64_t),
+                               cudaMemcpyHostToDevice, c->st));
+            CK(cudaStreamSynchronize(c->st));
+        }
+        first = pr.step;
+        kd = false;
+    }
+    return fail(c, MD_ERR_NL_OVERFLOW, "neighbour list kept overflowing");
+}
+
+int md_get_positions(md_ctx *c, double *out)
+{
+    if (!c || !out) return fail(c, MD_ERR_INVAL, "null argument");
+    int nl = 0;
+    if (launch_gather_out(view(c), 0, c->io_d, c->st, &nl)) return fail(c, MD_ERR_CUDA, "gather failed");
+    c->launches += nl;
+    CK(cudaMemcpyAsync(out, c->io_d, sizeof(double) * 3 * c->n, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return MD_OK;
+}
+
+int md_get_velocities(md_ctx *c, double *out)
+{
+    if (!c || !out) return fail(c, MD_ERR_INVAL, "null argument");
+    int nl = 0;
+    if (launch_gather_out(view(c), 1, c->io_d, c->st, &nl)) return fail(c, MD_ERR_CUDA, "gather failed");
+    c->launches += nl;
+    CK(cudaMemcpyAsync(out, c->io_d, sizeof(double) * 3 * c->n, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return MD_OK;
+}
+
+int md_get_forces(md_ctx *c, double *out)
+{
+    if (!c || !out) return fail(c, MD_ERR_INVAL, "null argument");
+    int rc = ensure_forces(c);
+    if (rc) return rc;
+    int nl = 0;
+    if (launch_gather_out(view(c), is_mixed(c) ? 3 : 2, c->io_d, c->st, &nl))
+        return fail(c, MD_ERR_CUDA, "gather failed");
+    c->launches += nl;
+    CK(cudaMemcpyAsync(out, c->io_d, sizeof(double) * 3 * c->n, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return MD_OK;
+}
+
+int md_get_cells(md_ctx *c, int32_t *cell_start, int32_t *cell_atoms)
+{
+    if (!c || !cell_start || !cell_atoms) return fail(c, MD_ERR_INVAL, "null argument");
+    std::vector<int32_t> cs((size_t)c->ncells + 1), ids((size_t)c->n);
+    CK(cudaMemcpyAsync(cs.data(), c->cell_start, sizeof(int32_t) * cs.size(), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(ids.data(), c->id[c->xb], sizeof(int32_t) * ids.size(), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    int64_t o = 0;
+    for (int32_t r = 0; r < c->nrep; r++) {
+        const Rep &R = c->reps_h[r];
+        const int64_t nc = (int64_t)R.nc[0] * R.nc[1] * R.nc[2];
+        for (int64_t k = 0; k <= nc; k++) cell_start[o++] = (int32_t)(cs[R.cell_off + k] - R.atom_off);
+        for (int64_t a = R.atom_off; a < R.atom_off + R.natoms; a++) cell_atoms[a] = (int32_t)(ids[a] - R.atom_off);
+    }
+    return MD_OK;
+}
+
+int md_get_neighbors(md_ctx *c, int32_t *counts, int32_t *rows, int32_t cap)
+{
+    if (!c || !counts || !rows || cap <= 0) return fail(c, MD_ERR_INVAL, "bad argument");
+    int rc = ensure_list(c);
+    if (rc) return rc;
+    std::vector<int32_t> cnt((size_t)c->n), ids((size_t)c->n);
+    CK(cudaMemcpyAsync(cnt.data(), c->nb_count, sizeof(int32_t) * c->n, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(ids.data(), c->id[c->xb], sizeof(int32_t) * c->n, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    for (int64_t a = 0; a < c->n; a++) {
+        if (cnt[a] > cap) return fail(c, MD_ERR_INVAL, "a row is longer than cap");
+        counts[ids[a]] = cnt[a];
+    }
+    int32_t *rows_d = nullptr;
+    if ((rc = dalloc(c, &rows_d, (size_t)c->n * (size_t)cap))) return rc;
+    int nl = 0;
+    if (launch_decode_list(view(c), rows_d, cap, c->st, &nl)) {
+        cudaFree(rows_d);
+        return fail(c, MD_ERR_CUDA, "decode failed");
+    }
+    c->launches += nl;
+    cudaError_t e = cudaMemcpyAsync(rows, rows_d, sizeof(int32_t) * c->n * cap, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    cudaFree(rows_d);
+    if (e != cudaSuccess) return fail(c, MD_ERR_CUDA, cudaGetErrorString(e));
+    return MD_OK;
+}
+
+int md_get_info(md_ctx *c, md_info *info)
+{
+    if (!c || !info) return fail(c, MD_ERR_INVAL, "null argument");
+    info->n = c->n;
+    info->nrep = c->nrep;
+    info->precision = c->p.precision;
+    info->half_list = c->p.half_list;
+    info->threads_per_atom = c->tpa;
+    info->list_capacity = c->cap;
+    info->max_neighbors = c->last_max;
+    info->ncells = c->ncells;
+    info->step = c->step;
+    info->kernel_launches = c->launches;
+    info->rebuilds = c->rebuilds;
+    return MD_OK;
+}
+
+int md_set_capacity(md_ctx *c, int32_t cap)
+{
+    if (!c || cap < 4) return fail(c, MD_ERR_INVAL, "bad argument");
+    CK(cudaStreamSynchronize(c->st));
+    int rc = alloc_list(c, cap);
+    if (rc) return rc;
+    c->list_valid = false;
+    c->forces_valid = false;
+    return rebuild_now(c, c->moved_since_bin);
+}
+
+int md_autotune(md_ctx *c, int32_t steps, md_params *chosen)
+{
+    (void)steps;
+    if (!c) return fail(c, MD_ERR_INVAL, "null context");
+    if (chosen) {
+        *chosen = c->p;
+        chosen->threads_per_atom = c->tpa;
+    }
+    return MD_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Context construction
+// ---------------------------------------------------------------------------
+namespace {
+
+int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64_t *counts,
+                 int32_t nrep, const double *pos, const double *vel, void *stream)
+{
+    if (!boxes || !p || !counts || !pos || !vel || nrep <= 0)
+        return fail(c, MD_ERR_INVAL, "null argument or nrep <= 0");
+    const md_params &q = *p;
+    if (!(q.epsilon > 0) || !(q.sigma > 0) || !(q.mass > 0) || !(q.cutoff > 0) || !(q.skin >= 0) ||
+        !(q.dt > 0) || q.rebuild_every < 1 || (q.precision != MD_FP64 && q.precision != MD_MIXED) ||
+        (q.half_list != 0 && q.half_list != 1) ||
+        !(q.threads_per_atom == 0 || q.threads_per_atom == 1 || q.threads_per_atom == 2 ||
+          q.threads_per_atom == 4))
+        return fail(c, MD_ERR_INVAL, "invalid md_params");
+    c->p = q;
+    c->nrep = nrep;
+    c->tpa = q.threads_per_atom ? q.threads_per_atom : 1;
+    const double rs = q.cutoff + q.skin;
+    int64_t n = 0, cells = 0;
+    double maxrho = 0;
+    int64_t maxn = 0;
+    c->reps_h.resize(nrep);
+    c->counts_h.assign(counts, counts + nrep);
+    std::vector<int64_t> chunk_rep, chunk_first;
+    for (int32_t r = 0; r < nrep; r++) {
+        if (counts[r] <= 0) return fail(c, MD_ERR_INVAL, "a replica has no atoms");
+        const double L[3] = {boxes[r].lx, boxes[r].ly, boxes[r].lz};
+        Rep R{};
+        double vol = 1;
+        for (int d = 0; d < 3; d++) {
+            if (!std::isfinite(L[d]) || !(L[d] > 0)) return fail(c, MD_ERR_INVAL, "invalid box");
+            if (!(L[d] >= 2.0 * rs)) return fail(c, MD_ERR_BOX_TOO_SMALL, "box smaller than 2 (rc + skin)");
+            R.L[d] = L[d];
+            R.halfL[d] = 0.5 * L[d];
+            R.nc[d] = (int32_t)std::floor(L[d] / rs);
+            if (R.nc[d] > kMaxNc) return fail(c, MD_ERR_INVAL, "more than 1023 cells along a box edge");
+            R.s[d] = L[d] / (double)R.nc[d];
+            R.nsf[d] = -(float)R.s[d];
+            vol *= L[d];
+        }
+        R.cell_off = cells;
+        R.atom_off = n;
+        R.natoms = counts[r];
+        cells += (int64_t)R.nc[0] * R.nc[1] * R.nc[2];
+        chunk_first.push_back((int64_t)chunk_rep.size() / 2);
+        for (int64_t k = 0; k < energy_chunks_of(counts[r]); k++) {
+            chunk_rep.push_back(r);
+            chunk_rep.push_back(k);
+        }
+        n += counts[r];
+        maxrho = std::max(maxrho, counts[r] / vol);
+        maxn = std::max(maxn, counts[r]);
+        c->reps_h[r] = R;
+    }
+    chunk_first.push_back((int64_t)chunk_rep.size() / 2);
+    if (n > (int64_t)kJMask) return fail(c, MD_ERR_INVAL, "too many atoms for 27-bit indices");
+    if (cells >= (int64_t)1 << 31) return fail(c, MD_ERR_INVAL, "too many cells");
+    for (int64_t t = 0; t < 3 * n; t++)
+        if (!std::isfinite(pos[t]) || !std::isfinite(vel[t]))
+            return fail(c, MD_ERR_NONFINITE, "non-finite input");
+    c->n = n;
+    c->ncells = cells;
+    c->nchunks = (int64_t)chunk_rep.size() / 2;
+
+    // LJ constants (the same expressions as the FP64 definition).
+    LJ &lj = c->lj;
+    lj.rc2 = q.cutoff * q.cutoff;
+    lj.rs2 = rs * rs;
+    const double s2 = q.sigma * q.sigma;
+    lj.sigma6 = s2 * s2 * s2;
+    lj.c48e = 48.0 * q.epsilon;
+    lj.c4e = 4.0 * q.epsilon;
+    lj.eps = q.epsilon;
+    lj.rc2f = (float)lj.rc2;
+    lj.sigma6f = (float)lj.sigma6;
+    lj.c48ef = (float)lj.c48e;
+    lj.c4ef = (float)lj.c4e;
+    lj.half_dt_m = 0.5 * q.dt / q.mass;
+    lj.dt = q.dt;
+    lj.mass = q.mass;
+    lj.rs2f_lo = (float)(lj.rs2 * (1.0 - 2.5e-4));
+    lj.rs2f_hi = (float)(lj.rs2 * (1.0 + 2.5e-4));
+
+    CK(cudaGetDevice(&c->device));
+    if (stream) {
+        c->st = (cudaStream_t)stream;
+    } else {
+        CK(cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking));
+        c->own_stream = true;
+    }
+
+    int rc;
+    const size_t N = (size_t)n;
+    if ((rc = dalloc(c, &c->reps_d, nrep))) return rc;
+    if ((rc = dalloc(c, &c->rep_of_d, N))) return rc;
+    for (int b = 0; b < 2; b++) {
+        if ((rc = dalloc(c, &c->x[b], N))) return rc;
+        if ((rc = dalloc(c, &c->v[b], N))) return rc;
+        if ((rc = dalloc(c, &c->id[b], N))) return rc;
+        if ((rc = dalloc(c, &c->p32[b], N))) return rc;
+    }
+    if ((rc = dalloc(c, &c->f32, N))) return rc;
+    if ((rc = dalloc(c, &c->f64, N))) return rc;
+    if ((rc = dalloc(c, &c->cell_key, N))) return rc;
+    if ((rc = dalloc(c, &c->cell_count, (size_t)cells))) return rc;
+    if ((rc = dalloc(c, &c->cell_start, (size_t)cells + 1))) return rc;
+    if ((rc = dalloc(c, &c->perm, N))) return rc;
+    c->scan_len = scan_tmp_elems(cells);
+    if ((rc = dalloc(c, &c->scan_tmp, (size_t)c->scan_len))) return rc;
+    if ((rc = dalloc(c, &c->nb_count, N))) return rc;
+    if ((rc = dalloc(c, &c->pe_atom, N))) return rc;
+    if ((rc = dalloc(c, &c->w_atom, N))) return rc;
+    if ((rc = dalloc(c, &c->pe64, N))) return rc;
+    if ((rc = dalloc(c, &c->w64, N))) return rc;
+    if ((rc = dalloc(c, &c->ke64, N))) return rc;
+    if ((rc = dalloc(c, &c->status, 1))) return rc;
+    if ((rc = dalloc(c, &c->chunk_rep_d, chunk_rep.size()))) return rc;
+    if ((rc = dalloc(c, &c->chunk_first_d, chunk_first.size()))) return rc;
+    if ((rc = dalloc(c, &c->partials_d, 3 * (size_t)c->nchunks))) return rc;
+    if ((rc = dalloc(c, &c->eout_d, 3 * (size_t)nrep))) return rc;
+    if ((rc = dalloc(c, &c->io_d, 6 * N))) return rc;
+
+    std::vector<int32_t> rep_of(N);
+    for (int32_t r = 0; r < nrep; r++)
+        for (int64_t a = 0; a < counts[r]; a++) rep_of[(size_t)(c->reps_h[r].atom_off + a)] = r;
+    CK(cudaMemcpyAsync(c->reps_d, c->reps_h.data(), sizeof(Rep) * nrep, cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->rep_of_d, rep_of.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->chunk_rep_d, chunk_rep.data(), sizeof(int64_t) * chunk_rep.size(), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->chunk_first_d, chunk_first.data(), sizeof(int64_t) * chunk_first.size(), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemsetAsync(c->cell_count, 0, sizeof(int32_t) * (size_t)cells, c->st));
+    CK(cudaMemsetAsync(c->status, 0, sizeof(DevStatus), c->st));
+    CK(cudaMemsetAsync(c->f32, 0, sizeof(float4) * N, c->st));
+    CK(cudaMemsetAsync(c->f64, 0, sizeof(dvec4) * N, c->st));
+    CK(cudaStreamSynchronize(c->st));
+
+    // Initial capacity: expected full-list count at the densest replica with
+    // margin, never more than the replica's size allows.
+    const double expect = maxrho * 4.0 / 3.0 * M_PI * rs * rs * rs * (q.half_list ? 0.5 : 1.0);
+    int64_t cap0 = (int64_t)(1.3 * expect) + 16;
+    cap0 = std::min<int64_t>(cap0, maxn + 3);
+    if ((rc = alloc_list(c, (int32_t)std::max<int64_t>(cap0, 4)))) return rc;
+    return md_set_state(c, pos, vel);
+}
+
+}  // namespace

@@ -1,0 +1,123 @@
+// Internal declarations shared by the kernels and the host runtime of the
+// GB300 LJ MD library.  Nothing here is part of the public ABI (include/md.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mdk {
+
+// FP64 3-vectors are stored padded to 32 bytes (one DRAM sector per atom).
+typedef double4_32a dvec4;
+__host__ __device__ __forceinline__ dvec4 mk_dvec4(double x, double y, double z, double w)
+{
+    return make_double4_32a(x, y, z, w);
+}
+#ifdef __CUDACC__
+// Read-only (L1-cached) load of a padded FP64 3-vector.
+__device__ __forceinline__ dvec4 ldg_dvec4(const dvec4 *p)
+{
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    return mk_dvec4(a.x, a.y, b.x, b.y);
+}
+#endif
+
+// A list entry packs the neighbour's slot index (low 27 bits) and its
+// stencil slot (high 5 bits): slot = (ox+1)*9 + (oy+1)*3 + (oz+1) for the
+// cell offset o in {-1,0,1}^3 of the neighbour's periodic image relative to
+// the owner's cell.  Slot 27 marks padding (a self entry far outside rc).
+constexpr int kJBits = 27;
+constexpr uint32_t kJMask = (1u << kJBits) - 1u;
+constexpr int kPadSlot = 27;
+constexpr int kMaxNc = 1023;        // cell coordinates are packed in 10 bits each
+
+// Bits of the device error word.  Every kernel returns immediately while it
+// is non-zero, so the state freezes at the first failure.
+enum : int32_t { FLAG_NL_OVERFLOW = 1, FLAG_NONFINITE = 2, FLAG_BADPOS = 4 };
+
+// Device error word and step bookkeeping (one per context, in device memory).
+struct DevStatus {
+    int32_t flags;
+    int32_t max_count;        // largest list row of the last build (counted even past cap)
+    int64_t rebuild_count;    // binnings run since the host last cleared it
+    int64_t overflow_at;      // rebuild_count when a build overflowed
+    int64_t elog_cursor;      // next record of the on-device energy log
+};
+
+// One periodic replica.
+struct Rep {
+    double L[3];
+    double halfL[3];
+    double s[3];              // cell side L / nc (FP64)
+    float nsf[3];             // -s in FP32 (stencil offsets of the mixed path)
+    int32_t nc[3];
+    int64_t cell_off;         // first global cell id of this replica
+    int64_t atom_off;         // first atom slot of this replica
+    int64_t natoms;
+};
+
+// LJ constants in both precisions.
+struct LJ {
+    double rc2, rs2, sigma6, c48e, c4e, eps;
+    float rc2f, sigma6f, c48ef, c4ef;
+    double half_dt_m;         // dt / (2 m)
+    double dt;
+    double mass;
+    float rs2f_lo, rs2f_hi;   // FP32 prefilter band around rs^2 (exact FP64 test inside)
+};
+
+// Device pointers of one context (passed by value to kernels).
+struct Dev {
+    int64_t n;
+    int32_t nrep;
+    int32_t cap;              // list capacity (multiple of 4)
+    const Rep *reps;
+    const int32_t *rep_of;    // replica of each atom slot (static)
+    dvec4 *x;               // current positions (FP64, .w unused)
+    dvec4 *v;               // current velocities
+    dvec4 *x_alt, *v_alt;   // reorder targets
+    int32_t *id, *id_alt;     // caller id of each slot
+    float4 *p32, *p32_nxt;    // cell-relative FP32 positions; .w = packed cell coords
+    float4 *f32;              // mixed-path forces
+    dvec4 *f64;             // FP64-path forces
+    int32_t *cell_key;        // global cell of each slot (binning scratch)
+    int32_t *cell_count;      // per global cell (returns to zero after scatter)
+    int32_t *cell_start;      // per global cell + 1
+    int32_t *perm;            // scatter target: slot -> old slot
+    int32_t *nb;              // list: int4 chunks, chunk q of atom i at ((q*n)+i)*4
+    int32_t *nb_count;
+    float *pe_atom, *w_atom;  // per-atom energy / virial (mixed)
+    double *pe_atom64, *w_atom64, *ke_atom64;
+    DevStatus *status;
+};
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (defined in the k_*.cu files).
+// ---------------------------------------------------------------------------
+int launch_bin(const Dev &d, int64_t ncells_total, int32_t *scan_tmp, int64_t scan_tmp_len,
+               cudaStream_t st, int *nlaunch);
+int launch_build(const Dev &d, const LJ &lj, bool half, cudaStream_t st, int *nlaunch);
+
+enum Epi : int { EPI_F = 0, EPI_FK = 1, EPI_FKKD = 2 };
+int launch_force(const Dev &d, const LJ &lj, int precision, bool half, int tpa, int epi,
+                 bool energy, bool batched, cudaStream_t st, int *nlaunch);
+int launch_integrate(const Dev &d, const LJ &lj, int precision, int phase, bool batched,
+                     cudaStream_t st, int *nlaunch);
+// out3 != NULL: write (PE, KE, W) per replica there; otherwise append one
+// record to log_base at status->elog_cursor and advance the cursor.
+int launch_energy(const Dev &d, const LJ &lj, int precision, bool ke_from_v,
+                  const int64_t *chunk_rep, const int64_t *chunk_first, int64_t nchunks,
+                  double *partials, double *out3, double *log_base, cudaStream_t st,
+                  int *nlaunch);
+int64_t energy_chunks_of(int64_t natoms);
+// what: 0 positions, 1 velocities, 2 FP64 forces, 3 mixed-path forces
+int launch_gather_out(const Dev &d, int what, double *out_dev, cudaStream_t st, int *nlaunch);
+int launch_scatter_in(const Dev &d, const double *pos_dev, const double *vel_dev,
+                      cudaStream_t st, int *nlaunch);
+int launch_decode_list(const Dev &d, int32_t *rows_dev, int32_t cap, cudaStream_t st,
+                       int *nlaunch);
+
+int64_t scan_tmp_elems(int64_t ncells_total);
+
+}  // namespace mdk

@@ -1,0 +1,264 @@
+"""Thin ctypes binding of the C ABI in ``include/md.h`` (same names).
+
+Argument marshalling only: every step of the MD path runs in the CUDA
+library ``libmdgb300.so``.  There is no fallback; if the library is missing
+or cannot be loaded the import of a context raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmdgb300.so")
+
+MD_OK = 0
+ERRORS = {
+    -1: "MD_ERR_INVAL", -2: "MD_ERR_BOX_TOO_SMALL", -3: "MD_ERR_NOMEM", -4: "MD_ERR_CUDA",
+    -5: "MD_ERR_NL_OVERFLOW", -6: "MD_ERR_TIMEOUT", -7: "MD_ERR_NONFINITE",
+    -8: "MD_ERR_BADPOS", -9: "MD_ERR_STATE",
+}
+MD_FP64, MD_MIXED = 0, 1
+
+# Every exported entry point of the ABI (checked by the load test).
+ABI_SYMBOLS = [
+    "md_create", "md_create_batch", "md_destroy", "md_last_error", "md_set_state",
+    "md_bin_cells", "md_build_neighbors", "md_compute_forces", "md_integrate", "md_energy",
+    "md_run", "md_get_positions", "md_get_velocities", "md_get_forces", "md_get_cells",
+    "md_get_neighbors", "md_get_info", "md_autotune", "md_set_capacity",
+]
+
+
+class MDError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class md_box(ctypes.Structure):
+    _fields_ = [("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double)]
+
+
+class md_params(ctypes.Structure):
+    _fields_ = [("epsilon", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("mass", ctypes.c_double), ("cutoff", ctypes.c_double),
+                ("skin", ctypes.c_double), ("dt", ctypes.c_double),
+                ("rebuild_every", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("half_list", ctypes.c_int32), ("threads_per_atom", ctypes.c_int32)]
+
+
+class md_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nrep", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("half_list", ctypes.c_int32),
+                ("threads_per_atom", ctypes.c_int32), ("list_capacity", ctypes.c_int32),
+                ("max_neighbors", ctypes.c_int32), ("ncells", ctypes.c_int64),
+                ("step", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("rebuilds", ctypes.c_int64)]
+
+
+_lib = None
+_lock = threading.Lock()
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+_I32 = ctypes.POINTER(ctypes.c_int32)
+_I64 = ctypes.POINTER(ctypes.c_int64)
+
+
+def load(path: str | None = None):
+    """Loads libmdgb300.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(f"CUDA library {p} is missing; run paper_2009_07400_gb300.build")
+            lib = ctypes.CDLL(p)
+            ctx = ctypes.c_void_p
+            sig = {
+                "md_create": [ctypes.POINTER(md_box), ctypes.POINTER(md_params), ctypes.c_int64,
+                              _D, _D, _P, ctypes.POINTER(ctx)],
+                "md_create_batch": [ctypes.c_int32, ctypes.POINTER(md_box),
+                                    ctypes.POINTER(md_params), _I64, _D, _D, _P,
+                                    ctypes.POINTER(ctx)],
+                "md_destroy": [ctx],
+                "md_last_error": [ctx],
+                "md_set_state": [ctx, _D, _D],
+                "md_bin_cells": [ctx],
+                "md_build_neighbors": [ctx],
+                "md_compute_forces": [ctx],
+                "md_integrate": [ctx, ctypes.c_int32],
+                "md_energy": [ctx, _D, _D, _D],
+                "md_run": [ctx, ctypes.c_int64, ctypes.c_int32, _D],
+                "md_get_positions": [ctx, _D],
+                "md_get_velocities": [ctx, _D],
+                "md_get_forces": [ctx, _D],
+                "md_get_cells": [ctx, _I32, _I32],
+                "md_get_neighbors": [ctx, _I32, _I32, ctypes.c_int32],
+                "md_get_info": [ctx, ctypes.POINTER(md_info)],
+                "md_autotune": [ctx, ctypes.c_int32, ctypes.POINTER(md_params)],
+                "md_set_capacity": [ctx, ctypes.c_int32],
+            }
+            for name, args in sig.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = ctypes.c_int
+            lib.md_destroy.restype = None
+            lib.md_last_error.restype = ctypes.c_char_p
+            _lib = lib
+    return _lib
+
+
+def _f64(a, n):
+    a = np.ascontiguousarray(a, dtype=np.float64).reshape(n, 3)
+    return a
+
+
+def make_params(epsilon=1.0, sigma=1.0, mass=1.0, cutoff=2.5, skin=0.3, dt=0.005,
+                rebuild_every=20, precision=MD_FP64, half_list=False, threads_per_atom=0):
+    return md_params(epsilon, sigma, mass, cutoff, skin, dt, int(rebuild_every), int(precision),
+                     int(bool(half_list)), int(threads_per_atom))
+
+
+class MDContext:
+    """One md_ctx: a periodic system (or a batch of replicas) on the GPU."""
+
+    def __init__(self, pos, vel, box, stream=None, counts=None, **params):
+        lib = load()
+        self._lib = lib
+        self.params = make_params(**params)
+        if counts is None:
+            pos = np.asarray(pos, np.float64).reshape(-1, 3)
+            boxes = [np.broadcast_to(np.asarray(box, np.float64), (3,))]
+            counts = [pos.shape[0]]
+        else:
+            boxes = [np.broadcast_to(np.asarray(b, np.float64), (3,)) for b in box]
+        self.counts = np.ascontiguousarray(counts, dtype=np.int64)
+        self.n = int(self.counts.sum())
+        self.nrep = len(self.counts)
+        pos = _f64(pos, self.n)
+        vel = _f64(vel, self.n)
+        barr = (md_box * self.nrep)(*[md_box(*map(float, b)) for b in boxes])
+        h = ctypes.c_void_p()
+        st = ctypes.c_void_p(int(stream)) if stream else None
+        rc = lib.md_create_batch(self.nrep, barr, ctypes.byref(self.params),
+                                 self.counts.ctypes.data_as(_I64), pos.ctypes.data_as(_D),
+                                 vel.ctypes.data_as(_D), st, ctypes.byref(h))
+        if rc != MD_OK:
+            raise MDError(rc, lib.md_last_error(None).decode())
+        self._h = h
+
+    # -- helpers --------------------------------------------------------------
+    def _check(self, rc):
+        if rc != MD_OK:
+            raise MDError(rc, self._lib.md_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.md_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- the ABI --------------------------------------------------------------
+    def set_state(self, pos, vel):
+        pos = _f64(pos, self.n)
+        vel = _f64(vel, self.n)
+        self._check(self._lib.md_set_state(self._h, pos.ctypes.data_as(_D), vel.ctypes.data_as(_D)))
+
+    def bin_cells(self):
+        self._check(self._lib.md_bin_cells(self._h))
+
+    def build_neighbors(self):
+        self._check(self._lib.md_build_neighbors(self._h))
+
+    def compute_forces(self):
+        self._check(self._lib.md_compute_forces(self._h))
+
+    def integrate(self, phase):
+        self._check(self._lib.md_integrate(self._h, int(phase)))
+
+    def energy(self):
+        """(PE, KE, W) arrays of length nrep (FP64)."""
+        pe = np.zeros(self.nrep)
+        ke = np.zeros(self.nrep)
+        w = np.zeros(self.nrep)
+        self._check(self._lib.md_energy(self._h, pe.ctypes.data_as(_D), ke.ctypes.data_as(_D),
+                                        w.ctypes.data_as(_D)))
+        return pe, ke, w
+
+    def run(self, nsteps, energy_every=0):
+        """Advance nsteps; with energy_every > 0 returns (nsteps//every, nrep, 3)."""
+        if energy_every > 0:
+            out = np.zeros((nsteps // energy_every, self.nrep, 3))
+            self._check(self._lib.md_run(self._h, int(nsteps), int(energy_every),
+                                         out.ctypes.data_as(_D)))
+            return out
+        self._check(self._lib.md_run(self._h, int(nsteps), 0, None))
+        return None
+
+    def _get3(self, fn):
+        out = np.zeros((self.n, 3))
+        self._check(fn(self._h, out.ctypes.data_as(_D)))
+        return out
+
+    def positions(self):
+        return self._get3(self._lib.md_get_positions)
+
+    def velocities(self):
+        return self._get3(self._lib.md_get_velocities)
+
+    def forces(self):
+        return self._get3(self._lib.md_get_forces)
+
+    def cells(self):
+        """(cell_start per replica incl. end, cell_atoms replica-local ids)."""
+        info = self.info()
+        start = np.zeros(info.ncells + self.nrep, np.int32)
+        atoms = np.zeros(self.n, np.int32)
+        self._check(self._lib.md_get_cells(self._h, start.ctypes.data_as(_I32),
+                                           atoms.ctypes.data_as(_I32)))
+        return start, atoms
+
+    def neighbors(self):
+        """Per-atom rows (caller order, replica-local ids) of the current list."""
+        cap = max(4, self.info().list_capacity)
+        counts = np.zeros(self.n, np.int32)
+        rows = np.zeros(self.n * cap, np.int32)
+        self._check(self._lib.md_get_neighbors(self._h, counts.ctypes.data_as(_I32),
+                                               rows.ctypes.data_as(_I32), cap))
+        return [rows[i * cap:i * cap + counts[i]].copy() for i in range(self.n)]
+
+    def neighbors_raw(self):
+        """(counts[n], rows[n, cap]) of the current list, caller order."""
+        cap = max(4, self.info().list_capacity)
+        counts = np.zeros(self.n, np.int32)
+        rows = np.zeros((self.n, cap), np.int32)
+        self._check(self._lib.md_get_neighbors(self._h, counts.ctypes.data_as(_I32),
+                                               rows.ctypes.data_as(_I32), cap))
+        return counts, rows
+
+    def set_capacity(self, cap):
+        self._check(self._lib.md_set_capacity(self._h, int(cap)))
+
+    def info(self) -> md_info:
+        inf = md_info()
+        self._check(self._lib.md_get_info(self._h, ctypes.byref(inf)))
+        return inf
+
+    def autotune(self, steps=20) -> md_params:
+        out = md_params()
+        self._check(self._lib.md_autotune(self._h, int(steps), ctypes.byref(out)))
+        return out

@@ -1,0 +1,321 @@
+"""CUDA path vs the FP64 oracle, through the C ABI.
+
+Tolerances (stated by the method's target):
+  * cells and Verlet lists: bit-exact (cells as ordered lists, rows as sets);
+  * FP64 forces: |dF_i| <= 1e-10 max(|F_i|, F_rms) per atom;
+  * mixed forces: sqrt(sum |dF|^2 / sum |F|^2) <= 1e-5 on the same FP64 state;
+  * mixed NVE: |E_mixed(1000) - E_oracle(1000)| / N <= 1e-4.
+"""
+import numpy as np
+import pytest
+
+from paper_2009_07400_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+RC, SKIN = 2.5, 0.3
+
+
+@pytest.fixture(scope="module")
+def md():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2009_07400_gb300 import build
+    build.build()
+    from paper_2009_07400_gb300 import md as m
+    m.load()
+    return m
+
+
+def ctx_of(md, s, **kw):
+    return md.MDContext(s.pos, s.vel, s.box, **kw)
+
+
+def fp64_force_ok(F, Fr):
+    frms = np.sqrt(np.mean(np.sum(Fr ** 2, axis=1)))
+    scale = np.maximum(np.linalg.norm(Fr, axis=1), frms)
+    return np.max(np.linalg.norm(F - Fr, axis=1) / scale)
+
+
+def rms_rel(F, Fr):
+    return np.sqrt(np.sum((F - Fr) ** 2) / np.sum(Fr ** 2))
+
+
+def sorted_rows(counts, rows):
+    big = np.iinfo(np.int32).max
+    width = max(1, int(counts.max()))
+    out = np.full((counts.shape[0], width), big, np.int64)
+    mask = np.arange(width)[None, :] < counts[:, None]
+    out[mask] = rows[:, :width][mask]
+    out.sort(axis=1)
+    return out
+
+
+def assert_lists_equal(orc, ctx, x, L, half):
+    c_g, r_g = ctx.neighbors_raw()
+    c_o, r_o = orc.neighbors_cells_raw(orc.wrap(x, L), L, RC + SKIN, half=half)
+    assert np.array_equal(c_g, c_o)
+    assert np.array_equal(sorted_rows(c_g, r_g), sorted_rows(c_o, r_o))
+
+
+def liquid(orc, n_cells=7, steps=60, seed=3):
+    s = inputs.fcc_system(n_cells, jitter=0.05, seed=seed)
+    x, v, _ = orc.vv_run(s.pos, s.vel, s.box, steps)
+    return inputs.System(x, v, s.box, seed)
+
+
+def band_system(seed=5):
+    """Pairs placed within 1e-15 .. 1e-5 of the list radius (and exactly on
+    it) so that the FP64 decision inside the FP32 band is exercised."""
+    rng = np.random.default_rng(seed)
+    L = np.array([30.0, 31.0, 29.0])
+    rs = RC + SKIN
+    a = rng.uniform(0, 1, size=(120, 3)) * L
+    u = rng.normal(size=(120, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    delta = rng.choice([-1, 1], 120) * 10.0 ** rng.uniform(-15, -5, 120)
+    b = a + rs * (1 + delta)[:, None] * u
+    ax = np.array([[3.0, 4.0, 5.0], [3.0 + rs, 4.0, 5.0]])       # exactly on rs along x
+    pos = np.concatenate([a, b, ax]) % L
+    return inputs.System(pos, np.zeros_like(pos), L, seed)
+
+
+# --------------------------------------------------------------------------
+# Binning (Sec. 3.2, Fig. 1)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", ["fcc8", "uniform_nc2", "aniso", "outside"])
+def test_bin_parity(md, orc, case):
+    if case == "fcc8":
+        s = inputs.fcc_system(8, seed=1001)
+    elif case == "uniform_nc2":
+        s = inputs.uniform_box(300, (5.7, 5.7, 5.7), seed=3)
+    elif case == "aniso":
+        s = inputs.uniform_box(777, (5.7, 9.0, 12.3), seed=4)
+    else:
+        s = inputs.uniform_box(999, (9.0, 10.0, 11.0), seed=5)
+        s.pos[::3] -= s.box          # one box length below
+        s.pos[1::7] += s.box * 0.99  # almost one box length above
+    with ctx_of(md, s) as ctx:
+        start, atoms = ctx.cells()
+        _, o_start, o_atoms = orc.bin_cells(orc.wrap(s.pos, s.box), s.box, RC + SKIN)
+        assert np.array_equal(start, o_start)
+        assert np.array_equal(atoms, o_atoms)
+        assert np.array_equal(ctx.positions(), orc.wrap(s.pos, s.box))
+
+
+# --------------------------------------------------------------------------
+# Verlet lists: bit-exact sets under the FP64 criterion.
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("half", [False, True])
+@pytest.mark.parametrize("case", ["fcc8", "jitter7", "nc2", "aniso", "band", "liquid"])
+def test_list_parity(md, orc, case, half):
+    if case == "fcc8":
+        s = inputs.fcc_system(8, seed=1001)
+    elif case == "jitter7":
+        s = inputs.fcc_system(7, jitter=0.1, seed=8)
+    elif case == "nc2":
+        s = inputs.uniform_box(400, (5.7, 5.7, 5.7), seed=9)
+    elif case == "aniso":
+        s = inputs.uniform_box(900, (5.7, 9.0, 12.3), seed=10)
+    elif case == "band":
+        s = band_system()
+    else:
+        s = liquid(orc)
+    for precision in (md.MD_FP64, md.MD_MIXED):
+        with ctx_of(md, s, half_list=half, precision=precision) as ctx:
+            assert_lists_equal(orc, ctx, s.pos, s.box, half)
+
+
+# --------------------------------------------------------------------------
+# Forces (Sec. 3.2 Eq. 2 / Sec. 4.2 kernel), all list and lane variants.
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("half,tpa", [(False, 1), (False, 2), (False, 4), (True, 1)])
+@pytest.mark.parametrize("case", ["jitter7", "liquid", "ragged"])
+def test_force_parity(md, orc, case, half, tpa):
+    if case == "jitter7":
+        s = inputs.fcc_system(7, jitter=0.1, seed=8)
+    elif case == "liquid":
+        s = liquid(orc)
+    else:
+        s = inputs.replica_system(2999, 0.82, 1.3, seed=12)
+    xw = orc.wrap(s.pos, s.box)
+    Fr = orc.forces_list(xw, s.box, orc.neighbors_cells(xw, s.box, RC + SKIN))
+    with ctx_of(md, s, half_list=half, threads_per_atom=tpa, precision=md.MD_FP64) as ctx:
+        assert fp64_force_ok(ctx.forces(), Fr) <= 1e-10
+    with ctx_of(md, s, half_list=half, threads_per_atom=tpa, precision=md.MD_MIXED) as ctx:
+        assert rms_rel(ctx.forces(), Fr) <= 1e-5
+
+
+def test_force_params(md, orc):
+    s = liquid(orc, n_cells=6)
+    kw = dict(epsilon=1.7, sigma=0.93, cutoff=2.2, skin=0.4)
+    xw = orc.wrap(s.pos, s.box)
+    Fr = orc.forces_list(xw, s.box, orc.neighbors_cells(xw, s.box, 2.6), epsilon=1.7,
+                         sigma=0.93, cutoff=2.2, skin=0.4)
+    with ctx_of(md, s, precision=md.MD_FP64, **kw) as ctx:
+        assert fp64_force_ok(ctx.forces(), Fr) <= 1e-10
+    with ctx_of(md, s, precision=md.MD_MIXED, **kw) as ctx:
+        assert rms_rel(ctx.forces(), Fr) <= 1e-5
+
+
+# --------------------------------------------------------------------------
+# Energies, integration, trajectories.
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("half", [False, True])
+def test_energy_parity(md, orc, half):
+    s = liquid(orc)
+    xw = orc.wrap(s.pos, s.box)
+    pe, w = orc.energy_list(xw, s.box, orc.neighbors_cells(xw, s.box, RC + SKIN, half=True),
+                            half=True)
+    ke = orc.kinetic(s.vel)
+    with ctx_of(md, s, half_list=half, precision=md.MD_FP64) as ctx:
+        gpe, gke, gw = ctx.energy()
+        assert gpe[0] == pytest.approx(pe, rel=1e-12)
+        assert gke[0] == pytest.approx(ke, rel=1e-13)
+        assert gw[0] == pytest.approx(w, rel=1e-11)
+    with ctx_of(md, s, half_list=half, precision=md.MD_MIXED) as ctx:
+        gpe, gke, gw = ctx.energy()
+        assert gpe[0] == pytest.approx(pe, rel=1e-6)
+        assert gke[0] == pytest.approx(ke, rel=1e-13)
+        assert gw[0] == pytest.approx(w, rel=1e-5)
+
+
+def test_integrate_phases(md, orc):
+    """md_integrate(1) then md_compute_forces then md_integrate(2) is one
+    velocity-Verlet step (Eq. 1), as the oracle takes it."""
+    s = liquid(orc, n_cells=6)
+    with ctx_of(md, s, precision=md.MD_FP64) as ctx:
+        for _ in range(3):
+            ctx.integrate(1)
+            ctx.compute_forces()
+            ctx.integrate(2)
+        x_ref, v_ref, F_ref = orc.vv_run(s.pos, s.vel, s.box, 3, rebuild_every=10 ** 6)
+        dx = np.mod(ctx.positions() - x_ref + s.box / 2, s.box) - s.box / 2
+        assert np.abs(dx).max() < 1e-12
+        assert np.abs(ctx.velocities() - v_ref).max() < 1e-11
+        assert fp64_force_ok(ctx.forces(), F_ref) <= 1e-10
+
+
+@pytest.mark.parametrize("half", [False, True])
+def test_run_fp64_matches_oracle(md, orc, half):
+    """100 steps of the 2,048-atom FCC workload (rebuild every 20)."""
+    s = inputs.workload("fcc8_2048")
+    x_ref, v_ref, _, E_ref = orc.vv_run(s.pos, s.vel, s.box, 100, energies=True)
+    with ctx_of(md, s, half_list=half, precision=md.MD_FP64) as ctx:
+        E = ctx.run(100, energy_every=20)
+        dx = np.mod(ctx.positions() - x_ref + s.box / 2, s.box) - s.box / 2
+        assert np.abs(dx).max() < 1e-9
+        assert np.abs(ctx.velocities() - v_ref).max() < 1e-8
+        assert ctx.info().rebuilds >= 6
+        for k in range(5):
+            pe, ke, w = E[k, 0]
+            assert pe == pytest.approx(E_ref[20 * k + 19, 0], rel=1e-10)
+            assert ke == pytest.approx(E_ref[20 * k + 19, 1], rel=1e-10)
+            assert w == pytest.approx(E_ref[20 * k + 19, 2], rel=1e-9)
+
+
+def test_run_chunks_equal_one_run(md, orc):
+    """Splitting a run (graphs of different shapes) changes nothing."""
+    s = liquid(orc, n_cells=6)
+    with ctx_of(md, s, precision=md.MD_MIXED) as a, ctx_of(md, s, precision=md.MD_MIXED) as b:
+        a.run(57)
+        b.run(13)
+        b.run(20)
+        b.run(24)
+        assert np.array_equal(a.positions(), b.positions())
+        assert np.array_equal(a.velocities(), b.velocities())
+
+
+def test_mixed_nve_vs_oracle(md, orc):
+    """Mixed path, 1000 steps: total energy within 1e-4 per atom of the
+    FP64 oracle's (same initial state, both rebuilding every 20 steps)."""
+    s = inputs.workload("fcc8_2048")
+    _, _, _, E_ref = orc.vv_run(s.pos, s.vel, s.box, 1000, energies=True)
+    with ctx_of(md, s, precision=md.MD_MIXED) as ctx:
+        E = ctx.run(1000, energy_every=100)
+    e_gpu = E[-1, 0, 0] + E[-1, 0, 1]
+    e_ref = E_ref[-1, 0] + E_ref[-1, 1]
+    assert abs(e_gpu - e_ref) / s.n <= 1e-4
+
+
+def test_overflow_recovery(md, orc):
+    """A list that overflows at an in-run rebuild is grown and the run
+    resumes at that rebuild: the result equals an undisturbed run."""
+    s = inputs.workload("fcc8_2048")          # every row is 78 at the start
+    with ctx_of(md, s, precision=md.MD_MIXED) as a, ctx_of(md, s, precision=md.MD_MIXED) as b:
+        b.set_capacity(80)
+        assert b.info().list_capacity == 80
+        a.run(100)
+        b.run(100)
+        assert b.info().list_capacity > 80
+        assert np.array_equal(a.positions(), b.positions())
+        assert np.array_equal(a.velocities(), b.velocities())
+
+
+# --------------------------------------------------------------------------
+# Batched replicas (independent systems advanced together).
+# --------------------------------------------------------------------------
+
+def test_batched_replicas(md, orc):
+    reps = inputs.replica_ensemble(6, seed=77, n_min=500, n_max=3000)
+    pos = np.concatenate([r.pos for r in reps])
+    vel = np.concatenate([r.vel for r in reps])
+    counts = [r.n for r in reps]
+    boxes = [r.box for r in reps]
+    for precision in (md.MD_FP64, md.MD_MIXED):
+        with md.MDContext(pos, vel, boxes, counts=counts, precision=precision) as ctx:
+            c_g, r_g = ctx.neighbors_raw()
+            F = ctx.forces()
+            o = 0
+            for r in reps:
+                xw = orc.wrap(r.pos, r.box)
+                c_o, r_o = orc.neighbors_cells_raw(xw, r.box, RC + SKIN)
+                assert np.array_equal(c_g[o:o + r.n], c_o)
+                assert np.array_equal(sorted_rows(c_g[o:o + r.n], r_g[o:o + r.n]),
+                                      sorted_rows(c_o, r_o))
+                Fr = orc.forces_list(xw, r.box, orc.neighbors_cells(xw, r.box, RC + SKIN))
+                if precision == md.MD_FP64:
+                    assert fp64_force_ok(F[o:o + r.n], Fr) <= 1e-10
+                else:
+                    assert rms_rel(F[o:o + r.n], Fr) <= 1e-5
+                o += r.n
+            E = ctx.run(40, energy_every=40)
+            X = ctx.positions()
+            o = 0
+            for k, r in enumerate(reps):
+                x_ref, _, _, E_ref = orc.vv_run(r.pos, r.vel, r.box, 40, energies=True)
+                if precision == md.MD_FP64:
+                    dx = np.mod(X[o:o + r.n] - x_ref + r.box / 2, r.box) - r.box / 2
+                    assert np.abs(dx).max() < 1e-9
+                    assert E[0, k, 0] == pytest.approx(E_ref[-1, 0], rel=1e-10)
+                else:
+                    etot = E[0, k, 0] + E[0, k, 1]
+                    assert abs(etot - E_ref[-1, 0] - E_ref[-1, 1]) / r.n < 1e-5
+                o += r.n
+
+
+# --------------------------------------------------------------------------
+# Full size (1,048,576 atoms, the benchmark workload and launch shape):
+# lists compared whole, forces on sampled atoms, after a graph-replayed cycle.
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_full_size(md, orc, precision):
+    s = inputs.workload("fcc64_1048576")
+    prec = md.MD_FP64 if precision == "fp64" else md.MD_MIXED
+    with ctx_of(md, s, precision=prec) as ctx:
+        ctx.run(20)                              # one rebuild cycle, graph-replayed
+        x = ctx.positions()
+        assert_lists_equal(orc, ctx, x, s.box, False)
+        ids = np.random.default_rng(0).choice(s.n, 4096, replace=False)
+        Fr = orc.forces_sample(x, s.box, ids)
+        F = ctx.forces()[ids]
+        if prec == md.MD_FP64:
+            assert fp64_force_ok(F, Fr) <= 1e-10
+        else:
+            assert rms_rel(F, Fr) <= 1e-5
