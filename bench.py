@@ -1,0 +1,397 @@
+#!/usr/bin/env python3
+"""Benchmark of the LJ MD hot path: atom-timesteps/s on the 1,048,576-atom
+FCC workload (64^3 unit cells, density 0.8442, T = 1.44, +-0.05 sigma jitter,
+rc 2.5, skin 0.3, dt 0.005, rebuild every 20 steps).
+
+One benchmark step = one rebuild cycle: binning + list build + 20 velocity-
+Verlet time steps (force kernel with fused integration), replayed from one
+CUDA graph.  value = atoms x 20 x steps / device time of the timed region
+(mixed path); the FP64 path is timed the same way beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun every rank advances its own replica of the workload (weak
+scaling, no collective on the data path) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2009_07400_gb300 import inputs  # noqa: E402
+
+WORKLOAD = "fcc64_1048576"
+METRIC = "atom-timesteps/s, LJ 1M atoms, mixed-FP32 vs FP64 path at stated force error"
+UNIT = "atom-timesteps/s"
+STEPS_PER_CYCLE = 20
+FORCE_SRC = os.path.join(ROOT, "paper_2009_07400_gb300", "csrc", "k_force.cu")
+PROFILE_MD = os.path.join(ROOT, "profiles", "force_mixed_fcc64.md")
+
+
+def config_dict(s):
+    return {"workload": "LJ 12-6 FCC 64^3 unit cells, 1,048,576 atoms, rho 0.8442, T 1.44, "
+                        "jitter 0.05 sigma, rc 2.5, skin 0.3, dt 0.005, rebuild every 20 steps",
+            "atoms": int(s.n), "timesteps_per_step": STEPS_PER_CYCLE, "list": "full",
+            "l2": "inputs larger than L2: the neighbour list (~0.33 GB) is streamed every "
+                  "time step; positions (16 MB FP32) stay L2-resident by design",
+            "seed": 1003}
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                mhz.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not mhz:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(mhz)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+# --------------------------------------------------------------------------
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic():
+    """DRAM bytes per launch of the mixed force kernel from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    if not os.path.exists(PROFILE_MD):
+        return None
+    text = open(PROFILE_MD).read()
+    h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
+    t = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", text)
+    if not h or not t:
+        return None
+    cur = hashlib.sha256(open(FORCE_SRC, "rb").read()).hexdigest()
+    return float(t.group(1)) if h.group(1) == cur else None
+
+
+def algorithmic_bytes_per_atom(mean_nb):
+    """Mixed force kernel with the fused velocity-Verlet epilogue, per atom
+    and time step: the 4-byte list entries, the row length, the FP32
+    position read and the next step's FP32 position write (16 + 16), and
+    read + write of FP64 position and velocity (24 B each way, 3 doubles).
+    Neighbour positions are gathered from L2 and not counted."""
+    return 4.0 * mean_nb + 4 + 16 + 16 + 2 * 24 + 2 * 24
+
+
+def time_cycles(ctx, steps, warmup, dist, torch):
+    """Device time of `steps` rebuild cycles after `warmup` ones (CUDA events
+    on the context's stream, barrier + synchronize on both sides)."""
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        ctx.run(STEPS_PER_CYCLE)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    l0 = ctx.info().kernel_launches
+    start.record(stream)
+    ctx.run(STEPS_PER_CYCLE * steps)
+    end.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = start.elapsed_time(end)
+    return ms, ctx.info().kernel_launches - l0
+
+
+def run_gpu(args):
+    import torch
+
+    from paper_2009_07400_gb300 import build, md
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as td
+        td.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        dist = td
+    torch.cuda.set_device(local)
+    build.build()
+    md.load()
+    s = inputs.workload(WORKLOAD)
+    # The C library enqueues on its own stream (a stream handle of 0 means:
+    # create one); events are recorded on torch's stream, so synchronise the
+    # context stream through the library before stopping the clock: md_run
+    # already synchronises at its end.
+    res = {}
+    with md.MDContext(s.pos, s.vel, s.box, precision=md.MD_MIXED) as ctx:
+        with ClockSampler(local) as clk:
+            ms, launches = time_cycles(ctx, args.steps, args.warmup, dist, torch)
+        res["mixed_ms"] = ms
+        res["launches"] = launches
+        res["clocks"] = clk.summary()
+        prof = ctx.profile(2 * STEPS_PER_CYCLE)
+        res["prof"] = prof
+        res["mixed_state"] = (ctx.positions(), ctx.forces())
+    fp64_cycles = max(1, min(args.steps, 3))
+    with md.MDContext(s.pos, s.vel, s.box, precision=md.MD_FP64) as ctx:
+        ms64, _ = time_cycles(ctx, fp64_cycles, 1, dist, torch)
+        res["fp64_ms"] = ms64 / fp64_cycles
+        prof64 = ctx.profile(STEPS_PER_CYCLE)
+        res["prof64"] = prof64
+        res["fp64_state"] = (ctx.positions(), ctx.forces())
+    # end to end: host state in pinned memory -> md_set_state -> one cycle ->
+    # energies back to the host, every step
+    pin_pos = torch.empty((s.n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    pin_vel = torch.empty((s.n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    pin_pos[:] = s.pos
+    pin_vel[:] = s.vel
+    with md.MDContext(s.pos, s.vel, s.box, precision=md.MD_MIXED) as ctx:
+        for _ in range(2):
+            ctx.set_state(pin_pos, pin_vel)
+            ctx.run(STEPS_PER_CYCLE, energy_every=STEPS_PER_CYCLE)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        e_steps = max(3, args.steps // 5)
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            ctx.set_state(pin_pos, pin_vel)
+            ctx.run(STEPS_PER_CYCLE, energy_every=STEPS_PER_CYCLE)
+        e2e_s = time.perf_counter() - t0
+        if dist:
+            dist.barrier()
+    res["e2e"] = (e2e_s, e_steps)
+
+    # max over ranks
+    times = [res["mixed_ms"], res["fp64_ms"], res["e2e"][0]]
+    if dist:
+        t = torch.tensor(times, dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        times = t.tolist()
+    mixed_ms, fp64_ms, e2e_s = times
+    n_total = s.n * world
+    value = n_total * STEPS_PER_CYCLE * args.steps / (mixed_ms / 1e3)
+    fp64_value = n_total * STEPS_PER_CYCLE / (fp64_ms / 1e3)
+    e2e_value = n_total * STEPS_PER_CYCLE * res["e2e"][1] / e2e_s
+    if rank == 0:
+        prof = res["prof"]
+        force_ms_per_launch = prof.force_ms / max(1, prof.force_launches)
+        bpa = algorithmic_bytes_per_atom(prof.mean_neighbors)
+        achieved = bpa * s.n / (force_ms_per_launch / 1e3) / 1e9
+        peak, peak_kind = measured_peaks()
+        traffic = ncu_traffic()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": mixed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64 (mixed: FP32 pair arithmetic, Kahan sums, "
+                                          "FP64 integration and reductions)",
+            "data": "synthetic", "config": config_dict(s),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_force_mixed_full (fused velocity-Verlet epilogue)",
+                         "bytes_per_atom": bpa, "mean_neighbors": prof.mean_neighbors,
+                         "launch_ms": force_ms_per_launch, "peak_source": peak_kind},
+            "phases_ms_per_timestep": {
+                "force": prof.force_ms / prof.steps, "neigh": prof.neigh_ms / prof.steps,
+                "other": prof.other_ms / prof.steps},
+            "fp64_path": {"value": fp64_value, "ms_per_step": fp64_ms,
+                          "phases_ms_per_timestep": {
+                              "force": res["prof64"].force_ms / res["prof64"].steps,
+                              "neigh": res["prof64"].neigh_ms / res["prof64"].steps,
+                              "other": res["prof64"].other_ms / res["prof64"].steps}},
+            "speedup_mixed_over_fp64": value / fp64_value,
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": int(2 * 3 * 8 * s.n),
+                    "d2h_bytes_per_step": int(3 * 8)},
+            "gpu_launches": int(res["launches"]),
+            "clocks": res["clocks"],
+        }
+        if not args.no_cpu_baseline:
+            line.update(cpu_baseline_leg(s, res))
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------
+# CPU baseline leg: the FP64 oracle as it stands, on this host's cores, on a
+# bounded sample of the same workload; it also states the force error of
+# both GPU paths against the oracle on sampled atoms.
+# --------------------------------------------------------------------------
+def oracle_rate(s, nsteps=4):
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.vv_run(s.pos, s.vel, s.box, 0)            # wrap + bin + build + one force pass
+    t_build_force = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.vv_run(s.pos, s.vel, s.box, nsteps)
+    t_run = time.perf_counter() - t0
+    t_step = (t_run - t_build_force) / nsteps
+    t_build = max(t_build_force - t_step, 0.0)
+    rate = s.n * STEPS_PER_CYCLE / (t_build + STEPS_PER_CYCLE * t_step)
+    return rate, t_step, t_build, oracle.num_threads()
+
+
+def cpu_baseline_leg(s, res):
+    import oracle
+    rate, t_step, t_build, cores = oracle_rate(s)
+    out = {"cpu_baseline": {
+        "value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+        "sample": f"FP64 C oracle (OpenMP, {cores} threads) on the full 1,048,576-atom "
+                  f"workload: one list build ({t_build:.2f} s) and 4 velocity-Verlet steps "
+                  f"({t_step:.3f} s each), rate = atoms x 20 / (build + 20 steps)"}}
+    rng = np.random.default_rng(0)
+    errs = {}
+    for key, name in (("mixed_state", "mixed_rms_rel"), ("fp64_state", "fp64_max_rel")):
+        x, F = res[key]
+        ids = rng.choice(s.n, 2048, replace=False)
+        Fr = oracle.forces_sample(x, s.box, ids)
+        Fg = F[ids]
+        if name == "mixed_rms_rel":
+            errs[name] = float(np.sqrt(np.sum((Fg - Fr) ** 2) / np.sum(Fr ** 2)))
+        else:
+            frms = np.sqrt(np.mean(np.sum(Fr ** 2, axis=1)))
+            sc = np.maximum(np.linalg.norm(Fr, axis=1), frms)
+            errs[name] = float(np.max(np.linalg.norm(Fg - Fr, axis=1) / sc))
+    errs["sample"] = "2048 random atoms after the timed runs, plain-definition oracle forces"
+    out["force_error"] = errs
+    return out
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle, as it stands, on the host cores;
+    each step is one oracle time step of the full workload with the list
+    build amortised over 20 steps."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    s = inputs.workload(WORKLOAD)
+    t0 = time.perf_counter()
+    x, v, _ = oracle.vv_run(s.pos, s.vel, s.box, 0)
+    t_build = time.perf_counter() - t0
+    x, v, _ = oracle.vv_run(x, v, s.box, max(1, args.warmup))
+    t0 = time.perf_counter()
+    oracle.vv_run(x, v, s.box, args.steps)
+    t_steps = time.perf_counter() - t0 - t_build
+    t_step = max(t_steps / args.steps, 1e-9)
+    per_step = t_step + t_build / STEPS_PER_CYCLE
+    value = s.n / per_step
+    cores = oracle.num_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": int(os.environ.get("WORLD_SIZE", args.gpus)), "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(s),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} oracle time steps of the full workload "
+                                       f"after {max(1, args.warmup)} warm-up steps; list "
+                                       f"build ({t_build:.2f} s) amortised over 20 steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ncu_case(which):
+    """Create the workload's context and run 2 cycles: 1 first drift, then
+    per cycle 19 fused steps, a rebuild (6 binning kernels + build) and the
+    20th fused step."""
+    import torch
+
+    from paper_2009_07400_gb300 import build, md
+    torch.cuda.set_device(0)
+    build.build()
+    s = inputs.workload(WORKLOAD)
+    prec = md.MD_MIXED if which == "mixed" else md.MD_FP64
+    with md.MDContext(s.pos, s.vel, s.box, precision=prec) as ctx:
+        ctx.run(2 * STEPS_PER_CYCLE)
+    torch.cuda.synchronize()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-case", choices=["mixed", "fp64"],
+                    help="only build the workload and run 2 rebuild cycles (a short, "
+                         "fixed launch sequence for an ncu capture); prints nothing")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.ncu_case:
+        run_ncu_case(args.ncu_case)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

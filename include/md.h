@@ -91,6 +91,18 @@ typedef struct {
     int64_t rebuilds;        /* list builds done                                    */
 } md_info;
 
+/* Per-phase device time of md_profile (Force / Neigh / Other, the
+ * breakdown of the paper's Fig. 4 and 5).  "force" is the force kernel with
+ * its fused velocity-Verlet epilogue; "neigh" is binning plus list build;
+ * "other" is every remaining kernel (first drift, energies, half-list
+ * integration). */
+typedef struct {
+    double force_ms, neigh_ms, other_ms;
+    int64_t force_launches, neigh_launches, other_launches;
+    int64_t steps;
+    double mean_neighbors;   /* mean row length of the list in use at the end */
+} md_phase_times;
+
 typedef struct md_ctx md_ctx;
 
 /* Creates a context for one periodic system of n atoms.
@@ -181,6 +193,11 @@ int md_get_info(md_ctx *ctx, md_info *info);
  * more.  Later rebuilds grow it again whenever a row overflows.
  * Errors: MD_ERR_INVAL (cap < 4), MD_ERR_NOMEM, MD_ERR_NL_OVERFLOW. */
 int md_set_capacity(md_ctx *ctx, int32_t cap);
+
+/* Runs nsteps like md_run (same kernels, same schedule) but launches them
+ * one by one with a CUDA event pair around each phase on the context stream,
+ * and reports the device time per phase.  Synchronises. */
+int md_profile(md_ctx *ctx, int64_t nsteps, md_phase_times *out);
 
 /* Chooses threads_per_atom and full/half lists by timing each candidate for
  * `steps` steps on the context's own state (which it restores), keeps the

@@ -24,7 +24,8 @@
 //   EPI_FK   store F; v += c F                          (last step of a run)
 //   EPI_FKKD v += c F (full step n); v += c F; x += dt v; write the FP32
 //            position of step n+1 into the other p32 buffer (other atoms are
-//            still gathering this step's positions).
+//            still gathering this step's positions), and in the FP64 path
+//            the FP64 position into the other x buffer for the same reason.
 #include "md_internal.cuh"
 
 namespace mdk {
@@ -90,7 +91,10 @@ __device__ __forceinline__ void epilogue(const Dev &d, const LJ &lj, const Rep &
         x.x = fma(lj.dt, v.x, x.x);
         x.y = fma(lj.dt, v.y, x.y);
         x.z = fma(lj.dt, v.z, x.z);
-        d.x[i] = x;
+        // the FP64 path gathers neighbours from x itself: write the next
+        // positions to the other buffer; the mixed path gathers p32 only
+        if (mixed) d.x[i] = x;
+        else d.x_nxt[i] = x;
         const double cx = ((double)(pack & 1023u) + 0.5) * R.s[0];
         const double cy = ((double)((pack >> 10) & 1023u) + 0.5) * R.s[1];
         const double cz = ((double)((pack >> 20) & 1023u) + 0.5) * R.s[2];
@@ -125,7 +129,7 @@ __global__ void __launch_bounds__(256) k_force_mixed_full(Dev d, LJ lj)
     const int4 *nb4 = reinterpret_cast<const int4 *>(d.nb);
 
     float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
-    float pe = 0.f, w = 0.f;
+    float pe = 0.f, w = 0.f, cpe = 0.f, cw = 0.f;
 
     auto pair = [&](int32_t e) {
         const int32_t j = (int32_t)((uint32_t)e & kJMask);
@@ -144,8 +148,8 @@ __global__ void __launch_bounds__(256) k_force_mixed_full(Dev d, LJ lj)
         kahan_add(sy, cy, f * dy);
         kahan_add(sz, cz, f * dz);
         if (ENERGY) {
-            pe += in ? lj.c4ef * sr6 * (sr6 - 1.f) : 0.f;
-            w += f * rsq;
+            kahan_add(pe, cpe, in ? lj.c4ef * sr6 * (sr6 - 1.f) : 0.f);
+            kahan_add(w, cw, f * rsq);
         }
     };
 
@@ -160,6 +164,10 @@ __global__ void __launch_bounds__(256) k_force_mixed_full(Dev d, LJ lj)
         pair(e.w);
     }
     float fx = sx - cx, fy = sy - cy, fz = sz - cz;
+    if (ENERGY) {
+        pe -= cpe;
+        w -= cw;
+    }
     if (TPA > 1) {
 #pragma unroll
         for (int o = TPA / 2; o > 0; o >>= 1) {
@@ -202,7 +210,7 @@ __global__ void __launch_bounds__(256) k_force_mixed_half(Dev d, LJ lj)
     const int nq = (cnt + 3) >> 2;
     const int4 *nb4 = reinterpret_cast<const int4 *>(d.nb);
     float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
-    float pe = 0.f, w = 0.f;
+    float pe = 0.f, w = 0.f, cpe = 0.f, cw = 0.f;
 
     auto pair = [&](int32_t e) {
         const uint32_t slot = (uint32_t)e >> kJBits;
@@ -224,8 +232,8 @@ __global__ void __launch_bounds__(256) k_force_mixed_half(Dev d, LJ lj)
         kahan_add(sz, cz, tz);
         atomicAdd(&d.f32[j], make_float4(-tx, -ty, -tz, 0.f));
         if (ENERGY) {
-            pe += lj.c4ef * sr6 * (sr6 - 1.f);
-            w += f * rsq;
+            kahan_add(pe, cpe, lj.c4ef * sr6 * (sr6 - 1.f));
+            kahan_add(w, cw, f * rsq);
         }
     };
     for (int q = 0; q < nq; q++) {
@@ -237,8 +245,8 @@ __global__ void __launch_bounds__(256) k_force_mixed_half(Dev d, LJ lj)
     }
     atomicAdd(&d.f32[i], make_float4(sx - cx, sy - cy, sz - cz, 0.f));
     if (ENERGY) {
-        d.pe_atom[i] = pe;
-        d.w_atom[i] = w;
+        d.pe_atom[i] = pe - cpe;
+        d.w_atom[i] = w - cw;
     }
 }
 

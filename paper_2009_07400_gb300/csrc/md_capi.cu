@@ -41,7 +41,7 @@ struct Op {
 struct GraphRec {
     cudaGraphExec_t exec;
     int launches;
-    int xb_after, pb_after;
+    int xp_after, vp_after, pb_after;
 };
 
 }  // namespace
@@ -81,7 +81,9 @@ struct md_ctx {
     int64_t elog_cap = 0;
     double *io_d = nullptr;
 
-    int xb = 0, pb = 0;
+    // buffer parities: x (flips at binning and at each fused FP64 step), v and
+    // id (flip at binning), p32 (flips at each fused step)
+    int xp = 0, vp = 0, pb = 0;
     bool moved_since_bin = true, list_valid = false, forces_valid = false;
     int64_t step = 0, launches = 0, rebuilds = 0, builds_enqueued = 0;
     int32_t last_max = 0;
@@ -113,12 +115,13 @@ Dev view(const md_ctx *c)
     d.cap = c->cap;
     d.reps = c->reps_d;
     d.rep_of = c->rep_of_d;
-    d.x = c->x[c->xb];
-    d.v = c->v[c->xb];
-    d.x_alt = c->x[1 - c->xb];
-    d.v_alt = c->v[1 - c->xb];
-    d.id = c->id[c->xb];
-    d.id_alt = c->id[1 - c->xb];
+    d.x = c->x[c->xp];
+    d.v = c->v[c->vp];
+    d.x_alt = c->x[1 - c->xp];
+    d.x_nxt = c->x[1 - c->xp];
+    d.v_alt = c->v[1 - c->vp];
+    d.id = c->id[c->vp];
+    d.id_alt = c->id[1 - c->vp];
     d.p32 = c->p32[c->pb];
     d.p32_nxt = c->p32[1 - c->pb];
     d.f32 = c->f32;
@@ -190,7 +193,8 @@ int enq_bin(md_ctx *c, int *nl)
     Dev d = view(c);
     if (launch_bin(d, c->ncells, c->scan_tmp, c->scan_len, c->st, nl) != 0)
         return fail(c, MD_ERR_CUDA, "binning launch failed");
-    c->xb = 1 - c->xb;  // reordered state now lives in the other buffers
+    c->xp = 1 - c->xp;  // reordered state now lives in the other buffers
+    c->vp = 1 - c->vp;
     c->moved_since_bin = false;
     c->list_valid = false;
     c->forces_valid = false;
@@ -239,7 +243,10 @@ int enq_force(md_ctx *c, int epi, bool energy, int *nl)
         if (launch_force(d, c->lj, c->p.precision, false, c->tpa, epi, energy, batched(c), c->st,
                          nl))
             return fail(c, MD_ERR_CUDA, "force launch failed");
-        if (epi == EPI_FKKD) c->pb = 1 - c->pb;
+        if (epi == EPI_FKKD) {
+            c->pb = 1 - c->pb;
+            if (!is_mixed(c)) c->xp = 1 - c->xp;
+        }
     }
     if (epi == EPI_FKKD) c->moved_since_bin = true;
     c->forces_valid = (epi != EPI_FKKD);
@@ -272,7 +279,7 @@ int enq_op(md_ctx *c, const Op &op, int *nl)
 
 std::string key_of(const md_ctx *c, const std::vector<Op> &ops)
 {
-    std::string k = std::to_string(c->xb) + std::to_string(c->pb) + ":";
+    std::string k = std::to_string(c->xp) + std::to_string(c->vp) + std::to_string(c->pb) + ":";
     for (const Op &o : ops) {
         if (o.kind == Op::KD) k += 'K';
         else if (o.kind == Op::REBUILD) k += 'R';
@@ -287,7 +294,7 @@ int run_segment(md_ctx *c, const std::vector<Op> &ops)
     const std::string key = key_of(c, ops);
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
-        const int xb0 = c->xb, pb0 = c->pb;
+        const int xp0 = c->xp, vp0 = c->vp, pb0 = c->pb;
         const bool mv = c->moved_since_bin, lv = c->list_valid, fv = c->forces_valid;
         const int64_t be = c->builds_enqueued;
         CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
@@ -306,17 +313,19 @@ int run_segment(md_ctx *c, const std::vector<Op> &ops)
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return fail(c, MD_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
         rec.launches = nl;
-        rec.xb_after = c->xb;
+        rec.xp_after = c->xp;
+        rec.vp_after = c->vp;
         rec.pb_after = c->pb;
         it = c->graphs.emplace(key, rec).first;
         // capture changed the host bookkeeping; rewind, the replay re-applies it
-        c->xb = xb0; c->pb = pb0;
+        c->xp = xp0; c->vp = vp0; c->pb = pb0;
         c->moved_since_bin = mv; c->list_valid = lv; c->forces_valid = fv;
         c->builds_enqueued = be;
     }
     CK(cudaGraphLaunch(it->second.exec, c->st));
     c->launches += it->second.launches;
-    c->xb = it->second.xb_after;
+    c->xp = it->second.xp_after;
+    c->vp = it->second.vp_after;
     c->pb = it->second.pb_after;
     for (const Op &op : ops) {
         if (op.kind == Op::REBUILD) {
@@ -400,7 +409,7 @@ int ensure_forces(md_ctx *c)
 // after its binning (the state a resume after an overflow starts from).
 struct PlannedRebuild {
     int64_t step;
-    int xb_after_bin, pb;
+    int xp_after_bin, vp_after_bin, pb;
 };
 
 // Plans steps (first .. last) and executes them; `kd` = the drift to x_first
@@ -420,7 +429,7 @@ int run_span(md_ctx *c, int64_t s0, int64_t first, int64_t last, bool kd, int32_
                 seg.clear();
             }
             seg.push_back({Op::REBUILD, nstep, false, false});
-            rebuilds->push_back({nstep, 1 - c->xb, c->pb});
+            rebuilds->push_back({nstep, 1 - c->xp, 1 - c->vp, c->pb});
         }
         // energies are logged every energy_every steps counted from the run's start
         const bool en = energy_every > 0 && ((nstep - s0) % energy_every) == 0;
@@ -432,6 +441,37 @@ int run_span(md_ctx *c, int64_t s0, int64_t first, int64_t last, bool kd, int32_
 
 int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64_t *counts,
                  int32_t nrep, const double *pos, const double *vel, void *stream);
+
+// Process-wide autotuner cache: (precision, log2 atoms per replica, batched)
+// -> (threads per atom, half list).
+std::map<std::string, std::pair<int, int>> &tune_cache()
+{
+    static std::map<std::string, std::pair<int, int>> m;
+    return m;
+}
+
+std::mutex &tune_mutex()
+{
+    static std::mutex m;
+    return m;
+}
+
+// Switches lanes-per-atom / list type; a list-type change rebuilds the list.
+int apply_tuning(md_ctx *c, int tpa, int half)
+{
+    const bool relist = (half != c->p.half_list);
+    c->tpa = tpa;
+    c->p.threads_per_atom = tpa;
+    c->p.half_list = half;
+    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+    c->graphs.clear();
+    if (relist) {
+        c->list_valid = false;
+        c->forces_valid = false;
+        return ensure_forces(c);
+    }
+    return MD_OK;
+}
 
 }  // namespace
 
@@ -486,7 +526,8 @@ int md_set_state(md_ctx *c, const double *pos, const double *vel)
     const size_t bytes = sizeof(double) * 3 * (size_t)c->n;
     CK(cudaMemcpyAsync(c->io_d, pos, bytes, cudaMemcpyHostToDevice, c->st));
     CK(cudaMemcpyAsync(c->io_d + 3 * c->n, vel, bytes, cudaMemcpyHostToDevice, c->st));
-    c->xb = 0;
+    c->xp = 0;
+    c->vp = 0;
     c->pb = 0;
     int nl = 0;
     Dev d = view(c);
@@ -619,7 +660,8 @@ int md_run(md_ctx *c, int64_t nsteps, int32_t energy_every, double *energies)
         if (k < 1 || k > (int64_t)planned.size())
             return fail(c, MD_ERR_NL_OVERFLOW, "list overflow at an unknown rebuild");
         const PlannedRebuild &pr = planned[(size_t)k - 1];
-        c->xb = pr.xb_after_bin;
+        c->xp = pr.xp_after_bin;
+        c->vp = pr.vp_after_bin;
         c->pb = pr.pb;
         c->moved_since_bin = false;
         c->list_valid = false;
@@ -680,7 +722,7 @@ int md_get_cells(md_ctx *c, int32_t *cell_start, int32_t *cell_atoms)
     if (!c || !cell_start || !cell_atoms) return fail(c, MD_ERR_INVAL, "null argument");
     std::vector<int32_t> cs((size_t)c->ncells + 1), ids((size_t)c->n);
     CK(cudaMemcpyAsync(cs.data(), c->cell_start, sizeof(int32_t) * cs.size(), cudaMemcpyDeviceToHost, c->st));
-    CK(cudaMemcpyAsync(ids.data(), c->id[c->xb], sizeof(int32_t) * ids.size(), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(ids.data(), c->id[c->vp], sizeof(int32_t) * ids.size(), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
     int64_t o = 0;
     for (int32_t r = 0; r < c->nrep; r++) {
@@ -699,7 +741,7 @@ int md_get_neighbors(md_ctx *c, int32_t *counts, int32_t *rows, int32_t cap)
     if (rc) return rc;
     std::vector<int32_t> cnt((size_t)c->n), ids((size_t)c->n);
     CK(cudaMemcpyAsync(cnt.data(), c->nb_count, sizeof(int32_t) * c->n, cudaMemcpyDeviceToHost, c->st));
-    CK(cudaMemcpyAsync(ids.data(), c->id[c->xb], sizeof(int32_t) * c->n, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(ids.data(), c->id[c->vp], sizeof(int32_t) * c->n, cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
     for (int64_t a = 0; a < c->n; a++) {
         if (cnt[a] > cap) return fail(c, MD_ERR_INVAL, "a row is longer than cap");
@@ -748,14 +790,136 @@ int md_set_capacity(md_ctx *c, int32_t cap)
     return rebuild_now(c, c->moved_since_bin);
 }
 
+int md_profile(md_ctx *c, int64_t nsteps, md_phase_times *out)
+{
+    if (!c || !out || nsteps < 1) return fail(c, MD_ERR_INVAL, "bad argument");
+    int rc = ensure_forces(c);
+    if (rc) return rc;
+    std::memset(out, 0, sizeof(*out));
+    const int64_t s0 = c->step, every = c->p.rebuild_every;
+    std::vector<Op> ops;
+    ops.push_back({Op::KD, s0 + 1, false, false});
+    for (int64_t n = s0 + 1; n <= s0 + nsteps; n++) {
+        if (n % every == 0) ops.push_back({Op::REBUILD, n, false, false});
+        ops.push_back({Op::FORCE, n, n == s0 + nsteps, false});
+    }
+    std::vector<cudaEvent_t> ev(2 * ops.size());
+    for (auto &e : ev) CK(cudaEventCreate(&e));
+    CK(cudaMemsetAsync(&c->status->rebuild_count, 0, sizeof(int64_t), c->st));
+    std::vector<int> cat(ops.size()), nls(ops.size());
+    for (size_t k = 0; k < ops.size(); k++) {
+        int nl = 0;
+        CK(cudaEventRecord(ev[2 * k], c->st));
+        if ((rc = enq_op(c, ops[k], &nl))) break;
+        CK(cudaEventRecord(ev[2 * k + 1], c->st));
+        cat[k] = ops[k].kind == Op::REBUILD ? 1 : (ops[k].kind == Op::FORCE ? 0 : 2);
+        nls[k] = nl;
+        c->launches += nl;
+        if (ops[k].kind == Op::REBUILD) c->rebuilds++;
+    }
+    if (!rc) {
+        DevStatus s;
+        if (!(rc = read_status(c, &s))) rc = check_flags(c, s);
+        if (!rc && (s.flags & FLAG_NL_OVERFLOW)) rc = fail(c, MD_ERR_NL_OVERFLOW, "list overflow while profiling");
+        if (!rc) c->last_max = s.max_count;
+    }
+    for (size_t k = 0; !rc && k < ops.size(); k++) {
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]));
+        double *dst = cat[k] == 0 ? &out->force_ms : cat[k] == 1 ? &out->neigh_ms : &out->other_ms;
+        int64_t *cnt = cat[k] == 0 ? &out->force_launches : cat[k] == 1 ? &out->neigh_launches : &out->other_launches;
+        // a half-list FORCE op also launches the integration kernel; its time
+        // stays in "force" (the fused epilogue does the same work)
+        *dst += ms;
+        *cnt += nls[k];
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (rc) return rc;
+    c->step = s0 + nsteps;
+    out->steps = nsteps;
+    std::vector<int32_t> cnt((size_t)c->n);
+    CK(cudaMemcpy(cnt.data(), c->nb_count, sizeof(int32_t) * c->n, cudaMemcpyDeviceToHost));
+    double sum = 0;
+    for (int32_t q : cnt) sum += q;
+    out->mean_neighbors = sum / (double)c->n;
+    return MD_OK;
+}
+
 int md_autotune(md_ctx *c, int32_t steps, md_params *chosen)
 {
-    (void)steps;
-    if (!c) return fail(c, MD_ERR_INVAL, "null context");
-    if (chosen) {
-        *chosen = c->p;
-        chosen->threads_per_atom = c->tpa;
+    if (!c || steps < 1) return fail(c, MD_ERR_INVAL, "bad argument");
+    const int64_t per_rep = c->n / c->nrep;
+    int bucket = 0;
+    while (((int64_t)1 << (bucket + 1)) <= per_rep) bucket++;
+    const std::string key = std::to_string(c->p.precision) + ":" + std::to_string(bucket) + ":" +
+                            std::to_string(c->nrep > 1);
+    {
+        std::lock_guard<std::mutex> g(tune_mutex());
+        auto it = tune_cache().find(key);
+        if (it != tune_cache().end()) {
+            int rc = apply_tuning(c, it->second.first, it->second.second);
+            if (rc) return rc;
+            if (chosen) { *chosen = c->p; chosen->threads_per_atom = c->tpa; }
+            return MD_OK;
+        }
     }
+    int rc = ensure_forces(c);
+    if (rc) return rc;
+    // device backup of the current (cell-ordered) state
+    dvec4 *xb = nullptr, *vb = nullptr;
+    int32_t *ib = nullptr;
+    if ((rc = dalloc(c, &xb, (size_t)c->n)) || (rc = dalloc(c, &vb, (size_t)c->n)) ||
+        (rc = dalloc(c, &ib, (size_t)c->n))) {
+        cudaFree(xb); cudaFree(vb); cudaFree(ib);
+        return rc;
+    }
+    const int64_t step0 = c->step;
+    auto save = [&]() {
+        cudaMemcpyAsync(xb, c->x[c->xp], sizeof(dvec4) * c->n, cudaMemcpyDeviceToDevice, c->st);
+        cudaMemcpyAsync(vb, c->v[c->vp], sizeof(dvec4) * c->n, cudaMemcpyDeviceToDevice, c->st);
+        cudaMemcpyAsync(ib, c->id[c->vp], sizeof(int32_t) * c->n, cudaMemcpyDeviceToDevice, c->st);
+    };
+    auto restore = [&]() -> int {
+        cudaMemcpyAsync(c->x[c->xp], xb, sizeof(dvec4) * c->n, cudaMemcpyDeviceToDevice, c->st);
+        cudaMemcpyAsync(c->v[c->vp], vb, sizeof(dvec4) * c->n, cudaMemcpyDeviceToDevice, c->st);
+        cudaMemcpyAsync(c->id[c->vp], ib, sizeof(int32_t) * c->n, cudaMemcpyDeviceToDevice, c->st);
+        c->step = step0;
+        c->moved_since_bin = true;
+        c->list_valid = false;
+        c->forces_valid = false;
+        int r = ensure_forces(c);
+        return r;
+    };
+    save();
+    const int cands[4][2] = {{1, 0}, {2, 0}, {4, 0}, {1, 1}};
+    float best = 1e30f;
+    int best_k = 0;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int k = 0; k < 4 && !rc; k++) {
+        if ((rc = apply_tuning(c, cands[k][0], cands[k][1]))) break;
+        if ((rc = md_run(c, steps, 0, nullptr))) break;  // warm-up (graph capture)
+        if ((rc = restore())) break;
+        CK(cudaEventRecord(e0, c->st));
+        if ((rc = md_run(c, steps, 0, nullptr))) break;
+        CK(cudaEventRecord(e1, c->st));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) { best = ms; best_k = k; }
+        if ((rc = restore())) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(xb); cudaFree(vb); cudaFree(ib);
+    if (rc) return rc;
+    if ((rc = apply_tuning(c, cands[best_k][0], cands[best_k][1]))) return rc;
+    {
+        std::lock_guard<std::mutex> g(tune_mutex());
+        tune_cache()[key] = {cands[best_k][0], cands[best_k][1]};
+    }
+    if (chosen) { *chosen = c->p; chosen->threads_per_atom = c->tpa; }
     return MD_OK;
 }
 

@@ -77,6 +77,8 @@ struct Dev {
     dvec4 *x;               // current positions (FP64, .w unused)
     dvec4 *v;               // current velocities
     dvec4 *x_alt, *v_alt;   // reorder targets
+    dvec4 *x_nxt;             // next positions of the fused FP64 step (other atoms
+                              // still gather this step's x)
     int32_t *id, *id_alt;     // caller id of each slot
     float4 *p32, *p32_nxt;    // cell-relative FP32 positions; .w = packed cell coords
     float4 *f32;              // mixed-path forces

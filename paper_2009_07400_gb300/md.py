@@ -28,7 +28,7 @@ ABI_SYMBOLS = [
     "md_create", "md_create_batch", "md_destroy", "md_last_error", "md_set_state",
     "md_bin_cells", "md_build_neighbors", "md_compute_forces", "md_integrate", "md_energy",
     "md_run", "md_get_positions", "md_get_velocities", "md_get_forces", "md_get_cells",
-    "md_get_neighbors", "md_get_info", "md_autotune", "md_set_capacity",
+    "md_get_neighbors", "md_get_info", "md_autotune", "md_set_capacity", "md_profile",
 ]
 
 
@@ -48,6 +48,13 @@ class md_params(ctypes.Structure):
                 ("skin", ctypes.c_double), ("dt", ctypes.c_double),
                 ("rebuild_every", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("half_list", ctypes.c_int32), ("threads_per_atom", ctypes.c_int32)]
+
+
+class md_phase_times(ctypes.Structure):
+    _fields_ = [("force_ms", ctypes.c_double), ("neigh_ms", ctypes.c_double),
+                ("other_ms", ctypes.c_double), ("force_launches", ctypes.c_int64),
+                ("neigh_launches", ctypes.c_int64), ("other_launches", ctypes.c_int64),
+                ("steps", ctypes.c_int64), ("mean_neighbors", ctypes.c_double)]
 
 
 class md_info(ctypes.Structure):
@@ -100,6 +107,7 @@ def load(path: str | None = None):
                 "md_get_info": [ctx, ctypes.POINTER(md_info)],
                 "md_autotune": [ctx, ctypes.c_int32, ctypes.POINTER(md_params)],
                 "md_set_capacity": [ctx, ctypes.c_int32],
+                "md_profile": [ctx, ctypes.c_int64, ctypes.POINTER(md_phase_times)],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -249,6 +257,11 @@ class MDContext:
         self._check(self._lib.md_get_neighbors(self._h, counts.ctypes.data_as(_I32),
                                                rows.ctypes.data_as(_I32), cap))
         return counts, rows
+
+    def profile(self, nsteps) -> md_phase_times:
+        out = md_phase_times()
+        self._check(self._lib.md_profile(self._h, int(nsteps), ctypes.byref(out)))
+        return out
 
     def set_capacity(self, cap):
         self._check(self._lib.md_set_capacity(self._h, int(cap)))
