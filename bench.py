@@ -179,12 +179,13 @@ def run_gpu(args):
     build.build()
     md.load()
     s = inputs.workload(WORKLOAD)
-    # The C library enqueues on its own stream (a stream handle of 0 means:
-    # create one); events are recorded on torch's stream, so synchronise the
-    # context stream through the library before stopping the clock: md_run
-    # already synchronises at its end.
+    # The library enqueues on the stream it is given: use one torch stream for
+    # the contexts and for the CUDA events that bracket the timed region.
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    sh = stream.cuda_stream
     res = {}
-    with md.MDContext(s.pos, s.vel, s.box, precision=md.MD_MIXED) as ctx:
+    with md.MDContext(s.pos, s.vel, s.box, stream=sh, precision=md.MD_MIXED) as ctx:
         with ClockSampler(local) as clk:
             ms, launches = time_cycles(ctx, args.steps, args.warmup, dist, torch)
         res["mixed_ms"] = ms
@@ -194,7 +195,7 @@ def run_gpu(args):
         res["prof"] = prof
         res["mixed_state"] = (ctx.positions(), ctx.forces())
     fp64_cycles = max(1, min(args.steps, 3))
-    with md.MDContext(s.pos, s.vel, s.box, precision=md.MD_FP64) as ctx:
+    with md.MDContext(s.pos, s.vel, s.box, stream=sh, precision=md.MD_FP64) as ctx:
         ms64, _ = time_cycles(ctx, fp64_cycles, 1, dist, torch)
         res["fp64_ms"] = ms64 / fp64_cycles
         prof64 = ctx.profile(STEPS_PER_CYCLE)
@@ -206,7 +207,7 @@ def run_gpu(args):
     pin_vel = torch.empty((s.n, 3), dtype=torch.float64, pin_memory=True).numpy()
     pin_pos[:] = s.pos
     pin_vel[:] = s.vel
-    with md.MDContext(s.pos, s.vel, s.box, precision=md.MD_MIXED) as ctx:
+    with md.MDContext(s.pos, s.vel, s.box, stream=sh, precision=md.MD_MIXED) as ctx:
         for _ in range(2):
             ctx.set_state(pin_pos, pin_vel)
             ctx.run(STEPS_PER_CYCLE, energy_every=STEPS_PER_CYCLE)

@@ -8,10 +8,11 @@
 // so every candidate is first classified in FP32 from the cell-relative
 // positions p = fl32(x - C_cell):
 //     d = (p_i - p_j) + o * (-s)        (o = stencil offset of j's image)
-// The FP32 r^2 of a candidate differs from the FP64 one by far less than
-// 2.5e-4 rs^2 (a few FP32 ulps of |p| <= s/2 and |o s| <= s propagated
-// through the three squares), so only candidates inside that band are
-// decided by the FP64 test: about 3 % of the atoms meet one.  The FP64 test
+// d is formed as (p_i + o(-s)) - p_j.  The FP32 r^2 of a candidate differs
+// from the FP64 one by far less than 2.5e-4 rs^2 (a few FP32 ulps of
+// |p| <= s/2 and |o s| <= s propagated through the three squares), so only
+// candidates inside that band are decided by the FP64 test: about 3 % of the
+// atoms meet one.  The FP64 test
 // applies the image shift the way the minimum-image branch does,
 // (x_i - x_j) -/+ L, with __dmul_rn/__dadd_rn so nothing is contracted.
 //
@@ -53,41 +54,38 @@ __device__ __forceinline__ int32_t build_row(const Dev &d, const LJ &lj, int64_t
     const int ci[3] = {(int)(pack & 1023u), (int)((pack >> 10) & 1023u), (int)((pack >> 20) & 1023u)};
     const int32_t idi = HALF ? d.id[i] : 0;
     const int64_t n = d.n;
-    int4 *nb4 = reinterpret_cast<int4 *>(d.nb);
-    const int cap4 = d.cap >> 2;
+    const int32_t cap = d.cap;
+    int32_t *row = d.nb + 4 * i;          // entry k of row i: row[(k>>2)*4n + (k&3)]
+    const float4 *p32 = d.p32;
+    const float lo = lj.rs2f_lo, hi = lj.rs2f_hi;
 
     int32_t cnt = 0;
-    int4 buf = make_int4(0, 0, 0, 0);
     bool have_xi = false;
     dvec4 xi = mk_dvec4(0, 0, 0, 0);
 
     for (int ox = -1; ox <= 1; ox++) {
         int ux = ci[0] + ox, kx = 0;
         if (ux < 0) { ux += R.nc[0]; kx = -1; } else if (ux >= R.nc[0]) { ux -= R.nc[0]; kx = 1; }
+        const float qx = pi.x + (float)ox * R.nsf[0];
         for (int oy = -1; oy <= 1; oy++) {
             int uy = ci[1] + oy, ky = 0;
             if (uy < 0) { uy += R.nc[1]; ky = -1; } else if (uy >= R.nc[1]) { uy -= R.nc[1]; ky = 1; }
+            const float qy = pi.y + (float)oy * R.nsf[1];
+            const int64_t col = R.cell_off + ((int64_t)ux * R.nc[1] + uy) * R.nc[2];
             for (int oz = -1; oz <= 1; oz++) {
                 int uz = ci[2] + oz, kz = 0;
                 if (uz < 0) { uz += R.nc[2]; kz = -1; } else if (uz >= R.nc[2]) { uz -= R.nc[2]; kz = 1; }
-                const int64_t cell = R.cell_off + ((int64_t)ux * R.nc[1] + uy) * R.nc[2] + uz;
-                const int32_t j0 = d.cell_start[cell], j1 = d.cell_start[cell + 1];
-                const uint32_t slot = (uint32_t)((ox + 1) * 9 + (oy + 1) * 3 + (oz + 1));
-                const float offx = (float)ox * R.nsf[0];
-                const float offy = (float)oy * R.nsf[1];
-                const float offz = (float)oz * R.nsf[2];
+                const float qz = pi.z + (float)oz * R.nsf[2];
+                const int32_t j0 = d.cell_start[col + uz], j1 = d.cell_start[col + uz + 1];
+                const uint32_t tag = (uint32_t)((ox + 1) * 9 + (oy + 1) * 3 + (oz + 1)) << kJBits;
                 for (int32_t j = j0; j < j1; j++) {
+                    const float4 pj = __ldg(p32 + j);
+                    const float dx = qx - pj.x, dy = qy - pj.y, dz = qz - pj.z;
+                    const float r2f = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                    if (!(r2f < hi)) continue;                 // clearly outside rs
                     if (j == i) continue;
                     if (HALF && d.id[j] <= idi) continue;
-                    const float4 pj = d.p32[j];
-                    const float dx = (pi.x - pj.x) + offx;
-                    const float dy = (pi.y - pj.y) + offy;
-                    const float dz = (pi.z - pj.z) + offz;
-                    const float r2f = dx * dx + dy * dy + dz * dz;
-                    bool keep;
-                    if (r2f < lj.rs2f_lo) keep = true;
-                    else if (r2f > lj.rs2f_hi) keep = false;
-                    else {
+                    if (!(r2f < lo)) {                         // inside the band: decide in FP64
                         if (!have_xi) { xi = d.x[i]; have_xi = true; }
                         const dvec4 xj = d.x[j];
                         const double tx = image_diff(xi.x, xj.x, kx, R.L[0]);
@@ -95,36 +93,21 @@ __device__ __forceinline__ int32_t build_row(const Dev &d, const LJ &lj, int64_t
                         const double tz = image_diff(xi.z, xj.z, kz, R.L[2]);
                         const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(tx, tx), __dmul_rn(ty, ty)),
                                                     __dmul_rn(tz, tz));
-                        keep = r2 < lj.rs2;
+                        if (!(r2 < lj.rs2)) continue;
                     }
-                    if (keep) {
-                        const int32_t e = (int32_t)((uint32_t)j | (slot << kJBits));
-                        switch (cnt & 3) {
-                            case 0: buf.x = e; break;
-                            case 1: buf.y = e; break;
-                            case 2: buf.z = e; break;
-                            default:
-                                buf.w = e;
-                                if ((cnt >> 2) < cap4) nb4[(int64_t)(cnt >> 2) * n + i] = buf;
-                        }
-                        cnt++;
-                    }
+                    if (cnt < cap) row[(int64_t)(cnt >> 2) * 4 * n + (cnt & 3)] = (int32_t)((uint32_t)j | tag);
+                    cnt++;
                 }
             }
         }
     }
-    if ((cnt & 3) != 0 && (cnt >> 2) < cap4) {
+    if (cnt < cap) {   // pad the last chunk with self entries in slot 27
         const int32_t pad = (int32_t)((uint32_t)i | ((uint32_t)kPadSlot << kJBits));
-        const int r = cnt & 3;
-        if (r <= 1) buf.y = pad;
-        if (r <= 2) buf.z = pad;
-        buf.w = pad;
-        nb4[(int64_t)(cnt >> 2) * n + i] = buf;
+        for (int32_t k = cnt; (k & 3) != 0; k++) row[(int64_t)(k >> 2) * 4 * n + (k & 3)] = pad;
     }
     d.nb_count[i] = cnt;
     return cnt;
 }
-
 
 template <bool BATCHED, bool HALF>
 __global__ void __launch_bounds__(128) k_build(Dev d, LJ lj)

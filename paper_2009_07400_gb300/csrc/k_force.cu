@@ -11,13 +11,22 @@
 // per-atom sum stays in registers.  No tensor cores: the pair gather is not a
 // dense contraction.
 //
+// Pair arithmetic as executed: t = sr2^3 sigma^6 (the paper's sr6) and
+// f = sr2 t (48 eps t - 24 eps), the same product regrouped so that the two
+// constant factors fold into one FMA.
+//
 // Mixed path: positions are FP32 offsets from the centre of the atom's cell
 // at the last binning; a neighbour's displacement is
 //     d = (p_i - p_j) + o * (-s)
 // with o its stencil offset (decoded from the entry's 5-bit slot through a
 // 27-entry shared table), so |d|'s FP32 rounding error is that of numbers of
 // size ~s rather than of the box length.  Per-atom sums are Kahan
-// compensated.  Positions and velocities are integrated in FP64.
+// compensated: the four pairs of a list chunk are summed in a plain FP32
+// partial and each partial enters a Kahan sum (the compensation then covers
+// the long per-atom sum, where the rounding error accumulates).  The
+// reciprocal is the hardware approximation (rcp.approx, relative error
+// below 2^-22), which keeps the force error far inside the 1e-5 budget.
+// Positions and velocities are integrated in FP64.
 //
 // Epilogues (velocity Verlet, Sec. 3.2 Eq. 1, kick-drift-kick, c = dt/(2m)):
 //   EPI_F    store F
@@ -48,16 +57,23 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float term)
     s = t;
 }
 
-// FP64 reciprocal: FP32 seed refined by two Newton-Raphson steps
-// r <- r + r (1 - a r); each squares the relative error (2^-24 -> 2^-48 ->
-// below FP64 rounding).  Cheaper than an IEEE FP64 division on GB300.
+// FP64 reciprocal: a correctly rounded FP32 seed (relative error <= 2^-24)
+// refined by one Newton-Raphson step r <- r + r (1 - a r), which squares the
+// relative error to <= 2^-48 (~4e-15), far inside the FP64 path's 1e-10
+// force tolerance.  Cheaper than an IEEE FP64 division on GB300, whose FP64
+// pipe is the bound of this path.
 __device__ __forceinline__ double rcp_nr(double a)
 {
-    double r = (double)__frcp_rn((float)a);
-    double e = fma(-a, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-a, r, 1.0);
-    return fma(r, e, r);
+    const double r = (double)__frcp_rn((float)a);
+    return fma(r, fma(-a, r, 1.0), r);
+}
+
+// FP32 reciprocal on the special-function unit (one instruction).
+__device__ __forceinline__ float rcp_approx(float a)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
 }
 
 __device__ __forceinline__ float4 stencil_entry(int s)
@@ -130,26 +146,27 @@ __global__ void __launch_bounds__(256) k_force_mixed_full(Dev d, LJ lj)
 
     float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
     float pe = 0.f, w = 0.f, cpe = 0.f, cw = 0.f;
+    const float4 *p32 = d.p32;
 
-    auto pair = [&](int32_t e) {
-        const int32_t j = (int32_t)((uint32_t)e & kJMask);
-        const float4 o = otab[(uint32_t)e >> kJBits];
-        const float4 pj = __ldg(&d.p32[j]);
+    // one pair: adds f*d to (px, py, pz) and, with ENERGY, V and f r^2
+    auto pair = [&](uint32_t e, float &px, float &py, float &pz, float &pv, float &pw) {
+        const float4 pj = __ldg(p32 + (e & kJMask));
+        const float4 o = otab[e >> kJBits];
         const float dx = fmaf(o.x, nsx, pi.x - pj.x);
         const float dy = fmaf(o.y, nsy, pi.y - pj.y);
         const float dz = fmaf(o.z, nsz, pi.z - pj.z);
         const float rsq = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        const float sr2 = __frcp_rn(rsq);
-        const float sr6 = sr2 * sr2 * sr2 * lj.sigma6f;
-        float f = lj.c48ef * sr6 * (sr6 - 0.5f) * sr2;
+        const float sr2 = rcp_approx(rsq);
+        const float t = sr2 * sr2 * sr2 * lj.sigma6f;
+        float f = sr2 * t * fmaf(lj.c48ef, t, -lj.c24ef);
         const bool in = rsq < lj.rc2f;
         f = in ? f : 0.f;
-        kahan_add(sx, cx, f * dx);
-        kahan_add(sy, cy, f * dy);
-        kahan_add(sz, cz, f * dz);
+        px = fmaf(f, dx, px);
+        py = fmaf(f, dy, py);
+        pz = fmaf(f, dz, pz);
         if (ENERGY) {
-            kahan_add(pe, cpe, in ? lj.c4ef * sr6 * (sr6 - 1.f) : 0.f);
-            kahan_add(w, cw, f * rsq);
+            pv += in ? lj.c4ef * t * (t - 1.f) : 0.f;
+            pw = fmaf(f, rsq, pw);
         }
     };
 
@@ -158,10 +175,18 @@ __global__ void __launch_bounds__(256) k_force_mixed_full(Dev d, LJ lj)
     for (; q < nq; q += TPA) {
         const int4 e = nxt;
         if (q + TPA < nq) nxt = ld_stream(nb4 + (int64_t)(q + TPA) * n + i);
-        pair(e.x);
-        pair(e.y);
-        pair(e.z);
-        pair(e.w);
+        float px = 0.f, py = 0.f, pz = 0.f, pv = 0.f, pw = 0.f;
+        pair((uint32_t)e.x, px, py, pz, pv, pw);
+        pair((uint32_t)e.y, px, py, pz, pv, pw);
+        pair((uint32_t)e.z, px, py, pz, pv, pw);
+        pair((uint32_t)e.w, px, py, pz, pv, pw);
+        kahan_add(sx, cx, px);
+        kahan_add(sy, cy, py);
+        kahan_add(sz, cz, pz);
+        if (ENERGY) {
+            kahan_add(pe, cpe, pv);
+            kahan_add(w, cw, pw);
+        }
     }
     float fx = sx - cx, fy = sy - cy, fz = sz - cz;
     if (ENERGY) {
@@ -223,9 +248,9 @@ __global__ void __launch_bounds__(256) k_force_mixed_half(Dev d, LJ lj)
         const float dz = fmaf(o.z, nsz, pi.z - pj.z);
         const float rsq = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
         if (!(rsq < lj.rc2f)) return;
-        const float sr2 = __frcp_rn(rsq);
+        const float sr2 = rcp_approx(rsq);
         const float sr6 = sr2 * sr2 * sr2 * lj.sigma6f;
-        const float f = lj.c48ef * sr6 * (sr6 - 0.5f) * sr2;
+        const float f = sr2 * sr6 * fmaf(lj.c48ef, sr6, -lj.c24ef);
         const float tx = f * dx, ty = f * dy, tz = f * dz;
         kahan_add(sx, cx, tx);
         kahan_add(sy, cy, ty);
@@ -278,14 +303,14 @@ __device__ __forceinline__ void f64_pair(const Dev &d, const LJ &lj, const dvec4
     const double rsq = fma(dz, dz, fma(dy, dy, dx * dx));
     const bool in = (rsq < lj.rc2) && (slot < 27);
     const double sr2 = rcp_nr(rsq);
-    const double sr6 = sr2 * sr2 * sr2 * lj.sigma6;
-    double f = lj.c48e * sr6 * (sr6 - 0.5) * sr2;
+    const double t = sr2 * sr2 * sr2 * lj.sigma6;
+    double f = sr2 * t * fma(lj.c48e, t, -lj.c24e);
     f = in ? f : 0.0;
     fx = fma(f, dx, fx);
     fy = fma(f, dy, fy);
     fz = fma(f, dz, fz);
     if (energy) {
-        pe += in ? lj.c4e * sr6 * (sr6 - 1.0) : 0.0;
+        pe += in ? lj.c4e * t * (t - 1.0) : 0.0;
         w = fma(f, rsq, w);
     }
 }

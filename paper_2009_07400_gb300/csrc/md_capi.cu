@@ -999,11 +999,13 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
     const double s2 = q.sigma * q.sigma;
     lj.sigma6 = s2 * s2 * s2;
     lj.c48e = 48.0 * q.epsilon;
+    lj.c24e = 24.0 * q.epsilon;
     lj.c4e = 4.0 * q.epsilon;
     lj.eps = q.epsilon;
     lj.rc2f = (float)lj.rc2;
     lj.sigma6f = (float)lj.sigma6;
     lj.c48ef = (float)lj.c48e;
+    lj.c24ef = (float)lj.c24e;
     lj.c4ef = (float)lj.c4e;
     lj.half_dt_m = 0.5 * q.dt / q.mass;
     lj.dt = q.dt;

@@ -59,8 +59,8 @@ struct Rep {
 
 // LJ constants in both precisions.
 struct LJ {
-    double rc2, rs2, sigma6, c48e, c4e, eps;
-    float rc2f, sigma6f, c48ef, c4ef;
+    double rc2, rs2, sigma6, c48e, c24e, c4e, eps;
+    float rc2f, sigma6f, c48ef, c24ef, c4ef;
     double half_dt_m;         // dt / (2 m)
     double dt;
     double mass;
