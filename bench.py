@@ -131,12 +131,17 @@ def ncu_traffic():
     return float(t.group(1)) if h.group(1) == cur else None
 
 
-def algorithmic_bytes_per_atom(mean_nb):
-    """Mixed force kernel with the fused velocity-Verlet epilogue, per atom
-    and time step: the 4-byte list entries, the row length, the FP32
-    position read and the next step's FP32 position write (16 + 16), and
-    read + write of FP64 position and velocity (24 B each way, 3 doubles).
-    Neighbour positions are gathered from L2 and not counted."""
+def algorithmic_bytes_per_atom(mean_nb, half):
+    """DRAM bytes per atom and time step the dominant kernel must move.
+    Full list (force kernel with the fused velocity-Verlet epilogue): the
+    4-byte list entries, the row length, the FP32 position read and the next
+    step's FP32 position write (16 + 16), and read + write of FP64 position
+    and velocity (24 B each way, 3 doubles).  Half list (force kernel alone):
+    the list entries, the row length, the FP32 position read and the final
+    force (16); the j-side force updates are L2 atomics.  Neighbour positions
+    are gathered from L2 and are not counted."""
+    if half:
+        return 4.0 * mean_nb + 4 + 16 + 16
     return 4.0 * mean_nb + 4 + 16 + 16 + 2 * 24 + 2 * 24
 
 
@@ -186,6 +191,8 @@ def run_gpu(args):
     sh = stream.cuda_stream
     res = {}
     with md.MDContext(s.pos, s.vel, s.box, stream=sh, precision=md.MD_MIXED) as ctx:
+        tuned = ctx.autotune(STEPS_PER_CYCLE)
+        res["tuned"] = {"threads_per_atom": tuned.threads_per_atom, "half_list": bool(tuned.half_list)}
         with ClockSampler(local) as clk:
             ms, launches = time_cycles(ctx, args.steps, args.warmup, dist, torch)
         res["mixed_ms"] = ms
@@ -196,6 +203,8 @@ def run_gpu(args):
         res["mixed_state"] = (ctx.positions(), ctx.forces())
     fp64_cycles = max(1, min(args.steps, 3))
     with md.MDContext(s.pos, s.vel, s.box, stream=sh, precision=md.MD_FP64) as ctx:
+        t64 = ctx.autotune(STEPS_PER_CYCLE)
+        res["tuned64"] = {"threads_per_atom": t64.threads_per_atom, "half_list": bool(t64.half_list)}
         ms64, _ = time_cycles(ctx, fp64_cycles, 1, dist, torch)
         res["fp64_ms"] = ms64 / fp64_cycles
         prof64 = ctx.profile(STEPS_PER_CYCLE)
@@ -207,7 +216,9 @@ def run_gpu(args):
     pin_vel = torch.empty((s.n, 3), dtype=torch.float64, pin_memory=True).numpy()
     pin_pos[:] = s.pos
     pin_vel[:] = s.vel
-    with md.MDContext(s.pos, s.vel, s.box, stream=sh, precision=md.MD_MIXED) as ctx:
+    with md.MDContext(s.pos, s.vel, s.box, stream=sh, precision=md.MD_MIXED,
+                      threads_per_atom=res["tuned"]["threads_per_atom"],
+                      half_list=res["tuned"]["half_list"]) as ctx:
         for _ in range(2):
             ctx.set_state(pin_pos, pin_vel)
             ctx.run(STEPS_PER_CYCLE, energy_every=STEPS_PER_CYCLE)
@@ -238,7 +249,8 @@ def run_gpu(args):
     if rank == 0:
         prof = res["prof"]
         force_ms_per_launch = prof.force_ms / max(1, prof.force_launches)
-        bpa = algorithmic_bytes_per_atom(prof.mean_neighbors)
+        half = res["tuned"]["half_list"]
+        bpa = algorithmic_bytes_per_atom(prof.mean_neighbors, half)
         achieved = bpa * s.n / (force_ms_per_launch / 1e3) / 1e9
         peak, peak_kind = measured_peaks()
         traffic = ncu_traffic()
@@ -251,13 +263,14 @@ def run_gpu(args):
             "data": "synthetic", "config": config_dict(s),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_force_mixed_full (fused velocity-Verlet epilogue)",
+                         "kernel": ("k_force_mixed_half" if half else
+                                    "k_force_mixed_full (fused velocity-Verlet epilogue)"),
                          "bytes_per_atom": bpa, "mean_neighbors": prof.mean_neighbors,
                          "launch_ms": force_ms_per_launch, "peak_source": peak_kind},
             "phases_ms_per_timestep": {
                 "force": prof.force_ms / prof.steps, "neigh": prof.neigh_ms / prof.steps,
                 "other": prof.other_ms / prof.steps},
-            "fp64_path": {"value": fp64_value, "ms_per_step": fp64_ms,
+            "fp64_path": {"value": fp64_value, "ms_per_step": fp64_ms, "tuned": res["tuned64"],
                           "phases_ms_per_timestep": {
                               "force": res["prof64"].force_ms / res["prof64"].steps,
                               "neigh": res["prof64"].neigh_ms / res["prof64"].steps,
@@ -347,7 +360,8 @@ def run_reference(args):
             "n_gpus": int(os.environ.get("WORLD_SIZE", args.gpus)), "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_dict(s),
+            "config": dict(config_dict(s), tuned=res["tuned"],
+                           list="half" if res["tuned"]["half_list"] else "full"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{args.steps} oracle time steps of the full workload "
                                        f"after {max(1, args.warmup)} warm-up steps; list "

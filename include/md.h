@@ -72,8 +72,10 @@ typedef struct {
     int32_t rebuild_every;   /* rebuild cells + list after the drift of step n when
                                 n % rebuild_every == 0 (plus once at start)          */
     int32_t precision;       /* MD_FP64 or MD_MIXED                                 */
-    int32_t half_list;       /* 0: full lists; 1: half lists (pair (i,j) stored
-                                with i iff id_j > id_i)                              */
+    int32_t half_list;       /* 0: full lists; 1: half lists: pair (i,j) stored
+                                with i iff j's nearest image is in i's upper
+                                half-space (del = x_i - x_j: del.z < 0, ties by
+                                del.y, del.x, then id_j > id_i)                 */
     int32_t threads_per_atom;/* 0 = tuned default; 1, 2 or 4 lanes per atom in the
                                 full-list force kernels                              */
 } md_params;
@@ -92,10 +94,10 @@ typedef struct {
 } md_info;
 
 /* Per-phase device time of md_profile (Force / Neigh / Other, the
- * breakdown of the paper's Fig. 4 and 5).  "force" is the force kernel with
- * its fused velocity-Verlet epilogue; "neigh" is binning plus list build;
- * "other" is every remaining kernel (first drift, energies, half-list
- * integration). */
+ * breakdown of the paper's Fig. 4 and 5).  "force" is the force kernel alone
+ * (with its fused velocity-Verlet epilogue on full lists); "neigh" is binning
+ * plus list build; "other" is everything else (first drift, energies, the
+ * half-list force clear and integration). */
 typedef struct {
     double force_ms, neigh_ms, other_ms;
     int64_t force_launches, neigh_launches, other_launches;
@@ -198,6 +200,27 @@ int md_set_capacity(md_ctx *ctx, int32_t cap);
  * one by one with a CUDA event pair around each phase on the context stream,
  * and reports the device time per phase.  Synchronises. */
 int md_profile(md_ctx *ctx, int64_t nsteps, md_phase_times *out);
+
+/* Changes epsilon and sigma (both > 0); forces are recomputed on next use. */
+int md_set_lj(md_ctx *ctx, double epsilon, double sigma);
+
+/* Differentiable rollout (not in the paper; it differentiates the Sec. 3.2
+ * Eq. 1 / Eq. 2 forward map).  From the current state (x0, v0) of a
+ * single-system context, runs nsteps velocity-Verlet steps with the rebuild
+ * schedule counted from this call (rebuild at step 0 and whenever
+ * step % rebuild_every == 0) and returns
+ *     loss = (1/window) * sum_{n = nsteps-window+1 .. nsteps} PE(x_n)
+ * and its gradient with respect to epsilon, sigma (rc held fixed), x0 and v0
+ * by a hand-written reverse sweep: states are checkpointed every ckpt_every
+ * steps and each block is recomputed bit-exactly (same list, same kernels)
+ * before it is reversed.  g_x0 / g_v0: host, n x 3 doubles in caller order
+ * (each may be NULL).  The context is left at (x0, v0).  Work memory is
+ * allocated for the call and freed before it returns.
+ * Errors: MD_ERR_INVAL (nrep != 1; window not in [1, nsteps]; ckpt_every not
+ * dividing both rebuild_every and nsteps), MD_ERR_NOMEM, MD_ERR_CUDA and
+ * those of md_run. */
+int md_adjoint(md_ctx *ctx, int64_t nsteps, int64_t window, int32_t ckpt_every, double *loss,
+               double *g_eps, double *g_sigma, double *g_x0, double *g_v0);
 
 /* Chooses threads_per_atom and full/half lists by timing each candidate for
  * `steps` steps on the context's own state (which it restores), keeps the

@@ -38,7 +38,11 @@
  *     (cx*nc_y + cy)*nc_z + cz;
  *   - binning is a stable counting sort (atoms of a cell in ascending id);
  *   - when nc < 3 the 27 neighbour cells are de-duplicated;
- *   - a half list keeps pair (i,j) in row i iff j > i;
+ *   - a half list keeps pair (i,j) in row i iff j's nearest image lies in
+ *     i's upper half-space: del = x_i - x_j (minimum image) has del.z < 0,
+ *     or del.z == 0 and del.y < 0, or both zero and del.x < 0, or del == 0
+ *     and j > i (del of the pair seen from j is exactly -del, so each pair
+ *     is kept once, and every row holds about half of its neighbours);
  *   - rebuild after the drift of step n iff n % rebuild_every == 0, plus an
  *     initial build at step 0;
  *   - KE = 1/2 m sum v^2, W = sum over pairs of f*r^2 (= sum r_ij . F_ij).
@@ -146,6 +150,16 @@ static void displacement(const double *x, int64_t i, int64_t j, const double L[3
         del[d] = min_image(x[3 * i + d] - x[3 * j + d], L[d]);
 }
 
+/* Half-list ownership of the pair (i, j) with displacement del = x_i - x_j
+ * (minimum image): j's image in i's upper half-space (header comment). */
+static int half_owner(const double del[3], int64_t i, int64_t j)
+{
+    if (del[2] != 0.0) return del[2] < 0.0;
+    if (del[1] != 0.0) return del[1] < 0.0;
+    if (del[0] != 0.0) return del[0] < 0.0;
+    return j > i;
+}
+
 static double norm2(const double del[3])
 {
     double a = del[0] * del[0];
@@ -170,10 +184,10 @@ int32_t orc_neighbors_brute(int64_t n, const double *x, const double L[3], doubl
         int32_t k = 0;
         for (int64_t j = 0; j < n; j++) {
             if (j == i) continue;
-            if (half && j < i) continue;
             double del[3];
             displacement(x, i, j, L, del);
             if (norm2(del) < r2) {
+                if (half && !half_owner(del, i, j)) continue;
                 if (k < cap) list[i * cap + k] = (int32_t)j;
                 k++;
             }
@@ -225,10 +239,10 @@ int32_t orc_neighbors_cells(int64_t n, const double *x, const double L[3], const
             for (int32_t t = cell_start[cells[q]]; t < cell_start[cells[q] + 1]; t++) {
                 int64_t j = cell_atoms[t];
                 if (j == i) continue;
-                if (half && j < i) continue;
                 double del[3];
                 displacement(x, i, j, L, del);
                 if (norm2(del) < r2) {
+                    if (half && !half_owner(del, i, j)) continue;
                     if (k < cap) list[i * cap + k] = (int32_t)j;
                     k++;
                 }

@@ -54,7 +54,10 @@ __global__ void __launch_bounds__(256) k_bin_assign(Dev d)
     d.x[a] = mk_dvec4(c[0], c[1], c[2], 0.0);
     int32_t key = (int32_t)(R.cell_off + ((int64_t)k[0] * R.nc[1] + k[1]) * R.nc[2] + k[2]);
     d.cell_key[a] = key;
-    atomicAdd(&d.cell_count[key], 1);
+    // atoms arrive roughly in cell order, so lanes of a warp share cells:
+    // one atomic per distinct cell of the warp
+    const unsigned same = __match_any_sync(__activemask(), key);
+    if ((threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&d.cell_count[key], __popc(same));
 }
 
 // Block-wide exclusive scan of 4 values per thread (1024 threads).

@@ -2,6 +2,15 @@
 // every j within r = rc + skin; half lists store each pair once; Sec. 4.2:
 // neighbour-major layout on GPUs).
 //
+// Half-list ownership: pair (i, j) is stored in row i iff j's image lies in
+// i's upper half-space: del = x_i - x_j (FP64, as the list criterion) has
+// del.z < 0, ties broken by del.y < 0, del.x < 0, then id_j > id_i.  del is
+// exactly antisymmetric, so each pair is stored once and rows are balanced.
+// Cell coordinates are monotone in z, so a lower neighbour cell that is not a
+// periodic image holds no owned atom (skipped), an upper one holds only owned
+// atoms, and only the same z-layer and image cells need the sign test (FP32,
+// or FP64 when the FP32 value is within 1e-4 of zero).
+//
 // The list criterion is exact FP64: r^2 = ((dx*dx + dy*dy) + dz*dz) with dx
 // the minimum-image difference, each operation rounded, compared strictly
 // with (rc+skin)^2.  GB300's FP64 rate is a small fraction of its FP32 rate,
@@ -43,6 +52,25 @@ __device__ __forceinline__ double image_diff(double xi, double xj, int k, double
     return t;
 }
 
+// Half-list ownership of candidate j (FP32 d = p_i + o(-s) - p_j first; the
+// exact FP64 del when the FP32 z-component is within 1e-4 of zero).
+__device__ __forceinline__ bool owns(const Dev &d, const LJ &lj, int64_t i, int32_t j, int32_t idi,
+                                     float dx, float dy, float dz, int kx, int ky, int kz,
+                                     const Rep &R, dvec4 &xi, bool &have_xi)
+{
+    (void)lj; (void)dx; (void)dy;
+    if (fabsf(dz) > 1e-4f) return dz < 0.f;
+    if (!have_xi) { xi = d.x[i]; have_xi = true; }
+    const dvec4 xj = d.x[j];
+    const double ez = image_diff(xi.z, xj.z, kz, R.L[2]);
+    if (ez != 0.0) return ez < 0.0;
+    const double ey = image_diff(xi.y, xj.y, ky, R.L[1]);
+    if (ey != 0.0) return ey < 0.0;
+    const double ex = image_diff(xi.x, xj.x, kx, R.L[0]);
+    if (ex != 0.0) return ex < 0.0;
+    return d.id[j] > idi;
+}
+
 // Builds row i; returns its length (rows longer than the capacity are
 // counted in full but stored only up to the capacity).
 template <bool BATCHED, bool HALF>
@@ -77,14 +105,18 @@ __device__ __forceinline__ int32_t build_row(const Dev &d, const LJ &lj, int64_t
                 if (uz < 0) { uz += R.nc[2]; kz = -1; } else if (uz >= R.nc[2]) { uz -= R.nc[2]; kz = 1; }
                 const float qz = pi.z + (float)oz * R.nsf[2];
                 const int32_t j0 = d.cell_start[col + uz], j1 = d.cell_start[col + uz + 1];
-                const uint32_t tag = (uint32_t)((ox + 1) * 9 + (oy + 1) * 3 + (oz + 1)) << kJBits;
+                const int slot = (ox + 1) * 9 + (oy + 1) * 3 + (oz + 1);
+                if (HALF && oz < 0 && kz == 0) continue;        // entirely below
+                const bool test_sign = HALF && (oz == 0 || kz != 0);
+                const uint32_t tag = (uint32_t)slot << kJBits;
                 for (int32_t j = j0; j < j1; j++) {
                     const float4 pj = __ldg(p32 + j);
                     const float dx = qx - pj.x, dy = qy - pj.y, dz = qz - pj.z;
                     const float r2f = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                     if (!(r2f < hi)) continue;                 // clearly outside rs
                     if (j == i) continue;
-                    if (HALF && d.id[j] <= idi) continue;
+                    if (test_sign && !owns(d, lj, i, j, idi, dx, dy, dz, kx, ky, kz, R, xi, have_xi))
+                        continue;
                     if (!(r2f < lo)) {                         // inside the band: decide in FP64
                         if (!have_xi) { xi = d.x[i]; have_xi = true; }
                         const dvec4 xj = d.x[j];

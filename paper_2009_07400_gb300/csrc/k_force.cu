@@ -123,14 +123,18 @@ __device__ __forceinline__ void epilogue(const Dev &d, const LJ &lj, const Rep &
 // ---------------------------------------------------------------------------
 // Mixed precision, full list.
 // ---------------------------------------------------------------------------
+#ifndef MD_OFFSET_MODE
+#define MD_OFFSET_MODE 1
+#endif
+#ifndef MD_FORCE_MINBLOCKS
+#define MD_FORCE_MINBLOCKS 1
+#endif
+
+// One tile of atoms of the mixed full-list kernel (tile = gt / blockDim).
 template <int TPA, bool BATCHED, int EPI, bool ENERGY>
-__global__ void __launch_bounds__(256) k_force_mixed_full(Dev d, LJ lj)
+__device__ __forceinline__ void mixed_full_tile(const Dev &d, const LJ &lj, const float4 (&otab)[32],
+                                                const float (&ot)[3][32], int64_t gt)
 {
-    __shared__ float4 otab[32];
-    if (threadIdx.x < 32) otab[threadIdx.x] = stencil_entry(threadIdx.x);
-    __syncthreads();
-    if (stopped(d.status)) return;
-    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t i0 = gt / TPA;
     const int sub = (int)(gt % TPA);
     const bool valid = i0 < d.n;
@@ -147,14 +151,35 @@ __global__ void __launch_bounds__(256) k_force_mixed_full(Dev d, LJ lj)
     float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
     float pe = 0.f, w = 0.f, cpe = 0.f, cw = 0.f;
     const float4 *p32 = d.p32;
+    // p_i shifted by o*(-s) for o = -1, 0, +1 (mode 2)
+    const float qx0 = pi.x - nsx, qx2 = pi.x + nsx;
+    const float qy0 = pi.y - nsy, qy2 = pi.y + nsy;
+    const float qz0 = pi.z - nsz, qz2 = pi.z + nsz;
 
     // one pair: adds f*d to (px, py, pz) and, with ENERGY, V and f r^2
     auto pair = [&](uint32_t e, float &px, float &py, float &pz, float &pv, float &pw) {
         const float4 pj = __ldg(p32 + (e & kJMask));
-        const float4 o = otab[e >> kJBits];
-        const float dx = fmaf(o.x, nsx, pi.x - pj.x);
-        const float dy = fmaf(o.y, nsy, pi.y - pj.y);
-        const float dz = fmaf(o.z, nsz, pi.z - pj.z);
+        const uint32_t slot = e >> kJBits;
+        float dx, dy, dz;
+        if (MD_OFFSET_MODE == 0) {
+            const float4 o = otab[slot];
+            dx = fmaf(o.x, nsx, pi.x - pj.x);
+            dy = fmaf(o.y, nsy, pi.y - pj.y);
+            dz = fmaf(o.z, nsz, pi.z - pj.z);
+        } else if (MD_OFFSET_MODE == 1) {
+            dx = fmaf(ot[0][slot], nsx, pi.x - pj.x);
+            dy = fmaf(ot[1][slot], nsy, pi.y - pj.y);
+            dz = fmaf(ot[2][slot], nsz, pi.z - pj.z);
+        } else {
+            // slot = 9 (ox+1) + 3 (oy+1) + (oz+1); padding (27) has ox = +2
+            const uint32_t sx3 = slot / 9, r9 = slot - 9 * sx3, sy3 = r9 / 3, sz3 = r9 - 3 * sy3;
+            const float qx = sx3 == 0 ? qx0 : (sx3 == 1 ? pi.x : (sx3 == 2 ? qx2 : 3.0e4f));
+            const float qy = sy3 == 0 ? qy0 : (sy3 == 1 ? pi.y : qy2);
+            const float qz = sz3 == 0 ? qz0 : (sz3 == 1 ? pi.z : qz2);
+            dx = qx - pj.x;
+            dy = qy - pj.y;
+            dz = qz - pj.z;
+        }
         const float rsq = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
         const float sr2 = rcp_approx(rsq);
         const float t = sr2 * sr2 * sr2 * lj.sigma6f;
@@ -212,6 +237,51 @@ __global__ void __launch_bounds__(256) k_force_mixed_full(Dev d, LJ lj)
     }
     epilogue<EPI, ENERGY>(d, lj, R, i, (double)fx, (double)fy, (double)fz,
                           __float_as_uint(pi.w), true);
+}
+
+// Stencil offsets o of the 27 slots (slot 27: padding, far away), scaled by
+// -s in the pair loop.  Mode 0: one float4 table (LDS.128); mode 1: three
+// float tables, each read with a conflict-free LDS.32 (27 words in 27
+// banks); mode 2: no table, a per-dimension select between p_i - s, p_i and
+// p_i + s.  Mode 1 measured fastest on GB300 (L1 data pipe is the limit).
+__device__ __forceinline__ void fill_offsets(float4 (&otab)[32], float (&ot)[3][32])
+{
+    if (threadIdx.x < 32) {
+        const float4 o = stencil_entry(threadIdx.x);
+        otab[threadIdx.x] = o;
+        ot[0][threadIdx.x] = o.x;
+        ot[1][threadIdx.x] = o.y;
+        ot[2][threadIdx.x] = o.z;
+    }
+    __syncthreads();
+}
+
+template <int TPA, bool BATCHED, int EPI, bool ENERGY>
+__global__ void __launch_bounds__(256, MD_FORCE_MINBLOCKS) k_force_mixed_full(Dev d, LJ lj)
+{
+    __shared__ float4 otab[32];
+    __shared__ float ot[3][32];
+    fill_offsets(otab, ot);
+    if (stopped(d.status)) return;
+    mixed_full_tile<TPA, BATCHED, EPI, ENERGY>(d, lj, otab, ot,
+                                               (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// Persistent form: block b walks the contiguous tile range
+// [b * ntiles / grid, (b + 1) * ntiles / grid) of cell-ordered atoms, so
+// consecutive tiles of a block share most neighbours in L1.
+template <bool BATCHED, int EPI, bool ENERGY>
+__global__ void __launch_bounds__(256, MD_FORCE_MINBLOCKS) k_force_mixed_full_persist(Dev d, LJ lj,
+                                                                                      int64_t ntiles)
+{
+    __shared__ float4 otab[32];
+    __shared__ float ot[3][32];
+    fill_offsets(otab, ot);
+    if (stopped(d.status)) return;
+    const int64_t t0 = (int64_t)blockIdx.x * ntiles / gridDim.x;
+    const int64_t t1 = (int64_t)(blockIdx.x + 1) * ntiles / gridDim.x;
+    for (int64_t t = t0; t < t1; t++)
+        mixed_full_tile<1, BATCHED, EPI, ENERGY>(d, lj, otab, ot, t * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -426,14 +496,43 @@ __global__ void __launch_bounds__(256) k_force_f64_half(Dev d, LJ lj)
     }
 }
 
+// The persistent walk measured slower on GB300 (171.5 vs 160.9 us at 1M
+// atoms), so the plain grid is the default.
+#ifndef MD_FORCE_PERSIST
+#define MD_FORCE_PERSIST 0
+#endif
+
+// Blocks of the persistent mixed kernel that fit on the GPU at once.
+template <bool B, int EP, bool EN>
+unsigned persist_grid(int64_t ntiles)
+{
+    static int blocks = -1, sms = 0;
+    if (blocks < 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaFuncSetAttribute(k_force_mixed_full_persist<B, EP, EN>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_force_mixed_full_persist<B, EP, EN>,
+                                                      256, 0);
+        if (blocks < 1) blocks = 1;
+    }
+    const int64_t g = (int64_t)blocks * sms;
+    return (unsigned)(g < ntiles ? g : ntiles);
+}
+
 template <int TPA, bool B>
 int launch_full(const Dev &d, const LJ &lj, bool mixed, int epi, bool energy, cudaStream_t st)
 {
     const int64_t threads = d.n * TPA;
     const unsigned g = (unsigned)((threads + 255) / 256);
+    const int64_t ntiles = (d.n + 255) / 256;
 #define MD_FULL(EP, EN)                                                                    \
     do {                                                                                   \
-        if (mixed) k_force_mixed_full<TPA, B, EP, EN><<<g, 256, 0, st>>>(d, lj);           \
+        if (mixed && TPA == 1 && MD_FORCE_PERSIST)                                         \
+            k_force_mixed_full_persist<B, EP, EN>                                          \
+                <<<persist_grid<B, EP, EN>(ntiles), 256, 0, st>>>(d, lj, ntiles);         \
+        else if (mixed) k_force_mixed_full<TPA, B, EP, EN><<<g, 256, 0, st>>>(d, lj);      \
         else k_force_f64_full<TPA, B, EP, EN><<<g, 256, 0, st>>>(d, lj);                   \
     } while (0)
     if (epi == EPI_F) { if (energy) MD_FULL(EPI_F, true); else MD_FULL(EPI_F, false); }
@@ -444,6 +543,18 @@ int launch_full(const Dev &d, const LJ &lj, bool mixed, int epi, bool energy, cu
 }
 
 }  // namespace
+
+// Sets the carveout and caches the occupancy of every persistent force-kernel
+// instance (outside any stream capture).
+void init_force_kernels()
+{
+    persist_grid<false, EPI_F, false>(1); persist_grid<false, EPI_F, true>(1);
+    persist_grid<false, EPI_FK, false>(1); persist_grid<false, EPI_FK, true>(1);
+    persist_grid<false, EPI_FKKD, false>(1); persist_grid<false, EPI_FKKD, true>(1);
+    persist_grid<true, EPI_F, false>(1); persist_grid<true, EPI_F, true>(1);
+    persist_grid<true, EPI_FK, false>(1); persist_grid<true, EPI_FK, true>(1);
+    persist_grid<true, EPI_FKKD, false>(1); persist_grid<true, EPI_FKKD, true>(1);
+}
 
 // Half lists only support EPI_F (the caller zeroes the force array first and
 // integrates in a separate kernel).

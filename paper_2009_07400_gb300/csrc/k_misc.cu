@@ -98,20 +98,24 @@ __global__ void __launch_bounds__(256) k_energy_chunks(Dev d, LJ lj, const int64
     }
 }
 
-// One block: thread t sums quantity t%3 of replica t/3 over its chunks in
-// order (deterministic).  With log_base the record goes to the on-device
-// energy log at the cursor, which the block then advances.
+// One block; warp w sums (replica, quantity) pairs t = w, w + 32, ...: lane l
+// adds chunks l, l+32, ... in order, then a fixed shuffle tree combines the
+// lanes, so the result does not depend on scheduling.  With log_base the
+// record goes to the on-device energy log at the cursor, which the block then
+// advances.
 __global__ void __launch_bounds__(1024) k_energy_final(const int64_t *chunk_first, int32_t nrep,
                                                        const double *partials, double *out,
                                                        double *log_base, DevStatus *st)
 {
     if (stopped(st)) return;
     double *dst = out ? out : log_base + st->elog_cursor * 3 * (int64_t)nrep;
-    for (int64_t t = threadIdx.x; t < 3 * (int64_t)nrep; t += blockDim.x) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int64_t t = w; t < 3 * (int64_t)nrep; t += 32) {
         const int64_t r = t / 3, q = t % 3;
         double s = 0;
-        for (int64_t c = chunk_first[r]; c < chunk_first[r + 1]; c++) s += partials[3 * c + q];
-        dst[t] = s;
+        for (int64_t c = chunk_first[r] + lane; c < chunk_first[r + 1]; c += 32) s += partials[3 * c + q];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) dst[t] = s;
     }
     __syncthreads();
     if (!out && threadIdx.x == 0) st->elog_cursor += 1;

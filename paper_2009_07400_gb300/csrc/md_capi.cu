@@ -224,14 +224,17 @@ int enq_energy(md_ctx *c, bool ke_from_v, double *out3, int *nl)
 
 // Forces at the current positions followed by `epi` (EPI_F / EPI_FK /
 // EPI_FKKD); with `energy`, per-atom PE/W (and KE of the full-step v).
-int enq_force(md_ctx *c, int epi, bool energy, int *nl)
+// ev (optional): an event pair recorded around the force kernel alone.
+int enq_force(md_ctx *c, int epi, bool energy, int *nl, cudaEvent_t *ev = nullptr)
 {
     Dev d = view(c);
     if (is_half(c)) {
         if (is_mixed(c)) CK(cudaMemsetAsync(c->f32, 0, sizeof(float4) * c->n, c->st));
         else CK(cudaMemsetAsync(c->f64, 0, sizeof(dvec4) * c->n, c->st));
+        if (ev) CK(cudaEventRecord(ev[0], c->st));
         if (launch_force(d, c->lj, c->p.precision, true, 1, EPI_F, energy, batched(c), c->st, nl))
             return fail(c, MD_ERR_CUDA, "force launch failed");
+        if (ev) CK(cudaEventRecord(ev[1], c->st));
         if (epi == EPI_FK) {
             if (launch_integrate(d, c->lj, c->p.precision, 2, batched(c), c->st, nl))
                 return fail(c, MD_ERR_CUDA, "integrate launch failed");
@@ -240,9 +243,11 @@ int enq_force(md_ctx *c, int epi, bool energy, int *nl)
                 return fail(c, MD_ERR_CUDA, "integrate launch failed");
         }
     } else {
+        if (ev) CK(cudaEventRecord(ev[0], c->st));
         if (launch_force(d, c->lj, c->p.precision, false, c->tpa, epi, energy, batched(c), c->st,
                          nl))
             return fail(c, MD_ERR_CUDA, "force launch failed");
+        if (ev) CK(cudaEventRecord(ev[1], c->st));
         if (epi == EPI_FKKD) {
             c->pb = 1 - c->pb;
             if (!is_mixed(c)) c->xp = 1 - c->xp;
@@ -441,6 +446,33 @@ int run_span(md_ctx *c, int64_t s0, int64_t first, int64_t last, bool kd, int32_
 
 int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64_t *counts,
                  int32_t nrep, const double *pos, const double *vel, void *stream);
+
+// LJ constants of c->p (the same expressions as the FP64 definition).
+void set_lj_constants(md_ctx *c)
+{
+    const md_params &q = c->p;
+    const double rs = q.cutoff + q.skin;
+    LJ &lj = c->lj;
+    lj.rc2 = q.cutoff * q.cutoff;
+    lj.rs2 = rs * rs;
+    const double s2 = q.sigma * q.sigma;
+    lj.sigma6 = s2 * s2 * s2;
+    lj.sigma = q.sigma;
+    lj.c48e = 48.0 * q.epsilon;
+    lj.c24e = 24.0 * q.epsilon;
+    lj.c4e = 4.0 * q.epsilon;
+    lj.eps = q.epsilon;
+    lj.rc2f = (float)lj.rc2;
+    lj.sigma6f = (float)lj.sigma6;
+    lj.c48ef = (float)lj.c48e;
+    lj.c24ef = (float)lj.c24e;
+    lj.c4ef = (float)lj.c4e;
+    lj.half_dt_m = 0.5 * q.dt / q.mass;
+    lj.dt = q.dt;
+    lj.mass = q.mass;
+    lj.rs2f_lo = (float)(lj.rs2 * (1.0 - 2.5e-4));
+    lj.rs2f_hi = (float)(lj.rs2 * (1.0 + 2.5e-4));
+}
 
 // Process-wide autotuner cache: (precision, log2 atoms per replica, batched)
 // -> (threads per atom, half list).
@@ -803,16 +835,23 @@ int md_profile(md_ctx *c, int64_t nsteps, md_phase_times *out)
         if (n % every == 0) ops.push_back({Op::REBUILD, n, false, false});
         ops.push_back({Op::FORCE, n, n == s0 + nsteps, false});
     }
-    std::vector<cudaEvent_t> ev(2 * ops.size());
+    // per op: an outer event pair around all of its launches and, for force
+    // ops, an inner pair around the force kernel alone
+    std::vector<cudaEvent_t> ev(4 * ops.size());
     for (auto &e : ev) CK(cudaEventCreate(&e));
     CK(cudaMemsetAsync(&c->status->rebuild_count, 0, sizeof(int64_t), c->st));
-    std::vector<int> cat(ops.size()), nls(ops.size());
+    std::vector<int> nls(ops.size());
     for (size_t k = 0; k < ops.size(); k++) {
         int nl = 0;
-        CK(cudaEventRecord(ev[2 * k], c->st));
-        if ((rc = enq_op(c, ops[k], &nl))) break;
-        CK(cudaEventRecord(ev[2 * k + 1], c->st));
-        cat[k] = ops[k].kind == Op::REBUILD ? 1 : (ops[k].kind == Op::FORCE ? 0 : 2);
+        CK(cudaEventRecord(ev[4 * k], c->st));
+        if (ops[k].kind == Op::FORCE) {
+            const int epi = ops[k].last ? EPI_FK : EPI_FKKD;
+            rc = enq_force(c, epi, ops[k].energy, &nl, &ev[4 * k + 2]);
+        } else {
+            rc = enq_op(c, ops[k], &nl);
+        }
+        if (rc) break;
+        CK(cudaEventRecord(ev[4 * k + 1], c->st));
         nls[k] = nl;
         c->launches += nl;
         if (ops[k].kind == Op::REBUILD) c->rebuilds++;
@@ -824,14 +863,21 @@ int md_profile(md_ctx *c, int64_t nsteps, md_phase_times *out)
         if (!rc) c->last_max = s.max_count;
     }
     for (size_t k = 0; !rc && k < ops.size(); k++) {
-        float ms = 0;
-        CK(cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]));
-        double *dst = cat[k] == 0 ? &out->force_ms : cat[k] == 1 ? &out->neigh_ms : &out->other_ms;
-        int64_t *cnt = cat[k] == 0 ? &out->force_launches : cat[k] == 1 ? &out->neigh_launches : &out->other_launches;
-        // a half-list FORCE op also launches the integration kernel; its time
-        // stays in "force" (the fused epilogue does the same work)
-        *dst += ms;
-        *cnt += nls[k];
+        float all = 0, kern = 0;
+        CK(cudaEventElapsedTime(&all, ev[4 * k], ev[4 * k + 1]));
+        if (ops[k].kind == Op::FORCE) {
+            CK(cudaEventElapsedTime(&kern, ev[4 * k + 2], ev[4 * k + 3]));
+            out->force_ms += kern;
+            out->force_launches += 1;
+            out->other_ms += all - kern;
+            out->other_launches += nls[k] - 1;
+        } else if (ops[k].kind == Op::REBUILD) {
+            out->neigh_ms += all;
+            out->neigh_launches += nls[k];
+        } else {
+            out->other_ms += all;
+            out->other_launches += nls[k];
+        }
     }
     for (auto &e : ev) cudaEventDestroy(e);
     if (rc) return rc;
@@ -843,6 +889,179 @@ int md_profile(md_ctx *c, int64_t nsteps, md_phase_times *out)
     for (int32_t q : cnt) sum += q;
     out->mean_neighbors = sum / (double)c->n;
     return MD_OK;
+}
+
+int md_set_lj(md_ctx *c, double epsilon, double sigma)
+{
+    if (!c || !(epsilon > 0) || !(sigma > 0) || !std::isfinite(epsilon) || !std::isfinite(sigma))
+        return fail(c, MD_ERR_INVAL, "bad argument");
+    CK(cudaStreamSynchronize(c->st));
+    c->p.epsilon = epsilon;
+    c->p.sigma = sigma;
+    set_lj_constants(c);
+    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+    c->graphs.clear();
+    c->forces_valid = false;
+    return MD_OK;
+}
+
+int md_adjoint(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt, double *loss,
+               double *g_eps, double *g_sigma, double *g_x0, double *g_v0)
+{
+    if (!c || !loss || nsteps < 1 || window < 1 || window > nsteps || ckpt < 1)
+        return fail(c, MD_ERR_INVAL, "bad argument");
+    if (c->nrep != 1) return fail(c, MD_ERR_INVAL, "md_adjoint takes a single system");
+    const int64_t every = c->p.rebuild_every;
+    if (every % ckpt != 0 || nsteps % ckpt != 0)
+        return fail(c, MD_ERR_INVAL, "ckpt_every must divide rebuild_every and nsteps");
+    const int64_t n = c->n, nck = nsteps / ckpt + 1;
+    const bool mixed = is_mixed(c);
+    const int half0 = c->p.half_list, tpa0 = c->tpa;
+    int rc = MD_OK;
+    if (half0 && (rc = apply_tuning(c, 1, 0))) return rc;   // the adjoint walks full lists
+
+    dvec4 *ck_x = nullptr, *ck_v = nullptr, *blk_x = nullptr, *xbar = nullptr, *wbar = nullptr;
+    float4 *blk_p = nullptr, *ck_p = nullptr;
+    int32_t *ck_id = nullptr;
+    double *ge = nullptr, *gs = nullptr, *g2 = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(ck_x); cudaFree(ck_v); cudaFree(ck_id); cudaFree(ck_p); cudaFree(blk_x); cudaFree(blk_p);
+        cudaFree(xbar); cudaFree(wbar); cudaFree(ge); cudaFree(gs); cudaFree(g2);
+    };
+    if ((rc = dalloc(c, &ck_x, (size_t)(nck * n))) || (rc = dalloc(c, &ck_v, (size_t)(nck * n))) ||
+        (rc = dalloc(c, &ck_id, (size_t)(nck * n))) || (rc = dalloc(c, &ck_p, (size_t)(nck * n))) ||
+        (rc = dalloc(c, &blk_x, (size_t)(ckpt * n))) ||
+        (rc = dalloc(c, &blk_p, (size_t)(ckpt * n))) || (rc = dalloc(c, &xbar, (size_t)n)) ||
+        (rc = dalloc(c, &wbar, (size_t)n)) || (rc = dalloc(c, &ge, (size_t)n)) ||
+        (rc = dalloc(c, &gs, (size_t)n)) || (rc = dalloc(c, &g2, 2))) {
+        cleanup();
+        return rc;
+    }
+    if (window > c->elog_cap) {
+        if (c->elog_d) cudaFree(c->elog_d);
+        c->elog_d = nullptr;
+        if ((rc = dalloc(c, &c->elog_d, (size_t)window * 3))) { cleanup(); return rc; }
+        c->elog_cap = window;
+        for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+        c->graphs.clear();
+    }
+    int nl = 0;
+    auto save_ck = [&](int64_t k) {
+        cudaMemcpyAsync(ck_x + k * n, c->x[c->xp], sizeof(dvec4) * n, cudaMemcpyDeviceToDevice, c->st);
+        cudaMemcpyAsync(ck_v + k * n, c->v[c->vp], sizeof(dvec4) * n, cudaMemcpyDeviceToDevice, c->st);
+        cudaMemcpyAsync(ck_id + k * n, c->id[c->vp], sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, c->st);
+        cudaMemcpyAsync(ck_p + k * n, c->p32[c->pb], sizeof(float4) * n, cudaMemcpyDeviceToDevice, c->st);
+    };
+    auto load_ck = [&](int64_t k, bool with_id) {
+        cudaMemcpyAsync(c->x[c->xp], ck_x + k * n, sizeof(dvec4) * n, cudaMemcpyDeviceToDevice, c->st);
+        cudaMemcpyAsync(c->v[c->vp], ck_v + k * n, sizeof(dvec4) * n, cudaMemcpyDeviceToDevice, c->st);
+        if (with_id)
+            cudaMemcpyAsync(c->id[c->vp], ck_id + k * n, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, c->st);
+        else  // mid-epoch: the FP32 cell-relative copy of the same step
+            cudaMemcpyAsync(c->p32[c->pb], ck_p + k * n, sizeof(float4) * n, cudaMemcpyDeviceToDevice, c->st);
+    };
+    // state at force point cb: the list of its epoch (built from the epoch's
+    // start positions, which re-binning reproduces bit for bit), then x, v
+    auto restore = [&](int64_t cb) -> int {
+        const int64_t e = cb - cb % every;
+        load_ck(e / ckpt, true);
+        c->moved_since_bin = true;
+        int r = rebuild_now(c, true);
+        if (r) return r;
+        if (e != cb) load_ck(cb / ckpt, false);
+        return MD_OK;
+    };
+    auto kick_drift = [&]() -> int {
+        Dev d = view(c);
+        if (launch_integrate(d, c->lj, c->p.precision, 1, false, c->st, &nl))
+            return fail(c, MD_ERR_CUDA, "integrate launch failed");
+        return MD_OK;
+    };
+
+    // ---- forward, with checkpoints ---------------------------------------
+    if ((rc = rebuild_now(c, true))) { cleanup(); return rc; }
+    if ((rc = enq_force(c, EPI_F, false, &nl))) { cleanup(); return rc; }
+    save_ck(0);
+    CK(cudaMemsetAsync(&c->status->elog_cursor, 0, sizeof(int64_t), c->st));
+    for (int64_t s = 1; s <= nsteps && !rc; s++) {
+        if ((rc = kick_drift())) break;
+        if (s % every == 0) {
+            c->moved_since_bin = true;
+            if ((rc = rebuild_now(c, true))) break;
+        }
+        const bool en = s > nsteps - window;
+        if ((rc = enq_force(c, EPI_FK, en, &nl))) break;
+        if (en && (rc = enq_energy(c, true, nullptr, &nl))) break;
+        if (s % ckpt == 0) save_ck(s / ckpt);
+    }
+    std::vector<double> elog((size_t)window * 3);
+    if (!rc) {
+        CK(cudaMemcpyAsync(elog.data(), c->elog_d, sizeof(double) * elog.size(), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        DevStatus st;
+        if (!(rc = read_status(c, &st))) rc = check_flags(c, st);
+    }
+    if (rc) { cleanup(); return rc; }
+    double acc = 0;
+    for (int64_t k = 0; k < window; k++) acc += elog[3 * k];
+    *loss = acc / (double)window;
+
+    // ---- reverse sweep ------------------------------------------------------
+    CK(cudaMemsetAsync(xbar, 0, sizeof(dvec4) * n, c->st));
+    CK(cudaMemsetAsync(wbar, 0, sizeof(dvec4) * n, c->st));
+    CK(cudaMemsetAsync(ge, 0, sizeof(double) * n, c->st));
+    CK(cudaMemsetAsync(gs, 0, sizeof(double) * n, c->st));
+    const double cdt = c->lj.half_dt_m;
+    for (int64_t b = nck - 1; b >= 0 && !rc; b--) {
+        const int64_t cb = b * ckpt;
+        const int64_t npts = (b == nck - 1) ? 1 : ckpt;
+        if ((rc = restore(cb))) break;
+        if ((rc = enq_force(c, EPI_F, false, &nl))) break;
+        for (int64_t m = 0; m < npts && !rc; m++) {
+            if (m > 0) {
+                if ((rc = kick_drift())) break;
+                if ((rc = enq_force(c, EPI_FK, false, &nl))) break;
+            }
+            cudaMemcpyAsync(blk_x + m * n, c->x[c->xp], sizeof(dvec4) * n, cudaMemcpyDeviceToDevice, c->st);
+            cudaMemcpyAsync(blk_p + m * n, c->p32[c->pb], sizeof(float4) * n, cudaMemcpyDeviceToDevice, c->st);
+        }
+        for (int64_t m = npts - 1; m >= 0 && !rc; m--) {
+            const int64_t pt = cb + m;
+            cudaMemcpyAsync(c->x[c->xp], blk_x + m * n, sizeof(dvec4) * n, cudaMemcpyDeviceToDevice, c->st);
+            cudaMemcpyAsync(c->p32[c->pb], blk_p + m * n, sizeof(float4) * n, cudaMemcpyDeviceToDevice, c->st);
+            if (pt < nsteps && launch_adjoint_axpy(n, c->lj.dt, xbar, wbar, c->st, &nl)) {
+                rc = fail(c, MD_ERR_CUDA, "adjoint launch failed");
+                break;
+            }
+            const double k = pt == nsteps ? 0.0 : (pt == 0 ? cdt : 2.0 * cdt);
+            const double lw = pt > nsteps - window ? 1.0 / (double)window : 0.0;
+            if (launch_adjoint_pairs(view(c), c->lj, mixed, wbar, xbar, ge, gs, k, lw, c->st, &nl)) {
+                rc = fail(c, MD_ERR_CUDA, "adjoint launch failed");
+                break;
+            }
+        }
+    }
+    if (!rc && launch_sum2(n, ge, gs, g2, c->st, &nl)) rc = fail(c, MD_ERR_CUDA, "sum launch failed");
+    if (!rc) {
+        double g[2];
+        std::vector<dvec4> hx((size_t)n), hw((size_t)n);
+        CK(cudaMemcpyAsync(g, g2, sizeof(g), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaMemcpyAsync(hx.data(), xbar, sizeof(dvec4) * n, cudaMemcpyDeviceToHost, c->st));
+        CK(cudaMemcpyAsync(hw.data(), wbar, sizeof(dvec4) * n, cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        if (g_eps) *g_eps = g[0];
+        if (g_sigma) *g_sigma = g[1];
+        for (int64_t a = 0; a < n; a++) {
+            if (g_x0) { g_x0[3 * a] = hx[a].x; g_x0[3 * a + 1] = hx[a].y; g_x0[3 * a + 2] = hx[a].z; }
+            if (g_v0) { g_v0[3 * a] = hw[a].x; g_v0[3 * a + 1] = hw[a].y; g_v0[3 * a + 2] = hw[a].z; }
+        }
+        rc = restore(0);            // leave the context at the initial state
+    }
+    c->launches += nl;
+    c->forces_valid = false;
+    cleanup();
+    if (!rc && half0) rc = apply_tuning(c, tpa0, half0);
+    return rc;
 }
 
 int md_autotune(md_ctx *c, int32_t steps, md_params *chosen)
@@ -992,28 +1211,10 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
     c->ncells = cells;
     c->nchunks = (int64_t)chunk_rep.size() / 2;
 
-    // LJ constants (the same expressions as the FP64 definition).
-    LJ &lj = c->lj;
-    lj.rc2 = q.cutoff * q.cutoff;
-    lj.rs2 = rs * rs;
-    const double s2 = q.sigma * q.sigma;
-    lj.sigma6 = s2 * s2 * s2;
-    lj.c48e = 48.0 * q.epsilon;
-    lj.c24e = 24.0 * q.epsilon;
-    lj.c4e = 4.0 * q.epsilon;
-    lj.eps = q.epsilon;
-    lj.rc2f = (float)lj.rc2;
-    lj.sigma6f = (float)lj.sigma6;
-    lj.c48ef = (float)lj.c48e;
-    lj.c24ef = (float)lj.c24e;
-    lj.c4ef = (float)lj.c4e;
-    lj.half_dt_m = 0.5 * q.dt / q.mass;
-    lj.dt = q.dt;
-    lj.mass = q.mass;
-    lj.rs2f_lo = (float)(lj.rs2 * (1.0 - 2.5e-4));
-    lj.rs2f_hi = (float)(lj.rs2 * (1.0 + 2.5e-4));
+    set_lj_constants(c);
 
     CK(cudaGetDevice(&c->device));
+    init_force_kernels();
     if (stream) {
         c->st = (cudaStream_t)stream;
     } else {

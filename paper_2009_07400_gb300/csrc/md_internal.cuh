@@ -59,7 +59,7 @@ struct Rep {
 
 // LJ constants in both precisions.
 struct LJ {
-    double rc2, rs2, sigma6, c48e, c24e, c4e, eps;
+    double rc2, rs2, sigma6, c48e, c24e, c4e, eps, sigma;
     float rc2f, sigma6f, c48ef, c24ef, c4ef;
     double half_dt_m;         // dt / (2 m)
     double dt;
@@ -121,5 +121,15 @@ int launch_decode_list(const Dev &d, int32_t *rows_dev, int32_t cap, cudaStream_
                        int *nlaunch);
 
 int64_t scan_tmp_elems(int64_t ncells_total);
+void init_force_kernels();
+
+// Adjoint (k_adjoint.cu)
+int launch_adjoint_pairs(const Dev &d, const LJ &lj, bool mixed, const dvec4 *wbar, dvec4 *xbar,
+                         double *g_eps, double *g_sig, double k, double lw, cudaStream_t st,
+                         int *nlaunch);
+int launch_adjoint_axpy(int64_t n, double dt, const dvec4 *xbar, dvec4 *wbar, cudaStream_t st,
+                        int *nlaunch);
+int launch_sum2(int64_t n, const double *a, const double *b, double *out, cudaStream_t st,
+                int *nlaunch);
 
 }  // namespace mdk

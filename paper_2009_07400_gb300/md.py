@@ -29,6 +29,7 @@ ABI_SYMBOLS = [
     "md_bin_cells", "md_build_neighbors", "md_compute_forces", "md_integrate", "md_energy",
     "md_run", "md_get_positions", "md_get_velocities", "md_get_forces", "md_get_cells",
     "md_get_neighbors", "md_get_info", "md_autotune", "md_set_capacity", "md_profile",
+    "md_set_lj", "md_adjoint",
 ]
 
 
@@ -108,6 +109,9 @@ def load(path: str | None = None):
                 "md_autotune": [ctx, ctypes.c_int32, ctypes.POINTER(md_params)],
                 "md_set_capacity": [ctx, ctypes.c_int32],
                 "md_profile": [ctx, ctypes.c_int64, ctypes.POINTER(md_phase_times)],
+                "md_set_lj": [ctx, ctypes.c_double, ctypes.c_double],
+                "md_adjoint": [ctx, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, _D, _D, _D,
+                               _D, _D],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -262,6 +266,21 @@ class MDContext:
         out = md_phase_times()
         self._check(self._lib.md_profile(self._h, int(nsteps), ctypes.byref(out)))
         return out
+
+    def set_lj(self, epsilon, sigma):
+        self._check(self._lib.md_set_lj(self._h, float(epsilon), float(sigma)))
+
+    def adjoint(self, nsteps, window, ckpt_every=10):
+        """(loss, dL/deps, dL/dsigma, dL/dx0 (n x 3), dL/dv0 (n x 3))."""
+        loss = ctypes.c_double()
+        ge = ctypes.c_double()
+        gs = ctypes.c_double()
+        gx = np.zeros((self.n, 3))
+        gv = np.zeros((self.n, 3))
+        self._check(self._lib.md_adjoint(self._h, int(nsteps), int(window), int(ckpt_every),
+                                         ctypes.byref(loss), ctypes.byref(ge), ctypes.byref(gs),
+                                         gx.ctypes.data_as(_D), gv.ctypes.data_as(_D)))
+        return loss.value, ge.value, gs.value, gx, gv
 
     def set_capacity(self, cap):
         self._check(self._lib.md_set_capacity(self._h, int(cap)))

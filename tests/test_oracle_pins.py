@@ -156,6 +156,8 @@ def test_fcc_lattice(orc, n_cells, density):
     z_skin = shell_count(density, RC + SKIN)
     assert {len(r) for r in full} == {z_skin}
     assert sum(len(r) for r in half) * 2 == z_skin * s.n
+    # half rows are balanced: each row holds about half of its neighbours
+    assert max(len(r) for r in half) <= 0.75 * z_skin
     within_rc = orc.neighbors_cells(x, s.box, RC)
     assert {len(r) for r in within_rc} == {shell_count(density, RC)}
     pe_exact, w_exact = lattice_sums(density)
@@ -187,11 +189,13 @@ def test_cells_equal_brute(orc, L, n, half):
     for ra, rb in zip(a, b):
         assert len(set(rb.tolist())) == len(rb)          # no duplicates
         assert sorted(ra.tolist()) == sorted(rb.tolist())
-    # a half list is the j > i part of the full list
+    # a half list holds every pair of the full list exactly once
     if half:
         full = orc.neighbors_brute(x, s.box, RC + SKIN)
-        for i, (rf, rh) in enumerate(zip(full, b)):
-            assert sorted(j for j in rf.tolist() if j > i) == sorted(rh.tolist())
+        pairs_full = {(min(i, j), max(i, j)) for i, r in enumerate(full) for j in r.tolist()}
+        pairs_half = [(min(i, j), max(i, j)) for i, r in enumerate(b) for j in r.tolist()]
+        assert len(pairs_half) == len(set(pairs_half)) == len(pairs_full)
+        assert set(pairs_half) == pairs_full
 
 
 def test_binning(orc):
