@@ -228,6 +228,27 @@ int md_adjoint(md_ctx *ctx, int64_t nsteps, int64_t window, int32_t ckpt_every, 
  * (precision, atoms-per-replica bucket) for the life of the process. */
 int md_autotune(md_ctx *ctx, int32_t steps, md_params *chosen);
 
+/* Allocation-free FP64 totals: out3[0] = sum pe_atom, out3[1] = 1/2 mass
+ * sum |v|^2, out3[2] = sum w_atom, for callers that cannot allocate device
+ * memory where they need these totals (an external engine that reserved the
+ * whole GPU for its own pool, a fixed device-memory budget, or a loop that
+ * must not call cudaMalloc because it can synchronise the device).  The
+ * paper has no counterpart; this is a service of the library.
+ *   pe_atom, w_atom: device, n doubles; vel: device, n x 3 doubles (row
+ *   major); out3: device, 3 doubles; stream: cudaStream_t or NULL.
+ * Sums are taken in a fixed order (deterministic).  The only scratch is a
+ * fixed 192 KiB array in the library's device data, so n may be at most
+ * 33,554,432; larger n returns MD_ERR_INVAL with a message from
+ * md_last_error(NULL).  No call allocates or frees device memory.  The first
+ * call on a device looks up that array's device address (once per device,
+ * with the device current): make it before any stream capture.  All calls
+ * share the array: calls that overlap on the GPU (other streams, other
+ * threads) race and must be serialised by the caller.  Every call writes the
+ * scratch it reads, so nothing is left over from an earlier call.
+ * Errors: MD_ERR_INVAL, MD_ERR_CUDA. */
+int md_energy_sums_static(int64_t n, const double *pe_atom, const double *w_atom,
+                          const double *vel, double mass, double *out3, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

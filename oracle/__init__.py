@@ -82,6 +82,8 @@ def _load():
                 "orc_energy_list": (None, [ctypes.c_int64, _D, _D, ctypes.c_int32, _I32, _I32, P,
                                            _D, _D, _D]),
                 "orc_kinetic": (ctypes.c_double, [ctypes.c_int64, _D, ctypes.c_double]),
+                "orc_energy_atoms": (None, [ctypes.c_int64, _D, _D, ctypes.c_int32, _I32, _I32, P,
+                                            _D, _D]),
                 "orc_vv_run": (ctypes.c_int, [ctypes.c_int64, _D, P, _D, _D, _D, ctypes.c_int64,
                                               ctypes.c_int64, _D]),
                 "orc_jvp": (ctypes.c_int, [ctypes.c_int64, _D, P, _D, _D, _D]),
@@ -282,6 +284,18 @@ def energy(x, L, **kw):
     xw = wrap(x, L)
     rows = neighbors_cells(xw, L, p.cutoff + p.skin, half=True)
     return energy_list(xw, L, rows, half=True, **kw)
+
+
+def energy_atoms(x, L, rows, half=False, **kw):
+    """Per-atom (PE, W) arrays over a list (each pair split half and half)."""
+    x = _f64(x, (-1, 3))
+    cap, counts, lst = _pack(rows)
+    pe = np.zeros(x.shape[0], np.float64)
+    w = np.zeros(x.shape[0], np.float64)
+    p = params(half=half, **kw)
+    _load().orc_energy_atoms(x.shape[0], _dp(x), _dp(_box(L)), cap, _ip(counts), _ip(lst),
+                             ctypes.byref(p), _dp(pe), _dp(w))
+    return pe, w
 
 
 def kinetic(v, mass=1.0):

@@ -410,6 +410,37 @@ void orc_energy_list(int64_t n, const double *x, const double L[3], int32_t cap,
     *virial = w;
 }
 
+/* Per-atom split of the potential energy and pair virial over a list (each
+ * pair's V and f r^2 shared half and half by its two atoms); the sums of the
+ * two arrays are the totals of orc_energy_list. */
+void orc_energy_atoms(int64_t n, const double *x, const double L[3], int32_t cap,
+                      const int32_t *counts, const int32_t *list, const orc_params *p,
+                      double *pe_atom, double *w_atom)
+{
+    double rc2 = p->cutoff * p->cutoff;
+    double sigma6 = pow6(p->sigma);
+    for (int64_t i = 0; i < n; i++) {
+        pe_atom[i] = 0.0;
+        w_atom[i] = 0.0;
+    }
+    for (int64_t i = 0; i < n; i++)
+        for (int32_t k = 0; k < counts[i]; k++) {
+            int64_t j = list[i * cap + k];
+            if (!p->half && j < i) continue;
+            double del[3];
+            displacement(x, i, j, L, del);
+            double rsq = norm2(del);
+            if (rsq < rc2) {
+                double v = lj_v(rsq, p->epsilon, sigma6);
+                double w = lj_f(rsq, p->epsilon, sigma6) * rsq;
+                pe_atom[i] += 0.5 * v;
+                pe_atom[j] += 0.5 * v;
+                w_atom[i] += 0.5 * w;
+                w_atom[j] += 0.5 * w;
+            }
+        }
+}
+
 double orc_kinetic(int64_t n, const double *v, double mass)
 {
     double s = 0.0;

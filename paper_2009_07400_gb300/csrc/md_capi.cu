@@ -507,6 +507,11 @@ int apply_tuning(md_ctx *c, int tpa, int half)
 
 }  // namespace
 
+// Error text for calls without a context (read by md_last_error(NULL)).
+namespace mdk {
+void set_global_error(const std::string &msg) { g_create_error = msg; }
+}  // namespace mdk
+
 // ---------------------------------------------------------------------------
 // Public ABI
 // ---------------------------------------------------------------------------

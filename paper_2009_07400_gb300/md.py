@@ -29,7 +29,7 @@ ABI_SYMBOLS = [
     "md_bin_cells", "md_build_neighbors", "md_compute_forces", "md_integrate", "md_energy",
     "md_run", "md_get_positions", "md_get_velocities", "md_get_forces", "md_get_cells",
     "md_get_neighbors", "md_get_info", "md_autotune", "md_set_capacity", "md_profile",
-    "md_set_lj", "md_adjoint",
+    "md_set_lj", "md_adjoint", "md_energy_sums_static",
 ]
 
 
@@ -112,6 +112,7 @@ def load(path: str | None = None):
                 "md_set_lj": [ctx, ctypes.c_double, ctypes.c_double],
                 "md_adjoint": [ctx, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, _D, _D, _D,
                                _D, _D],
+                "md_energy_sums_static": [ctypes.c_int64, _P, _P, _P, ctypes.c_double, _P, _P],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -121,6 +122,17 @@ def load(path: str | None = None):
             lib.md_last_error.restype = ctypes.c_char_p
             _lib = lib
     return _lib
+
+
+def energy_sums_static(n, pe_atom_ptr, w_atom_ptr, vel_ptr, mass, out3_ptr, stream=None):
+    """md_energy_sums_static on device pointers (ints); raises MDError."""
+    lib = load()
+    rc = lib.md_energy_sums_static(int(n), ctypes.c_void_p(pe_atom_ptr), ctypes.c_void_p(w_atom_ptr),
+                                   ctypes.c_void_p(vel_ptr), float(mass),
+                                   ctypes.c_void_p(out3_ptr),
+                                   ctypes.c_void_p(int(stream)) if stream else None)
+    if rc != MD_OK:
+        raise MDError(rc, lib.md_last_error(None).decode())
 
 
 def _f64(a, n):
