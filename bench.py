@@ -33,6 +33,11 @@ sys.path.insert(0, ROOT)
 from paper_2009_07400_gb300 import inputs  # noqa: E402
 
 WORKLOAD = "fcc64_1048576"
+WORKLOADS = {
+    "fcc64": "fcc64_1048576",      # the benchmark configuration (default)
+    "fcc128": "fcc128_8388608",    # sizing run
+    "ensemble": "ensemble256",     # 256 independent replicas, one context
+}
 METRIC = "atom-timesteps/s, LJ 1M atoms, mixed-FP32 vs FP64 path at stated force error"
 UNIT = "atom-timesteps/s"
 STEPS_PER_CYCLE = 20
@@ -40,13 +45,29 @@ FORCE_SRC = os.path.join(ROOT, "paper_2009_07400_gb300", "csrc", "k_force.cu")
 PROFILE_MD = os.path.join(ROOT, "profiles", "force_mixed_fcc64.md")
 
 
-def config_dict(s):
-    return {"workload": "LJ 12-6 FCC 64^3 unit cells, 1,048,576 atoms, rho 0.8442, T 1.44, "
-                        "jitter 0.05 sigma, rc 2.5, skin 0.3, dt 0.005, rebuild every 20 steps",
-            "atoms": int(s.n), "timesteps_per_step": STEPS_PER_CYCLE, "list": "full",
-            "l2": "inputs larger than L2: the neighbour list (~0.33 GB) is streamed every "
-                  "time step; positions (16 MB FP32) stay L2-resident by design",
-            "seed": 1003}
+def make_workload(name):
+    """(positions, velocities, boxes, counts or None, description) of a workload."""
+    if name == "ensemble256":
+        reps = inputs.replica_ensemble(256, seed=1004)
+        pos = np.concatenate([r.pos for r in reps])
+        vel = np.concatenate([r.vel for r in reps])
+        desc = ("256 independent periodic LJ replicas, atoms log-uniform in [500, 20000] "
+                f"({pos.shape[0]:,} in total), density U[0.70, 0.90], T U[0.8, 1.6], rc 2.5, "
+                "skin 0.3, dt 0.005, rebuild every 20 steps, one context")
+        return pos, vel, [r.box for r in reps], [r.n for r in reps], desc, 1004
+    s = inputs.workload(name)
+    cells = {"fcc64_1048576": 64, "fcc128_8388608": 128}[name]
+    desc = (f"LJ 12-6 FCC {cells}^3 unit cells, {s.n:,} atoms, rho 0.8442, T 1.44, "
+            "jitter 0.05 sigma, rc 2.5, skin 0.3, dt 0.005, rebuild every 20 steps")
+    return s.pos, s.vel, s.box, None, desc, inputs.WORKLOADS[name]["seed"]
+
+
+def config_dict(n_atoms, desc, seed):
+    return {"workload": desc, "atoms": int(n_atoms), "timesteps_per_step": STEPS_PER_CYCLE,
+            "l2": "inputs larger than L2: the neighbour list (~0.33 GB per million atoms) "
+                  "is streamed every time step; positions (16 B per atom, FP32) stay "
+                  "L2-resident by design",
+            "seed": seed}
 
 
 # --------------------------------------------------------------------------
@@ -171,10 +192,9 @@ def run_gpu(args):
     import torch
 
     from paper_2009_07400_gb300 import build, md
+    from paper_2009_07400_gb300 import dist as mdist
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = mdist.rank_info()
     dist = None
     if world > 1:
         import torch.distributed as td
@@ -183,14 +203,20 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     build.build()
     md.load()
-    s = inputs.workload(WORKLOAD)
+    name = WORKLOADS[args.workload]
+    pos, vel, box, counts, desc, seed = make_workload(name)
+    n = pos.shape[0]
     # The library enqueues on the stream it is given: use one torch stream for
     # the contexts and for the CUDA events that bracket the timed region.
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     sh = stream.cuda_stream
+
+    def make(**kw):
+        return md.MDContext(pos, vel, box, counts=counts, stream=sh, **kw)
+
     res = {}
-    with md.MDContext(s.pos, s.vel, s.box, stream=sh, precision=md.MD_MIXED) as ctx:
+    with make(precision=md.MD_MIXED) as ctx:
         tuned = ctx.autotune(STEPS_PER_CYCLE)
         res["tuned"] = {"threads_per_atom": tuned.threads_per_atom, "half_list": bool(tuned.half_list)}
         with ClockSampler(local) as clk:
@@ -198,27 +224,24 @@ def run_gpu(args):
         res["mixed_ms"] = ms
         res["launches"] = launches
         res["clocks"] = clk.summary()
-        prof = ctx.profile(2 * STEPS_PER_CYCLE)
-        res["prof"] = prof
+        res["prof"] = ctx.profile(2 * STEPS_PER_CYCLE)
         res["mixed_state"] = (ctx.positions(), ctx.forces())
     fp64_cycles = max(1, min(args.steps, 3))
-    with md.MDContext(s.pos, s.vel, s.box, stream=sh, precision=md.MD_FP64) as ctx:
+    with make(precision=md.MD_FP64) as ctx:
         t64 = ctx.autotune(STEPS_PER_CYCLE)
         res["tuned64"] = {"threads_per_atom": t64.threads_per_atom, "half_list": bool(t64.half_list)}
         ms64, _ = time_cycles(ctx, fp64_cycles, 1, dist, torch)
         res["fp64_ms"] = ms64 / fp64_cycles
-        prof64 = ctx.profile(STEPS_PER_CYCLE)
-        res["prof64"] = prof64
+        res["prof64"] = ctx.profile(STEPS_PER_CYCLE)
         res["fp64_state"] = (ctx.positions(), ctx.forces())
     # end to end: host state in pinned memory -> md_set_state -> one cycle ->
     # energies back to the host, every step
-    pin_pos = torch.empty((s.n, 3), dtype=torch.float64, pin_memory=True).numpy()
-    pin_vel = torch.empty((s.n, 3), dtype=torch.float64, pin_memory=True).numpy()
-    pin_pos[:] = s.pos
-    pin_vel[:] = s.vel
-    with md.MDContext(s.pos, s.vel, s.box, stream=sh, precision=md.MD_MIXED,
-                      threads_per_atom=res["tuned"]["threads_per_atom"],
-                      half_list=res["tuned"]["half_list"]) as ctx:
+    pin_pos = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    pin_vel = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    pin_pos[:] = pos
+    pin_vel[:] = vel
+    with make(precision=md.MD_MIXED, threads_per_atom=res["tuned"]["threads_per_atom"],
+              half_list=res["tuned"]["half_list"]) as ctx:
         for _ in range(2):
             ctx.set_state(pin_pos, pin_vel)
             ctx.run(STEPS_PER_CYCLE, energy_every=STEPS_PER_CYCLE)
@@ -233,34 +256,31 @@ def run_gpu(args):
         e2e_s = time.perf_counter() - t0
         if dist:
             dist.barrier()
-    res["e2e"] = (e2e_s, e_steps)
+    nrep = 1 if counts is None else len(counts)
 
-    # max over ranks
-    times = [res["mixed_ms"], res["fp64_ms"], res["e2e"][0]]
-    if dist:
-        t = torch.tensor(times, dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        times = t.tolist()
-    mixed_ms, fp64_ms, e2e_s = times
-    n_total = s.n * world
+    mixed_ms, fp64_ms, e2e_s = mdist.max_over_ranks(
+        [res["mixed_ms"], res["fp64_ms"], e2e_s], dist, device="cuda" if dist else None)
+    n_total = n * world
     value = n_total * STEPS_PER_CYCLE * args.steps / (mixed_ms / 1e3)
     fp64_value = n_total * STEPS_PER_CYCLE / (fp64_ms / 1e3)
-    e2e_value = n_total * STEPS_PER_CYCLE * res["e2e"][1] / e2e_s
+    e2e_value = n_total * STEPS_PER_CYCLE * e_steps / e2e_s
     if rank == 0:
         prof = res["prof"]
         force_ms_per_launch = prof.force_ms / max(1, prof.force_launches)
         half = res["tuned"]["half_list"]
         bpa = algorithmic_bytes_per_atom(prof.mean_neighbors, half)
-        achieved = bpa * s.n / (force_ms_per_launch / 1e3) / 1e9
+        achieved = bpa * n / (force_ms_per_launch / 1e3) / 1e9
         peak, peak_kind = measured_peaks()
-        traffic = ncu_traffic()
+        traffic = ncu_traffic() if name == WORKLOAD and not half else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": mixed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64 (mixed: FP32 pair arithmetic, Kahan sums, "
                                           "FP64 integration and reductions)",
-            "data": "synthetic", "config": config_dict(s),
+            "data": "synthetic",
+            "config": dict(config_dict(n, desc, seed), tuned=res["tuned"], replicas=nrep,
+                           list="half" if half else "full"),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": ("k_force_mixed_half" if half else
@@ -277,13 +297,13 @@ def run_gpu(args):
                               "other": res["prof64"].other_ms / res["prof64"].steps}},
             "speedup_mixed_over_fp64": value / fp64_value,
             "e2e": {"value": e2e_value, "unit": UNIT,
-                    "h2d_bytes_per_step": int(2 * 3 * 8 * s.n),
-                    "d2h_bytes_per_step": int(3 * 8)},
+                    "h2d_bytes_per_step": int(2 * 3 * 8 * n),
+                    "d2h_bytes_per_step": int(3 * 8 * nrep)},
             "gpu_launches": int(res["launches"]),
             "clocks": res["clocks"],
         }
         if not args.no_cpu_baseline:
-            line.update(cpu_baseline_leg(s, res))
+            line.update(cpu_baseline_leg(pos, vel, box, counts, res))
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -294,43 +314,68 @@ def run_gpu(args):
 # bounded sample of the same workload; it also states the force error of
 # both GPU paths against the oracle on sampled atoms.
 # --------------------------------------------------------------------------
-def oracle_rate(s, nsteps=4):
+def _systems(pos, vel, box, counts, max_atoms):
+    """(pos, vel, box, offset) of the workload's systems, at most max_atoms."""
+    if counts is None:
+        return [(pos, vel, np.asarray(box), 0)]
+    out, off, tot = [], 0, 0
+    for c, b in zip(counts, box):
+        if tot + c <= max_atoms or not out:
+            out.append((pos[off:off + c], vel[off:off + c], np.asarray(b), off))
+            tot += c
+        off += c
+    return out
+
+
+def oracle_rate(systems, nsteps=4):
     import oracle
     oracle.build()
-    t0 = time.perf_counter()
-    oracle.vv_run(s.pos, s.vel, s.box, 0)            # wrap + bin + build + one force pass
-    t_build_force = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    oracle.vv_run(s.pos, s.vel, s.box, nsteps)
-    t_run = time.perf_counter() - t0
-    t_step = (t_run - t_build_force) / nsteps
-    t_build = max(t_build_force - t_step, 0.0)
-    rate = s.n * STEPS_PER_CYCLE / (t_build + STEPS_PER_CYCLE * t_step)
-    return rate, t_step, t_build, oracle.num_threads()
+    atoms = t_build = t_step = 0.0
+    for p, v, b, _ in systems:
+        t0 = time.perf_counter()
+        oracle.vv_run(p, v, b, 0)            # wrap + bin + build + one force pass
+        tb = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        oracle.vv_run(p, v, b, nsteps)
+        ts = (time.perf_counter() - t0 - tb) / nsteps
+        t_build += max(tb - ts, 0.0)
+        t_step += ts
+        atoms += p.shape[0]
+    rate = atoms * STEPS_PER_CYCLE / (t_build + STEPS_PER_CYCLE * t_step)
+    return rate, t_step, t_build, oracle.num_threads(), int(atoms)
 
 
-def cpu_baseline_leg(s, res):
+def cpu_baseline_leg(pos, vel, box, counts, res):
     import oracle
-    rate, t_step, t_build, cores = oracle_rate(s)
+    systems = _systems(pos, vel, box, counts, 2_000_000 if counts is None else 60_000)
+    rate, t_step, t_build, cores, atoms = oracle_rate(systems)
+    what = ("the full workload" if counts is None else
+            f"{len(systems)} of the replicas ({atoms:,} atoms)")
     out = {"cpu_baseline": {
         "value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-        "sample": f"FP64 C oracle (OpenMP, {cores} threads) on the full 1,048,576-atom "
-                  f"workload: one list build ({t_build:.2f} s) and 4 velocity-Verlet steps "
-                  f"({t_step:.3f} s each), rate = atoms x 20 / (build + 20 steps)"}}
+        "sample": f"FP64 C oracle (OpenMP, {cores} threads) on {what}: one list build "
+                  f"({t_build:.2f} s) and 4 velocity-Verlet steps ({t_step:.3f} s each), "
+                  f"rate = atoms x 20 / (build + 20 steps)"}}
     rng = np.random.default_rng(0)
     errs = {}
     for key, name in (("mixed_state", "mixed_rms_rel"), ("fp64_state", "fp64_max_rel")):
         x, F = res[key]
-        ids = rng.choice(s.n, 2048, replace=False)
-        Fr = oracle.forces_sample(x, s.box, ids)
-        Fg = F[ids]
+        Fg, Fr = [], []
+        per = 2048 // len(systems[:4])
+        for p_r, _, b, off in systems[:4]:
+            nr = p_r.shape[0]
+            ids = rng.choice(nr, min(nr, per), replace=False)
+            Fr.append(oracle.forces_sample(x[off:off + nr], b, ids))
+            Fg.append(F[off + ids])
+        Fr = np.concatenate(Fr)
+        Fg = np.concatenate(Fg)
         if name == "mixed_rms_rel":
             errs[name] = float(np.sqrt(np.sum((Fg - Fr) ** 2) / np.sum(Fr ** 2)))
         else:
             frms = np.sqrt(np.mean(np.sum(Fr ** 2, axis=1)))
             sc = np.maximum(np.linalg.norm(Fr, axis=1), frms)
             errs[name] = float(np.max(np.linalg.norm(Fg - Fr, axis=1) / sc))
-    errs["sample"] = "2048 random atoms after the timed runs, plain-definition oracle forces"
+    errs["sample"] = "about 2048 random atoms after the timed runs, plain-definition oracle forces"
     out["force_error"] = errs
     return out
 
@@ -344,17 +389,22 @@ def run_reference(args):
         return
     import oracle
     oracle.build()
-    s = inputs.workload(WORKLOAD)
+    name = WORKLOADS[args.workload]
+    pos, vel, box, counts, desc, seed = make_workload(name)
+    if counts is not None:     # a bounded sample of the replicas
+        p, v, b, _ = _systems(pos, vel, box, counts, 60_000)[0]
+    else:
+        p, v, b = pos, vel, np.asarray(box)
     t0 = time.perf_counter()
-    x, v, _ = oracle.vv_run(s.pos, s.vel, s.box, 0)
+    x, vv, _ = oracle.vv_run(p, v, b, 0)
     t_build = time.perf_counter() - t0
-    x, v, _ = oracle.vv_run(x, v, s.box, max(1, args.warmup))
+    x, vv, _ = oracle.vv_run(x, vv, b, max(1, args.warmup))
     t0 = time.perf_counter()
-    oracle.vv_run(x, v, s.box, args.steps)
+    oracle.vv_run(x, vv, b, args.steps)
     t_steps = time.perf_counter() - t0 - t_build
     t_step = max(t_steps / args.steps, 1e-9)
     per_step = t_step + t_build / STEPS_PER_CYCLE
-    value = s.n / per_step
+    value = p.shape[0] / per_step
     cores = oracle.num_threads()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": int(os.environ.get("WORLD_SIZE", args.gpus)), "steps": args.steps,
@@ -394,6 +444,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="fcc64", choices=sorted(WORKLOADS),
+                    help="fcc64: the 1,048,576-atom benchmark (default); fcc128: the "
+                         "8,388,608-atom sizing run; ensemble: 256 replicas")
     ap.add_argument("--ncu-case", choices=["mixed", "fp64"],
                     help="only build the workload and run 2 rebuild cycles (a short, "
                          "fixed launch sequence for an ncu capture); prints nothing")

@@ -112,6 +112,8 @@ typedef struct md_ctx md_ctx;
  *   stream: a cudaStream_t to enqueue on, or NULL for a stream owned by the
  *   context.  The initial state is binned, a list is built and forces are
  *   computed before md_create returns.
+ * At most 67,108,863 atoms per context (26-bit list indices) and 1023 cells
+ * per box edge.
  * Errors: MD_ERR_INVAL, MD_ERR_BOX_TOO_SMALL, MD_ERR_NONFINITE, MD_ERR_NOMEM,
  *   MD_ERR_CUDA.  On error *out is NULL. */
 int md_create(const md_box *box, const md_params *params, int64_t n, const double *pos,

@@ -67,19 +67,18 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs(Dev d, LJ lj, AdjArgs a)
     for (int k = 0; k < cnt; k++) {
         const int4 e4 = nb4[(int64_t)(k >> 2) * d.n + i];
         const int32_t e = (k & 3) == 0 ? e4.x : (k & 3) == 1 ? e4.y : (k & 3) == 2 ? e4.z : e4.w;
-        const uint32_t slot = (uint32_t)e >> kJBits;
+        const uint32_t code = (uint32_t)e >> kJBits;
+        const int ox = (int)(code & 3u) - 1, oy = (int)((code >> 2) & 3u) - 1, oz = (int)(code >> 4) - 1;
         const int32_t j = (int32_t)((uint32_t)e & kJMask);
         double dx, dy, dz;
         if (MIXED) {
             // cell-relative FP32 geometry, as in the mixed force kernel
             const float4 pj = d.p32[j];
-            const int ox = (int)(slot / 9) - 1, oy = (int)((slot / 3) % 3) - 1, oz = (int)(slot % 3) - 1;
             dx = (double)fmaf((float)ox, R.nsf[0], pi.x - pj.x);
             dy = (double)fmaf((float)oy, R.nsf[1], pi.y - pj.y);
             dz = (double)fmaf((float)oz, R.nsf[2], pi.z - pj.z);
         } else {
             const dvec4 xj = d.x[j];
-            const int ox = (int)(slot / 9) - 1, oy = (int)((slot / 3) % 3) - 1, oz = (int)(slot % 3) - 1;
             dx = xi.x - xj.x;
             dy = xi.y - xj.y;
             dz = xi.z - xj.z;

@@ -17,10 +17,10 @@
 //
 // Mixed path: positions are FP32 offsets from the centre of the atom's cell
 // at the last binning; a neighbour's displacement is
-//     d = (p_i - p_j) + o * (-s)
-// with o its stencil offset (decoded from the entry's 5-bit slot through a
-// 27-entry shared table), so |d|'s FP32 rounding error is that of numbers of
-// size ~s rather than of the box length.  Per-atom sums are Kahan
+//     d = (p_i - o s) - p_j
+// with o its stencil offset (2 bits per dimension in the list entry), so
+// |d|'s FP32 rounding error is that of numbers of size ~s rather than of the
+// box length.  Per-atom sums are Kahan
 // compensated: the four pairs of a list chunk are summed in a plain FP32
 // partial and each partial enters a Kahan sum (the compensation then covers
 // the long per-atom sum, where the rounding error accumulates).  The
@@ -76,12 +76,6 @@ __device__ __forceinline__ float rcp_approx(float a)
     return r;
 }
 
-__device__ __forceinline__ float4 stencil_entry(int s)
-{
-    // slot 27 (padding) sits 4096 cells away: far outside rc, masked.
-    return s < 27 ? make_float4((float)(s / 9 - 1), (float)((s / 3) % 3 - 1), (float)(s % 3 - 1), 0.f)
-                  : make_float4(4096.f, 0.f, 0.f, 0.f);
-}
 
 // FP64 epilogue shared by both precisions.  fx..fz: force on atom i.
 template <int EPI, bool ENERGY>
@@ -123,17 +117,26 @@ __device__ __forceinline__ void epilogue(const Dev &d, const LJ &lj, const Rep &
 // ---------------------------------------------------------------------------
 // Mixed precision, full list.
 // ---------------------------------------------------------------------------
+// How the stencil offset o (2 bits per dimension in the entry) enters
+// d = p_i - o s - p_j.  Mode 1: o read from three 3-entry shared tables
+// (conflict-free LDS.32, one L1 wavefront each per warp).  Mode 3: p_i - s,
+// p_i, p_i + s held in registers and chosen with two bit tests and two
+// selects per dimension (no L1 traffic, more ALU).
 #ifndef MD_OFFSET_MODE
-#define MD_OFFSET_MODE 1
+#define MD_OFFSET_MODE 3
 #endif
 #ifndef MD_FORCE_MINBLOCKS
 #define MD_FORCE_MINBLOCKS 1
 #endif
+// List chunks (4 pairs each) per loop round of the mixed full-list kernel.
+#ifndef MD_FORCE_UNROLL
+#define MD_FORCE_UNROLL 1
+#endif
 
 // One tile of atoms of the mixed full-list kernel (tile = gt / blockDim).
 template <int TPA, bool BATCHED, int EPI, bool ENERGY>
-__device__ __forceinline__ void mixed_full_tile(const Dev &d, const LJ &lj, const float4 (&otab)[32],
-                                                const float (&ot)[3][32], int64_t gt)
+__device__ __forceinline__ void mixed_full_tile(const Dev &d, const LJ &lj, const float (&ot)[3],
+                                                int64_t gt)
 {
     const int64_t i0 = gt / TPA;
     const int sub = (int)(gt % TPA);
@@ -151,7 +154,7 @@ __device__ __forceinline__ void mixed_full_tile(const Dev &d, const LJ &lj, cons
     float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
     float pe = 0.f, w = 0.f, cpe = 0.f, cw = 0.f;
     const float4 *p32 = d.p32;
-    // p_i shifted by o*(-s) for o = -1, 0, +1 (mode 2)
+    // p_i - o s for o = -1, 0, +1 (mode 3); ns = -s
     const float qx0 = pi.x - nsx, qx2 = pi.x + nsx;
     const float qy0 = pi.y - nsy, qy2 = pi.y + nsy;
     const float qz0 = pi.z - nsz, qz2 = pi.z + nsz;
@@ -159,26 +162,16 @@ __device__ __forceinline__ void mixed_full_tile(const Dev &d, const LJ &lj, cons
     // one pair: adds f*d to (px, py, pz) and, with ENERGY, V and f r^2
     auto pair = [&](uint32_t e, float &px, float &py, float &pz, float &pv, float &pw) {
         const float4 pj = __ldg(p32 + (e & kJMask));
-        const uint32_t slot = e >> kJBits;
+        const uint32_t c = e >> kJBits;
         float dx, dy, dz;
-        if (MD_OFFSET_MODE == 0) {
-            const float4 o = otab[slot];
-            dx = fmaf(o.x, nsx, pi.x - pj.x);
-            dy = fmaf(o.y, nsy, pi.y - pj.y);
-            dz = fmaf(o.z, nsz, pi.z - pj.z);
-        } else if (MD_OFFSET_MODE == 1) {
-            dx = fmaf(ot[0][slot], nsx, pi.x - pj.x);
-            dy = fmaf(ot[1][slot], nsy, pi.y - pj.y);
-            dz = fmaf(ot[2][slot], nsz, pi.z - pj.z);
+        if (MD_OFFSET_MODE == 1) {
+            dx = fmaf(ot[c & 3u], nsx, pi.x - pj.x);
+            dy = fmaf(ot[(c >> 2) & 3u], nsy, pi.y - pj.y);
+            dz = fmaf(ot[c >> 4], nsz, pi.z - pj.z);
         } else {
-            // slot = 9 (ox+1) + 3 (oy+1) + (oz+1); padding (27) has ox = +2
-            const uint32_t sx3 = slot / 9, r9 = slot - 9 * sx3, sy3 = r9 / 3, sz3 = r9 - 3 * sy3;
-            const float qx = sx3 == 0 ? qx0 : (sx3 == 1 ? pi.x : (sx3 == 2 ? qx2 : 3.0e4f));
-            const float qy = sy3 == 0 ? qy0 : (sy3 == 1 ? pi.y : qy2);
-            const float qz = sz3 == 0 ? qz0 : (sz3 == 1 ? pi.z : qz2);
-            dx = qx - pj.x;
-            dy = qy - pj.y;
-            dz = qz - pj.z;
+            dx = ((c & 2u) ? qx2 : ((c & 1u) ? pi.x : qx0)) - pj.x;
+            dy = ((c & 8u) ? qy2 : ((c & 4u) ? pi.y : qy0)) - pj.y;
+            dz = ((c & 32u) ? qz2 : ((c & 16u) ? pi.z : qz0)) - pj.z;
         }
         const float rsq = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
         const float sr2 = rcp_approx(rsq);
@@ -195,11 +188,7 @@ __device__ __forceinline__ void mixed_full_tile(const Dev &d, const LJ &lj, cons
         }
     };
 
-    int q = sub;
-    int4 nxt = q < nq ? ld_stream(nb4 + (int64_t)q * n + i) : make_int4(0, 0, 0, 0);
-    for (; q < nq; q += TPA) {
-        const int4 e = nxt;
-        if (q + TPA < nq) nxt = ld_stream(nb4 + (int64_t)(q + TPA) * n + i);
+    auto chunk = [&](const int4 &e) {
         float px = 0.f, py = 0.f, pz = 0.f, pv = 0.f, pw = 0.f;
         pair((uint32_t)e.x, px, py, pz, pv, pw);
         pair((uint32_t)e.y, px, py, pz, pv, pw);
@@ -211,6 +200,24 @@ __device__ __forceinline__ void mixed_full_tile(const Dev &d, const LJ &lj, cons
         if (ENERGY) {
             kahan_add(pe, cpe, pv);
             kahan_add(w, cw, pw);
+        }
+    };
+    int q = sub;
+    if (MD_FORCE_UNROLL == 2 && TPA == 1) {
+        // two chunks (8 pairs, 8 independent gathers) per round
+        for (; q + 1 < nq; q += 2) {
+            const int4 e0 = ld_stream(nb4 + (int64_t)q * n + i);
+            const int4 e1 = ld_stream(nb4 + (int64_t)(q + 1) * n + i);
+            chunk(e0);
+            chunk(e1);
+        }
+        if (q < nq) chunk(ld_stream(nb4 + (int64_t)q * n + i));
+    } else {
+        int4 nxt = q < nq ? ld_stream(nb4 + (int64_t)q * n + i) : make_int4(0, 0, 0, 0);
+        for (; q < nq; q += TPA) {
+            const int4 e = nxt;
+            if (q + TPA < nq) nxt = ld_stream(nb4 + (int64_t)(q + TPA) * n + i);
+            chunk(e);
         }
     }
     float fx = sx - cx, fy = sy - cy, fz = sz - cz;
@@ -239,31 +246,20 @@ __device__ __forceinline__ void mixed_full_tile(const Dev &d, const LJ &lj, cons
                           __float_as_uint(pi.w), true);
 }
 
-// Stencil offsets o of the 27 slots (slot 27: padding, far away), scaled by
-// -s in the pair loop.  Mode 0: one float4 table (LDS.128); mode 1: three
-// float tables, each read with a conflict-free LDS.32 (27 words in 27
-// banks); mode 2: no table, a per-dimension select between p_i - s, p_i and
-// p_i + s.  Mode 1 measured fastest on GB300 (L1 data pipe is the limit).
-__device__ __forceinline__ void fill_offsets(float4 (&otab)[32], float (&ot)[3][32])
+// o + 1 -> o for the per-dimension offset tables of mode 1.
+__device__ __forceinline__ void fill_offsets(float (&ot)[3])
 {
-    if (threadIdx.x < 32) {
-        const float4 o = stencil_entry(threadIdx.x);
-        otab[threadIdx.x] = o;
-        ot[0][threadIdx.x] = o.x;
-        ot[1][threadIdx.x] = o.y;
-        ot[2][threadIdx.x] = o.z;
-    }
+    if (threadIdx.x < 3) ot[threadIdx.x] = (float)((int)threadIdx.x - 1);
     __syncthreads();
 }
 
 template <int TPA, bool BATCHED, int EPI, bool ENERGY>
 __global__ void __launch_bounds__(256, MD_FORCE_MINBLOCKS) k_force_mixed_full(Dev d, LJ lj)
 {
-    __shared__ float4 otab[32];
-    __shared__ float ot[3][32];
-    fill_offsets(otab, ot);
+    __shared__ float ot[3];
+    fill_offsets(ot);
     if (stopped(d.status)) return;
-    mixed_full_tile<TPA, BATCHED, EPI, ENERGY>(d, lj, otab, ot,
+    mixed_full_tile<TPA, BATCHED, EPI, ENERGY>(d, lj, ot,
                                                (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
@@ -274,14 +270,13 @@ template <bool BATCHED, int EPI, bool ENERGY>
 __global__ void __launch_bounds__(256, MD_FORCE_MINBLOCKS) k_force_mixed_full_persist(Dev d, LJ lj,
                                                                                       int64_t ntiles)
 {
-    __shared__ float4 otab[32];
-    __shared__ float ot[3][32];
-    fill_offsets(otab, ot);
+    __shared__ float ot[3];
+    fill_offsets(ot);
     if (stopped(d.status)) return;
     const int64_t t0 = (int64_t)blockIdx.x * ntiles / gridDim.x;
     const int64_t t1 = (int64_t)(blockIdx.x + 1) * ntiles / gridDim.x;
     for (int64_t t = t0; t < t1; t++)
-        mixed_full_tile<1, BATCHED, EPI, ENERGY>(d, lj, otab, ot, t * blockDim.x + threadIdx.x);
+        mixed_full_tile<1, BATCHED, EPI, ENERGY>(d, lj, ot, t * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -291,9 +286,8 @@ __global__ void __launch_bounds__(256, MD_FORCE_MINBLOCKS) k_force_mixed_full_pe
 template <bool BATCHED, bool ENERGY>
 __global__ void __launch_bounds__(256) k_force_mixed_half(Dev d, LJ lj)
 {
-    __shared__ float4 otab[32];
-    if (threadIdx.x < 32) otab[threadIdx.x] = stencil_entry(threadIdx.x);
-    __syncthreads();
+    __shared__ float ot[3];
+    fill_offsets(ot);
     if (stopped(d.status)) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n) return;
@@ -308,14 +302,13 @@ __global__ void __launch_bounds__(256) k_force_mixed_half(Dev d, LJ lj)
     float pe = 0.f, w = 0.f, cpe = 0.f, cw = 0.f;
 
     auto pair = [&](int32_t e) {
-        const uint32_t slot = (uint32_t)e >> kJBits;
-        if (slot >= 27) return;
+        const uint32_t c = (uint32_t)e >> kJBits;
         const int32_t j = (int32_t)((uint32_t)e & kJMask);
-        const float4 o = otab[slot];
+        if (j == n) return;                                 // padding
         const float4 pj = __ldg(&d.p32[j]);
-        const float dx = fmaf(o.x, nsx, pi.x - pj.x);
-        const float dy = fmaf(o.y, nsy, pi.y - pj.y);
-        const float dz = fmaf(o.z, nsz, pi.z - pj.z);
+        const float dx = fmaf(ot[c & 3u], nsx, pi.x - pj.x);
+        const float dy = fmaf(ot[(c >> 2) & 3u], nsy, pi.y - pj.y);
+        const float dz = fmaf(ot[c >> 4], nsz, pi.z - pj.z);
         const float rsq = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
         if (!(rsq < lj.rc2f)) return;
         const float sr2 = rcp_approx(rsq);
@@ -360,18 +353,18 @@ __device__ __forceinline__ void f64_pair(const Dev &d, const LJ &lj, const dvec4
                                          const Shift &sh, int32_t e, double &fx, double &fy,
                                          double &fz, double &pe, double &w, bool energy)
 {
-    const uint32_t slot = (uint32_t)e >> kJBits;
+    const uint32_t c = (uint32_t)e >> kJBits;
     const int32_t j = (int32_t)((uint32_t)e & kJMask);
     const dvec4 xj = ldg_dvec4(&d.x[j]);
     double dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
     if (EDGE) {
-        const int ox = (int)(slot / 9) - 1, oy = (int)((slot / 3) % 3) - 1, oz = (int)(slot % 3) - 1;
+        const int ox = (int)(c & 3u) - 1, oy = (int)((c >> 2) & 3u) - 1, oz = (int)(c >> 4) - 1;
         if (ox) dx = dx + (ox < 0 ? sh.lo[0] : sh.hi[0]);
         if (oy) dy = dy + (oy < 0 ? sh.lo[1] : sh.hi[1]);
         if (oz) dz = dz + (oz < 0 ? sh.lo[2] : sh.hi[2]);
     }
     const double rsq = fma(dz, dz, fma(dy, dy, dx * dx));
-    const bool in = (rsq < lj.rc2) && (slot < 27);
+    const bool in = rsq < lj.rc2;        // padding points at the far-away sentinel
     const double sr2 = rcp_nr(rsq);
     const double t = sr2 * sr2 * sr2 * lj.sigma6;
     double f = sr2 * t * fma(lj.c48e, t, -lj.c24e);

@@ -205,7 +205,7 @@ int enq_build(md_ctx *c, int *nl)
 {
     CK(cudaMemsetAsync(&c->status->max_count, 0, sizeof(int32_t), c->st));
     Dev d = view(c);
-    if (launch_build(d, c->lj, is_half(c), c->st, nl) != 0)
+    if (launch_build(d, c->lj, is_half(c), c->ncells, c->st, nl) != 0)
         return fail(c, MD_ERR_CUDA, "list build launch failed");
     c->list_valid = true;
     c->builds_enqueued++;
@@ -1207,7 +1207,7 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
         c->reps_h[r] = R;
     }
     chunk_first.push_back((int64_t)chunk_rep.size() / 2);
-    if (n > (int64_t)kJMask) return fail(c, MD_ERR_INVAL, "too many atoms for 27-bit indices");
+    if (n > (int64_t)kJMask) return fail(c, MD_ERR_INVAL, "more than 67,108,863 atoms (26-bit list indices)");
     if (cells >= (int64_t)1 << 31) return fail(c, MD_ERR_INVAL, "too many cells");
     for (int64_t t = 0; t < 3 * n; t++)
         if (!std::isfinite(pos[t]) || !std::isfinite(vel[t]))
@@ -1231,11 +1231,18 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
     const size_t N = (size_t)n;
     if ((rc = dalloc(c, &c->reps_d, nrep))) return rc;
     if ((rc = dalloc(c, &c->rep_of_d, N))) return rc;
+    // x, v and p32 carry one extra slot n: the sentinel atom that list
+    // padding points at, parked far outside every cutoff
+    const dvec4 far64 = mk_dvec4(1.0e6, 1.0e6, 1.0e6, 0.0), zero64 = mk_dvec4(0.0, 0.0, 0.0, 0.0);
+    const float4 far32 = make_float4(1.0e4f, 1.0e4f, 1.0e4f, 0.0f);
     for (int b = 0; b < 2; b++) {
-        if ((rc = dalloc(c, &c->x[b], N))) return rc;
-        if ((rc = dalloc(c, &c->v[b], N))) return rc;
+        if ((rc = dalloc(c, &c->x[b], N + 1))) return rc;
+        if ((rc = dalloc(c, &c->v[b], N + 1))) return rc;
         if ((rc = dalloc(c, &c->id[b], N))) return rc;
-        if ((rc = dalloc(c, &c->p32[b], N))) return rc;
+        if ((rc = dalloc(c, &c->p32[b], N + 1))) return rc;
+        CK(cudaMemcpy(c->x[b] + N, &far64, sizeof(dvec4), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->v[b] + N, &zero64, sizeof(dvec4), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->p32[b] + N, &far32, sizeof(float4), cudaMemcpyHostToDevice));
     }
     if ((rc = dalloc(c, &c->f32, N))) return rc;
     if ((rc = dalloc(c, &c->f64, N))) return rc;

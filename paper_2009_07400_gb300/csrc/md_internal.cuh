@@ -23,13 +23,18 @@ __device__ __forceinline__ dvec4 ldg_dvec4(const dvec4 *p)
 }
 #endif
 
-// A list entry packs the neighbour's slot index (low 27 bits) and its
-// stencil slot (high 5 bits): slot = (ox+1)*9 + (oy+1)*3 + (oz+1) for the
-// cell offset o in {-1,0,1}^3 of the neighbour's periodic image relative to
-// the owner's cell.  Slot 27 marks padding (a self entry far outside rc).
-constexpr int kJBits = 27;
+// A list entry packs the neighbour's slot index (low 26 bits) and the cell
+// offset o in {-1,0,1}^3 of the neighbour's periodic image relative to the
+// owner's cell, as o+1 in 2 bits per dimension: bits 26-27 x, 28-29 y, 30-31
+// z.  Rows are padded to a multiple of 4 with entries that point at the
+// sentinel slot n, an atom parked far outside every cutoff.
+constexpr int kJBits = 26;
 constexpr uint32_t kJMask = (1u << kJBits) - 1u;
-constexpr int kPadSlot = 27;
+constexpr uint32_t kZeroOffset = 0x15u;   // o = (0, 0, 0)
+__host__ __device__ __forceinline__ uint32_t offset_code(int ox, int oy, int oz)
+{
+    return (uint32_t)(ox + 1) | ((uint32_t)(oy + 1) << 2) | ((uint32_t)(oz + 1) << 4);
+}
 constexpr int kMaxNc = 1023;        // cell coordinates are packed in 10 bits each
 
 // Bits of the device error word.  Every kernel returns immediately while it
@@ -99,7 +104,8 @@ struct Dev {
 // ---------------------------------------------------------------------------
 int launch_bin(const Dev &d, int64_t ncells_total, int32_t *scan_tmp, int64_t scan_tmp_len,
                cudaStream_t st, int *nlaunch);
-int launch_build(const Dev &d, const LJ &lj, bool half, cudaStream_t st, int *nlaunch);
+int launch_build(const Dev &d, const LJ &lj, bool half, int64_t ncells, cudaStream_t st,
+                 int *nlaunch);
 
 enum Epi : int { EPI_F = 0, EPI_FK = 1, EPI_FKKD = 2 };
 int launch_force(const Dev &d, const LJ &lj, int precision, bool half, int tpa, int epi,
