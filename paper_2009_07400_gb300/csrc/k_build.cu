@@ -53,6 +53,10 @@ __device__ __forceinline__ double image_diff(double xi, double xj, int k, double
     return t;
 }
 
+#ifndef MD_BUILD_MASK
+#define MD_BUILD_MASK 1
+#endif
+
 // Half-list ownership of candidate j (FP32 d = p_i + o(-s) - p_j first; the
 // exact FP64 del when the FP32 z-component is within 1e-4 of zero).
 __device__ __forceinline__ bool owns(const Dev &d, const LJ &lj, int64_t i, int32_t j, int32_t idi,
@@ -109,14 +113,11 @@ __device__ __forceinline__ int32_t build_row(const Dev &d, const LJ &lj, int64_t
                 if (HALF && oz < 0 && kz == 0) continue;        // entirely below
                 const bool test_sign = HALF && (oz == 0 || kz != 0);
                 const uint32_t tag = offset_code(ox, oy, oz) << kJBits;
-                for (int32_t j = j0; j < j1; j++) {
-                    const float4 pj = __ldg(p32 + j);
-                    const float dx = qx - pj.x, dy = qy - pj.y, dz = qz - pj.z;
-                    const float r2f = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                    if (!(r2f < hi)) continue;                 // clearly outside rs
-                    if (j == i) continue;
+                // full test of candidate j (self, ownership, FP64 in the band)
+                auto accept = [&](int32_t j, float dx, float dy, float dz, float r2f) {
+                    if (j == i) return;
                     if (test_sign && !owns(d, lj, i, j, idi, dx, dy, dz, kx, ky, kz, R, xi, have_xi))
-                        continue;
+                        return;
                     if (!(r2f < lo)) {                         // inside the band: decide in FP64
                         if (!have_xi) { xi = d.x[i]; have_xi = true; }
                         const dvec4 xj = d.x[j];
@@ -125,11 +126,42 @@ __device__ __forceinline__ int32_t build_row(const Dev &d, const LJ &lj, int64_t
                         const double tz = image_diff(xi.z, xj.z, kz, R.L[2]);
                         const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(tx, tx), __dmul_rn(ty, ty)),
                                                     __dmul_rn(tz, tz));
-                        if (!(r2 < lj.rs2)) continue;
+                        if (!(r2 < lj.rs2)) return;
                     }
                     if (cnt < cap) row[(int64_t)(cnt >> 2) * 4 * n + (cnt & 3)] = (int32_t)((uint32_t)j | tag);
                     cnt++;
+                };
+#if MD_BUILD_MASK
+                // hot loop: a bit per candidate inside the FP32 band's upper
+                // edge (about 1 in 6), independent loads; then the hits
+                for (int32_t jb = j0; jb < j1; jb += 32) {
+                    const int m = min(32, (int)(j1 - jb));
+                    uint32_t hits = 0;
+#pragma unroll 4
+                    for (int t = 0; t < m; t++) {
+                        const float4 pj = __ldg(p32 + jb + t);
+                        const float dx = qx - pj.x, dy = qy - pj.y, dz = qz - pj.z;
+                        const float r2f = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                        hits |= (uint32_t)(r2f < hi) << t;
+                    }
+                    while (hits) {
+                        const int t = __ffs(hits) - 1;
+                        hits &= hits - 1;
+                        const int32_t j = jb + t;
+                        const float4 pj = __ldg(p32 + j);
+                        const float dx = qx - pj.x, dy = qy - pj.y, dz = qz - pj.z;
+                        accept(j, dx, dy, dz, fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+                    }
                 }
+#else
+                for (int32_t j = j0; j < j1; j++) {
+                    const float4 pj = __ldg(p32 + j);
+                    const float dx = qx - pj.x, dy = qy - pj.y, dz = qz - pj.z;
+                    const float r2f = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                    if (!(r2f < hi)) continue;                 // clearly outside rs
+                    accept(j, dx, dy, dz, r2f);
+                }
+#endif
             }
         }
     }

@@ -348,3 +348,29 @@ def test_autotune_keeps_state(md, orc):
                 assert fp64_force_ok(F, Fr) <= 1e-10
             else:
                 assert rms_rel(F, Fr) <= 1e-5
+
+
+def test_ensemble_256_sampled(md, orc):
+    """The 256-replica ensemble (about 1.4 M atoms in one context, the
+    batched benchmark workload) after one graph-replayed rebuild cycle:
+    sampled replicas' lists bit-exact and mixed forces within 1e-5 RMS."""
+    reps = inputs.replica_ensemble(256, seed=1004)
+    pos = np.concatenate([r.pos for r in reps])
+    vel = np.concatenate([r.vel for r in reps])
+    counts = [r.n for r in reps]
+    with md.MDContext(pos, vel, [r.box for r in reps], counts=counts,
+                      precision=md.MD_MIXED) as ctx:
+        ctx.run(20)
+        X, F = ctx.positions(), ctx.forces()
+        c_g, r_g = ctx.neighbors_raw()
+    offs = np.concatenate([[0], np.cumsum(counts)])
+    for k in np.random.default_rng(5).choice(256, 6, replace=False):
+        r = reps[k]
+        a, b = offs[k], offs[k + 1]
+        x = X[a:b]
+        c_o, r_o = orc.neighbors_cells_raw(orc.wrap(x, r.box), r.box, RC + SKIN)
+        assert np.array_equal(c_g[a:b], c_o)
+        assert np.array_equal(sorted_rows(c_g[a:b], r_g[a:b]), sorted_rows(c_o, r_o))
+        Fr = orc.forces_list(orc.wrap(x, r.box), r.box,
+                             orc.neighbors_cells(orc.wrap(x, r.box), r.box, RC + SKIN))
+        assert rms_rel(F[a:b], Fr) <= 1e-5
