@@ -47,7 +47,14 @@ __global__ void __launch_bounds__(256) k_bin_assign(Dev d)
         else if (u >= R.L[q]) u = u - R.L[q];
         if (u < 0.0 || u > R.L[q]) { bad |= FLAG_BADPOS; u = 0.0; }
         c[q] = u;
-        int32_t kk = (int32_t)(u / R.s[q]);
+        // (int)(u / s) with the IEEE FP64 quotient.  GB300's FP64 divide is
+        // slow, so the quotient is estimated in FP32 (error < 2e-4 for
+        // u/s <= 1023) and the exact division runs only when the estimate
+        // lies within 1e-3 of an integer, where the two could disagree.
+        const float y = (float)u * (1.0f / (float)R.s[q]);
+        int32_t kk = (int32_t)y;
+        const float fr = y - (float)kk;
+        if (fr < 1e-3f || fr > 1.0f - 1e-3f) kk = (int32_t)(u / R.s[q]);
         k[q] = kk >= R.nc[q] ? R.nc[q] - 1 : kk;
     }
     if (bad) atomicOr(&d.status->flags, bad);

@@ -77,6 +77,13 @@ __device__ __forceinline__ float rcp_approx(float a)
 }
 
 
+// Cell centres in the velocity-Verlet epilogue: 1 = read from the
+// per-replica FP64 table, 0 = computed ((c + 0.5) s, integer-to-FP64
+// conversions and FP64 FMAs on GB300's slow FP64 pipe).  Same values.
+#ifndef MD_CENTER_TABLE
+#define MD_CENTER_TABLE 1
+#endif
+
 // FP64 epilogue shared by both precisions.  fx..fz: force on atom i.
 template <int EPI, bool ENERGY>
 __device__ __forceinline__ void epilogue(const Dev &d, const LJ &lj, const Rep &R, int64_t i,
@@ -105,9 +112,17 @@ __device__ __forceinline__ void epilogue(const Dev &d, const LJ &lj, const Rep &
         // positions to the other buffer; the mixed path gathers p32 only
         if (mixed) d.x[i] = x;
         else d.x_nxt[i] = x;
-        const double cx = ((double)(pack & 1023u) + 0.5) * R.s[0];
-        const double cy = ((double)((pack >> 10) & 1023u) + 0.5) * R.s[1];
-        const double cz = ((double)((pack >> 20) & 1023u) + 0.5) * R.s[2];
+        double cx, cy, cz;
+        if (MD_CENTER_TABLE) {   // centre coordinates from the per-replica table
+            const double *ct = d.ctr + R.ctr_off;
+            cx = __ldg(ct + (pack & 1023u));
+            cy = __ldg(ct + R.nc[0] + ((pack >> 10) & 1023u));
+            cz = __ldg(ct + R.nc[0] + R.nc[1] + ((pack >> 20) & 1023u));
+        } else {
+            cx = ((double)(pack & 1023u) + 0.5) * R.s[0];
+            cy = ((double)((pack >> 10) & 1023u) + 0.5) * R.s[1];
+            cz = ((double)((pack >> 20) & 1023u) + 0.5) * R.s[2];
+        }
         d.p32_nxt[i] = make_float4((float)(x.x - cx), (float)(x.y - cy), (float)(x.z - cz),
                                    __uint_as_float(pack));
     }
@@ -131,6 +146,10 @@ __device__ __forceinline__ void epilogue(const Dev &d, const LJ &lj, const Rep &
 // List chunks (4 pairs each) per loop round of the mixed full-list kernel.
 #ifndef MD_FORCE_UNROLL
 #define MD_FORCE_UNROLL 1
+#endif
+// How many rounds ahead the list chunks are loaded.
+#ifndef MD_LIST_PREFETCH
+#define MD_LIST_PREFETCH 1
 #endif
 
 // One tile of atoms of the mixed full-list kernel (tile = gt / blockDim).
@@ -212,6 +231,16 @@ __device__ __forceinline__ void mixed_full_tile(const Dev &d, const LJ &lj, cons
             chunk(e1);
         }
         if (q < nq) chunk(ld_stream(nb4 + (int64_t)q * n + i));
+    } else if (MD_LIST_PREFETCH == 2) {
+        // list chunks loaded two rounds ahead (covers more of the DRAM latency)
+        int4 n1 = q < nq ? ld_stream(nb4 + (int64_t)q * n + i) : make_int4(0, 0, 0, 0);
+        int4 n2 = q + TPA < nq ? ld_stream(nb4 + (int64_t)(q + TPA) * n + i) : make_int4(0, 0, 0, 0);
+        for (; q < nq; q += TPA) {
+            const int4 e = n1;
+            n1 = n2;
+            if (q + 2 * TPA < nq) n2 = ld_stream(nb4 + (int64_t)(q + 2 * TPA) * n + i);
+            chunk(e);
+        }
     } else {
         int4 nxt = q < nq ? ld_stream(nb4 + (int64_t)q * n + i) : make_int4(0, 0, 0, 0);
         for (; q < nq; q += TPA) {

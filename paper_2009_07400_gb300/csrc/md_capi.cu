@@ -80,6 +80,7 @@ struct md_ctx {
     double *elog_d = nullptr;
     int64_t elog_cap = 0;
     double *io_d = nullptr;
+    double *ctr_d = nullptr;
 
     // buffer parities: x (flips at binning and at each fused FP64 step), v and
     // id (flip at binning), p32 (flips at each fused step)
@@ -138,6 +139,7 @@ Dev view(const md_ctx *c)
     d.w_atom64 = c->w64;
     d.ke_atom64 = c->ke64;
     d.status = c->status;
+    d.ctr = c->ctr_d;
     return d;
 }
 
@@ -162,7 +164,7 @@ void free_all(md_ctx *c)
                     c->id[1], c->p32[0], c->p32[1], c->f32, c->f64, c->cell_key, c->cell_count,
                     c->cell_start, c->perm, c->scan_tmp, c->nb, c->nb_count, c->pe_atom,
                     c->w_atom, c->pe64, c->w64, c->ke64, c->status, c->chunk_rep_d,
-                    c->chunk_first_d, c->partials_d, c->eout_d, c->elog_d, c->io_d};
+                    c->chunk_first_d, c->partials_d, c->eout_d, c->elog_d, c->io_d, c->ctr_d};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->own_stream && c->st) cudaStreamDestroy(c->st);
@@ -1193,6 +1195,7 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
             vol *= L[d];
         }
         R.cell_off = cells;
+        R.ctr_off = 0;   // set below
         R.atom_off = n;
         R.natoms = counts[r];
         cells += (int64_t)R.nc[0] * R.nc[1] * R.nc[2];
@@ -1265,6 +1268,17 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
     if ((rc = dalloc(c, &c->eout_d, 3 * (size_t)nrep))) return rc;
     if ((rc = dalloc(c, &c->io_d, 6 * N))) return rc;
 
+    // cell-centre table: (c + 0.5) s per replica and dimension, the same
+    // expression the kernels would evaluate
+    std::vector<double> ctr;
+    for (int32_t r = 0; r < nrep; r++) {
+        Rep &R = c->reps_h[r];
+        R.ctr_off = (int64_t)ctr.size();
+        for (int dd = 0; dd < 3; dd++)
+            for (int32_t k = 0; k < R.nc[dd]; k++) ctr.push_back(((double)k + 0.5) * R.s[dd]);
+    }
+    if ((rc = dalloc(c, &c->ctr_d, ctr.size()))) return rc;
+    CK(cudaMemcpyAsync(c->ctr_d, ctr.data(), sizeof(double) * ctr.size(), cudaMemcpyHostToDevice, c->st));
     std::vector<int32_t> rep_of(N);
     for (int32_t r = 0; r < nrep; r++)
         for (int64_t a = 0; a < counts[r]; a++) rep_of[(size_t)(c->reps_h[r].atom_off + a)] = r;

@@ -57,6 +57,7 @@ struct Rep {
     double s[3];              // cell side L / nc (FP64)
     float nsf[3];             // -s in FP32 (stencil offsets of the mixed path)
     int32_t nc[3];
+    int64_t ctr_off;          // first entry of this replica in Dev::ctr
     int64_t cell_off;         // first global cell id of this replica
     int64_t atom_off;         // first atom slot of this replica
     int64_t natoms;
@@ -97,6 +98,8 @@ struct Dev {
     float *pe_atom, *w_atom;  // per-atom energy / virial (mixed)
     double *pe_atom64, *w_atom64, *ke_atom64;
     DevStatus *status;
+    const double *ctr;        // cell-centre coordinates (c + 0.5) s: per replica
+                              // nc_x, then nc_y, then nc_z values
 };
 
 // ---------------------------------------------------------------------------
