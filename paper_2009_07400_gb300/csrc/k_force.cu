@@ -132,30 +132,10 @@ __device__ __forceinline__ void epilogue(const Dev &d, const LJ &lj, const Rep &
 // ---------------------------------------------------------------------------
 // Mixed precision, full list.
 // ---------------------------------------------------------------------------
-// How the stencil offset o (2 bits per dimension in the entry) enters
-// d = p_i - o s - p_j.  Mode 1: o read from three 3-entry shared tables
-// (conflict-free LDS.32, one L1 wavefront each per warp).  Mode 3: p_i - s,
-// p_i, p_i + s held in registers and chosen with two bit tests and two
-// selects per dimension (no L1 traffic, more ALU).
-#ifndef MD_OFFSET_MODE
-#define MD_OFFSET_MODE 3
-#endif
-#ifndef MD_FORCE_MINBLOCKS
-#define MD_FORCE_MINBLOCKS 1
-#endif
-// List chunks (4 pairs each) per loop round of the mixed full-list kernel.
-#ifndef MD_FORCE_UNROLL
-#define MD_FORCE_UNROLL 1
-#endif
-// How many rounds ahead the list chunks are loaded.
-#ifndef MD_LIST_PREFETCH
-#define MD_LIST_PREFETCH 1
-#endif
 
 // One tile of atoms of the mixed full-list kernel (tile = gt / blockDim).
 template <int TPA, bool BATCHED, int EPI, bool ENERGY>
-__device__ __forceinline__ void mixed_full_tile(const Dev &d, const LJ &lj, const float (&ot)[3],
-                                                int64_t gt)
+__device__ __forceinline__ void mixed_full_tile(const Dev &d, const LJ &lj, int64_t gt)
 {
     const int64_t i0 = gt / TPA;
     const int sub = (int)(gt % TPA);
@@ -173,7 +153,7 @@ __device__ __forceinline__ void mixed_full_tile(const Dev &d, const LJ &lj, cons
     float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
     float pe = 0.f, w = 0.f, cpe = 0.f, cw = 0.f;
     const float4 *p32 = d.p32;
-    // p_i - o s for o = -1, 0, +1 (mode 3); ns = -s
+    // p_i - o s for o = -1, 0, +1; ns = -s
     const float qx0 = pi.x - nsx, qx2 = pi.x + nsx;
     const float qy0 = pi.y - nsy, qy2 = pi.y + nsy;
     const float qz0 = pi.z - nsz, qz2 = pi.z + nsz;
@@ -182,16 +162,12 @@ __device__ __forceinline__ void mixed_full_tile(const Dev &d, const LJ &lj, cons
     auto pair = [&](uint32_t e, float &px, float &py, float &pz, float &pv, float &pw) {
         const float4 pj = __ldg(p32 + (e & kJMask));
         const uint32_t c = e >> kJBits;
-        float dx, dy, dz;
-        if (MD_OFFSET_MODE == 1) {
-            dx = fmaf(ot[c & 3u], nsx, pi.x - pj.x);
-            dy = fmaf(ot[(c >> 2) & 3u], nsy, pi.y - pj.y);
-            dz = fmaf(ot[c >> 4], nsz, pi.z - pj.z);
-        } else {
-            dx = ((c & 2u) ? qx2 : ((c & 1u) ? pi.x : qx0)) - pj.x;
-            dy = ((c & 8u) ? qy2 : ((c & 4u) ? pi.y : qy0)) - pj.y;
-            dz = ((c & 32u) ? qz2 : ((c & 16u) ? pi.z : qz0)) - pj.z;
-        }
+        // the stencil offset selects p_i + s, p_i or p_i - s in registers
+        // (measured faster than offset tables in shared memory, whose reads
+        // compete with the gathers for the L1 data pipe)
+        const float dx = ((c & 2u) ? qx2 : ((c & 1u) ? pi.x : qx0)) - pj.x;
+        const float dy = ((c & 8u) ? qy2 : ((c & 4u) ? pi.y : qy0)) - pj.y;
+        const float dz = ((c & 32u) ? qz2 : ((c & 16u) ? pi.z : qz0)) - pj.z;
         const float rsq = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
         const float sr2 = rcp_approx(rsq);
         const float t = sr2 * sr2 * sr2 * lj.sigma6f;
@@ -221,33 +197,14 @@ __device__ __forceinline__ void mixed_full_tile(const Dev &d, const LJ &lj, cons
             kahan_add(w, cw, pw);
         }
     };
+    // the next list chunk is loaded one round ahead (deeper prefetch and
+    // two chunks per round measured slower: more registers, less occupancy)
     int q = sub;
-    if (MD_FORCE_UNROLL == 2 && TPA == 1) {
-        // two chunks (8 pairs, 8 independent gathers) per round
-        for (; q + 1 < nq; q += 2) {
-            const int4 e0 = ld_stream(nb4 + (int64_t)q * n + i);
-            const int4 e1 = ld_stream(nb4 + (int64_t)(q + 1) * n + i);
-            chunk(e0);
-            chunk(e1);
-        }
-        if (q < nq) chunk(ld_stream(nb4 + (int64_t)q * n + i));
-    } else if (MD_LIST_PREFETCH == 2) {
-        // list chunks loaded two rounds ahead (covers more of the DRAM latency)
-        int4 n1 = q < nq ? ld_stream(nb4 + (int64_t)q * n + i) : make_int4(0, 0, 0, 0);
-        int4 n2 = q + TPA < nq ? ld_stream(nb4 + (int64_t)(q + TPA) * n + i) : make_int4(0, 0, 0, 0);
-        for (; q < nq; q += TPA) {
-            const int4 e = n1;
-            n1 = n2;
-            if (q + 2 * TPA < nq) n2 = ld_stream(nb4 + (int64_t)(q + 2 * TPA) * n + i);
-            chunk(e);
-        }
-    } else {
-        int4 nxt = q < nq ? ld_stream(nb4 + (int64_t)q * n + i) : make_int4(0, 0, 0, 0);
-        for (; q < nq; q += TPA) {
-            const int4 e = nxt;
-            if (q + TPA < nq) nxt = ld_stream(nb4 + (int64_t)(q + TPA) * n + i);
-            chunk(e);
-        }
+    int4 nxt = q < nq ? ld_stream(nb4 + (int64_t)q * n + i) : make_int4(0, 0, 0, 0);
+    for (; q < nq; q += TPA) {
+        const int4 e = nxt;
+        if (q + TPA < nq) nxt = ld_stream(nb4 + (int64_t)(q + TPA) * n + i);
+        chunk(e);
     }
     float fx = sx - cx, fy = sy - cy, fz = sz - cz;
     if (ENERGY) {
@@ -275,7 +232,7 @@ __device__ __forceinline__ void mixed_full_tile(const Dev &d, const LJ &lj, cons
                           __float_as_uint(pi.w), true);
 }
 
-// o + 1 -> o for the per-dimension offset tables of mode 1.
+// o + 1 -> o, a 3-entry table per block for the half-list kernel.
 __device__ __forceinline__ void fill_offsets(float (&ot)[3])
 {
     if (threadIdx.x < 3) ot[threadIdx.x] = (float)((int)threadIdx.x - 1);
@@ -283,29 +240,10 @@ __device__ __forceinline__ void fill_offsets(float (&ot)[3])
 }
 
 template <int TPA, bool BATCHED, int EPI, bool ENERGY>
-__global__ void __launch_bounds__(256, MD_FORCE_MINBLOCKS) k_force_mixed_full(Dev d, LJ lj)
+__global__ void __launch_bounds__(256) k_force_mixed_full(Dev d, LJ lj)
 {
-    __shared__ float ot[3];
-    fill_offsets(ot);
     if (stopped(d.status)) return;
-    mixed_full_tile<TPA, BATCHED, EPI, ENERGY>(d, lj, ot,
-                                               (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
-}
-
-// Persistent form: block b walks the contiguous tile range
-// [b * ntiles / grid, (b + 1) * ntiles / grid) of cell-ordered atoms, so
-// consecutive tiles of a block share most neighbours in L1.
-template <bool BATCHED, int EPI, bool ENERGY>
-__global__ void __launch_bounds__(256, MD_FORCE_MINBLOCKS) k_force_mixed_full_persist(Dev d, LJ lj,
-                                                                                      int64_t ntiles)
-{
-    __shared__ float ot[3];
-    fill_offsets(ot);
-    if (stopped(d.status)) return;
-    const int64_t t0 = (int64_t)blockIdx.x * ntiles / gridDim.x;
-    const int64_t t1 = (int64_t)(blockIdx.x + 1) * ntiles / gridDim.x;
-    for (int64_t t = t0; t < t1; t++)
-        mixed_full_tile<1, BATCHED, EPI, ENERGY>(d, lj, ot, t * blockDim.x + threadIdx.x);
+    mixed_full_tile<TPA, BATCHED, EPI, ENERGY>(d, lj, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -518,43 +456,14 @@ __global__ void __launch_bounds__(256) k_force_f64_half(Dev d, LJ lj)
     }
 }
 
-// The persistent walk measured slower on GB300 (171.5 vs 160.9 us at 1M
-// atoms), so the plain grid is the default.
-#ifndef MD_FORCE_PERSIST
-#define MD_FORCE_PERSIST 0
-#endif
-
-// Blocks of the persistent mixed kernel that fit on the GPU at once.
-template <bool B, int EP, bool EN>
-unsigned persist_grid(int64_t ntiles)
-{
-    static int blocks = -1, sms = 0;
-    if (blocks < 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(k_force_mixed_full_persist<B, EP, EN>,
-                             cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_force_mixed_full_persist<B, EP, EN>,
-                                                      256, 0);
-        if (blocks < 1) blocks = 1;
-    }
-    const int64_t g = (int64_t)blocks * sms;
-    return (unsigned)(g < ntiles ? g : ntiles);
-}
-
 template <int TPA, bool B>
 int launch_full(const Dev &d, const LJ &lj, bool mixed, int epi, bool energy, cudaStream_t st)
 {
     const int64_t threads = d.n * TPA;
     const unsigned g = (unsigned)((threads + 255) / 256);
-    const int64_t ntiles = (d.n + 255) / 256;
 #define MD_FULL(EP, EN)                                                                    \
     do {                                                                                   \
-        if (mixed && TPA == 1 && MD_FORCE_PERSIST)                                         \
-            k_force_mixed_full_persist<B, EP, EN>                                          \
-                <<<persist_grid<B, EP, EN>(ntiles), 256, 0, st>>>(d, lj, ntiles);         \
-        else if (mixed) k_force_mixed_full<TPA, B, EP, EN><<<g, 256, 0, st>>>(d, lj);      \
+        if (mixed) k_force_mixed_full<TPA, B, EP, EN><<<g, 256, 0, st>>>(d, lj);           \
         else k_force_f64_full<TPA, B, EP, EN><<<g, 256, 0, st>>>(d, lj);                   \
     } while (0)
     if (epi == EPI_F) { if (energy) MD_FULL(EPI_F, true); else MD_FULL(EPI_F, false); }
@@ -565,18 +474,6 @@ int launch_full(const Dev &d, const LJ &lj, bool mixed, int epi, bool energy, cu
 }
 
 }  // namespace
-
-// Sets the carveout and caches the occupancy of every persistent force-kernel
-// instance (outside any stream capture).
-void init_force_kernels()
-{
-    persist_grid<false, EPI_F, false>(1); persist_grid<false, EPI_F, true>(1);
-    persist_grid<false, EPI_FK, false>(1); persist_grid<false, EPI_FK, true>(1);
-    persist_grid<false, EPI_FKKD, false>(1); persist_grid<false, EPI_FKKD, true>(1);
-    persist_grid<true, EPI_F, false>(1); persist_grid<true, EPI_F, true>(1);
-    persist_grid<true, EPI_FK, false>(1); persist_grid<true, EPI_FK, true>(1);
-    persist_grid<true, EPI_FKKD, false>(1); persist_grid<true, EPI_FKKD, true>(1);
-}
 
 // Half lists only support EPI_F (the caller zeroes the force array first and
 // integrates in a separate kernel).

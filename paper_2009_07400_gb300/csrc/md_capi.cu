@@ -1222,7 +1222,6 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
     set_lj_constants(c);
 
     CK(cudaGetDevice(&c->device));
-    init_force_kernels();
     if (stream) {
         c->st = (cudaStream_t)stream;
     } else {

@@ -130,7 +130,6 @@ int launch_decode_list(const Dev &d, int32_t *rows_dev, int32_t cap, cudaStream_
                        int *nlaunch);
 
 int64_t scan_tmp_elems(int64_t ncells_total);
-void init_force_kernels();
 
 // Adjoint (k_adjoint.cu)
 int launch_adjoint_pairs(const Dev &d, const LJ &lj, bool mixed, const dvec4 *wbar, dvec4 *xbar,

@@ -80,3 +80,33 @@ def test_host_validation_without_gpu(lib):
     pos[2, 1] = np.nan
     rc, _ = _create(lib, (20.0, 20.0, 20.0), p, pos=pos)
     assert rc == -7
+
+
+def _create_batch(lib, boxes, counts, params, pos=None):
+    from paper_2009_07400_gb300 import md
+    n_pos = max(1, min(int(sum(counts)), 8))
+    pos = np.zeros((n_pos, 3)) if pos is None else pos
+    barr = (md.md_box * len(boxes))(*[md.md_box(*b) for b in boxes])
+    cnt = np.asarray(counts, np.int64)
+    h = ctypes.c_void_p()
+    rc = lib.md_create_batch(len(boxes), barr, ctypes.byref(params),
+                             cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                             pos.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                             pos.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), None,
+                             ctypes.byref(h))
+    return rc, h
+
+
+def test_size_limits_rejected_before_device_work(lib):
+    """Limits are checked on the host before any array is read or any
+    device memory is touched (the position array here is deliberately tiny)."""
+    from paper_2009_07400_gb300 import md
+    p = md.make_params()
+    rc, h = _create_batch(lib, [(20.0, 20.0, 20.0)], [0], p)
+    assert rc == -1 and not h.value                            # empty replica
+    rc, h = _create_batch(lib, [(20.0, 20.0, 20.0)], [1 << 26], p)
+    assert rc == -1 and b"67,108,863" in lib.md_last_error(None)
+    rc, h = _create_batch(lib, [(1024 * 2.8 + 1.0, 20.0, 20.0)], [4], p)
+    assert rc == -1 and b"1023 cells" in lib.md_last_error(None)
+    rc, h = _create_batch(lib, [(20.0, 20.0, 20.0), (5.0, 20.0, 20.0)], [2, 2], p)
+    assert rc == -2                                            # second box too small

@@ -374,3 +374,49 @@ def test_ensemble_256_sampled(md, orc):
         Fr = orc.forces_list(orc.wrap(x, r.box), r.box,
                              orc.neighbors_cells(orc.wrap(x, r.box), r.box, RC + SKIN))
         assert rms_rel(F[a:b], Fr) <= 1e-5
+
+
+def test_runaway_is_reported_not_faulted(md, orc):
+    """Failure detection without a GPU fault: two atoms almost on top of
+    each other blow up; the binning kernel flags the non-finite positions in
+    the device error word, every later kernel returns at once, and md_run
+    reports MD_ERR_NONFINITE with the state frozen."""
+    L = np.full(3, 12.0)
+    pos = np.array([[6.0, 6.0, 6.0], [6.0005, 6.0, 6.0], [2.0, 2.0, 2.0], [9.0, 9.0, 2.5]])
+    vel = np.zeros_like(pos)
+    with md.MDContext(pos, vel, L, precision=md.MD_FP64, rebuild_every=2) as ctx:
+        with pytest.raises(md.MDError) as e:
+            ctx.run(40)
+        assert e.value.code in (-7, -8)      # non-finite, or flung beyond one box length
+        x = ctx.positions()
+        assert np.allclose(x[2:], pos[2:])   # the far atoms never moved
+
+
+def test_single_atom_and_sparse(md, orc):
+    """Rows of length zero, empty cells and an isolated atom."""
+    L = np.full(3, 6.0)                      # nc = 2 per dimension
+    with md.MDContext(np.array([[1.0, 2.0, 3.0]]), np.array([[0.1, 0.0, 0.0]]), L) as ctx:
+        assert np.abs(ctx.forces()).max() == 0.0
+        ctx.run(25)
+        assert ctx.positions()[0, 0] == pytest.approx(1.0 + 25 * 0.005 * 0.1, rel=1e-12)
+        pe, ke, w = ctx.energy()
+        assert pe[0] == 0.0 and w[0] == 0.0 and ke[0] == pytest.approx(0.5 * 0.01)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("half", [False, True])
+def test_run_131k_energy(md, orc, precision, half):
+    """The paper's CPU workload size (32^3 cells, 131,072 atoms), both
+    precisions and list types: total energy after 100 steps against the
+    oracle (FP64: 1e-10 relative; mixed: 1e-4 per atom)."""
+    s = inputs.workload("fcc32_131072")
+    x_ref, v_ref, _ = orc.vv_run(s.pos, s.vel, s.box, 100)
+    e_ref = orc.energy(x_ref, s.box)[0] + orc.kinetic(v_ref)
+    prec = md.MD_FP64 if precision == "fp64" else md.MD_MIXED
+    with ctx_of(md, s, precision=prec, half_list=half) as ctx:
+        E = ctx.run(100, energy_every=100)
+    e = E[-1, 0, 0] + E[-1, 0, 1]
+    if precision == "fp64":
+        assert e == pytest.approx(e_ref, rel=1e-10)
+    else:
+        assert abs(e - e_ref) / s.n <= 1e-4
