@@ -381,9 +381,11 @@ def cpu_baseline_leg(pos, vel, box, counts, res):
 
 
 def run_reference(args):
-    """The reference arm: the FP64 oracle, as it stands, on the host cores;
-    each step is one oracle time step of the full workload with the list
-    build amortised over 20 steps."""
+    """The reference arm: the FP64 oracle, as it stands, on the host cores.
+    Its sample is `steps` oracle time steps of the full workload (after
+    `warmup` steps) with the list build amortised over 20 steps; value is in
+    atom-timesteps/s and ms_per_step is per 20-timestep cycle, like the GPU
+    arm's step."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -408,12 +410,14 @@ def run_reference(args):
     cores = oracle.num_threads()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": int(os.environ.get("WORLD_SIZE", args.gpus)), "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": per_step * STEPS_PER_CYCLE * 1e3,
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(config_dict(s), tuned=res["tuned"],
-                           list="half" if res["tuned"]["half_list"] else "full"),
+            "config": dict(config_dict(pos.shape[0], desc, seed), list="full",
+                           replicas=1 if counts is None else len(counts)),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{args.steps} oracle time steps of the full workload "
+                             "sample": f"{args.steps} oracle time steps of "
+                                       f"{'the full workload' if counts is None else 'one replica'} "
                                        f"after {max(1, args.warmup)} warm-up steps; list "
                                        f"build ({t_build:.2f} s) amortised over 20 steps"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
