@@ -127,6 +127,17 @@ int md_create_batch(int32_t nrep, const md_box *boxes, const md_params *params,
                     const int64_t *counts, const double *pos, const double *vel, void *stream,
                     md_ctx **out);
 
+/* As md_create, with pos and vel in device memory of the current device
+ * (n x 3 doubles, row major, caller order), e.g. the data pointers of CUDA
+ * tensors; nothing is copied through the host.  They are read on `stream`
+ * (the context's stream), so the caller orders their producer before the
+ * call; they may be freed once md_create_device has returned.  Non-finite
+ * values are detected on the device and reported as MD_ERR_NONFINITE.
+ * Errors: as md_create, and MD_ERR_INVAL if pos or vel is not device memory
+ * of the current device. */
+int md_create_device(const md_box *box, const md_params *params, int64_t n, const double *pos,
+                     const double *vel, void *stream, md_ctx **out);
+
 void md_destroy(md_ctx *ctx);
 
 /* Text of the last error of ctx (or of the last failed md_create* when ctx is
@@ -134,8 +145,15 @@ void md_destroy(md_ctx *ctx);
 const char *md_last_error(const md_ctx *ctx);
 
 /* Replaces positions and velocities (host, n x 3, caller order) and
- * re-establishes cells, list and forces.  Used for restarts. */
+ * re-establishes cells, list and forces.  Used for restarts.  The values are
+ * checked on the device as they are uploaded.
+ * Errors: MD_ERR_NONFINITE (a NaN or Inf; the context holds no valid state
+ * until the next successful md_set_state*), MD_ERR_BADPOS, MD_ERR_CUDA. */
 int md_set_state(md_ctx *ctx, const double *pos, const double *vel);
+
+/* md_set_state with pos and vel in device memory (the conventions of
+ * md_create_device). */
+int md_set_state_device(md_ctx *ctx, const double *pos, const double *vel);
 
 /* Cell binning (Sec. 3.2, Fig. 1): wraps every position into the box with
  * one conditional +/-L per component, assigns cell (int)(x/s) (clamped to
@@ -178,6 +196,15 @@ int md_run(md_ctx *ctx, int64_t nsteps, int32_t energy_every, double *energies);
 int md_get_positions(md_ctx *ctx, double *pos);
 int md_get_velocities(md_ctx *ctx, double *vel);
 int md_get_forces(md_ctx *ctx, double *force);
+
+/* Device-memory getters: write positions, velocities or forces (n x 3
+ * doubles, caller order, the values the host getters return) to `out`,
+ * device memory of the current device, asynchronously on the context's
+ * stream (no synchronisation; the caller orders its readers after it).
+ * Errors: MD_ERR_INVAL (null, or out is not device memory), MD_ERR_CUDA. */
+int md_get_positions_device(md_ctx *ctx, double *out);
+int md_get_velocities_device(md_ctx *ctx, double *out);
+int md_get_forces_device(md_ctx *ctx, double *out);
 
 /* The cells of the last binning, per replica in order: cell_start (host,
  * ncells + nrep int32: each replica's exclusive prefix sums including its

@@ -142,8 +142,13 @@ __global__ void __launch_bounds__(256) k_scatter_in(Dev d, const double *pos, co
 {
     const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= d.n) return;
-    d.x[a] = mk_dvec4(pos[3 * a], pos[3 * a + 1], pos[3 * a + 2], 0.0);
-    d.v[a] = mk_dvec4(vel[3 * a], vel[3 * a + 1], vel[3 * a + 2], 0.0);
+    const double x0 = pos[3 * a], x1 = pos[3 * a + 1], x2 = pos[3 * a + 2];
+    const double v0 = vel[3 * a], v1 = vel[3 * a + 1], v2 = vel[3 * a + 2];
+    // inputs from device memory are checked here (host inputs were already)
+    if (!(isfinite(x0) && isfinite(x1) && isfinite(x2) && isfinite(v0) && isfinite(v1) && isfinite(v2)))
+        atomicOr(&d.status->flags, FLAG_NONFINITE);
+    d.x[a] = mk_dvec4(x0, x1, x2, 0.0);
+    d.v[a] = mk_dvec4(v0, v1, v2, 0.0);
     d.id[a] = (int32_t)a;
 }
 

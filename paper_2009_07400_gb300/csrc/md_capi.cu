@@ -360,7 +360,7 @@ int read_status(md_ctx *c, DevStatus *s)
 
 int check_flags(md_ctx *c, const DevStatus &s)
 {
-    if (s.flags & FLAG_NONFINITE) return fail(c, MD_ERR_NONFINITE, "non-finite position found at binning");
+    if (s.flags & FLAG_NONFINITE) return fail(c, MD_ERR_NONFINITE, "non-finite position or velocity");
     if (s.flags & FLAG_BADPOS) return fail(c, MD_ERR_BADPOS, "an atom moved more than one box length between wraps");
     return MD_OK;
 }
@@ -447,7 +447,10 @@ int run_span(md_ctx *c, int64_t s0, int64_t first, int64_t last, bool kd, int32_
 }
 
 int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64_t *counts,
-                 int32_t nrep, const double *pos, const double *vel, void *stream);
+                 int32_t nrep, const double *pos, const double *vel, void *stream, bool on_device);
+int set_state(md_ctx *c, const double *pos, const double *vel, bool on_device);
+int gather_to(md_ctx *c, int what, double *dst);
+bool is_device_pointer(const void *p);
 
 // LJ constants of c->p (the same expressions as the FP64 definition).
 void set_lj_constants(md_ctx *c)
@@ -524,14 +527,15 @@ const char *md_last_error(const md_ctx *c)
     return c ? c->err.c_str() : g_create_error.c_str();
 }
 
-int md_create_batch(int32_t nrep, const md_box *boxes, const md_params *p, const int64_t *counts,
-                    const double *pos, const double *vel, void *stream, md_ctx **out)
+static int create_impl(int32_t nrep, const md_box *boxes, const md_params *p,
+                       const int64_t *counts, const double *pos, const double *vel, void *stream,
+                       md_ctx **out, bool on_device)
 {
     if (!out) return fail(nullptr, MD_ERR_INVAL, "out is NULL");
     *out = nullptr;
     md_ctx *c = new (std::nothrow) md_ctx();
     if (!c) return fail(nullptr, MD_ERR_NOMEM, "host allocation failed");
-    int rc = make_context(c, boxes, p, counts, nrep, pos, vel, stream);
+    int rc = make_context(c, boxes, p, counts, nrep, pos, vel, stream, on_device);
     if (rc) {
         g_create_error = c->err;
         free_all(c);
@@ -542,10 +546,22 @@ int md_create_batch(int32_t nrep, const md_box *boxes, const md_params *p, const
     return MD_OK;
 }
 
+int md_create_batch(int32_t nrep, const md_box *boxes, const md_params *p, const int64_t *counts,
+                    const double *pos, const double *vel, void *stream, md_ctx **out)
+{
+    return create_impl(nrep, boxes, p, counts, pos, vel, stream, out, false);
+}
+
 int md_create(const md_box *box, const md_params *p, int64_t n, const double *pos,
               const double *vel, void *stream, md_ctx **out)
 {
-    return md_create_batch(1, box, p, &n, pos, vel, stream, out);
+    return create_impl(1, box, p, &n, pos, vel, stream, out, false);
+}
+
+int md_create_device(const md_box *box, const md_params *p, int64_t n, const double *pos,
+                     const double *vel, void *stream, md_ctx **out)
+{
+    return create_impl(1, box, p, &n, pos, vel, stream, out, true);
 }
 
 void md_destroy(md_ctx *c)
@@ -559,27 +575,13 @@ void md_destroy(md_ctx *c)
 int md_set_state(md_ctx *c, const double *pos, const double *vel)
 {
     if (!c || !pos || !vel) return fail(c, MD_ERR_INVAL, "null argument");
-    for (int64_t t = 0; t < 3 * c->n; t++)
-        if (!std::isfinite(pos[t]) || !std::isfinite(vel[t]))
-            return fail(c, MD_ERR_NONFINITE, "non-finite input");
-    const size_t bytes = sizeof(double) * 3 * (size_t)c->n;
-    CK(cudaMemcpyAsync(c->io_d, pos, bytes, cudaMemcpyHostToDevice, c->st));
-    CK(cudaMemcpyAsync(c->io_d + 3 * c->n, vel, bytes, cudaMemcpyHostToDevice, c->st));
-    c->xp = 0;
-    c->vp = 0;
-    c->pb = 0;
-    int nl = 0;
-    Dev d = view(c);
-    if (launch_scatter_in(d, c->io_d, c->io_d + 3 * c->n, c->st, &nl))
-        return fail(c, MD_ERR_CUDA, "upload launch failed");
-    c->launches += nl;
-    CK(cudaMemsetAsync(c->status, 0, sizeof(DevStatus), c->st));
-    c->moved_since_bin = true;
-    c->list_valid = false;
-    c->forces_valid = false;
-    int rc = rebuild_now(c, true);
-    if (rc) return rc;
-    return ensure_forces(c);
+    return set_state(c, pos, vel, false);
+}
+
+int md_set_state_device(md_ctx *c, const double *pos, const double *vel)
+{
+    if (!c || !pos || !vel) return fail(c, MD_ERR_INVAL, "null argument");
+    return set_state(c, pos, vel, true);
 }
 
 int md_bin_cells(md_ctx *c)
@@ -754,6 +756,29 @@ int md_get_forces(md_ctx *c, double *out)
     CK(cudaMemcpyAsync(out, c->io_d, sizeof(double) * 3 * c->n, cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
     return MD_OK;
+}
+
+int md_get_positions_device(md_ctx *c, double *out)
+{
+    if (!c || !out) return fail(c, MD_ERR_INVAL, "null argument");
+    if (!is_device_pointer(out)) return fail(c, MD_ERR_INVAL, "out is not a device pointer");
+    return gather_to(c, 0, out);
+}
+
+int md_get_velocities_device(md_ctx *c, double *out)
+{
+    if (!c || !out) return fail(c, MD_ERR_INVAL, "null argument");
+    if (!is_device_pointer(out)) return fail(c, MD_ERR_INVAL, "out is not a device pointer");
+    return gather_to(c, 1, out);
+}
+
+int md_get_forces_device(md_ctx *c, double *out)
+{
+    if (!c || !out) return fail(c, MD_ERR_INVAL, "null argument");
+    if (!is_device_pointer(out)) return fail(c, MD_ERR_INVAL, "out is not a device pointer");
+    int rc = ensure_forces(c);
+    if (rc) return rc;
+    return gather_to(c, is_mixed(c) ? 3 : 2, out);
 }
 
 int md_get_cells(md_ctx *c, int32_t *cell_start, int32_t *cell_atoms)
@@ -1156,8 +1181,19 @@ int md_autotune(md_ctx *c, int32_t steps, md_params *chosen)
 // ---------------------------------------------------------------------------
 namespace {
 
+// True if p is memory the current device can read (device or managed).
+bool is_device_pointer(const void *p)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
 int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64_t *counts,
-                 int32_t nrep, const double *pos, const double *vel, void *stream)
+                 int32_t nrep, const double *pos, const double *vel, void *stream, bool on_device)
 {
     if (!boxes || !p || !counts || !pos || !vel || nrep <= 0)
         return fail(c, MD_ERR_INVAL, "null argument or nrep <= 0");
@@ -1212,9 +1248,14 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
     chunk_first.push_back((int64_t)chunk_rep.size() / 2);
     if (n > (int64_t)kJMask) return fail(c, MD_ERR_INVAL, "more than 67,108,863 atoms (26-bit list indices)");
     if (cells >= (int64_t)1 << 31) return fail(c, MD_ERR_INVAL, "too many cells");
-    for (int64_t t = 0; t < 3 * n; t++)
-        if (!std::isfinite(pos[t]) || !std::isfinite(vel[t]))
-            return fail(c, MD_ERR_NONFINITE, "non-finite input");
+    if (on_device) {
+        if (!is_device_pointer(pos) || !is_device_pointer(vel))
+            return fail(c, MD_ERR_INVAL, "pos/vel are not device pointers of the current device");
+    } else {
+        for (int64_t t = 0; t < 3 * n; t++)
+            if (!std::isfinite(pos[t]) || !std::isfinite(vel[t]))
+                return fail(c, MD_ERR_NONFINITE, "non-finite input");
+    }
     c->n = n;
     c->ncells = cells;
     c->nchunks = (int64_t)chunk_rep.size() / 2;
@@ -1297,7 +1338,51 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
     int64_t cap0 = (int64_t)(1.3 * expect) + 16;
     cap0 = std::min<int64_t>(cap0, maxn + 3);
     if ((rc = alloc_list(c, (int32_t)std::max<int64_t>(cap0, 4)))) return rc;
-    return md_set_state(c, pos, vel);
+    return set_state(c, pos, vel, on_device);
+}
+
+// Replaces the state from host or device arrays (n x 3, caller order).
+// Inputs are checked for non-finite values by the upload kernel
+// (FLAG_NONFINITE, reported by the rebuild that follows).
+int set_state(md_ctx *c, const double *pos, const double *vel, bool on_device)
+{
+    const double *src_x = pos, *src_v = vel;
+    if (on_device) {
+        if (!is_device_pointer(pos) || !is_device_pointer(vel))
+            return fail(c, MD_ERR_INVAL, "pos/vel are not device pointers of the current device");
+    } else {
+        // no host-side scan: the upload kernel checks every value
+        const size_t bytes = sizeof(double) * 3 * (size_t)c->n;
+        CK(cudaMemcpyAsync(c->io_d, pos, bytes, cudaMemcpyHostToDevice, c->st));
+        CK(cudaMemcpyAsync(c->io_d + 3 * c->n, vel, bytes, cudaMemcpyHostToDevice, c->st));
+        src_x = c->io_d;
+        src_v = c->io_d + 3 * c->n;
+    }
+    c->xp = 0;
+    c->vp = 0;
+    c->pb = 0;
+    CK(cudaMemsetAsync(c->status, 0, sizeof(DevStatus), c->st));
+    int nl = 0;
+    Dev d = view(c);
+    if (launch_scatter_in(d, src_x, src_v, c->st, &nl))
+        return fail(c, MD_ERR_CUDA, "upload launch failed");
+    c->launches += nl;
+    c->moved_since_bin = true;
+    c->list_valid = false;
+    c->forces_valid = false;
+    int rc = rebuild_now(c, true);
+    if (rc) return rc;
+    return ensure_forces(c);
+}
+
+// Writes quantity `what` (launch_gather_out codes) in caller order to dst
+// (device, n x 3 doubles) on the context's stream.
+int gather_to(md_ctx *c, int what, double *dst)
+{
+    int nl = 0;
+    if (launch_gather_out(view(c), what, dst, c->st, &nl)) return fail(c, MD_ERR_CUDA, "gather failed");
+    c->launches += nl;
+    return MD_OK;
 }
 
 }  // namespace

@@ -22,6 +22,8 @@ ERRORS = {
     -8: "MD_ERR_BADPOS", -9: "MD_ERR_STATE",
 }
 MD_FP64, MD_MIXED = 0, 1
+(MD_ERR_INVAL, MD_ERR_BOX_TOO_SMALL, MD_ERR_NOMEM, MD_ERR_CUDA, MD_ERR_NL_OVERFLOW,
+ MD_ERR_TIMEOUT, MD_ERR_NONFINITE, MD_ERR_BADPOS, MD_ERR_STATE) = range(-1, -10, -1)
 
 # Every exported entry point of the ABI (checked by the load test).
 ABI_SYMBOLS = [
@@ -29,7 +31,9 @@ ABI_SYMBOLS = [
     "md_bin_cells", "md_build_neighbors", "md_compute_forces", "md_integrate", "md_energy",
     "md_run", "md_get_positions", "md_get_velocities", "md_get_forces", "md_get_cells",
     "md_get_neighbors", "md_get_info", "md_autotune", "md_set_capacity", "md_profile",
-    "md_set_lj", "md_adjoint", "md_energy_sums_static",
+    "md_set_lj", "md_adjoint", "md_energy_sums_static", "md_create_device",
+    "md_set_state_device", "md_get_positions_device", "md_get_velocities_device",
+    "md_get_forces_device",
 ]
 
 
@@ -113,6 +117,12 @@ def load(path: str | None = None):
                 "md_adjoint": [ctx, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, _D, _D, _D,
                                _D, _D],
                 "md_energy_sums_static": [ctypes.c_int64, _P, _P, _P, ctypes.c_double, _P, _P],
+                "md_create_device": [ctypes.POINTER(md_box), ctypes.POINTER(md_params),
+                                     ctypes.c_int64, _P, _P, _P, ctypes.POINTER(ctx)],
+                "md_set_state_device": [ctx, _P, _P],
+                "md_get_positions_device": [ctx, _P],
+                "md_get_velocities_device": [ctx, _P],
+                "md_get_forces_device": [ctx, _P],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -133,6 +143,16 @@ def energy_sums_static(n, pe_atom_ptr, w_atom_ptr, vel_ptr, mass, out3_ptr, stre
                                    ctypes.c_void_p(int(stream)) if stream else None)
     if rc != MD_OK:
         raise MDError(rc, lib.md_last_error(None).decode())
+
+
+def _dev3(a):
+    """A contiguous CUDA float64 (n, 3) tensor, or TypeError."""
+    import torch
+    if not isinstance(a, torch.Tensor) or not a.is_cuda or a.dtype != torch.float64:
+        raise TypeError("expected a CUDA float64 tensor")
+    if a.dim() != 2 or a.shape[1] != 3 or not a.is_contiguous():
+        raise TypeError("expected a contiguous n x 3 tensor")
+    return a
 
 
 def _f64(a, n):
@@ -174,6 +194,35 @@ class MDContext:
             raise MDError(rc, lib.md_last_error(None).decode())
         self._h = h
 
+    @classmethod
+    def from_device(cls, pos, vel, box, stream=None, **params):
+        """A single-system context from CUDA float64 tensors (n x 3) without a
+        host copy (md_create_device).  The context runs on `stream` (a
+        torch.cuda.Stream; a new one if None), which first waits for the
+        current stream, where pos and vel were produced."""
+        import torch
+        pos, vel = _dev3(pos), _dev3(vel)
+        if pos.shape != vel.shape:
+            raise ValueError("pos and vel differ in shape")
+        self = cls.__new__(cls)
+        self._lib = load()
+        self.params = make_params(**params)
+        self.counts = np.array([pos.shape[0]], np.int64)
+        self.n = int(pos.shape[0])
+        self.nrep = 1
+        self._tstream = stream if stream is not None else torch.cuda.Stream(device=pos.device)
+        self._tstream.wait_stream(torch.cuda.current_stream(pos.device))
+        b = md_box(*map(float, np.broadcast_to(np.asarray(box, np.float64), (3,))))
+        h = ctypes.c_void_p()
+        rc = self._lib.md_create_device(ctypes.byref(b), ctypes.byref(self.params), self.n,
+                                        ctypes.c_void_p(pos.data_ptr()),
+                                        ctypes.c_void_p(vel.data_ptr()),
+                                        ctypes.c_void_p(self._tstream.cuda_stream), ctypes.byref(h))
+        if rc != MD_OK:
+            raise MDError(rc, self._lib.md_last_error(None).decode())
+        self._h = h
+        return self
+
     # -- helpers --------------------------------------------------------------
     def _check(self, rc):
         if rc != MD_OK:
@@ -201,6 +250,49 @@ class MDContext:
         pos = _f64(pos, self.n)
         vel = _f64(vel, self.n)
         self._check(self._lib.md_set_state(self._h, pos.ctypes.data_as(_D), vel.ctypes.data_as(_D)))
+
+    def set_state_device(self, pos, vel):
+        """md_set_state_device from CUDA float64 tensors (n x 3)."""
+        import torch
+        pos, vel = _dev3(pos), _dev3(vel)
+        if tuple(pos.shape) != (self.n, 3) or tuple(vel.shape) != (self.n, 3):
+            raise ValueError("expected n x 3 tensors")
+        self._before_device_call(torch)
+        self._check(self._lib.md_set_state_device(self._h, ctypes.c_void_p(pos.data_ptr()),
+                                                  ctypes.c_void_p(vel.data_ptr())))
+
+    def _before_device_call(self, torch):
+        ts = getattr(self, "_tstream", None)
+        if ts is not None:
+            ts.wait_stream(torch.cuda.current_stream(ts.device))
+        else:
+            torch.cuda.current_stream().synchronize()
+
+    def _get3_device(self, fn, out):
+        import torch
+        if out is None:
+            out = torch.empty((self.n, 3), dtype=torch.float64, device="cuda")
+        out = _dev3(out)
+        if tuple(out.shape) != (self.n, 3):
+            raise ValueError("expected an n x 3 tensor")
+        self._before_device_call(torch)
+        self._check(fn(self._h, ctypes.c_void_p(out.data_ptr())))
+        ts = getattr(self, "_tstream", None)
+        if ts is not None:
+            torch.cuda.current_stream(ts.device).wait_stream(ts)
+        else:
+            torch.cuda.synchronize()
+        return out
+
+    def positions_device(self, out=None):
+        """Positions into a CUDA float64 tensor (n x 3), caller order."""
+        return self._get3_device(self._lib.md_get_positions_device, out)
+
+    def velocities_device(self, out=None):
+        return self._get3_device(self._lib.md_get_velocities_device, out)
+
+    def forces_device(self, out=None):
+        return self._get3_device(self._lib.md_get_forces_device, out)
 
     def bin_cells(self):
         self._check(self._lib.md_bin_cells(self._h))

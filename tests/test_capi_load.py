@@ -110,3 +110,18 @@ def test_size_limits_rejected_before_device_work(lib):
     assert rc == -1 and b"1023 cells" in lib.md_last_error(None)
     rc, h = _create_batch(lib, [(20.0, 20.0, 20.0), (5.0, 20.0, 20.0)], [2, 2], p)
     assert rc == -2                                            # second box too small
+
+
+def test_device_entry_points_reject_host_memory(lib):
+    """md_create_device checks that pos/vel are device memory before any
+    device work (here there is no device at all, or the arrays are host)."""
+    from paper_2009_07400_gb300 import md
+    p = md.make_params()
+    pos = np.zeros((4, 3))
+    b = md.md_box(20.0, 20.0, 20.0)
+    h = ctypes.c_void_p()
+    rc = lib.md_create_device(ctypes.byref(b), ctypes.byref(p), 4,
+                              ctypes.c_void_p(pos.ctypes.data), ctypes.c_void_p(pos.ctypes.data),
+                              None, ctypes.byref(h))
+    assert rc == -1 and not h.value
+    assert b"not device pointers" in lib.md_last_error(None)

@@ -443,3 +443,43 @@ def test_run_131k_energy(md, orc, precision, half):
         assert e == pytest.approx(e_ref, rel=1e-10)
     else:
         assert abs(e - e_ref) / s.n <= 1e-4
+
+
+def test_device_pointer_api(md, orc):
+    """md_create_device / md_set_state_device / md_get_*_device on CUDA
+    tensors give bit-for-bit the trajectory of the host-array entry points;
+    a non-finite device input is reported, not propagated."""
+    torch = pytest.importorskip("torch")
+    s = inputs.workload("fcc8_2048")
+    pos_t = torch.tensor(s.pos, dtype=torch.float64, device="cuda")
+    vel_t = torch.tensor(s.vel, dtype=torch.float64, device="cuda")
+    for precision in (md.MD_FP64, md.MD_MIXED):
+        with ctx_of(md, s, precision=precision) as a:
+            b = md.MDContext.from_device(pos_t, vel_t, s.box, precision=precision)
+            try:
+                a.run(45)
+                b.run(45)
+                assert np.array_equal(a.positions(), b.positions_device().cpu().numpy())
+                assert np.array_equal(a.velocities(), b.velocities_device().cpu().numpy())
+                assert np.array_equal(a.forces(), b.forces_device().cpu().numpy())
+                a.set_state(s.pos, s.vel)
+                b.set_state_device(pos_t, vel_t)
+                a.run(7)
+                b.run(7)
+                out = torch.full((s.n, 3), float("nan"), dtype=torch.float64, device="cuda")
+                b.positions_device(out)
+                assert np.array_equal(a.positions(), out.cpu().numpy())
+                bad = vel_t.clone()
+                bad[17, 2] = float("inf")
+                with pytest.raises(md.MDError) as e:
+                    b.set_state_device(pos_t, bad)
+                assert e.value.code == md.MD_ERR_NONFINITE
+                b.set_state_device(pos_t, vel_t)          # usable again
+                b.run(7)
+                a.set_state(s.pos, s.vel)
+                a.run(7)
+                assert np.array_equal(a.positions(), b.positions_device().cpu().numpy())
+            finally:
+                b.close()
+    with pytest.raises(TypeError):
+        md.MDContext.from_device(pos_t.cpu(), vel_t.cpu(), s.box)
