@@ -123,6 +123,8 @@ WORKLOADS = {
     "fcc64_1048576": dict(n_cells=64, jitter=0.05, seed=1003),
     "fcc128_8388608": dict(n_cells=128, jitter=0.05, seed=1003),
     "fcc16_16384": dict(n_cells=16, jitter=0.0, seed=1005),
+    # the paper's single-GPU workload (Sec. 6: 80^3 unit cells, 2,048,000 atoms)
+    "fcc80_2048000": dict(n_cells=80, jitter=0.0, seed=1006),
 }
 
 

@@ -65,11 +65,14 @@ def liquid(orc, n_cells=7, steps=60, seed=3):
     return inputs.System(x, v, s.box, seed)
 
 
-def band_system(seed=5):
+def band_system(seed=5, L=(30.0, 31.0, 29.0)):
     """Pairs placed within 1e-15 .. 1e-5 of the list radius (and exactly on
-    it) so that the FP64 decision inside the FP32 band is exercised."""
+    it) so that the FP64 decision inside the FP32 band is exercised.  With
+    L = (8.39, 5.75, 30.0) the cell sides differ by 1.5x (nc = 2, 2, 10): the
+    largest cell-relative coordinates and stencil offsets the FP32 prefilter
+    meets."""
     rng = np.random.default_rng(seed)
-    L = np.array([30.0, 31.0, 29.0])
+    L = np.array(L)
     rs = RC + SKIN
     a = rng.uniform(0, 1, size=(120, 3)) * L
     u = rng.normal(size=(120, 3))
@@ -110,7 +113,7 @@ def test_bin_parity(md, orc, case):
 # --------------------------------------------------------------------------
 
 @pytest.mark.parametrize("half", [False, True])
-@pytest.mark.parametrize("case", ["fcc8", "jitter7", "nc2", "aniso", "band", "liquid"])
+@pytest.mark.parametrize("case", ["fcc8", "jitter7", "nc2", "aniso", "band", "band_wide", "liquid"])
 def test_list_parity(md, orc, case, half):
     if case == "fcc8":
         s = inputs.fcc_system(8, seed=1001)
@@ -122,6 +125,8 @@ def test_list_parity(md, orc, case, half):
         s = inputs.uniform_box(900, (5.7, 9.0, 12.3), seed=10)
     elif case == "band":
         s = band_system()
+    elif case == "band_wide":
+        s = band_system(seed=6, L=(8.39, 5.75, 30.0))
     else:
         s = liquid(orc)
     for precision in (md.MD_FP64, md.MD_MIXED):
