@@ -69,8 +69,14 @@ typedef struct {
     double cutoff;           /* rc, an absolute length; pairs with r^2 < rc^2 act   */
     double skin;             /* Verlet buffer; list radius rs = rc + skin (strict)  */
     double dt;               /* time step                                           */
-    int32_t rebuild_every;   /* rebuild cells + list after the drift of step n when
-                                n % rebuild_every == 0 (plus once at start)          */
+    int32_t rebuild_every;   /* > 0: rebuild cells + list after the drift of step n
+                                when n % rebuild_every == 0 (plus once at start),
+                                the schedule of Sec. 6.  0: rebuild after any drift
+                                that moved some atom more than skin/2 (less 1e-5)
+                                since the last binning, so every list holds all
+                                pairs inside rc; checked on the device each step,
+                                the rebuild is a conditional node of the captured
+                                step graph (no host round trip)                   */
     int32_t precision;       /* MD_FP64 or MD_MIXED                                 */
     int32_t half_list;       /* 0: full lists; 1: half lists: pair (i,j) stored
                                 with i iff j's nearest image is in i's upper
@@ -245,9 +251,9 @@ int md_set_lj(md_ctx *ctx, double epsilon, double sigma);
  * before it is reversed.  g_x0 / g_v0: host, n x 3 doubles in caller order
  * (each may be NULL).  The context is left at (x0, v0).  Work memory is
  * allocated for the call and freed before it returns.
- * Errors: MD_ERR_INVAL (nrep != 1; window not in [1, nsteps]; ckpt_every not
- * dividing both rebuild_every and nsteps), MD_ERR_NOMEM, MD_ERR_CUDA and
- * those of md_run. */
+ * Errors: MD_ERR_INVAL (nrep != 1; rebuild_every == 0; window not in
+ * [1, nsteps]; ckpt_every not dividing both rebuild_every and nsteps),
+ * MD_ERR_NOMEM, MD_ERR_CUDA and those of md_run. */
 int md_adjoint(md_ctx *ctx, int64_t nsteps, int64_t window, int32_t ckpt_every, double *loss,
                double *g_eps, double *g_sigma, double *g_x0, double *g_v0);
 

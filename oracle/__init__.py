@@ -304,7 +304,9 @@ def kinetic(v, mass=1.0):
 
 
 def vv_run(x, v, L, nsteps, step0=0, energies=False, **kw):
-    """Velocity Verlet with the fixed rebuild schedule (Sec. 3.2 Eq. 1; Sec. 6).
+    """Velocity Verlet with the fixed rebuild schedule (Sec. 3.2 Eq. 1; Sec. 6),
+    or, with rebuild_every=0, rebuilding whenever an atom has moved more than
+    skin/2 since the last build.
 
     Returns (x, v, F[, E]) where E is (nsteps, 3) = (PE, KE, W) after each step.
     """

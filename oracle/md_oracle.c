@@ -44,7 +44,10 @@
  *     and j > i (del of the pair seen from j is exactly -del, so each pair
  *     is kept once, and every row holds about half of its neighbours);
  *   - rebuild after the drift of step n iff n % rebuild_every == 0, plus an
- *     initial build at step 0;
+ *     initial build at step 0; rebuild_every == 0 instead rebuilds after any
+ *     drift that leaves some atom more than skin/2 from where it was at the
+ *     last build (the condition under which a list built with the skin still
+ *     holds every pair inside rc, Sec. 3.2, Fig. 1);
  *   - KE = 1/2 m sum v^2, W = sum over pairs of f*r^2 (= sum r_ij . F_ij).
  *
  * Parity unpinned: none of the functions here.  Each is pinned by a test
@@ -518,6 +521,13 @@ int orc_vv_run(int64_t n, const double L[3], const orc_params *p, double *x, dou
     int rc = sim_init(&S, n, L, p);
     if (rc) return rc;
     if ((rc = sim_rebuild(&S, x))) { sim_free(&S); return rc; }
+    /* displacement trigger: positions at the last build */
+    double *xref = NULL;
+    if (p->rebuild_every == 0) {
+        xref = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+        if (!xref) { sim_free(&S); return -2; }
+        memcpy(xref, x, sizeof(double) * 3 * (size_t)n);
+    }
     orc_forces_list(n, x, S.L, S.cap, S.counts, S.list, p, F);
     double half_dt_m = 0.5 * p->dt / p->mass;
     for (int64_t q = 1; q <= nsteps; q++) {
@@ -526,8 +536,25 @@ int orc_vv_run(int64_t n, const double L[3], const orc_params *p, double *x, dou
             v[t] += half_dt_m * F[t];
             x[t] += p->dt * v[t];
         }
-        if (p->rebuild_every > 0 && step % p->rebuild_every == 0)
-            if ((rc = sim_rebuild(&S, x))) { sim_free(&S); return rc; }
+        int rebuild = 0;
+        if (p->rebuild_every > 0) {
+            rebuild = step % p->rebuild_every == 0;
+        } else {
+            double h = 0.5 * p->skin, m2 = 0.0;
+            for (int64_t i = 0; i < n; i++) {
+                double d2 = 0.0;
+                for (int k = 0; k < 3; k++) {
+                    double d = x[3 * i + k] - xref[3 * i + k];
+                    d2 += d * d;
+                }
+                if (d2 > m2) m2 = d2;
+            }
+            rebuild = m2 > h * h;
+        }
+        if (rebuild) {
+            if ((rc = sim_rebuild(&S, x))) { sim_free(&S); free(xref); return rc; }
+            if (xref) memcpy(xref, x, sizeof(double) * 3 * (size_t)n);
+        }
         orc_forces_list(n, x, S.L, S.cap, S.counts, S.list, p, F);
         for (int64_t t = 0; t < 3 * n; t++) v[t] += half_dt_m * F[t];
         if (energies) {
@@ -539,5 +566,6 @@ int orc_vv_run(int64_t n, const double L[3], const orc_params *p, double *x, dou
         }
     }
     sim_free(&S);
+    free(xref);
     return 0;
 }

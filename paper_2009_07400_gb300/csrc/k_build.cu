@@ -185,6 +185,7 @@ __global__ void __launch_bounds__(128) k_build(Dev d, LJ lj)
     if (cnt > d.cap) {
         atomicOr(&d.status->flags, FLAG_NL_OVERFLOW);
         d.status->overflow_at = d.status->rebuild_count;
+        d.status->overflow_step = d.status->dev_step;
     }
 }
 

@@ -123,8 +123,10 @@ __device__ __forceinline__ void epilogue(const Dev &d, const LJ &lj, const Rep &
             cy = ((double)((pack >> 10) & 1023u) + 0.5) * R.s[1];
             cz = ((double)((pack >> 20) & 1023u) + 0.5) * R.s[2];
         }
-        d.p32_nxt[i] = make_float4((float)(x.x - cx), (float)(x.y - cy), (float)(x.z - cz),
-                                   __uint_as_float(pack));
+        const float4 pn = make_float4((float)(x.x - cx), (float)(x.y - cy), (float)(x.z - cz),
+                                      __uint_as_float(pack));
+        d.p32_nxt[i] = pn;
+        check_displacement(d, i, pn);
     }
     d.v[i] = v;
 }

@@ -54,7 +54,38 @@ __global__ void __launch_bounds__(256) k_integrate(Dev d, LJ lj, int phase, int 
     const double cx = ((double)(pack & 1023u) + 0.5) * R.s[0];
     const double cy = ((double)((pack >> 10) & 1023u) + 0.5) * R.s[1];
     const double cz = ((double)((pack >> 20) & 1023u) + 0.5) * R.s[2];
-    d.p32[i] = make_float4((float)(x.x - cx), (float)(x.y - cy), (float)(x.z - cz), p.w);
+    const float4 pn = make_float4((float)(x.x - cx), (float)(x.y - cy), (float)(x.z - cz), p.w);
+    d.p32[i] = pn;
+    check_displacement(d, i, pn);
+}
+
+// After a binning with the displacement trigger: the reordered state goes
+// back into the current buffers (so the buffer roles of the captured step
+// graph do not depend on whether the rebuild ran) and p32 becomes the
+// reference of the next displacement checks.
+__global__ void __launch_bounds__(256) k_copy_back(Dev d)
+{
+    if (stopped(d.status)) return;
+    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= d.n) return;
+    d.x[a] = d.x_alt[a];
+    d.v[a] = d.v_alt[a];
+    d.id[a] = d.id_alt[a];
+    d.p32_ref[a] = d.p32[a];
+}
+
+// One thread: decides whether the step's conditional rebuild runs (an atom
+// moved past the trigger distance and no error is pending) and prepares the
+// status word for it.
+__global__ void k_rebuild_check(DevStatus *st, cudaGraphConditionalHandle h)
+{
+    const bool go = st->need_rebuild != 0 && *((volatile const int32_t *)&st->flags) == 0;
+    st->dev_step += 1;
+    if (go) {
+        st->need_rebuild = 0;
+        st->max_count = 0;
+    }
+    cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
 constexpr int kChunk = 4096;   // atoms per reduction chunk
@@ -220,6 +251,21 @@ int launch_scatter_in(const Dev &d, const double *pos, const double *vel, cudaSt
     if (d.n <= 0) return 0;
     const unsigned g = (unsigned)((d.n + 255) / 256);
     k_scatter_in<<<g, 256, 0, st>>>(d, pos, vel);
+    *nl += 1;
+    return (int)cudaGetLastError();
+}
+
+int launch_copy_back(const Dev &d, cudaStream_t st, int *nl)
+{
+    if (d.n <= 0 || !d.p32_ref) return d.p32_ref ? 0 : -1;
+    k_copy_back<<<(unsigned)((d.n + 255) / 256), 256, 0, st>>>(d);
+    *nl += 1;
+    return (int)cudaGetLastError();
+}
+
+int launch_rebuild_check(const Dev &d, cudaGraphConditionalHandle h, cudaStream_t st, int *nl)
+{
+    k_rebuild_check<<<1, 1, 0, st>>>(d.status, h);
     *nl += 1;
     return (int)cudaGetLastError();
 }

@@ -32,7 +32,9 @@ namespace {
 thread_local std::string g_create_error;
 
 struct Op {
-    enum Kind { KD, REBUILD, FORCE } kind;
+    // COND: the displacement-triggered rebuild check of step n (a graph
+    // conditional node whose body bins and rebuilds)
+    enum Kind { KD, REBUILD, FORCE, COND } kind;
     int64_t step;   // step n the op belongs to
     bool last;      // FORCE: last step of the run (store F, no next drift)
     bool energy;    // FORCE: log (PE, KE, W) of step n
@@ -65,6 +67,10 @@ struct md_ctx {
     dvec4 *x[2] = {nullptr, nullptr}, *v[2] = {nullptr, nullptr};
     int32_t *id[2] = {nullptr, nullptr};
     float4 *p32[2] = {nullptr, nullptr};
+    float4 *p32_ref = nullptr;      // displacement trigger: p32 at the last binning
+    cudaStream_t side = nullptr;    // displacement trigger: captures the conditional bodies
+    bool disp = false;              // md_params.rebuild_every == 0
+    float disp2_thr = 0.f;
     float4 *f32 = nullptr;
     dvec4 *f64 = nullptr;
     int32_t *cell_key = nullptr, *cell_count = nullptr, *cell_start = nullptr, *perm = nullptr;
@@ -125,6 +131,8 @@ Dev view(const md_ctx *c)
     d.id_alt = c->id[1 - c->vp];
     d.p32 = c->p32[c->pb];
     d.p32_nxt = c->p32[1 - c->pb];
+    d.p32_ref = c->p32_ref;
+    d.disp2_thr = c->disp2_thr;
     d.f32 = c->f32;
     d.f64 = c->f64;
     d.cell_key = c->cell_key;
@@ -164,10 +172,12 @@ void free_all(md_ctx *c)
                     c->id[1], c->p32[0], c->p32[1], c->f32, c->f64, c->cell_key, c->cell_count,
                     c->cell_start, c->perm, c->scan_tmp, c->nb, c->nb_count, c->pe_atom,
                     c->w_atom, c->pe64, c->w64, c->ke64, c->status, c->chunk_rep_d,
-                    c->chunk_first_d, c->partials_d, c->eout_d, c->elog_d, c->io_d, c->ctr_d};
+                    c->chunk_first_d, c->partials_d, c->eout_d, c->elog_d, c->io_d, c->ctr_d,
+                    c->p32_ref};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->own_stream && c->st) cudaStreamDestroy(c->st);
+    if (c->side) cudaStreamDestroy(c->side);
 }
 
 bool is_mixed(const md_ctx *c) { return c->p.precision == MD_MIXED; }
@@ -195,8 +205,14 @@ int enq_bin(md_ctx *c, int *nl)
     Dev d = view(c);
     if (launch_bin(d, c->ncells, c->scan_tmp, c->scan_len, c->st, nl) != 0)
         return fail(c, MD_ERR_CUDA, "binning launch failed");
-    c->xp = 1 - c->xp;  // reordered state now lives in the other buffers
-    c->vp = 1 - c->vp;
+    if (c->disp) {
+        // the reordered state is copied back: buffer roles never change
+        if (launch_copy_back(d, c->st, nl) != 0) return fail(c, MD_ERR_CUDA, "copy-back launch failed");
+        CK(cudaMemsetAsync(&c->status->need_rebuild, 0, sizeof(int32_t), c->st));
+    } else {
+        c->xp = 1 - c->xp;  // reordered state now lives in the other buffers
+        c->vp = 1 - c->vp;
+    }
     c->moved_since_bin = false;
     c->list_valid = false;
     c->forces_valid = false;
@@ -260,6 +276,47 @@ int enq_force(md_ctx *c, int epi, bool energy, int *nl, cudaEvent_t *ev = nullpt
     return MD_OK;
 }
 
+// Under stream capture: a one-thread kernel that sets a graph conditional
+// when some atom moved past the trigger distance, then an IF node whose body
+// bins (copying the state back) and rebuilds the list.  Buffer parities are
+// the same whether or not the body runs.
+int enq_cond_rebuild(md_ctx *c, int *nl)
+{
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(c->st, &cs, nullptr, &g, &deps, nullptr, &nd));
+    if (cs != cudaStreamCaptureStatusActive)
+        return fail(c, MD_ERR_STATE, "conditional rebuild outside a graph capture");
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+    const Dev d = view(c);
+    if (launch_rebuild_check(d, h, c->st, nl)) return fail(c, MD_ERR_CUDA, "check launch failed");
+    CK(cudaStreamGetCaptureInfo(c->st, &cs, nullptr, &g, &deps, nullptr, &nd));
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeIf;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &np));
+    CK(cudaStreamUpdateCaptureDependencies(c->st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    CK(cudaStreamBeginCaptureToGraph(c->side, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    int bl = 0, rc = MD_OK;
+    if (launch_bin(d, c->ncells, c->scan_tmp, c->scan_len, c->side, &bl) != 0 ||
+        launch_copy_back(d, c->side, &bl) != 0 ||
+        launch_build(d, c->lj, is_half(c), c->ncells, c->side, &bl) != 0)
+        rc = fail(c, MD_ERR_CUDA, "rebuild body launch failed");
+    cudaGraph_t out = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->side, &out);
+    if (rc) return rc;
+    if (e != cudaSuccess) return fail(c, MD_ERR_CUDA, std::string("body capture: ") + cudaGetErrorString(e));
+    // counted as launches only when the body runs; the host does not know
+    return MD_OK;
+}
+
 int enq_op(md_ctx *c, const Op &op, int *nl)
 {
     int rc = MD_OK;
@@ -272,6 +329,8 @@ int enq_op(md_ctx *c, const Op &op, int *nl)
     } else if (op.kind == Op::REBUILD) {
         if ((rc = enq_bin(c, nl))) return rc;
         if ((rc = enq_build(c, nl))) return rc;
+    } else if (op.kind == Op::COND) {
+        if ((rc = enq_cond_rebuild(c, nl))) return rc;
     } else {
         const int epi = op.last ? EPI_FK : EPI_FKKD;
         // For FK with energy on half lists the KE is of the final v: the
@@ -290,6 +349,7 @@ std::string key_of(const md_ctx *c, const std::vector<Op> &ops)
     for (const Op &o : ops) {
         if (o.kind == Op::KD) k += 'K';
         else if (o.kind == Op::REBUILD) k += 'R';
+        else if (o.kind == Op::COND) k += 'C';
         else k += o.last ? (o.energy ? 'L' : 'l') : (o.energy ? 'E' : 'e');
     }
     return k;
@@ -343,6 +403,8 @@ int run_segment(md_ctx *c, const std::vector<Op> &ops)
         } else if (op.kind == Op::KD) {
             c->moved_since_bin = true;
             c->forces_valid = false;
+        } else if (op.kind == Op::COND) {
+            c->list_valid = true;   // valid under the displacement criterion
         } else {
             c->forces_valid = op.last;
             if (!op.last) c->moved_since_bin = true;
@@ -426,6 +488,23 @@ int run_span(md_ctx *c, int64_t s0, int64_t first, int64_t last, bool kd, int32_
 {
     const int64_t every = c->p.rebuild_every;
     std::vector<Op> seg;
+    if (c->disp) {
+        // every step: conditional rebuild, then the fused force step; graphs
+        // of up to kDispSeg steps (the same shapes recur and are replayed)
+        constexpr int64_t kDispSeg = 20;
+        if (kd) seg.push_back({Op::KD, first, false, false});
+        for (int64_t nstep = first; nstep <= last; nstep++) {
+            const bool en = energy_every > 0 && ((nstep - s0) % energy_every) == 0;
+            seg.push_back({Op::COND, nstep, false, false});
+            seg.push_back({Op::FORCE, nstep, nstep == last, en});
+            if ((nstep - first + 1) % kDispSeg == 0 || nstep == last) {
+                int rc = run_segment(c, seg);
+                if (rc) return rc;
+                seg.clear();
+            }
+        }
+        return MD_OK;
+    }
     if (kd) seg.push_back({Op::KD, first, false, false});
     for (int64_t nstep = first; nstep <= last; nstep++) {
         const bool rebuild = (nstep % every) == 0;
@@ -679,13 +758,44 @@ int md_run(md_ctx *c, int64_t nsteps, int32_t energy_every, double *energies)
     bool kd = true;
     for (int attempt = 0; attempt < 8; attempt++) {
         std::vector<PlannedRebuild> planned;
+        const int xp0 = c->xp, pb0 = c->pb;
         CK(cudaMemsetAsync(&c->status->rebuild_count, 0, sizeof(int64_t), c->st));
+        CK(cudaMemsetAsync(&c->status->dev_step, 0, sizeof(int64_t), c->st));
         if ((rc = run_span(c, s0, first, last, kd, ev, &planned))) return rc;
         DevStatus s;
         if ((rc = read_status(c, &s))) return rc;
         if ((rc = check_flags(c, s))) return rc;
+        if (c->disp) c->rebuilds += s.rebuild_count;
+        if (c->disp && (s.flags & FLAG_NL_OVERFLOW)) {
+            // The rebuild before the force of step n_fail overflowed and every
+            // kernel after it returned at once: the state is x_n (drifted,
+            // binned, copied back).  Parities at that step follow from the
+            // fused steps done before it.  Grow the list, build, resume there.
+            const int64_t n_fail = first + s.overflow_step - 1;
+            if (s.overflow_step < 1 || n_fail > last)
+                return fail(c, MD_ERR_NL_OVERFLOW, "list overflow at an unknown step");
+            const int64_t done = n_fail - first;
+            c->pb = pb0 ^ (int)(done & 1);
+            c->xp = is_mixed(c) ? xp0 : (xp0 ^ (int)(done & 1));
+            c->moved_since_bin = false;
+            c->list_valid = false;
+            c->forces_valid = false;
+            CK(cudaMemsetAsync(&c->status->flags, 0, sizeof(int32_t), c->st));
+            if ((rc = grow_list(c, s.max_count))) return rc;
+            if ((rc = rebuild_now(c, false))) return rc;
+            if (log) {
+                int64_t before = 0;
+                for (int64_t t = s0 + 1; t < n_fail; t++) before += ((t - s0) % ev) == 0;
+                CK(cudaMemcpyAsync(&c->status->elog_cursor, &before, sizeof(int64_t),
+                                   cudaMemcpyHostToDevice, c->st));
+                CK(cudaStreamSynchronize(c->st));
+            }
+            first = n_fail;
+            kd = false;
+            continue;
+        }
         if (!(s.flags & FLAG_NL_OVERFLOW)) {
-            if (!planned.empty()) c->last_max = s.max_count;
+            if (!planned.empty() || c->disp) c->last_max = s.max_count;
             c->step = last;
             if (log) {
                 CK(cudaMemcpyAsync(energies, c->elog_d, sizeof(double) * 3 * c->nrep * nlog,
@@ -861,32 +971,44 @@ int md_profile(md_ctx *c, int64_t nsteps, md_phase_times *out)
     if (rc) return rc;
     std::memset(out, 0, sizeof(*out));
     const int64_t s0 = c->step, every = c->p.rebuild_every;
-    std::vector<Op> ops;
-    ops.push_back({Op::KD, s0 + 1, false, false});
-    for (int64_t n = s0 + 1; n <= s0 + nsteps; n++) {
-        if (n % every == 0) ops.push_back({Op::REBUILD, n, false, false});
-        ops.push_back({Op::FORCE, n, n == s0 + nsteps, false});
-    }
     // per op: an outer event pair around all of its launches and, for force
-    // ops, an inner pair around the force kernel alone
-    std::vector<cudaEvent_t> ev(4 * ops.size());
-    for (auto &e : ev) CK(cudaEventCreate(&e));
+    // ops, an inner pair around the force kernel alone.  Ops are enqueued one
+    // by one; with the displacement trigger the rebuild decision of each step
+    // is read back from the device first (profiling only).
+    std::vector<Op> ops;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> nls;
     CK(cudaMemsetAsync(&c->status->rebuild_count, 0, sizeof(int64_t), c->st));
-    std::vector<int> nls(ops.size());
-    for (size_t k = 0; k < ops.size(); k++) {
-        int nl = 0;
-        CK(cudaEventRecord(ev[4 * k], c->st));
-        if (ops[k].kind == Op::FORCE) {
-            const int epi = ops[k].last ? EPI_FK : EPI_FKKD;
-            rc = enq_force(c, epi, ops[k].energy, &nl, &ev[4 * k + 2]);
-        } else {
-            rc = enq_op(c, ops[k], &nl);
-        }
-        if (rc) break;
-        CK(cudaEventRecord(ev[4 * k + 1], c->st));
-        nls[k] = nl;
+    auto enqueue = [&](const Op &op) -> int {
+        cudaEvent_t e[4];
+        for (auto &x : e) CK(cudaEventCreate(&x));
+        for (auto &x : e) ev.push_back(x);
+        int nl = 0, r;
+        CK(cudaEventRecord(e[0], c->st));
+        if (op.kind == Op::FORCE) r = enq_force(c, op.last ? EPI_FK : EPI_FKKD, op.energy, &nl, &e[2]);
+        else r = enq_op(c, op, &nl);
+        if (r) return r;
+        CK(cudaEventRecord(e[1], c->st));
+        ops.push_back(op);
+        nls.push_back(nl);
         c->launches += nl;
-        if (ops[k].kind == Op::REBUILD) c->rebuilds++;
+        if (op.kind == Op::REBUILD) c->rebuilds++;
+        return MD_OK;
+    };
+    rc = enqueue({Op::KD, s0 + 1, false, false});
+    for (int64_t n = s0 + 1; !rc && n <= s0 + nsteps; n++) {
+        bool rebuild = false;
+        if (c->disp) {
+            int32_t need = 0;
+            CK(cudaMemcpyAsync(&need, &c->status->need_rebuild, sizeof(int32_t), cudaMemcpyDeviceToHost, c->st));
+            CK(cudaStreamSynchronize(c->st));
+            if (need) CK(cudaMemsetAsync(&c->status->need_rebuild, 0, sizeof(int32_t), c->st));
+            rebuild = need != 0;
+        } else {
+            rebuild = n % every == 0;
+        }
+        if (rebuild && (rc = enqueue({Op::REBUILD, n, false, false}))) break;
+        rc = enqueue({Op::FORCE, n, n == s0 + nsteps, false});
     }
     if (!rc) {
         DevStatus s;
@@ -943,6 +1065,8 @@ int md_adjoint(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt, double *
     if (!c || !loss || nsteps < 1 || window < 1 || window > nsteps || ckpt < 1)
         return fail(c, MD_ERR_INVAL, "bad argument");
     if (c->nrep != 1) return fail(c, MD_ERR_INVAL, "md_adjoint takes a single system");
+    if (c->disp)
+        return fail(c, MD_ERR_INVAL, "md_adjoint needs the fixed rebuild schedule (rebuild_every > 0)");
     const int64_t every = c->p.rebuild_every;
     if (every % ckpt != 0 || nsteps % ckpt != 0)
         return fail(c, MD_ERR_INVAL, "ckpt_every must divide rebuild_every and nsteps");
@@ -1199,13 +1323,20 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
         return fail(c, MD_ERR_INVAL, "null argument or nrep <= 0");
     const md_params &q = *p;
     if (!(q.epsilon > 0) || !(q.sigma > 0) || !(q.mass > 0) || !(q.cutoff > 0) || !(q.skin >= 0) ||
-        !(q.dt > 0) || q.rebuild_every < 1 || (q.precision != MD_FP64 && q.precision != MD_MIXED) ||
+        !(q.dt > 0) || q.rebuild_every < 0 || (q.precision != MD_FP64 && q.precision != MD_MIXED) ||
         (q.half_list != 0 && q.half_list != 1) ||
         !(q.threads_per_atom == 0 || q.threads_per_atom == 1 || q.threads_per_atom == 2 ||
           q.threads_per_atom == 4))
         return fail(c, MD_ERR_INVAL, "invalid md_params");
     c->p = q;
     c->nrep = nrep;
+    c->disp = q.rebuild_every == 0;
+    {
+        // trigger distance just below skin/2 (FP32 displacements are good to ~1e-7)
+        const double h = std::max(0.0, 0.5 * q.skin - 1e-5);
+        c->disp2_thr = std::nextafter((float)(h * h), 0.0f);
+        if (!(c->disp2_thr > 0.f)) c->disp2_thr = 0.f;
+    }
     c->tpa = q.threads_per_atom ? q.threads_per_atom : 1;
     const double rs = q.cutoff + q.skin;
     int64_t n = 0, cells = 0;
@@ -1288,6 +1419,10 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
         CK(cudaMemcpy(c->p32[b] + N, &far32, sizeof(float4), cudaMemcpyHostToDevice));
     }
     if ((rc = dalloc(c, &c->f32, N))) return rc;
+    if (c->disp) {
+        if ((rc = dalloc(c, &c->p32_ref, N))) return rc;
+        CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    }
     if ((rc = dalloc(c, &c->f64, N))) return rc;
     if ((rc = dalloc(c, &c->cell_key, N))) return rc;
     if ((rc = dalloc(c, &c->cell_count, (size_t)cells))) return rc;

@@ -48,6 +48,11 @@ struct DevStatus {
     int64_t rebuild_count;    // binnings run since the host last cleared it
     int64_t overflow_at;      // rebuild_count when a build overflowed
     int64_t elog_cursor;      // next record of the on-device energy log
+    // displacement-triggered rebuilds (md_params.rebuild_every == 0)
+    int64_t dev_step;         // rebuild checks run since the host last cleared it
+    int64_t overflow_step;    // dev_step when a build overflowed
+    int32_t need_rebuild;     // set by any atom that moved more than the trigger distance
+    int32_t pad_;
 };
 
 // One periodic replica.
@@ -87,6 +92,8 @@ struct Dev {
                               // still gather this step's x)
     int32_t *id, *id_alt;     // caller id of each slot
     float4 *p32, *p32_nxt;    // cell-relative FP32 positions; .w = packed cell coords
+    float4 *p32_ref;          // p32 at the last binning (displacement trigger only, else null)
+    float disp2_thr;          // squared trigger distance (FP32, below (skin/2)^2)
     float4 *f32;              // mixed-path forces
     dvec4 *f64;             // FP64-path forces
     int32_t *cell_key;        // global cell of each slot (binning scratch)
@@ -101,6 +108,20 @@ struct Dev {
     const double *ctr;        // cell-centre coordinates (c + 0.5) s: per replica
                               // nc_x, then nc_y, then nc_z values
 };
+
+#ifdef __CUDACC__
+// Displacement trigger: flags a rebuild when atom i's new cell-relative
+// position p lies farther than the trigger distance from its position at the
+// last binning (same cell frame, FP32; error ~1e-7 against a trigger distance
+// set 1e-5 below skin/2).
+__device__ __forceinline__ void check_displacement(const Dev &d, int64_t i, const float4 &p)
+{
+    if (!d.p32_ref) return;
+    const float4 r = d.p32_ref[i];
+    const float dx = p.x - r.x, dy = p.y - r.y, dz = p.z - r.z;
+    if (fmaf(dz, dz, fmaf(dy, dy, dx * dx)) > d.disp2_thr) d.status->need_rebuild = 1;
+}
+#endif
 
 // ---------------------------------------------------------------------------
 // Kernel launchers (defined in the k_*.cu files).
@@ -128,6 +149,12 @@ int launch_scatter_in(const Dev &d, const double *pos_dev, const double *vel_dev
                       cudaStream_t st, int *nlaunch);
 int launch_decode_list(const Dev &d, int32_t *rows_dev, int32_t cap, cudaStream_t st,
                        int *nlaunch);
+// Displacement-triggered rebuilds: move the binned state from the alt
+// buffers into the current ones and record p32 as the reference; and the
+// per-step check that sets a graph conditional to 1 when a rebuild is due.
+int launch_copy_back(const Dev &d, cudaStream_t st, int *nlaunch);
+int launch_rebuild_check(const Dev &d, cudaGraphConditionalHandle h, cudaStream_t st,
+                         int *nlaunch);
 
 int64_t scan_tmp_elems(int64_t ncells_total);
 

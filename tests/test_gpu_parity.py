@@ -488,3 +488,88 @@ def test_device_pointer_api(md, orc):
                 b.close()
     with pytest.raises(TypeError):
         md.MDContext.from_device(pos_t.cpu(), vel_t.cpu(), s.box)
+
+
+# --------------------------------------------------------------------------
+# Displacement-triggered rebuilds (rebuild_every = 0): every list holds all
+# pairs inside rc, so the run equals the oracle run with a fresh list every
+# step (rebuild_every = 1), whatever steps the trigger picks.
+# --------------------------------------------------------------------------
+
+def _mi(d, L):
+    return np.mod(d + L / 2, L) - L / 2
+
+
+@pytest.mark.parametrize("half", [False, True])
+def test_displacement_trigger_fp64(md, orc, half):
+    """FP64 path, the 2,048-atom FCC workload at T = 1.44, 200 steps."""
+    s = inputs.workload("fcc8_2048")
+    x_ref, v_ref, F_ref = orc.vv_run(s.pos, s.vel, s.box, 200, rebuild_every=1)
+    with ctx_of(md, s, precision=md.MD_FP64, half_list=half, rebuild_every=0) as ctx:
+        r0 = ctx.info().rebuilds
+        ctx.run(200)
+        nreb = ctx.info().rebuilds - r0
+        assert np.abs(_mi(ctx.positions() - x_ref, s.box)).max() < 1e-9
+        assert np.abs(ctx.velocities() - v_ref).max() < 1e-8
+        assert fp64_force_ok(ctx.forces(), F_ref) <= 1e-10
+    # the trigger fires well before every 20 steps at this temperature,
+    # but not at every step
+    assert 200 // 20 < nreb < 200
+
+
+def test_displacement_trigger_mixed_and_chunks(md, orc):
+    """Mixed path: the trajectory follows the oracle's fresh-list run to the
+    mixed path's own accuracy; splitting the run changes nothing (the
+    conditional rebuilds live inside the replayed step graphs)."""
+    s = liquid(orc, n_cells=7)
+    x_ref, v_ref, _, E_ref = orc.vv_run(s.pos, s.vel, s.box, 120, rebuild_every=1, energies=True)
+    with ctx_of(md, s, precision=md.MD_MIXED, rebuild_every=0) as a, \
+            ctx_of(md, s, precision=md.MD_MIXED, rebuild_every=0) as b:
+        E = a.run(120, energy_every=40)
+        for k in (13, 40, 27, 40):
+            b.run(k)
+        xa = a.positions()
+        assert np.array_equal(xa, b.positions())
+        assert np.array_equal(a.velocities(), b.velocities())
+        assert np.abs(_mi(xa - x_ref, s.box)).max() < 1e-5
+        for k in range(3):
+            e_ref = E_ref[40 * k + 39, 0] + E_ref[40 * k + 39, 1]
+            assert abs(E[k, 0, 0] + E[k, 0, 1] - e_ref) / s.n < 1e-5
+
+
+def test_displacement_trigger_overflow_and_batch(md, orc):
+    """A list that overflows at a triggered rebuild is grown and the run
+    resumes at that step (same result as an ample list); replicas of a batch
+    follow their own fresh-list oracle runs."""
+    s = inputs.workload("fcc8_2048")          # every row is 78 at the start
+    for precision in (md.MD_FP64, md.MD_MIXED):
+        with ctx_of(md, s, precision=precision, rebuild_every=0) as a, \
+                ctx_of(md, s, precision=precision, rebuild_every=0) as b:
+            b.set_capacity(80)
+            assert b.info().list_capacity == 80
+            a.run(100, energy_every=10)
+            E = b.run(100, energy_every=10)
+            assert b.info().list_capacity > 80
+            assert np.array_equal(a.positions(), b.positions())
+            assert np.array_equal(a.velocities(), b.velocities())
+            assert np.all(np.isfinite(E)) and np.all(E[:, 0, 1] > 0)
+    reps = inputs.replica_ensemble(3, seed=77, n_min=500, n_max=3000)
+    pos = np.concatenate([r.pos for r in reps])
+    vel = np.concatenate([r.vel for r in reps])
+    with md.MDContext(pos, vel, [r.box for r in reps], counts=[r.n for r in reps],
+                      precision=md.MD_FP64, rebuild_every=0) as ctx:
+        ctx.run(60)
+        xg = ctx.positions()
+    o = 0
+    for r in reps:
+        xr, _, _ = orc.vv_run(r.pos, r.vel, r.box, 60, rebuild_every=1)
+        assert np.abs(_mi(xg[o:o + r.n] - xr, r.box)).max() < 1e-9
+        o += r.n
+
+
+def test_displacement_trigger_rejected_by_adjoint(md, orc):
+    s = inputs.fcc_system(4, seed=5)
+    with ctx_of(md, s, precision=md.MD_FP64, rebuild_every=0) as ctx:
+        with pytest.raises(md.MDError) as e:
+            ctx.adjoint(20, 10, 10)
+        assert e.value.code == md.MD_ERR_INVAL

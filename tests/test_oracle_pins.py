@@ -342,6 +342,23 @@ def test_fixed_schedule_can_go_stale(orc, liquid):
     assert stale.sum() < 0.02 * x0.shape[0]
 
 
+def test_displacement_schedule_keeps_lists_exact(orc, liquid):
+    """With rebuild_every=0 (rebuild once an atom has moved more than skin/2
+    since the last build) every list holds all pairs inside rc, so the run
+    is the run with a fresh list at every step (rebuild_every=1), up to the
+    summation order; the fixed 20-step schedule is not (its stale lists miss
+    pairs at this temperature)."""
+    x0, v0, L = liquid
+    n = 100
+    xa, va, Fa = orc.vv_run(x0, v0, L, n, rebuild_every=0)
+    xb, vb, Fb = orc.vv_run(x0, v0, L, n, rebuild_every=1)
+    xc, vc, _ = orc.vv_run(x0, v0, L, n, rebuild_every=20)
+    mi = lambda d: np.mod(d + L / 2, L) - L / 2
+    assert np.abs(mi(xa - xb)).max() < 1e-9 and np.abs(va - vb).max() < 1e-8
+    assert np.abs(Fa - orc.forces_brute(orc.wrap(xa, L), L)).max() < 1e-9
+    assert np.abs(mi(xc - xb)).max() > 1e3 * np.abs(mi(xa - xb)).max()
+
+
 def test_nve_energy(orc):
     """Total energy is conserved while KE and PE exchange; the residual comes
     from pairs crossing the unshifted cutoff, which no dt removes (the
