@@ -51,7 +51,9 @@ class _Params(ctypes.Structure):
     _fields_ = [("epsilon", ctypes.c_double), ("sigma", ctypes.c_double),
                 ("mass", ctypes.c_double), ("cutoff", ctypes.c_double),
                 ("skin", ctypes.c_double), ("dt", ctypes.c_double),
-                ("rebuild_every", ctypes.c_int32), ("half", ctypes.c_int32)]
+                ("rebuild_every", ctypes.c_int32), ("half", ctypes.c_int32),
+                ("potential", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("k_spring", ctypes.c_double), ("gamma", ctypes.c_double)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -82,6 +84,11 @@ def _load():
                 "orc_energy_list": (None, [ctypes.c_int64, _D, _D, ctypes.c_int32, _I32, _I32, P,
                                            _D, _D, _D]),
                 "orc_kinetic": (ctypes.c_double, [ctypes.c_int64, _D, ctypes.c_double]),
+                "orc_forces_sd_list": (None, [ctypes.c_int64, _D, _D, _D, ctypes.c_int32, _I32,
+                                              _I32, P, _D]),
+                "orc_forces_sd_brute": (None, [ctypes.c_int64, _D, _D, _D, P, _D]),
+                "orc_energy_sd_list": (None, [ctypes.c_int64, _D, _D, _D, ctypes.c_int32, _I32,
+                                              _I32, P, _D, _D, _D]),
                 "orc_energy_atoms": (None, [ctypes.c_int64, _D, _D, ctypes.c_int32, _I32, _I32, P,
                                             _D, _D]),
                 "orc_vv_run": (ctypes.c_int, [ctypes.c_int64, _D, P, _D, _D, _D, ctypes.c_int64,
@@ -127,8 +134,9 @@ def _box(L):
 
 
 def params(epsilon=1.0, sigma=1.0, mass=1.0, cutoff=2.5, skin=0.3, dt=0.005,
-           rebuild_every=20, half=False) -> _Params:
-    return _Params(epsilon, sigma, mass, cutoff, skin, dt, int(rebuild_every), int(bool(half)))
+           rebuild_every=20, half=False, potential=0, k_spring=0.0, gamma=0.0) -> _Params:
+    return _Params(epsilon, sigma, mass, cutoff, skin, dt, int(rebuild_every), int(bool(half)),
+                   int(potential), 0, float(k_spring), float(gamma))
 
 
 def num_threads() -> int:
@@ -260,6 +268,47 @@ def forces_sample(x, L, ids, **kw):
                               _ip(start), _ip(atoms), ctypes.byref(p), ids.shape[0],
                               ids.ctypes.data_as(_I64), _dp(F))
     return F
+
+
+def forces_sd_list(x, v, L, rows, **kw):
+    """Spring-dashpot forces (Sec. 3.2 Eq. 3) over a full list; kw must give
+    k_spring, gamma and sigma (the sphere diameter)."""
+    x = _f64(x, (-1, 3))
+    v = _f64(v, (-1, 3))
+    cap, counts, lst = _pack(rows)
+    F = np.zeros_like(x)
+    p = params(potential=1, **kw)
+    _load().orc_forces_sd_list(x.shape[0], _dp(x), _dp(v), _dp(_box(L)), cap, _ip(counts),
+                               _ip(lst), ctypes.byref(p), _dp(F))
+    return F
+
+
+def forces_sd_brute(x, v, L, **kw):
+    """The plain definition of Eq. 3 over every pair (minimum image)."""
+    x = _f64(x, (-1, 3))
+    v = _f64(v, (-1, 3))
+    F = np.zeros_like(x)
+    p = params(potential=1, **kw)
+    _load().orc_forces_sd_brute(x.shape[0], _dp(x), _dp(v), _dp(_box(L)), ctypes.byref(p),
+                                _dp(F))
+    return F
+
+
+def energy_sd_list(x, v, L, rows, per_atom=False, **kw):
+    """(elastic PE, W) of Eq. 3 over a full list; optionally per-atom PE."""
+    x = _f64(x, (-1, 3))
+    v = _f64(v, (-1, 3))
+    cap, counts, lst = _pack(rows)
+    pe = ctypes.c_double()
+    w = ctypes.c_double()
+    pa = np.zeros(x.shape[0], np.float64)
+    p = params(potential=1, **kw)
+    _load().orc_energy_sd_list(x.shape[0], _dp(x), _dp(v), _dp(_box(L)), cap, _ip(counts),
+                               _ip(lst), ctypes.byref(p), ctypes.byref(pe), ctypes.byref(w),
+                               _dp(pa) if per_atom else None)
+    if per_atom:
+        return pe.value, w.value, pa
+    return pe.value, w.value
 
 
 def energy_list(x, L, rows, half=False, per_atom=False, **kw):

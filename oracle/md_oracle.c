@@ -50,6 +50,17 @@
  *     holds every pair inside rc, Sec. 3.2, Fig. 1);
  *   - KE = 1/2 m sum v^2, W = sum over pairs of f*r^2 (= sum r_ij . F_ij).
  *
+ * Spring-dashpot contact (Sec. 3.2, Eq. 3; potential = 1): spheres of
+ * diameter sigma, for |x_ij| < sigma (strict)
+ *     F_i += K xi + gamma xi_dot,   xi = xhat (sigma - r),
+ *     xi_dot = -xhat (xhat . v_ij),  xhat = x_ij / r,  r = |x_ij|,
+ * with x_ij = x_i - x_j (minimum image) and v_ij = v_i - v_j.  Readings:
+ * v_ij is the relative velocity of i to j; in velocity Verlet the force
+ * after the drift uses the half-step velocities (the latest ones), i.e. the
+ * integrator stays explicit; the elastic energy is 1/2 K (sigma - r)^2 per
+ * overlapping pair; W = sum over pairs of x_ij . F_ij (dashpot included).
+ * The list radius is cutoff + skin, so cutoff >= sigma.
+ *
  * Parity unpinned: none of the functions here.  Each is pinned by a test
  * against closed forms, textbook lattice sums, brute force, conservation
  * laws or finite differences (tests/test_oracle_*.py).
@@ -68,6 +79,9 @@ typedef struct {
     double epsilon, sigma, mass, cutoff, skin, dt;
     int32_t rebuild_every;
     int32_t half;
+    int32_t potential;      /* 0: Lennard-Jones (Eq. 2); 1: spring-dashpot (Eq. 3) */
+    int32_t pad_;
+    double k_spring, gamma; /* Eq. 3: K and the dissipation constant; sigma is the diameter */
 } orc_params;
 
 int orc_num_threads(void)
@@ -444,6 +458,93 @@ void orc_energy_atoms(int64_t n, const double *x, const double L[3], int32_t cap
         }
 }
 
+/* Eq. 3 for one pair: adds the force on i to fi, returns 1 if in contact
+ * (and then the pair's elastic energy and x_ij . F_ij through pe, w). */
+static int sd_pair(const double del[3], const double vij[3], const orc_params *p, double fi[3],
+                   double *pe, double *w)
+{
+    double rsq = norm2(del);
+    if (!(rsq < p->sigma * p->sigma)) return 0;
+    double r = sqrt(rsq);
+    double xhat[3] = {del[0] / r, del[1] / r, del[2] / r};
+    double vn = xhat[0] * vij[0] + xhat[1] * vij[1] + xhat[2] * vij[2];
+    double overlap = p->sigma - r;
+    double f[3];
+    for (int d = 0; d < 3; d++) {
+        double xi = xhat[d] * overlap;
+        double xi_dot = -xhat[d] * vn;
+        f[d] = p->k_spring * xi + p->gamma * xi_dot;
+        fi[d] += f[d];
+    }
+    *pe = 0.5 * p->k_spring * overlap * overlap;
+    *w = del[0] * f[0] + del[1] * f[1] + del[2] * f[2];
+    return 1;
+}
+
+/* Spring-dashpot forces over a full list (each row holds every j within
+ * the list radius of i). */
+void orc_forces_sd_list(int64_t n, const double *x, const double *v, const double L[3],
+                        int32_t cap, const int32_t *counts, const int32_t *list,
+                        const orc_params *p, double *F)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; i++) {
+        double fi[3] = {0.0, 0.0, 0.0};
+        for (int32_t k = 0; k < counts[i]; k++) {
+            int64_t j = list[i * cap + k];
+            double del[3], vij[3], pe, w;
+            displacement(x, i, j, L, del);
+            for (int d = 0; d < 3; d++) vij[d] = v[3 * i + d] - v[3 * j + d];
+            sd_pair(del, vij, p, fi, &pe, &w);
+        }
+        for (int d = 0; d < 3; d++) F[3 * i + d] = fi[d];
+    }
+}
+
+/* The plain definition of Eq. 3: every j != i (minimum image). */
+void orc_forces_sd_brute(int64_t n, const double *x, const double *v, const double L[3],
+                         const orc_params *p, double *F)
+{
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; i++) {
+        double fi[3] = {0.0, 0.0, 0.0};
+        for (int64_t j = 0; j < n; j++) {
+            if (j == i) continue;
+            double del[3], vij[3], pe, w;
+            displacement(x, i, j, L, del);
+            for (int d = 0; d < 3; d++) vij[d] = v[3 * i + d] - v[3 * j + d];
+            sd_pair(del, vij, p, fi, &pe, &w);
+        }
+        for (int d = 0; d < 3; d++) F[3 * i + d] = fi[d];
+    }
+}
+
+/* Elastic energy and virial over a full list (each pair counted from both
+ * sides, halved); per-atom values (half of each pair) when pe_atom != NULL. */
+void orc_energy_sd_list(int64_t n, const double *x, const double *v, const double L[3],
+                        int32_t cap, const int32_t *counts, const int32_t *list,
+                        const orc_params *p, double *pe_out, double *w_out, double *pe_atom)
+{
+    double pe_t = 0.0, w_t = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+        double pi = 0.0;
+        for (int32_t k = 0; k < counts[i]; k++) {
+            int64_t j = list[i * cap + k];
+            double del[3], vij[3], pe, w, fi[3] = {0.0, 0.0, 0.0};
+            displacement(x, i, j, L, del);
+            for (int d = 0; d < 3; d++) vij[d] = v[3 * i + d] - v[3 * j + d];
+            if (sd_pair(del, vij, p, fi, &pe, &w)) {
+                pi += 0.5 * pe;
+                w_t += 0.5 * w;
+            }
+        }
+        pe_t += pi;
+        if (pe_atom) pe_atom[i] = pi;
+    }
+    *pe_out = pe_t;
+    *w_out = w_t;
+}
+
 double orc_kinetic(int64_t n, const double *v, double mass)
 {
     double s = 0.0;
@@ -528,7 +629,9 @@ int orc_vv_run(int64_t n, const double L[3], const orc_params *p, double *x, dou
         if (!xref) { sim_free(&S); return -2; }
         memcpy(xref, x, sizeof(double) * 3 * (size_t)n);
     }
-    orc_forces_list(n, x, S.L, S.cap, S.counts, S.list, p, F);
+    const int sd = p->potential == 1;
+    if (sd) orc_forces_sd_list(n, x, v, S.L, S.cap, S.counts, S.list, p, F);
+    else orc_forces_list(n, x, S.L, S.cap, S.counts, S.list, p, F);
     double half_dt_m = 0.5 * p->dt / p->mass;
     for (int64_t q = 1; q <= nsteps; q++) {
         int64_t step = step0 + q;
@@ -555,11 +658,14 @@ int orc_vv_run(int64_t n, const double L[3], const orc_params *p, double *x, dou
             if ((rc = sim_rebuild(&S, x))) { sim_free(&S); free(xref); return rc; }
             if (xref) memcpy(xref, x, sizeof(double) * 3 * (size_t)n);
         }
-        orc_forces_list(n, x, S.L, S.cap, S.counts, S.list, p, F);
+        /* Eq. 3's dashpot reads the half-step velocities held in v here */
+        if (sd) orc_forces_sd_list(n, x, v, S.L, S.cap, S.counts, S.list, p, F);
+        else orc_forces_list(n, x, S.L, S.cap, S.counts, S.list, p, F);
         for (int64_t t = 0; t < 3 * n; t++) v[t] += half_dt_m * F[t];
         if (energies) {
             double pe, w;
-            orc_energy_list(n, x, S.L, S.cap, S.counts, S.list, p, &pe, &w, NULL);
+            if (sd) orc_energy_sd_list(n, x, v, S.L, S.cap, S.counts, S.list, p, &pe, &w, NULL);
+            else orc_energy_list(n, x, S.L, S.cap, S.counts, S.list, p, &pe, &w, NULL);
             energies[3 * (q - 1) + 0] = pe;
             energies[3 * (q - 1) + 1] = orc_kinetic(n, v, p->mass);
             energies[3 * (q - 1) + 2] = w;

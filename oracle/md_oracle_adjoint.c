@@ -45,6 +45,9 @@ typedef struct {
     double epsilon, sigma, mass, cutoff, skin, dt;
     int32_t rebuild_every;
     int32_t half;
+    int32_t potential;      /* the adjoint covers Lennard-Jones (potential 0) only */
+    int32_t pad_;
+    double k_spring, gamma;
 } orc_params;
 
 /* From md_oracle.c */
