@@ -236,8 +236,23 @@ int md_set_capacity(md_ctx *ctx, int32_t cap);
  * and reports the device time per phase.  Synchronises. */
 int md_profile(md_ctx *ctx, int64_t nsteps, md_phase_times *out);
 
-/* Changes epsilon and sigma (both > 0); forces are recomputed on next use. */
+/* Changes epsilon and sigma (both > 0) and selects the Lennard-Jones force
+ * (the default); forces are recomputed on next use. */
 int md_set_lj(md_ctx *ctx, double epsilon, double sigma);
+
+/* Switches the context to the spring-dashpot contact model of Sec. 3.2,
+ * Eq. 3 (a second pair force on the same cells and lists): spheres of
+ * diameter params.sigma touch when r = |x_ij| < sigma and then
+ *     F_i += K xi + gamma xi_dot,  xi = xhat (sigma - r),
+ *     xi_dot = -xhat (xhat . v_ij),  x_ij = x_i - x_j,  v_ij = v_i - v_j.
+ * The force after a drift reads the half-step velocities (the latest).  PE
+ * reported by md_energy is the elastic 1/2 K (sigma - r)^2 per contact, W the
+ * sum of x_ij . F_ij.  Full lists are used (a half-list context switches and
+ * rebuilds); md_set_lj switches back to Lennard-Jones.  K = gamma = 0 is the
+ * paper's static setting (no force).
+ * Errors: MD_ERR_INVAL (negative or non-finite K or gamma, cutoff < sigma),
+ * MD_ERR_CUDA. */
+int md_set_spring_dashpot(md_ctx *ctx, double k_spring, double gamma);
 
 /* Differentiable rollout (not in the paper; it differentiates the Sec. 3.2
  * Eq. 1 / Eq. 2 forward map).  From the current state (x0, v0) of a
@@ -251,7 +266,7 @@ int md_set_lj(md_ctx *ctx, double epsilon, double sigma);
  * before it is reversed.  g_x0 / g_v0: host, n x 3 doubles in caller order
  * (each may be NULL).  The context is left at (x0, v0).  Work memory is
  * allocated for the call and freed before it returns.
- * Errors: MD_ERR_INVAL (nrep != 1; rebuild_every == 0; window not in
+ * Errors: MD_ERR_INVAL (nrep != 1; rebuild_every == 0; spring-dashpot model; window not in
  * [1, nsteps]; ckpt_every not dividing both rebuild_every and nsteps),
  * MD_ERR_NOMEM, MD_ERR_CUDA and those of md_run. */
 int md_adjoint(md_ctx *ctx, int64_t nsteps, int64_t window, int32_t ckpt_every, double *loss,

@@ -1,0 +1,169 @@
+// Spring-dashpot contact forces (tinyMD Sec. 3.2, Eq. 3) over the same cell
+// binning and Verlet list as the Lennard-Jones path.  Spheres of diameter
+// sigma touch when r = |x_ij| < sigma (strict); then
+//     F_i += K xi + gamma xi_dot,  xi = xhat (sigma - r),
+//     xi_dot = -xhat (xhat . v_ij),  xhat = x_ij / r,
+// i.e. F_i += x_ij [K (sigma - r) - gamma (x_ij . v_ij) / r] / r, with
+// x_ij = x_i - x_j (minimum image) and v_ij = v_i - v_j.  The list radius
+// is cutoff + skin with cutoff >= sigma.
+//
+// GPU mapping: one thread per atom over its full-list row (neighbour-major
+// int4 chunks), like the LJ kernels.  Unlike them the pair term reads the
+// neighbour's velocity, so the step is not fused: this kernel stores the
+// force and the velocity-Verlet update runs in its own kernel afterwards
+// (the velocities the dashpot reads are then those of the half step, the
+// latest ones, as in the oracle).  Mixed path: displacements from the
+// cell-relative FP32 positions plus the stencil offset (as the LJ mixed
+// kernel), v_ij rounded to FP32 from the FP64 difference, FP32 pair
+// arithmetic with compensated per-atom sums.  FP64 path: FP64 throughout.
+#include "md_internal.cuh"
+
+namespace mdk {
+
+namespace {
+
+__device__ __forceinline__ bool stopped(const DevStatus *st)
+{
+    return *((volatile const int32_t *)&st->flags) != 0;
+}
+
+__device__ __forceinline__ void kahan(float &s, float &c, float term)
+{
+    const float y = term - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+template <bool BATCHED, bool ENERGY>
+__global__ void __launch_bounds__(256) k_force_sd_mixed(Dev d, LJ lj)
+{
+    if (stopped(d.status)) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.n) return;
+    const int64_t n = d.n;
+    const Rep &R = d.reps[BATCHED ? d.rep_of[i] : 0];
+    const float4 pi = d.p32[i];
+    const dvec4 vi = d.v[i];
+    const int cnt = d.nb_count[i];
+    const int nq = (cnt + 3) >> 2;
+    const int4 *nb4 = reinterpret_cast<const int4 *>(d.nb);
+    float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
+    float pe = 0.f, w = 0.f, cpe = 0.f, cw = 0.f;
+    for (int q = 0; q < nq; q++) {
+        const int4 e4 = __ldcs(nb4 + (int64_t)q * n + i);
+        const uint32_t es[4] = {(uint32_t)e4.x, (uint32_t)e4.y, (uint32_t)e4.z, (uint32_t)e4.w};
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            const uint32_t e = es[t];
+            const int32_t j = (int32_t)(e & kJMask);
+            const uint32_t c = e >> kJBits;
+            const float4 pj = __ldg(d.p32 + j);
+            // d = (p_i - o s) - p_j, o = code - 1 per dimension, nsf = -s
+            const float dx = fmaf((float)((int)(c & 3u) - 1), R.nsf[0], pi.x) - pj.x;
+            const float dy = fmaf((float)((int)((c >> 2) & 3u) - 1), R.nsf[1], pi.y) - pj.y;
+            const float dz = fmaf((float)((int)(c >> 4) - 1), R.nsf[2], pi.z) - pj.z;
+            const float rsq = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            if (!(rsq < lj.sd_sig2f)) continue;            // padding is far away
+            const dvec4 vj = ldg_dvec4(d.v + j);
+            const float vx = (float)(vi.x - vj.x), vy = (float)(vi.y - vj.y), vz = (float)(vi.z - vj.z);
+            const float r = sqrtf(rsq);
+            const float vn = fmaf(dz, vz, fmaf(dy, vy, dx * vx)) / r;
+            const float ov = lj.sigmaf - r;
+            const float fo = (lj.sd_kf * ov - lj.sd_gf * vn) / r;
+            kahan(sx, cx, fo * dx);
+            kahan(sy, cy, fo * dy);
+            kahan(sz, cz, fo * dz);
+            if (ENERGY) {
+                kahan(pe, cpe, 0.5f * lj.sd_kf * ov * ov);
+                kahan(w, cw, fo * rsq);
+            }
+        }
+    }
+    d.f32[i] = make_float4(sx - cx, sy - cy, sz - cz, 0.f);
+    if (ENERGY) {
+        d.pe_atom[i] = 0.5f * (pe - cpe);
+        d.w_atom[i] = 0.5f * (w - cw);
+    }
+}
+
+template <bool BATCHED, bool ENERGY>
+__global__ void __launch_bounds__(256) k_force_sd_f64(Dev d, LJ lj)
+{
+    if (stopped(d.status)) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.n) return;
+    const int64_t n = d.n;
+    const Rep &R = d.reps[BATCHED ? d.rep_of[i] : 0];
+    const dvec4 xi = d.x[i];
+    const dvec4 vi = d.v[i];
+    const uint32_t pack = __float_as_uint(d.p32[i].w);
+    const int ci[3] = {(int)(pack & 1023u), (int)((pack >> 10) & 1023u), (int)((pack >> 20) & 1023u)};
+    const int cnt = d.nb_count[i];
+    const int nq = (cnt + 3) >> 2;
+    const int4 *nb4 = reinterpret_cast<const int4 *>(d.nb);
+    double fx = 0, fy = 0, fz = 0, pe = 0, w = 0;
+    for (int q = 0; q < nq; q++) {
+        const int4 e4 = __ldcs(nb4 + (int64_t)q * n + i);
+        const uint32_t es[4] = {(uint32_t)e4.x, (uint32_t)e4.y, (uint32_t)e4.z, (uint32_t)e4.w};
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            const uint32_t e = es[t];
+            const int32_t j = (int32_t)(e & kJMask);
+            const uint32_t c = e >> kJBits;
+            const dvec4 xj = ldg_dvec4(d.x + j);
+            double dd[3] = {xi.x - xj.x, xi.y - xj.y, xi.z - xj.z};
+            // periodic image: a neighbour cell across the box face sits one
+            // box length away (same rule as the list criterion)
+            const int o[3] = {(int)(c & 3u) - 1, (int)((c >> 2) & 3u) - 1, (int)(c >> 4) - 1};
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                if (o[k] < 0 && ci[k] == 0) dd[k] += R.L[k];
+                else if (o[k] > 0 && ci[k] == R.nc[k] - 1) dd[k] -= R.L[k];
+            }
+            const double rsq = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
+            if (!(rsq < lj.sd_sig2)) continue;
+            const dvec4 vj = ldg_dvec4(d.v + j);
+            const double r = sqrt(rsq);
+            const double vn = (dd[0] * (vi.x - vj.x) + dd[1] * (vi.y - vj.y) + dd[2] * (vi.z - vj.z)) / r;
+            const double ov = lj.sigma - r;
+            const double fo = (lj.sd_k * ov - lj.sd_g * vn) / r;
+            fx = fma(fo, dd[0], fx);
+            fy = fma(fo, dd[1], fy);
+            fz = fma(fo, dd[2], fz);
+            if (ENERGY) {
+                pe += 0.5 * lj.sd_k * ov * ov;
+                w = fma(fo, rsq, w);
+            }
+        }
+    }
+    d.f64[i] = mk_dvec4(fx, fy, fz, 0.0);
+    if (ENERGY) {
+        d.pe_atom64[i] = 0.5 * pe;
+        d.w_atom64[i] = 0.5 * w;
+    }
+}
+
+}  // namespace
+
+int launch_force_sd(const Dev &d, const LJ &lj, bool mixed, bool energy, cudaStream_t st, int *nl)
+{
+    if (d.n <= 0) return 0;
+    const unsigned g = (unsigned)((d.n + 255) / 256);
+    const bool b = d.nrep > 1;
+    if (mixed) {
+        if (b && energy) k_force_sd_mixed<true, true><<<g, 256, 0, st>>>(d, lj);
+        else if (b) k_force_sd_mixed<true, false><<<g, 256, 0, st>>>(d, lj);
+        else if (energy) k_force_sd_mixed<false, true><<<g, 256, 0, st>>>(d, lj);
+        else k_force_sd_mixed<false, false><<<g, 256, 0, st>>>(d, lj);
+    } else {
+        if (b && energy) k_force_sd_f64<true, true><<<g, 256, 0, st>>>(d, lj);
+        else if (b) k_force_sd_f64<true, false><<<g, 256, 0, st>>>(d, lj);
+        else if (energy) k_force_sd_f64<false, true><<<g, 256, 0, st>>>(d, lj);
+        else k_force_sd_f64<false, false><<<g, 256, 0, st>>>(d, lj);
+    }
+    *nl += 1;
+    return (int)cudaGetLastError();
+}
+
+}  // namespace mdk

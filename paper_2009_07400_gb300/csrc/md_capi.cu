@@ -182,6 +182,7 @@ void free_all(md_ctx *c)
 
 bool is_mixed(const md_ctx *c) { return c->p.precision == MD_MIXED; }
 bool is_half(const md_ctx *c) { return c->p.half_list != 0; }
+bool is_sd(const md_ctx *c) { return c->lj.pot == 1; }
 bool batched(const md_ctx *c) { return c->nrep > 1; }
 
 int32_t round4(int64_t v) { return (int32_t)((v + 3) / 4 * 4); }
@@ -246,12 +247,19 @@ int enq_energy(md_ctx *c, bool ke_from_v, double *out3, int *nl)
 int enq_force(md_ctx *c, int epi, bool energy, int *nl, cudaEvent_t *ev = nullptr)
 {
     Dev d = view(c);
-    if (is_half(c)) {
-        if (is_mixed(c)) CK(cudaMemsetAsync(c->f32, 0, sizeof(float4) * c->n, c->st));
-        else CK(cudaMemsetAsync(c->f64, 0, sizeof(dvec4) * c->n, c->st));
+    if (is_half(c) || is_sd(c)) {
+        // force store, then the velocity-Verlet update in its own kernel
         if (ev) CK(cudaEventRecord(ev[0], c->st));
-        if (launch_force(d, c->lj, c->p.precision, true, 1, EPI_F, energy, batched(c), c->st, nl))
-            return fail(c, MD_ERR_CUDA, "force launch failed");
+        if (is_sd(c)) {
+            if (launch_force_sd(d, c->lj, is_mixed(c), energy, c->st, nl))
+                return fail(c, MD_ERR_CUDA, "force launch failed");
+        } else {
+            if (is_mixed(c)) CK(cudaMemsetAsync(c->f32, 0, sizeof(float4) * c->n, c->st));
+            else CK(cudaMemsetAsync(c->f64, 0, sizeof(dvec4) * c->n, c->st));
+            if (ev) CK(cudaEventRecord(ev[0], c->st));
+            if (launch_force(d, c->lj, c->p.precision, true, 1, EPI_F, energy, batched(c), c->st, nl))
+                return fail(c, MD_ERR_CUDA, "force launch failed");
+        }
         if (ev) CK(cudaEventRecord(ev[1], c->st));
         if (epi == EPI_FK) {
             if (launch_integrate(d, c->lj, c->p.precision, 2, batched(c), c->st, nl))
@@ -556,6 +564,12 @@ void set_lj_constants(md_ctx *c)
     lj.mass = q.mass;
     lj.rs2f_lo = (float)(lj.rs2 * (1.0 - 2.5e-4));
     lj.rs2f_hi = (float)(lj.rs2 * (1.0 + 2.5e-4));
+    // spring-dashpot constants (pot, sd_k, sd_g are set by md_set_spring_dashpot)
+    lj.sigmaf = (float)q.sigma;
+    lj.sd_sig2 = q.sigma * q.sigma;
+    lj.sd_sig2f = (float)lj.sd_sig2;
+    lj.sd_kf = (float)lj.sd_k;
+    lj.sd_gf = (float)lj.sd_g;
 }
 
 // Process-wide autotuner cache: (precision, log2 atoms per replica, batched)
@@ -1052,6 +1066,26 @@ int md_set_lj(md_ctx *c, double epsilon, double sigma)
     CK(cudaStreamSynchronize(c->st));
     c->p.epsilon = epsilon;
     c->p.sigma = sigma;
+    c->lj.pot = 0;
+    set_lj_constants(c);
+    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+    c->graphs.clear();
+    c->forces_valid = false;
+    return MD_OK;
+}
+
+int md_set_spring_dashpot(md_ctx *c, double k_spring, double gamma)
+{
+    if (!c || !(k_spring >= 0) || !(gamma >= 0) || !std::isfinite(k_spring) || !std::isfinite(gamma))
+        return fail(c, MD_ERR_INVAL, "bad argument");
+    if (!(c->p.cutoff >= c->p.sigma))
+        return fail(c, MD_ERR_INVAL, "cutoff must be >= sigma (the sphere diameter) so lists hold every contact");
+    CK(cudaStreamSynchronize(c->st));
+    int rc = MD_OK;
+    if (is_half(c) && (rc = apply_tuning(c, 1, 0))) return rc;   // contacts use full lists
+    c->lj.pot = 1;
+    c->lj.sd_k = k_spring;
+    c->lj.sd_g = gamma;
     set_lj_constants(c);
     for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
     c->graphs.clear();
@@ -1067,6 +1101,7 @@ int md_adjoint(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt, double *
     if (c->nrep != 1) return fail(c, MD_ERR_INVAL, "md_adjoint takes a single system");
     if (c->disp)
         return fail(c, MD_ERR_INVAL, "md_adjoint needs the fixed rebuild schedule (rebuild_every > 0)");
+    if (is_sd(c)) return fail(c, MD_ERR_INVAL, "md_adjoint differentiates the Lennard-Jones force only");
     const int64_t every = c->p.rebuild_every;
     if (every % ckpt != 0 || nsteps % ckpt != 0)
         return fail(c, MD_ERR_INVAL, "ckpt_every must divide rebuild_every and nsteps");
@@ -1223,6 +1258,10 @@ int md_adjoint(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt, double *
 int md_autotune(md_ctx *c, int32_t steps, md_params *chosen)
 {
     if (!c || steps < 1) return fail(c, MD_ERR_INVAL, "bad argument");
+    if (is_sd(c)) {   // one contact kernel: nothing to choose
+        if (chosen) { *chosen = c->p; chosen->threads_per_atom = c->tpa; }
+        return MD_OK;
+    }
     const int64_t per_rep = c->n / c->nrep;
     int bucket = 0;
     while (((int64_t)1 << (bucket + 1)) <= per_rep) bucket++;

@@ -76,6 +76,10 @@ struct LJ {
     double dt;
     double mass;
     float rs2f_lo, rs2f_hi;   // FP32 prefilter band around rs^2 (exact FP64 test inside)
+    // spring-dashpot contact (Eq. 3; pot == 1): K, gamma, sigma^2 (sigma = diameter)
+    int32_t pot;
+    double sd_k, sd_g, sd_sig2;
+    float sd_kf, sd_gf, sd_sig2f, sigmaf;
 };
 
 // Device pointers of one context (passed by value to kernels).
@@ -136,6 +140,9 @@ int launch_force(const Dev &d, const LJ &lj, int precision, bool half, int tpa, 
                  bool energy, bool batched, cudaStream_t st, int *nlaunch);
 int launch_integrate(const Dev &d, const LJ &lj, int precision, int phase, bool batched,
                      cudaStream_t st, int *nlaunch);
+// Spring-dashpot forces (full list; force store only, no fused integration).
+int launch_force_sd(const Dev &d, const LJ &lj, bool mixed, bool energy, cudaStream_t st,
+                    int *nlaunch);
 // out3 != NULL: write (PE, KE, W) per replica there; otherwise append one
 // record to log_base at status->elog_cursor and advance the cursor.
 int launch_energy(const Dev &d, const LJ &lj, int precision, bool ke_from_v,

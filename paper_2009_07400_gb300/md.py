@@ -33,7 +33,7 @@ ABI_SYMBOLS = [
     "md_get_neighbors", "md_get_info", "md_autotune", "md_set_capacity", "md_profile",
     "md_set_lj", "md_adjoint", "md_energy_sums_static", "md_create_device",
     "md_set_state_device", "md_get_positions_device", "md_get_velocities_device",
-    "md_get_forces_device",
+    "md_get_forces_device", "md_set_spring_dashpot",
 ]
 
 
@@ -123,6 +123,7 @@ def load(path: str | None = None):
                 "md_get_positions_device": [ctx, _P],
                 "md_get_velocities_device": [ctx, _P],
                 "md_get_forces_device": [ctx, _P],
+                "md_set_spring_dashpot": [ctx, ctypes.c_double, ctypes.c_double],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -373,6 +374,10 @@ class MDContext:
 
     def set_lj(self, epsilon, sigma):
         self._check(self._lib.md_set_lj(self._h, float(epsilon), float(sigma)))
+
+    def set_spring_dashpot(self, k_spring, gamma):
+        """Contact model of Eq. 3 (spheres of diameter params.sigma)."""
+        self._check(self._lib.md_set_spring_dashpot(self._h, float(k_spring), float(gamma)))
 
     def adjoint(self, nsteps, window, ckpt_every=10):
         """(loss, dL/deps, dL/dsigma, dL/dx0 (n x 3), dL/dv0 (n x 3))."""

@@ -1,0 +1,127 @@
+"""Spring-dashpot contact model (Sec. 3.2, Eq. 3) on the GPU against the
+oracle: forces and energies on the same state, trajectories, and the
+closed-form restitution of a two-sphere collision."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+SIG, SKIN = 1.0, 0.3
+
+
+@pytest.fixture(scope="module")
+def md():
+    from paper_2009_07400_gb300 import build
+    build.build()
+    from paper_2009_07400_gb300 import md as m
+    m.load()
+    return m
+
+
+def dense(seed=3, n=600, L=(8.0, 8.5, 9.0)):
+    """Overlapping spheres (packing fraction ~0.75) with random velocities."""
+    rng = np.random.default_rng(seed)
+    L = np.array(L)
+    return rng.uniform(0, 1, (n, 3)) * L, rng.normal(size=(n, 3)), L
+
+
+def sd_ctx(md, x, v, L, k, g, **kw):
+    ctx = md.MDContext(x, v, L, sigma=SIG, cutoff=SIG, skin=SKIN, **kw)
+    ctx.set_spring_dashpot(k, g)
+    return ctx
+
+
+def rel_rms(F, Fr):
+    return np.sqrt(np.sum((F - Fr) ** 2) / np.sum(Fr ** 2))
+
+
+@pytest.mark.parametrize("half", [False, True])
+def test_forces_and_energy(md, orc, half):
+    x, v, L = dense()
+    xw = orc.wrap(x, L)
+    rows = orc.neighbors_cells(xw, L, SIG + SKIN)
+    ok = dict(k_spring=500.0, gamma=3.0, sigma=SIG)
+    Fr = orc.forces_sd_list(xw, v, L, rows, **ok)
+    pe_r, w_r = orc.energy_sd_list(xw, v, L, rows, **ok)
+    for precision, tol in ((md.MD_FP64, 1e-12), (md.MD_MIXED, 1e-5)):
+        with sd_ctx(md, x, v, L, 500.0, 3.0, precision=precision, half_list=half) as ctx:
+            assert ctx.info().half_list == 0        # contacts use full lists
+            F = ctx.forces()
+            assert rel_rms(F, Fr) < tol
+            pe, ke, w = (q[0] for q in ctx.energy())
+            assert pe == pytest.approx(pe_r, rel=max(tol, 1e-12))
+            assert w == pytest.approx(w_r, rel=max(10 * tol, 1e-11))
+            assert ke == pytest.approx(0.5 * np.sum(v ** 2), rel=1e-13)
+    # K = gamma = 0: no force at all (the paper's static setting)
+    with sd_ctx(md, x, v, L, 0.0, 0.0, precision=md.MD_FP64) as ctx:
+        assert np.all(ctx.forces() == 0.0)
+
+
+@pytest.mark.parametrize("every", [20, 0])
+def test_trajectory_fp64(md, orc, every):
+    """300 steps of a dissipative dense gas: FP64 path against the oracle's
+    velocity Verlet (dashpot on the half-step velocities)."""
+    x, v, L = dense(seed=9, n=400)
+    kw = dict(k_spring=200.0, gamma=2.0, sigma=SIG, cutoff=SIG, skin=SKIN, dt=0.001)
+    xr, vr, Fr, Er = orc.vv_run(x, v, L, 300, energies=True, potential=1,
+                                rebuild_every=every if every else 0, **kw)
+    with sd_ctx(md, x, v, L, 200.0, 2.0, precision=md.MD_FP64, dt=0.001, rebuild_every=every) as ctx:
+        E = ctx.run(300, energy_every=100)
+        d = np.mod(ctx.positions() - xr + L / 2, L) - L / 2
+        assert np.abs(d).max() < 1e-9
+        assert np.abs(ctx.velocities() - vr).max() < 1e-8
+    for k in range(3):
+        et = E[k, 0, 0] + E[k, 0, 1]
+        er = Er[100 * k + 99, 0] + Er[100 * k + 99, 1]
+        assert et == pytest.approx(er, rel=1e-10)
+    assert E[2, 0, 0] + E[2, 0, 1] < 0.8 * (E[0, 0, 0] + E[0, 0, 1])   # the gas cools
+
+
+def test_trajectory_mixed(md, orc):
+    x, v, L = dense(seed=9, n=400)
+    kw = dict(k_spring=200.0, gamma=2.0, sigma=SIG, cutoff=SIG, skin=SKIN, dt=0.001)
+    xr, vr, _, Er = orc.vv_run(x, v, L, 200, energies=True, potential=1, **kw)
+    with sd_ctx(md, x, v, L, 200.0, 2.0, precision=md.MD_MIXED, dt=0.001) as ctx:
+        E = ctx.run(200, energy_every=200)
+        d = np.mod(ctx.positions() - xr + L / 2, L) - L / 2
+        assert np.abs(d).max() < 1e-4
+    et = E[0, 0, 0] + E[0, 0, 1]
+    er = Er[199, 0] + Er[199, 1]
+    assert abs(et - er) / abs(er) < 1e-4
+
+
+def test_restitution_on_gpu(md):
+    """Two spheres meeting head-on leave with e = exp(-zeta pi/sqrt(1-zeta^2))
+    times the approach speed (damped oscillator of the overlap, mu = m/2)."""
+    k, g, u, dt = 1000.0, 5.0, 1.0, 1e-5
+    mu = 0.5
+    zeta = g / (2.0 * math.sqrt(mu * k))
+    e = math.exp(-zeta * math.pi / math.sqrt(1.0 - zeta ** 2))
+    wd = math.sqrt(k / mu) * math.sqrt(1.0 - zeta ** 2)
+    L = np.array([20.0, 20.0, 20.0])
+    x = np.array([[10.0, 10.0, 10.0], [10.0 + SIG + 0.25 * u * dt, 10.0, 10.0]])
+    v = np.array([[0.5 * u, 0.0, 0.0], [-0.5 * u, 0.0, 0.0]])
+    steps = int(1.5 * math.pi / wd / dt)
+    with sd_ctx(md, x, v, L, k, g, precision=md.MD_FP64, dt=dt) as ctx:
+        ctx.run(steps)
+        vn = ctx.velocities()
+    assert abs((vn[1, 0] - vn[0, 0]) / u - e) < 1e-4
+    assert abs(vn[:, 0].sum()) < 1e-12
+
+
+def test_contact_model_argument_checks(md):
+    x, v, L = dense(n=50)
+    with md.MDContext(x, v, L, sigma=SIG, cutoff=0.9, skin=SKIN) as ctx:
+        with pytest.raises(md.MDError) as e:
+            ctx.set_spring_dashpot(10.0, 1.0)                 # cutoff < sigma
+        assert e.value.code == md.MD_ERR_INVAL
+    with sd_ctx(md, x, v, L, 10.0, 1.0) as ctx:
+        with pytest.raises(md.MDError):
+            ctx.set_spring_dashpot(-1.0, 0.0)
+        with pytest.raises(md.MDError) as e:
+            ctx.adjoint(20, 10, 10)
+        assert e.value.code == md.MD_ERR_INVAL
+        ctx.set_lj(1.0, 1.0)                                  # back to Lennard-Jones
+        ctx.forces()
