@@ -38,7 +38,11 @@ WORKLOADS = {
     "fcc128": "fcc128_8388608",    # sizing run
     "ensemble": "ensemble256",     # 256 independent replicas, one context
     "fcc80": "fcc80_2048000",      # the paper's single-GPU shape; FP64 leg: full list, 1 lane/atom
+    "dem": "dem64_1048576",        # spring-dashpot contacts (Eq. 3), 1,048,576 spheres
 }
+# the contact model's parameters for the dem workload (sigma = sphere diameter)
+DEM_PARAMS = dict(sigma=1.0, cutoff=1.0, skin=0.3, dt=0.001)
+DEM_K, DEM_GAMMA = 1000.0, 5.0
 METRIC = "atom-timesteps/s, LJ 1M atoms, mixed-FP32 vs FP64 path at stated force error"
 UNIT = "atom-timesteps/s"
 STEPS_PER_CYCLE = 20
@@ -451,6 +455,122 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_dem(args):
+    """The contact model of Eq. 3 on a dense granular packing of 1,048,576
+    spheres (mixed and FP64 paths, rebuild every 20 steps), with the force
+    error of both paths against the oracle on the full final state and the
+    oracle's own rate on the host cores."""
+    import torch
+
+    import oracle
+    from paper_2009_07400_gb300 import build, md
+    torch.cuda.set_device(0)
+    build.build()
+    md.load()
+    name = WORKLOADS["dem"]
+    s = inputs.workload(name)
+    n, L = s.n, s.box
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+
+    def make(prec):
+        ctx = md.MDContext(s.pos, s.vel, L, stream=stream.cuda_stream, precision=prec, **DEM_PARAMS)
+        ctx.set_spring_dashpot(DEM_K, DEM_GAMMA)
+        return ctx
+
+    with make(md.MD_MIXED) as ctx:
+        with ClockSampler(0) as clk:
+            ms, launches = time_cycles(ctx, args.steps, args.warmup, None, torch)
+        prof = ctx.profile(2 * STEPS_PER_CYCLE)
+        x, v = ctx.positions(), ctx.velocities()
+        ctx.set_state(x, v)
+        F_mix = ctx.forces()
+    with make(md.MD_FP64) as ctx:
+        c64 = max(1, min(args.steps, 3))
+        ms64, _ = time_cycles(ctx, c64, 1, None, torch)
+        prof64 = ctx.profile(STEPS_PER_CYCLE)
+        ctx.set_state(x, v)
+        F_64 = ctx.forces()
+    # end to end: state from pinned host memory, one cycle, energies back
+    pin_x = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    pin_v = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    pin_x[:] = s.pos
+    pin_v[:] = s.vel
+    with make(md.MD_MIXED) as ctx:
+        ctx.set_state(pin_x, pin_v)
+        ctx.run(STEPS_PER_CYCLE, energy_every=STEPS_PER_CYCLE)
+        torch.cuda.synchronize()
+        e_steps = max(3, args.steps // 5)
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            ctx.set_state(pin_x, pin_v)
+            ctx.run(STEPS_PER_CYCLE, energy_every=STEPS_PER_CYCLE)
+        e2e_s = time.perf_counter() - t0
+    value = n * STEPS_PER_CYCLE * args.steps / (ms / 1e3)
+    ok = dict(k_spring=DEM_K, gamma=DEM_GAMMA, sigma=DEM_PARAMS["sigma"])
+    xw = oracle.wrap(x, L)
+    rows = oracle.neighbors_cells(xw, L, DEM_PARAMS["cutoff"] + DEM_PARAMS["skin"])
+    Fr = oracle.forces_sd_list(xw, v, L, rows, **ok)
+    frms = np.sqrt(np.mean(np.sum(Fr ** 2, axis=1)))
+    sc = np.maximum(np.linalg.norm(Fr, axis=1), frms)
+    # the oracle's own rate: one build + 4 steps on the full packing
+    okw = dict(potential=1, rebuild_every=STEPS_PER_CYCLE, mass=1.0, **ok,
+               cutoff=DEM_PARAMS["cutoff"], skin=DEM_PARAMS["skin"], dt=DEM_PARAMS["dt"])
+    t0 = time.perf_counter()
+    oracle.vv_run(s.pos, s.vel, L, 0, **okw)
+    tb = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.vv_run(s.pos, s.vel, L, 4, **okw)
+    ts = (time.perf_counter() - t0 - tb) / 4
+    cpu_rate = n * STEPS_PER_CYCLE / (max(tb - ts, 0.0) + STEPS_PER_CYCLE * ts)
+    kbar = prof.mean_neighbors
+    # per atom: list entries and row length, p_i, v_i (FP32 copy), the force
+    # store, and the FP32 velocity copy pass (read 32 B, write 16 B) that the
+    # timed force phase includes; neighbour gathers come from L2
+    bpa = 4.0 * kbar + 4 + 16 + 16 + 16 + 48
+    launch_ms = prof.force_ms / max(1, prof.force_launches)
+    peak, peak_kind = measured_peaks()
+    achieved = bpa * n / (launch_ms / 1e3) / 1e9
+    line = {
+        "metric": "atom-timesteps/s, spring-dashpot contacts (Eq. 3), 1M spheres, mixed vs FP64 path",
+        "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64 (mixed: FP32 pair arithmetic, FP64 integration)",
+        "data": "synthetic",
+        "config": {"workload": f"dense granular packing: {n:,} spheres of diameter 1, FCC with "
+                               "nearest-neighbour distance 0.98 (12 contacts each), jitter 0.02, "
+                               f"T 0.05, K {DEM_K:g}, gamma {DEM_GAMMA:g}, skin 0.3, dt 0.001, "
+                               "rebuild every 20 steps", "atoms": n,
+                   "timesteps_per_step": STEPS_PER_CYCLE, "seed": inputs.WORKLOADS[name]["seed"]},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "k_velocity_f32 + k_force_sd_mixed",
+                     "bytes_per_atom": bpa, "mean_neighbors": kbar, "launch_ms": launch_ms,
+                     "peak_source": peak_kind},
+        "phases_ms_per_timestep": {"force": prof.force_ms / prof.steps,
+                                   "neigh": prof.neigh_ms / prof.steps,
+                                   "other": prof.other_ms / prof.steps},
+        "fp64_path": {"value": n * STEPS_PER_CYCLE * c64 / (ms64 / 1e3),
+                      "phases_ms_per_timestep": {"force": prof64.force_ms / prof64.steps,
+                                                 "neigh": prof64.neigh_ms / prof64.steps,
+                                                 "other": prof64.other_ms / prof64.steps}},
+        "force_error": {
+            "mixed_rms_rel": float(np.sqrt(np.sum((F_mix - Fr) ** 2) / np.sum(Fr ** 2))),
+            "fp64_max_rel": float(np.max(np.linalg.norm(F_64 - Fr, axis=1) / sc)),
+            "sample": "every sphere, final state of the mixed run, oracle list forces"},
+        "e2e": {"value": n * STEPS_PER_CYCLE * e_steps / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": int(2 * 3 * 8 * n), "d2h_bytes_per_step": 24},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": oracle.num_threads(),
+                         "kind": "oracle",
+                         "sample": f"FP64 C oracle (OpenMP, {oracle.num_threads()} threads) on the "
+                                   f"full packing: one list build ({max(tb - ts, 0.0):.2f} s) and 4 "
+                                   f"steps ({ts:.3f} s each), rate = atoms x 20 / (build + 20 steps)"},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_ncu_case(which):
     """Create the workload's context and run 2 cycles: 1 first drift, then
     per cycle 19 fused steps, a rebuild (6 binning kernels + build) and the
@@ -476,7 +596,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="fcc64", choices=sorted(WORKLOADS),
                     help="fcc64: the 1,048,576-atom benchmark (default); fcc128: the "
-                         "8,388,608-atom sizing run; ensemble: 256 replicas")
+                         "8,388,608-atom sizing run; ensemble: 256 replicas; fcc80: the "
+                         "paper's 2,048,000-atom GPU shape; dem: 1,048,576 spheres with "
+                         "the contact model of Eq. 3")
     ap.add_argument("--ncu-case", choices=["mixed", "fp64"],
                     help="only build the workload and run 2 rebuild cycles (a short, "
                          "fixed launch sequence for an ncu capture); prints nothing")
@@ -485,6 +607,13 @@ def main():
         args.warmup = 3
     if args.ncu_case:
         run_ncu_case(args.ncu_case)
+    elif args.workload == "dem":
+        if args.impl == "native":
+            run_dem(args)
+        else:
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle arm covers the "
+                              "Lennard-Jones workloads; the dem line carries its own "
+                              "cpu_baseline"}), flush=True)
     elif args.impl == "reference":
         run_reference(args)
     else:

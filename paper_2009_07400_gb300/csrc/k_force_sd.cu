@@ -14,8 +14,9 @@
 // (the velocities the dashpot reads are then those of the half step, the
 // latest ones, as in the oracle).  Mixed path: displacements from the
 // cell-relative FP32 positions plus the stencil offset (as the LJ mixed
-// kernel), v_ij rounded to FP32 from the FP64 difference, FP32 pair
-// arithmetic with compensated per-atom sums.  FP64 path: FP64 throughout.
+// kernel), velocities from an FP32 copy made before each force pass, FP32
+// pair arithmetic (r by a correctly rounded square root, since sigma - r
+// cancels) with compensated per-atom sums.  FP64 path: FP64 throughout.
 #include "md_internal.cuh"
 
 namespace mdk {
@@ -35,8 +36,27 @@ __device__ __forceinline__ void kahan(float &s, float &c, float term)
     s = t;
 }
 
+__device__ __forceinline__ float rcp_approx(float a)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+
+// FP32 copies of the velocities for the mixed contact kernel (one pass per
+// force evaluation: the neighbour gathers then read 16 B instead of 32 B and
+// convert nothing on GB300's narrow FP64 pipe).
+__global__ void __launch_bounds__(256) k_velocity_f32(Dev d, float4 *v32)
+{
+    if (stopped(d.status)) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > d.n) return;                     // slot n: the sentinel (zero velocity)
+    const dvec4 v = d.v[i];
+    v32[i] = make_float4((float)v.x, (float)v.y, (float)v.z, 0.f);
+}
+
 template <bool BATCHED, bool ENERGY>
-__global__ void __launch_bounds__(256) k_force_sd_mixed(Dev d, LJ lj)
+__global__ void __launch_bounds__(256) k_force_sd_mixed(Dev d, LJ lj, const float4 *v32)
 {
     if (stopped(d.status)) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -44,7 +64,11 @@ __global__ void __launch_bounds__(256) k_force_sd_mixed(Dev d, LJ lj)
     const int64_t n = d.n;
     const Rep &R = d.reps[BATCHED ? d.rep_of[i] : 0];
     const float4 pi = d.p32[i];
-    const dvec4 vi = d.v[i];
+    const float4 vi = v32[i];
+    // p_i - o s for o = -1, 0, +1 (nsf = -s), selected per pair in registers
+    const float qx0 = pi.x - R.nsf[0], qx2 = pi.x + R.nsf[0];
+    const float qy0 = pi.y - R.nsf[1], qy2 = pi.y + R.nsf[1];
+    const float qz0 = pi.z - R.nsf[2], qz2 = pi.z + R.nsf[2];
     const int cnt = d.nb_count[i];
     const int nq = (cnt + 3) >> 2;
     const int4 *nb4 = reinterpret_cast<const int4 *>(d.nb);
@@ -59,18 +83,19 @@ __global__ void __launch_bounds__(256) k_force_sd_mixed(Dev d, LJ lj)
             const int32_t j = (int32_t)(e & kJMask);
             const uint32_t c = e >> kJBits;
             const float4 pj = __ldg(d.p32 + j);
-            // d = (p_i - o s) - p_j, o = code - 1 per dimension, nsf = -s
-            const float dx = fmaf((float)((int)(c & 3u) - 1), R.nsf[0], pi.x) - pj.x;
-            const float dy = fmaf((float)((int)((c >> 2) & 3u) - 1), R.nsf[1], pi.y) - pj.y;
-            const float dz = fmaf((float)((int)(c >> 4) - 1), R.nsf[2], pi.z) - pj.z;
+            // d = (p_i - o s) - p_j with o = code - 1 per dimension
+            const float dx = ((c & 2u) ? qx2 : ((c & 1u) ? pi.x : qx0)) - pj.x;
+            const float dy = ((c & 8u) ? qy2 : ((c & 4u) ? pi.y : qy0)) - pj.y;
+            const float dz = ((c & 32u) ? qz2 : ((c & 16u) ? pi.z : qz0)) - pj.z;
             const float rsq = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
             if (!(rsq < lj.sd_sig2f)) continue;            // padding is far away
-            const dvec4 vj = ldg_dvec4(d.v + j);
-            const float vx = (float)(vi.x - vj.x), vy = (float)(vi.y - vj.y), vz = (float)(vi.z - vj.z);
-            const float r = sqrtf(rsq);
-            const float vn = fmaf(dz, vz, fmaf(dy, vy, dx * vx)) / r;
+            const float4 vj = __ldg(v32 + j);
+            const float vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
+            const float r = sqrtf(rsq);                     // correctly rounded: sigma - r cancels
+            const float ir = rcp_approx(r);
+            const float vn = fmaf(dz, vz, fmaf(dy, vy, dx * vx)) * ir;
             const float ov = lj.sigmaf - r;
-            const float fo = (lj.sd_kf * ov - lj.sd_gf * vn) / r;
+            const float fo = (lj.sd_kf * ov - lj.sd_gf * vn) * ir;
             kahan(sx, cx, fo * dx);
             kahan(sy, cy, fo * dy);
             kahan(sz, cz, fo * dz);
@@ -146,16 +171,20 @@ __global__ void __launch_bounds__(256) k_force_sd_f64(Dev d, LJ lj)
 
 }  // namespace
 
-int launch_force_sd(const Dev &d, const LJ &lj, bool mixed, bool energy, cudaStream_t st, int *nl)
+int launch_force_sd(const Dev &d, const LJ &lj, bool mixed, bool energy, float4 *v32,
+                    cudaStream_t st, int *nl)
 {
     if (d.n <= 0) return 0;
     const unsigned g = (unsigned)((d.n + 255) / 256);
     const bool b = d.nrep > 1;
     if (mixed) {
-        if (b && energy) k_force_sd_mixed<true, true><<<g, 256, 0, st>>>(d, lj);
-        else if (b) k_force_sd_mixed<true, false><<<g, 256, 0, st>>>(d, lj);
-        else if (energy) k_force_sd_mixed<false, true><<<g, 256, 0, st>>>(d, lj);
-        else k_force_sd_mixed<false, false><<<g, 256, 0, st>>>(d, lj);
+        if (!v32) return -1;
+        k_velocity_f32<<<(unsigned)((d.n + 256) / 256), 256, 0, st>>>(d, v32);
+        *nl += 1;
+        if (b && energy) k_force_sd_mixed<true, true><<<g, 256, 0, st>>>(d, lj, v32);
+        else if (b) k_force_sd_mixed<true, false><<<g, 256, 0, st>>>(d, lj, v32);
+        else if (energy) k_force_sd_mixed<false, true><<<g, 256, 0, st>>>(d, lj, v32);
+        else k_force_sd_mixed<false, false><<<g, 256, 0, st>>>(d, lj, v32);
     } else {
         if (b && energy) k_force_sd_f64<true, true><<<g, 256, 0, st>>>(d, lj);
         else if (b) k_force_sd_f64<true, false><<<g, 256, 0, st>>>(d, lj);

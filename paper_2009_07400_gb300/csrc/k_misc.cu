@@ -51,9 +51,11 @@ __global__ void __launch_bounds__(256) k_integrate(Dev d, LJ lj, int phase, int 
     const Rep &R = d.reps[BATCHED ? d.rep_of[i] : 0];
     const float4 p = d.p32[i];
     const uint32_t pack = __float_as_uint(p.w);
-    const double cx = ((double)(pack & 1023u) + 0.5) * R.s[0];
-    const double cy = ((double)((pack >> 10) & 1023u) + 0.5) * R.s[1];
-    const double cz = ((double)((pack >> 20) & 1023u) + 0.5) * R.s[2];
+    // cell centres (c + 0.5) s from the per-replica table (no FP64 arithmetic)
+    const double *ct = d.ctr + R.ctr_off;
+    const double cx = __ldg(ct + (pack & 1023u));
+    const double cy = __ldg(ct + R.nc[0] + ((pack >> 10) & 1023u));
+    const double cz = __ldg(ct + R.nc[0] + R.nc[1] + ((pack >> 20) & 1023u));
     const float4 pn = make_float4((float)(x.x - cx), (float)(x.y - cy), (float)(x.z - cz), p.w);
     d.p32[i] = pn;
     check_displacement(d, i, pn);

@@ -68,6 +68,7 @@ struct md_ctx {
     int32_t *id[2] = {nullptr, nullptr};
     float4 *p32[2] = {nullptr, nullptr};
     float4 *p32_ref = nullptr;      // displacement trigger: p32 at the last binning
+    float4 *v32 = nullptr;          // contact model, mixed path: FP32 velocity copies
     cudaStream_t side = nullptr;    // displacement trigger: captures the conditional bodies
     bool disp = false;              // md_params.rebuild_every == 0
     float disp2_thr = 0.f;
@@ -173,7 +174,7 @@ void free_all(md_ctx *c)
                     c->cell_start, c->perm, c->scan_tmp, c->nb, c->nb_count, c->pe_atom,
                     c->w_atom, c->pe64, c->w64, c->ke64, c->status, c->chunk_rep_d,
                     c->chunk_first_d, c->partials_d, c->eout_d, c->elog_d, c->io_d, c->ctr_d,
-                    c->p32_ref};
+                    c->p32_ref, c->v32};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->own_stream && c->st) cudaStreamDestroy(c->st);
@@ -251,7 +252,7 @@ int enq_force(md_ctx *c, int epi, bool energy, int *nl, cudaEvent_t *ev = nullpt
         // force store, then the velocity-Verlet update in its own kernel
         if (ev) CK(cudaEventRecord(ev[0], c->st));
         if (is_sd(c)) {
-            if (launch_force_sd(d, c->lj, is_mixed(c), energy, c->st, nl))
+            if (launch_force_sd(d, c->lj, is_mixed(c), energy, c->v32, c->st, nl))
                 return fail(c, MD_ERR_CUDA, "force launch failed");
         } else {
             if (is_mixed(c)) CK(cudaMemsetAsync(c->f32, 0, sizeof(float4) * c->n, c->st));
@@ -1082,6 +1083,7 @@ int md_set_spring_dashpot(md_ctx *c, double k_spring, double gamma)
         return fail(c, MD_ERR_INVAL, "cutoff must be >= sigma (the sphere diameter) so lists hold every contact");
     CK(cudaStreamSynchronize(c->st));
     int rc = MD_OK;
+    if (!c->v32 && (rc = dalloc(c, &c->v32, (size_t)c->n + 1))) return rc;
     if (is_half(c) && (rc = apply_tuning(c, 1, 0))) return rc;   // contacts use full lists
     c->lj.pot = 1;
     c->lj.sd_k = k_spring;

@@ -141,8 +141,9 @@ int launch_force(const Dev &d, const LJ &lj, int precision, bool half, int tpa, 
 int launch_integrate(const Dev &d, const LJ &lj, int precision, int phase, bool batched,
                      cudaStream_t st, int *nlaunch);
 // Spring-dashpot forces (full list; force store only, no fused integration).
-int launch_force_sd(const Dev &d, const LJ &lj, bool mixed, bool energy, cudaStream_t st,
-                    int *nlaunch);
+// v32: n + 1 float4 of scratch for the mixed path (FP32 velocity copies).
+int launch_force_sd(const Dev &d, const LJ &lj, bool mixed, bool energy, float4 *v32,
+                    cudaStream_t st, int *nlaunch);
 // out3 != NULL: write (PE, KE, W) per replica there; otherwise append one
 // record to log_base at status->elog_cursor and advance the cursor.
 int launch_energy(const Dev &d, const LJ &lj, int precision, bool ke_from_v,

@@ -125,6 +125,11 @@ WORKLOADS = {
     "fcc16_16384": dict(n_cells=16, jitter=0.0, seed=1005),
     # the paper's single-GPU workload (Sec. 6: 80^3 unit cells, 2,048,000 atoms)
     "fcc80_2048000": dict(n_cells=80, jitter=0.0, seed=1006),
+    # dense granular packing for the contact model of Eq. 3: spheres of
+    # diameter 1 on an FCC lattice with nearest-neighbour distance 0.98
+    # (12 contacts each), jitter 0.02, cold velocities
+    "dem64_1048576": dict(n_cells=64, density=4.0 / (0.98 * 2.0 ** 0.5) ** 3, temperature=0.05,
+                          jitter=0.02, seed=1007),
 }
 
 
