@@ -225,6 +225,12 @@ int md_get_neighbors(md_ctx *ctx, int32_t *counts, int32_t *rows, int32_t cap);
 
 int md_get_info(md_ctx *ctx, md_info *info);
 
+/* Sets the step counter (md_info.step) that the fixed rebuild schedule
+ * counts with, e.g. to resume a run from a saved state: md_set_state with the
+ * saved positions and velocities, then md_set_step with the saved step.
+ * Errors: MD_ERR_INVAL (step < 0). */
+int md_set_step(md_ctx *ctx, int64_t step);
+
 /* Reallocates the list for `cap` entries per atom (rounded up to a multiple
  * of 4) and rebuilds it now, growing past `cap` if the current state needs
  * more.  Later rebuilds grow it again whenever a row overflows.

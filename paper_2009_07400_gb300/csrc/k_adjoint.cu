@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs(Dev d, LJ lj, AdjArgs a)
         hi[q] = c[q] == R.nc[q] - 1 ? -R.L[q] : 0.0;
     }
     const dvec4 ui = a.wbar[idi];
-    const int cnt = d.nb_count[i];
+    const int cnt = MD_CHECK(d, d.nb_count[i] <= d.cap) ? d.nb_count[i] : 0;
     const int4 *nb4 = reinterpret_cast<const int4 *>(d.nb);
     const double eps = lj.eps, sigma6 = lj.sigma6, sigma = lj.sigma;
     double jx = 0, jy = 0, jz = 0, fx = 0, fy = 0, fz = 0, ge = 0, gs = 0, pe_e = 0, pe_s = 0;
@@ -70,6 +70,7 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs(Dev d, LJ lj, AdjArgs a)
         const uint32_t code = (uint32_t)e >> kJBits;
         const int ox = (int)(code & 3u) - 1, oy = (int)((code >> 2) & 3u) - 1, oz = (int)(code >> 4) - 1;
         const int32_t j = (int32_t)((uint32_t)e & kJMask);
+        if (!MD_CHECK(d, j <= d.n)) continue;
         double dx, dy, dz;
         if (MIXED) {
             // cell-relative FP32 geometry, as in the mixed force kernel

@@ -60,6 +60,7 @@ __global__ void __launch_bounds__(256) k_bin_assign(Dev d)
     if (bad) atomicOr(&d.status->flags, bad);
     d.x[a] = mk_dvec4(c[0], c[1], c[2], 0.0);
     int32_t key = (int32_t)(R.cell_off + ((int64_t)k[0] * R.nc[1] + k[1]) * R.nc[2] + k[2]);
+    if (!MD_CHECK(d, key >= 0 && key < d.ncells)) return;
     d.cell_key[a] = key;
     // atoms arrive roughly in cell order, so lanes of a warp share cells:
     // one atomic per distinct cell of the warp
@@ -157,7 +158,9 @@ __global__ void __launch_bounds__(256) k_bin_scatter(Dev d)
     int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= d.n) return;
     int32_t key = d.cell_key[a];
+    if (!MD_CHECK(d, key >= 0 && key < d.ncells)) return;
     int32_t pos = d.cell_start[key] + atomicSub(&d.cell_count[key], 1) - 1;
+    if (!MD_CHECK(d, pos >= 0 && pos < d.n)) return;
     d.perm[pos] = (int32_t)a;
 }
 
@@ -171,6 +174,7 @@ __global__ void __launch_bounds__(256) k_sort_gather(Dev d, int64_t ncells)
     if (cell >= ncells) return;
     const int32_t start = d.cell_start[cell];
     const int32_t m = d.cell_start[cell + 1] - start;
+    if (!MD_CHECK(d, start >= 0 && m >= 0 && start + m <= d.n)) return;
     if (m == 0) return;
     for (int32_t mine = lane; mine - lane < m; mine += 32) {
         const bool have = mine < m;

@@ -109,7 +109,9 @@ __device__ __forceinline__ int32_t build_row(const Dev &d, const LJ &lj, int64_t
                 int uz = ci[2] + oz, kz = 0;
                 if (uz < 0) { uz += R.nc[2]; kz = -1; } else if (uz >= R.nc[2]) { uz -= R.nc[2]; kz = 1; }
                 const float qz = pi.z + (float)oz * R.nsf[2];
+                if (!MD_CHECK(d, col + uz >= 0 && col + uz < d.ncells)) continue;
                 const int32_t j0 = d.cell_start[col + uz], j1 = d.cell_start[col + uz + 1];
+                if (!MD_CHECK(d, j0 >= 0 && j0 <= j1 && j1 <= d.n)) continue;
                 if (HALF && oz < 0 && kz == 0) continue;        // entirely below
                 const bool test_sign = HALF && (oz == 0 || kz != 0);
                 const uint32_t tag = offset_code(ox, oy, oz) << kJBits;

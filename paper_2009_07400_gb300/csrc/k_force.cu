@@ -148,7 +148,7 @@ __device__ __forceinline__ void mixed_full_tile(const Dev &d, const LJ &lj, int6
     const Rep &R = d.reps[BATCHED ? d.rep_of[i] : 0];
     const float nsx = R.nsf[0], nsy = R.nsf[1], nsz = R.nsf[2];
     const float4 pi = d.p32[i];
-    const int cnt = valid ? d.nb_count[i] : 0;
+    const int cnt = valid && MD_CHECK(d, d.nb_count[i] <= d.cap) ? d.nb_count[i] : 0;
     const int nq = (cnt + 3) >> 2;
     const int4 *nb4 = reinterpret_cast<const int4 *>(d.nb);
 
@@ -162,6 +162,7 @@ __device__ __forceinline__ void mixed_full_tile(const Dev &d, const LJ &lj, int6
 
     // one pair: adds f*d to (px, py, pz) and, with ENERGY, V and f r^2
     auto pair = [&](uint32_t e, float &px, float &py, float &pz, float &pv, float &pw) {
+        if (!MD_CHECK(d, (e & kJMask) <= (uint32_t)d.n)) return;
         const float4 pj = __ldg(p32 + (e & kJMask));
         const uint32_t c = e >> kJBits;
         // the stencil offset selects p_i + s, p_i or p_i - s in registers
@@ -264,7 +265,7 @@ __global__ void __launch_bounds__(256) k_force_mixed_half(Dev d, LJ lj)
     const Rep &R = d.reps[BATCHED ? d.rep_of[i] : 0];
     const float nsx = R.nsf[0], nsy = R.nsf[1], nsz = R.nsf[2];
     const float4 pi = d.p32[i];
-    const int cnt = d.nb_count[i];
+    const int cnt = MD_CHECK(d, d.nb_count[i] <= d.cap) ? d.nb_count[i] : 0;
     const int nq = (cnt + 3) >> 2;
     const int4 *nb4 = reinterpret_cast<const int4 *>(d.nb);
     float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
@@ -274,6 +275,7 @@ __global__ void __launch_bounds__(256) k_force_mixed_half(Dev d, LJ lj)
         const uint32_t c = (uint32_t)e >> kJBits;
         const int32_t j = (int32_t)((uint32_t)e & kJMask);
         if (j == n) return;                                 // padding
+        if (!MD_CHECK(d, j < n)) return;
         const float4 pj = __ldg(&d.p32[j]);
         const float dx = fmaf(ot[c & 3u], nsx, pi.x - pj.x);
         const float dy = fmaf(ot[(c >> 2) & 3u], nsy, pi.y - pj.y);
@@ -324,6 +326,7 @@ __device__ __forceinline__ void f64_pair(const Dev &d, const LJ &lj, const dvec4
 {
     const uint32_t c = (uint32_t)e >> kJBits;
     const int32_t j = (int32_t)((uint32_t)e & kJMask);
+    if (!MD_CHECK(d, j <= d.n)) return;
     const dvec4 xj = ldg_dvec4(&d.x[j]);
     double dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
     if (EDGE) {
@@ -377,7 +380,7 @@ __global__ void __launch_bounds__(256) k_force_f64_full(Dev d, LJ lj)
     const uint32_t pack = __float_as_uint(d.p32[i].w);
     bool edge;
     const Shift sh = make_shift(R, pack, edge);
-    const int cnt = valid ? d.nb_count[i] : 0;
+    const int cnt = valid && MD_CHECK(d, d.nb_count[i] <= d.cap) ? d.nb_count[i] : 0;
     const int nq = (cnt + 3) >> 2;
     const int4 *nb4 = reinterpret_cast<const int4 *>(d.nb);
     double fx = 0, fy = 0, fz = 0, pe = 0, w = 0;
@@ -429,7 +432,7 @@ __global__ void __launch_bounds__(256) k_force_f64_half(Dev d, LJ lj)
     const uint32_t pack = __float_as_uint(d.p32[i].w);
     bool edge;
     const Shift sh = make_shift(R, pack, edge);
-    const int cnt = d.nb_count[i];
+    const int cnt = MD_CHECK(d, d.nb_count[i] <= d.cap) ? d.nb_count[i] : 0;
     const int nq = (cnt + 3) >> 2;
     const int4 *nb4 = reinterpret_cast<const int4 *>(d.nb);
     double fx = 0, fy = 0, fz = 0, pe = 0, w = 0;

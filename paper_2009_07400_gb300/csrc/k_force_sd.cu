@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(256) k_force_sd_mixed(Dev d, LJ lj, const floa
     const float qx0 = pi.x - R.nsf[0], qx2 = pi.x + R.nsf[0];
     const float qy0 = pi.y - R.nsf[1], qy2 = pi.y + R.nsf[1];
     const float qz0 = pi.z - R.nsf[2], qz2 = pi.z + R.nsf[2];
-    const int cnt = d.nb_count[i];
+    const int cnt = MD_CHECK(d, d.nb_count[i] <= d.cap) ? d.nb_count[i] : 0;
     const int nq = (cnt + 3) >> 2;
     const int4 *nb4 = reinterpret_cast<const int4 *>(d.nb);
     float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(256) k_force_sd_mixed(Dev d, LJ lj, const floa
             const uint32_t e = es[t];
             const int32_t j = (int32_t)(e & kJMask);
             const uint32_t c = e >> kJBits;
+            if (!MD_CHECK(d, j <= d.n)) continue;
             const float4 pj = __ldg(d.p32 + j);
             // d = (p_i - o s) - p_j with o = code - 1 per dimension
             const float dx = ((c & 2u) ? qx2 : ((c & 1u) ? pi.x : qx0)) - pj.x;
@@ -124,7 +125,7 @@ __global__ void __launch_bounds__(256) k_force_sd_f64(Dev d, LJ lj)
     const dvec4 vi = d.v[i];
     const uint32_t pack = __float_as_uint(d.p32[i].w);
     const int ci[3] = {(int)(pack & 1023u), (int)((pack >> 10) & 1023u), (int)((pack >> 20) & 1023u)};
-    const int cnt = d.nb_count[i];
+    const int cnt = MD_CHECK(d, d.nb_count[i] <= d.cap) ? d.nb_count[i] : 0;
     const int nq = (cnt + 3) >> 2;
     const int4 *nb4 = reinterpret_cast<const int4 *>(d.nb);
     double fx = 0, fy = 0, fz = 0, pe = 0, w = 0;
@@ -136,6 +137,7 @@ __global__ void __launch_bounds__(256) k_force_sd_f64(Dev d, LJ lj)
             const uint32_t e = es[t];
             const int32_t j = (int32_t)(e & kJMask);
             const uint32_t c = e >> kJBits;
+            if (!MD_CHECK(d, j <= d.n)) continue;
             const dvec4 xj = ldg_dvec4(d.x + j);
             double dd[3] = {xi.x - xj.x, xi.y - xj.y, xi.z - xj.z};
             // periodic image: a neighbour cell across the box face sits one

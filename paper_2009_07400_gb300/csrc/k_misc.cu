@@ -192,13 +192,14 @@ __global__ void __launch_bounds__(256) k_decode_list(Dev d, int32_t *rows, int32
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n) return;
     const Rep &R = d.reps[BATCHED ? d.rep_of[i] : 0];
-    const int32_t cnt = d.nb_count[i];
+    const int32_t cnt = MD_CHECK(d, d.nb_count[i] <= d.cap) ? d.nb_count[i] : 0;
     const int64_t o = d.id[i];
     const int4 *nb4 = reinterpret_cast<const int4 *>(d.nb);
     for (int32_t k = 0; k < cnt && k < cap; k++) {
         const int4 e4 = nb4[(int64_t)(k >> 2) * d.n + i];
         const int32_t e = (k & 3) == 0 ? e4.x : (k & 3) == 1 ? e4.y : (k & 3) == 2 ? e4.z : e4.w;
         const int32_t j = (int32_t)((uint32_t)e & kJMask);
+        if (!MD_CHECK(d, j < d.n)) continue;
         rows[o * cap + k] = (int32_t)(d.id[j] - R.atom_off);
     }
 }

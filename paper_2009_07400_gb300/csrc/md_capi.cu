@@ -14,8 +14,11 @@
 // kernel returns at once while it is set, so the state freezes at the first
 // failure.  md_run synchronises once at its end; a list overflow is repaired
 // by growing the capacity and resuming at the rebuild that overflowed.
+#include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -119,6 +122,7 @@ Dev view(const md_ctx *c)
 {
     Dev d{};
     d.n = c->n;
+    d.ncells = c->ncells;
     d.nrep = c->nrep;
     d.cap = c->cap;
     d.reps = c->reps_d;
@@ -152,10 +156,27 @@ Dev view(const md_ctx *c)
     return d;
 }
 
+// Host-side fault injection for tests: with MD_FAIL_ALLOC=k in the
+// environment, the k-th device allocation of the process (counting from 0)
+// fails as if the device were out of memory.  Nothing is injected on the GPU.
+bool injected_alloc_failure()
+{
+    static const long fail_at = [] {
+        const char *s = std::getenv("MD_FAIL_ALLOC");
+        return s ? std::strtol(s, nullptr, 10) : -1L;
+    }();
+    static std::atomic<long> count{0};
+    return fail_at >= 0 && count.fetch_add(1) == fail_at;
+}
+
 template <typename T>
 int dalloc(md_ctx *c, T **p, size_t count)
 {
     if (count == 0) count = 1;
+    if (injected_alloc_failure()) {
+        *p = nullptr;
+        return fail(c, MD_ERR_NOMEM, "cudaMalloc: injected allocation failure (MD_FAIL_ALLOC)");
+    }
     cudaError_t e = cudaMalloc((void **)p, sizeof(T) * count);
     if (e != cudaSuccess) {
         *p = nullptr;
@@ -433,6 +454,7 @@ int check_flags(md_ctx *c, const DevStatus &s)
 {
     if (s.flags & FLAG_NONFINITE) return fail(c, MD_ERR_NONFINITE, "non-finite position or velocity");
     if (s.flags & FLAG_BADPOS) return fail(c, MD_ERR_BADPOS, "an atom moved more than one box length between wraps");
+    if (s.flags & FLAG_BOUNDS) return fail(c, MD_ERR_STATE, "a device bounds check failed (debug build)");
     return MD_OK;
 }
 
@@ -965,6 +987,13 @@ int md_get_info(md_ctx *c, md_info *info)
     info->step = c->step;
     info->kernel_launches = c->launches;
     info->rebuilds = c->rebuilds;
+    return MD_OK;
+}
+
+int md_set_step(md_ctx *c, int64_t step)
+{
+    if (!c || step < 0) return fail(c, MD_ERR_INVAL, "bad argument");
+    c->step = step;
     return MD_OK;
 }
 

@@ -39,7 +39,19 @@ constexpr int kMaxNc = 1023;        // cell coordinates are packed in 10 bits ea
 
 // Bits of the device error word.  Every kernel returns immediately while it
 // is non-zero, so the state freezes at the first failure.
-enum : int32_t { FLAG_NL_OVERFLOW = 1, FLAG_NONFINITE = 2, FLAG_BADPOS = 4 };
+enum : int32_t { FLAG_NL_OVERFLOW = 1, FLAG_NONFINITE = 2, FLAG_BADPOS = 4, FLAG_BOUNDS = 8 };
+
+// Bounds checks of the debug build (MD_DEBUG_CHECKS=1): MD_CHECK(d, cond) is
+// true when cond holds; otherwise it raises FLAG_BOUNDS and is false, and
+// the caller skips the access.  In the normal build it is the constant true.
+#ifndef MD_DEBUG_CHECKS
+#define MD_DEBUG_CHECKS 0
+#endif
+#if MD_DEBUG_CHECKS
+#define MD_CHECK(d, cond) ((cond) ? true : (atomicOr(&(d).status->flags, FLAG_BOUNDS), false))
+#else
+#define MD_CHECK(d, cond) true
+#endif
 
 // Device error word and step bookkeeping (one per context, in device memory).
 struct DevStatus {
@@ -85,6 +97,7 @@ struct LJ {
 // Device pointers of one context (passed by value to kernels).
 struct Dev {
     int64_t n;
+    int64_t ncells;           // cells over all replicas (bounds checks)
     int32_t nrep;
     int32_t cap;              // list capacity (multiple of 4)
     const Rep *reps;

@@ -33,7 +33,7 @@ ABI_SYMBOLS = [
     "md_get_neighbors", "md_get_info", "md_autotune", "md_set_capacity", "md_profile",
     "md_set_lj", "md_adjoint", "md_energy_sums_static", "md_create_device",
     "md_set_state_device", "md_get_positions_device", "md_get_velocities_device",
-    "md_get_forces_device", "md_set_spring_dashpot",
+    "md_get_forces_device", "md_set_spring_dashpot", "md_set_step",
 ]
 
 
@@ -124,6 +124,7 @@ def load(path: str | None = None):
                 "md_get_velocities_device": [ctx, _P],
                 "md_get_forces_device": [ctx, _P],
                 "md_set_spring_dashpot": [ctx, ctypes.c_double, ctypes.c_double],
+                "md_set_step": [ctx, ctypes.c_int64],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -185,6 +186,7 @@ class MDContext:
         self.nrep = len(self.counts)
         pos = _f64(pos, self.n)
         vel = _f64(vel, self.n)
+        self._boxes = [np.array(b, np.float64) for b in boxes]
         barr = (md_box * self.nrep)(*[md_box(*map(float, b)) for b in boxes])
         h = ctypes.c_void_p()
         st = ctypes.c_void_p(int(stream)) if stream else None
@@ -213,7 +215,9 @@ class MDContext:
         self.nrep = 1
         self._tstream = stream if stream is not None else torch.cuda.Stream(device=pos.device)
         self._tstream.wait_stream(torch.cuda.current_stream(pos.device))
-        b = md_box(*map(float, np.broadcast_to(np.asarray(box, np.float64), (3,))))
+        bx = np.array(np.broadcast_to(np.asarray(box, np.float64), (3,)))
+        self._boxes = [bx]
+        b = md_box(*map(float, bx))
         h = ctypes.c_void_p()
         rc = self._lib.md_create_device(ctypes.byref(b), ctypes.byref(self.params), self.n,
                                         ctypes.c_void_p(pos.data_ptr()),
@@ -393,6 +397,24 @@ class MDContext:
 
     def set_capacity(self, cap):
         self._check(self._lib.md_set_capacity(self._h, int(cap)))
+
+    def set_step(self, step):
+        """Step counter of the rebuild schedule (for resuming a saved run)."""
+        self._check(self._lib.md_set_step(self._h, int(step)))
+
+    def thermo(self, energies=None):
+        """Thermodynamic outputs per replica from (PE, KE, W) triples (the
+        last axis of md_run's energy log, or md_energy now): total energy,
+        temperature T = 2 KE / (3 N - 3) and pressure P = (N T + W / 3) / V."""
+        if energies is None:
+            energies = np.stack(self.energy(), axis=-1)
+        e = np.asarray(energies, np.float64)
+        pe, ke, w = e[..., 0], e[..., 1], e[..., 2]
+        n = self.counts.astype(np.float64)
+        vol = np.array([float(np.prod(b)) for b in self._boxes])
+        temp = 2.0 * ke / (3.0 * n - 3.0)
+        return {"pe": pe, "ke": ke, "etot": pe + ke, "virial": w, "temperature": temp,
+                "pressure": (n * temp + w / 3.0) / vol}
 
     def info(self) -> md_info:
         inf = md_info()

@@ -573,3 +573,88 @@ def test_displacement_trigger_rejected_by_adjoint(md, orc):
         with pytest.raises(md.MDError) as e:
             ctx.adjoint(20, 10, 10)
         assert e.value.code == md.MD_ERR_INVAL
+
+
+# --------------------------------------------------------------------------
+# Checkpoint / resume, thermodynamic outputs, host-side fault injection.
+# --------------------------------------------------------------------------
+
+def test_resume_from_saved_state(md, orc):
+    """A run saved at step 57 (positions, velocities, step counter) and
+    resumed in a new context keeps the rebuild schedule (rebuilds at 60, 80,
+    100) and follows the uninterrupted run up to the summation order after the
+    resume's own rebuild.  A skin of 1.0 keeps every list valid for 20 steps,
+    so the list built at the resume holds the same pairs inside rc as the
+    older list of the uninterrupted run."""
+    s = inputs.workload("fcc8_2048")
+    kw = dict(skin=1.0)
+    for precision, tol in ((md.MD_FP64, 1e-11), (md.MD_MIXED, 1e-5)):
+        with ctx_of(md, s, precision=precision, **kw) as a:
+            a.run(100)
+            x_ref, v_ref = a.positions(), a.velocities()
+        with ctx_of(md, s, precision=precision, **kw) as b:
+            b.run(57)
+            x57, v57, step = b.positions(), b.velocities(), b.info().step
+        assert step == 57
+        s57 = inputs.System(x57, v57, s.box, 0)
+        with ctx_of(md, s57, precision=precision, **kw) as c, \
+                ctx_of(md, s57, precision=precision, **kw) as u:
+            c.set_step(step)
+            r0, u0 = c.info().rebuilds, u.info().rebuilds
+            c.run(43)
+            u.run(43)                     # no step counter: rebuilds at 20 and 40
+            assert c.info().step == 100
+            assert c.info().rebuilds - r0 == 3 and u.info().rebuilds - u0 == 2
+            d = np.mod(c.positions() - x_ref + s.box / 2, s.box) - s.box / 2
+            assert np.abs(d).max() < tol
+            assert np.abs(c.velocities() - v_ref).max() < 10 * tol
+
+
+def test_thermo_outputs(md, orc):
+    s = inputs.workload("fcc8_2048")
+    with ctx_of(md, s, precision=md.MD_FP64) as ctx:
+        E = ctx.run(40, energy_every=20)
+        th = ctx.thermo(E)
+        pe, ke, w = E[-1, 0]
+        t_ref = 2.0 * ke / (3 * s.n - 3)
+        assert th["temperature"][-1, 0] == pytest.approx(t_ref, rel=1e-15)
+        assert th["pressure"][-1, 0] == pytest.approx((s.n * t_ref + w / 3) / np.prod(s.box), rel=1e-15)
+        assert th["etot"][-1, 0] == pytest.approx(pe + ke, rel=1e-15)
+        now = ctx.thermo()
+        v = ctx.velocities()
+        assert now["ke"][0] == pytest.approx(0.5 * np.sum(v ** 2), rel=1e-12)
+
+
+def test_injected_allocation_failures_are_clean(md):
+    """MD_FAIL_ALLOC=k makes the k-th device allocation of a process fail on
+    the host side: md_create returns MD_ERR_NOMEM with nothing leaked, and
+    the next context in the same process works."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = (
+        "import sys, numpy as np\n"
+        "sys.path.insert(0, %r)\n"
+        "from paper_2009_07400_gb300 import inputs, md\n"
+        "md.load()\n"
+        "s = inputs.fcc_system(4, seed=1)\n"
+        "try:\n"
+        "    md.MDContext(s.pos, s.vel, s.box, rebuild_every=0).close()\n"
+        "    print('created')\n"
+        "except md.MDError as e:\n"
+        "    print('failed', e.code)\n"
+        "with md.MDContext(s.pos, s.vel, s.box) as c:\n"
+        "    c.run(25)\n"
+        "    print('ok', np.isfinite(c.positions()).all())\n" % root)
+    seen_fail = 0
+    for k in (0, 2, 5, 9, 14, 20, 27, 31, 10 ** 6):
+        out = subprocess.run([sys.executable, "-c", script], capture_output=True, text=True,
+                             env=dict(os.environ, MD_FAIL_ALLOC=str(k)), timeout=300)
+        assert out.returncode == 0, out.stderr[-2000:]
+        lines = out.stdout.split()
+        assert lines[-2:] == ["ok", "True"], out.stdout
+        if "failed" in lines:
+            assert lines[lines.index("failed") + 1] == str(md.MD_ERR_NOMEM)
+            seen_fail += 1
+    assert seen_fail >= 7
