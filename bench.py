@@ -574,12 +574,20 @@ def run_dem(args):
 def run_ncu_case(which):
     """Create the workload's context and run 2 cycles: 1 first drift, then
     per cycle 19 fused steps, a rebuild (6 binning kernels + build) and the
-    20th fused step."""
+    20th fused step.  `dem`: the contact model on the 1M-sphere packing
+    (mixed path, force and integration kernels per step)."""
     import torch
 
     from paper_2009_07400_gb300 import build, md
     torch.cuda.set_device(0)
     build.build()
+    if which == "dem":
+        s = inputs.workload(WORKLOADS["dem"])
+        with md.MDContext(s.pos, s.vel, s.box, precision=md.MD_MIXED, **DEM_PARAMS) as ctx:
+            ctx.set_spring_dashpot(DEM_K, DEM_GAMMA)
+            ctx.run(2 * STEPS_PER_CYCLE)
+        torch.cuda.synchronize()
+        return
     s = inputs.workload(WORKLOAD)
     prec = md.MD_MIXED if which == "mixed" else md.MD_FP64
     with md.MDContext(s.pos, s.vel, s.box, precision=prec) as ctx:
@@ -599,7 +607,7 @@ def main():
                          "8,388,608-atom sizing run; ensemble: 256 replicas; fcc80: the "
                          "paper's 2,048,000-atom GPU shape; dem: 1,048,576 spheres with "
                          "the contact model of Eq. 3")
-    ap.add_argument("--ncu-case", choices=["mixed", "fp64"],
+    ap.add_argument("--ncu-case", choices=["mixed", "fp64", "dem"],
                     help="only build the workload and run 2 rebuild cycles (a short, "
                          "fixed launch sequence for an ncu capture); prints nothing")
     args = ap.parse_args()

@@ -164,27 +164,36 @@ __global__ void __launch_bounds__(256) k_bin_scatter(Dev d)
     d.perm[pos] = (int32_t)a;
 }
 
-// One warp per cell: rank members by caller id, gather into the new order.
-template <bool BATCHED>
+// G lanes per cell (G = 32, 16, 8 or 4, chosen from the mean cell
+// occupancy, so that small cells do not leave most of a warp idle): rank
+// each cell's members by caller id with shuffles inside the group, gather
+// into the new order.  All 32 lanes run the same number of loop trips (the
+// warp's largest cell), so every shuffle has the whole warp converged.
+template <int G, bool BATCHED>
 __global__ void __launch_bounds__(256) k_sort_gather(Dev d, int64_t ncells)
 {
     if (stopped(d.status)) return;
-    const int lane = threadIdx.x & 31;
-    int64_t cell = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (cell >= ncells) return;
-    const int32_t start = d.cell_start[cell];
-    const int32_t m = d.cell_start[cell + 1] - start;
-    if (!MD_CHECK(d, start >= 0 && m >= 0 && start + m <= d.n)) return;
-    if (m == 0) return;
-    for (int32_t mine = lane; mine - lane < m; mine += 32) {
+    const int gl = threadIdx.x % G;
+    const int64_t cell = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    int32_t start = 0, m = 0;
+    if (cell < ncells) {
+        start = d.cell_start[cell];
+        m = d.cell_start[cell + 1] - start;
+        if (!MD_CHECK(d, start >= 0 && m >= 0 && start + m <= d.n)) m = 0;
+    }
+    int32_t mmax = m;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mmax = max(mmax, __shfl_xor_sync(0xffffffffu, mmax, o));
+    for (int32_t base = 0; base < mmax; base += G) {
+        const int32_t mine = base + gl;
         const bool have = mine < m;
         const int32_t old = have ? d.perm[start + mine] : 0;
         const int32_t my_id = have ? d.id[old] : INT32_MAX;
         int32_t rank = 0;
-        for (int32_t c0 = 0; c0 < m; c0 += 32) {
-            int32_t other = (c0 + lane < m) ? d.id[d.perm[start + c0 + lane]] : INT32_MAX;
-#pragma unroll 8
-            for (int t = 0; t < 32; t++) rank += (__shfl_sync(0xffffffffu, other, t) < my_id);
+        for (int32_t c0 = 0; c0 < mmax; c0 += G) {
+            const int32_t other = (c0 + gl < m) ? d.id[d.perm[start + c0 + gl]] : INT32_MAX;
+#pragma unroll
+            for (int t = 0; t < G; t++) rank += (__shfl_sync(0xffffffffu, other, t, G) < my_id);
         }
         if (!have) continue;
         const int32_t ns = start + rank;
@@ -203,6 +212,14 @@ __global__ void __launch_bounds__(256) k_sort_gather(Dev d, int64_t ncells)
         uint32_t pack = (uint32_t)cx | ((uint32_t)cy << 10) | ((uint32_t)cz << 20);
         d.p32[ns] = make_float4((float)px, (float)py, (float)pz, __uint_as_float(pack));
     }
+}
+
+template <int G>
+void launch_sort_gather(const Dev &d, int64_t ncells, cudaStream_t st)
+{
+    const unsigned gs = (unsigned)((ncells * G + 255) / 256);
+    if (d.nrep > 1) k_sort_gather<G, true><<<gs, 256, 0, st>>>(d, ncells);
+    else k_sort_gather<G, false><<<gs, 256, 0, st>>>(d, ncells);
 }
 
 inline unsigned blocks_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
@@ -230,9 +247,13 @@ int launch_bin(const Dev &d, int64_t ncells, int32_t *tmp, int64_t tmp_len, cuda
     k_scan_tops<<<1, 1024, 0, st>>>(tmp, nb, d.cell_start, ncells);
     k_scan_add<<<(unsigned)nb, 1024, 0, st>>>(d.cell_start, ncells, tmp);
     k_bin_scatter<<<gb, 256, 0, st>>>(d);
-    unsigned gs = blocks_for(ncells * 32, 256);
-    if (batched) k_sort_gather<true><<<gs, 256, 0, st>>>(d, ncells);
-    else k_sort_gather<false><<<gs, 256, 0, st>>>(d, ncells);
+    // lanes per cell from the mean occupancy (about 19 atoms at the LJ
+    // benchmark's density, about 3 for dense granular packings)
+    const int64_t mean = d.n / (ncells > 0 ? ncells : 1);
+    if (mean >= 12) launch_sort_gather<32>(d, ncells, st);
+    else if (mean >= 6) launch_sort_gather<16>(d, ncells, st);
+    else if (mean >= 3) launch_sort_gather<8>(d, ncells, st);
+    else launch_sort_gather<4>(d, ncells, st);
     *nl += 6;
     return (int)cudaGetLastError();
 }
