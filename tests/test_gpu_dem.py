@@ -125,3 +125,27 @@ def test_contact_model_argument_checks(md):
         assert e.value.code == md.MD_ERR_INVAL
         ctx.set_lj(1.0, 1.0)                                  # back to Lennard-Jones
         ctx.forces()
+
+
+def test_batched_packings_with_displacement_trigger(md, orc):
+    """Three independent packings of different sizes in one context, the
+    displacement-triggered schedule, FP64: each replica follows its own
+    oracle run (dashpot on the half-step velocities)."""
+    systems = [dense(seed=s, n=n, L=L) for s, n, L in
+               ((11, 300, (7.0, 7.0, 7.5)), (12, 450, (8.0, 8.0, 8.0)), (13, 200, (6.0, 6.5, 7.0)))]
+    pos = np.concatenate([x for x, _, _ in systems])
+    vel = np.concatenate([v for _, v, _ in systems])
+    kw = dict(sigma=SIG, cutoff=SIG, skin=SKIN, dt=0.001)
+    with md.MDContext(pos, vel, [L for _, _, L in systems], counts=[x.shape[0] for x, _, _ in systems],
+                      precision=md.MD_FP64, rebuild_every=0, **kw) as ctx:
+        ctx.set_spring_dashpot(300.0, 1.5)
+        ctx.run(150)
+        xg = ctx.positions()
+        assert ctx.info().rebuilds > 1
+    o = 0
+    for x, v, L in systems:
+        xr, _, _ = orc.vv_run(x, v, L, 150, potential=1, k_spring=300.0, gamma=1.5,
+                              rebuild_every=0, **kw)
+        d = np.mod(xg[o:o + x.shape[0]] - xr + L / 2, L) - L / 2
+        assert np.abs(d).max() < 1e-9
+        o += x.shape[0]
