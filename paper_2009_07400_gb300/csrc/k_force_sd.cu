@@ -16,7 +16,8 @@
 // cell-relative FP32 positions plus the stencil offset (as the LJ mixed
 // kernel), velocities from an FP32 copy made before each force pass, FP32
 // pair arithmetic (r by a correctly rounded square root, since sigma - r
-// cancels) with compensated per-atom sums.  FP64 path: FP64 throughout.
+// cancels) with compensated per-atom sums.  FP64 path: FP64 throughout,
+// 1/r by a refined FP32 estimate (below FP64 rounding after two steps).
 #include "md_internal.cuh"
 
 namespace mdk {
@@ -151,10 +152,17 @@ __global__ void __launch_bounds__(256) k_force_sd_f64(Dev d, LJ lj)
             const double rsq = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
             if (!(rsq < lj.sd_sig2)) continue;
             const dvec4 vj = ldg_dvec4(d.v + j);
-            const double r = sqrt(rsq);
-            const double vn = (dd[0] * (vi.x - vj.x) + dd[1] * (vi.y - vj.y) + dd[2] * (vi.z - vj.z)) / r;
+            // 1/r: FP32 reciprocal square root refined by two Newton steps
+            // y <- y (3 - rsq y^2) / 2 (relative error 2^-22 -> ~2^-44 ->
+            // below FP64 rounding), then r = rsq / r; cheaper on GB300's FP64
+            // pipe than an FP64 square root and two divisions
+            double ir = (double)rsqrtf((float)rsq);
+            ir = ir * fma(-0.5 * rsq, ir * ir, 1.5);
+            ir = ir * fma(-0.5 * rsq, ir * ir, 1.5);
+            const double r = rsq * ir;
+            const double vn = (dd[0] * (vi.x - vj.x) + dd[1] * (vi.y - vj.y) + dd[2] * (vi.z - vj.z)) * ir;
             const double ov = lj.sigma - r;
-            const double fo = (lj.sd_k * ov - lj.sd_g * vn) / r;
+            const double fo = (lj.sd_k * ov - lj.sd_g * vn) * ir;
             fx = fma(fo, dd[0], fx);
             fy = fma(fo, dd[1], fy);
             fz = fma(fo, dd[2], fz);

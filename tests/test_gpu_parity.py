@@ -681,3 +681,21 @@ def test_displacement_trigger_removes_stale_list_drift(md, orc):
         drift[every] = (es - es0) / s.n
     assert drift[20] < -1e-4
     assert abs(drift[0]) < 6e-5
+
+
+def test_profile_phases_both_schedules(md, orc):
+    """md_profile splits device time into Force / Neigh / Other (the paper's
+    Fig. 4/5 categories) on the fixed and the displacement-triggered
+    schedules, and leaves the state where md_run would."""
+    s = inputs.workload("fcc8_2048")
+    for every in (20, 0):
+        with ctx_of(md, s, precision=md.MD_FP64, rebuild_every=every) as a, \
+                ctx_of(md, s, precision=md.MD_FP64, rebuild_every=every) as b:
+            p = a.profile(60)
+            b.run(60)
+            assert p.steps == 60 and p.force_launches == 60
+            assert p.force_ms > 0 and p.neigh_ms > 0 and p.other_ms > 0
+            assert p.neigh_launches >= 7 * 2        # at least two rebuilds of 7 launches
+            assert abs(p.mean_neighbors - 78) < 6
+            d = np.mod(a.positions() - b.positions() + s.box / 2, s.box) - s.box / 2
+            assert np.abs(d).max() < 1e-9
