@@ -381,11 +381,23 @@ def cpu_baseline_leg(pos, vel, box, counts, res):
     rate, t_step, t_build, cores, atoms = oracle_rate(systems)
     what = ("the full workload" if counts is None else
             f"{len(systems)} of the replicas ({atoms:,} atoms)")
+    # one core, on the paper's single-core CPU workload shape (Sec. 6: FCC
+    # 32^3, 131,072 atoms), as the paper's own CPU comparison runs
+    s1 = inputs.workload("fcc32_131072")
+    oracle.set_num_threads(1)
+    try:
+        rate1, t_step1, t_build1, _, _ = oracle_rate([(s1.pos, s1.vel, s1.box, 0)])
+    finally:
+        oracle.set_num_threads(cores)
     out = {"cpu_baseline": {
         "value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
         "sample": f"FP64 C oracle (OpenMP, {cores} threads) on {what}: one list build "
                   f"({t_build:.2f} s) and 4 velocity-Verlet steps ({t_step:.3f} s each), "
-                  f"rate = atoms x 20 / (build + 20 steps)"}}
+                  f"rate = atoms x 20 / (build + 20 steps)",
+        "single_core": {"value": rate1, "unit": UNIT, "cores": 1,
+                        "sample": f"the same oracle on one thread, FCC 32^3 (131,072 atoms, the "
+                                  f"paper's single-core workload): build {t_build1:.2f} s, "
+                                  f"{t_step1:.3f} s per step"}}}
     rng = np.random.default_rng(0)
     errs = {}
     for key, name in (("mixed_state", "mixed_rms_rel"), ("fp64_state", "fp64_max_rel")):

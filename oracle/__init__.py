@@ -69,6 +69,7 @@ def _load():
             P = ctypes.POINTER(_Params)
             sig = {
                 "orc_num_threads": (ctypes.c_int, []),
+                "orc_set_num_threads": (None, [ctypes.c_int]),
                 "orc_cell_grid": (ctypes.c_int, [_D, ctypes.c_double, _I32, _D]),
                 "orc_wrap": (None, [ctypes.c_int64, _D, _D]),
                 "orc_bin": (None, [ctypes.c_int64, _D, _I32, _D, _I32, _I32, _I32]),
@@ -142,6 +143,11 @@ def params(epsilon=1.0, sigma=1.0, mass=1.0, cutoff=2.5, skin=0.3, dt=0.005,
 def num_threads() -> int:
     """OpenMP threads the oracle's per-atom loops use."""
     return int(_load().orc_num_threads())
+
+
+def set_num_threads(k: int) -> None:
+    """Threads for the oracle's later parallel loops (timing runs only)."""
+    _load().orc_set_num_threads(int(k))
 
 
 def cell_grid(L, r):

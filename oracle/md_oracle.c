@@ -93,6 +93,16 @@ int orc_num_threads(void)
 #endif
 }
 
+/* Threads for the following parallel loops (timing runs only). */
+void orc_set_num_threads(int k)
+{
+#ifdef _OPENMP
+    if (k > 0) omp_set_num_threads(k);
+#else
+    (void)k;
+#endif
+}
+
 /* ---------------------------------------------------------------------------
  * Geometry
  * ------------------------------------------------------------------------- */
