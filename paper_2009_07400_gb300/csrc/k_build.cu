@@ -53,9 +53,6 @@ __device__ __forceinline__ double image_diff(double xi, double xj, int k, double
     return t;
 }
 
-#ifndef MD_BUILD_MASK
-#define MD_BUILD_MASK 1
-#endif
 
 // Half-list ownership of candidate j (FP32 d = p_i + o(-s) - p_j first; the
 // exact FP64 del when the FP32 z-component is within 1e-4 of zero).
@@ -133,7 +130,6 @@ __device__ __forceinline__ int32_t build_row(const Dev &d, const LJ &lj, int64_t
                     if (cnt < cap) row[(int64_t)(cnt >> 2) * 4 * n + (cnt & 3)] = (int32_t)((uint32_t)j | tag);
                     cnt++;
                 };
-#if MD_BUILD_MASK
                 // hot loop: a bit per candidate inside the FP32 band's upper
                 // edge (about 1 in 6), independent loads; then the hits
                 for (int32_t jb = j0; jb < j1; jb += 32) {
@@ -155,15 +151,6 @@ __device__ __forceinline__ int32_t build_row(const Dev &d, const LJ &lj, int64_t
                         accept(j, dx, dy, dz, fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
                     }
                 }
-#else
-                for (int32_t j = j0; j < j1; j++) {
-                    const float4 pj = __ldg(p32 + j);
-                    const float dx = qx - pj.x, dy = qy - pj.y, dz = qz - pj.z;
-                    const float r2f = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                    if (!(r2f < hi)) continue;                 // clearly outside rs
-                    accept(j, dx, dy, dz, r2f);
-                }
-#endif
             }
         }
     }

@@ -77,12 +77,6 @@ __device__ __forceinline__ float rcp_approx(float a)
 }
 
 
-// Cell centres in the velocity-Verlet epilogue: 1 = read from the
-// per-replica FP64 table, 0 = computed ((c + 0.5) s, integer-to-FP64
-// conversions and FP64 FMAs on GB300's slow FP64 pipe).  Same values.
-#ifndef MD_CENTER_TABLE
-#define MD_CENTER_TABLE 1
-#endif
 
 // FP64 epilogue shared by both precisions.  fx..fz: force on atom i.
 template <int EPI, bool ENERGY>
@@ -112,17 +106,13 @@ __device__ __forceinline__ void epilogue(const Dev &d, const LJ &lj, const Rep &
         // positions to the other buffer; the mixed path gathers p32 only
         if (mixed) d.x[i] = x;
         else d.x_nxt[i] = x;
-        double cx, cy, cz;
-        if (MD_CENTER_TABLE) {   // centre coordinates from the per-replica table
-            const double *ct = d.ctr + R.ctr_off;
-            cx = __ldg(ct + (pack & 1023u));
-            cy = __ldg(ct + R.nc[0] + ((pack >> 10) & 1023u));
-            cz = __ldg(ct + R.nc[0] + R.nc[1] + ((pack >> 20) & 1023u));
-        } else {
-            cx = ((double)(pack & 1023u) + 0.5) * R.s[0];
-            cy = ((double)((pack >> 10) & 1023u) + 0.5) * R.s[1];
-            cz = ((double)((pack >> 20) & 1023u) + 0.5) * R.s[2];
-        }
+        // cell centres (c + 0.5) s from the per-replica table: the same values
+        // as computing them, without integer conversions and FP64 products
+        // on GB300's narrow FP64 pipe
+        const double *ct = d.ctr + R.ctr_off;
+        const double cx = __ldg(ct + (pack & 1023u));
+        const double cy = __ldg(ct + R.nc[0] + ((pack >> 10) & 1023u));
+        const double cz = __ldg(ct + R.nc[0] + R.nc[1] + ((pack >> 20) & 1023u));
         const float4 pn = make_float4((float)(x.x - cx), (float)(x.y - cy), (float)(x.z - cz),
                                       __uint_as_float(pack));
         d.p32_nxt[i] = pn;
