@@ -699,3 +699,32 @@ def test_profile_phases_both_schedules(md, orc):
             assert abs(p.mean_neighbors - 78) < 6
             d = np.mod(a.positions() - b.positions() + s.box / 2, s.box) - s.box / 2
             assert np.abs(d).max() < 1e-9
+
+
+def test_random_geometry_sweep(md, orc):
+    """Twenty seeded random systems: box edges from 2 (rc + skin) to 6.5
+    (rc + skin) (1 to 6 cells per edge, anisotropic cells), densities from
+    0.05 to 1.1, cutoff and skin varied.  For each: bit-exact lists (full
+    and half) and FP64 forces within 1e-10 of the plain definition."""
+    rng = np.random.default_rng(2024)
+    for case in range(20):
+        rc = float(rng.uniform(1.2, 3.0))
+        skin = float(rng.uniform(0.0, 0.6))
+        rs = rc + skin
+        L = rng.uniform(2.0, 6.5, 3) * rs
+        rho = float(rng.uniform(0.05, 1.1))
+        n = max(2, min(6000, int(rho * np.prod(L))))
+        x = rng.uniform(0, 1, (n, 3)) * L
+        # keep atoms apart (the repulsion of overlapping random atoms only
+        # adds rounding noise to the force comparison)
+        v = rng.normal(size=(n, 3))
+        kw = dict(cutoff=rc, skin=skin)
+        for half in (False, True):
+            with md.MDContext(x, v, L, precision=md.MD_FP64, half_list=half, **kw) as ctx:
+                c_g, r_g = ctx.neighbors_raw()
+                c_o, r_o = orc.neighbors_cells_raw(orc.wrap(x, L), L, rs, half=half, cap=1024)
+                assert np.array_equal(c_g, c_o), (case, half)
+                assert np.array_equal(sorted_rows(c_g, r_g), sorted_rows(c_o, r_o)), (case, half)
+                if not half:
+                    Fr = orc.forces_brute(x, L, cutoff=rc)
+                    assert fp64_force_ok(ctx.forces(), Fr) <= 1e-10, case
