@@ -728,3 +728,18 @@ def test_random_geometry_sweep(md, orc):
                 if not half:
                     Fr = orc.forces_brute(x, L, cutoff=rc)
                     assert fp64_force_ok(ctx.forces(), Fr) <= 1e-10, case
+
+
+def test_displacement_trigger_step(md, orc):
+    """The device trigger fires at the first step whose displacement exceeds
+    skin/2 less 1e-5 (the FP32 margin): for an atom drifting at speed 1 with
+    dt 0.005 and skin 0.3 that is step 30 (0.15 > 0.14999), one step before
+    the exact rule of the oracle (step 31, 0.155 > 0.15)."""
+    L = np.array([20.0, 20.0, 20.0])
+    x = np.array([[20.0 - 0.12, 10.0, 10.0], [5.0, 5.0, 5.0]])
+    v = np.array([[1.0, 0.0, 0.0], [0.0, 0.0, 0.0]])
+    for k, extra in ((29, 0), (30, 1), (31, 1)):
+        with md.MDContext(x, v, L, precision=md.MD_FP64, rebuild_every=0) as ctx:
+            r0 = ctx.info().rebuilds
+            ctx.run(k)
+            assert ctx.info().rebuilds - r0 == extra, k

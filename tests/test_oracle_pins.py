@@ -359,6 +359,21 @@ def test_displacement_schedule_keeps_lists_exact(orc, liquid):
     assert np.abs(mi(xc - xb)).max() > 1e3 * np.abs(mi(xa - xb)).max()
 
 
+def test_displacement_trigger_step_is_exact(orc):
+    """One atom drifting at constant speed 1 (dt 0.005, skin 0.3) from just
+    inside the box face: it has moved 0.005 k after k steps, so the rule
+    "rebuild once some atom moved more than skin/2" first fires at k = 31
+    (0.155 > 0.15; at k = 30 the distance equals 0.15).  The rebuild wraps
+    the coordinate back into the box, which makes the step visible."""
+    L = np.array([20.0, 20.0, 20.0])
+    x = np.array([[20.0 - 0.12, 10.0, 10.0], [5.0, 5.0, 5.0]])
+    v = np.array([[1.0, 0.0, 0.0], [0.0, 0.0, 0.0]])
+    for k, wrapped in ((30, False), (31, True)):
+        xk, _, _ = orc.vv_run(x, v, L, k, rebuild_every=0)
+        assert (xk[0, 0] < L[0]) == wrapped, k
+        assert abs(xk[0, 0] % L[0] - (20.0 - 0.12 + 0.005 * k) % L[0]) < 1e-12
+
+
 def test_nve_energy(orc):
     """Total energy is conserved while KE and PE exchange; the residual comes
     from pairs crossing the unshifted cutoff, which no dt removes (the
