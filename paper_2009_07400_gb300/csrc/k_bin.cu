@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(256) k_bin_assign(Dev d)
     }
     if (bad) atomicOr(&d.status->flags, bad);
     d.x[a] = mk_dvec4(c[0], c[1], c[2], 0.0);
-    int32_t key = (int32_t)(R.cell_off + ((int64_t)k[0] * R.nc[1] + k[1]) * R.nc[2] + k[2]);
+    int32_t key = (int32_t)cell_id(R, k[0], k[1], k[2]);
     if (!MD_CHECK(d, key >= 0 && key < d.ncells)) return;
     d.cell_key[a] = key;
     // atoms arrive roughly in cell order, so lanes of a warp share cells:
@@ -202,10 +202,8 @@ __global__ void __launch_bounds__(256) k_sort_gather(Dev d, int64_t ncells)
         d.v_alt[ns] = d.v[old];
         d.id_alt[ns] = my_id;
         const Rep &R = d.reps[BATCHED ? d.rep_of[ns] : 0];
-        int64_t local = cell - R.cell_off;
-        int32_t cz = (int32_t)(local % R.nc[2]);
-        int32_t cy = (int32_t)((local / R.nc[2]) % R.nc[1]);
-        int32_t cx = (int32_t)(local / ((int64_t)R.nc[2] * R.nc[1]));
+        int cx, cy, cz;
+        cell_coords(R, cell, cx, cy, cz);
         double px = x.x - ((double)cx + 0.5) * R.s[0];
         double py = x.y - ((double)cy + 0.5) * R.s[1];
         double pz = x.z - ((double)cz + 0.5) * R.s[2];

@@ -101,13 +101,14 @@ __device__ __forceinline__ int32_t build_row(const Dev &d, const LJ &lj, int64_t
             int uy = ci[1] + oy, ky = 0;
             if (uy < 0) { uy += R.nc[1]; ky = -1; } else if (uy >= R.nc[1]) { uy -= R.nc[1]; ky = 1; }
             const float qy = pi.y + (float)oy * R.nsf[1];
-            const int64_t col = R.cell_off + ((int64_t)ux * R.nc[1] + uy) * R.nc[2];
+            const int32_t col = (int32_t)cell_id(R, ux, uy, 0);
             for (int oz = -1; oz <= 1; oz++) {
                 int uz = ci[2] + oz, kz = 0;
                 if (uz < 0) { uz += R.nc[2]; kz = -1; } else if (uz >= R.nc[2]) { uz -= R.nc[2]; kz = 1; }
                 const float qz = pi.z + (float)oz * R.nsf[2];
-                if (!MD_CHECK(d, col + uz >= 0 && col + uz < d.ncells)) continue;
-                const int32_t j0 = d.cell_start[col + uz], j1 = d.cell_start[col + uz + 1];
+                const int32_t cid = cell_id_z(col, uz);
+                if (!MD_CHECK(d, cid >= 0 && cid < d.ncells)) continue;
+                const int32_t j0 = d.cell_start[cid], j1 = d.cell_start[cid + 1];
                 if (!MD_CHECK(d, j0 >= 0 && j0 <= j1 && j1 <= d.n)) continue;
                 if (HALF && oz < 0 && kz == 0) continue;        // entirely below
                 const bool test_sign = HALF && (oz == 0 || kz != 0);

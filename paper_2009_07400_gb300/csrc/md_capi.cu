@@ -58,7 +58,8 @@ struct md_ctx {
     LJ lj{};
     std::vector<Rep> reps_h;
     std::vector<int64_t> counts_h;
-    int64_t ncells = 0;
+    int64_t ncells = 0;     // cells over all replicas
+    int64_t nids = 0;       // cell ids (tile padding included): sizes of cell arrays
     int64_t nchunks = 0;
     cudaStream_t st = nullptr;
     bool own_stream = false;
@@ -122,7 +123,7 @@ Dev view(const md_ctx *c)
 {
     Dev d{};
     d.n = c->n;
-    d.ncells = c->ncells;
+    d.ncells = c->nids;
     d.nrep = c->nrep;
     d.cap = c->cap;
     d.reps = c->reps_d;
@@ -226,7 +227,7 @@ int alloc_list(md_ctx *c, int32_t cap)
 int enq_bin(md_ctx *c, int *nl)
 {
     Dev d = view(c);
-    if (launch_bin(d, c->ncells, c->scan_tmp, c->scan_len, c->st, nl) != 0)
+    if (launch_bin(d, c->nids, c->scan_tmp, c->scan_len, c->st, nl) != 0)
         return fail(c, MD_ERR_CUDA, "binning launch failed");
     if (c->disp) {
         // the reordered state is copied back: buffer roles never change
@@ -246,7 +247,7 @@ int enq_build(md_ctx *c, int *nl)
 {
     CK(cudaMemsetAsync(&c->status->max_count, 0, sizeof(int32_t), c->st));
     Dev d = view(c);
-    if (launch_build(d, c->lj, is_half(c), c->ncells, c->st, nl) != 0)
+    if (launch_build(d, c->lj, is_half(c), c->nids, c->st, nl) != 0)
         return fail(c, MD_ERR_CUDA, "list build launch failed");
     c->list_valid = true;
     c->builds_enqueued++;
@@ -335,9 +336,9 @@ int enq_cond_rebuild(md_ctx *c, int *nl)
     cudaGraph_t body = np.conditional.phGraph_out[0];
     CK(cudaStreamBeginCaptureToGraph(c->side, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     int bl = 0, rc = MD_OK;
-    if (launch_bin(d, c->ncells, c->scan_tmp, c->scan_len, c->side, &bl) != 0 ||
+    if (launch_bin(d, c->nids, c->scan_tmp, c->scan_len, c->side, &bl) != 0 ||
         launch_copy_back(d, c->side, &bl) != 0 ||
-        launch_build(d, c->lj, is_half(c), c->ncells, c->side, &bl) != 0)
+        launch_build(d, c->lj, is_half(c), c->nids, c->side, &bl) != 0)
         rc = fail(c, MD_ERR_CUDA, "rebuild body launch failed");
     cudaGraph_t out = nullptr;
     cudaError_t e = cudaStreamEndCapture(c->side, &out);
@@ -931,16 +932,23 @@ int md_get_forces_device(md_ctx *c, double *out)
 int md_get_cells(md_ctx *c, int32_t *cell_start, int32_t *cell_atoms)
 {
     if (!c || !cell_start || !cell_atoms) return fail(c, MD_ERR_INVAL, "null argument");
-    std::vector<int32_t> cs((size_t)c->ncells + 1), ids((size_t)c->n);
+    std::vector<int32_t> cs((size_t)c->nids + 1), ids((size_t)c->n);
     CK(cudaMemcpyAsync(cs.data(), c->cell_start, sizeof(int32_t) * cs.size(), cudaMemcpyDeviceToHost, c->st));
     CK(cudaMemcpyAsync(ids.data(), c->id[c->vp], sizeof(int32_t) * ids.size(), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
+    // device cells are numbered by tiles; report them in (cx, cy, cz) order
     int64_t o = 0;
     for (int32_t r = 0; r < c->nrep; r++) {
         const Rep &R = c->reps_h[r];
-        const int64_t nc = (int64_t)R.nc[0] * R.nc[1] * R.nc[2];
-        for (int64_t k = 0; k <= nc; k++) cell_start[o++] = (int32_t)(cs[R.cell_off + k] - R.atom_off);
-        for (int64_t a = R.atom_off; a < R.atom_off + R.natoms; a++) cell_atoms[a] = (int32_t)(ids[a] - R.atom_off);
+        int64_t at = R.atom_off;
+        for (int cx = 0; cx < R.nc[0]; cx++)
+            for (int cy = 0; cy < R.nc[1]; cy++)
+                for (int cz = 0; cz < R.nc[2]; cz++) {
+                    const int64_t id = cell_id(R, cx, cy, cz);
+                    cell_start[o++] = (int32_t)(at - R.atom_off);
+                    for (int32_t a = cs[id]; a < cs[id + 1]; a++) cell_atoms[at++] = (int32_t)(ids[a] - R.atom_off);
+                }
+        cell_start[o++] = (int32_t)(at - R.atom_off);
     }
     return MD_OK;
 }
@@ -1409,7 +1417,7 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
     }
     c->tpa = q.threads_per_atom ? q.threads_per_atom : 1;
     const double rs = q.cutoff + q.skin;
-    int64_t n = 0, cells = 0;
+    int64_t n = 0, cells = 0, ids = 0;   // cells, and cell ids with tile padding
     double maxrho = 0;
     int64_t maxn = 0;
     c->reps_h.resize(nrep);
@@ -1431,11 +1439,13 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
             R.nsf[d] = -(float)R.s[d];
             vol *= L[d];
         }
-        R.cell_off = cells;
+        for (int d = 0; d < 3; d++) R.nt[d] = (R.nc[d] + 1) / 2;
+        R.cell_off = ids;
         R.ctr_off = 0;   // set below
         R.atom_off = n;
         R.natoms = counts[r];
         cells += (int64_t)R.nc[0] * R.nc[1] * R.nc[2];
+        ids += (int64_t)R.nt[0] * R.nt[1] * R.nt[2] * 8;
         chunk_first.push_back((int64_t)chunk_rep.size() / 2);
         for (int64_t k = 0; k < energy_chunks_of(counts[r]); k++) {
             chunk_rep.push_back(r);
@@ -1448,7 +1458,7 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
     }
     chunk_first.push_back((int64_t)chunk_rep.size() / 2);
     if (n > (int64_t)kJMask) return fail(c, MD_ERR_INVAL, "more than 67,108,863 atoms (26-bit list indices)");
-    if (cells >= (int64_t)1 << 31) return fail(c, MD_ERR_INVAL, "too many cells");
+    if (ids >= (int64_t)1 << 31) return fail(c, MD_ERR_INVAL, "too many cells");
     if (on_device) {
         if (!is_device_pointer(pos) || !is_device_pointer(vel))
             return fail(c, MD_ERR_INVAL, "pos/vel are not device pointers of the current device");
@@ -1459,6 +1469,7 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
     }
     c->n = n;
     c->ncells = cells;
+    c->nids = ids;
     c->nchunks = (int64_t)chunk_rep.size() / 2;
 
     set_lj_constants(c);
@@ -1495,10 +1506,10 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
     }
     if ((rc = dalloc(c, &c->f64, N))) return rc;
     if ((rc = dalloc(c, &c->cell_key, N))) return rc;
-    if ((rc = dalloc(c, &c->cell_count, (size_t)cells))) return rc;
-    if ((rc = dalloc(c, &c->cell_start, (size_t)cells + 1))) return rc;
+    if ((rc = dalloc(c, &c->cell_count, (size_t)ids))) return rc;
+    if ((rc = dalloc(c, &c->cell_start, (size_t)ids + 1))) return rc;
     if ((rc = dalloc(c, &c->perm, N))) return rc;
-    c->scan_len = scan_tmp_elems(cells);
+    c->scan_len = scan_tmp_elems(ids);
     if ((rc = dalloc(c, &c->scan_tmp, (size_t)c->scan_len))) return rc;
     if ((rc = dalloc(c, &c->nb_count, N))) return rc;
     if ((rc = dalloc(c, &c->pe_atom, N))) return rc;
@@ -1531,7 +1542,7 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
     CK(cudaMemcpyAsync(c->rep_of_d, rep_of.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, c->st));
     CK(cudaMemcpyAsync(c->chunk_rep_d, chunk_rep.data(), sizeof(int64_t) * chunk_rep.size(), cudaMemcpyHostToDevice, c->st));
     CK(cudaMemcpyAsync(c->chunk_first_d, chunk_first.data(), sizeof(int64_t) * chunk_first.size(), cudaMemcpyHostToDevice, c->st));
-    CK(cudaMemsetAsync(c->cell_count, 0, sizeof(int32_t) * (size_t)cells, c->st));
+    CK(cudaMemsetAsync(c->cell_count, 0, sizeof(int32_t) * (size_t)ids, c->st));
     CK(cudaMemsetAsync(c->status, 0, sizeof(DevStatus), c->st));
     CK(cudaMemsetAsync(c->f32, 0, sizeof(float4) * N, c->st));
     CK(cudaMemsetAsync(c->f64, 0, sizeof(dvec4) * N, c->st));
