@@ -39,6 +39,7 @@ WORKLOADS = {
     "ensemble": "ensemble256",     # 256 independent replicas, one context
     "fcc80": "fcc80_2048000",      # the paper's single-GPU shape; FP64 leg: full list, 1 lane/atom
     "dem": "dem64_1048576",        # spring-dashpot contacts (Eq. 3), 1,048,576 spheres
+    "adjoint": "fcc16_16384",      # differentiable rollout: 200 steps, loss window 50
 }
 # the contact model's parameters for the dem workload (sigma = sphere diameter)
 DEM_PARAMS = dict(sigma=1.0, cutoff=1.0, skin=0.3, dt=0.001)
@@ -583,6 +584,84 @@ def run_dem(args):
     print(json.dumps(line), flush=True)
 
 
+def run_adjoint(args):
+    """The differentiable rollout (16,384 atoms, 200 velocity-Verlet steps,
+    loss = mean PE over the last 50, checkpoints every 10): md_adjoint's
+    forward + reverse sweep timed for both paths against the forward run
+    alone, with the gradients compared to the oracle's FP64 reverse sweep,
+    whose time on the host cores is the CPU baseline."""
+    import torch
+
+    import oracle
+    from paper_2009_07400_gb300 import build, md
+    torch.cuda.set_device(0)
+    build.build()
+    md.load()
+    name = WORKLOADS["adjoint"]
+    s = inputs.workload(name)
+    n = s.n
+    nsteps, window, ckpt = 200, 50, 10
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    res = {}
+    for label, prec in (("mixed", md.MD_MIXED), ("fp64", md.MD_FP64)):
+        with md.MDContext(s.pos, s.vel, s.box, stream=stream.cuda_stream, precision=prec) as ctx:
+            for _ in range(max(1, args.warmup)):
+                out = ctx.adjoint(nsteps, window, ckpt)
+            torch.cuda.synchronize()
+            reps = max(1, min(args.steps, 5))
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                out = ctx.adjoint(nsteps, window, ckpt)
+            t_adj = (time.perf_counter() - t0) / reps
+            x0, v0 = ctx.positions(), ctx.velocities()
+        with md.MDContext(s.pos, s.vel, s.box, stream=stream.cuda_stream, precision=prec) as ctx:
+            ctx.run(nsteps)
+            ctx.set_state(s.pos, s.vel)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.run(nsteps)
+            torch.cuda.synchronize()
+            t_fwd = time.perf_counter() - t0
+        res[label] = (out, t_adj, t_fwd)
+    t0 = time.perf_counter()
+    ref = oracle.adjoint(s.pos, s.vel, s.box, nsteps, window)
+    t_orc = time.perf_counter() - t0
+
+    def errs(out):
+        loss, ge, gs, gx, gv = out
+        return {"loss_rel": abs(loss - ref[0]) / abs(ref[0]),
+                "d_eps_rel": abs(ge - ref[1]) / abs(ref[1]),
+                "d_sigma_rel": abs(gs - ref[2]) / abs(ref[2]),
+                "d_x0_rel_norm": float(np.linalg.norm(gx - ref[3]) / np.linalg.norm(ref[3])),
+                "d_v0_rel_norm": float(np.linalg.norm(gv - ref[4]) / np.linalg.norm(ref[4]))}
+
+    out_m, t_m, f_m = res["mixed"]
+    out_d, t_d, f_d = res["fp64"]
+    rate = lambda t: n * nsteps / t                          # noqa: E731
+    line = {
+        "metric": "atom-timesteps/s of the differentiated LJ rollout (forward + reverse sweep)",
+        "value": rate(t_m), "unit": UNIT, "n_gpus": 1, "steps": max(1, min(args.steps, 5)),
+        "warmup": args.warmup, "ms_per_step": t_m * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64 (mixed forward, FP64 adjoint accumulation)", "data": "synthetic",
+        "config": {"workload": f"LJ FCC 16^3, {n:,} atoms, rho 0.8442, T 1.44, {nsteps} steps, "
+                               f"loss = mean PE over the last {window}, checkpoints every {ckpt}, "
+                               "gradients w.r.t. epsilon, sigma, x0, v0", "atoms": n,
+                   "timesteps_per_step": nsteps, "seed": inputs.WORKLOADS[name]["seed"]},
+        "adjoint_over_forward": {"mixed": t_m / f_m, "fp64": t_d / f_d},
+        "fp64_path": {"value": rate(t_d), "ms_per_step": t_d * 1e3},
+        "gradient_error_vs_oracle": {"mixed": errs(out_m), "fp64": errs(out_d)},
+        "cpu_baseline": {"value": rate(t_orc), "unit": UNIT, "cores": oracle.num_threads(),
+                         "kind": "oracle",
+                         "sample": f"the oracle's FP64 reverse sweep of the same rollout "
+                                   f"({t_orc:.2f} s, OpenMP {oracle.num_threads()} threads)"},
+        "timing": "host wall clock around md_adjoint (it synchronises: loss and gradients "
+                  "are returned in host memory)",
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_ncu_case(which):
     """Create the workload's context and run 2 cycles: 1 first drift, then
     per cycle 19 fused steps, a rebuild (6 binning kernels + build) and the
@@ -627,6 +706,13 @@ def main():
         args.warmup = 3
     if args.ncu_case:
         run_ncu_case(args.ncu_case)
+    elif args.workload == "adjoint":
+        if args.impl == "native":
+            run_adjoint(args)
+        else:
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle arm covers the "
+                              "forward workloads; the adjoint line carries its own "
+                              "cpu_baseline"}), flush=True)
     elif args.workload == "dem":
         if args.impl == "native":
             run_dem(args)
