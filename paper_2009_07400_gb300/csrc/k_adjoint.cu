@@ -17,7 +17,9 @@
 //     df/deps = f/eps,  df/dsigma = 144 eps sr2 t (4t - 1) / sigma,
 //     V = 4 eps t (t - 1),  dV/dsigma = 24 eps t (2t - 1) / sigma.
 // rc is held fixed; pairs crossing it are a measure-zero set whose jump the
-// derivative ignores.  Adjoint vectors live in caller order (the atom order
+// derivative ignores.  The FP64 path evaluates the pair terms in FP64; the
+// mixed path in FP32 (its forward forces are FP32 too), with per-atom sums
+// added to the FP64 adjoint state.  Adjoint vectors live in caller order (the atom order
 // changes at every rebuild); one thread per atom of the cell-ordered state
 // owns the caller-order entry of its atom, so no atomics are needed.
 #include "md_internal.cuh"
@@ -31,7 +33,18 @@ __device__ __forceinline__ bool stopped(const DevStatus *st)
     return *((volatile const int32_t *)&st->flags) != 0;
 }
 
+// FP64 reciprocal: correctly rounded FP32 seed, two Newton steps (relative
+// error below FP64 rounding); avoids an FP64 division per pair on GB300's
+// narrow FP64 pipe.
+__device__ __forceinline__ double rcp64(double a)
+{
+    double r = (double)__frcp_rn((float)a);
+    r = fma(r, fma(-a, r, 1.0), r);
+    return fma(r, fma(-a, r, 1.0), r);
+}
+
 struct AdjArgs {
+    const float4 *wbar32; // FP32 copy of wbar (mixed path)
     const dvec4 *wbar;   // dloss/dw (caller order)
     dvec4 *xbar;         // dloss/dx carry (caller order), updated
     double *g_eps;       // per-atom accumulators (caller order)
@@ -40,9 +53,9 @@ struct AdjArgs {
     double lw;           // 1/W inside the loss window, else 0
 };
 
-// FP64 pair geometry: the image shift of the neighbour's stencil slot is added
-// to (x_i - x_j) as the minimum-image branch would.
-template <bool MIXED>
+// FP64 path: FP64 pair geometry (the image shift of the neighbour's stencil
+// slot is added to (x_i - x_j) as the minimum-image branch would) and FP64
+// arithmetic.
 __global__ void __launch_bounds__(128) k_adjoint_pairs(Dev d, LJ lj, AdjArgs a)
 {
     if (stopped(d.status)) return;
@@ -63,6 +76,7 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs(Dev d, LJ lj, AdjArgs a)
     const int cnt = MD_CHECK(d, d.nb_count[i] <= d.cap) ? d.nb_count[i] : 0;
     const int4 *nb4 = reinterpret_cast<const int4 *>(d.nb);
     const double eps = lj.eps, sigma6 = lj.sigma6, sigma = lj.sigma;
+    const double inv_eps = 1.0 / eps, inv_sigma = 1.0 / sigma;   // once per atom
     double jx = 0, jy = 0, jz = 0, fx = 0, fy = 0, fz = 0, ge = 0, gs = 0, pe_e = 0, pe_s = 0;
     for (int k = 0; k < cnt; k++) {
         const int4 e4 = nb4[(int64_t)(k >> 2) * d.n + i];
@@ -71,25 +85,14 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs(Dev d, LJ lj, AdjArgs a)
         const int ox = (int)(code & 3u) - 1, oy = (int)((code >> 2) & 3u) - 1, oz = (int)(code >> 4) - 1;
         const int32_t j = (int32_t)((uint32_t)e & kJMask);
         if (!MD_CHECK(d, j <= d.n)) continue;
-        double dx, dy, dz;
-        if (MIXED) {
-            // cell-relative FP32 geometry, as in the mixed force kernel
-            const float4 pj = d.p32[j];
-            dx = (double)fmaf((float)ox, R.nsf[0], pi.x - pj.x);
-            dy = (double)fmaf((float)oy, R.nsf[1], pi.y - pj.y);
-            dz = (double)fmaf((float)oz, R.nsf[2], pi.z - pj.z);
-        } else {
-            const dvec4 xj = d.x[j];
-            dx = xi.x - xj.x;
-            dy = xi.y - xj.y;
-            dz = xi.z - xj.z;
-            if (ox) dx = dx + (ox < 0 ? lo[0] : hi[0]);
-            if (oy) dy = dy + (oy < 0 ? lo[1] : hi[1]);
-            if (oz) dz = dz + (oz < 0 ? lo[2] : hi[2]);
-        }
+        const dvec4 xj = d.x[j];
+        double dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+        if (ox) dx = dx + (ox < 0 ? lo[0] : hi[0]);
+        if (oy) dy = dy + (oy < 0 ? lo[1] : hi[1]);
+        if (oz) dz = dz + (oz < 0 ? lo[2] : hi[2]);
         const double rsq = dx * dx + dy * dy + dz * dz;
         if (!(rsq < lj.rc2)) continue;
-        const double sr2 = 1.0 / rsq;
+        const double sr2 = rcp64(rsq);
         const double t = sr2 * sr2 * sr2 * sigma6;
         const double f = 48.0 * eps * t * (t - 0.5) * sr2;
         const double fp = 48.0 * eps * sr2 * sr2 * t * (2.0 - 7.0 * t);
@@ -100,13 +103,13 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs(Dev d, LJ lj, AdjArgs a)
         jy += f * duy + 2.0 * fp * dy * ddu;
         jz += f * duz + 2.0 * fp * dz * ddu;
         const double dui = dx * ui.x + dy * ui.y + dz * ui.z;
-        ge += (f / eps) * dui;
-        gs += (144.0 * eps * sr2 * t * (4.0 * t - 1.0) / sigma) * dui;
+        ge += (f * inv_eps) * dui;
+        gs += (144.0 * eps * sr2 * t * (4.0 * t - 1.0) * inv_sigma) * dui;
         fx += f * dx;
         fy += f * dy;
         fz += f * dz;
         pe_e += 0.5 * 4.0 * t * (t - 1.0);
-        pe_s += 0.5 * 24.0 * eps * t * (2.0 * t - 1.0) / sigma;
+        pe_s += 0.5 * 24.0 * eps * t * (2.0 * t - 1.0) * inv_sigma;
     }
     dvec4 xb = a.xbar[idi];
     xb.x += a.k * jx - a.lw * fx;
@@ -117,8 +120,69 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs(Dev d, LJ lj, AdjArgs a)
     a.g_sig[idi] += a.k * gs + a.lw * pe_s;
 }
 
+// Mixed path: the same pair terms in FP32 (geometry from the cell-relative
+// FP32 positions, the neighbour's adjoint from an FP32 copy), summed per atom
+// in FP32 and added to the FP64 adjoint state once per atom.  The FP64 pipe
+// then only sees the per-atom updates.
+__global__ void __launch_bounds__(128) k_adjoint_pairs_f32(Dev d, LJ lj, AdjArgs a)
+{
+    if (stopped(d.status)) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.n) return;
+    const Rep &R = d.reps[0];
+    const int32_t idi = d.id[i];
+    const float4 pi = d.p32[i];
+    const float4 ui = a.wbar32[idi];
+    const int cnt = MD_CHECK(d, d.nb_count[i] <= d.cap) ? d.nb_count[i] : 0;
+    const int4 *nb4 = reinterpret_cast<const int4 *>(d.nb);
+    const float eps = (float)lj.eps, sig6 = lj.sigma6f;
+    const float inv_eps = (float)(1.0 / lj.eps), inv_sig = (float)(1.0 / lj.sigma);
+    const float qx0 = pi.x - R.nsf[0], qx2 = pi.x + R.nsf[0];
+    const float qy0 = pi.y - R.nsf[1], qy2 = pi.y + R.nsf[1];
+    const float qz0 = pi.z - R.nsf[2], qz2 = pi.z + R.nsf[2];
+    float jx = 0, jy = 0, jz = 0, fx = 0, fy = 0, fz = 0, ge = 0, gs = 0, pe_e = 0, pe_s = 0;
+    for (int k = 0; k < cnt; k++) {
+        const int4 e4 = nb4[(int64_t)(k >> 2) * d.n + i];
+        const uint32_t e = (uint32_t)((k & 3) == 0 ? e4.x : (k & 3) == 1 ? e4.y : (k & 3) == 2 ? e4.z : e4.w);
+        const uint32_t c = e >> kJBits;
+        const int32_t j = (int32_t)(e & kJMask);
+        if (!MD_CHECK(d, j <= d.n)) continue;
+        const float4 pj = d.p32[j];
+        const float dx = ((c & 2u) ? qx2 : ((c & 1u) ? pi.x : qx0)) - pj.x;
+        const float dy = ((c & 8u) ? qy2 : ((c & 4u) ? pi.y : qy0)) - pj.y;
+        const float dz = ((c & 32u) ? qz2 : ((c & 16u) ? pi.z : qz0)) - pj.z;
+        const float rsq = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        if (!(rsq < lj.rc2f)) continue;
+        const float sr2 = 1.0f / rsq;
+        const float t = sr2 * sr2 * sr2 * sig6;
+        const float f = 48.0f * eps * t * (t - 0.5f) * sr2;
+        const float fp = 48.0f * eps * sr2 * sr2 * t * (2.0f - 7.0f * t);
+        const float4 uj = a.wbar32[d.id[j]];
+        const float dux = ui.x - uj.x, duy = ui.y - uj.y, duz = ui.z - uj.z;
+        const float ddu = fmaf(dz, duz, fmaf(dy, duy, dx * dux));
+        jx += f * dux + 2.0f * fp * dx * ddu;
+        jy += f * duy + 2.0f * fp * dy * ddu;
+        jz += f * duz + 2.0f * fp * dz * ddu;
+        const float dui = fmaf(dz, ui.z, fmaf(dy, ui.y, dx * ui.x));
+        ge += (f * inv_eps) * dui;
+        gs += (144.0f * eps * sr2 * t * (4.0f * t - 1.0f) * inv_sig) * dui;
+        fx += f * dx;
+        fy += f * dy;
+        fz += f * dz;
+        pe_e += 2.0f * t * (t - 1.0f);
+        pe_s += 12.0f * eps * t * (2.0f * t - 1.0f) * inv_sig;
+    }
+    dvec4 xb = a.xbar[idi];
+    xb.x += a.k * (double)jx - a.lw * (double)fx;
+    xb.y += a.k * (double)jy - a.lw * (double)fy;
+    xb.z += a.k * (double)jz - a.lw * (double)fz;
+    a.xbar[idi] = xb;
+    a.g_eps[idi] += a.k * (double)ge + a.lw * (double)pe_e;
+    a.g_sig[idi] += a.k * (double)gs + a.lw * (double)pe_s;
+}
+
 __global__ void __launch_bounds__(256) k_adjoint_axpy(int64_t n, double dt, const dvec4 *xbar,
-                                                      dvec4 *wbar)
+                                                      dvec4 *wbar, float4 *wbar32)
 {
     const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= n) return;
@@ -128,6 +192,7 @@ __global__ void __launch_bounds__(256) k_adjoint_axpy(int64_t n, double dt, cons
     w.y = fma(dt, x.y, w.y);
     w.z = fma(dt, x.z, w.z);
     wbar[a] = w;
+    if (wbar32) wbar32[a] = make_float4((float)w.x, (float)w.y, (float)w.z, 0.f);
 }
 
 // Deterministic sum of two per-atom arrays (one block, fixed order).
@@ -157,22 +222,26 @@ __global__ void __launch_bounds__(1024) k_sum2(int64_t n, const double *a, const
 
 }  // namespace
 
-int launch_adjoint_pairs(const Dev &d, const LJ &lj, bool mixed, const dvec4 *wbar, dvec4 *xbar,
-                         double *g_eps, double *g_sig, double k, double lw, cudaStream_t st,
-                         int *nl)
+int launch_adjoint_pairs(const Dev &d, const LJ &lj, bool mixed, const dvec4 *wbar,
+                         const float4 *wbar32, dvec4 *xbar, double *g_eps, double *g_sig,
+                         double k, double lw, cudaStream_t st, int *nl)
 {
-    AdjArgs a{wbar, xbar, g_eps, g_sig, k, lw};
+    AdjArgs a{wbar32, wbar, xbar, g_eps, g_sig, k, lw};
     const unsigned g = (unsigned)((d.n + 127) / 128);
-    if (mixed) k_adjoint_pairs<true><<<g, 128, 0, st>>>(d, lj, a);
-    else k_adjoint_pairs<false><<<g, 128, 0, st>>>(d, lj, a);
+    if (mixed) {
+        if (!wbar32) return -1;
+        k_adjoint_pairs_f32<<<g, 128, 0, st>>>(d, lj, a);
+    } else {
+        k_adjoint_pairs<<<g, 128, 0, st>>>(d, lj, a);
+    }
     *nl += 1;
     return (int)cudaGetLastError();
 }
 
-int launch_adjoint_axpy(int64_t n, double dt, const dvec4 *xbar, dvec4 *wbar, cudaStream_t st,
-                        int *nl)
+int launch_adjoint_axpy(int64_t n, double dt, const dvec4 *xbar, dvec4 *wbar, float4 *wbar32,
+                        cudaStream_t st, int *nl)
 {
-    k_adjoint_axpy<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, dt, xbar, wbar);
+    k_adjoint_axpy<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, dt, xbar, wbar, wbar32);
     *nl += 1;
     return (int)cudaGetLastError();
 }

@@ -1151,19 +1151,20 @@ int md_adjoint(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt, double *
     if (half0 && (rc = apply_tuning(c, 1, 0))) return rc;   // the adjoint walks full lists
 
     dvec4 *ck_x = nullptr, *ck_v = nullptr, *blk_x = nullptr, *xbar = nullptr, *wbar = nullptr;
-    float4 *blk_p = nullptr, *ck_p = nullptr;
+    float4 *blk_p = nullptr, *ck_p = nullptr, *wbar32 = nullptr;
     int32_t *ck_id = nullptr;
     double *ge = nullptr, *gs = nullptr, *g2 = nullptr;
     auto cleanup = [&]() {
         cudaFree(ck_x); cudaFree(ck_v); cudaFree(ck_id); cudaFree(ck_p); cudaFree(blk_x); cudaFree(blk_p);
-        cudaFree(xbar); cudaFree(wbar); cudaFree(ge); cudaFree(gs); cudaFree(g2);
+        cudaFree(xbar); cudaFree(wbar); cudaFree(wbar32); cudaFree(ge); cudaFree(gs); cudaFree(g2);
     };
     if ((rc = dalloc(c, &ck_x, (size_t)(nck * n))) || (rc = dalloc(c, &ck_v, (size_t)(nck * n))) ||
         (rc = dalloc(c, &ck_id, (size_t)(nck * n))) || (rc = dalloc(c, &ck_p, (size_t)(nck * n))) ||
         (rc = dalloc(c, &blk_x, (size_t)(ckpt * n))) ||
         (rc = dalloc(c, &blk_p, (size_t)(ckpt * n))) || (rc = dalloc(c, &xbar, (size_t)n)) ||
         (rc = dalloc(c, &wbar, (size_t)n)) || (rc = dalloc(c, &ge, (size_t)n)) ||
-        (rc = dalloc(c, &gs, (size_t)n)) || (rc = dalloc(c, &g2, 2))) {
+        (rc = dalloc(c, &gs, (size_t)n)) || (rc = dalloc(c, &g2, 2)) ||
+        (mixed && (rc = dalloc(c, &wbar32, (size_t)n)))) {
         cleanup();
         return rc;
     }
@@ -1239,6 +1240,7 @@ int md_adjoint(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt, double *
     // ---- reverse sweep ------------------------------------------------------
     CK(cudaMemsetAsync(xbar, 0, sizeof(dvec4) * n, c->st));
     CK(cudaMemsetAsync(wbar, 0, sizeof(dvec4) * n, c->st));
+    if (wbar32) CK(cudaMemsetAsync(wbar32, 0, sizeof(float4) * n, c->st));
     CK(cudaMemsetAsync(ge, 0, sizeof(double) * n, c->st));
     CK(cudaMemsetAsync(gs, 0, sizeof(double) * n, c->st));
     const double cdt = c->lj.half_dt_m;
@@ -1259,13 +1261,13 @@ int md_adjoint(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt, double *
             const int64_t pt = cb + m;
             cudaMemcpyAsync(c->x[c->xp], blk_x + m * n, sizeof(dvec4) * n, cudaMemcpyDeviceToDevice, c->st);
             cudaMemcpyAsync(c->p32[c->pb], blk_p + m * n, sizeof(float4) * n, cudaMemcpyDeviceToDevice, c->st);
-            if (pt < nsteps && launch_adjoint_axpy(n, c->lj.dt, xbar, wbar, c->st, &nl)) {
+            if (pt < nsteps && launch_adjoint_axpy(n, c->lj.dt, xbar, wbar, wbar32, c->st, &nl)) {
                 rc = fail(c, MD_ERR_CUDA, "adjoint launch failed");
                 break;
             }
             const double k = pt == nsteps ? 0.0 : (pt == 0 ? cdt : 2.0 * cdt);
             const double lw = pt > nsteps - window ? 1.0 / (double)window : 0.0;
-            if (launch_adjoint_pairs(view(c), c->lj, mixed, wbar, xbar, ge, gs, k, lw, c->st, &nl)) {
+            if (launch_adjoint_pairs(view(c), c->lj, mixed, wbar, wbar32, xbar, ge, gs, k, lw, c->st, &nl)) {
                 rc = fail(c, MD_ERR_CUDA, "adjoint launch failed");
                 break;
             }
