@@ -56,6 +56,7 @@ struct AdjArgs {
 // FP64 path: FP64 pair geometry (the image shift of the neighbour's stencil
 // slot is added to (x_i - x_j) as the minimum-image branch would) and FP64
 // arithmetic.
+template <bool WINDOW>
 __global__ void __launch_bounds__(128) k_adjoint_pairs(Dev d, LJ lj, AdjArgs a)
 {
     if (stopped(d.status)) return;
@@ -78,8 +79,10 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs(Dev d, LJ lj, AdjArgs a)
     const double eps = lj.eps, sigma6 = lj.sigma6, sigma = lj.sigma;
     const double inv_eps = 1.0 / eps, inv_sigma = 1.0 / sigma;   // once per atom
     double jx = 0, jy = 0, jz = 0, fx = 0, fy = 0, fz = 0, ge = 0, gs = 0, pe_e = 0, pe_s = 0;
+    int4 e4 = make_int4(0, 0, 0, 0);
+    // each int4 chunk of the row is loaded once
     for (int k = 0; k < cnt; k++) {
-        const int4 e4 = nb4[(int64_t)(k >> 2) * d.n + i];
+        if ((k & 3) == 0) e4 = nb4[(int64_t)(k >> 2) * d.n + i];
         const int32_t e = (k & 3) == 0 ? e4.x : (k & 3) == 1 ? e4.y : (k & 3) == 2 ? e4.z : e4.w;
         const uint32_t code = (uint32_t)e >> kJBits;
         const int ox = (int)(code & 3u) - 1, oy = (int)((code >> 2) & 3u) - 1, oz = (int)(code >> 4) - 1;
@@ -105,11 +108,13 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs(Dev d, LJ lj, AdjArgs a)
         const double dui = dx * ui.x + dy * ui.y + dz * ui.z;
         ge += (f * inv_eps) * dui;
         gs += (144.0 * eps * sr2 * t * (4.0 * t - 1.0) * inv_sigma) * dui;
-        fx += f * dx;
-        fy += f * dy;
-        fz += f * dz;
-        pe_e += 0.5 * 4.0 * t * (t - 1.0);
-        pe_s += 0.5 * 24.0 * eps * t * (2.0 * t - 1.0) * inv_sigma;
+        if (WINDOW) {   // -F/W and dPE/dtheta: only inside the loss window
+            fx += f * dx;
+            fy += f * dy;
+            fz += f * dz;
+            pe_e += 0.5 * 4.0 * t * (t - 1.0);
+            pe_s += 0.5 * 24.0 * eps * t * (2.0 * t - 1.0) * inv_sigma;
+        }
     }
     dvec4 xb = a.xbar[idi];
     xb.x += a.k * jx - a.lw * fx;
@@ -124,6 +129,7 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs(Dev d, LJ lj, AdjArgs a)
 // FP32 positions, the neighbour's adjoint from an FP32 copy), summed per atom
 // in FP32 and added to the FP64 adjoint state once per atom.  The FP64 pipe
 // then only sees the per-atom updates.
+template <bool WINDOW>
 __global__ void __launch_bounds__(128) k_adjoint_pairs_f32(Dev d, LJ lj, AdjArgs a)
 {
     if (stopped(d.status)) return;
@@ -141,8 +147,9 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs_f32(Dev d, LJ lj, AdjArgs
     const float qy0 = pi.y - R.nsf[1], qy2 = pi.y + R.nsf[1];
     const float qz0 = pi.z - R.nsf[2], qz2 = pi.z + R.nsf[2];
     float jx = 0, jy = 0, jz = 0, fx = 0, fy = 0, fz = 0, ge = 0, gs = 0, pe_e = 0, pe_s = 0;
+    int4 e4 = make_int4(0, 0, 0, 0);
     for (int k = 0; k < cnt; k++) {
-        const int4 e4 = nb4[(int64_t)(k >> 2) * d.n + i];
+        if ((k & 3) == 0) e4 = nb4[(int64_t)(k >> 2) * d.n + i];
         const uint32_t e = (uint32_t)((k & 3) == 0 ? e4.x : (k & 3) == 1 ? e4.y : (k & 3) == 2 ? e4.z : e4.w);
         const uint32_t c = e >> kJBits;
         const int32_t j = (int32_t)(e & kJMask);
@@ -166,11 +173,13 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs_f32(Dev d, LJ lj, AdjArgs
         const float dui = fmaf(dz, ui.z, fmaf(dy, ui.y, dx * ui.x));
         ge += (f * inv_eps) * dui;
         gs += (144.0f * eps * sr2 * t * (4.0f * t - 1.0f) * inv_sig) * dui;
-        fx += f * dx;
-        fy += f * dy;
-        fz += f * dz;
-        pe_e += 2.0f * t * (t - 1.0f);
-        pe_s += 12.0f * eps * t * (2.0f * t - 1.0f) * inv_sig;
+        if (WINDOW) {
+            fx += f * dx;
+            fy += f * dy;
+            fz += f * dz;
+            pe_e += 2.0f * t * (t - 1.0f);
+            pe_s += 12.0f * eps * t * (2.0f * t - 1.0f) * inv_sig;
+        }
     }
     dvec4 xb = a.xbar[idi];
     xb.x += a.k * (double)jx - a.lw * (double)fx;
@@ -228,11 +237,14 @@ int launch_adjoint_pairs(const Dev &d, const LJ &lj, bool mixed, const dvec4 *wb
 {
     AdjArgs a{wbar32, wbar, xbar, g_eps, g_sig, k, lw};
     const unsigned g = (unsigned)((d.n + 127) / 128);
+    const bool win = lw != 0.0;
     if (mixed) {
         if (!wbar32) return -1;
-        k_adjoint_pairs_f32<<<g, 128, 0, st>>>(d, lj, a);
+        if (win) k_adjoint_pairs_f32<true><<<g, 128, 0, st>>>(d, lj, a);
+        else k_adjoint_pairs_f32<false><<<g, 128, 0, st>>>(d, lj, a);
     } else {
-        k_adjoint_pairs<<<g, 128, 0, st>>>(d, lj, a);
+        if (win) k_adjoint_pairs<true><<<g, 128, 0, st>>>(d, lj, a);
+        else k_adjoint_pairs<false><<<g, 128, 0, st>>>(d, lj, a);
     }
     *nl += 1;
     return (int)cudaGetLastError();
