@@ -159,6 +159,20 @@ def ncu_traffic():
     return float(t.group(1)) if h.group(1) == cur else None
 
 
+def parse_tuned(text):
+    """--tuned "TPA,HALF,TPA64,HALF64" -> ({mixed kwargs}, {FP64 kwargs}) or
+    None.  Skips the autotuner: under a profiler its timings include the
+    profiler's per-launch overhead and it may choose another candidate than
+    the timed run did, so profiling commands pin the timed run's choice."""
+    if not text:
+        return None
+    v = [int(x) for x in text.split(",")]
+    if len(v) != 4 or v[0] not in (1, 2, 4) or v[2] not in (1, 2, 4):
+        raise SystemExit("--tuned wants TPA,HALF,TPA64,HALF64 with TPA in {1,2,4}")
+    return (dict(threads_per_atom=v[0], half_list=bool(v[1])),
+            dict(threads_per_atom=v[2], half_list=bool(v[3])))
+
+
 def algorithmic_bytes_per_atom(mean_nb, half):
     """DRAM bytes per atom and time step the dominant kernel must move.
     Full list (force kernel with the fused velocity-Verlet epilogue): the
@@ -223,9 +237,14 @@ def run_gpu(args):
         return md.MDContext(pos, vel, box, counts=counts, stream=sh, **kw)
 
     res = {}
-    with make(precision=md.MD_MIXED) as ctx:
-        tuned = ctx.autotune(STEPS_PER_CYCLE)
-        res["tuned"] = {"threads_per_atom": tuned.threads_per_atom, "half_list": bool(tuned.half_list)}
+    pin = parse_tuned(args.tuned)
+    with make(precision=md.MD_MIXED, **(pin[0] if pin else {})) as ctx:
+        if pin:
+            res["tuned"] = dict(pin[0], pinned=True)
+        else:
+            tuned = ctx.autotune(STEPS_PER_CYCLE)
+            res["tuned"] = {"threads_per_atom": tuned.threads_per_atom,
+                            "half_list": bool(tuned.half_list)}
         with ClockSampler(local) as clk:
             ms, launches = time_cycles(ctx, args.steps, args.warmup, dist, torch)
         res["mixed_ms"] = ms
@@ -248,9 +267,13 @@ def run_gpu(args):
     # paper-shaped workload keeps that layout for its FP64 leg
     paper_shaped = name == "fcc80_2048000"
     fp64_kw = dict(half_list=False, threads_per_atom=1) if paper_shaped else {}
+    if pin and not paper_shaped:
+        fp64_kw = pin[1]
     with make(precision=md.MD_FP64, **fp64_kw) as ctx:
         if paper_shaped:
             res["tuned64"] = {"threads_per_atom": 1, "half_list": False, "paper_shaped": True}
+        elif pin:
+            res["tuned64"] = dict(pin[1], pinned=True)
         else:
             t64 = ctx.autotune(STEPS_PER_CYCLE)
             res["tuned64"] = {"threads_per_atom": t64.threads_per_atom,
@@ -698,6 +721,9 @@ def main():
                          "8,388,608-atom sizing run; ensemble: 256 replicas; fcc80: the "
                          "paper's 2,048,000-atom GPU shape; dem: 1,048,576 spheres with "
                          "the contact model of Eq. 3")
+    ap.add_argument("--tuned", metavar="TPA,HALF,TPA64,HALF64",
+                    help="skip the autotuner and use these lanes per atom and list "
+                         "types for the mixed and FP64 legs (for profiling commands)")
     ap.add_argument("--ncu-case", choices=["mixed", "fp64", "dem"],
                     help="only build the workload and run 2 rebuild cycles (a short, "
                          "fixed launch sequence for an ncu capture); prints nothing")

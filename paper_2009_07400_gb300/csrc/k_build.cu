@@ -36,6 +36,8 @@
 // (overflow flag).
 #include "md_internal.cuh"
 
+#include <type_traits>
+
 namespace mdk {
 
 namespace {
@@ -90,6 +92,8 @@ __device__ __forceinline__ int32_t build_row(const Dev &d, const LJ &lj, int64_t
     const float lo = lj.rs2f_lo, hi = lj.rs2f_hi;
 
     int32_t cnt = 0;
+    int32_t *wp = row;                    // address of entry cnt
+    const int64_t wstep = 4 * n - 3;      // from entry 4q+3 to entry 4q+4
     bool have_xi = false;
     dvec4 xi = mk_dvec4(0, 0, 0, 0);
 
@@ -128,24 +132,47 @@ __device__ __forceinline__ int32_t build_row(const Dev &d, const LJ &lj, int64_t
                                                     __dmul_rn(tz, tz));
                         if (!(r2 < lj.rs2)) return;
                     }
-                    if (cnt < cap) row[(int64_t)(cnt >> 2) * 4 * n + (cnt & 3)] = (int32_t)((uint32_t)j | tag);
+                    if (cnt < cap) *wp = (int32_t)((uint32_t)j | tag);
+                    wp += ((cnt & 3) == 3) ? wstep : 1;
                     cnt++;
                 };
-                // hot loop: a bit per candidate inside the FP32 band's upper
-                // edge (about 1 in 6), independent loads; then the hits
+                // hot loop, 32 candidates at a time: a candidate clearly
+                // inside (FP32 r^2 below the band) is appended at once by a
+                // predicated store, so the lanes of a warp stay converged;
+                // the few in the band (and, in half lists, those whose
+                // ownership the FP32 sign cannot decide) are marked and go
+                // through accept() after the chunk
                 for (int32_t jb = j0; jb < j1; jb += 32) {
                     const int m = min(32, (int)(j1 - jb));
-                    uint32_t hits = 0;
+                    uint32_t slow = 0;
+                    // CAP: the row may reach its capacity within this chunk
+                    // (the per-candidate test costs ~7 % of the build, so it
+                    // is compiled in only where it can matter)
+                    auto scan = [&](auto CAP) {
 #pragma unroll 4
-                    for (int t = 0; t < m; t++) {
-                        const float4 pj = __ldg(p32 + jb + t);
-                        const float dx = qx - pj.x, dy = qy - pj.y, dz = qz - pj.z;
-                        const float r2f = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                        hits |= (uint32_t)(r2f < hi) << t;
-                    }
-                    while (hits) {
-                        const int t = __ffs(hits) - 1;
-                        hits &= hits - 1;
+                        for (int t = 0; t < m; t++) {
+                            const int32_t j = jb + t;
+                            const float4 pj = __ldg(p32 + j);
+                            const float dx = qx - pj.x, dy = qy - pj.y, dz = qz - pj.z;
+                            const float r2f = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                            bool in = (r2f < lo) & (j != (int32_t)i);
+                            bool sl = (r2f >= lo) & (r2f < hi);
+                            if (HALF && test_sign) {
+                                const bool amb = fabsf(dz) <= 1e-4f;
+                                sl |= amb & (r2f < lo);
+                                in &= !amb & (dz < 0.f);
+                            }
+                            if (CAP.value ? (in & (cnt < cap)) : in) *wp = (int32_t)((uint32_t)j | tag);
+                            wp += in ? (((cnt & 3) == 3) ? wstep : 1) : 0;
+                            cnt += in;
+                            slow |= (uint32_t)sl << t;
+                        }
+                    };
+                    if (cnt + m <= cap) scan(std::false_type{});
+                    else scan(std::true_type{});
+                    while (slow) {
+                        const int t = __ffs(slow) - 1;
+                        slow &= slow - 1;
                         const int32_t j = jb + t;
                         const float4 pj = __ldg(p32 + j);
                         const float dx = qx - pj.x, dy = qy - pj.y, dz = qz - pj.z;
@@ -163,8 +190,11 @@ __device__ __forceinline__ int32_t build_row(const Dev &d, const LJ &lj, int64_t
     return cnt;
 }
 
+// The explicit minimum of one block per SM matters: with the bare block size
+// ptxas capped the full-list instance at 56 registers and spilled; with it
+// the kernel takes 72 registers (7 blocks of 4 warps per SM) and no spills.
 template <bool BATCHED, bool HALF>
-__global__ void __launch_bounds__(128) k_build(Dev d, LJ lj)
+__global__ void __launch_bounds__(128, 1) k_build(Dev d, LJ lj)
 {
     if (stopped(d.status)) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
