@@ -3,8 +3,10 @@
 //
 // GPU design: a counting sort in four passes over HBM-resident SoA data.
 //   1. k_bin_assign   one thread per atom: wrap x into the box (one
-//                     conditional +/-L per component), cell = (int)(x/s)
-//                     clamped to nc-1, histogram with one atomicAdd.
+//                     conditional +/-L per component, written back only
+//                     when it changed), cell = (int)(x/s) clamped to nc-1,
+//                     histogram with one atomicAdd per distinct cell of a
+//                     warp.
 //   2. scan           exclusive prefix sum of the histogram (three kernels,
 //                     4096 cells per 1024-thread block, warp shuffles).
 //   3. k_bin_scatter  one thread per atom: slot = start + atomicSub(count)-1
@@ -36,29 +38,44 @@ __global__ void __launch_bounds__(256) k_bin_assign(Dev d)
     if (a == 0) d.status->rebuild_count += 1;
     if (a >= d.n) return;
     const Rep &R = d.reps[BATCHED ? d.rep_of[a] : 0];
-    dvec4 x = d.x[a];
+    const dvec4 x = d.x[a];
     double c[3] = {x.x, x.y, x.z};
     int32_t k[3];
     int32_t bad = 0;
+    bool moved = false;
     for (int q = 0; q < 3; q++) {
         double u = c[q];
-        if (!isfinite(u)) { bad |= FLAG_NONFINITE; u = 0.0; }
-        if (u < 0.0) u = u + R.L[q];
-        else if (u >= R.L[q]) u = u - R.L[q];
-        if (u < 0.0 || u > R.L[q]) { bad |= FLAG_BADPOS; u = 0.0; }
+        const double L = R.L[q];
+        // The tests read the IEEE bit patterns as integers (GB300's FP64
+        // pipe is narrow): all-ones exponent = inf or NaN; u < 0 iff the
+        // sign is set and u is not -0.0; and for u >= 0, u >= L iff its
+        // pattern is at least L's.  Only atoms outside [0, L) do FP64 work.
+        const int64_t b = __double_as_longlong(u);
+        if ((b & 0x7ff0000000000000LL) == 0x7ff0000000000000LL) {
+            bad |= FLAG_NONFINITE;
+            u = 0.0;
+            moved = true;
+        } else {
+            const bool neg = b < 0 && b != (int64_t)0x8000000000000000LL;
+            if (neg || b >= __double_as_longlong(L)) {
+                u = neg ? u + L : u - L;
+                if (u < 0.0 || u > L) { bad |= FLAG_BADPOS; u = 0.0; }
+                moved = true;
+            }
+        }
         c[q] = u;
         // (int)(u / s) with the IEEE FP64 quotient.  GB300's FP64 divide is
         // slow, so the quotient is estimated in FP32 (error < 2e-4 for
         // u/s <= 1023) and the exact division runs only when the estimate
         // lies within 1e-3 of an integer, where the two could disagree.
-        const float y = (float)u * (1.0f / (float)R.s[q]);
+        const float y = (float)u * R.invsf[q];
         int32_t kk = (int32_t)y;
         const float fr = y - (float)kk;
         if (fr < 1e-3f || fr > 1.0f - 1e-3f) kk = (int32_t)(u / R.s[q]);
         k[q] = kk >= R.nc[q] ? R.nc[q] - 1 : kk;
     }
     if (bad) atomicOr(&d.status->flags, bad);
-    d.x[a] = mk_dvec4(c[0], c[1], c[2], 0.0);
+    if (moved) d.x[a] = mk_dvec4(c[0], c[1], c[2], 0.0);
     int32_t key = (int32_t)cell_id(R, k[0], k[1], k[2]);
     if (!MD_CHECK(d, key >= 0 && key < d.ncells)) return;
     d.cell_key[a] = key;
@@ -204,9 +221,12 @@ __global__ void __launch_bounds__(256) k_sort_gather(Dev d, int64_t ncells)
         const Rep &R = d.reps[BATCHED ? d.rep_of[ns] : 0];
         int cx, cy, cz;
         cell_coords(R, cell, cx, cy, cz);
-        double px = x.x - ((double)cx + 0.5) * R.s[0];
-        double py = x.y - ((double)cy + 0.5) * R.s[1];
-        double pz = x.z - ((double)cz + 0.5) * R.s[2];
+        // centres (c + 0.5) s from the table the force epilogue uses, so
+        // both compute p = fl32(x - C) from the same C
+        const double *ct = d.ctr + R.ctr_off;
+        const double px = x.x - __ldg(ct + cx);
+        const double py = x.y - __ldg(ct + R.nc[0] + cy);
+        const double pz = x.z - __ldg(ct + R.nc[0] + R.nc[1] + cz);
         uint32_t pack = (uint32_t)cx | ((uint32_t)cy << 10) | ((uint32_t)cz << 20);
         d.p32[ns] = make_float4((float)px, (float)py, (float)pz, __uint_as_float(pack));
     }

@@ -1439,6 +1439,7 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
             if (R.nc[d] > kMaxNc) return fail(c, MD_ERR_INVAL, "more than 1023 cells along a box edge");
             R.s[d] = L[d] / (double)R.nc[d];
             R.nsf[d] = -(float)R.s[d];
+            R.invsf[d] = 1.0f / (float)R.s[d];
             vol *= L[d];
         }
         for (int d = 0; d < 3; d++) R.nt[d] = (R.nc[d] + 1) / 2;

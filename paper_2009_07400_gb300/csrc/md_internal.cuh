@@ -73,6 +73,7 @@ struct Rep {
     double halfL[3];
     double s[3];              // cell side L / nc (FP64)
     float nsf[3];             // -s in FP32 (stencil offsets of the mixed path)
+    float invsf[3];           // fl32(1 / fl32(s)) (binning's quotient estimate)
     int32_t nc[3];
     int32_t nt[3];            // 2x2x2-cell tiles per dimension, (nc + 1) / 2
     int64_t ctr_off;          // first entry of this replica in Dev::ctr
