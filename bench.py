@@ -518,6 +518,12 @@ def run_dem(args):
         with ClockSampler(0) as clk:
             ms, launches = time_cycles(ctx, args.steps, args.warmup, None, torch)
         prof = ctx.profile(2 * STEPS_PER_CYCLE)
+    # force errors at a fixed state, the packing after one cycle of the mixed
+    # path: the packing dissipates energy, and the longer it runs the closer
+    # the net forces come to balance, which inflates a relative error of the
+    # net forces whatever the arithmetic
+    with make(md.MD_MIXED) as ctx:
+        ctx.run(STEPS_PER_CYCLE)
         x, v = ctx.positions(), ctx.velocities()
         ctx.set_state(x, v)
         F_mix = ctx.forces()
@@ -593,7 +599,8 @@ def run_dem(args):
         "force_error": {
             "mixed_rms_rel": float(np.sqrt(np.sum((F_mix - Fr) ** 2) / np.sum(Fr ** 2))),
             "fp64_max_rel": float(np.max(np.linalg.norm(F_64 - Fr, axis=1) / sc)),
-            "sample": "every sphere, final state of the mixed run, oracle list forces"},
+            "sample": "every sphere, the packing after one 20-step cycle of the mixed path, "
+                      "oracle list forces"},
         "e2e": {"value": n * STEPS_PER_CYCLE * e_steps / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(2 * 3 * 8 * n), "d2h_bytes_per_step": 24},
         "gpu_launches": int(launches),

@@ -9,8 +9,10 @@
 //                     warp.
 //   2. scan           exclusive prefix sum of the histogram (three kernels,
 //                     4096 cells per 1024-thread block, warp shuffles).
-//   3. k_bin_scatter  one thread per atom: slot = start + atomicSub(count)-1
-//                     (leaves the histogram at zero for the next binning).
+//   3. k_bin_scatter  one thread per atom: slot = start + count - 1 - rank,
+//                     count taken down by one atomicSub per distinct cell of
+//                     a warp (leaves the histogram at zero for the next
+//                     binning).
 //   4. k_sort_gather  one warp per cell: rank the cell's members by caller
 //                     id (so the order is the stable (cell, id) order,
 //                     independent of atomic arrival order) and gather x, v,
@@ -176,7 +178,16 @@ __global__ void __launch_bounds__(256) k_bin_scatter(Dev d)
     if (a >= d.n) return;
     int32_t key = d.cell_key[a];
     if (!MD_CHECK(d, key >= 0 && key < d.ncells)) return;
-    int32_t pos = d.cell_start[key] + atomicSub(&d.cell_count[key], 1) - 1;
+    // one atomic per distinct cell of the warp (atoms arrive roughly in cell
+    // order); the slots inside a cell are re-ranked by id afterwards, so
+    // their order here does not matter
+    const unsigned same = __match_any_sync(__activemask(), key);
+    const int leader = __ffs(same) - 1;
+    int32_t top = 0;
+    if ((int)(threadIdx.x & 31) == leader) top = atomicSub(&d.cell_count[key], __popc(same));
+    top = __shfl_sync(same, top, leader);
+    const int32_t below = __popc(same & ((1u << (threadIdx.x & 31)) - 1u));
+    int32_t pos = d.cell_start[key] + top - 1 - below;
     if (!MD_CHECK(d, pos >= 0 && pos < d.n)) return;
     d.perm[pos] = (int32_t)a;
 }

@@ -88,7 +88,31 @@ def band_system(seed=5, L=(30.0, 31.0, 29.0)):
 # Binning (Sec. 3.2, Fig. 1)
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("case", ["fcc8", "uniform_nc2", "aniso", "outside"])
+def edge_coordinates(seed=6, L=(9.0, 10.0, 11.0)):
+    """Coordinates on the edges of the wrap and the binning: -0.0, 0, L,
+    the doubles next to 0 and L, -1e-300 (wraps to exactly L, so into the
+    last cell), -L, one box length above, and the cell faces k s and their
+    neighbouring doubles (where the quotient estimate must defer to the
+    exact division)."""
+    rng = np.random.default_rng(seed)
+    L = np.array(L)
+    pos = rng.uniform(0, 1, (240, 3)) * L
+    row = 0
+    for d in range(3):
+        s = L[d] / np.floor(L[d] / (RC + SKIN))
+        faces = [k * s for k in range(1, int(round(L[d] / s)))]
+        vals = [-0.0, 0.0, L[d], np.nextafter(L[d], 0.0), np.nextafter(0.0, 1.0), -1e-300,
+                -L[d], 2 * L[d] - 1e-9, L[d] + 1e-12, np.nextafter(-0.0, -1.0)]
+        for f in faces:
+            vals += [f, np.nextafter(f, 0.0), np.nextafter(f, np.inf), f - L[d], f + L[d]]
+        for v in vals:
+            pos[row, d] = v
+            row += 1
+    assert row <= pos.shape[0]
+    return inputs.System(pos, np.zeros_like(pos), L, seed)
+
+
+@pytest.mark.parametrize("case", ["fcc8", "uniform_nc2", "aniso", "outside", "edges"])
 def test_bin_parity(md, orc, case):
     if case == "fcc8":
         s = inputs.fcc_system(8, seed=1001)
@@ -96,10 +120,12 @@ def test_bin_parity(md, orc, case):
         s = inputs.uniform_box(300, (5.7, 5.7, 5.7), seed=3)
     elif case == "aniso":
         s = inputs.uniform_box(777, (5.7, 9.0, 12.3), seed=4)
-    else:
+    elif case == "outside":
         s = inputs.uniform_box(999, (9.0, 10.0, 11.0), seed=5)
         s.pos[::3] -= s.box          # one box length below
         s.pos[1::7] += s.box * 0.99  # almost one box length above
+    else:
+        s = edge_coordinates()
     with ctx_of(md, s) as ctx:
         start, atoms = ctx.cells()
         _, o_start, o_atoms = orc.bin_cells(orc.wrap(s.pos, s.box), s.box, RC + SKIN)
