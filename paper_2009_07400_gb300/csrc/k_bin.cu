@@ -13,7 +13,8 @@
 //                     count taken down by one atomicSub per distinct cell of
 //                     a warp (leaves the histogram at zero for the next
 //                     binning).
-//   4. k_sort_gather  one warp per cell: rank the cell's members by caller
+//   4. k_sort_gather  a group of 32, 16, 8 or 4 lanes per cell (from the
+//                     mean occupancy): rank the cell's members by caller
 //                     id (so the order is the stable (cell, id) order,
 //                     independent of atomic arrival order) and gather x, v,
 //                     id into the reordered buffers; also writes the
