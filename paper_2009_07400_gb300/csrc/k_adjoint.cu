@@ -35,10 +35,11 @@ __device__ __forceinline__ bool stopped(const DevStatus *st)
 
 // FP64 reciprocal: correctly rounded FP32 seed, two Newton steps (relative
 // error below FP64 rounding); avoids an FP64 division per pair on GB300's
-// narrow FP64 pipe.
+// narrow FP64 pipe (the seed's conversions are integer operations on the
+// bit patterns).
 __device__ __forceinline__ double rcp64(double a)
 {
-    double r = (double)__frcp_rn((float)a);
+    double r = f64_of_pos(__frcp_rn(f32_of_pos(a)));
     r = fma(r, fma(-a, r, 1.0), r);
     return fma(r, fma(-a, r, 1.0), r);
 }
@@ -94,7 +95,7 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs(Dev d, LJ lj, AdjArgs a)
         if (oy) dy = dy + (oy < 0 ? lo[1] : hi[1]);
         if (oz) dz = dz + (oz < 0 ? lo[2] : hi[2]);
         const double rsq = dx * dx + dy * dy + dz * dz;
-        if (!(rsq < lj.rc2)) continue;
+        if (!lt_nonneg(rsq, lj.rc2)) continue;
         const double sr2 = rcp64(rsq);
         const double t = sr2 * sr2 * sr2 * sigma6;
         const double f = 48.0 * eps * t * (t - 0.5) * sr2;

@@ -57,14 +57,15 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float term)
     s = t;
 }
 
-// FP64 reciprocal: a correctly rounded FP32 seed (relative error <= 2^-24)
-// refined by one Newton-Raphson step r <- r + r (1 - a r), which squares the
-// relative error to <= 2^-48 (~4e-15), far inside the FP64 path's 1e-10
-// force tolerance.  Cheaper than an IEEE FP64 division on GB300, whose FP64
-// pipe is the bound of this path.
+// FP64 reciprocal: a correctly rounded FP32 reciprocal of fl32(a) as the
+// seed (relative error <= 2^-23), refined by one Newton-Raphson step
+// r <- r + r (1 - a r), which squares it to <= 2^-46 (~1.4e-14), far inside
+// the FP64 path's 1e-10 force tolerance.  The seed's two conversions run as
+// integer operations on the bit patterns: GB300's FP64 pipe bounds this path,
+// and this keeps it to the two FMAs of the Newton step.
 __device__ __forceinline__ double rcp_nr(double a)
 {
-    const double r = (double)__frcp_rn((float)a);
+    const double r = f64_of_pos(__frcp_rn(f32_of_pos(a)));
     return fma(r, fma(-a, r, 1.0), r);
 }
 
@@ -326,7 +327,9 @@ __device__ __forceinline__ void f64_pair(const Dev &d, const LJ &lj, const dvec4
         if (oz) dz = dz + (oz < 0 ? sh.lo[2] : sh.hi[2]);
     }
     const double rsq = fma(dz, dz, fma(dy, dy, dx * dx));
-    const bool in = rsq < lj.rc2;        // padding points at the far-away sentinel
+    // rsq < rc^2 on the bit patterns (an integer compare instead of an FP64
+    // one); padding points at the far-away sentinel
+    const bool in = lt_nonneg(rsq, lj.rc2);
     const double sr2 = rcp_nr(rsq);
     const double t = sr2 * sr2 * sr2 * lj.sigma6;
     double f = sr2 * t * fma(lj.c48e, t, -lj.c24e);

@@ -150,13 +150,14 @@ __global__ void __launch_bounds__(256) k_force_sd_f64(Dev d, LJ lj)
                 else if (o[k] > 0 && ci[k] == R.nc[k] - 1) dd[k] -= R.L[k];
             }
             const double rsq = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
-            if (!(rsq < lj.sd_sig2)) continue;
+            if (!lt_nonneg(rsq, lj.sd_sig2)) continue;
             const dvec4 vj = ldg_dvec4(d.v + j);
             // 1/r: FP32 reciprocal square root refined by two Newton steps
             // y <- y (3 - rsq y^2) / 2 (relative error 2^-22 -> ~2^-44 ->
             // below FP64 rounding), then r = rsq / r; cheaper on GB300's FP64
-            // pipe than an FP64 square root and two divisions
-            double ir = (double)rsqrtf((float)rsq);
+            // pipe than an FP64 square root and two divisions (the seed's
+            // conversions are integer operations on the bit patterns)
+            double ir = f64_of_pos(rsqrtf(f32_of_pos(rsq)));
             ir = ir * fma(-0.5 * rsq, ir * ir, 1.5);
             ir = ir * fma(-0.5 * rsq, ir * ir, 1.5);
             const double r = rsq * ir;

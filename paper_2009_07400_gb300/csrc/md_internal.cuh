@@ -161,6 +161,31 @@ struct Dev {
 };
 
 #ifdef __CUDACC__
+// Conversions and compares of positive doubles done on their IEEE bit
+// patterns with integer operations: on GB300 the FP64 pipe, which executes
+// FP64 compares and FP64<->FP32 conversions, is a small fraction of the
+// integer and FP32 rates.  Valid for finite a > 0 within FP32's normal range
+// (f32_of_pos) and any finite float > 0 (f64_of_pos).
+constexpr long long kF64F32Rebias = (long long)(1023 - 127) << 23;
+// fl32(a), rounded to nearest with ties away from zero (add half of the 29
+// dropped mantissa bits; a carry moves into the exponent as it should)
+__device__ __forceinline__ float f32_of_pos(double a)
+{
+    const long long b = __double_as_longlong(a);
+    return __int_as_float((int)(((b + (1LL << 28)) >> 29) - kF64F32Rebias));
+}
+// (double)f, exact
+__device__ __forceinline__ double f64_of_pos(float f)
+{
+    return __longlong_as_double(((long long)__float_as_int(f) + kF64F32Rebias) << 29);
+}
+// a < b for a >= +0 and b > 0 (non-negative doubles order like their
+// patterns; a NaN a compares false, as in FP64)
+__device__ __forceinline__ bool lt_nonneg(double a, double b)
+{
+    return __double_as_longlong(a) < __double_as_longlong(b);
+}
+
 // Displacement trigger: flags a rebuild when atom i's new cell-relative
 // position p lies farther than the trigger distance from its position at the
 // last binning (same cell frame, FP32; error ~1e-7 against a trigger distance
