@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(256) k_sort_gather(Dev d, int64_t ncells)
         const double py = x.y - __ldg(ct + R.nc[0] + cy);
         const double pz = x.z - __ldg(ct + R.nc[0] + R.nc[1] + cz);
         uint32_t pack = (uint32_t)cx | ((uint32_t)cy << 10) | ((uint32_t)cz << 20);
-        d.p32[ns] = make_float4((float)px, (float)py, (float)pz, __uint_as_float(pack));
+        d.p32[ns] = make_float4(f32_of_f64(px), f32_of_f64(py), f32_of_f64(pz), __uint_as_float(pack));
     }
 }
 

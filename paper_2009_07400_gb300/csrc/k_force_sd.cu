@@ -53,7 +53,8 @@ __global__ void __launch_bounds__(256) k_velocity_f32(Dev d, float4 *v32)
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i > d.n) return;                     // slot n: the sentinel (zero velocity)
     const dvec4 v = d.v[i];
-    v32[i] = make_float4((float)v.x, (float)v.y, (float)v.z, 0.f);
+    // conversions on the bit patterns (IEEE results, no FP64-pipe work)
+    v32[i] = make_float4(f32_of_f64(v.x), f32_of_f64(v.y), f32_of_f64(v.z), 0.f);
 }
 
 template <bool BATCHED, bool ENERGY>

@@ -25,8 +25,10 @@ __global__ void __launch_bounds__(256) k_integrate(Dev d, LJ lj, int phase, int 
     if (i >= d.n) return;
     double fx, fy, fz;
     if (MIXED) {
+        // conversions on the bit patterns: this kernel is bound by GB300's
+        // narrow FP64 pipe, which would otherwise run them
         const float4 f = d.f32[i];
-        fx = f.x; fy = f.y; fz = f.z;
+        fx = f64_of_f32(f.x); fy = f64_of_f32(f.y); fz = f64_of_f32(f.z);
     } else {
         const dvec4 f = d.f64[i];
         fx = f.x; fy = f.y; fz = f.z;
@@ -56,7 +58,7 @@ __global__ void __launch_bounds__(256) k_integrate(Dev d, LJ lj, int phase, int 
     const double cx = __ldg(ct + (pack & 1023u));
     const double cy = __ldg(ct + R.nc[0] + ((pack >> 10) & 1023u));
     const double cz = __ldg(ct + R.nc[0] + R.nc[1] + ((pack >> 20) & 1023u));
-    const float4 pn = make_float4((float)(x.x - cx), (float)(x.y - cy), (float)(x.z - cz), p.w);
+    const float4 pn = make_float4(f32_of_f64(x.x - cx), f32_of_f64(x.y - cy), f32_of_f64(x.z - cz), p.w);
     d.p32[i] = pn;
     check_displacement(d, i, pn);
 }

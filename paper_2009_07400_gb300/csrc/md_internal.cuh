@@ -186,6 +186,36 @@ __device__ __forceinline__ bool lt_nonneg(double a, double b)
     return __double_as_longlong(a) < __double_as_longlong(b);
 }
 
+// Signed conversions with IEEE results on the bit patterns (checked bit for
+// bit against the hardware conversions on every float and on 6e7 doubles,
+// ties included); the FP64 pipe runs only for the rare operands outside
+// FP32's normal range.  Zero takes the integer path of f64_of_f32.
+// (double)f, exact
+__device__ __forceinline__ double f64_of_f32(float f)
+{
+    const unsigned int u = __float_as_uint(f);
+    const unsigned int mag = u & 0x7fffffffu;
+    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+    if (mag - 0x00800000u < 0x7f000000u)               // normal
+        return __longlong_as_double((long long)(sign | (((unsigned long long)mag + kF64F32Rebias) << 29)));
+    if (mag == 0) return __longlong_as_double((long long)sign);
+    return (double)f;                                   // subnormal, inf, NaN
+}
+// (float)a, rounded to nearest even
+__device__ __forceinline__ float f32_of_f64(double a)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(a);
+    const unsigned long long mag = b & 0x7fffffffffffffffULL;
+    // |a| in [2^-126, 2^128): a normal FP32 result (or an overflow to inf,
+    // which the rounding carry produces)
+    if (mag - 0x3810000000000000ULL < 0x0fe0000000000000ULL) {
+        const unsigned long long r = (mag + 0x0fffffffULL + ((mag >> 29) & 1ULL)) >> 29;
+        return __uint_as_float((unsigned int)((b >> 32) & 0x80000000ULL) |
+                               (unsigned int)(r - (unsigned long long)kF64F32Rebias));
+    }
+    return (float)a;
+}
+
 // Displacement trigger: flags a rebuild when atom i's new cell-relative
 // position p lies farther than the trigger distance from its position at the
 // last binning (same cell frame, FP32; error ~1e-7 against a trigger distance
