@@ -566,10 +566,11 @@ def run_dem(args):
     ts = (time.perf_counter() - t0 - tb) / 4
     cpu_rate = n * STEPS_PER_CYCLE / (max(tb - ts, 0.0) + STEPS_PER_CYCLE * ts)
     kbar = prof.mean_neighbors
-    # per atom: list entries and row length, p_i, v_i (FP32 copy), the force
-    # store, and the FP32 velocity copy pass (read 32 B, write 16 B) that the
-    # timed force phase includes; neighbour gathers come from L2
-    bpa = 4.0 * kbar + 4 + 16 + 16 + 16 + 48
+    # per atom and step of the fused kernel: list entries and row length,
+    # p_i and v_i (FP32 copies) read, the next p32 and v32 written, and read +
+    # write of the FP64 position and velocity (24 B each way); neighbour
+    # gathers come from L2
+    bpa = 4.0 * kbar + 4 + 16 + 16 + 16 + 16 + 2 * 24 + 2 * 24
     launch_ms = prof.force_ms / max(1, prof.force_launches)
     peak, peak_kind = measured_peaks()
     achieved = bpa * n / (launch_ms / 1e3) / 1e9
@@ -586,7 +587,7 @@ def run_dem(args):
                    "timesteps_per_step": STEPS_PER_CYCLE, "seed": inputs.WORKLOADS[name]["seed"]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "k_velocity_f32 + k_force_sd_mixed",
+                     "kernel": "k_force_sd_mixed (fused velocity-Verlet epilogue)",
                      "bytes_per_atom": bpa, "mean_neighbors": kbar, "launch_ms": launch_ms,
                      "peak_source": peak_kind},
         "phases_ms_per_timestep": {"force": prof.force_ms / prof.steps,

@@ -227,9 +227,12 @@ __global__ void __launch_bounds__(256) k_sort_gather(Dev d, int64_t ncells)
         if (!have) continue;
         const int32_t ns = start + rank;
         const dvec4 x = d.x[old];
+        const dvec4 v = d.v[old];
         d.x_alt[ns] = x;
-        d.v_alt[ns] = d.v[old];
+        d.v_alt[ns] = v;
         d.id_alt[ns] = my_id;
+        // contact model, mixed path: the FP32 velocity copies in the new order
+        if (d.v32) d.v32[ns] = make_float4(f32_of_f64(v.x), f32_of_f64(v.y), f32_of_f64(v.z), 0.f);
         const Rep &R = d.reps[BATCHED ? d.rep_of[ns] : 0];
         int cx, cy, cz;
         cell_coords(R, cell, cx, cy, cz);

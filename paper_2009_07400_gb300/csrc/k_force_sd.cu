@@ -8,16 +8,19 @@
 // is cutoff + skin with cutoff >= sigma.
 //
 // GPU mapping: one thread per atom over its full-list row (neighbour-major
-// int4 chunks), like the LJ kernels.  Unlike them the pair term reads the
-// neighbour's velocity, so the step is not fused: this kernel stores the
-// force and the velocity-Verlet update runs in its own kernel afterwards
-// (the velocities the dashpot reads are then those of the half step, the
-// latest ones, as in the oracle).  Mixed path: displacements from the
-// cell-relative FP32 positions plus the stencil offset (as the LJ mixed
-// kernel), velocities from an FP32 copy made before each force pass, FP32
+// int4 chunks), like the LJ kernels.  The pair term reads the neighbours'
+// velocities, those of the half step (the latest ones, as in the oracle).
+// Mixed path: displacements from the cell-relative FP32 positions plus the
+// stencil offset (as the LJ mixed kernel), velocities from FP32 copies, FP32
 // pair arithmetic (r by a correctly rounded square root, since sigma - r
-// cancels) with compensated per-atom sums.  FP64 path: FP64 throughout,
-// 1/r by a refined FP32 estimate (below FP64 rounding after two steps).
+// cancels) with compensated per-atom sums; the velocity-Verlet update is
+// fused into the kernel's epilogue like the LJ step, which writes the next
+// FP32 positions and the next FP32 velocity copies into the other buffers
+// of their pairs (the neighbours still gather this step's), so one launch
+// makes a time step.  FP64 path: FP64 throughout, 1/r by a refined FP32
+// estimate (below FP64 rounding after two steps); it gathers the FP64
+// velocities themselves, so it stores the force and the update runs in its
+// own kernel afterwards.
 #include "md_internal.cuh"
 
 namespace mdk {
@@ -44,21 +47,60 @@ __device__ __forceinline__ float rcp_approx(float a)
     return r;
 }
 
-// FP32 copies of the velocities for the mixed contact kernel (one pass per
-// force evaluation: the neighbour gathers then read 16 B instead of 32 B and
-// convert nothing on GB300's narrow FP64 pipe).
-__global__ void __launch_bounds__(256) k_velocity_f32(Dev d, float4 *v32)
+// FP32 copies of the velocities for the mixed contact kernel (the neighbour
+// gathers then read 16 B instead of 32 B and convert nothing on GB300's
+// narrow FP64 pipe).  The fused step keeps them current; this pass runs only
+// where something else changed the velocities (the first step of a run, a
+// new state, a lone final kick).
+__global__ void __launch_bounds__(256) k_velocity_f32(Dev d)
 {
     if (stopped(d.status)) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i > d.n) return;                     // slot n: the sentinel (zero velocity)
     const dvec4 v = d.v[i];
     // conversions on the bit patterns (IEEE results, no FP64-pipe work)
-    v32[i] = make_float4(f32_of_f64(v.x), f32_of_f64(v.y), f32_of_f64(v.z), 0.f);
+    d.v32[i] = make_float4(f32_of_f64(v.x), f32_of_f64(v.y), f32_of_f64(v.z), 0.f);
 }
 
-template <bool BATCHED, bool ENERGY>
-__global__ void __launch_bounds__(256) k_force_sd_mixed(Dev d, LJ lj, const float4 *v32)
+// Velocity-Verlet epilogue of the mixed contact step, in the operation order
+// of the standalone update (kick; with EPI_FKKD the second kick, the drift,
+// the next p32 and the next v32).  f: the FP32 force on atom i.
+template <int EPI, bool ENERGY>
+__device__ __forceinline__ void sd_epilogue(const Dev &d, const LJ &lj, const Rep &R, int64_t i,
+                                            float4 f, uint32_t pack)
+{
+    if (EPI == EPI_F || EPI == EPI_FK) d.f32[i] = f;
+    if (EPI == EPI_F) return;
+    const double fx = f64_of_f32(f.x), fy = f64_of_f32(f.y), fz = f64_of_f32(f.z);
+    dvec4 v = d.v[i];
+    v.x = fma(lj.half_dt_m, fx, v.x);
+    v.y = fma(lj.half_dt_m, fy, v.y);
+    v.z = fma(lj.half_dt_m, fz, v.z);
+    if (ENERGY) d.ke_atom64[i] = 0.5 * lj.mass * fma(v.x, v.x, fma(v.y, v.y, v.z * v.z));
+    if (EPI == EPI_FKKD) {
+        v.x = fma(lj.half_dt_m, fx, v.x);
+        v.y = fma(lj.half_dt_m, fy, v.y);
+        v.z = fma(lj.half_dt_m, fz, v.z);
+        dvec4 x = d.x[i];
+        x.x = fma(lj.dt, v.x, x.x);
+        x.y = fma(lj.dt, v.y, x.y);
+        x.z = fma(lj.dt, v.z, x.z);
+        d.x[i] = x;                          // neighbours gather p32 and v32 only
+        const double *ct = d.ctr + R.ctr_off;
+        const double cx = __ldg(ct + (pack & 1023u));
+        const double cy = __ldg(ct + R.nc[0] + ((pack >> 10) & 1023u));
+        const double cz = __ldg(ct + R.nc[0] + R.nc[1] + ((pack >> 20) & 1023u));
+        const float4 pn = make_float4(f32_of_f64(x.x - cx), f32_of_f64(x.y - cy),
+                                      f32_of_f64(x.z - cz), __uint_as_float(pack));
+        d.p32_nxt[i] = pn;
+        check_displacement(d, i, pn);
+        d.v32_nxt[i] = make_float4(f32_of_f64(v.x), f32_of_f64(v.y), f32_of_f64(v.z), 0.f);
+    }
+    d.v[i] = v;
+}
+
+template <bool BATCHED, bool ENERGY, int EPI>
+__global__ void __launch_bounds__(256) k_force_sd_mixed(Dev d, LJ lj)
 {
     if (stopped(d.status)) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -66,6 +108,7 @@ __global__ void __launch_bounds__(256) k_force_sd_mixed(Dev d, LJ lj, const floa
     const int64_t n = d.n;
     const Rep &R = d.reps[BATCHED ? d.rep_of[i] : 0];
     const float4 pi = d.p32[i];
+    const float4 *v32 = d.v32;
     const float4 vi = v32[i];
     // p_i - o s for o = -1, 0, +1 (nsf = -s), selected per pair in registers
     const float qx0 = pi.x - R.nsf[0], qx2 = pi.x + R.nsf[0];
@@ -121,11 +164,12 @@ __global__ void __launch_bounds__(256) k_force_sd_mixed(Dev d, LJ lj, const floa
             }
         }
     }
-    d.f32[i] = make_float4(sx - cx, sy - cy, sz - cz, 0.f);
     if (ENERGY) {
         d.pe_atom[i] = 0.5f * (pe - cpe);
         d.w_atom[i] = 0.5f * (w - cw);
     }
+    sd_epilogue<EPI, ENERGY>(d, lj, R, i, make_float4(sx - cx, sy - cy, sz - cz, 0.f),
+                             __float_as_uint(pi.w));
 }
 
 template <bool BATCHED, bool ENERGY>
@@ -194,22 +238,37 @@ __global__ void __launch_bounds__(256) k_force_sd_f64(Dev d, LJ lj)
     }
 }
 
+template <bool B, bool EN>
+void launch_sd_mixed(const Dev &d, const LJ &lj, int epi, unsigned g, cudaStream_t st)
+{
+    if (epi == EPI_F) k_force_sd_mixed<B, EN, EPI_F><<<g, 256, 0, st>>>(d, lj);
+    else if (epi == EPI_FK) k_force_sd_mixed<B, EN, EPI_FK><<<g, 256, 0, st>>>(d, lj);
+    else k_force_sd_mixed<B, EN, EPI_FKKD><<<g, 256, 0, st>>>(d, lj);
+}
+
 }  // namespace
 
-int launch_force_sd(const Dev &d, const LJ &lj, bool mixed, bool energy, float4 *v32,
+int launch_velocity_f32(const Dev &d, cudaStream_t st, int *nl)
+{
+    if (d.n <= 0) return 0;
+    if (!d.v32) return -1;
+    k_velocity_f32<<<(unsigned)((d.n + 256) / 256), 256, 0, st>>>(d);
+    *nl += 1;
+    return (int)cudaGetLastError();
+}
+
+int launch_force_sd(const Dev &d, const LJ &lj, bool mixed, int epi, bool energy,
                     cudaStream_t st, int *nl)
 {
     if (d.n <= 0) return 0;
     const unsigned g = (unsigned)((d.n + 255) / 256);
     const bool b = d.nrep > 1;
     if (mixed) {
-        if (!v32) return -1;
-        k_velocity_f32<<<(unsigned)((d.n + 256) / 256), 256, 0, st>>>(d, v32);
-        *nl += 1;
-        if (b && energy) k_force_sd_mixed<true, true><<<g, 256, 0, st>>>(d, lj, v32);
-        else if (b) k_force_sd_mixed<true, false><<<g, 256, 0, st>>>(d, lj, v32);
-        else if (energy) k_force_sd_mixed<false, true><<<g, 256, 0, st>>>(d, lj, v32);
-        else k_force_sd_mixed<false, false><<<g, 256, 0, st>>>(d, lj, v32);
+        if (!d.v32 || !d.v32_nxt) return -1;
+        if (b && energy) launch_sd_mixed<true, true>(d, lj, epi, g, st);
+        else if (b) launch_sd_mixed<true, false>(d, lj, epi, g, st);
+        else if (energy) launch_sd_mixed<false, true>(d, lj, epi, g, st);
+        else launch_sd_mixed<false, false>(d, lj, epi, g, st);
     } else {
         if (b && energy) k_force_sd_f64<true, true><<<g, 256, 0, st>>>(d, lj);
         else if (b) k_force_sd_f64<true, false><<<g, 256, 0, st>>>(d, lj);

@@ -72,7 +72,9 @@ struct md_ctx {
     int32_t *id[2] = {nullptr, nullptr};
     float4 *p32[2] = {nullptr, nullptr};
     float4 *p32_ref = nullptr;      // displacement trigger: p32 at the last binning
-    float4 *v32 = nullptr;          // contact model, mixed path: FP32 velocity copies
+    float4 *v32[2] = {nullptr, nullptr};   // contact model, mixed path: FP32 velocity
+                                    // copies, same parity as p32
+    bool v32_fresh = false;         // v32[pb] == fl32(v) (else regenerated before a force)
     cudaStream_t side = nullptr;    // displacement trigger: captures the conditional bodies
     bool disp = false;              // md_params.rebuild_every == 0
     float disp2_thr = 0.f;
@@ -154,6 +156,10 @@ Dev view(const md_ctx *c)
     d.ke_atom64 = c->ke64;
     d.status = c->status;
     d.ctr = c->ctr_d;
+    if (c->lj.pot == 1 && c->p.precision == MD_MIXED) {   // contact model, mixed path
+        d.v32 = c->v32[c->pb];
+        d.v32_nxt = c->v32[1 - c->pb];
+    }
     return d;
 }
 
@@ -196,7 +202,7 @@ void free_all(md_ctx *c)
                     c->cell_start, c->perm, c->scan_tmp, c->nb, c->nb_count, c->pe_atom,
                     c->w_atom, c->pe64, c->w64, c->ke64, c->status, c->chunk_rep_d,
                     c->chunk_first_d, c->partials_d, c->eout_d, c->elog_d, c->io_d, c->ctr_d,
-                    c->p32_ref, c->v32};
+                    c->p32_ref, c->v32[0], c->v32[1]};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->own_stream && c->st) cudaStreamDestroy(c->st);
@@ -207,6 +213,8 @@ bool is_mixed(const md_ctx *c) { return c->p.precision == MD_MIXED; }
 bool is_half(const md_ctx *c) { return c->p.half_list != 0; }
 bool is_sd(const md_ctx *c) { return c->lj.pot == 1; }
 bool batched(const md_ctx *c) { return c->nrep > 1; }
+// the contact model's mixed path keeps FP32 velocity copies (v32)
+bool uses_v32(const md_ctx *c) { return c->lj.pot == 1 && c->p.precision == MD_MIXED; }
 
 int32_t round4(int64_t v) { return (int32_t)((v + 3) / 4 * 4); }
 
@@ -229,6 +237,7 @@ int enq_bin(md_ctx *c, int *nl)
     Dev d = view(c);
     if (launch_bin(d, c->nids, c->scan_tmp, c->scan_len, c->st, nl) != 0)
         return fail(c, MD_ERR_CUDA, "binning launch failed");
+    if (d.v32) c->v32_fresh = true;   // the gather writes v32 in the new order
     if (c->disp) {
         // the reordered state is copied back: buffer roles never change
         if (launch_copy_back(d, c->st, nl) != 0) return fail(c, MD_ERR_CUDA, "copy-back launch failed");
@@ -270,11 +279,25 @@ int enq_energy(md_ctx *c, bool ke_from_v, double *out3, int *nl)
 int enq_force(md_ctx *c, int epi, bool energy, int *nl, cudaEvent_t *ev = nullptr)
 {
     Dev d = view(c);
-    if (is_half(c) || is_sd(c)) {
+    if (is_sd(c) && is_mixed(c)) {
+        // contact model, mixed path: one fused kernel; the FP32 velocity
+        // copies are regenerated only when something other than the fused
+        // step or a binning changed v since they were made
+        if (ev) CK(cudaEventRecord(ev[0], c->st));
+        if (!c->v32_fresh) {
+            if (launch_velocity_f32(d, c->st, nl)) return fail(c, MD_ERR_CUDA, "velocity copy launch failed");
+            c->v32_fresh = true;
+        }
+        if (launch_force_sd(d, c->lj, true, epi, energy, c->st, nl))
+            return fail(c, MD_ERR_CUDA, "force launch failed");
+        if (ev) CK(cudaEventRecord(ev[1], c->st));
+        if (epi == EPI_FKKD) c->pb = 1 - c->pb;      // next p32 and v32 written
+        else if (epi == EPI_FK) c->v32_fresh = false;
+    } else if (is_half(c) || is_sd(c)) {
         // force store, then the velocity-Verlet update in its own kernel
         if (ev) CK(cudaEventRecord(ev[0], c->st));
         if (is_sd(c)) {
-            if (launch_force_sd(d, c->lj, is_mixed(c), energy, c->v32, c->st, nl))
+            if (launch_force_sd(d, c->lj, false, EPI_F, energy, c->st, nl))
                 return fail(c, MD_ERR_CUDA, "force launch failed");
         } else {
             if (is_mixed(c)) CK(cudaMemsetAsync(c->f32, 0, sizeof(float4) * c->n, c->st));
@@ -357,6 +380,7 @@ int enq_op(md_ctx *c, const Op &op, int *nl)
             return fail(c, MD_ERR_CUDA, "integrate launch failed");
         c->moved_since_bin = true;
         c->forces_valid = false;
+        c->v32_fresh = false;
     } else if (op.kind == Op::REBUILD) {
         if ((rc = enq_bin(c, nl))) return rc;
         if ((rc = enq_build(c, nl))) return rc;
@@ -376,7 +400,8 @@ int enq_op(md_ctx *c, const Op &op, int *nl)
 
 std::string key_of(const md_ctx *c, const std::vector<Op> &ops)
 {
-    std::string k = std::to_string(c->xp) + std::to_string(c->vp) + std::to_string(c->pb) + ":";
+    std::string k = std::to_string(c->xp) + std::to_string(c->vp) + std::to_string(c->pb) +
+                    (uses_v32(c) && c->v32_fresh ? "f" : "") + ":";
     for (const Op &o : ops) {
         if (o.kind == Op::KD) k += 'K';
         else if (o.kind == Op::REBUILD) k += 'R';
@@ -393,7 +418,8 @@ int run_segment(md_ctx *c, const std::vector<Op> &ops)
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
         const int xp0 = c->xp, vp0 = c->vp, pb0 = c->pb;
-        const bool mv = c->moved_since_bin, lv = c->list_valid, fv = c->forces_valid;
+        const bool mv = c->moved_since_bin, lv = c->list_valid, fv = c->forces_valid,
+                   vf = c->v32_fresh;
         const int64_t be = c->builds_enqueued;
         CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
         int nl = 0, rc = MD_OK;
@@ -418,6 +444,7 @@ int run_segment(md_ctx *c, const std::vector<Op> &ops)
         // capture changed the host bookkeeping; rewind, the replay re-applies it
         c->xp = xp0; c->vp = vp0; c->pb = pb0;
         c->moved_since_bin = mv; c->list_valid = lv; c->forces_valid = fv;
+        c->v32_fresh = vf;
         c->builds_enqueued = be;
     }
     CK(cudaGraphLaunch(it->second.exec, c->st));
@@ -431,13 +458,16 @@ int run_segment(md_ctx *c, const std::vector<Op> &ops)
             c->rebuilds++;
             c->moved_since_bin = false;
             c->list_valid = true;
+            if (uses_v32(c)) c->v32_fresh = true;
         } else if (op.kind == Op::KD) {
             c->moved_since_bin = true;
             c->forces_valid = false;
+            c->v32_fresh = false;
         } else if (op.kind == Op::COND) {
             c->list_valid = true;   // valid under the displacement criterion
         } else {
             c->forces_valid = op.last;
+            if (uses_v32(c)) c->v32_fresh = !op.last;   // fused contact step: next v32 written
             if (!op.last) c->moved_since_bin = true;
         }
     }
@@ -741,6 +771,7 @@ int md_integrate(md_ctx *c, int32_t phase)
     if (launch_integrate(d, c->lj, c->p.precision, phase, batched(c), c->st, &nl))
         return fail(c, MD_ERR_CUDA, "integrate launch failed");
     c->launches += nl;
+    c->v32_fresh = false;
     if (phase == 1) {
         c->moved_since_bin = true;
         c->forces_valid = false;
@@ -855,6 +886,7 @@ int md_run(md_ctx *c, int64_t nsteps, int32_t energy_every, double *energies)
         c->moved_since_bin = false;
         c->list_valid = false;
         c->forces_valid = false;
+        c->v32_fresh = false;
         CK(cudaMemsetAsync(&c->status->flags, 0, sizeof(int32_t), c->st));
         if ((rc = grow_list(c, s.max_count))) return rc;
         if (log) {
@@ -1120,7 +1152,13 @@ int md_set_spring_dashpot(md_ctx *c, double k_spring, double gamma)
         return fail(c, MD_ERR_INVAL, "cutoff must be >= sigma (the sphere diameter) so lists hold every contact");
     CK(cudaStreamSynchronize(c->st));
     int rc = MD_OK;
-    if (!c->v32 && (rc = dalloc(c, &c->v32, (size_t)c->n + 1))) return rc;
+    for (int b = 0; b < 2; b++) {
+        if (c->v32[b]) continue;
+        if ((rc = dalloc(c, &c->v32[b], (size_t)c->n + 1))) return rc;
+        // slot n (the sentinel) stays zero: the fused step writes slots < n
+        CK(cudaMemsetAsync(c->v32[b], 0, sizeof(float4) * ((size_t)c->n + 1), c->st));
+    }
+    c->v32_fresh = false;
     if (is_half(c) && (rc = apply_tuning(c, 1, 0))) return rc;   // contacts use full lists
     c->lj.pot = 1;
     c->lj.sd_k = k_spring;
@@ -1589,6 +1627,7 @@ int set_state(md_ctx *c, const double *pos, const double *vel, bool on_device)
     c->moved_since_bin = true;
     c->list_valid = false;
     c->forces_valid = false;
+    c->v32_fresh = false;
     int rc = rebuild_now(c, true);
     if (rc) return rc;
     return ensure_forces(c);

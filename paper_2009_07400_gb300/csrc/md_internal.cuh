@@ -158,6 +158,8 @@ struct Dev {
     DevStatus *status;
     const double *ctr;        // cell-centre coordinates (c + 0.5) s: per replica
                               // nc_x, then nc_y, then nc_z values
+    float4 *v32, *v32_nxt;    // contact model, mixed path: FP32 velocity copies
+                              // (n + 1 each, slot n zero; flip with p32), else null
 };
 
 #ifdef __CUDACC__
@@ -242,10 +244,15 @@ int launch_force(const Dev &d, const LJ &lj, int precision, bool half, int tpa, 
                  bool energy, bool batched, cudaStream_t st, int *nlaunch);
 int launch_integrate(const Dev &d, const LJ &lj, int precision, int phase, bool batched,
                      cudaStream_t st, int *nlaunch);
-// Spring-dashpot forces (full list; force store only, no fused integration).
-// v32: n + 1 float4 of scratch for the mixed path (FP32 velocity copies).
-int launch_force_sd(const Dev &d, const LJ &lj, bool mixed, bool energy, float4 *v32,
+// Spring-dashpot forces (full list).  Mixed path: one kernel with the
+// epilogue epi (EPI_F / EPI_FK / EPI_FKKD, as the LJ kernels), gathering the
+// neighbours' FP32 velocities from d.v32 and, for EPI_FKKD, writing the next
+// p32 and v32 to d.p32_nxt / d.v32_nxt.  FP64 path: force store only (epi is
+// ignored; the update runs in launch_integrate).
+int launch_force_sd(const Dev &d, const LJ &lj, bool mixed, int epi, bool energy,
                     cudaStream_t st, int *nlaunch);
+// d.v32[i] = fl32(d.v[i]) for i <= n (slot n: the sentinel's zero velocity).
+int launch_velocity_f32(const Dev &d, cudaStream_t st, int *nlaunch);
 // out3 != NULL: write (PE, KE, W) per replica there; otherwise append one
 // record to log_base at status->elog_cursor and advance the cursor.
 int launch_energy(const Dev &d, const LJ &lj, int precision, bool ke_from_v,

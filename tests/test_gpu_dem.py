@@ -149,3 +149,73 @@ def test_batched_packings_with_displacement_trigger(md, orc):
         d = np.mod(xg[o:o + x.shape[0]] - xr + L / 2, L) - L / 2
         assert np.abs(d).max() < 1e-9
         o += x.shape[0]
+
+
+@pytest.mark.parametrize("every", [20, 0])
+def test_mixed_fused_step_split_runs_are_bitwise_equal(md, every):
+    """The mixed contact step is one fused kernel that also writes the next
+    FP32 velocity copies; copies are regenerated only where something else
+    changed v (the first drift of a run, a final lone kick).  A run split
+    into pieces, with energies logged and an eager profiled stretch, must
+    give the same bits as one run, on both rebuild schedules."""
+    x, v, L = dense(seed=21, n=500)
+    kw = dict(precision=md.MD_MIXED, dt=0.001, rebuild_every=every)
+    with sd_ctx(md, x, v, L, 300.0, 2.5, **kw) as ctx:
+        ctx.run(75)
+        ref = (ctx.positions(), ctx.velocities(), ctx.forces())
+    with sd_ctx(md, x, v, L, 300.0, 2.5, **kw) as ctx:
+        ctx.run(7, energy_every=3)
+        ctx.run(20)
+        ctx.profile(21)
+        ctx.run(27, energy_every=27)
+        got = (ctx.positions(), ctx.velocities(), ctx.forces())
+    for a, b in zip(ref, got):
+        assert np.array_equal(a, b)
+
+
+def test_mixed_batched_packings_with_displacement_trigger(md, orc):
+    """Three packings in one context on the mixed fused step with the
+    displacement-triggered schedule, against the oracle."""
+    systems = [dense(seed=s, n=n, L=L) for s, n, L in
+               ((31, 300, (7.0, 7.0, 7.5)), (32, 450, (8.0, 8.0, 8.0)), (33, 200, (6.0, 6.5, 7.0)))]
+    pos = np.concatenate([x for x, _, _ in systems])
+    vel = np.concatenate([v for _, v, _ in systems])
+    kw = dict(sigma=SIG, cutoff=SIG, skin=SKIN, dt=0.001)
+    with md.MDContext(pos, vel, [L for _, _, L in systems], counts=[x.shape[0] for x, _, _ in systems],
+                      precision=md.MD_MIXED, rebuild_every=0, **kw) as ctx:
+        ctx.set_spring_dashpot(300.0, 1.5)
+        ctx.run(150)
+        xg = ctx.positions()
+        assert ctx.info().rebuilds > 1
+    o = 0
+    for x, v, L in systems:
+        xr, _, _ = orc.vv_run(x, v, L, 150, potential=1, k_spring=300.0, gamma=1.5,
+                              rebuild_every=0, **kw)
+        d = np.mod(xg[o:o + x.shape[0]] - xr + L / 2, L) - L / 2
+        assert np.abs(d).max() < 1e-4
+        o += x.shape[0]
+
+
+def test_mixed_state_changes_refresh_velocity_copies(md, orc):
+    """New velocities from set_state, a direct half kick (md_integrate) and a
+    switch of the contact constants must reach the dashpot term: each case
+    against the oracle's forces on the same state."""
+    x, v, L = dense(seed=41, n=400)
+    ok = dict(k_spring=250.0, gamma=4.0, sigma=SIG)
+    with sd_ctx(md, x, v, L, 250.0, 4.0, precision=md.MD_MIXED, dt=0.001) as ctx:
+        ctx.run(30)
+        v2 = -ctx.velocities()                   # reverse every velocity
+        x2 = ctx.positions()
+        ctx.set_state(x2, v2)
+        xw = orc.wrap(x2, L)
+        rows = orc.neighbors_cells(xw, L, SIG + SKIN)
+        assert rel_rms(ctx.forces(), orc.forces_sd_list(xw, v2, L, rows, **ok)) < 1e-5
+        ctx.run(10)
+        ctx.integrate(1)                         # half kick + drift outside a run
+        xi, vi = ctx.positions(), ctx.velocities()
+        xw = orc.wrap(xi, L)
+        rows = orc.neighbors_cells(xw, L, SIG + SKIN)
+        assert rel_rms(ctx.forces(), orc.forces_sd_list(xw, vi, L, rows, **ok)) < 1e-5
+        ctx.set_spring_dashpot(250.0, 8.0)
+        ok8 = dict(ok, gamma=8.0)
+        assert rel_rms(ctx.forces(), orc.forces_sd_list(xw, vi, L, rows, **ok8)) < 1e-5
