@@ -137,10 +137,7 @@ __global__ void __launch_bounds__(256) k_force_sd_mixed(Dev d, LJ lj)
         }
 #pragma unroll
         for (int t = 0; t < 4; t++) {
-            const uint32_t e = es[t];
-            const int32_t j = (int32_t)(e & kJMask);
-            const uint32_t c = e >> kJBits;
-            if (!MD_CHECK(d, j <= d.n)) continue;
+            const uint32_t c = es[t] >> kJBits;   // (a bad j was replaced by the sentinel above)
             const float4 pj = pjs[t];
             // d = (p_i - o s) - p_j with o = code - 1 per dimension
             const float dx = ((c & 2u) ? qx2 : ((c & 1u) ? pi.x : qx0)) - pj.x;

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 namespace mdk {
 
@@ -163,6 +164,48 @@ struct Dev {
 };
 
 #ifdef __CUDACC__
+// Bit casts on host and device (the host side serves the conversion tests).
+__host__ __device__ __forceinline__ long long bits_of(double a)
+{
+#ifdef __CUDA_ARCH__
+    return __double_as_longlong(a);
+#else
+    long long b;
+    memcpy(&b, &a, sizeof b);
+    return b;
+#endif
+}
+__host__ __device__ __forceinline__ double double_of(long long b)
+{
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double(b);
+#else
+    double a;
+    memcpy(&a, &b, sizeof a);
+    return a;
+#endif
+}
+__host__ __device__ __forceinline__ unsigned int bits_of(float f)
+{
+#ifdef __CUDA_ARCH__
+    return __float_as_uint(f);
+#else
+    unsigned int b;
+    memcpy(&b, &f, sizeof b);
+    return b;
+#endif
+}
+__host__ __device__ __forceinline__ float float_of(unsigned int b)
+{
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(b);
+#else
+    float f;
+    memcpy(&f, &b, sizeof f);
+    return f;
+#endif
+}
+
 // Conversions and compares of positive doubles done on their IEEE bit
 // patterns with integer operations: on GB300 the FP64 pipe, which executes
 // FP64 compares and FP64<->FP32 conversions, is a small fraction of the
@@ -171,49 +214,50 @@ struct Dev {
 constexpr long long kF64F32Rebias = (long long)(1023 - 127) << 23;
 // fl32(a), rounded to nearest with ties away from zero (add half of the 29
 // dropped mantissa bits; a carry moves into the exponent as it should)
-__device__ __forceinline__ float f32_of_pos(double a)
+__host__ __device__ __forceinline__ float f32_of_pos(double a)
 {
-    const long long b = __double_as_longlong(a);
-    return __int_as_float((int)(((b + (1LL << 28)) >> 29) - kF64F32Rebias));
+    const long long b = bits_of(a);
+    return float_of((unsigned int)(((b + (1LL << 28)) >> 29) - kF64F32Rebias));
 }
 // (double)f, exact
-__device__ __forceinline__ double f64_of_pos(float f)
+__host__ __device__ __forceinline__ double f64_of_pos(float f)
 {
-    return __longlong_as_double(((long long)__float_as_int(f) + kF64F32Rebias) << 29);
+    return double_of(((long long)bits_of(f) + kF64F32Rebias) << 29);
 }
 // a < b for a >= +0 and b > 0 (non-negative doubles order like their
 // patterns; a NaN a compares false, as in FP64)
-__device__ __forceinline__ bool lt_nonneg(double a, double b)
+__host__ __device__ __forceinline__ bool lt_nonneg(double a, double b)
 {
-    return __double_as_longlong(a) < __double_as_longlong(b);
+    return bits_of(a) < bits_of(b);
 }
 
 // Signed conversions with IEEE results on the bit patterns (checked bit for
-// bit against the hardware conversions on every float and on 6e7 doubles,
-// ties included); the FP64 pipe runs only for the rare operands outside
-// FP32's normal range.  Zero takes the integer path of f64_of_f32.
+// bit against the hardware conversions on every float and on random and
+// edge-case doubles, ties included, by tests/bitconv_check.cu); the FP64
+// pipe runs only for the rare operands outside FP32's normal range.  Zero
+// takes the integer path of f64_of_f32.
 // (double)f, exact
-__device__ __forceinline__ double f64_of_f32(float f)
+__host__ __device__ __forceinline__ double f64_of_f32(float f)
 {
-    const unsigned int u = __float_as_uint(f);
+    const unsigned int u = bits_of(f);
     const unsigned int mag = u & 0x7fffffffu;
     const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
     if (mag - 0x00800000u < 0x7f000000u)               // normal
-        return __longlong_as_double((long long)(sign | (((unsigned long long)mag + kF64F32Rebias) << 29)));
-    if (mag == 0) return __longlong_as_double((long long)sign);
+        return double_of((long long)(sign | (((unsigned long long)mag + kF64F32Rebias) << 29)));
+    if (mag == 0) return double_of((long long)sign);
     return (double)f;                                   // subnormal, inf, NaN
 }
 // (float)a, rounded to nearest even
-__device__ __forceinline__ float f32_of_f64(double a)
+__host__ __device__ __forceinline__ float f32_of_f64(double a)
 {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(a);
+    const unsigned long long b = (unsigned long long)bits_of(a);
     const unsigned long long mag = b & 0x7fffffffffffffffULL;
     // |a| in [2^-126, 2^128): a normal FP32 result (or an overflow to inf,
     // which the rounding carry produces)
     if (mag - 0x3810000000000000ULL < 0x0fe0000000000000ULL) {
         const unsigned long long r = (mag + 0x0fffffffULL + ((mag >> 29) & 1ULL)) >> 29;
-        return __uint_as_float((unsigned int)((b >> 32) & 0x80000000ULL) |
-                               (unsigned int)(r - (unsigned long long)kF64F32Rebias));
+        return float_of((unsigned int)((b >> 32) & 0x80000000ULL) |
+                        (unsigned int)(r - (unsigned long long)kF64F32Rebias));
     }
     return (float)a;
 }
