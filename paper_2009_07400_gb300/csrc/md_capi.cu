@@ -1297,15 +1297,18 @@ int md_adjoint(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt, double *
         }
         for (int64_t m = npts - 1; m >= 0 && !rc; m--) {
             const int64_t pt = cb + m;
-            cudaMemcpyAsync(c->x[c->xp], blk_x + m * n, sizeof(dvec4) * n, cudaMemcpyDeviceToDevice, c->st);
-            cudaMemcpyAsync(c->p32[c->pb], blk_p + m * n, sizeof(float4) * n, cudaMemcpyDeviceToDevice, c->st);
             if (pt < nsteps && launch_adjoint_axpy(n, c->lj.dt, xbar, wbar, wbar32, c->st, &nl)) {
                 rc = fail(c, MD_ERR_CUDA, "adjoint launch failed");
                 break;
             }
             const double k = pt == nsteps ? 0.0 : (pt == 0 ? cdt : 2.0 * cdt);
             const double lw = pt > nsteps - window ? 1.0 / (double)window : 0.0;
-            if (launch_adjoint_pairs(view(c), c->lj, mixed, wbar, wbar32, xbar, ge, gs, k, lw, c->st, &nl)) {
+            // the pair terms read the recomputed snapshot of force point pt
+            // in place (same atom order and list as the whole block)
+            Dev dv = view(c);
+            dv.x = blk_x + m * n;
+            dv.p32 = blk_p + m * n;
+            if (launch_adjoint_pairs(dv, c->lj, mixed, wbar, wbar32, xbar, ge, gs, k, lw, c->st, &nl)) {
                 rc = fail(c, MD_ERR_CUDA, "adjoint launch failed");
                 break;
             }
