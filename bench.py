@@ -637,6 +637,10 @@ def run_adjoint(args):
     res = {}
     for label, prec in (("mixed", md.MD_MIXED), ("fp64", md.MD_FP64)):
         with md.MDContext(s.pos, s.vel, s.box, stream=stream.cuda_stream, precision=prec) as ctx:
+            # lanes per atom of the force kernels tuned as in the main bench
+            # (md_adjoint walks full lists: a half-list choice falls back)
+            tuned = ctx.autotune(20)
+            tune = dict(threads_per_atom=tuned.threads_per_atom, half_list=bool(tuned.half_list))
             for _ in range(max(1, args.warmup)):
                 out = ctx.adjoint(nsteps, window, ckpt)
             torch.cuda.synchronize()
@@ -646,7 +650,8 @@ def run_adjoint(args):
                 out = ctx.adjoint(nsteps, window, ckpt)
             t_adj = (time.perf_counter() - t0) / reps
             x0, v0 = ctx.positions(), ctx.velocities()
-        with md.MDContext(s.pos, s.vel, s.box, stream=stream.cuda_stream, precision=prec) as ctx:
+        with md.MDContext(s.pos, s.vel, s.box, stream=stream.cuda_stream, precision=prec,
+                          **tune) as ctx:
             ctx.run(nsteps)
             ctx.set_state(s.pos, s.vel)
             torch.cuda.synchronize()
@@ -654,7 +659,7 @@ def run_adjoint(args):
             ctx.run(nsteps)
             torch.cuda.synchronize()
             t_fwd = time.perf_counter() - t0
-        res[label] = (out, t_adj, t_fwd)
+        res[label] = (out, t_adj, t_fwd, tune)
     t0 = time.perf_counter()
     ref = oracle.adjoint(s.pos, s.vel, s.box, nsteps, window)
     t_orc = time.perf_counter() - t0
@@ -667,8 +672,8 @@ def run_adjoint(args):
                 "d_x0_rel_norm": float(np.linalg.norm(gx - ref[3]) / np.linalg.norm(ref[3])),
                 "d_v0_rel_norm": float(np.linalg.norm(gv - ref[4]) / np.linalg.norm(ref[4]))}
 
-    out_m, t_m, f_m = res["mixed"]
-    out_d, t_d, f_d = res["fp64"]
+    out_m, t_m, f_m, tune_m = res["mixed"]
+    out_d, t_d, f_d, tune_d = res["fp64"]
     rate = lambda t: n * nsteps / t                          # noqa: E731
     line = {
         "metric": "atom-timesteps/s of the differentiated LJ rollout (forward + reverse sweep)",
@@ -679,7 +684,8 @@ def run_adjoint(args):
         "config": {"workload": f"LJ FCC 16^3, {n:,} atoms, rho 0.8442, T 1.44, {nsteps} steps, "
                                f"loss = mean PE over the last {window}, checkpoints every {ckpt}, "
                                "gradients w.r.t. epsilon, sigma, x0, v0", "atoms": n,
-                   "timesteps_per_step": nsteps, "seed": inputs.WORKLOADS[name]["seed"]},
+                   "timesteps_per_step": nsteps, "seed": inputs.WORKLOADS[name]["seed"],
+                   "tuned": {"mixed": tune_m, "fp64": tune_d}},
         "adjoint_over_forward": {"mixed": t_m / f_m, "fp64": t_d / f_d},
         "fp64_path": {"value": rate(t_d), "ms_per_step": t_d * 1e3},
         "gradient_error_vs_oracle": {"mixed": errs(out_m), "fp64": errs(out_d)},

@@ -57,12 +57,16 @@ struct AdjArgs {
 // FP64 path: FP64 pair geometry (the image shift of the neighbour's stencil
 // slot is added to (x_i - x_j) as the minimum-image branch would) and FP64
 // arithmetic.
-template <bool WINDOW>
+template <bool WINDOW, int TPA>
 __global__ void __launch_bounds__(128) k_adjoint_pairs(Dev d, LJ lj, AdjArgs a)
 {
     if (stopped(d.status)) return;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= d.n) return;
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i0 = gt / TPA;
+    const int sub = (int)(gt % TPA);
+    const bool valid = i0 < d.n;
+    if (TPA == 1 && !valid) return;
+    const int64_t i = valid ? i0 : d.n - 1;   // idle lanes still join the shuffles
     const Rep &R = d.reps[0];
     const int32_t idi = d.id[i];
     const dvec4 xi = d.x[i];
@@ -75,16 +79,20 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs(Dev d, LJ lj, AdjArgs a)
         hi[q] = c[q] == R.nc[q] - 1 ? -R.L[q] : 0.0;
     }
     const dvec4 ui = a.wbar[idi];
-    const int cnt = MD_CHECK(d, d.nb_count[i] <= d.cap) ? d.nb_count[i] : 0;
+    const int cnt = valid && MD_CHECK(d, d.nb_count[i] <= d.cap) ? d.nb_count[i] : 0;
     const int4 *nb4 = reinterpret_cast<const int4 *>(d.nb);
     const double eps = lj.eps, sigma6 = lj.sigma6, sigma = lj.sigma;
     const double inv_eps = 1.0 / eps, inv_sigma = 1.0 / sigma;   // once per atom
     double jx = 0, jy = 0, jz = 0, fx = 0, fy = 0, fz = 0, ge = 0, gs = 0, pe_e = 0, pe_s = 0;
-    int4 e4 = make_int4(0, 0, 0, 0);
-    // each int4 chunk of the row is loaded once
-    for (int k = 0; k < cnt; k++) {
-        if ((k & 3) == 0) e4 = nb4[(int64_t)(k >> 2) * d.n + i];
-        const int32_t e = (k & 3) == 0 ? e4.x : (k & 3) == 1 ? e4.y : (k & 3) == 2 ? e4.z : e4.w;
+    // the TPA lanes of an atom take the row's int4 chunks in turn; each
+    // chunk is loaded once
+    for (int q = sub; 4 * q < cnt; q += TPA) {
+      const int4 e4 = nb4[(int64_t)q * d.n + i];
+      const int32_t es[4] = {e4.x, e4.y, e4.z, e4.w};
+#pragma unroll
+      for (int t4 = 0; t4 < 4; t4++) {
+        if (4 * q + t4 >= cnt) break;
+        const int32_t e = es[t4];
         const uint32_t code = (uint32_t)e >> kJBits;
         const int ox = (int)(code & 3u) - 1, oy = (int)((code >> 2) & 3u) - 1, oz = (int)(code >> 4) - 1;
         const int32_t j = (int32_t)((uint32_t)e & kJMask);
@@ -116,6 +124,25 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs(Dev d, LJ lj, AdjArgs a)
             pe_e += 0.5 * 4.0 * t * (t - 1.0);
             pe_s += 0.5 * 24.0 * eps * t * (2.0 * t - 1.0) * inv_sigma;
         }
+      }
+    }
+    if (TPA > 1) {
+#pragma unroll
+        for (int o = TPA / 2; o > 0; o >>= 1) {
+            jx += __shfl_xor_sync(0xffffffffu, jx, o);
+            jy += __shfl_xor_sync(0xffffffffu, jy, o);
+            jz += __shfl_xor_sync(0xffffffffu, jz, o);
+            ge += __shfl_xor_sync(0xffffffffu, ge, o);
+            gs += __shfl_xor_sync(0xffffffffu, gs, o);
+            if (WINDOW) {
+                fx += __shfl_xor_sync(0xffffffffu, fx, o);
+                fy += __shfl_xor_sync(0xffffffffu, fy, o);
+                fz += __shfl_xor_sync(0xffffffffu, fz, o);
+                pe_e += __shfl_xor_sync(0xffffffffu, pe_e, o);
+                pe_s += __shfl_xor_sync(0xffffffffu, pe_s, o);
+            }
+        }
+        if (sub != 0 || !valid) return;
     }
     dvec4 xb = a.xbar[idi];
     xb.x += a.k * jx - a.lw * fx;
@@ -130,17 +157,21 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs(Dev d, LJ lj, AdjArgs a)
 // FP32 positions, the neighbour's adjoint from an FP32 copy), summed per atom
 // in FP32 and added to the FP64 adjoint state once per atom.  The FP64 pipe
 // then only sees the per-atom updates.
-template <bool WINDOW>
+template <bool WINDOW, int TPA>
 __global__ void __launch_bounds__(128) k_adjoint_pairs_f32(Dev d, LJ lj, AdjArgs a)
 {
     if (stopped(d.status)) return;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= d.n) return;
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i0 = gt / TPA;
+    const int sub = (int)(gt % TPA);
+    const bool valid = i0 < d.n;
+    if (TPA == 1 && !valid) return;
+    const int64_t i = valid ? i0 : d.n - 1;   // idle lanes still join the shuffles
     const Rep &R = d.reps[0];
     const int32_t idi = d.id[i];
     const float4 pi = d.p32[i];
     const float4 ui = a.wbar32[idi];
-    const int cnt = MD_CHECK(d, d.nb_count[i] <= d.cap) ? d.nb_count[i] : 0;
+    const int cnt = valid && MD_CHECK(d, d.nb_count[i] <= d.cap) ? d.nb_count[i] : 0;
     const int4 *nb4 = reinterpret_cast<const int4 *>(d.nb);
     const float eps = (float)lj.eps, sig6 = lj.sigma6f;
     const float inv_eps = (float)(1.0 / lj.eps), inv_sig = (float)(1.0 / lj.sigma);
@@ -148,10 +179,13 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs_f32(Dev d, LJ lj, AdjArgs
     const float qy0 = pi.y - R.nsf[1], qy2 = pi.y + R.nsf[1];
     const float qz0 = pi.z - R.nsf[2], qz2 = pi.z + R.nsf[2];
     float jx = 0, jy = 0, jz = 0, fx = 0, fy = 0, fz = 0, ge = 0, gs = 0, pe_e = 0, pe_s = 0;
-    int4 e4 = make_int4(0, 0, 0, 0);
-    for (int k = 0; k < cnt; k++) {
-        if ((k & 3) == 0) e4 = nb4[(int64_t)(k >> 2) * d.n + i];
-        const uint32_t e = (uint32_t)((k & 3) == 0 ? e4.x : (k & 3) == 1 ? e4.y : (k & 3) == 2 ? e4.z : e4.w);
+    for (int q = sub; 4 * q < cnt; q += TPA) {
+      const int4 e4 = nb4[(int64_t)q * d.n + i];
+      const int32_t es[4] = {e4.x, e4.y, e4.z, e4.w};
+#pragma unroll
+      for (int t4 = 0; t4 < 4; t4++) {
+        if (4 * q + t4 >= cnt) break;
+        const uint32_t e = (uint32_t)es[t4];
         const uint32_t c = e >> kJBits;
         const int32_t j = (int32_t)(e & kJMask);
         if (!MD_CHECK(d, j <= d.n)) continue;
@@ -181,6 +215,25 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs_f32(Dev d, LJ lj, AdjArgs
             pe_e += 2.0f * t * (t - 1.0f);
             pe_s += 12.0f * eps * t * (2.0f * t - 1.0f) * inv_sig;
         }
+      }
+    }
+    if (TPA > 1) {
+#pragma unroll
+        for (int o = TPA / 2; o > 0; o >>= 1) {
+            jx += __shfl_xor_sync(0xffffffffu, jx, o);
+            jy += __shfl_xor_sync(0xffffffffu, jy, o);
+            jz += __shfl_xor_sync(0xffffffffu, jz, o);
+            ge += __shfl_xor_sync(0xffffffffu, ge, o);
+            gs += __shfl_xor_sync(0xffffffffu, gs, o);
+            if (WINDOW) {
+                fx += __shfl_xor_sync(0xffffffffu, fx, o);
+                fy += __shfl_xor_sync(0xffffffffu, fy, o);
+                fz += __shfl_xor_sync(0xffffffffu, fz, o);
+                pe_e += __shfl_xor_sync(0xffffffffu, pe_e, o);
+                pe_s += __shfl_xor_sync(0xffffffffu, pe_s, o);
+            }
+        }
+        if (sub != 0 || !valid) return;
     }
     dvec4 xb = a.xbar[idi];
     xb.x += a.k * (double)jx - a.lw * (double)fx;
@@ -237,16 +290,20 @@ int launch_adjoint_pairs(const Dev &d, const LJ &lj, bool mixed, const dvec4 *wb
                          double k, double lw, cudaStream_t st, int *nl)
 {
     AdjArgs a{wbar32, wbar, xbar, g_eps, g_sig, k, lw};
-    const unsigned g = (unsigned)((d.n + 127) / 128);
+    // four lanes per atom while one lane per atom would leave SMs idle (fewer
+    // threads than 152 SMs x 8 blocks of 128), else one
+    const bool four = d.n * 1 <= (int64_t)152 * 8 * 128;
+    const unsigned g = (unsigned)((d.n * (four ? 4 : 1) + 127) / 128);
     const bool win = lw != 0.0;
-    if (mixed) {
-        if (!wbar32) return -1;
-        if (win) k_adjoint_pairs_f32<true><<<g, 128, 0, st>>>(d, lj, a);
-        else k_adjoint_pairs_f32<false><<<g, 128, 0, st>>>(d, lj, a);
-    } else {
-        if (win) k_adjoint_pairs<true><<<g, 128, 0, st>>>(d, lj, a);
-        else k_adjoint_pairs<false><<<g, 128, 0, st>>>(d, lj, a);
-    }
+    if (mixed && !wbar32) return -1;
+#define MD_ADJ(K, W)                                                             \
+    do {                                                                         \
+        if (four) K<W, 4><<<g, 128, 0, st>>>(d, lj, a);                          \
+        else K<W, 1><<<g, 128, 0, st>>>(d, lj, a);                               \
+    } while (0)
+    if (mixed) { if (win) MD_ADJ(k_adjoint_pairs_f32, true); else MD_ADJ(k_adjoint_pairs_f32, false); }
+    else { if (win) MD_ADJ(k_adjoint_pairs, true); else MD_ADJ(k_adjoint_pairs, false); }
+#undef MD_ADJ
     *nl += 1;
     return (int)cudaGetLastError();
 }
