@@ -1512,6 +1512,14 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
                 return fail(c, MD_ERR_NONFINITE, "non-finite input");
     }
     c->n = n;
+    if (q.threads_per_atom == 0) {
+        // lanes per atom of the full-list force kernels from the atom count:
+        // the choices md_autotune measured on GB300 for FCC liquids (mixed: 4
+        // up to ~16k atoms, 2 at ~55k, 1 from 131k; FP64, bound by its FP64
+        // pipe: 4 up to ~256k, 2 up to ~2M, 1 at 4M)
+        if (q.precision == MD_MIXED) c->tpa = n <= 32768 ? 4 : (n <= 98304 ? 2 : 1);
+        else c->tpa = n <= 393216 ? 4 : (n <= 3000000 ? 2 : 1);
+    }
     c->ncells = cells;
     c->nids = ids;
     c->nchunks = (int64_t)chunk_rep.size() / 2;
