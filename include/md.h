@@ -272,8 +272,12 @@ int md_set_spring_dashpot(md_ctx *ctx, double k_spring, double gamma);
  * by a hand-written reverse sweep: states are checkpointed every ckpt_every
  * steps and each block is recomputed bit-exactly (same list, same kernels)
  * before it is reversed.  g_x0 / g_v0: host, n x 3 doubles in caller order
- * (each may be NULL).  The context is left at (x0, v0).  Work memory is
- * allocated for the call and freed before it returns.
+ * (each may be NULL).  The context is left at (x0, v0).  Work memory
+ * (nsteps/ckpt_every + 1 checkpoints of 84 B per atom, ckpt_every recomputed
+ * snapshots of 48 B per atom, and the adjoint state) stays with the context
+ * for later calls, grown when a call needs more, and is freed by md_destroy;
+ * if growing it fails the whole workspace is released and MD_ERR_NOMEM
+ * returned.
  * Errors: MD_ERR_INVAL (nrep != 1; rebuild_every == 0; spring-dashpot model; window not in
  * [1, nsteps]; ckpt_every not dividing both rebuild_every and nsteps),
  * MD_ERR_NOMEM, MD_ERR_CUDA and those of md_run. */

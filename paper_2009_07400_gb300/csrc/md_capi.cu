@@ -103,6 +103,15 @@ struct md_ctx {
     int32_t last_max = 0;
     std::string err;
     std::map<std::string, GraphRec> graphs;
+    // md_adjoint's workspace, kept between calls (grow-only): checkpoints
+    // (nck x n), the block's recomputed snapshots (ckpt x n), adjoint state
+    struct {
+        int64_t nck = 0, ckpt = 0;
+        dvec4 *ck_x = nullptr, *ck_v = nullptr, *blk_x = nullptr, *xbar = nullptr, *wbar = nullptr;
+        float4 *blk_p = nullptr, *ck_p = nullptr, *wbar32 = nullptr;
+        int32_t *ck_id = nullptr;
+        double *ge = nullptr, *gs = nullptr, *g2 = nullptr;
+    } adj;
 };
 
 namespace {
@@ -202,7 +211,9 @@ void free_all(md_ctx *c)
                     c->cell_start, c->perm, c->scan_tmp, c->nb, c->nb_count, c->pe_atom,
                     c->w_atom, c->pe64, c->w64, c->ke64, c->status, c->chunk_rep_d,
                     c->chunk_first_d, c->partials_d, c->eout_d, c->elog_d, c->io_d, c->ctr_d,
-                    c->p32_ref, c->v32[0], c->v32[1]};
+                    c->p32_ref, c->v32[0], c->v32[1], c->adj.ck_x, c->adj.ck_v, c->adj.blk_x,
+                    c->adj.xbar, c->adj.wbar, c->adj.blk_p, c->adj.ck_p, c->adj.wbar32,
+                    c->adj.ck_id, c->adj.ge, c->adj.gs, c->adj.g2};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->own_stream && c->st) cudaStreamDestroy(c->st);
@@ -1188,28 +1199,34 @@ int md_adjoint(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt, double *
     int rc = MD_OK;
     if (half0 && (rc = apply_tuning(c, 1, 0))) return rc;   // the adjoint walks full lists
 
-    dvec4 *ck_x = nullptr, *ck_v = nullptr, *blk_x = nullptr, *xbar = nullptr, *wbar = nullptr;
-    float4 *blk_p = nullptr, *ck_p = nullptr, *wbar32 = nullptr;
-    int32_t *ck_id = nullptr;
-    double *ge = nullptr, *gs = nullptr, *g2 = nullptr;
-    auto cleanup = [&]() {
-        cudaFree(ck_x); cudaFree(ck_v); cudaFree(ck_id); cudaFree(ck_p); cudaFree(blk_x); cudaFree(blk_p);
-        cudaFree(xbar); cudaFree(wbar); cudaFree(wbar32); cudaFree(ge); cudaFree(gs); cudaFree(g2);
-    };
-    if ((rc = dalloc(c, &ck_x, (size_t)(nck * n))) || (rc = dalloc(c, &ck_v, (size_t)(nck * n))) ||
-        (rc = dalloc(c, &ck_id, (size_t)(nck * n))) || (rc = dalloc(c, &ck_p, (size_t)(nck * n))) ||
-        (rc = dalloc(c, &blk_x, (size_t)(ckpt * n))) ||
-        (rc = dalloc(c, &blk_p, (size_t)(ckpt * n))) || (rc = dalloc(c, &xbar, (size_t)n)) ||
-        (rc = dalloc(c, &wbar, (size_t)n)) || (rc = dalloc(c, &ge, (size_t)n)) ||
-        (rc = dalloc(c, &gs, (size_t)n)) || (rc = dalloc(c, &g2, 2)) ||
-        (mixed && (rc = dalloc(c, &wbar32, (size_t)n)))) {
-        cleanup();
+    // workspace: reused between calls, grown when a call needs more
+    auto &W = c->adj;
+    auto drop = [](auto *&p) { if (p) cudaFree(p); p = nullptr; };
+    if (nck > W.nck) { drop(W.ck_x); drop(W.ck_v); drop(W.ck_id); drop(W.ck_p); W.nck = 0; }
+    if (ckpt > W.ckpt) { drop(W.blk_x); drop(W.blk_p); W.ckpt = 0; }
+    if ((!W.ck_x && ((rc = dalloc(c, &W.ck_x, (size_t)(nck * n))) || (rc = dalloc(c, &W.ck_v, (size_t)(nck * n))) ||
+                     (rc = dalloc(c, &W.ck_id, (size_t)(nck * n))) || (rc = dalloc(c, &W.ck_p, (size_t)(nck * n))))) ||
+        (!W.blk_x && ((rc = dalloc(c, &W.blk_x, (size_t)(ckpt * n))) || (rc = dalloc(c, &W.blk_p, (size_t)(ckpt * n))))) ||
+        (!W.xbar && ((rc = dalloc(c, &W.xbar, (size_t)n)) || (rc = dalloc(c, &W.wbar, (size_t)n)) ||
+                     (rc = dalloc(c, &W.ge, (size_t)n)) || (rc = dalloc(c, &W.gs, (size_t)n)) ||
+                     (rc = dalloc(c, &W.g2, 2)))) ||
+        (mixed && !W.wbar32 && (rc = dalloc(c, &W.wbar32, (size_t)n)))) {
+        // release the whole workspace: a later call starts from scratch
+        drop(W.ck_x); drop(W.ck_v); drop(W.ck_id); drop(W.ck_p); drop(W.blk_x); drop(W.blk_p);
+        drop(W.xbar); drop(W.wbar); drop(W.wbar32); drop(W.ge); drop(W.gs); drop(W.g2);
+        W.nck = W.ckpt = 0;
         return rc;
     }
+    W.nck = std::max<int64_t>(W.nck, nck);
+    W.ckpt = std::max<int64_t>(W.ckpt, ckpt);
+    dvec4 *ck_x = W.ck_x, *ck_v = W.ck_v, *blk_x = W.blk_x, *xbar = W.xbar, *wbar = W.wbar;
+    float4 *blk_p = W.blk_p, *ck_p = W.ck_p, *wbar32 = mixed ? W.wbar32 : nullptr;
+    int32_t *ck_id = W.ck_id;
+    double *ge = W.ge, *gs = W.gs, *g2 = W.g2;
     if (window > c->elog_cap) {
         if (c->elog_d) cudaFree(c->elog_d);
         c->elog_d = nullptr;
-        if ((rc = dalloc(c, &c->elog_d, (size_t)window * 3))) { cleanup(); return rc; }
+        if ((rc = dalloc(c, &c->elog_d, (size_t)window * 3))) return rc;
         c->elog_cap = window;
         for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
         c->graphs.clear();
@@ -1248,8 +1265,8 @@ int md_adjoint(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt, double *
     };
 
     // ---- forward, with checkpoints ---------------------------------------
-    if ((rc = rebuild_now(c, true))) { cleanup(); return rc; }
-    if ((rc = enq_force(c, EPI_F, false, &nl))) { cleanup(); return rc; }
+    if ((rc = rebuild_now(c, true))) return rc;
+    if ((rc = enq_force(c, EPI_F, false, &nl))) return rc;
     save_ck(0);
     CK(cudaMemsetAsync(&c->status->elog_cursor, 0, sizeof(int64_t), c->st));
     for (int64_t s = 1; s <= nsteps && !rc; s++) {
@@ -1270,7 +1287,7 @@ int md_adjoint(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt, double *
         DevStatus st;
         if (!(rc = read_status(c, &st))) rc = check_flags(c, st);
     }
-    if (rc) { cleanup(); return rc; }
+    if (rc) return rc;
     double acc = 0;
     for (int64_t k = 0; k < window; k++) acc += elog[3 * k];
     *loss = acc / (double)window;
@@ -1332,7 +1349,6 @@ int md_adjoint(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt, double *
     }
     c->launches += nl;
     c->forces_valid = false;
-    cleanup();
     if (!rc && half0) rc = apply_tuning(c, tpa0, half0);
     return rc;
 }
