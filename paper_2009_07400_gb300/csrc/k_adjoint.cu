@@ -285,20 +285,19 @@ __global__ void __launch_bounds__(1024) k_sum2(int64_t n, const double *a, const
 
 }  // namespace
 
-int launch_adjoint_pairs(const Dev &d, const LJ &lj, bool mixed, const dvec4 *wbar,
+int launch_adjoint_pairs(const Dev &d, const LJ &lj, bool mixed, int lanes, const dvec4 *wbar,
                          const float4 *wbar32, dvec4 *xbar, double *g_eps, double *g_sig,
                          double k, double lw, cudaStream_t st, int *nl)
 {
     AdjArgs a{wbar32, wbar, xbar, g_eps, g_sig, k, lw};
-    // four lanes per atom while one lane per atom would leave SMs idle (fewer
-    // threads than 152 SMs x 8 blocks of 128), else one
-    const bool four = d.n * 1 <= (int64_t)152 * 8 * 128;
-    const unsigned g = (unsigned)((d.n * (four ? 4 : 1) + 127) / 128);
-    const bool win = lw != 0.0;
+    if (lanes != 1 && lanes != 2 && lanes != 4) return -1;
     if (mixed && !wbar32) return -1;
+    const unsigned g = (unsigned)((d.n * lanes + 127) / 128);
+    const bool win = lw != 0.0;
 #define MD_ADJ(K, W)                                                             \
     do {                                                                         \
-        if (four) K<W, 4><<<g, 128, 0, st>>>(d, lj, a);                          \
+        if (lanes == 4) K<W, 4><<<g, 128, 0, st>>>(d, lj, a);                    \
+        else if (lanes == 2) K<W, 2><<<g, 128, 0, st>>>(d, lj, a);               \
         else K<W, 1><<<g, 128, 0, st>>>(d, lj, a);                               \
     } while (0)
     if (mixed) { if (win) MD_ADJ(k_adjoint_pairs_f32, true); else MD_ADJ(k_adjoint_pairs_f32, false); }

@@ -1325,7 +1325,7 @@ int md_adjoint(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt, double *
             Dev dv = view(c);
             dv.x = blk_x + m * n;
             dv.p32 = blk_p + m * n;
-            if (launch_adjoint_pairs(dv, c->lj, mixed, wbar, wbar32, xbar, ge, gs, k, lw, c->st, &nl)) {
+            if (launch_adjoint_pairs(dv, c->lj, mixed, c->tpa, wbar, wbar32, xbar, ge, gs, k, lw, c->st, &nl)) {
                 rc = fail(c, MD_ERR_CUDA, "adjoint launch failed");
                 break;
             }

@@ -38,12 +38,14 @@ def rel(a, b):
     return abs(a - b) / abs(b)
 
 
-@pytest.mark.parametrize("nsteps,window,every,ckpt", [(40, 10, 20, 10), (60, 25, 20, 20),
-                                                      (30, 30, 10, 5)])
-def test_adjoint_matches_oracle(md, orc, small, nsteps, window, every, ckpt):
+@pytest.mark.parametrize("nsteps,window,every,ckpt,lanes", [(40, 10, 20, 10, 1), (60, 25, 20, 20, 2),
+                                                            (30, 30, 10, 5, 4), (40, 10, 20, 10, 4)])
+def test_adjoint_matches_oracle(md, orc, small, nsteps, window, every, ckpt, lanes):
+    """FP64 path; the pair kernel runs with the context's lanes per atom."""
     x0, v0, L = small
     loss_o, ge_o, gs_o, gx_o, gv_o = orc.adjoint(x0, v0, L, nsteps, window, rebuild_every=every)
-    with md.MDContext(x0, v0, L, precision=md.MD_FP64, rebuild_every=every) as ctx:
+    with md.MDContext(x0, v0, L, precision=md.MD_FP64, rebuild_every=every,
+                      threads_per_atom=lanes) as ctx:
         loss, ge, gs, gx, gv = ctx.adjoint(nsteps, window, ckpt)
         # the context is left at the initial state
         assert np.array_equal(ctx.positions(), orc.wrap(x0, L))
@@ -87,6 +89,21 @@ def test_adjoint_eps_sigma_parameters(md, orc, small):
     assert rel(loss, loss_o) < 1e-12 and rel(ge, ge_o) < 1e-9 and rel(gs, gs_o) < 1e-9
     assert np.linalg.norm(gx - gx_o) < 1e-9 * np.linalg.norm(gx_o)
     assert rel(loss1, orc.traj_loss(x0, v0, L, 20, 10)) < 1e-12
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4])
+def test_adjoint_mixed_lanes(md, orc, small, lanes):
+    """Mixed path (FP32 pair terms) with 1, 2 and 4 lanes per atom against the
+    FP64 oracle gradient of a short rollout."""
+    x0, v0, L = small
+    loss_o, ge_o, gs_o, gx_o, gv_o = orc.adjoint(x0, v0, L, 40, 10)
+    with md.MDContext(x0, v0, L, precision=md.MD_MIXED, threads_per_atom=lanes) as ctx:
+        loss, ge, gs, gx, gv = ctx.adjoint(40, 10, 10)
+    assert rel(loss, loss_o) < 1e-6
+    for g, go in ((ge, ge_o), (gs, gs_o)):
+        assert rel(g, go) < 1e-4
+    assert np.linalg.norm(gx - gx_o) < 1e-4 * np.linalg.norm(gx_o)
+    assert np.linalg.norm(gv - gv_o) < 1e-4 * np.linalg.norm(gv_o)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
