@@ -72,7 +72,7 @@ __device__ __forceinline__ void sd_epilogue(const Dev &d, const LJ &lj, const Re
     if (EPI == EPI_F || EPI == EPI_FK) d.f32[i] = f;
     if (EPI == EPI_F) return;
     const double fx = f64_of_f32(f.x), fy = f64_of_f32(f.y), fz = f64_of_f32(f.z);
-    dvec4 v = d.v[i];
+    dvec4 v = ld_cs_dvec4(d.v + i);        // streaming: keeps the gathered lines in L1
     v.x = fma(lj.half_dt_m, fx, v.x);
     v.y = fma(lj.half_dt_m, fy, v.y);
     v.z = fma(lj.half_dt_m, fz, v.z);
@@ -81,11 +81,11 @@ __device__ __forceinline__ void sd_epilogue(const Dev &d, const LJ &lj, const Re
         v.x = fma(lj.half_dt_m, fx, v.x);
         v.y = fma(lj.half_dt_m, fy, v.y);
         v.z = fma(lj.half_dt_m, fz, v.z);
-        dvec4 x = d.x[i];
+        dvec4 x = ld_cs_dvec4(d.x + i);
         x.x = fma(lj.dt, v.x, x.x);
         x.y = fma(lj.dt, v.y, x.y);
         x.z = fma(lj.dt, v.z, x.z);
-        d.x[i] = x;                          // neighbours gather p32 and v32 only
+        st_cs_dvec4(d.x + i, x);             // neighbours gather p32 and v32 only
         const double *ct = d.ctr + R.ctr_off;
         const double cx = __ldg(ct + (pack & 1023u));
         const double cy = __ldg(ct + R.nc[0] + ((pack >> 10) & 1023u));
@@ -96,7 +96,7 @@ __device__ __forceinline__ void sd_epilogue(const Dev &d, const LJ &lj, const Re
         check_displacement(d, i, pn);
         d.v32_nxt[i] = make_float4(f32_of_f64(v.x), f32_of_f64(v.y), f32_of_f64(v.z), 0.f);
     }
-    d.v[i] = v;
+    st_cs_dvec4(d.v + i, v);
 }
 
 template <bool BATCHED, bool ENERGY, int EPI>

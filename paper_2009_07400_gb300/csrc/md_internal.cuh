@@ -22,6 +22,19 @@ __device__ __forceinline__ dvec4 ldg_dvec4(const dvec4 *p)
     const double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
     return mk_dvec4(a.x, a.y, b.x, b.y);
 }
+// Streaming (evict-first) load and store of a padded FP64 3-vector: per-atom
+// state that a kernel touches once, kept from evicting gathered lines.
+__device__ __forceinline__ dvec4 ld_cs_dvec4(const dvec4 *p)
+{
+    const double2 a = __ldcs(reinterpret_cast<const double2 *>(p));
+    const double2 b = __ldcs(reinterpret_cast<const double2 *>(p) + 1);
+    return mk_dvec4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void st_cs_dvec4(dvec4 *p, const dvec4 &v)
+{
+    __stcs(reinterpret_cast<double2 *>(p), make_double2(v.x, v.y));
+    __stcs(reinterpret_cast<double2 *>(p) + 1, make_double2(v.z, v.w));
+}
 #endif
 
 // A list entry packs the neighbour's slot index (low 26 bits) and the cell
