@@ -141,3 +141,22 @@ def test_autograd_function(md, orc, small):
     assert rel(eps.grad.item(), 2 * ge_o) < 1e-9
     assert rel(sig.grad.item(), 2 * gs_o) < 1e-9
     assert np.linalg.norm(xt.grad.numpy() - 2 * gx_o) < 1e-9 * np.linalg.norm(2 * gx_o)
+
+
+def test_adjoint_workspace_reuse(md, small):
+    """md_adjoint keeps its workspace between calls and grows it when a call
+    needs more checkpoints or a longer block: calls of growing and shrinking
+    sizes on one context give the same bits as fresh contexts."""
+    x0, v0, L = small
+    calls = [(20, 10, 10), (60, 20, 10), (40, 10, 20), (20, 5, 5)]
+
+    def run(ctx, a):
+        return ctx.adjoint(*a)
+
+    with md.MDContext(x0, v0, L, precision=md.MD_MIXED) as ctx:
+        reused = [run(ctx, a) for a in calls]
+    for a, got in zip(calls, reused):
+        with md.MDContext(x0, v0, L, precision=md.MD_MIXED) as ctx:
+            ref = run(ctx, a)
+        assert got[0] == ref[0] and got[1] == ref[1] and got[2] == ref[2]
+        assert np.array_equal(got[3], ref[3]) and np.array_equal(got[4], ref[4])
