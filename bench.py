@@ -167,8 +167,8 @@ def parse_tuned(text):
     if not text:
         return None
     v = [int(x) for x in text.split(",")]
-    if len(v) != 4 or v[0] not in (1, 2, 4) or v[2] not in (1, 2, 4):
-        raise SystemExit("--tuned wants TPA,HALF,TPA64,HALF64 with TPA in {1,2,4}")
+    if len(v) != 4 or v[0] not in (1, 2, 4, 8) or v[2] not in (1, 2, 4, 8):
+        raise SystemExit("--tuned wants TPA,HALF,TPA64,HALF64 with TPA in {1,2,4,8}")
     return (dict(threads_per_atom=v[0], half_list=bool(v[1])),
             dict(threads_per_atom=v[2], half_list=bool(v[3])))
 

@@ -82,7 +82,7 @@ typedef struct {
                                 with i iff j's nearest image is in i's upper
                                 half-space (del = x_i - x_j: del.z < 0, ties by
                                 del.y, del.x, then id_j > id_i)                 */
-    int32_t threads_per_atom;/* 1, 2 or 4 lanes per atom in the full-list force
+    int32_t threads_per_atom;/* 1, 2, 4 or 8 lanes per atom in the full-list force
                                 kernels; 0 = a default from the atom count and
                                 precision (md_autotune's choices measured on
                                 GB300; md_autotune itself times the candidates) */

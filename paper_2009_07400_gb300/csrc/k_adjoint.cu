@@ -290,13 +290,14 @@ int launch_adjoint_pairs(const Dev &d, const LJ &lj, bool mixed, int lanes, cons
                          double k, double lw, cudaStream_t st, int *nl)
 {
     AdjArgs a{wbar32, wbar, xbar, g_eps, g_sig, k, lw};
-    if (lanes != 1 && lanes != 2 && lanes != 4) return -1;
+    if (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8) return -1;
     if (mixed && !wbar32) return -1;
     const unsigned g = (unsigned)((d.n * lanes + 127) / 128);
     const bool win = lw != 0.0;
 #define MD_ADJ(K, W)                                                             \
     do {                                                                         \
-        if (lanes == 4) K<W, 4><<<g, 128, 0, st>>>(d, lj, a);                    \
+        if (lanes == 8) K<W, 8><<<g, 128, 0, st>>>(d, lj, a);                    \
+        else if (lanes == 4) K<W, 4><<<g, 128, 0, st>>>(d, lj, a);               \
         else if (lanes == 2) K<W, 2><<<g, 128, 0, st>>>(d, lj, a);               \
         else K<W, 1><<<g, 128, 0, st>>>(d, lj, a);                               \
     } while (0)

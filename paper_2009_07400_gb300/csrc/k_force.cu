@@ -3,8 +3,8 @@
 //     sr2 = 1/rsq; sr6 = sr2*sr2*sr2*sigma^6; f = 48 eps sr6 (sr6 - 1/2) sr2
 //     F_i += f * del,  del = x_i - x_j,  only if rsq < rc^2.
 //
-// GPU mapping (Sec. 3.1/4.1: one thread per particle; here TPA = 1, 2 or 4
-// lanes per atom): the neighbour-major list is streamed from HBM as int4
+// GPU mapping (Sec. 3.1/4.1: one thread per particle; here TPA = 1, 2, 4 or 8
+// lanes per atom, the larger counts for systems too small to fill the GPU): the neighbour-major list is streamed from HBM as int4
 // chunks (ld.global.cs: evict-first, it is read once per step), neighbour
 // positions are gathered through the read-only L1 path (16 B float4 in the
 // mixed path, so the whole position array stays L2-resident), and the
@@ -496,11 +496,13 @@ int launch_force(const Dev &d, const LJ &lj, int precision, bool half, int tpa, 
         else { if (energy) MD_HALF(false, true); else MD_HALF(false, false); }
 #undef MD_HALF
     } else if (batched) {
-        if (tpa == 4) launch_full<4, true>(d, lj, mixed, epi, energy, st);
+        if (tpa == 8) launch_full<8, true>(d, lj, mixed, epi, energy, st);
+        else if (tpa == 4) launch_full<4, true>(d, lj, mixed, epi, energy, st);
         else if (tpa == 2) launch_full<2, true>(d, lj, mixed, epi, energy, st);
         else launch_full<1, true>(d, lj, mixed, epi, energy, st);
     } else {
-        if (tpa == 4) launch_full<4, false>(d, lj, mixed, epi, energy, st);
+        if (tpa == 8) launch_full<8, false>(d, lj, mixed, epi, energy, st);
+        else if (tpa == 4) launch_full<4, false>(d, lj, mixed, epi, energy, st);
         else if (tpa == 2) launch_full<2, false>(d, lj, mixed, epi, energy, st);
         else launch_full<1, false>(d, lj, mixed, epi, energy, st);
     }

@@ -1403,7 +1403,7 @@ int md_autotune(md_ctx *c, int32_t steps, md_params *chosen)
         return r;
     };
     save();
-    const int cands[4][2] = {{1, 0}, {2, 0}, {4, 0}, {1, 1}};
+    const int cands[5][2] = {{1, 0}, {2, 0}, {4, 0}, {8, 0}, {1, 1}};
     float best = 1e30f;
     int best_k = 0;
     cudaEvent_t e0, e1;
@@ -1463,7 +1463,7 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
         !(q.dt > 0) || q.rebuild_every < 0 || (q.precision != MD_FP64 && q.precision != MD_MIXED) ||
         (q.half_list != 0 && q.half_list != 1) ||
         !(q.threads_per_atom == 0 || q.threads_per_atom == 1 || q.threads_per_atom == 2 ||
-          q.threads_per_atom == 4))
+          q.threads_per_atom == 4 || q.threads_per_atom == 8))
         return fail(c, MD_ERR_INVAL, "invalid md_params");
     c->p = q;
     c->nrep = nrep;
@@ -1530,11 +1530,13 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
     c->n = n;
     if (q.threads_per_atom == 0) {
         // lanes per atom of the full-list force kernels from the atom count:
-        // the choices md_autotune measured on GB300 for FCC liquids (mixed: 4
-        // up to ~16k atoms, 2 at ~55k, 1 from 131k; FP64, bound by its FP64
-        // pipe: 4 up to ~256k, 2 up to ~2M, 1 at 4M)
-        if (q.precision == MD_MIXED) c->tpa = n <= 32768 ? 4 : (n <= 98304 ? 2 : 1);
-        else c->tpa = n <= 393216 ? 4 : (n <= 3000000 ? 2 : 1);
+        // the choices md_autotune measured on GB300 for FCC liquids (mixed: 8
+        // at 4k atoms, 4 at ~16k, 2 at ~55k, 1 from 131k; FP64, bound by its
+        // FP64 pipe: 8 at 4k, 4 up to ~256k, 2 up to ~2M, 1 at 4M)
+        if (q.precision == MD_MIXED)
+            c->tpa = n <= 8192 ? 8 : (n <= 32768 ? 4 : (n <= 98304 ? 2 : 1));
+        else
+            c->tpa = n <= 8192 ? 8 : (n <= 393216 ? 4 : (n <= 3000000 ? 2 : 1));
     }
     c->ncells = cells;
     c->nids = ids;

@@ -335,7 +335,7 @@ int64_t scan_tmp_elems(int64_t ncells_total);
 // Adjoint (k_adjoint.cu)
 // mixed: FP32 pair terms reading wbar32 (an FP32 copy of wbar kept by the
 // axpy kernel); FP64 path: wbar32 may be null.
-// lanes: 1, 2 or 4 lanes per atom (the context's lanes per atom: several
+// lanes: 1, 2, 4 or 8 lanes per atom (the context's lanes per atom: several
 // lanes keep small systems from leaving SMs idle)
 int launch_adjoint_pairs(const Dev &d, const LJ &lj, bool mixed, int lanes, const dvec4 *wbar,
                          const float4 *wbar32, dvec4 *xbar, double *g_eps, double *g_sig,

@@ -31,7 +31,7 @@ def test_parse_tuned():
     mixed, fp64 = bench.parse_tuned("1,0,2,1")
     assert mixed == {"threads_per_atom": 1, "half_list": False}
     assert fp64 == {"threads_per_atom": 2, "half_list": True}
-    for bad in ("3,0,1,0", "1,0,1", "1,0,8,0"):
+    for bad in ("3,0,1,0", "1,0,1", "1,0,16,0"):
         with pytest.raises(SystemExit):
             bench.parse_tuned(bad)
 

@@ -164,7 +164,7 @@ def test_list_parity(md, orc, case, half):
 # Forces (Sec. 3.2 Eq. 2 / Sec. 4.2 kernel), all list and lane variants.
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("half,tpa", [(False, 1), (False, 2), (False, 4), (True, 1)])
+@pytest.mark.parametrize("half,tpa", [(False, 1), (False, 2), (False, 4), (False, 8), (True, 1)])
 @pytest.mark.parametrize("case", ["jitter7", "liquid", "ragged"])
 def test_force_parity(md, orc, case, half, tpa):
     if case == "jitter7":
@@ -393,7 +393,7 @@ def test_autotune_keeps_state(md, orc):
         with ctx_of(md, s, precision=precision) as ctx:
             x0, v0 = ctx.positions(), ctx.velocities()
             chosen = ctx.autotune(steps=20)
-            assert chosen.threads_per_atom in (1, 2, 4) and chosen.half_list in (0, 1)
+            assert chosen.threads_per_atom in (1, 2, 4, 8) and chosen.half_list in (0, 1)
             assert ctx.info().step == 0
             assert np.array_equal(ctx.positions(), x0)
             assert np.array_equal(ctx.velocities(), v0)
@@ -611,10 +611,14 @@ def test_resume_from_saved_state(md, orc):
     100) and follows the uninterrupted run up to the summation order after the
     resume's own rebuild.  A skin of 1.0 keeps every list valid for 20 steps,
     so the list built at the resume holds the same pairs inside rc as the
-    older list of the uninterrupted run."""
+    older list of the uninterrupted run.  Mixed path: the re-binned order
+    changes the FP32 sums at the 1e-7 level, and 43 steps of the chaotic
+    liquid grow that to ~1e-5 in the positions, depending on how the lanes
+    per atom split the rows (a missing or spurious pair would show at
+    ~1e-2)."""
     s = inputs.workload("fcc8_2048")
     kw = dict(skin=1.0)
-    for precision, tol in ((md.MD_FP64, 1e-11), (md.MD_MIXED, 1e-5)):
+    for precision, tol in ((md.MD_FP64, 1e-11), (md.MD_MIXED, 5e-5)):
         with ctx_of(md, s, precision=precision, **kw) as a:
             a.run(100)
             x_ref, v_ref = a.positions(), a.velocities()
