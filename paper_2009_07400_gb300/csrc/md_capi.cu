@@ -1409,7 +1409,8 @@ int md_autotune(md_ctx *c, int32_t steps, md_params *chosen)
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    for (int k = 0; k < 4 && !rc; k++) {
+    const int ncand = (int)(sizeof(cands) / sizeof(cands[0]));
+    for (int k = 0; k < ncand && !rc; k++) {
         if ((rc = apply_tuning(c, cands[k][0], cands[k][1]))) break;
         if ((rc = md_run(c, steps, 0, nullptr))) break;  // warm-up (graph capture)
         if ((rc = restore())) break;
