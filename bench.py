@@ -3,15 +3,17 @@
 FCC workload (64^3 unit cells, density 0.8442, T = 1.44, +-0.05 sigma jitter,
 rc 2.5, skin 0.3, dt 0.005, rebuild every 20 steps).
 
-One benchmark step = one rebuild cycle: binning + list build + 20 velocity-
-Verlet time steps (force kernel with fused integration), replayed from one
-CUDA graph.  value = atoms x 20 x steps / device time of the timed region
-(mixed path); the FP64 path is timed the same way beside it.
+One benchmark step = ten rebuild cycles, each binning + list build + 20
+velocity-Verlet time steps (force kernel with fused integration) replayed
+from one CUDA graph: 200 time steps.  value = atoms x 200 x steps / device
+time of the timed region (mixed path); the FP64 path is timed beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-Under torchrun every rank advances its own replica of the workload (weak
-scaling, no collective on the data path) and rank 0 prints one JSON line.
+Under torchrun every rank advances its own copy of a single-system workload
+(weak scaling, no collective on the data path); the 256-replica ensemble is
+split between the ranks instead (strong scaling).  Rank 0 prints one JSON
+line.
 """
 from __future__ import annotations
 
@@ -46,20 +48,29 @@ DEM_PARAMS = dict(sigma=1.0, cutoff=1.0, skin=0.3, dt=0.001)
 DEM_K, DEM_GAMMA = 1000.0, 5.0
 METRIC = "atom-timesteps/s, LJ 1M atoms, mixed-FP32 vs FP64 path at stated force error"
 UNIT = "atom-timesteps/s"
-STEPS_PER_CYCLE = 20
+STEPS_PER_CYCLE = 20                    # time steps per rebuild cycle
+CYCLES_PER_STEP = 10                    # rebuild cycles per benchmark step
+TIMESTEPS_PER_STEP = STEPS_PER_CYCLE * CYCLES_PER_STEP
 FORCE_SRC = os.path.join(ROOT, "paper_2009_07400_gb300", "csrc", "k_force.cu")
 PROFILE_MD = os.path.join(ROOT, "profiles", "force_mixed_fcc64.md")
 
 
-def make_workload(name):
-    """(positions, velocities, boxes, counts or None, description) of a workload."""
+def make_workload(name, rank=0, world=1):
+    """(positions, velocities, boxes, counts or None, description, seed) of a
+    workload.  The ensemble is split between `world` ranks (rank's contiguous
+    block of replicas, every replica generated from its own seed); the other
+    workloads are one system that every rank advances on its own."""
     if name == "ensemble256":
-        reps = inputs.replica_ensemble(256, seed=1004)
+        from paper_2009_07400_gb300 import dist as mdist
+        allr = inputs.replica_ensemble(256, seed=1004)
+        reps = [allr[k] for k in mdist.shard(len(allr), rank, world)]
         pos = np.concatenate([r.pos for r in reps])
         vel = np.concatenate([r.vel for r in reps])
+        total = sum(r.n for r in allr)
         desc = ("256 independent periodic LJ replicas, atoms log-uniform in [500, 20000] "
-                f"({pos.shape[0]:,} in total), density U[0.70, 0.90], T U[0.8, 1.6], rc 2.5, "
-                "skin 0.3, dt 0.005, rebuild every 20 steps, one context")
+                f"({total:,} in total), density U[0.70, 0.90], T U[0.8, 1.6], rc 2.5, "
+                "skin 0.3, dt 0.005, rebuild every 20 steps, one context per GPU"
+                + (f" (this rank: {len(reps)} replicas, {pos.shape[0]:,} atoms)" if world > 1 else ""))
         return pos, vel, [r.box for r in reps], [r.n for r in reps], desc, 1004
     s = inputs.workload(name)
     cells = {"fcc64_1048576": 64, "fcc128_8388608": 128, "fcc80_2048000": 80}[name]
@@ -69,8 +80,8 @@ def make_workload(name):
     return s.pos, s.vel, s.box, None, desc, inputs.WORKLOADS[name]["seed"]
 
 
-def config_dict(n_atoms, desc, seed):
-    return {"workload": desc, "atoms": int(n_atoms), "timesteps_per_step": STEPS_PER_CYCLE,
+def config_dict(n_atoms, desc, seed, timesteps_per_step=TIMESTEPS_PER_STEP):
+    return {"workload": desc, "atoms": int(n_atoms), "timesteps_per_step": timesteps_per_step,
             "l2": "inputs larger than L2: the neighbour list (~0.33 GB per million atoms) "
                   "is streamed every time step; positions (16 B per atom, FP32) stay "
                   "L2-resident by design",
@@ -94,7 +105,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -147,7 +158,9 @@ def measured_peaks():
 
 def ncu_traffic():
     """DRAM bytes per launch of the mixed force kernel from the committed ncu
-    summary, if it was taken on the current kernel source (else None)."""
+    summary, if it was taken on the current kernel source (else None).  Not
+    measured in the run: ncu's counters need a profiler, and a number taken
+    under one is no bench value."""
     if not os.path.exists(PROFILE_MD):
         return None
     text = open(PROFILE_MD).read()
@@ -187,12 +200,13 @@ def algorithmic_bytes_per_atom(mean_nb, half):
     return 4.0 * mean_nb + 4 + 16 + 16 + 2 * 24 + 2 * 24
 
 
-def time_cycles(ctx, steps, warmup, dist, torch):
-    """Device time of `steps` rebuild cycles after `warmup` ones (CUDA events
-    on the context's stream, barrier + synchronize on both sides)."""
+def time_cycles(ctx, steps, warmup, dist, torch, timesteps=TIMESTEPS_PER_STEP):
+    """Device time of `steps` steps of `timesteps` time steps each after
+    `warmup` such steps (CUDA events on the context's stream, barrier +
+    synchronize on both sides)."""
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
-        ctx.run(STEPS_PER_CYCLE)
+        ctx.run(timesteps)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -200,7 +214,7 @@ def time_cycles(ctx, steps, warmup, dist, torch):
     end = torch.cuda.Event(enable_timing=True)
     l0 = ctx.info().kernel_launches
     start.record(stream)
-    ctx.run(STEPS_PER_CYCLE * steps)
+    ctx.run(timesteps * steps)
     end.record(stream)
     torch.cuda.synchronize()
     if dist:
@@ -225,8 +239,11 @@ def run_gpu(args):
     build.build()
     md.load()
     name = WORKLOADS[args.workload]
-    pos, vel, box, counts, desc, seed = make_workload(name)
+    pos, vel, box, counts, desc, seed = make_workload(name, rank, world)
     n = pos.shape[0]
+    # the ensemble is split between the ranks (strong scaling); every rank
+    # advances its own copy of a single-system workload (weak scaling)
+    sharded = name == "ensemble256"
     # The library enqueues on the stream it is given: use one torch stream for
     # the contexts and for the CUDA events that bracket the timed region.
     stream = torch.cuda.Stream()
@@ -259,7 +276,7 @@ def run_gpu(args):
               half_list=res["tuned"]["half_list"]) as ctx:
         disp_cycles = max(1, min(args.steps, 5))
         r0 = ctx.info().rebuilds
-        ms_d, _ = time_cycles(ctx, disp_cycles, 1, dist, torch)
+        ms_d, _ = time_cycles(ctx, disp_cycles, 1, dist, torch, timesteps=STEPS_PER_CYCLE)
         res["disp_ms"] = ms_d / disp_cycles
         res["disp_rebuilds"] = (ctx.info().rebuilds - r0) / ((disp_cycles + 1) * STEPS_PER_CYCLE)
     fp64_cycles = max(1, min(args.steps, 3))
@@ -278,21 +295,28 @@ def run_gpu(args):
             t64 = ctx.autotune(STEPS_PER_CYCLE)
             res["tuned64"] = {"threads_per_atom": t64.threads_per_atom,
                               "half_list": bool(t64.half_list)}
-        ms64, _ = time_cycles(ctx, fp64_cycles, 1, dist, torch)
+        ms64, _ = time_cycles(ctx, fp64_cycles, 1, dist, torch, timesteps=STEPS_PER_CYCLE)
         res["fp64_ms"] = ms64 / fp64_cycles
         res["prof64"] = ctx.profile(STEPS_PER_CYCLE)
         res["fp64_state"] = (ctx.positions(), ctx.forces())
-    # end to end: host state in pinned memory -> md_set_state -> one cycle ->
-    # energies back to the host, every step
+    # end to end through the C ABI with host buffers, every step: the state
+    # (positions and velocities) from pinned host memory -> md_set_state ->
+    # one benchmark step (200 time steps) -> positions and velocities back
+    # into pinned host memory.  md_set_state bins and builds for the new
+    # state, so each step builds once more than the device-resident loop.
     pin_pos = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
     pin_vel = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    out_pos = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    out_vel = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
     pin_pos[:] = pos
     pin_vel[:] = vel
     with make(precision=md.MD_MIXED, threads_per_atom=res["tuned"]["threads_per_atom"],
               half_list=res["tuned"]["half_list"]) as ctx:
         for _ in range(2):
             ctx.set_state(pin_pos, pin_vel)
-            ctx.run(STEPS_PER_CYCLE, energy_every=STEPS_PER_CYCLE)
+            ctx.run(TIMESTEPS_PER_STEP)
+            ctx.positions(out=out_pos)
+            ctx.velocities(out=out_vel)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
@@ -300,7 +324,9 @@ def run_gpu(args):
         t0 = time.perf_counter()
         for _ in range(e_steps):
             ctx.set_state(pin_pos, pin_vel)
-            ctx.run(STEPS_PER_CYCLE, energy_every=STEPS_PER_CYCLE)
+            ctx.run(TIMESTEPS_PER_STEP)
+            ctx.positions(out=out_pos)
+            ctx.velocities(out=out_vel)
         e2e_s = time.perf_counter() - t0
         if dist:
             dist.barrier()
@@ -309,9 +335,13 @@ def run_gpu(args):
     mixed_ms, fp64_ms, e2e_s = mdist.max_over_ranks(
         [res["mixed_ms"], res["fp64_ms"], e2e_s], dist, device="cuda" if dist else None)
     n_total = n * world
-    value = n_total * STEPS_PER_CYCLE * args.steps / (mixed_ms / 1e3)
+    if dist and sharded:     # the ranks hold different parts of the ensemble
+        t = torch.tensor([n], dtype=torch.int64, device="cuda")
+        dist.all_reduce(t)
+        n_total = int(t.item())
+    value = n_total * TIMESTEPS_PER_STEP * args.steps / (mixed_ms / 1e3)
     fp64_value = n_total * STEPS_PER_CYCLE / (fp64_ms / 1e3)
-    e2e_value = n_total * STEPS_PER_CYCLE * e_steps / e2e_s
+    e2e_value = n_total * TIMESTEPS_PER_STEP * e_steps / e2e_s
     if rank == 0:
         prof = res["prof"]
         force_ms_per_launch = prof.force_ms / max(1, prof.force_launches)
@@ -323,7 +353,8 @@ def run_gpu(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": mixed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": mixed_ms / args.steps, "higher_is_better": True,
+            "scaling": "strong" if sharded and world > 1 else "weak",
             "vs_baseline": None, "dtype": "f32+f64 (mixed: FP32 pair arithmetic, Kahan sums, "
                                           "FP64 integration and reductions)",
             "data": "synthetic",
@@ -331,6 +362,12 @@ def run_gpu(args):
                            list="half" if half else "full"),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
+                         "traffic_source": ("dram__bytes_read.sum + dram__bytes_write.sum per "
+                                            "launch from the committed ncu summary "
+                                            "profiles/force_mixed_fcc64.md, taken on this "
+                                            "kernel source (hash-checked); not measured in "
+                                            "this run" if traffic is not None else
+                                            "no ncu capture of this kernel source"),
                          "kernel": ("k_force_mixed_half" if half else
                                     "k_force_mixed_full (fused velocity-Verlet epilogue)"),
                          "bytes_per_atom": bpa, "mean_neighbors": prof.mean_neighbors,
@@ -352,7 +389,11 @@ def run_gpu(args):
                         "schedule is the headline"},
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(2 * 3 * 8 * n),
-                    "d2h_bytes_per_step": int(3 * 8 * nrep)},
+                    "d2h_bytes_per_step": int(2 * 3 * 8 * n),
+                    "note": "per step: positions and velocities from pinned host memory "
+                            "(md_set_state, which bins and builds), 200 time steps, positions "
+                            "and velocities back into pinned host memory (md_get_positions, "
+                            "md_get_velocities)"},
             "gpu_launches": int(res["launches"]),
             "clocks": res["clocks"],
         }
@@ -448,10 +489,13 @@ def cpu_baseline_leg(pos, vel, box, counts, res):
 
 def run_reference(args):
     """The reference arm: the FP64 oracle, as it stands, on the host cores.
-    Its sample is `steps` oracle time steps of the full workload (after
-    `warmup` steps) with the list build amortised over 20 steps; value is in
-    atom-timesteps/s and ms_per_step is per 20-timestep cycle, like the GPU
-    arm's step."""
+    One step of this arm is one rebuild cycle of the workload: a call of the
+    oracle's velocity-Verlet loop for 19 steps, which bins, builds the list
+    and evaluates the forces once before its first step, so it holds exactly
+    one list build and 20 force evaluations (the steady cycle of the 20-step
+    schedule).  Steps continue from each other's final state.  The timed
+    region is `steps` such calls after `warmup` untimed ones: ms_per_step x
+    steps is the timed region, value = atoms x 20 x steps / its duration."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -463,29 +507,28 @@ def run_reference(args):
         p, v, b, _ = _systems(pos, vel, box, counts, 60_000)[0]
     else:
         p, v, b = pos, vel, np.asarray(box)
+    x, vv = p, v
+    for _ in range(max(1, args.warmup)):
+        x, vv, _ = oracle.vv_run(x, vv, b, STEPS_PER_CYCLE - 1)
     t0 = time.perf_counter()
-    x, vv, _ = oracle.vv_run(p, v, b, 0)
-    t_build = time.perf_counter() - t0
-    x, vv, _ = oracle.vv_run(x, vv, b, max(1, args.warmup))
-    t0 = time.perf_counter()
-    oracle.vv_run(x, vv, b, args.steps)
-    t_steps = time.perf_counter() - t0 - t_build
-    t_step = max(t_steps / args.steps, 1e-9)
-    per_step = t_step + t_build / STEPS_PER_CYCLE
-    value = p.shape[0] / per_step
+    for _ in range(args.steps):
+        x, vv, _ = oracle.vv_run(x, vv, b, STEPS_PER_CYCLE - 1)
+    t_region = time.perf_counter() - t0
+    value = p.shape[0] * STEPS_PER_CYCLE * args.steps / t_region
     cores = oracle.num_threads()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": int(os.environ.get("WORLD_SIZE", args.gpus)), "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": per_step * STEPS_PER_CYCLE * 1e3,
+            "warmup": args.warmup, "ms_per_step": t_region / args.steps * 1e3,
             "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(config_dict(pos.shape[0], desc, seed), list="full",
-                           replicas=1 if counts is None else len(counts)),
+            "config": dict(config_dict(p.shape[0], desc, seed, timesteps_per_step=STEPS_PER_CYCLE),
+                           list="full", replicas=1 if counts is None else len(counts)),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{args.steps} oracle time steps of "
+                             "sample": f"{args.steps} rebuild cycles of "
                                        f"{'the full workload' if counts is None else 'one replica'} "
-                                       f"after {max(1, args.warmup)} warm-up steps; list "
-                                       f"build ({t_build:.2f} s) amortised over 20 steps"},
+                                       f"after {max(1, args.warmup)} warm-up cycles; each cycle "
+                                       "is one list build and 20 force evaluations "
+                                       f"({t_region / args.steps:.2f} s per cycle)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

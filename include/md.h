@@ -191,6 +191,24 @@ int md_integrate(md_ctx *ctx, int32_t phase);
  * is a host array of nrep doubles (any may be NULL).  Synchronises. */
 int md_energy(md_ctx *ctx, double *pe, double *ke, double *virial);
 
+/* Thermodynamic outputs of one replica at one time. */
+typedef struct {
+    double pe, ke;           /* as md_energy                                        */
+    double etot;             /* pe + ke                                             */
+    double virial;           /* W = sum_pairs r_ij . F_ij                           */
+    double temperature;      /* T = 2 KE / (3N - 3) (momentum removed; 0 if N = 1)  */
+    double pressure;         /* P = (N T + W / 3) / V (0 if N = 1)                  */
+} md_thermo_rec;
+
+/* Temperature, pressure and total energy from (PE, KE, W) records, computed
+ * on the device.  energies: host, nrec x nrep x 3 doubles in the layout of
+ * md_run's energy log; or NULL with nrec = 1 for the current state (as
+ * md_energy).  out: host, nrec x nrep records.  Synchronises.  Not in the
+ * paper, whose outputs are the Eq. 2 forces and energies; the formulas are
+ * the standard ones for a periodic LJ system.
+ * Errors: MD_ERR_INVAL, MD_ERR_NOMEM, MD_ERR_CUDA. */
+int md_thermo(md_ctx *ctx, const double *energies, int64_t nrec, md_thermo_rec *out);
+
 /* Advances nsteps velocity-Verlet steps with the rebuild schedule; the
  * per-step work is replayed from CUDA graphs.  When energies is not NULL and
  * energy_every > 0, (PE, KE, W) of every replica after steps s0 + k *
@@ -284,6 +302,23 @@ int md_set_spring_dashpot(md_ctx *ctx, double k_spring, double gamma);
 int md_adjoint(md_ctx *ctx, int64_t nsteps, int64_t window, int32_t ckpt_every, double *loss,
                double *g_eps, double *g_sigma, double *g_x0, double *g_v0);
 
+/* md_adjoint with g_x0 and g_v0 in device memory of the current device (n x
+ * 3 doubles, caller order; each may be NULL), written on the context's
+ * stream; loss, g_eps and g_sigma stay host scalars.  Synchronises like
+ * md_adjoint.  Errors: those of md_adjoint, and MD_ERR_INVAL if g_x0 or g_v0
+ * is not device memory. */
+int md_adjoint_device(md_ctx *ctx, int64_t nsteps, int64_t window, int32_t ckpt_every,
+                      double *loss, double *g_eps, double *g_sigma, double *g_x0, double *g_v0);
+
+/* Precision of the pair terms of md_adjoint's reverse sweep (the Jacobian-
+ * vector products and the parameter derivatives): MD_MIXED evaluates them in
+ * FP32 from the cell-relative FP32 positions (the default of a mixed
+ * context), MD_FP64 in FP64 from the FP64 positions (the default of an FP64
+ * context).  The forward run keeps the context's precision, so a mixed
+ * context with MD_FP64 here differentiates its own mixed trajectory with
+ * FP64 pair terms.  Not in the paper.  Errors: MD_ERR_INVAL. */
+int md_set_adjoint_precision(md_ctx *ctx, int32_t precision);
+
 /* Chooses threads_per_atom and full/half lists by timing each candidate for
  * `steps` steps on the context's own state (which it restores), keeps the
  * fastest and reports it in *chosen (may be NULL).  Results are cached per
@@ -297,16 +332,22 @@ int md_autotune(md_ctx *ctx, int32_t steps, md_params *chosen);
  * must not call cudaMalloc because it can synchronise the device).  The
  * paper has no counterpart; this is a service of the library.
  *   pe_atom, w_atom: device, n doubles; vel: device, n x 3 doubles (row
- *   major); out3: device, 3 doubles; stream: cudaStream_t or NULL.
+ *   major, 24 bytes per atom: not a buffer of 4-double padded vectors such
+ *   as the library's own internal state); out3: device, 3 doubles; stream:
+ *   cudaStream_t or NULL.
  * Sums are taken in a fixed order (deterministic).  The only scratch is a
  * fixed 192 KiB array in the library's device data, so n may be at most
  * 33,554,432; larger n returns MD_ERR_INVAL with a message from
- * md_last_error(NULL).  No call allocates or frees device memory.  The first
- * call on a device looks up that array's device address (once per device,
- * with the device current): make it before any stream capture.  All calls
- * share the array: calls that overlap on the GPU (other streams, other
- * threads) race and must be serialised by the caller.  Every call writes the
- * scratch it reads, so nothing is left over from an earlier call.
+ * md_last_error(NULL).  No call allocates or frees device memory.  The
+ * array has its own address in every CUDA context that loads the library;
+ * the first call in a context (a device's primary context, or a driver-API
+ * context made current by the caller) looks that address up and caches it
+ * under the context's id: make that first call before any stream capture.
+ * All calls in a context share the array: calls that overlap on the GPU
+ * (other streams, other threads) race and must be serialised by the
+ * caller.  Every call writes the scratch it reads, so nothing is left over
+ * from an earlier call.  A non-sticky CUDA error left pending on the
+ * calling thread by earlier work is cleared before the launches.
  * Errors: MD_ERR_INVAL, MD_ERR_CUDA. */
 int md_energy_sums_static(int64_t n, const double *pe_atom, const double *w_atom,
                           const double *vel, double mass, double *out3, void *stream);

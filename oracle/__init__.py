@@ -85,6 +85,8 @@ def _load():
                 "orc_energy_list": (None, [ctypes.c_int64, _D, _D, ctypes.c_int32, _I32, _I32, P,
                                            _D, _D, _D]),
                 "orc_kinetic": (ctypes.c_double, [ctypes.c_int64, _D, ctypes.c_double]),
+                "orc_thermo": (None, [ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_int64, ctypes.c_double, _D]),
                 "orc_forces_sd_list": (None, [ctypes.c_int64, _D, _D, _D, ctypes.c_int32, _I32,
                                               _I32, P, _D]),
                 "orc_forces_sd_brute": (None, [ctypes.c_int64, _D, _D, _D, P, _D]),
@@ -356,6 +358,14 @@ def energy_atoms(x, L, rows, half=False, **kw):
 def kinetic(v, mass=1.0):
     v = _f64(v, (-1, 3))
     return float(_load().orc_kinetic(v.shape[0], _dp(v), float(mass)))
+
+
+def thermo(pe, ke, w, n, L):
+    """dict(pe, ke, etot, virial, temperature, pressure) of one (PE, KE, W)
+    record of an n-atom box of sides L (orc_thermo)."""
+    out = np.zeros(6, np.float64)
+    _load().orc_thermo(float(pe), float(ke), float(w), int(n), float(np.prod(_box(L))), _dp(out))
+    return dict(zip(("pe", "ke", "etot", "virial", "temperature", "pressure"), out.tolist()))
 
 
 def vv_run(x, v, L, nsteps, step0=0, energies=False, **kw):

@@ -562,6 +562,23 @@ double orc_kinetic(int64_t n, const double *v, double mass)
     return 0.5 * mass * s;
 }
 
+/* Thermodynamic outputs of one (PE, KE, W) record of an n-atom periodic box
+ * of volume vol: the temperature with the centre-of-mass momentum removed,
+ * T = 2 KE / (3n - 3), and the virial pressure P = (n T + W / 3) / vol.  Not
+ * printed in the paper (its outputs are forces and energies); these are the
+ * textbook definitions for a pair potential in a periodic box.  n = 1 has
+ * no free degree: T = P = 0. */
+void orc_thermo(double pe, double ke, double w, int64_t n, double vol, double out[6])
+{
+    const double t = n > 1 ? 2.0 * ke / (3.0 * (double)n - 3.0) : 0.0;
+    out[0] = pe;
+    out[1] = ke;
+    out[2] = pe + ke;
+    out[3] = w;
+    out[4] = t;
+    out[5] = n > 1 ? ((double)n * t + w / 3.0) / vol : 0.0;
+}
+
 /* ---------------------------------------------------------------------------
  * Velocity Verlet with the fixed rebuild schedule (Sec. 3.2 Eq. 1, Sec. 6).
  * ------------------------------------------------------------------------- */

@@ -258,6 +258,17 @@ __global__ void __launch_bounds__(256) k_adjoint_axpy(int64_t n, double dt, cons
     if (wbar32) wbar32[a] = make_float4((float)w.x, (float)w.y, (float)w.z, 0.f);
 }
 
+// out (n x 3 doubles) <- a (padded FP64 3-vectors), same atom order.
+__global__ void __launch_bounds__(256) k_unpad3(int64_t n, const dvec4 *a, double *out)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const dvec4 v = a[t];
+    out[3 * t] = v.x;
+    out[3 * t + 1] = v.y;
+    out[3 * t + 2] = v.z;
+}
+
 // Deterministic sum of two per-atom arrays (one block, fixed order).
 __global__ void __launch_bounds__(1024) k_sum2(int64_t n, const double *a, const double *b,
                                                double *out)
@@ -312,6 +323,14 @@ int launch_adjoint_axpy(int64_t n, double dt, const dvec4 *xbar, dvec4 *wbar, fl
                         cudaStream_t st, int *nl)
 {
     k_adjoint_axpy<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, dt, xbar, wbar, wbar32);
+    *nl += 1;
+    return (int)cudaGetLastError();
+}
+
+int launch_unpad3(int64_t n, const dvec4 *a, double *out, cudaStream_t st, int *nl)
+{
+    if (n <= 0) return 0;
+    k_unpad3<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, a, out);
     *nl += 1;
     return (int)cudaGetLastError();
 }

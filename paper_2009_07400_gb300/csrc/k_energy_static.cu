@@ -30,10 +30,45 @@ constexpr int64_t kMaxChunks = 8192;   // n <= 8192 * 4096 = 33,554,432 atoms
 // device address: host code obtains the address with cudaGetSymbolAddress.
 static __device__ __align__(256) double g_energy_partials[3 * kMaxChunks];
 
-// Device addresses of g_energy_partials, one per device, resolved once.
-constexpr int kMaxDevices = 64;
+// Device addresses of g_energy_partials, one per CUDA context.  The library's
+// module is loaded once per context, so the array has its own address in
+// every context that calls (a device's primary context, or a driver-API
+// context of an external engine made current on the calling thread); an
+// address resolved in one context is not valid in another.
+struct ScratchAddr {
+    unsigned long long ctx_id;   // unique id of the context (never reused in a process)
+    double *addr;
+};
+constexpr int kMaxContexts = 64;
 std::mutex g_mu;
-double *g_addr[kMaxDevices] = {nullptr};
+ScratchAddr g_addr[kMaxContexts];
+int g_naddr = 0;
+
+// cuCtxGetCurrent and cuCtxGetId fetched through the runtime (the library
+// does not link the driver library itself); null if the driver lacks them.
+void *driver_fn(const char *name, unsigned int version)
+{
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion(name, &f, version, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return f;
+}
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
+
+// Unique id of the calling thread's current context; false if unknown (no
+// current context yet, or an old driver).
+bool current_ctx_id(unsigned long long *id)
+{
+    static const CtxGetCurrentFn get_cur = (CtxGetCurrentFn)driver_fn("cuCtxGetCurrent", 4000);
+    static const CtxGetIdFn get_id = (CtxGetIdFn)driver_fn("cuCtxGetId", 12000);
+    void *ctx = nullptr;
+    return get_cur && get_id && get_cur(&ctx) == 0 && ctx && get_id(ctx, id) == 0;
+}
 
 __global__ void __launch_bounds__(256) k_static_chunks(int64_t n, const double *pe, const double *w,
                                                        const double *vel, double mass,
@@ -91,31 +126,41 @@ extern "C" int md_energy_sums_static(int64_t n, const double *pe_atom, const dou
                               " atoms (fixed scratch size)");
         return MD_ERR_INVAL;
     }
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-        mdk::set_global_error(std::string("md_energy_sums_static: cudaGetDevice: ") + cudaGetErrorString(e));
-        return MD_ERR_CUDA;
-    }
+    // the calling thread's current context: a device's primary context, or
+    // a context the caller made current through the driver API
+    unsigned long long ctx_id = 0;
+    bool keyed = current_ctx_id(&ctx_id);
     double *scratch = nullptr;
     {
         std::lock_guard<std::mutex> g(g_mu);
-        if (!g_addr[dev]) {   // first call on this device: resolve the array's device address
+        for (int k = 0; keyed && k < g_naddr; k++)
+            if (g_addr[k].ctx_id == ctx_id) scratch = g_addr[k].addr;
+        if (!scratch) {
+            // first call in this context: resolve the array's address (this
+            // also makes the device's primary context current when the
+            // thread had none; host-only work, nothing is allocated)
             void *p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_energy_partials);
+            cudaError_t e = cudaGetSymbolAddress(&p, g_energy_partials);
             if (e != cudaSuccess) {
                 mdk::set_global_error(std::string("md_energy_sums_static: cudaGetSymbolAddress: ") +
                                       cudaGetErrorString(e));
                 return MD_ERR_CUDA;
             }
-            g_addr[dev] = (double *)p;
+            scratch = (double *)p;
+            keyed = current_ctx_id(&ctx_id);
+            // without a context id nothing is cached and the next call
+            // resolves the address again
+            if (keyed && g_naddr < kMaxContexts) g_addr[g_naddr++] = {ctx_id, scratch};
         }
-        scratch = g_addr[dev];
     }
+    // an error left pending by unrelated earlier work on this thread would
+    // otherwise be reported as this call's launch failure: clear it (a
+    // sticky error of a broken context makes the launches below fail anyway)
+    cudaGetLastError();
     cudaStream_t st = (cudaStream_t)stream;
     k_static_chunks<<<(unsigned)nchunks, 256, 0, st>>>(n, pe_atom, w_atom, vel, mass, scratch);
     k_static_final<<<1, 96, 0, st>>>(nchunks, scratch, out3);
-    e = cudaGetLastError();
+    const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         mdk::set_global_error(std::string("md_energy_sums_static: launch: ") + cudaGetErrorString(e));
         return MD_ERR_CUDA;

@@ -156,6 +156,30 @@ __global__ void __launch_bounds__(1024) k_energy_final(const int64_t *chunk_firs
     if (!out && threadIdx.x == 0) st->elog_cursor += 1;
 }
 
+// Thermodynamic outputs of (PE, KE, W) records, one thread per (record,
+// replica): total energy, T = 2 KE / (3 N - 3) (the momentum-free degrees of
+// freedom) and P = (N T + W / 3) / V.  rec: nrec x nrep x 3; out: nrec x
+// nrep x 6 (pe, ke, etot, w, T, P).  N = 1 has no free degree: T and P are
+// reported as 0.
+__global__ void __launch_bounds__(256) k_thermo(const Rep *reps, int32_t nrep, int64_t nrec,
+                                                const double *rec, double *out)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nrec * nrep) return;
+    const Rep &R = reps[t % nrep];
+    const double pe = rec[3 * t], ke = rec[3 * t + 1], w = rec[3 * t + 2];
+    const double nat = (double)R.natoms;
+    const double vol = R.L[0] * R.L[1] * R.L[2];
+    const double temp = R.natoms > 1 ? 2.0 * ke / (3.0 * nat - 3.0) : 0.0;
+    double *o = out + 6 * t;
+    o[0] = pe;
+    o[1] = ke;
+    o[2] = pe + ke;
+    o[3] = w;
+    o[4] = temp;
+    o[5] = R.natoms > 1 ? (nat * temp + w / 3.0) / vol : 0.0;
+}
+
 // out (n x 3, caller order) <- x / v / F of the cell-ordered state.
 __global__ void __launch_bounds__(256) k_gather_out(Dev d, int what, int mixed, double *out)
 {
@@ -240,6 +264,16 @@ int launch_energy(const Dev &d, const LJ &lj, int precision, bool ke_from_v,
 }
 
 int64_t energy_chunks_of(int64_t natoms) { return (natoms + kChunk - 1) / kChunk; }
+
+int launch_thermo(const Rep *reps, int32_t nrep, int64_t nrec, const double *rec, double *out,
+                  cudaStream_t st, int *nl)
+{
+    const int64_t t = nrec * nrep;
+    if (t <= 0) return 0;
+    k_thermo<<<(unsigned)((t + 255) / 256), 256, 0, st>>>(reps, nrep, nrec, rec, out);
+    *nl += 1;
+    return (int)cudaGetLastError();
+}
 
 int launch_gather_out(const Dev &d, int what, double *out, cudaStream_t st, int *nl)
 {

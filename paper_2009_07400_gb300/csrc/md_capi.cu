@@ -65,6 +65,8 @@ struct md_ctx {
     bool own_stream = false;
     int device = 0;
     int tpa = 1;
+    int adj_prec = -1;      // md_set_adjoint_precision: pair terms of the reverse
+                            // sweep in MD_FP64 / MD_MIXED; -1 = the context's
 
     Rep *reps_d = nullptr;
     int32_t *rep_of_d = nullptr;
@@ -812,6 +814,32 @@ int md_energy(md_ctx *c, double *pe, double *ke, double *w)
     return MD_OK;
 }
 
+int md_thermo(md_ctx *c, const double *energies, int64_t nrec, md_thermo_rec *out)
+{
+    if (!c || !out || nrec < 1 || (!energies && nrec != 1))
+        return fail(c, MD_ERR_INVAL, "bad argument");
+    const size_t nin = 3 * (size_t)nrec * (size_t)c->nrep, nout = 6 * (size_t)nrec * (size_t)c->nrep;
+    int rc = MD_OK, nl = 0;
+    double *buf = nullptr;   // records in, thermo records out
+    if ((rc = dalloc(c, &buf, nin + nout))) return rc;
+    if (energies) {
+        cudaError_t e = cudaMemcpyAsync(buf, energies, sizeof(double) * nin, cudaMemcpyHostToDevice, c->st);
+        if (e != cudaSuccess) rc = fail(c, MD_ERR_CUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
+    } else if (!(rc = ensure_list(c)) && !(rc = enq_force(c, EPI_F, true, &nl))) {
+        rc = enq_energy(c, true, buf, &nl);
+    }
+    if (!rc && launch_thermo(c->reps_d, c->nrep, nrec, buf, buf + nin, c->st, &nl))
+        rc = fail(c, MD_ERR_CUDA, "thermo launch failed");
+    c->launches += nl;
+    if (!rc) {
+        cudaError_t e = cudaMemcpyAsync(out, buf + nin, sizeof(double) * nout, cudaMemcpyDeviceToHost, c->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+        if (e != cudaSuccess) rc = fail(c, MD_ERR_CUDA, std::string("thermo copy: ") + cudaGetErrorString(e));
+    }
+    cudaFree(buf);
+    return rc;
+}
+
 int md_run(md_ctx *c, int64_t nsteps, int32_t energy_every, double *energies)
 {
     if (!c || nsteps < 0) return fail(c, MD_ERR_INVAL, "bad argument");
@@ -1181,11 +1209,13 @@ int md_set_spring_dashpot(md_ctx *c, double k_spring, double gamma)
     return MD_OK;
 }
 
-int md_adjoint(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt, double *loss,
-               double *g_eps, double *g_sigma, double *g_x0, double *g_v0)
+static int adjoint_impl(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt, double *loss,
+                        double *g_eps, double *g_sigma, double *g_x0, double *g_v0, bool on_device)
 {
     if (!c || !loss || nsteps < 1 || window < 1 || window > nsteps || ckpt < 1)
         return fail(c, MD_ERR_INVAL, "bad argument");
+    if (on_device && ((g_x0 && !is_device_pointer(g_x0)) || (g_v0 && !is_device_pointer(g_v0))))
+        return fail(c, MD_ERR_INVAL, "g_x0 / g_v0 are not device pointers of the current device");
     if (c->nrep != 1) return fail(c, MD_ERR_INVAL, "md_adjoint takes a single system");
     if (c->disp)
         return fail(c, MD_ERR_INVAL, "md_adjoint needs the fixed rebuild schedule (rebuild_every > 0)");
@@ -1194,7 +1224,9 @@ int md_adjoint(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt, double *
     if (every % ckpt != 0 || nsteps % ckpt != 0)
         return fail(c, MD_ERR_INVAL, "ckpt_every must divide rebuild_every and nsteps");
     const int64_t n = c->n, nck = nsteps / ckpt + 1;
-    const bool mixed = is_mixed(c);
+    // precision of the reverse sweep's pair terms (the forward run always
+    // uses the context's precision)
+    const bool mixed = c->adj_prec < 0 ? is_mixed(c) : c->adj_prec == MD_MIXED;
     const int half0 = c->p.half_list, tpa0 = c->tpa;
     int rc = MD_OK;
     if (half0 && (rc = apply_tuning(c, 1, 0))) return rc;   // the adjoint walks full lists
@@ -1332,16 +1364,26 @@ int md_adjoint(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt, double *
         }
     }
     if (!rc && launch_sum2(n, ge, gs, g2, c->st, &nl)) rc = fail(c, MD_ERR_CUDA, "sum launch failed");
+    if (!rc && on_device) {
+        // gradients straight into the caller's device buffers (n x 3)
+        if ((g_x0 && launch_unpad3(n, xbar, g_x0, c->st, &nl)) ||
+            (g_v0 && launch_unpad3(n, wbar, g_v0, c->st, &nl)))
+            rc = fail(c, MD_ERR_CUDA, "gradient copy launch failed");
+    }
     if (!rc) {
         double g[2];
-        std::vector<dvec4> hx((size_t)n), hw((size_t)n);
         CK(cudaMemcpyAsync(g, g2, sizeof(g), cudaMemcpyDeviceToHost, c->st));
-        CK(cudaMemcpyAsync(hx.data(), xbar, sizeof(dvec4) * n, cudaMemcpyDeviceToHost, c->st));
-        CK(cudaMemcpyAsync(hw.data(), wbar, sizeof(dvec4) * n, cudaMemcpyDeviceToHost, c->st));
+        std::vector<dvec4> hx, hw;
+        if (!on_device) {
+            hx.resize((size_t)n);
+            hw.resize((size_t)n);
+            CK(cudaMemcpyAsync(hx.data(), xbar, sizeof(dvec4) * n, cudaMemcpyDeviceToHost, c->st));
+            CK(cudaMemcpyAsync(hw.data(), wbar, sizeof(dvec4) * n, cudaMemcpyDeviceToHost, c->st));
+        }
         CK(cudaStreamSynchronize(c->st));
         if (g_eps) *g_eps = g[0];
         if (g_sigma) *g_sigma = g[1];
-        for (int64_t a = 0; a < n; a++) {
+        for (int64_t a = 0; !on_device && a < n; a++) {
             if (g_x0) { g_x0[3 * a] = hx[a].x; g_x0[3 * a + 1] = hx[a].y; g_x0[3 * a + 2] = hx[a].z; }
             if (g_v0) { g_v0[3 * a] = hw[a].x; g_v0[3 * a + 1] = hw[a].y; g_v0[3 * a + 2] = hw[a].z; }
         }
@@ -1351,6 +1393,26 @@ int md_adjoint(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt, double *
     c->forces_valid = false;
     if (!rc && half0) rc = apply_tuning(c, tpa0, half0);
     return rc;
+}
+
+int md_adjoint(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt, double *loss,
+               double *g_eps, double *g_sigma, double *g_x0, double *g_v0)
+{
+    return adjoint_impl(c, nsteps, window, ckpt, loss, g_eps, g_sigma, g_x0, g_v0, false);
+}
+
+int md_adjoint_device(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt, double *loss,
+                      double *g_eps, double *g_sigma, double *g_x0, double *g_v0)
+{
+    return adjoint_impl(c, nsteps, window, ckpt, loss, g_eps, g_sigma, g_x0, g_v0, true);
+}
+
+int md_set_adjoint_precision(md_ctx *c, int32_t precision)
+{
+    if (!c || (precision != MD_FP64 && precision != MD_MIXED))
+        return fail(c, MD_ERR_INVAL, "precision must be MD_FP64 or MD_MIXED");
+    c->adj_prec = precision;
+    return MD_OK;
 }
 
 int md_autotune(md_ctx *c, int32_t steps, md_params *chosen)

@@ -317,6 +317,10 @@ int launch_energy(const Dev &d, const LJ &lj, int precision, bool ke_from_v,
                   double *partials, double *out3, double *log_base, cudaStream_t st,
                   int *nlaunch);
 int64_t energy_chunks_of(int64_t natoms);
+// (PE, KE, W) records (device, nrec x nrep x 3) -> (pe, ke, etot, W, T, P)
+// records (device, nrec x nrep x 6)
+int launch_thermo(const Rep *reps, int32_t nrep, int64_t nrec, const double *rec, double *out,
+                  cudaStream_t st, int *nlaunch);
 // what: 0 positions, 1 velocities, 2 FP64 forces, 3 mixed-path forces
 int launch_gather_out(const Dev &d, int what, double *out_dev, cudaStream_t st, int *nlaunch);
 int launch_scatter_in(const Dev &d, const double *pos_dev, const double *vel_dev,
@@ -344,5 +348,6 @@ int launch_adjoint_axpy(int64_t n, double dt, const dvec4 *xbar, dvec4 *wbar, fl
                         cudaStream_t st, int *nlaunch);
 int launch_sum2(int64_t n, const double *a, const double *b, double *out, cudaStream_t st,
                 int *nlaunch);
+int launch_unpad3(int64_t n, const dvec4 *a, double *out, cudaStream_t st, int *nlaunch);
 
 }  // namespace mdk

@@ -34,6 +34,7 @@ ABI_SYMBOLS = [
     "md_set_lj", "md_adjoint", "md_energy_sums_static", "md_create_device",
     "md_set_state_device", "md_get_positions_device", "md_get_velocities_device",
     "md_get_forces_device", "md_set_spring_dashpot", "md_set_step",
+    "md_set_adjoint_precision", "md_thermo", "md_adjoint_device",
 ]
 
 
@@ -60,6 +61,12 @@ class md_phase_times(ctypes.Structure):
                 ("other_ms", ctypes.c_double), ("force_launches", ctypes.c_int64),
                 ("neigh_launches", ctypes.c_int64), ("other_launches", ctypes.c_int64),
                 ("steps", ctypes.c_int64), ("mean_neighbors", ctypes.c_double)]
+
+
+class md_thermo_rec(ctypes.Structure):
+    _fields_ = [("pe", ctypes.c_double), ("ke", ctypes.c_double), ("etot", ctypes.c_double),
+                ("virial", ctypes.c_double), ("temperature", ctypes.c_double),
+                ("pressure", ctypes.c_double)]
 
 
 class md_info(ctypes.Structure):
@@ -125,6 +132,10 @@ def load(path: str | None = None):
                 "md_get_forces_device": [ctx, _P],
                 "md_set_spring_dashpot": [ctx, ctypes.c_double, ctypes.c_double],
                 "md_set_step": [ctx, ctypes.c_int64],
+                "md_set_adjoint_precision": [ctx, ctypes.c_int32],
+                "md_thermo": [ctx, _D, ctypes.c_int64, ctypes.POINTER(md_thermo_rec)],
+                "md_adjoint_device": [ctx, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, _D,
+                                      _D, _D, _P, _P],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -330,19 +341,25 @@ class MDContext:
         self._check(self._lib.md_run(self._h, int(nsteps), 0, None))
         return None
 
-    def _get3(self, fn):
-        out = np.zeros((self.n, 3))
+    def _get3(self, fn, out=None):
+        """n x 3 doubles from fn into `out` (a C-contiguous float64 array, e.g.
+        one in pinned host memory) or a new array."""
+        if out is None:
+            out = np.zeros((self.n, 3))
+        elif (out.dtype != np.float64 or out.shape != (self.n, 3)
+              or not out.flags["C_CONTIGUOUS"]):
+            raise ValueError("out must be a C-contiguous float64 n x 3 array")
         self._check(fn(self._h, out.ctypes.data_as(_D)))
         return out
 
-    def positions(self):
-        return self._get3(self._lib.md_get_positions)
+    def positions(self, out=None):
+        return self._get3(self._lib.md_get_positions, out)
 
-    def velocities(self):
-        return self._get3(self._lib.md_get_velocities)
+    def velocities(self, out=None):
+        return self._get3(self._lib.md_get_velocities, out)
 
-    def forces(self):
-        return self._get3(self._lib.md_get_forces)
+    def forces(self, out=None):
+        return self._get3(self._lib.md_get_forces, out)
 
     def cells(self):
         """(cell_start per replica incl. end, cell_atoms replica-local ids)."""
@@ -395,6 +412,31 @@ class MDContext:
                                          gx.ctypes.data_as(_D), gv.ctypes.data_as(_D)))
         return loss.value, ge.value, gs.value, gx, gv
 
+    def adjoint_device(self, nsteps, window, ckpt_every=10, g_x0=None, g_v0=None):
+        """md_adjoint_device: (loss, dL/deps, dL/dsigma, dL/dx0, dL/dv0) with the
+        two n x 3 gradients in CUDA float64 tensors (new ones if None)."""
+        import torch
+        if g_x0 is None:
+            g_x0 = torch.empty((self.n, 3), dtype=torch.float64, device="cuda")
+        if g_v0 is None:
+            g_v0 = torch.empty((self.n, 3), dtype=torch.float64, device="cuda")
+        g_x0, g_v0 = _dev3(g_x0), _dev3(g_v0)
+        if tuple(g_x0.shape) != (self.n, 3) or tuple(g_v0.shape) != (self.n, 3):
+            raise ValueError("expected n x 3 tensors")
+        loss = ctypes.c_double()
+        ge = ctypes.c_double()
+        gs = ctypes.c_double()
+        self._before_device_call(torch)
+        self._check(self._lib.md_adjoint_device(self._h, int(nsteps), int(window), int(ckpt_every),
+                                                ctypes.byref(loss), ctypes.byref(ge),
+                                                ctypes.byref(gs), ctypes.c_void_p(g_x0.data_ptr()),
+                                                ctypes.c_void_p(g_v0.data_ptr())))
+        return loss.value, ge.value, gs.value, g_x0, g_v0
+
+    def set_adjoint_precision(self, precision):
+        """Precision of the reverse sweep's pair terms (MD_FP64 or MD_MIXED)."""
+        self._check(self._lib.md_set_adjoint_precision(self._h, int(precision)))
+
     def set_capacity(self, cap):
         self._check(self._lib.md_set_capacity(self._h, int(cap)))
 
@@ -403,18 +445,24 @@ class MDContext:
         self._check(self._lib.md_set_step(self._h, int(step)))
 
     def thermo(self, energies=None):
-        """Thermodynamic outputs per replica from (PE, KE, W) triples (the
-        last axis of md_run's energy log, or md_energy now): total energy,
-        temperature T = 2 KE / (3 N - 3) and pressure P = (N T + W / 3) / V."""
+        """md_thermo: per-replica pe, ke, etot, virial, temperature and
+        pressure from (PE, KE, W) triples (md_run's energy log, any leading
+        shape) or, with None, from the current state.  Arrays of shape
+        energies.shape[:-1] (or (nrep,))."""
         if energies is None:
-            energies = np.stack(self.energy(), axis=-1)
-        e = np.asarray(energies, np.float64)
-        pe, ke, w = e[..., 0], e[..., 1], e[..., 2]
-        n = self.counts.astype(np.float64)
-        vol = np.array([float(np.prod(b)) for b in self._boxes])
-        temp = 2.0 * ke / (3.0 * n - 3.0)
-        return {"pe": pe, "ke": ke, "etot": pe + ke, "virial": w, "temperature": temp,
-                "pressure": (n * temp + w / 3.0) / vol}
+            shape, arg, nrec = (self.nrep,), None, 1
+        else:
+            e = np.ascontiguousarray(energies, np.float64)
+            if e.shape[-1] != 3 or e.size % (3 * self.nrep) != 0:
+                raise ValueError("expected (..., nrep, 3) energy records")
+            shape, nrec = e.shape[:-1], e.size // (3 * self.nrep)
+            arg = e.ctypes.data_as(_D)
+        out = (md_thermo_rec * (nrec * self.nrep))()
+        self._check(self._lib.md_thermo(self._h, arg, nrec, out))
+        raw = np.ctypeslib.as_array(ctypes.cast(out, ctypes.POINTER(ctypes.c_double)),
+                                    shape=(nrec * self.nrep * 6,)).reshape(shape + (6,)).copy()
+        names = ("pe", "ke", "etot", "virial", "temperature", "pressure")
+        return {k: raw[..., q] for q, k in enumerate(names)}
 
     def info(self) -> md_info:
         inf = md_info()

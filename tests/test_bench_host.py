@@ -52,9 +52,12 @@ def test_ncu_traffic_follows_the_kernel_source():
 def test_reference_arm_line():
     """--impl reference times the oracle on a bounded sample and prints one
     JSON line with the native arm's metric and unit."""
+    import time
+    t0 = time.perf_counter()
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
                         "--steps", "1", "--warmup", "3"],
                        capture_output=True, text=True, timeout=600, cwd=ROOT)
+    wall = time.perf_counter() - t0
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1
@@ -64,3 +67,9 @@ def test_reference_arm_line():
     assert d["value"] > 0 and d["steps"] == 1 and d["warmup"] == 3
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    # the timed region (ms_per_step x steps) lies inside the process's run,
+    # and the value is the atoms x time steps of that region over its length
+    assert d["ms_per_step"] * d["steps"] / 1e3 < wall
+    ts = d["config"]["timesteps_per_step"]
+    assert d["value"] == pytest.approx(d["config"]["atoms"] * ts * d["steps"]
+                                       / (d["ms_per_step"] * d["steps"] / 1e3), rel=1e-9)

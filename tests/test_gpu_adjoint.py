@@ -143,6 +143,30 @@ def test_autograd_function(md, orc, small):
     assert np.linalg.norm(xt.grad.numpy() - 2 * gx_o) < 1e-9 * np.linalg.norm(2 * gx_o)
 
 
+def test_autograd_function_device(md, orc, small):
+    """The same through CUDA tensors: the state goes in and the gradients
+    come out on the device (md_set_state_device / md_adjoint_device)."""
+    torch = pytest.importorskip("torch")
+    from paper_2009_07400_gb300.autodiff import rollout_loss
+    x0, v0, L = small
+    eps = torch.tensor(1.0, dtype=torch.float64, device="cuda", requires_grad=True)
+    sig = torch.tensor(1.0, dtype=torch.float64, device="cuda", requires_grad=True)
+    xt = torch.tensor(x0, dtype=torch.float64, device="cuda", requires_grad=True)
+    vt = torch.tensor(v0, dtype=torch.float64, device="cuda", requires_grad=True)
+    with md.MDContext(x0, v0, L, precision=md.MD_FP64) as ctx:
+        loss = rollout_loss(ctx, eps, sig, xt, vt, nsteps=20, window=10, ckpt_every=10)
+        (3.0 * loss).backward()
+    assert xt.grad.is_cuda and vt.grad.is_cuda
+    loss_o, ge_o, gs_o, gx_o, gv_o = orc.adjoint(x0, v0, L, 20, 10)
+    assert rel(loss.item(), loss_o) < 1e-12
+    assert rel(eps.grad.item(), 3 * ge_o) < 1e-9
+    assert rel(sig.grad.item(), 3 * gs_o) < 1e-9
+    gx = xt.grad.cpu().numpy()
+    gv = vt.grad.cpu().numpy()
+    assert np.linalg.norm(gx - 3 * gx_o) < 1e-9 * np.linalg.norm(3 * gx_o)
+    assert np.linalg.norm(gv - 3 * gv_o) < 1e-9 * np.linalg.norm(3 * gv_o)
+
+
 def test_adjoint_workspace_reuse(md, small):
     """md_adjoint keeps its workspace between calls and grows it when a call
     needs more checkpoints or a longer block: calls of growing and shrinking

@@ -641,18 +641,36 @@ def test_resume_from_saved_state(md, orc):
 
 
 def test_thermo_outputs(md, orc):
+    """md_thermo (T, P and E_tot on the device) against the oracle's
+    definitions on the same (PE, KE, W) records: md_run's energy log of
+    one system and of a batch of replicas, and the current state."""
     s = inputs.workload("fcc8_2048")
     with ctx_of(md, s, precision=md.MD_FP64) as ctx:
         E = ctx.run(40, energy_every=20)
         th = ctx.thermo(E)
-        pe, ke, w = E[-1, 0]
-        t_ref = 2.0 * ke / (3 * s.n - 3)
-        assert th["temperature"][-1, 0] == pytest.approx(t_ref, rel=1e-15)
-        assert th["pressure"][-1, 0] == pytest.approx((s.n * t_ref + w / 3) / np.prod(s.box), rel=1e-15)
-        assert th["etot"][-1, 0] == pytest.approx(pe + ke, rel=1e-15)
+        assert th["temperature"].shape == (2, 1)
+        for k in range(2):
+            ref = orc.thermo(*E[k, 0], s.n, s.box)
+            for key, val in ref.items():
+                assert th[key][k, 0] == pytest.approx(val, rel=1e-14, abs=1e-300)
         now = ctx.thermo()
-        v = ctx.velocities()
-        assert now["ke"][0] == pytest.approx(0.5 * np.sum(v ** 2), rel=1e-12)
+        pe, ke, w = (q[0] for q in ctx.energy())
+        ref = orc.thermo(pe, ke, w, s.n, s.box)
+        for key, val in ref.items():
+            assert now[key][0] == pytest.approx(val, rel=1e-14)
+        assert now["ke"][0] == pytest.approx(orc.kinetic(ctx.velocities()), rel=1e-12)
+    reps = inputs.replica_ensemble(3, seed=77)
+    pos = np.concatenate([r.pos for r in reps])
+    vel = np.concatenate([r.vel for r in reps])
+    with md.MDContext(pos, vel, [r.box for r in reps], counts=[r.n for r in reps],
+                      precision=md.MD_FP64) as ctx:
+        E = ctx.run(20, energy_every=10)
+        th = ctx.thermo(E)
+        for k in range(2):
+            for q, r in enumerate(reps):
+                ref = orc.thermo(*E[k, q], r.n, r.box)
+                assert th["pressure"][k, q] == pytest.approx(ref["pressure"], rel=1e-14)
+                assert th["temperature"][k, q] == pytest.approx(ref["temperature"], rel=1e-14)
 
 
 def test_injected_allocation_failures_are_clean(md):

@@ -281,6 +281,30 @@ def test_temperature_of_inputs():
     assert np.abs(s.vel.sum(axis=0)).max() < 1e-10
 
 
+def test_thermo_closed_forms(orc):
+    """orc_thermo against closed forms: with W = 0 it is the ideal-gas law
+    P = rho T; with the inputs' velocities T is the 1.44 they were drawn at
+    (3N - 3 degrees of freedom, momentum removed); a perfect FCC lattice at
+    rest has T = 0 and P = W / (3V) with W the textbook shell sum; one atom
+    has no free degree."""
+    s = inputs.fcc_system(5, temperature=1.44, seed=3)
+    vol = float(np.prod(s.box))
+    th = orc.thermo(0.0, orc.kinetic(s.vel), 0.0, s.n, s.box)
+    assert th["temperature"] == pytest.approx(1.44, rel=1e-12)
+    assert th["pressure"] == pytest.approx(s.n / vol * 1.44, rel=1e-12)
+    lat = inputs.fcc_system(5, density=0.8442, jitter=0.0, seed=5)
+    x = orc.wrap(lat.pos, lat.box)
+    pe, w = orc.energy_list(x, lat.box, orc.neighbors_cells(x, lat.box, RC + SKIN, half=True),
+                            half=True)
+    pe_exact, w_exact = lattice_sums(0.8442)
+    th = orc.thermo(pe, 0.0, w, lat.n, lat.box)
+    assert th["temperature"] == 0.0
+    assert th["pressure"] == pytest.approx(0.8442 * w_exact / 3.0, rel=1e-10)
+    assert th["etot"] == pytest.approx(lat.n * pe_exact, rel=1e-12)
+    one = orc.thermo(-1.0, 2.0, 3.0, 1, 10.0)
+    assert one["temperature"] == 0.0 and one["pressure"] == 0.0 and one["etot"] == 1.0
+
+
 # --------------------------------------------------------------------------
 # Velocity Verlet (Eq. 1): second order, time reversible, energy conserving.
 # --------------------------------------------------------------------------
