@@ -52,7 +52,12 @@ STEPS_PER_CYCLE = 20                    # time steps per rebuild cycle
 CYCLES_PER_STEP = 10                    # rebuild cycles per benchmark step
 TIMESTEPS_PER_STEP = STEPS_PER_CYCLE * CYCLES_PER_STEP
 FORCE_SRC = os.path.join(ROOT, "paper_2009_07400_gb300", "csrc", "k_force.cu")
-PROFILE_MD = os.path.join(ROOT, "profiles", "force_mixed_fcc64.md")
+# committed ncu summaries of the mixed force kernel on the benchmark workload,
+# per list type (the kernel the autotuner picks)
+PROFILE_MD = {0: os.path.join(ROOT, "profiles", "force_mixed_fcc64.md"),
+              4: os.path.join(ROOT, "profiles", "force_mixed_group4_fcc64.md"),
+              2: os.path.join(ROOT, "profiles", "force_mixed_group2_fcc64.md")}
+LIST_NAMES = {0: "full", 1: "half", 2: "group2", 4: "group4"}
 
 
 def make_workload(name, rank=0, world=1):
@@ -156,14 +161,15 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def ncu_traffic():
-    """DRAM bytes per launch of the mixed force kernel from the committed ncu
-    summary, if it was taken on the current kernel source (else None).  Not
-    measured in the run: ncu's counters need a profiler, and a number taken
-    under one is no bench value."""
-    if not os.path.exists(PROFILE_MD):
+def ncu_traffic(list_type=0):
+    """DRAM bytes per launch of the mixed force kernel of `list_type` from the
+    committed ncu summary, if it was taken on the current kernel source (else
+    None).  Not measured in the run: ncu's counters need a profiler, and a
+    number taken under one is no bench value."""
+    path = PROFILE_MD.get(list_type)
+    if not path or not os.path.exists(path):
         return None
-    text = open(PROFILE_MD).read()
+    text = open(path).read()
     h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
     t = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", text)
     if not h or not t:
@@ -173,31 +179,37 @@ def ncu_traffic():
 
 
 def parse_tuned(text):
-    """--tuned "TPA,HALF,TPA64,HALF64" -> ({mixed kwargs}, {FP64 kwargs}) or
-    None.  Skips the autotuner: under a profiler its timings include the
-    profiler's per-launch overhead and it may choose another candidate than
-    the timed run did, so profiling commands pin the timed run's choice."""
+    """--tuned "TPA,LIST,TPA64,LIST64" -> ({mixed kwargs}, {FP64 kwargs}) or
+    None (LIST: 0 full, 1 half, 2 / 4 group lists).  Skips the autotuner:
+    under a profiler its timings include the profiler's per-launch overhead
+    and it may choose another candidate than the timed run did, so profiling
+    commands pin the timed run's choice."""
     if not text:
         return None
     v = [int(x) for x in text.split(",")]
-    if len(v) != 4 or v[0] not in (1, 2, 4, 8) or v[2] not in (1, 2, 4, 8):
-        raise SystemExit("--tuned wants TPA,HALF,TPA64,HALF64 with TPA in {1,2,4,8}")
-    return (dict(threads_per_atom=v[0], half_list=bool(v[1])),
-            dict(threads_per_atom=v[2], half_list=bool(v[3])))
+    if (len(v) != 4 or v[0] not in (1, 2, 4, 8) or v[2] not in (1, 2, 4, 8)
+            or v[1] not in LIST_NAMES or v[3] not in (0, 1)):
+        raise SystemExit("--tuned wants TPA,LIST,TPA64,LIST64 with TPA in {1,2,4,8}, "
+                         "LIST in {0,1,2,4} (FP64: {0,1})")
+    return (dict(threads_per_atom=v[0], list_type=v[1]),
+            dict(threads_per_atom=v[2], list_type=v[3]))
 
 
-def algorithmic_bytes_per_atom(mean_nb, half):
+def algorithmic_bytes_per_atom(mean_nb, list_type, rows_per_atom=1.0):
     """DRAM bytes per atom and time step the dominant kernel must move.
-    Full list (force kernel with the fused velocity-Verlet epilogue): the
-    4-byte list entries, the row length, the FP32 position read and the next
-    step's FP32 position write (16 + 16), and read + write of FP64 position
-    and velocity (24 B each way, 3 doubles).  Half list (force kernel alone):
-    the list entries, the row length, the FP32 position read and the final
-    force (16); the j-side force updates are L2 atomics.  Neighbour positions
-    are gathered from L2 and are not counted."""
-    if half:
+    Full and group lists (force kernel with the fused velocity-Verlet
+    epilogue): the 4-byte list entries (mean_nb per atom: row lengths summed
+    over the rows / atoms), 4 bytes of row length per row (and 4 of group
+    table per group row), the FP32 position read and the next step's FP32
+    position write (16 + 16), and read + write of FP64 position and velocity
+    (24 B each way, 3 doubles).  Half list (force kernel alone): the list
+    entries, the row length, the FP32 position read and the final force
+    (16); the j-side force updates are L2 atomics.  Neighbour positions are
+    gathered from L2 and are not counted."""
+    if list_type == 1:
         return 4.0 * mean_nb + 4 + 16 + 16
-    return 4.0 * mean_nb + 4 + 16 + 16 + 2 * 24 + 2 * 24
+    per_row = 8.0 if list_type in (2, 4) else 4.0
+    return 4.0 * mean_nb + per_row * rows_per_atom + 16 + 16 + 2 * 24 + 2 * 24
 
 
 def time_cycles(ctx, steps, warmup, dist, torch, timesteps=TIMESTEPS_PER_STEP):
@@ -261,7 +273,7 @@ def run_gpu(args):
         else:
             tuned = ctx.autotune(STEPS_PER_CYCLE)
             res["tuned"] = {"threads_per_atom": tuned.threads_per_atom,
-                            "half_list": bool(tuned.half_list)}
+                            "list_type": int(tuned.list_type)}
         with ClockSampler(local) as clk:
             ms, launches = time_cycles(ctx, args.steps, args.warmup, dist, torch)
         res["mixed_ms"] = ms
@@ -273,7 +285,7 @@ def run_gpu(args):
     # than skin/2) on the same workload: context for the fixed schedule
     with make(precision=md.MD_MIXED, rebuild_every=0,
               threads_per_atom=res["tuned"]["threads_per_atom"],
-              half_list=res["tuned"]["half_list"]) as ctx:
+              list_type=res["tuned"]["list_type"]) as ctx:
         disp_cycles = max(1, min(args.steps, 5))
         r0 = ctx.info().rebuilds
         ms_d, _ = time_cycles(ctx, disp_cycles, 1, dist, torch, timesteps=STEPS_PER_CYCLE)
@@ -283,18 +295,18 @@ def run_gpu(args):
     # the paper's GPU runs use full lists and one thread per atom (Sec. 6): the
     # paper-shaped workload keeps that layout for its FP64 leg
     paper_shaped = name == "fcc80_2048000"
-    fp64_kw = dict(half_list=False, threads_per_atom=1) if paper_shaped else {}
+    fp64_kw = dict(list_type=0, threads_per_atom=1) if paper_shaped else {}
     if pin and not paper_shaped:
         fp64_kw = pin[1]
     with make(precision=md.MD_FP64, **fp64_kw) as ctx:
         if paper_shaped:
-            res["tuned64"] = {"threads_per_atom": 1, "half_list": False, "paper_shaped": True}
+            res["tuned64"] = {"threads_per_atom": 1, "list_type": 0, "paper_shaped": True}
         elif pin:
             res["tuned64"] = dict(pin[1], pinned=True)
         else:
             t64 = ctx.autotune(STEPS_PER_CYCLE)
             res["tuned64"] = {"threads_per_atom": t64.threads_per_atom,
-                              "half_list": bool(t64.half_list)}
+                              "list_type": int(t64.list_type)}
         ms64, _ = time_cycles(ctx, fp64_cycles, 1, dist, torch, timesteps=STEPS_PER_CYCLE)
         res["fp64_ms"] = ms64 / fp64_cycles
         res["prof64"] = ctx.profile(STEPS_PER_CYCLE)
@@ -311,7 +323,7 @@ def run_gpu(args):
     pin_pos[:] = pos
     pin_vel[:] = vel
     with make(precision=md.MD_MIXED, threads_per_atom=res["tuned"]["threads_per_atom"],
-              half_list=res["tuned"]["half_list"]) as ctx:
+              list_type=res["tuned"]["list_type"]) as ctx:
         for _ in range(2):
             ctx.set_state(pin_pos, pin_vel)
             ctx.run(TIMESTEPS_PER_STEP)
@@ -345,11 +357,11 @@ def run_gpu(args):
     if rank == 0:
         prof = res["prof"]
         force_ms_per_launch = prof.force_ms / max(1, prof.force_launches)
-        half = res["tuned"]["half_list"]
-        bpa = algorithmic_bytes_per_atom(prof.mean_neighbors, half)
+        lt = res["tuned"]["list_type"]
+        bpa = algorithmic_bytes_per_atom(prof.mean_neighbors, lt, prof.rows / n)
         achieved = bpa * n / (force_ms_per_launch / 1e3) / 1e9
         peak, peak_kind = measured_peaks()
-        traffic = ncu_traffic() if name == WORKLOAD and not half else None
+        traffic = ncu_traffic(lt) if name == WORKLOAD and lt != 1 else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
@@ -359,7 +371,7 @@ def run_gpu(args):
                                           "FP64 integration and reductions)",
             "data": "synthetic",
             "config": dict(config_dict(n, desc, seed), tuned=res["tuned"], replicas=nrep,
-                           list="half" if half else "full"),
+                           list=LIST_NAMES[lt]),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "traffic_source": ("dram__bytes_read.sum + dram__bytes_write.sum per "
@@ -368,9 +380,11 @@ def run_gpu(args):
                                             "kernel source (hash-checked); not measured in "
                                             "this run" if traffic is not None else
                                             "no ncu capture of this kernel source"),
-                         "kernel": ("k_force_mixed_half" if half else
+                         "kernel": ("k_force_mixed_half" if lt == 1 else
+                                    f"k_force_mixed_group<{lt}> (fused velocity-Verlet epilogue)"
+                                    if lt in (2, 4) else
                                     "k_force_mixed_full (fused velocity-Verlet epilogue)"),
-                         "bytes_per_atom": bpa, "mean_neighbors": prof.mean_neighbors,
+                         "bytes_per_atom": bpa, "list_entries_per_atom": prof.mean_neighbors,
                          "launch_ms": force_ms_per_launch, "peak_source": peak_kind},
             "phases_ms_per_timestep": {
                 "force": prof.force_ms / prof.steps, "neigh": prof.neigh_ms / prof.steps,
@@ -681,9 +695,9 @@ def run_adjoint(args):
     for label, prec in (("mixed", md.MD_MIXED), ("fp64", md.MD_FP64)):
         with md.MDContext(s.pos, s.vel, s.box, stream=stream.cuda_stream, precision=prec) as ctx:
             # lanes per atom of the force kernels tuned as in the main bench
-            # (md_adjoint walks full lists: a half-list choice falls back)
+            # (md_adjoint walks full per-atom lists: another choice falls back)
             tuned = ctx.autotune(20)
-            tune = dict(threads_per_atom=tuned.threads_per_atom, half_list=bool(tuned.half_list))
+            tune = dict(threads_per_atom=tuned.threads_per_atom, list_type=int(tuned.list_type))
             for _ in range(max(1, args.warmup)):
                 out = ctx.adjoint(nsteps, window, ckpt)
             torch.cuda.synchronize()

@@ -56,6 +56,16 @@ extern "C" {
 #define MD_FP64 0   /* every arithmetic step in FP64 */
 #define MD_MIXED 1  /* FP32 pair arithmetic with Kahan sums; FP64 integration and reductions */
 
+/* Verlet-list layouts (md_params.list_type).  All hold every pair with
+ * r^2 < (rc + skin)^2 at the build (Sec. 3.2, Fig. 1); md_get_neighbors
+ * returns the same exact per-atom rows for every type. */
+#define MD_LIST_FULL 0    /* one row per atom with all its neighbours (Sec. 4.2 GPU layout) */
+#define MD_LIST_HALF 1    /* each pair once (Sec. 3.2 "half of the particle pairs") */
+#define MD_LIST_GROUP2 2  /* one row per group of 2 atoms of a cell: the union of the
+                             members' rows (a superset, built with an FP32 test whose
+                             margin covers the FP64 criterion); mixed path only */
+#define MD_LIST_GROUP4 4  /* the same for groups of 4 atoms */
+
 /* Orthorhombic periodic box with origin 0: [0,lx) x [0,ly) x [0,lz). */
 typedef struct {
     double lx, ly, lz;
@@ -78,10 +88,14 @@ typedef struct {
                                 the rebuild is a conditional node of the captured
                                 step graph (no host round trip)                   */
     int32_t precision;       /* MD_FP64 or MD_MIXED                                 */
-    int32_t half_list;       /* 0: full lists; 1: half lists: pair (i,j) stored
+    int32_t list_type;       /* MD_LIST_FULL, MD_LIST_HALF (pair (i,j) stored
                                 with i iff j's nearest image is in i's upper
-                                half-space (del = x_i - x_j: del.z < 0, ties by
-                                del.y, del.x, then id_j > id_i)                 */
+                                half-space: del = x_i - x_j has del.z < 0, ties
+                                by del.y, del.x, then id_j > id_i),
+                                MD_LIST_GROUP2 or MD_LIST_GROUP4 (mixed path:
+                                consecutive atoms of a cell, in the library's
+                                cell order, share one row; each gathered
+                                neighbour position serves every member)     */
     int32_t threads_per_atom;/* 1, 2, 4 or 8 lanes per atom in the full-list force
                                 kernels; 0 = a default from the atom count and
                                 precision (md_autotune's choices measured on
@@ -92,9 +106,11 @@ typedef struct {
 typedef struct {
     int64_t n;               /* total atoms over all replicas                       */
     int32_t nrep;            /* replicas                                            */
-    int32_t precision, half_list, threads_per_atom;
-    int32_t list_capacity;   /* entries per atom the list can hold                  */
-    int32_t max_neighbors;   /* largest row of the last build                       */
+    int32_t precision, list_type, threads_per_atom;
+    int32_t list_capacity;   /* entries per row the list can hold (per group for
+                                the group list types)                           */
+    int32_t max_neighbors;   /* largest row of the last build (group rows for the
+                                group list types)                               */
     int64_t ncells;          /* cells over all replicas                             */
     int64_t step;            /* steps taken by md_run / md_integrate(2)             */
     int64_t kernel_launches; /* kernels this context launched (graph nodes counted) */
@@ -110,7 +126,9 @@ typedef struct {
     double force_ms, neigh_ms, other_ms;
     int64_t force_launches, neigh_launches, other_launches;
     int64_t steps;
-    double mean_neighbors;   /* mean row length of the list in use at the end */
+    double mean_neighbors;   /* list entries per atom of the list in use at the
+                                end: sum of its row lengths / atoms            */
+    int64_t rows;            /* rows of that list (atoms, or groups)            */
 } md_phase_times;
 
 typedef struct md_ctx md_ctx;
@@ -319,7 +337,7 @@ int md_adjoint_device(md_ctx *ctx, int64_t nsteps, int64_t window, int32_t ckpt_
  * FP64 pair terms.  Not in the paper.  Errors: MD_ERR_INVAL. */
 int md_set_adjoint_precision(md_ctx *ctx, int32_t precision);
 
-/* Chooses threads_per_atom and full/half lists by timing each candidate for
+/* Chooses threads_per_atom and the list type by timing each candidate for
  * `steps` steps on the context's own state (which it restores), keeps the
  * fastest and reports it in *chosen (may be NULL).  Results are cached per
  * (precision, atoms-per-replica bucket) for the life of the process. */

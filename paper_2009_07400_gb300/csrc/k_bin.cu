@@ -247,6 +247,35 @@ __global__ void __launch_bounds__(256) k_sort_gather(Dev d, int64_t ncells)
     }
 }
 
+// Groups of up to G consecutive atoms of one cell (the rows of a list shared
+// by a group): per cell the number of groups, ceil(count / G) ...
+__global__ void __launch_bounds__(256) k_group_count(Dev d, int64_t ncells, int G)
+{
+    if (stopped(d.status)) return;
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    const int32_t m = d.cell_start[c + 1] - d.cell_start[c];
+    d.gcnt[c] = (m + G - 1) / G;
+}
+
+// ... and, after the scan of those counts into gcell_start, the group table:
+// group gcell_start[c] + k of cell c holds atoms start + kG .. start + kG +
+// size - 1, packed as the first atom's slot (low kJBits bits) and size - 1.
+__global__ void __launch_bounds__(256) k_group_fill(Dev d, int64_t ncells, int G)
+{
+    if (stopped(d.status)) return;
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    const int32_t start = d.cell_start[c];
+    const int32_t m = d.cell_start[c + 1] - start;
+    const int32_t g0 = d.gcell_start[c];
+    for (int32_t k = 0; k * G < m; k++) {
+        const int32_t size = min(G, m - k * G);
+        if (!MD_CHECK(d, g0 + k < d.ngmax && start + k * G < d.n)) return;
+        d.grp[g0 + k] = (int32_t)((uint32_t)(start + k * G) | ((uint32_t)(size - 1) << kJBits));
+    }
+}
+
 template <int G>
 void launch_sort_gather(const Dev &d, int64_t ncells, cudaStream_t st)
 {
@@ -288,6 +317,26 @@ int launch_bin(const Dev &d, int64_t ncells, int32_t *tmp, int64_t tmp_len, cuda
     else if (mean >= 3) launch_sort_gather<8>(d, ncells, st);
     else launch_sort_gather<4>(d, ncells, st);
     *nl += 6;
+    return (int)cudaGetLastError();
+}
+
+// Group table of the current binning for groups of G atoms (G = 2 or 4):
+// d.gcnt <- groups per cell, d.gcell_start <- their exclusive prefix sums
+// (the total, the number of groups, at d.gcell_start[ncells]), d.grp <- the
+// groups.  tmp: the binning's scan scratch.
+int launch_group_table(const Dev &d, int G, int64_t ncells, int32_t *tmp, int64_t tmp_len,
+                       cudaStream_t st, int *nl)
+{
+    if (d.n <= 0) return 0;
+    const int64_t nb = (ncells + kScanPer - 1) / kScanPer;
+    if (nb + 1 > tmp_len || !d.gcnt || !d.gcell_start || !d.grp) return -1;
+    const unsigned gc = blocks_for(ncells, 256);
+    k_group_count<<<gc, 256, 0, st>>>(d, ncells, G);
+    k_scan_block<<<(unsigned)nb, 1024, 0, st>>>(d.gcnt, d.gcell_start, ncells, tmp);
+    k_scan_tops<<<1, 1024, 0, st>>>(tmp, nb, d.gcell_start, ncells);
+    k_scan_add<<<(unsigned)nb, 1024, 0, st>>>(d.gcell_start, ncells, tmp);
+    k_group_fill<<<gc, 256, 0, st>>>(d, ncells, G);
+    *nl += 5;
     return (int)cudaGetLastError();
 }
 

@@ -209,7 +209,198 @@ __global__ void __launch_bounds__(128, 1) k_build(Dev d, LJ lj)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Lists shared by groups of G atoms of one cell.  A group's row holds every
+// atom j outside the group whose FP32 r^2 to some member lies below the upper
+// edge of the band around rs^2, which contains every pair of the exact FP64
+// criterion (the FP32 r^2 is within far less than the band's 2.5e-4 rs^2 of
+// the FP64 one), so each member's exact row is a subset of the group's row
+// plus the other members.  The G lanes of a group take the candidates of a
+// stencil cell G at a time, each against all members (the members' positions
+// in registers), and append the accepted ones in candidate order with a
+// ballot over the group's lanes (rank = set bits below the lane).  Rows are
+// padded with sentinel entries to a multiple of 16.
+// ---------------------------------------------------------------------------
+template <int G, bool BATCHED>
+__global__ void __launch_bounds__(128) k_build_group(Dev d, LJ lj)
+{
+    if (stopped(d.status)) return;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gi = t / G;
+    const int l = (int)(t % G);
+    const int lane = threadIdx.x & 31;
+    const int gbase = lane & ~(G - 1);
+    const unsigned gmask = ((1u << G) - 1u) << gbase;
+    const int32_t ng = d.gcell_start[d.ncells];
+    if (gi >= ng) return;                                   // whole groups leave together
+    if (!MD_CHECK(d, gi < d.ngmax)) return;
+    const uint32_t gw = (uint32_t)d.grp[gi];
+    const int32_t a0 = (int32_t)(gw & kJMask);
+    const int m = (int)(gw >> kJBits) + 1;
+    if (!MD_CHECK(d, a0 + m <= d.n)) return;
+    const Rep &R = d.reps[BATCHED ? d.rep_of[a0] : 0];
+    float px[G], py[G], pz[G];
+    uint32_t pack = 0;
+#pragma unroll
+    for (int k = 0; k < G; k++) {
+        // absent members sit far away (and away from the sentinel slot)
+        const float4 q = k < m ? d.p32[a0 + k] : make_float4(-1.0e4f, -1.0e4f, -1.0e4f, 0.f);
+        px[k] = q.x; py[k] = q.y; pz[k] = q.z;
+        if (k == 0) pack = __float_as_uint(q.w);
+    }
+    const int ci[3] = {(int)(pack & 1023u), (int)((pack >> 10) & 1023u), (int)((pack >> 20) & 1023u)};
+    const int64_t ngmax = d.ngmax;
+    const int32_t cap = d.gcap;
+    const float4 *p32 = d.p32;
+    const float hi = lj.rs2f_hi;
+    int32_t *rows = d.gnb;
+    int32_t cnt = 0;
+
+    for (int ox = -1; ox <= 1; ox++) {
+        int ux = ci[0] + ox;
+        if (ux < 0) ux += R.nc[0]; else if (ux >= R.nc[0]) ux -= R.nc[0];
+        const float offx = (float)ox * -R.nsf[0];
+        for (int oy = -1; oy <= 1; oy++) {
+            int uy = ci[1] + oy;
+            if (uy < 0) uy += R.nc[1]; else if (uy >= R.nc[1]) uy -= R.nc[1];
+            const float offy = (float)oy * -R.nsf[1];
+            const int32_t col = (int32_t)cell_id(R, ux, uy, 0);
+            for (int oz = -1; oz <= 1; oz++) {
+                int uz = ci[2] + oz;
+                if (uz < 0) uz += R.nc[2]; else if (uz >= R.nc[2]) uz -= R.nc[2];
+                const float offz = (float)oz * -R.nsf[2];
+                const int32_t cid = cell_id_z(col, uz);
+                if (!MD_CHECK(d, cid >= 0 && cid < d.ncells)) continue;
+                const int32_t j0 = d.cell_start[cid], j1 = d.cell_start[cid + 1];
+                if (!MD_CHECK(d, j0 >= 0 && j0 <= j1 && j1 <= d.n)) continue;
+                const uint32_t tag = offset_code(ox, oy, oz) << kJBits;
+                // the same trip count on the group's lanes (one cell)
+#pragma unroll 2
+                for (int32_t jb = j0; jb < j1; jb += G) {
+                    const int32_t j = jb + l;
+                    const bool valid = j < j1;
+                    const float4 pj = __ldg(p32 + (valid ? j : d.n));
+                    const float qx = pj.x + offx, qy = pj.y + offy, qz = pj.z + offz;
+                    float r2 = 3.0e38f;
+#pragma unroll
+                    for (int k = 0; k < G; k++) {
+                        const float dx = px[k] - qx, dy = py[k] - qy, dz = pz[k] - qz;
+                        r2 = fminf(r2, fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+                    }
+                    const bool acc = valid && r2 < hi && (uint32_t)(j - a0) >= (uint32_t)m;
+                    const unsigned bal = (__ballot_sync(gmask, acc) >> gbase) & ((1u << G) - 1u);
+                    if (acc) {
+                        const int32_t k = cnt + __popc(bal & ((1u << l) - 1u));
+                        if (k < cap) rows[((int64_t)(k >> 4) * ngmax + gi) * 16 + (k & 15)] = (int32_t)((uint32_t)j | tag);
+                    }
+                    cnt += __popc(bal);
+                }
+            }
+        }
+    }
+    // pad the last 16-entry block with entries for the sentinel slot n
+    const int32_t pad = (int32_t)((uint32_t)d.n | (kZeroOffset << kJBits));
+    const int32_t end = min((cnt + 15) & ~15, cap);
+    for (int32_t k = cnt + l; k < end; k += G) rows[((int64_t)(k >> 4) * ngmax + gi) * 16 + (k & 15)] = pad;
+    if (l == 0) {
+        d.gnb_count[gi] = cnt;
+        atomicMax(&d.status->max_count, cnt);
+        if (cnt > cap) {
+            atomicOr(&d.status->flags, FLAG_NL_OVERFLOW);
+            d.status->overflow_at = d.status->rebuild_count;
+            d.status->overflow_step = d.status->dev_step;
+        }
+    }
+}
+
+// Exact rows of a group list: member k of group g keeps every candidate of
+// the group's row and every other member whose exact FP64 r^2 (the build's
+// criterion: image shift from the entry's cell offset and the member's cell,
+// each operation rounded, strict compare) lies below rs^2.  counts and rows
+// in caller order (rows: replica-local ids, at most cap per row; counts are
+// complete).
+template <int G, bool BATCHED>
+__global__ void __launch_bounds__(128) k_decode_group(Dev d, LJ lj, int32_t *counts,
+                                                      int32_t *rows, int32_t cap)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gi = t / G;
+    const int k = (int)(t % G);
+    if (gi >= d.gcell_start[d.ncells] || !MD_CHECK(d, gi < d.ngmax)) return;
+    const uint32_t gw = (uint32_t)d.grp[gi];
+    const int32_t a0 = (int32_t)(gw & kJMask);
+    const int m = (int)(gw >> kJBits) + 1;
+    if (k >= m) return;
+    const int32_t i = a0 + k;
+    if (!MD_CHECK(d, i < d.n)) return;
+    const Rep &R = d.reps[BATCHED ? d.rep_of[i] : 0];
+    const dvec4 xi = d.x[i];
+    const uint32_t pack = __float_as_uint(d.p32[i].w);
+    const int ci[3] = {(int)(pack & 1023u), (int)((pack >> 10) & 1023u), (int)((pack >> 20) & 1023u)};
+    const int64_t o = d.id[i];
+    int32_t cnt = 0;
+    auto test = [&](int32_t j, uint32_t code) {
+        if (!MD_CHECK(d, j >= 0 && j < d.n)) return;
+        int kk[3];
+        for (int q = 0; q < 3; q++) {
+            const int u = ci[q] + (int)((code >> (2 * q)) & 3u) - 1;
+            kk[q] = u < 0 ? -1 : (u >= R.nc[q] ? 1 : 0);
+        }
+        const dvec4 xj = d.x[j];
+        const double tx = image_diff(xi.x, xj.x, kk[0], R.L[0]);
+        const double ty = image_diff(xi.y, xj.y, kk[1], R.L[1]);
+        const double tz = image_diff(xi.z, xj.z, kk[2], R.L[2]);
+        const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(tx, tx), __dmul_rn(ty, ty)), __dmul_rn(tz, tz));
+        if (!(r2 < lj.rs2)) return;
+        if (cnt < cap) rows[o * cap + cnt] = (int32_t)(d.id[j] - R.atom_off);
+        cnt++;
+    };
+    for (int q = 0; q < m; q++)
+        if (q != k) test(a0 + q, kZeroOffset);
+    const int32_t gc = MD_CHECK(d, d.gnb_count[gi] <= d.gcap) ? d.gnb_count[gi] : 0;
+    for (int32_t e = 0; e < gc; e++) {
+        const uint32_t en = (uint32_t)d.gnb[((int64_t)(e >> 4) * d.ngmax + gi) * 16 + (e & 15)];
+        test((int32_t)(en & kJMask), en >> kJBits);
+    }
+    counts[o] = cnt;
+}
+
 }  // namespace
+
+int launch_decode_group(const Dev &d, const LJ &lj, int G, int32_t *counts, int32_t *rows,
+                        int32_t cap, cudaStream_t st, int *nl)
+{
+    if (d.n <= 0) return 0;
+    if ((G != 2 && G != 4) || !d.gnb || !d.grp) return -1;
+    const bool b = d.nrep > 1;
+    const unsigned g = (unsigned)((d.ngmax * G + 127) / 128);
+    if (G == 4) {
+        if (b) k_decode_group<4, true><<<g, 128, 0, st>>>(d, lj, counts, rows, cap);
+        else k_decode_group<4, false><<<g, 128, 0, st>>>(d, lj, counts, rows, cap);
+    } else {
+        if (b) k_decode_group<2, true><<<g, 128, 0, st>>>(d, lj, counts, rows, cap);
+        else k_decode_group<2, false><<<g, 128, 0, st>>>(d, lj, counts, rows, cap);
+    }
+    *nl += 1;
+    return (int)cudaGetLastError();
+}
+
+int launch_build_group(const Dev &d, const LJ &lj, int G, cudaStream_t st, int *nl)
+{
+    if (d.n <= 0) return 0;
+    if ((G != 2 && G != 4) || !d.gnb || !d.grp) return -1;
+    const bool b = d.nrep > 1;
+    const unsigned g = (unsigned)((d.ngmax * G + 127) / 128);
+    if (G == 4) {
+        if (b) k_build_group<4, true><<<g, 128, 0, st>>>(d, lj);
+        else k_build_group<4, false><<<g, 128, 0, st>>>(d, lj);
+    } else {
+        if (b) k_build_group<2, true><<<g, 128, 0, st>>>(d, lj);
+        else k_build_group<2, false><<<g, 128, 0, st>>>(d, lj);
+    }
+    *nl += 1;
+    return (int)cudaGetLastError();
+}
 
 // A warp-per-cell build (lanes = the cell's atoms, broadcast candidate loads)
 // executed ~40 % fewer instructions but measured slower on GB300 (1241 vs

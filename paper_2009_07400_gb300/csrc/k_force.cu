@@ -230,6 +230,169 @@ __device__ __forceinline__ void mixed_full_tile(const Dev &d, const LJ &lj, int6
                           __float_as_uint(pi.w), true);
 }
 
+// ---------------------------------------------------------------------------
+// Mixed precision, list shared by a group of G atoms of one cell.  The G
+// lanes of a group split the group's row (lane l takes the int4 chunks l,
+// l + 4, ... of each 16-entry block); each lane gathers its entries'
+// positions once and evaluates each of them against all G members, whose
+// positions it holds in registers, so a gathered position serves G pairs
+// and nothing is exchanged between lanes inside the loop.  The entry's cell
+// offset (shared by the members: one cell) is applied to the neighbour,
+//     d_k = p_k - (p_j + o s),
+// from a 64-entry table of o s per replica.  Each lane keeps a Kahan sum per
+// member over its chunks (four pairs per chunk and member in a plain
+// partial); the G lanes' sums are combined by a fixed butterfly (every lane
+// ends with the same totals), and lane k runs the epilogue of member k.
+// Pairs inside the group: lane l takes member l against the others.
+// ---------------------------------------------------------------------------
+template <int G, bool BATCHED, int EPI, bool ENERGY>
+__global__ void __launch_bounds__(256) k_force_mixed_group(Dev d, LJ lj)
+{
+    if (stopped(d.status)) return;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gi = t / G;
+    const int l = (int)(t % G);
+    const int lane = threadIdx.x & 31;
+    const unsigned gmask = ((1u << G) - 1u) << (lane & ~(G - 1));
+    if (gi >= d.gcell_start[d.ncells]) return;             // whole groups leave together
+    if (!MD_CHECK(d, gi < d.ngmax)) return;
+    const uint32_t gw = (uint32_t)d.grp[gi];
+    const int64_t a0 = gw & kJMask;
+    const int m = (int)(gw >> kJBits) + 1;
+    if (!MD_CHECK(d, a0 + m <= d.n)) return;
+    const int32_t rep = BATCHED ? d.rep_of[a0] : 0;
+    const Rep &R = d.reps[rep];
+    const float4 *offt = d.offtab + 64 * rep;
+    const float4 *p32 = d.p32;
+    float qx[G], qy[G], qz[G];
+    uint32_t pack = 0;
+#pragma unroll
+    for (int k = 0; k < G; k++) {
+        // absent members sit far away (and away from the sentinel slot)
+        const float4 q = k < m ? p32[a0 + k] : make_float4(-1.0e4f, -1.0e4f, -1.0e4f, 0.f);
+        qx[k] = q.x; qy[k] = q.y; qz[k] = q.z;
+        if (k == 0) pack = __float_as_uint(q.w);
+    }
+    float sx[G], sy[G], sz[G], cx[G], cy[G], cz[G], pe[G], w[G], cpe[G], cw[G];
+#pragma unroll
+    for (int k = 0; k < G; k++) {
+        sx[k] = sy[k] = sz[k] = cx[k] = cy[k] = cz[k] = 0.f;
+        pe[k] = w[k] = cpe[k] = cw[k] = 0.f;
+    }
+    // one pair: member position (x, y, z) against the neighbour image
+    // (jx, jy, jz); adds f d to (fx, fy, fz) and, with ENERGY, V and f r^2
+    auto pair = [&](float x, float y, float z, float jx, float jy, float jz, bool live, float &fx,
+                    float &fy, float &fz, float &pv, float &pw) {
+        const float dx = x - jx, dy = y - jy, dz = z - jz;
+        const float rsq = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        const float sr2 = rcp_approx(rsq);
+        const float tt = sr2 * sr2 * sr2 * lj.sigma6f;
+        float f = sr2 * tt * fmaf(lj.c48ef, tt, -lj.c24ef);
+        const bool in = live & (rsq < lj.rc2f);
+        f = in ? f : 0.f;
+        fx = fmaf(f, dx, fx);
+        fy = fmaf(f, dy, fy);
+        fz = fmaf(f, dz, fz);
+        if (ENERGY) {
+            pv += in ? lj.c4ef * tt * (tt - 1.f) : 0.f;
+            pw = fmaf(f, rsq, pw);
+        }
+    };
+    auto add_partials = [&](const float (&px)[G], const float (&py)[G], const float (&pz)[G],
+                            const float (&pv)[G], const float (&pw)[G]) {
+#pragma unroll
+        for (int k = 0; k < G; k++) {
+            kahan_add(sx[k], cx[k], px[k]);
+            kahan_add(sy[k], cy[k], py[k]);
+            kahan_add(sz[k], cz[k], pz[k]);
+            if (ENERGY) {
+                kahan_add(pe[k], cpe[k], pv[k]);
+                kahan_add(w[k], cw[k], pw[k]);
+            }
+        }
+    };
+    {   // pairs inside the group: member l against the other members
+        float px[G], py[G], pz[G], pv[G], pw[G];
+#pragma unroll
+        for (int k = 0; k < G; k++) px[k] = py[k] = pz[k] = pv[k] = pw[k] = 0.f;
+        float jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+        for (int k = 0; k < G; k++)
+            if (k == l) { jx = qx[k]; jy = qy[k]; jz = qz[k]; }
+        const bool lm = l < m;
+#pragma unroll
+        for (int k = 0; k < G; k++) {
+            // k == l would be the self pair (d = 0): moved out of range
+            const float ox = k == l ? 1.0e4f : 0.f;
+            pair(qx[k] + ox, qy[k], qz[k], jx, jy, jz, lm, px[k], py[k], pz[k], pv[k], pw[k]);
+        }
+        add_partials(px, py, pz, pv, pw);
+    }
+    const int cnt = MD_CHECK(d, d.gnb_count[gi] <= d.gcap) ? d.gnb_count[gi] : 0;
+    const int nblk = (cnt + 15) >> 4;
+    const int4 *nb4 = reinterpret_cast<const int4 *>(d.gnb) + gi * 4 + l;
+    const int64_t bstride = d.ngmax * 4;                   // int4s between 16-entry blocks
+    int4 nxt = nblk > 0 ? ld_stream(nb4) : make_int4(0, 0, 0, 0);
+    for (int b = 0; b < nblk; b++) {
+        const int4 e4 = nxt;
+        if (b + 1 < nblk) nxt = ld_stream(nb4 + (int64_t)(b + 1) * bstride);
+        const uint32_t es[4] = {(uint32_t)e4.x, (uint32_t)e4.y, (uint32_t)e4.z, (uint32_t)e4.w};
+        float4 pj[4], of[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const uint32_t j = es[u] & kJMask;
+            if (!MD_CHECK(d, j <= (uint32_t)d.n)) { pj[u] = make_float4(1.0e4f, 1.0e4f, 1.0e4f, 0.f); of[u] = make_float4(0.f, 0.f, 0.f, 0.f); continue; }
+            pj[u] = __ldg(p32 + j);
+            of[u] = __ldg(offt + (es[u] >> kJBits));
+        }
+        float px[G], py[G], pz[G], pv[G], pw[G];
+#pragma unroll
+        for (int k = 0; k < G; k++) px[k] = py[k] = pz[k] = pv[k] = pw[k] = 0.f;
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const float jx = pj[u].x + of[u].x, jy = pj[u].y + of[u].y, jz = pj[u].z + of[u].z;
+#pragma unroll
+            for (int k = 0; k < G; k++)
+                pair(qx[k], qy[k], qz[k], jx, jy, jz, true, px[k], py[k], pz[k], pv[k], pw[k]);
+        }
+        add_partials(px, py, pz, pv, pw);
+    }
+    // combine the lanes' sums (fixed butterfly: every lane gets the same bits)
+    float fx[G], fy[G], fz[G], ev[G], ew[G];
+#pragma unroll
+    for (int k = 0; k < G; k++) {
+        fx[k] = sx[k] - cx[k];
+        fy[k] = sy[k] - cy[k];
+        fz[k] = sz[k] - cz[k];
+        ev[k] = pe[k] - cpe[k];
+        ew[k] = w[k] - cw[k];
+    }
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) {
+#pragma unroll
+        for (int k = 0; k < G; k++) {
+            fx[k] += __shfl_xor_sync(gmask, fx[k], o);
+            fy[k] += __shfl_xor_sync(gmask, fy[k], o);
+            fz[k] += __shfl_xor_sync(gmask, fz[k], o);
+            if (ENERGY) {
+                ev[k] += __shfl_xor_sync(gmask, ev[k], o);
+                ew[k] += __shfl_xor_sync(gmask, ew[k], o);
+            }
+        }
+    }
+    if (l >= m) return;
+    float gx = 0.f, gy = 0.f, gz = 0.f, gv = 0.f, gww = 0.f;
+#pragma unroll
+    for (int k = 0; k < G; k++)
+        if (k == l) { gx = fx[k]; gy = fy[k]; gz = fz[k]; gv = ev[k]; gww = ew[k]; }
+    const int64_t i = a0 + l;
+    if (ENERGY) {
+        d.pe_atom[i] = 0.5f * gv;
+        d.w_atom[i] = 0.5f * gww;
+    }
+    epilogue<EPI, ENERGY>(d, lj, R, i, (double)gx, (double)gy, (double)gz, pack, true);
+}
+
 // o + 1 -> o, a 3-entry table per block for the half-list kernel.
 __device__ __forceinline__ void fill_offsets(float (&ot)[3])
 {
@@ -475,7 +638,36 @@ int launch_full(const Dev &d, const LJ &lj, bool mixed, int epi, bool energy, cu
     return 0;
 }
 
+template <int G, bool B>
+void launch_group_g(const Dev &d, const LJ &lj, int epi, bool energy, cudaStream_t st)
+{
+    const unsigned g = (unsigned)((d.ngmax * G + 255) / 256);
+#define MD_GRP(EP, EN) k_force_mixed_group<G, B, EP, EN><<<g, 256, 0, st>>>(d, lj)
+    if (epi == EPI_F) { if (energy) MD_GRP(EPI_F, true); else MD_GRP(EPI_F, false); }
+    else if (epi == EPI_FK) { if (energy) MD_GRP(EPI_FK, true); else MD_GRP(EPI_FK, false); }
+    else { if (energy) MD_GRP(EPI_FKKD, true); else MD_GRP(EPI_FKKD, false); }
+#undef MD_GRP
+}
+
 }  // namespace
+
+// Mixed path over a list shared by groups of G = 2 or 4 atoms; epilogues as
+// the full-list kernels.
+int launch_force_group(const Dev &d, const LJ &lj, int G, int epi, bool energy, bool batched,
+                       cudaStream_t st, int *nl)
+{
+    if (d.n <= 0) return 0;
+    if ((G != 2 && G != 4) || !d.gnb || !d.grp || !d.offtab) return -1;
+    if (G == 4) {
+        if (batched) launch_group_g<4, true>(d, lj, epi, energy, st);
+        else launch_group_g<4, false>(d, lj, epi, energy, st);
+    } else {
+        if (batched) launch_group_g<2, true>(d, lj, epi, energy, st);
+        else launch_group_g<2, false>(d, lj, epi, energy, st);
+    }
+    *nl += 1;
+    return (int)cudaGetLastError();
+}
 
 // Half lists only support EPI_F (the caller zeroes the force array first and
 // integrates in a separate kernel).

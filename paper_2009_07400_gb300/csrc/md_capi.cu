@@ -87,6 +87,15 @@ struct md_ctx {
     int64_t scan_len = 0;
     int32_t *nb = nullptr, *nb_count = nullptr;
     int32_t cap = 0;
+    // list shared by groups of gsz atoms (list types 2 and 4): group table,
+    // per-cell group counts and their prefix sums, rows, row lengths; sized
+    // for gsz when allocated (ngmax = ceil(n / gsz) + cell ids)
+    int32_t *grp = nullptr, *gcnt = nullptr, *gcell_start = nullptr, *gnb = nullptr,
+            *gnb_count = nullptr;
+    int64_t ngmax = 0;
+    int32_t gcap = 0, gsz = 0;
+    double expect_row = 0;          // expected full-list row at the densest replica
+    float4 *offtab_d = nullptr;     // per replica: o s for the 64 cell-offset codes
     float *pe_atom = nullptr, *w_atom = nullptr;
     double *pe64 = nullptr, *w64 = nullptr, *ke64 = nullptr;
     DevStatus *status = nullptr;
@@ -167,6 +176,14 @@ Dev view(const md_ctx *c)
     d.ke_atom64 = c->ke64;
     d.status = c->status;
     d.ctr = c->ctr_d;
+    d.grp = c->grp;
+    d.gcnt = c->gcnt;
+    d.gcell_start = c->gcell_start;
+    d.gnb = c->gnb;
+    d.gnb_count = c->gnb_count;
+    d.ngmax = c->ngmax;
+    d.gcap = c->gcap;
+    d.offtab = c->offtab_d;
     if (c->lj.pot == 1 && c->p.precision == MD_MIXED) {   // contact model, mixed path
         d.v32 = c->v32[c->pb];
         d.v32_nxt = c->v32[1 - c->pb];
@@ -215,7 +232,8 @@ void free_all(md_ctx *c)
                     c->chunk_first_d, c->partials_d, c->eout_d, c->elog_d, c->io_d, c->ctr_d,
                     c->p32_ref, c->v32[0], c->v32[1], c->adj.ck_x, c->adj.ck_v, c->adj.blk_x,
                     c->adj.xbar, c->adj.wbar, c->adj.blk_p, c->adj.ck_p, c->adj.wbar32,
-                    c->adj.ck_id, c->adj.ge, c->adj.gs, c->adj.g2};
+                    c->adj.ck_id, c->adj.ge, c->adj.gs, c->adj.g2, c->grp, c->gcnt,
+                    c->gcell_start, c->gnb, c->gnb_count, c->offtab_d};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->own_stream && c->st) cudaStreamDestroy(c->st);
@@ -223,7 +241,12 @@ void free_all(md_ctx *c)
 }
 
 bool is_mixed(const md_ctx *c) { return c->p.precision == MD_MIXED; }
-bool is_half(const md_ctx *c) { return c->p.half_list != 0; }
+bool is_half(const md_ctx *c) { return c->p.list_type == MD_LIST_HALF; }
+// group size of a list shared by groups of atoms (list types 2 and 4), else 0
+int list_g(const md_ctx *c)
+{
+    return (c->p.list_type == MD_LIST_GROUP2 || c->p.list_type == MD_LIST_GROUP4) ? c->p.list_type : 0;
+}
 bool is_sd(const md_ctx *c) { return c->lj.pot == 1; }
 bool batched(const md_ctx *c) { return c->nrep > 1; }
 // the contact model's mixed path keeps FP32 velocity copies (v32)
@@ -240,6 +263,49 @@ int alloc_list(md_ctx *c, int32_t cap)
     for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
     c->graphs.clear();
     return rc;
+}
+
+// Group-list storage for groups of g atoms with `cap` entries per group row
+// (rounded up to a multiple of 16); the group table arrays are (re)sized
+// when g changes.
+int alloc_group(md_ctx *c, int g, int32_t cap)
+{
+    int rc = MD_OK;
+    if (c->gsz != g) {
+        int32_t **arrs[] = {&c->grp, &c->gcnt, &c->gcell_start, &c->gnb, &c->gnb_count};
+        for (int32_t **a : arrs) {
+            if (*a) cudaFree(*a);
+            *a = nullptr;
+        }
+        c->gsz = 0;
+        c->ngmax = (c->n + g - 1) / g + c->nids;
+        if ((rc = dalloc(c, &c->grp, (size_t)c->ngmax)) || (rc = dalloc(c, &c->gnb_count, (size_t)c->ngmax)) ||
+            (rc = dalloc(c, &c->gcnt, (size_t)c->nids)) || (rc = dalloc(c, &c->gcell_start, (size_t)c->nids + 1)))
+            return rc;
+        c->gsz = g;
+    }
+    if (c->gnb) cudaFree(c->gnb);
+    c->gnb = nullptr;
+    c->gcap = (int32_t)((std::max<int64_t>(cap, 16) + 15) / 16 * 16);
+    rc = dalloc(c, &c->gnb, (size_t)c->ngmax * (size_t)c->gcap);
+    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+    c->graphs.clear();
+    return rc;
+}
+
+// Initial group-row capacity: the union of G rows of ~rho (4/3) pi rs^3
+// entries measured 1.34x (G = 2) and 1.78x (G = 4) one row on LJ liquids;
+// with margin.
+int32_t group_cap0(const md_ctx *c, int g)
+{
+    return (int32_t)(c->expect_row * (g == 4 ? 2.4 : 1.8)) + 32;
+}
+
+// Capacity of the list type in use, and growing it after an overflow.
+int32_t active_cap(const md_ctx *c) { return list_g(c) ? c->gcap : c->cap; }
+int realloc_active(md_ctx *c, int32_t cap)
+{
+    return list_g(c) ? alloc_group(c, list_g(c), cap) : alloc_list(c, cap);
 }
 
 // ---------------------------------------------------------------------------
@@ -265,11 +331,22 @@ int enq_bin(md_ctx *c, int *nl)
     return MD_OK;
 }
 
+// The list build of the context's list type on stream st (group lists: the
+// group table of the current binning first).
+int launch_list_build(md_ctx *c, const Dev &d, cudaStream_t st, int *nl)
+{
+    if (list_g(c)) {
+        if (launch_group_table(d, list_g(c), c->nids, c->scan_tmp, c->scan_len, st, nl) != 0) return -1;
+        return launch_build_group(d, c->lj, list_g(c), st, nl);
+    }
+    return launch_build(d, c->lj, is_half(c), c->nids, st, nl);
+}
+
 int enq_build(md_ctx *c, int *nl)
 {
     CK(cudaMemsetAsync(&c->status->max_count, 0, sizeof(int32_t), c->st));
     Dev d = view(c);
-    if (launch_build(d, c->lj, is_half(c), c->nids, c->st, nl) != 0)
+    if (launch_list_build(c, d, c->st, nl) != 0)
         return fail(c, MD_ERR_CUDA, "list build launch failed");
     c->list_valid = true;
     c->builds_enqueued++;
@@ -329,9 +406,10 @@ int enq_force(md_ctx *c, int epi, bool energy, int *nl, cudaEvent_t *ev = nullpt
         }
     } else {
         if (ev) CK(cudaEventRecord(ev[0], c->st));
-        if (launch_force(d, c->lj, c->p.precision, false, c->tpa, epi, energy, batched(c), c->st,
-                         nl))
-            return fail(c, MD_ERR_CUDA, "force launch failed");
+        const int rc = list_g(c) ? launch_force_group(d, c->lj, list_g(c), epi, energy, batched(c), c->st, nl)
+                                 : launch_force(d, c->lj, c->p.precision, false, c->tpa, epi, energy,
+                                                batched(c), c->st, nl);
+        if (rc) return fail(c, MD_ERR_CUDA, "force launch failed");
         if (ev) CK(cudaEventRecord(ev[1], c->st));
         if (epi == EPI_FKKD) {
             c->pb = 1 - c->pb;
@@ -373,8 +451,7 @@ int enq_cond_rebuild(md_ctx *c, int *nl)
     CK(cudaStreamBeginCaptureToGraph(c->side, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     int bl = 0, rc = MD_OK;
     if (launch_bin(d, c->nids, c->scan_tmp, c->scan_len, c->side, &bl) != 0 ||
-        launch_copy_back(d, c->side, &bl) != 0 ||
-        launch_build(d, c->lj, is_half(c), c->nids, c->side, &bl) != 0)
+        launch_copy_back(d, c->side, &bl) != 0 || launch_list_build(c, d, c->side, &bl) != 0)
         rc = fail(c, MD_ERR_CUDA, "rebuild body launch failed");
     cudaGraph_t out = nullptr;
     cudaError_t e = cudaStreamEndCapture(c->side, &out);
@@ -504,9 +581,9 @@ int check_flags(md_ctx *c, const DevStatus &s)
 
 int grow_list(md_ctx *c, int32_t seen_max)
 {
-    int64_t want = std::max<int64_t>((int64_t)(seen_max * 1.2) + 8, (int64_t)c->cap * 3 / 2);
+    int64_t want = std::max<int64_t>((int64_t)(seen_max * 1.2) + 8, (int64_t)active_cap(c) * 3 / 2);
     if (want > (int64_t)1 << 16) return fail(c, MD_ERR_NL_OVERFLOW, "neighbour list capacity limit reached");
-    int rc = alloc_list(c, (int32_t)want);
+    int rc = realloc_active(c, (int32_t)want);
     if (rc) return fail(c, MD_ERR_NL_OVERFLOW, "cannot grow the neighbour list: " + c->err);
     return MD_OK;
 }
@@ -654,12 +731,16 @@ std::mutex &tune_mutex()
 }
 
 // Switches lanes-per-atom / list type; a list-type change rebuilds the list.
-int apply_tuning(md_ctx *c, int tpa, int half)
+int apply_tuning(md_ctx *c, int tpa, int lt)
 {
-    const bool relist = (half != c->p.half_list);
+    const bool relist = (lt != c->p.list_type);
     c->tpa = tpa;
     c->p.threads_per_atom = tpa;
-    c->p.half_list = half;
+    c->p.list_type = lt;
+    if ((lt == MD_LIST_GROUP2 || lt == MD_LIST_GROUP4) && (c->gsz != lt || !c->gnb)) {
+        const int rc = alloc_group(c, lt, group_cap0(c, lt));
+        if (rc) return rc;
+    }
     for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
     c->graphs.clear();
     if (relist) {
@@ -1029,6 +1110,27 @@ int md_get_neighbors(md_ctx *c, int32_t *counts, int32_t *rows, int32_t cap)
     if (!c || !counts || !rows || cap <= 0) return fail(c, MD_ERR_INVAL, "bad argument");
     int rc = ensure_list(c);
     if (rc) return rc;
+    if (list_g(c)) {
+        // exact rows filtered from the group rows on the device (FP64
+        // criterion), then copied out with their lengths
+        int32_t *buf = nullptr;
+        if ((rc = dalloc(c, &buf, (size_t)c->n * ((size_t)cap + 1)))) return rc;
+        int nl = 0;
+        if (launch_decode_group(view(c), c->lj, list_g(c), buf, buf + c->n, cap, c->st, &nl)) {
+            cudaFree(buf);
+            return fail(c, MD_ERR_CUDA, "decode failed");
+        }
+        c->launches += nl;
+        cudaError_t e = cudaMemcpyAsync(counts, buf, sizeof(int32_t) * c->n, cudaMemcpyDeviceToHost, c->st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(rows, buf + c->n, sizeof(int32_t) * c->n * cap, cudaMemcpyDeviceToHost, c->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+        cudaFree(buf);
+        if (e != cudaSuccess) return fail(c, MD_ERR_CUDA, cudaGetErrorString(e));
+        for (int64_t a = 0; a < c->n; a++)
+            if (counts[a] > cap) return fail(c, MD_ERR_INVAL, "a row is longer than cap");
+        return MD_OK;
+    }
     std::vector<int32_t> cnt((size_t)c->n), ids((size_t)c->n);
     CK(cudaMemcpyAsync(cnt.data(), c->nb_count, sizeof(int32_t) * c->n, cudaMemcpyDeviceToHost, c->st));
     CK(cudaMemcpyAsync(ids.data(), c->id[c->vp], sizeof(int32_t) * c->n, cudaMemcpyDeviceToHost, c->st));
@@ -1058,9 +1160,9 @@ int md_get_info(md_ctx *c, md_info *info)
     info->n = c->n;
     info->nrep = c->nrep;
     info->precision = c->p.precision;
-    info->half_list = c->p.half_list;
+    info->list_type = c->p.list_type;
     info->threads_per_atom = c->tpa;
-    info->list_capacity = c->cap;
+    info->list_capacity = active_cap(c);
     info->max_neighbors = c->last_max;
     info->ncells = c->ncells;
     info->step = c->step;
@@ -1080,7 +1182,7 @@ int md_set_capacity(md_ctx *c, int32_t cap)
 {
     if (!c || cap < 4) return fail(c, MD_ERR_INVAL, "bad argument");
     CK(cudaStreamSynchronize(c->st));
-    int rc = alloc_list(c, cap);
+    int rc = realloc_active(c, cap);
     if (rc) return rc;
     c->list_valid = false;
     c->forces_valid = false;
@@ -1160,11 +1262,22 @@ int md_profile(md_ctx *c, int64_t nsteps, md_phase_times *out)
     if (rc) return rc;
     c->step = s0 + nsteps;
     out->steps = nsteps;
-    std::vector<int32_t> cnt((size_t)c->n);
-    CK(cudaMemcpy(cnt.data(), c->nb_count, sizeof(int32_t) * c->n, cudaMemcpyDeviceToHost));
+    // list entries per atom: row lengths (of the groups, for group lists)
+    // summed over the rows and divided by the atom count
+    int64_t nrows = c->n;
+    const int32_t *lens = c->nb_count;
+    if (list_g(c)) {
+        int32_t ng = 0;
+        CK(cudaMemcpy(&ng, c->gcell_start + c->nids, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        nrows = ng;
+        lens = c->gnb_count;
+    }
+    std::vector<int32_t> cnt((size_t)nrows);
+    CK(cudaMemcpy(cnt.data(), lens, sizeof(int32_t) * nrows, cudaMemcpyDeviceToHost));
     double sum = 0;
     for (int32_t q : cnt) sum += q;
     out->mean_neighbors = sum / (double)c->n;
+    out->rows = nrows;
     return MD_OK;
 }
 
@@ -1198,7 +1311,8 @@ int md_set_spring_dashpot(md_ctx *c, double k_spring, double gamma)
         CK(cudaMemsetAsync(c->v32[b], 0, sizeof(float4) * ((size_t)c->n + 1), c->st));
     }
     c->v32_fresh = false;
-    if (is_half(c) && (rc = apply_tuning(c, 1, 0))) return rc;   // contacts use full lists
+    // contacts use full per-atom lists
+    if (c->p.list_type != MD_LIST_FULL && (rc = apply_tuning(c, 1, MD_LIST_FULL))) return rc;
     c->lj.pot = 1;
     c->lj.sd_k = k_spring;
     c->lj.sd_g = gamma;
@@ -1227,9 +1341,10 @@ static int adjoint_impl(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt,
     // precision of the reverse sweep's pair terms (the forward run always
     // uses the context's precision)
     const bool mixed = c->adj_prec < 0 ? is_mixed(c) : c->adj_prec == MD_MIXED;
-    const int half0 = c->p.half_list, tpa0 = c->tpa;
+    const int lt0 = c->p.list_type, tpa0 = c->tpa;
     int rc = MD_OK;
-    if (half0 && (rc = apply_tuning(c, 1, 0))) return rc;   // the adjoint walks full lists
+    // the adjoint walks full per-atom lists
+    if (lt0 != MD_LIST_FULL && (rc = apply_tuning(c, tpa0, MD_LIST_FULL))) return rc;
 
     // workspace: reused between calls, grown when a call needs more
     auto &W = c->adj;
@@ -1391,7 +1506,7 @@ static int adjoint_impl(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt,
     }
     c->launches += nl;
     c->forces_valid = false;
-    if (!rc && half0) rc = apply_tuning(c, tpa0, half0);
+    if (!rc && lt0 != MD_LIST_FULL) rc = apply_tuning(c, tpa0, lt0);
     return rc;
 }
 
@@ -1465,13 +1580,16 @@ int md_autotune(md_ctx *c, int32_t steps, md_params *chosen)
         return r;
     };
     save();
-    const int cands[5][2] = {{1, 0}, {2, 0}, {4, 0}, {8, 0}, {1, 1}};
+    // (lanes per atom, list type); lists shared by groups are mixed-path only
+    const int cands[7][2] = {{1, MD_LIST_FULL},   {2, MD_LIST_FULL}, {4, MD_LIST_FULL},
+                             {8, MD_LIST_FULL},   {1, MD_LIST_HALF}, {1, MD_LIST_GROUP4},
+                             {1, MD_LIST_GROUP2}};
     float best = 1e30f;
     int best_k = 0;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    const int ncand = (int)(sizeof(cands) / sizeof(cands[0]));
+    const int ncand = is_mixed(c) ? 7 : 5;
     for (int k = 0; k < ncand && !rc; k++) {
         if ((rc = apply_tuning(c, cands[k][0], cands[k][1]))) break;
         if ((rc = md_run(c, steps, 0, nullptr))) break;  // warm-up (graph capture)
@@ -1524,10 +1642,13 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
     const md_params &q = *p;
     if (!(q.epsilon > 0) || !(q.sigma > 0) || !(q.mass > 0) || !(q.cutoff > 0) || !(q.skin >= 0) ||
         !(q.dt > 0) || q.rebuild_every < 0 || (q.precision != MD_FP64 && q.precision != MD_MIXED) ||
-        (q.half_list != 0 && q.half_list != 1) ||
+        (q.list_type != MD_LIST_FULL && q.list_type != MD_LIST_HALF &&
+         q.list_type != MD_LIST_GROUP2 && q.list_type != MD_LIST_GROUP4) ||
         !(q.threads_per_atom == 0 || q.threads_per_atom == 1 || q.threads_per_atom == 2 ||
           q.threads_per_atom == 4 || q.threads_per_atom == 8))
         return fail(c, MD_ERR_INVAL, "invalid md_params");
+    if ((q.list_type == MD_LIST_GROUP2 || q.list_type == MD_LIST_GROUP4) && q.precision != MD_MIXED)
+        return fail(c, MD_ERR_INVAL, "lists shared by groups of atoms need the mixed path");
     c->p = q;
     c->nrep = nrep;
     c->disp = q.rebuild_every == 0;
@@ -1667,6 +1788,20 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
             for (int32_t k = 0; k < R.nc[dd]; k++) ctr.push_back(((double)k + 0.5) * R.s[dd]);
     }
     if ((rc = dalloc(c, &c->ctr_d, ctr.size()))) return rc;
+    // per replica: o s for each 6-bit cell-offset code of a list entry (codes
+    // with a field of 3 do not occur and map to 0)
+    std::vector<float4> offt(64 * (size_t)nrep);
+    for (int32_t r = 0; r < nrep; r++)
+        for (uint32_t code = 0; code < 64; code++) {
+            float o[3];
+            for (int dd = 0; dd < 3; dd++) {
+                const uint32_t f = (code >> (2 * dd)) & 3u;
+                o[dd] = f == 3u ? 0.0f : (float)((int)f - 1) * -c->reps_h[r].nsf[dd];
+            }
+            offt[64 * (size_t)r + code] = make_float4(o[0], o[1], o[2], 0.0f);
+        }
+    if ((rc = dalloc(c, &c->offtab_d, offt.size()))) return rc;
+    CK(cudaMemcpyAsync(c->offtab_d, offt.data(), sizeof(float4) * offt.size(), cudaMemcpyHostToDevice, c->st));
     CK(cudaMemcpyAsync(c->ctr_d, ctr.data(), sizeof(double) * ctr.size(), cudaMemcpyHostToDevice, c->st));
     std::vector<int32_t> rep_of(N);
     for (int32_t r = 0; r < nrep; r++)
@@ -1683,10 +1818,14 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
 
     // Initial capacity: expected full-list count at the densest replica with
     // margin, never more than the replica's size allows.
-    const double expect = maxrho * 4.0 / 3.0 * M_PI * rs * rs * rs * (q.half_list ? 0.5 : 1.0);
+    c->expect_row = maxrho * 4.0 / 3.0 * M_PI * rs * rs * rs;
+    const double expect = c->expect_row * (q.list_type == MD_LIST_HALF ? 0.5 : 1.0);
     int64_t cap0 = (int64_t)(1.3 * expect) + 16;
     cap0 = std::min<int64_t>(cap0, maxn + 3);
     if ((rc = alloc_list(c, (int32_t)std::max<int64_t>(cap0, 4)))) return rc;
+    if (list_g(c) &&
+        (rc = alloc_group(c, list_g(c), (int32_t)std::min<int64_t>(group_cap0(c, list_g(c)), maxn + 16))))
+        return rc;
     return set_state(c, pos, vel, on_device);
 }
 

@@ -174,6 +174,17 @@ struct Dev {
                               // nc_x, then nc_y, then nc_z values
     float4 *v32, *v32_nxt;    // contact model, mixed path: FP32 velocity copies
                               // (n + 1 each, slot n zero; flip with p32), else null
+    // Lists shared by groups of G atoms of one cell (list types 2 and 4):
+    // group table, per-cell group counts and their prefix sums (the number of
+    // groups at gcell_start[ncells]), rows and row lengths.  Entry k of group
+    // g is at int index ((k / 16) * ngmax + g) * 16 + k % 16: lane l of the
+    // group's G lanes reads the int4 chunks l, l + 4, ... of each 16-entry
+    // block.  Null when no group list was set up.
+    int32_t *grp, *gcnt, *gcell_start, *gnb, *gnb_count;
+    int64_t ngmax;            // group slots allocated: ceil(n / G) + cells
+    int32_t gcap;             // entries per group row (multiple of 16)
+    const float4 *offtab;     // per replica 64 codes: (ox s_x, oy s_y, oz s_z) of a
+                              // list entry's 6-bit cell-offset code
 };
 
 #ifdef __CUDACC__
@@ -335,6 +346,17 @@ int launch_rebuild_check(const Dev &d, cudaGraphConditionalHandle h, cudaStream_
                          int *nlaunch);
 
 int64_t scan_tmp_elems(int64_t ncells_total);
+
+// Lists shared by groups of G atoms (k_bin.cu, k_build.cu, k_force.cu, k_misc.cu)
+int launch_group_table(const Dev &d, int G, int64_t ncells, int32_t *tmp, int64_t tmp_len,
+                       cudaStream_t st, int *nlaunch);
+int launch_build_group(const Dev &d, const LJ &lj, int G, cudaStream_t st, int *nlaunch);
+int launch_force_group(const Dev &d, const LJ &lj, int G, int epi, bool energy, bool batched,
+                       cudaStream_t st, int *nlaunch);
+// exact per-atom rows (FP64 criterion) from a group list: counts (n, caller
+// order) and rows (n x cap, caller order, replica-local ids)
+int launch_decode_group(const Dev &d, const LJ &lj, int G, int32_t *counts_dev, int32_t *rows_dev,
+                        int32_t cap, cudaStream_t st, int *nlaunch);
 
 // Adjoint (k_adjoint.cu)
 // mixed: FP32 pair terms reading wbar32 (an FP32 copy of wbar kept by the

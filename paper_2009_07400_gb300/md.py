@@ -22,6 +22,7 @@ ERRORS = {
     -8: "MD_ERR_BADPOS", -9: "MD_ERR_STATE",
 }
 MD_FP64, MD_MIXED = 0, 1
+MD_LIST_FULL, MD_LIST_HALF, MD_LIST_GROUP2, MD_LIST_GROUP4 = 0, 1, 2, 4
 (MD_ERR_INVAL, MD_ERR_BOX_TOO_SMALL, MD_ERR_NOMEM, MD_ERR_CUDA, MD_ERR_NL_OVERFLOW,
  MD_ERR_TIMEOUT, MD_ERR_NONFINITE, MD_ERR_BADPOS, MD_ERR_STATE) = range(-1, -10, -1)
 
@@ -53,14 +54,15 @@ class md_params(ctypes.Structure):
                 ("mass", ctypes.c_double), ("cutoff", ctypes.c_double),
                 ("skin", ctypes.c_double), ("dt", ctypes.c_double),
                 ("rebuild_every", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("half_list", ctypes.c_int32), ("threads_per_atom", ctypes.c_int32)]
+                ("list_type", ctypes.c_int32), ("threads_per_atom", ctypes.c_int32)]
 
 
 class md_phase_times(ctypes.Structure):
     _fields_ = [("force_ms", ctypes.c_double), ("neigh_ms", ctypes.c_double),
                 ("other_ms", ctypes.c_double), ("force_launches", ctypes.c_int64),
                 ("neigh_launches", ctypes.c_int64), ("other_launches", ctypes.c_int64),
-                ("steps", ctypes.c_int64), ("mean_neighbors", ctypes.c_double)]
+                ("steps", ctypes.c_int64), ("mean_neighbors", ctypes.c_double),
+                ("rows", ctypes.c_int64)]
 
 
 class md_thermo_rec(ctypes.Structure):
@@ -71,7 +73,7 @@ class md_thermo_rec(ctypes.Structure):
 
 class md_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nrep", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("half_list", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("list_type", ctypes.c_int32),
                 ("threads_per_atom", ctypes.c_int32), ("list_capacity", ctypes.c_int32),
                 ("max_neighbors", ctypes.c_int32), ("ncells", ctypes.c_int64),
                 ("step", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
@@ -174,9 +176,12 @@ def _f64(a, n):
 
 
 def make_params(epsilon=1.0, sigma=1.0, mass=1.0, cutoff=2.5, skin=0.3, dt=0.005,
-                rebuild_every=20, precision=MD_FP64, half_list=False, threads_per_atom=0):
+                rebuild_every=20, precision=MD_FP64, half_list=False, threads_per_atom=0,
+                list_type=None):
+    """md_params; list_type (MD_LIST_*) wins over the older half_list flag."""
+    lt = int(list_type) if list_type is not None else (MD_LIST_HALF if half_list else MD_LIST_FULL)
     return md_params(epsilon, sigma, mass, cutoff, skin, dt, int(rebuild_every), int(precision),
-                     int(bool(half_list)), int(threads_per_atom))
+                     lt, int(threads_per_atom))
 
 
 class MDContext:
@@ -370,9 +375,16 @@ class MDContext:
                                            atoms.ctypes.data_as(_I32)))
         return start, atoms
 
+    def _row_cap(self):
+        """A row capacity that holds every exact row of the current list (a
+        member of a group list can have up to its group row plus the other
+        members)."""
+        inf = self.info()
+        return max(4, inf.list_capacity, inf.max_neighbors) + 8
+
     def neighbors(self):
         """Per-atom rows (caller order, replica-local ids) of the current list."""
-        cap = max(4, self.info().list_capacity)
+        cap = self._row_cap()
         counts = np.zeros(self.n, np.int32)
         rows = np.zeros(self.n * cap, np.int32)
         self._check(self._lib.md_get_neighbors(self._h, counts.ctypes.data_as(_I32),
@@ -381,7 +393,7 @@ class MDContext:
 
     def neighbors_raw(self):
         """(counts[n], rows[n, cap]) of the current list, caller order."""
-        cap = max(4, self.info().list_capacity)
+        cap = self._row_cap()
         counts = np.zeros(self.n, np.int32)
         rows = np.zeros((self.n, cap), np.int32)
         self._check(self._lib.md_get_neighbors(self._h, counts.ctypes.data_as(_I32),

@@ -20,18 +20,22 @@ import bench  # noqa: E402
 def test_algorithmic_bytes_per_atom():
     # full list, fused step: 4 k + 4 (row length) + 16 + 16 (p32 in/out)
     # + 2 x 24 (x in/out) + 2 x 24 (v in/out)
-    assert bench.algorithmic_bytes_per_atom(75.0, False) == 4 * 75 + 4 + 32 + 96
+    assert bench.algorithmic_bytes_per_atom(75.0, 0) == 4 * 75 + 4 + 32 + 96
     # half list, force only: entries, row length, p32 in, force out
-    assert bench.algorithmic_bytes_per_atom(37.5, True) == 4 * 37.5 + 4 + 32
+    assert bench.algorithmic_bytes_per_atom(37.5, 1) == 4 * 37.5 + 4 + 32
+    # group list of 4, fused step: entries per atom, row length and group
+    # table entry per group (0.26 groups per atom)
+    assert bench.algorithmic_bytes_per_atom(35.0, 4, 0.26) == 4 * 35 + 8 * 0.26 + 32 + 96
 
 
 def test_parse_tuned():
     assert bench.parse_tuned(None) is None
     assert bench.parse_tuned("") is None
     mixed, fp64 = bench.parse_tuned("1,0,2,1")
-    assert mixed == {"threads_per_atom": 1, "half_list": False}
-    assert fp64 == {"threads_per_atom": 2, "half_list": True}
-    for bad in ("3,0,1,0", "1,0,1", "1,0,16,0"):
+    assert mixed == {"threads_per_atom": 1, "list_type": 0}
+    assert fp64 == {"threads_per_atom": 2, "list_type": 1}
+    assert bench.parse_tuned("1,4,2,0")[0] == {"threads_per_atom": 1, "list_type": 4}
+    for bad in ("3,0,1,0", "1,0,1", "1,0,16,0", "1,3,1,0", "1,0,1,4"):
         with pytest.raises(SystemExit):
             bench.parse_tuned(bad)
 
@@ -39,14 +43,18 @@ def test_parse_tuned():
 def test_ncu_traffic_follows_the_kernel_source():
     """The committed DRAM traffic is reported only while its recorded hash
     matches the force kernel's source; a changed kernel reports null."""
-    text = open(bench.PROFILE_MD).read()
-    recorded = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text).group(1)
     current = hashlib.sha256(open(bench.FORCE_SRC, "rb").read()).hexdigest()
-    t = bench.ncu_traffic()
-    if recorded == current:
-        assert t is not None and 4e8 < t < 5e8     # ~432 B per atom at 1M atoms
-    else:
-        assert t is None
+    for lt, path in bench.PROFILE_MD.items():
+        t = bench.ncu_traffic(lt)
+        if not os.path.exists(path):
+            assert t is None
+            continue
+        text = open(path).read()
+        recorded = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text).group(1)
+        if recorded == current:
+            assert t is not None and 1e8 < t < 6e8     # 250-450 B per atom at 1M atoms
+        else:
+            assert t is None
 
 
 def test_reference_arm_line():

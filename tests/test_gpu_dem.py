@@ -47,7 +47,7 @@ def test_forces_and_energy(md, orc, half):
     pe_r, w_r = orc.energy_sd_list(xw, v, L, rows, **ok)
     for precision, tol in ((md.MD_FP64, 1e-12), (md.MD_MIXED, 1e-5)):
         with sd_ctx(md, x, v, L, 500.0, 3.0, precision=precision, half_list=half) as ctx:
-            assert ctx.info().half_list == 0        # contacts use full lists
+            assert ctx.info().list_type == 0        # contacts use full lists
             F = ctx.forces()
             assert rel_rms(F, Fr) < tol
             pe, ke, w = (q[0] for q in ctx.energy())

@@ -275,34 +275,53 @@ def _pairs_inside(x, L, rc):
 
 def test_mixed_nve_vs_oracle(md, orc):
     """Mixed path, 1000 steps of the 131,072-atom FCC workload against the FP64
-    oracle's run from the same state (both rebuilding every 20 steps).
+    oracle's run from the same state (both rebuilding every 20 steps):
+    |E_tot(mixed) - E_tot(oracle)| / N with the unshifted potential of Eq. 2.
 
-    The potential of Eq. 2 is cut at rc without a shift, so the total energy
-    of either run jumps by V(rc) = -0.0163 whenever a pair crosses rc.  The
-    two runs agree to ~1e-6 per atom for ~500 steps and then decorrelate
-    (chaos); from there the difference of their unshifted totals is
-    V(rc) times the difference of their pair counts inside rc, which
-    fluctuates by ~1e3 pairs (~1e-4 per atom) between decorrelated runs.  The
-    criterion is therefore applied to the total energy of the shifted
-    potential V(r) - V(rc), which has the same forces:
-    E_s = PE + KE - V(rc) * (pairs inside rc).  (E_s itself is not conserved
-    exactly on either side: with the fixed 20-step rebuild schedule some
-    pairs come inside rc before their row holds them, and the oracle's own
-    E_s moves by about -2e-4 per atom over these steps.)  The unshifted
-    difference is bounded by the crossing noise (1e-3 per atom)."""
+    The two runs are chaotic: the mixed path's FP32 pair arithmetic (force
+    error ~1e-6 relative) acts like a perturbation of the positions of order
+    1e-7 sigma, which grows about e^3.5 per time unit, so the trajectories
+    decorrelate after ~500 of the 1000 steps.  After that the unshifted totals
+    differ by V(rc) times the difference of the pair counts inside rc, a
+    random quantity of the chaos (hundreds to ~1,300 pairs here, i.e. up to
+    ~2e-4 per atom), not of the arithmetic.  So:
+
+      * before decorrelation (steps 100-500) the literal criterion is checked
+        with a 10x tighter bound: |dE| / N <= 1e-5;
+      * at step 1000, |dE| / N must stay within 1e-4 or within three times
+        the largest value of a control: FP64 runs from the same state
+        perturbed by uniform +-1e-7 sigma (three seeds), i.e. exact
+        arithmetic started from a state as far from the oracle's as the
+        mixed path's rounding puts it.  (A perturbation of 1e-12 sigma does
+        not decorrelate within 1000 steps: positions 3e-5 apart at the end,
+        |dE| / N 9e-8.  That is why the control uses the FP32 scale);
+      * the shifted total E_s = PE + KE - V(rc) * (pairs inside rc) (same
+        forces, no crossing jumps) must agree within 1e-4 per atom at 1000
+        steps."""
     s = inputs.workload("fcc32_131072")
     L = s.box
+    n = s.n
     v_rc = 4.0 * (RC ** -12 - RC ** -6)
-    x_ref, v_ref, _ = orc.vv_run(s.pos, s.vel, L, 1000)
-    e_ref = orc.energy(x_ref, L)[0] + orc.kinetic(v_ref)
-    es_ref = e_ref - v_rc * _pairs_inside(x_ref, L[0], RC)
+    x_ref, v_ref, _, E_ref = orc.vv_run(s.pos, s.vel, L, 1000, energies=True)
+    e_ref = E_ref[99::100, 0] + E_ref[99::100, 1]
     with ctx_of(md, s, precision=md.MD_MIXED) as ctx:
         E = ctx.run(1000, energy_every=100)
         x_gpu = ctx.positions()
-    e_gpu = E[-1, 0, 0] + E[-1, 0, 1]
-    es_gpu = e_gpu - v_rc * _pairs_inside(x_gpu, L[0], RC)
-    assert abs(es_gpu - es_ref) / s.n <= 1e-4
-    assert abs(e_gpu - e_ref) / s.n <= 1e-3
+    de_mixed = (E[:, 0, 0] + E[:, 0, 1] - e_ref) / n
+    controls = []
+    for seed in (1, 2, 3):
+        dp = np.random.default_rng(seed).uniform(-1e-7, 1e-7, s.pos.shape)
+        with md.MDContext(s.pos + dp, s.vel, L, precision=md.MD_FP64) as ctx:
+            Ec = ctx.run(1000, energy_every=100)
+        controls.append((Ec[:, 0, 0] + Ec[:, 0, 1] - e_ref) / n)
+    spread = np.max(np.abs(np.array(controls)), axis=0)
+    print("mixed |dE|/N every 100 steps:", np.array2string(np.abs(de_mixed), precision=2))
+    print("control max (FP64, 1e-7 sigma):", np.array2string(spread, precision=2))
+    assert np.all(np.abs(de_mixed[:5]) <= 1e-5)
+    assert abs(de_mixed[-1]) <= max(1e-4, 3.0 * spread[-1])
+    es_ref = e_ref[-1] - v_rc * _pairs_inside(x_ref, L[0], RC)
+    es_gpu = E[-1, 0, 0] + E[-1, 0, 1] - v_rc * _pairs_inside(x_gpu, L[0], RC)
+    assert abs(es_gpu - es_ref) / n <= 1e-4
 
 
 def test_overflow_recovery(md, orc):
@@ -393,7 +412,7 @@ def test_autotune_keeps_state(md, orc):
         with ctx_of(md, s, precision=precision) as ctx:
             x0, v0 = ctx.positions(), ctx.velocities()
             chosen = ctx.autotune(steps=20)
-            assert chosen.threads_per_atom in (1, 2, 4, 8) and chosen.half_list in (0, 1)
+            assert chosen.threads_per_atom in (1, 2, 4, 8) and chosen.list_type in (0, 1, 2, 4)
             assert ctx.info().step == 0
             assert np.array_equal(ctx.positions(), x0)
             assert np.array_equal(ctx.velocities(), v0)
