@@ -756,11 +756,12 @@ def run_adjoint(args):
     print(json.dumps(line), flush=True)
 
 
-def run_ncu_case(which):
+def run_ncu_case(which, pin=None):
     """Create the workload's context and run 2 cycles: 1 first drift, then
-    per cycle 19 fused steps, a rebuild (6 binning kernels + build) and the
+    per cycle 19 fused steps, a rebuild (binning kernels + build) and the
     20th fused step.  `dem`: the contact model on the 1M-sphere packing
-    (mixed path, force and integration kernels per step)."""
+    (mixed path, force and integration kernels per step).  pin: the --tuned
+    lanes per atom and list type of the mixed (or FP64) context."""
     import torch
 
     from paper_2009_07400_gb300 import build, md
@@ -775,7 +776,8 @@ def run_ncu_case(which):
         return
     s = inputs.workload(WORKLOAD)
     prec = md.MD_MIXED if which == "mixed" else md.MD_FP64
-    with md.MDContext(s.pos, s.vel, s.box, precision=prec) as ctx:
+    kw = (pin[0] if which == "mixed" else pin[1]) if pin else {}
+    with md.MDContext(s.pos, s.vel, s.box, precision=prec, **kw) as ctx:
         ctx.run(2 * STEPS_PER_CYCLE)
     torch.cuda.synchronize()
 
@@ -802,7 +804,7 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     if args.ncu_case:
-        run_ncu_case(args.ncu_case)
+        run_ncu_case(args.ncu_case, parse_tuned(args.tuned))
     elif args.workload == "adjoint":
         if args.impl == "native":
             run_adjoint(args)

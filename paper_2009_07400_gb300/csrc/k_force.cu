@@ -329,13 +329,17 @@ __global__ void __launch_bounds__(256) k_force_mixed_group(Dev d, LJ lj)
         add_partials(px, py, pz, pv, pw);
     }
     const int cnt = MD_CHECK(d, d.gnb_count[gi] <= d.gcap) ? d.gnb_count[gi] : 0;
-    const int nblk = (cnt + 15) >> 4;
+    // the lane's int4 chunks: l, l + G, ... of every 16-entry block (4 chunks
+    // per block: one per lane for G = 4, two for G = 2)
+    constexpr int kPer = 4 / G;
+    const int nq = ((cnt + 15) >> 4) * kPer;
     const int4 *nb4 = reinterpret_cast<const int4 *>(d.gnb) + gi * 4 + l;
     const int64_t bstride = d.ngmax * 4;                   // int4s between 16-entry blocks
-    int4 nxt = nblk > 0 ? ld_stream(nb4) : make_int4(0, 0, 0, 0);
-    for (int b = 0; b < nblk; b++) {
+    auto chunk_at = [&](int q) { return nb4 + (int64_t)(q / kPer) * bstride + (q % kPer) * G; };
+    int4 nxt = nq > 0 ? ld_stream(chunk_at(0)) : make_int4(0, 0, 0, 0);
+    for (int q = 0; q < nq; q++) {
         const int4 e4 = nxt;
-        if (b + 1 < nblk) nxt = ld_stream(nb4 + (int64_t)(b + 1) * bstride);
+        if (q + 1 < nq) nxt = ld_stream(chunk_at(q + 1));
         const uint32_t es[4] = {(uint32_t)e4.x, (uint32_t)e4.y, (uint32_t)e4.z, (uint32_t)e4.w};
         float4 pj[4], of[4];
 #pragma unroll

@@ -402,6 +402,24 @@ def test_full_size(md, orc, precision):
             assert rms_rel(F, Fr) <= 1e-5
 
 
+def test_paper_gpu_shape_80(md, orc):
+    """The paper's single-GPU workload shape (Sec. 6: FCC 80^3 unit cells,
+    2,048,000 atoms, FP64, full lists, one thread per atom), after one
+    graph-replayed rebuild cycle: every row bit-exact against the oracle's
+    cell list, FP64 forces on sampled atoms within 1e-10, and the mixed path
+    on the same state within 1e-5 RMS."""
+    s = inputs.workload("fcc80_2048000")
+    with ctx_of(md, s, precision=md.MD_FP64, threads_per_atom=1) as ctx:
+        ctx.run(20)
+        x, v = ctx.positions(), ctx.velocities()
+        assert_lists_equal(orc, ctx, x, s.box, False)
+        ids = np.random.default_rng(1).choice(s.n, 4096, replace=False)
+        Fr = orc.forces_sample(x, s.box, ids)
+        assert fp64_force_ok(ctx.forces()[ids], Fr) <= 1e-10
+    with md.MDContext(x, v, s.box, precision=md.MD_MIXED) as ctx:
+        assert rms_rel(ctx.forces()[ids], Fr) <= 1e-5
+
+
 def test_autotune_keeps_state(md, orc):
     """The tuner times every candidate on the context's own state and puts
     the state back; the chosen variant still matches the oracle."""
