@@ -211,34 +211,65 @@ __global__ void __launch_bounds__(128, 1) k_build(Dev d, LJ lj)
 
 // ---------------------------------------------------------------------------
 // Lists shared by groups of G atoms of one cell.  A group's row holds every
-// atom j outside the group whose FP32 r^2 to some member lies below the upper
-// edge of the band around rs^2, which contains every pair of the exact FP64
-// criterion (the FP32 r^2 is within far less than the band's 2.5e-4 rs^2 of
-// the FP64 one), so each member's exact row is a subset of the group's row
-// plus the other members.  The G lanes of a group take the candidates of a
-// stencil cell G at a time, each against all members (the members' positions
-// in registers), and append the accepted ones in candidate order with a
-// ballot over the group's lanes (rank = set bits below the lane).  Rows are
-// padded with sentinel entries to a multiple of 16.
+// atom j outside the group that lies in the exact row of some member (the
+// FP64 criterion above: FP32 classification, FP64 inside the band), with a
+// byte of member bits per entry (bit k: j is in member k's row), so the force
+// kernel applies exactly each member's Verlet row.  The pairs of members are
+// decided the same way into a per-group mask.  Lanes: the G lanes of a group
+// take the candidates of a stencil cell G * U at a time, each candidate
+// against all members (their positions in registers), and append accepted
+// ones in candidate order with a ballot (rank = accepted lanes of the group
+// below the lane).  Every loop runs the warp's largest trip count (groups of
+// a warp can sit in different cells) so lanes stay converged and every
+// ballot has the whole warp.  Rows are padded with sentinel entries (mask 0)
+// to a multiple of 16.
 // ---------------------------------------------------------------------------
+
+// FP64 decision of the band members `band` (bits) of candidate j with image
+// flags k[3]: returns the bits of the members whose exact r^2 < rs^2.
+template <int G>
+__device__ __forceinline__ uint32_t exact_bits(const Dev &d, const LJ &lj, const Rep &R,
+                                               int32_t a0, int32_t j, uint32_t band, int kx,
+                                               int ky, int kz)
+{
+    uint32_t in = 0;
+    const dvec4 xj = d.x[j];
+#pragma unroll
+    for (int k = 0; k < G; k++) {
+        if (!((band >> k) & 1u)) continue;
+        const dvec4 xi = d.x[a0 + k];
+        const double tx = image_diff(xi.x, xj.x, kx, R.L[0]);
+        const double ty = image_diff(xi.y, xj.y, ky, R.L[1]);
+        const double tz = image_diff(xi.z, xj.z, kz, R.L[2]);
+        const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(tx, tx), __dmul_rn(ty, ty)), __dmul_rn(tz, tz));
+        if (r2 < lj.rs2) in |= 1u << k;
+    }
+    return in;
+}
+
 template <int G, bool BATCHED>
-__global__ void __launch_bounds__(128) k_build_group(Dev d, LJ lj)
+__global__ void __launch_bounds__(128, 4) k_build_group(Dev d, LJ lj)
 {
     if (stopped(d.status)) return;
+    constexpr int U = 2;                                    // candidates per lane per round
+    constexpr unsigned gbits = (1u << G) - 1u;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t gi = t / G;
     const int l = (int)(t % G);
     const int lane = threadIdx.x & 31;
     const int gbase = lane & ~(G - 1);
-    const unsigned gmask = ((1u << G) - 1u) << gbase;
     const int32_t ng = d.gcell_start[d.ncells];
-    if (gi >= ng) return;                                   // whole groups leave together
-    if (!MD_CHECK(d, gi < d.ngmax)) return;
-    const uint32_t gw = (uint32_t)d.grp[gi];
-    const int32_t a0 = (int32_t)(gw & kJMask);
-    const int m = (int)(gw >> kJBits) + 1;
-    if (!MD_CHECK(d, a0 + m <= d.n)) return;
-    const Rep &R = d.reps[BATCHED ? d.rep_of[a0] : 0];
+    // groups past the last one run the loops with empty ranges (no early
+    // return: trip counts and ballots stay uniform over the warp)
+    int32_t a0 = 0;
+    int m = 0;
+    if (gi < ng && MD_CHECK(d, gi < d.ngmax)) {
+        const uint32_t gw = (uint32_t)d.grp[gi];
+        a0 = (int32_t)(gw & kJMask);
+        m = (int)(gw >> kJBits) + 1;
+        if (!MD_CHECK(d, a0 + m <= d.n)) m = 0;
+    }
+    const Rep &R = d.reps[BATCHED && m > 0 ? d.rep_of[a0] : 0];
     float px[G], py[G], pz[G];
     uint32_t pack = 0;
 #pragma unroll
@@ -246,63 +277,107 @@ __global__ void __launch_bounds__(128) k_build_group(Dev d, LJ lj)
         // absent members sit far away (and away from the sentinel slot)
         const float4 q = k < m ? d.p32[a0 + k] : make_float4(-1.0e4f, -1.0e4f, -1.0e4f, 0.f);
         px[k] = q.x; py[k] = q.y; pz[k] = q.z;
-        if (k == 0) pack = __float_as_uint(q.w);
+        if (k == 0 && m > 0) pack = __float_as_uint(q.w);
     }
     const int ci[3] = {(int)(pack & 1023u), (int)((pack >> 10) & 1023u), (int)((pack >> 20) & 1023u)};
     const int64_t ngmax = d.ngmax;
     const int32_t cap = d.gcap;
     const float4 *p32 = d.p32;
-    const float hi = lj.rs2f_hi;
+    const float lo = lj.rs2f_lo, hi = lj.rs2f_hi;
     int32_t *rows = d.gnb;
+    uint8_t *masks = d.gmask;
     int32_t cnt = 0;
 
     for (int ox = -1; ox <= 1; ox++) {
-        int ux = ci[0] + ox;
-        if (ux < 0) ux += R.nc[0]; else if (ux >= R.nc[0]) ux -= R.nc[0];
+        int ux = ci[0] + ox, kx = 0;
+        if (ux < 0) { ux += R.nc[0]; kx = -1; } else if (ux >= R.nc[0]) { ux -= R.nc[0]; kx = 1; }
         const float offx = (float)ox * -R.nsf[0];
         for (int oy = -1; oy <= 1; oy++) {
-            int uy = ci[1] + oy;
-            if (uy < 0) uy += R.nc[1]; else if (uy >= R.nc[1]) uy -= R.nc[1];
+            int uy = ci[1] + oy, ky = 0;
+            if (uy < 0) { uy += R.nc[1]; ky = -1; } else if (uy >= R.nc[1]) { uy -= R.nc[1]; ky = 1; }
             const float offy = (float)oy * -R.nsf[1];
             const int32_t col = (int32_t)cell_id(R, ux, uy, 0);
             for (int oz = -1; oz <= 1; oz++) {
-                int uz = ci[2] + oz;
-                if (uz < 0) uz += R.nc[2]; else if (uz >= R.nc[2]) uz -= R.nc[2];
+                int uz = ci[2] + oz, kz = 0;
+                if (uz < 0) { uz += R.nc[2]; kz = -1; } else if (uz >= R.nc[2]) { uz -= R.nc[2]; kz = 1; }
                 const float offz = (float)oz * -R.nsf[2];
                 const int32_t cid = cell_id_z(col, uz);
-                if (!MD_CHECK(d, cid >= 0 && cid < d.ncells)) continue;
-                const int32_t j0 = d.cell_start[cid], j1 = d.cell_start[cid + 1];
-                if (!MD_CHECK(d, j0 >= 0 && j0 <= j1 && j1 <= d.n)) continue;
+                int32_t j0 = 0, j1 = 0;
+                if (m > 0 && MD_CHECK(d, cid >= 0 && cid < d.ncells)) {
+                    j0 = d.cell_start[cid];
+                    j1 = d.cell_start[cid + 1];
+                    if (!MD_CHECK(d, j0 >= 0 && j0 <= j1 && j1 <= d.n)) j1 = j0;
+                }
                 const uint32_t tag = offset_code(ox, oy, oz) << kJBits;
-                // the same trip count on the group's lanes (one cell)
-#pragma unroll 2
-                for (int32_t jb = j0; jb < j1; jb += G) {
-                    const int32_t j = jb + l;
-                    const bool valid = j < j1;
-                    const float4 pj = __ldg(p32 + (valid ? j : d.n));
-                    const float qx = pj.x + offx, qy = pj.y + offy, qz = pj.z + offz;
-                    float r2 = 3.0e38f;
+                const int nr = (j1 - j0 + G * U - 1) / (G * U);
+                const int rmax = __reduce_max_sync(0xffffffffu, nr);
+                for (int r = 0; r < rmax; r++) {
+                    uint32_t mk[U];
+                    int32_t jj[U];
 #pragma unroll
-                    for (int k = 0; k < G; k++) {
-                        const float dx = px[k] - qx, dy = py[k] - qy, dz = pz[k] - qz;
-                        r2 = fminf(r2, fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+                    for (int u = 0; u < U; u++) {
+                        const int32_t j = j0 + (r * U + u) * G + l;
+                        const bool valid = j < j1 && (uint32_t)(j - a0) >= (uint32_t)m;
+                        const float4 pj = __ldg(p32 + (j < j1 ? j : d.n));
+                        const float qx = pj.x + offx, qy = pj.y + offy, qz = pj.z + offz;
+                        uint32_t in = 0, band = 0;
+#pragma unroll
+                        for (int k = 0; k < G; k++) {
+                            const float dx = px[k] - qx, dy = py[k] - qy, dz = pz[k] - qz;
+                            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                            in |= (uint32_t)(r2 < lo) << k;
+                            band |= (uint32_t)((r2 >= lo) & (r2 < hi)) << k;
+                        }
+                        if (!valid) in = band = 0;
+                        if (band) in |= exact_bits<G>(d, lj, R, a0, j, band, kx, ky, kz);
+                        mk[u] = in;
+                        jj[u] = j;
                     }
-                    const bool acc = valid && r2 < hi && (uint32_t)(j - a0) >= (uint32_t)m;
-                    const unsigned bal = (__ballot_sync(gmask, acc) >> gbase) & ((1u << G) - 1u);
-                    if (acc) {
-                        const int32_t k = cnt + __popc(bal & ((1u << l) - 1u));
-                        if (k < cap) rows[((int64_t)(k >> 4) * ngmax + gi) * 16 + (k & 15)] = (int32_t)((uint32_t)j | tag);
+#pragma unroll
+                    for (int u = 0; u < U; u++) {
+                        const bool acc = mk[u] != 0u;
+                        const unsigned bal = (__ballot_sync(0xffffffffu, acc) >> gbase) & gbits;
+                        if (acc) {
+                            const int32_t k = cnt + __popc(bal & ((1u << l) - 1u));
+                            if (k < cap) {
+                                const int64_t at = ((int64_t)(k >> 4) * ngmax + gi) * 16 + (k & 15);
+                                rows[at] = (int32_t)((uint32_t)jj[u] | tag);
+                                masks[at] = (uint8_t)mk[u];
+                            }
+                        }
+                        cnt += __popc(bal);
                     }
-                    cnt += __popc(bal);
                 }
             }
         }
     }
+    if (m == 0) return;
     // pad the last 16-entry block with entries for the sentinel slot n
     const int32_t pad = (int32_t)((uint32_t)d.n | (kZeroOffset << kJBits));
     const int32_t end = min((cnt + 15) & ~15, cap);
-    for (int32_t k = cnt + l; k < end; k += G) rows[((int64_t)(k >> 4) * ngmax + gi) * 16 + (k & 15)] = pad;
+    for (int32_t k = cnt + l; k < end; k += G) {
+        const int64_t at = ((int64_t)(k >> 4) * ngmax + gi) * 16 + (k & 15);
+        rows[at] = pad;
+        masks[at] = 0;
+    }
     if (l == 0) {
+        // member pairs inside the list radius (same cell: the direct image)
+        uint32_t pairs = 0;
+        for (int a = 0; a < m; a++)
+            for (int b = a + 1; b < m; b++) {
+                const float dx = px[a] - px[b], dy = py[a] - py[b], dz = pz[a] - pz[b];
+                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                bool in = r2 < lo;
+                if (!in && r2 < hi) {
+                    const dvec4 xa = d.x[a0 + a], xb = d.x[a0 + b];
+                    const double tx = image_diff(xa.x, xb.x, 0, R.L[0]);
+                    const double ty = image_diff(xa.y, xb.y, 0, R.L[1]);
+                    const double tz = image_diff(xa.z, xb.z, 0, R.L[2]);
+                    in = __dadd_rn(__dadd_rn(__dmul_rn(tx, tx), __dmul_rn(ty, ty)), __dmul_rn(tz, tz)) < lj.rs2;
+                }
+                if (in) pairs |= (1u << (a * G + b)) | (1u << (b * G + a));
+            }
+        d.gpair[gi] = (uint16_t)pairs;
         d.gnb_count[gi] = cnt;
         atomicMax(&d.status->max_count, cnt);
         if (cnt > cap) {
@@ -313,16 +388,15 @@ __global__ void __launch_bounds__(128) k_build_group(Dev d, LJ lj)
     }
 }
 
-// Exact rows of a group list: member k of group g keeps every candidate of
-// the group's row and every other member whose exact FP64 r^2 (the build's
-// criterion: image shift from the entry's cell offset and the member's cell,
-// each operation rounded, strict compare) lies below rs^2.  counts and rows
-// in caller order (rows: replica-local ids, at most cap per row; counts are
-// complete).
+// Per-atom rows of a group list: member k of group g holds the entries of
+// the group's row with bit k set and the members paired with it; counts and
+// rows in caller order (rows: replica-local ids, at most cap per row; counts
+// are complete).
 template <int G, bool BATCHED>
 __global__ void __launch_bounds__(128) k_decode_group(Dev d, LJ lj, int32_t *counts,
                                                       int32_t *rows, int32_t cap)
 {
+    (void)lj;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t gi = t / G;
     const int k = (int)(t % G);
@@ -334,33 +408,20 @@ __global__ void __launch_bounds__(128) k_decode_group(Dev d, LJ lj, int32_t *cou
     const int32_t i = a0 + k;
     if (!MD_CHECK(d, i < d.n)) return;
     const Rep &R = d.reps[BATCHED ? d.rep_of[i] : 0];
-    const dvec4 xi = d.x[i];
-    const uint32_t pack = __float_as_uint(d.p32[i].w);
-    const int ci[3] = {(int)(pack & 1023u), (int)((pack >> 10) & 1023u), (int)((pack >> 20) & 1023u)};
     const int64_t o = d.id[i];
     int32_t cnt = 0;
-    auto test = [&](int32_t j, uint32_t code) {
+    auto put = [&](int32_t j) {
         if (!MD_CHECK(d, j >= 0 && j < d.n)) return;
-        int kk[3];
-        for (int q = 0; q < 3; q++) {
-            const int u = ci[q] + (int)((code >> (2 * q)) & 3u) - 1;
-            kk[q] = u < 0 ? -1 : (u >= R.nc[q] ? 1 : 0);
-        }
-        const dvec4 xj = d.x[j];
-        const double tx = image_diff(xi.x, xj.x, kk[0], R.L[0]);
-        const double ty = image_diff(xi.y, xj.y, kk[1], R.L[1]);
-        const double tz = image_diff(xi.z, xj.z, kk[2], R.L[2]);
-        const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(tx, tx), __dmul_rn(ty, ty)), __dmul_rn(tz, tz));
-        if (!(r2 < lj.rs2)) return;
         if (cnt < cap) rows[o * cap + cnt] = (int32_t)(d.id[j] - R.atom_off);
         cnt++;
     };
-    for (int q = 0; q < m; q++)
-        if (q != k) test(a0 + q, kZeroOffset);
+    const uint32_t pairs = d.gpair[gi];
+    for (int b = 0; b < m; b++)
+        if ((pairs >> (k * G + b)) & 1u) put(a0 + b);
     const int32_t gc = MD_CHECK(d, d.gnb_count[gi] <= d.gcap) ? d.gnb_count[gi] : 0;
     for (int32_t e = 0; e < gc; e++) {
-        const uint32_t en = (uint32_t)d.gnb[((int64_t)(e >> 4) * d.ngmax + gi) * 16 + (e & 15)];
-        test((int32_t)(en & kJMask), en >> kJBits);
+        const int64_t at = ((int64_t)(e >> 4) * d.ngmax + gi) * 16 + (e & 15);
+        if ((d.gmask[at] >> k) & 1u) put((int32_t)((uint32_t)d.gnb[at] & kJMask));
     }
     counts[o] = cnt;
 }
@@ -371,7 +432,7 @@ int launch_decode_group(const Dev &d, const LJ &lj, int G, int32_t *counts, int3
                         int32_t cap, cudaStream_t st, int *nl)
 {
     if (d.n <= 0) return 0;
-    if ((G != 2 && G != 4) || !d.gnb || !d.grp) return -1;
+    if ((G != 2 && G != 4) || !d.gnb || !d.grp || !d.gmask || !d.gpair) return -1;
     const bool b = d.nrep > 1;
     const unsigned g = (unsigned)((d.ngmax * G + 127) / 128);
     if (G == 4) {
@@ -388,7 +449,7 @@ int launch_decode_group(const Dev &d, const LJ &lj, int G, int32_t *counts, int3
 int launch_build_group(const Dev &d, const LJ &lj, int G, cudaStream_t st, int *nl)
 {
     if (d.n <= 0) return 0;
-    if ((G != 2 && G != 4) || !d.gnb || !d.grp) return -1;
+    if ((G != 2 && G != 4) || !d.gnb || !d.grp || !d.gmask || !d.gpair) return -1;
     const bool b = d.nrep > 1;
     const unsigned g = (unsigned)((d.ngmax * G + 127) / 128);
     if (G == 4) {

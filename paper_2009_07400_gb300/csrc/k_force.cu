@@ -233,17 +233,21 @@ __device__ __forceinline__ void mixed_full_tile(const Dev &d, const LJ &lj, int6
 // ---------------------------------------------------------------------------
 // Mixed precision, list shared by a group of G atoms of one cell.  The G
 // lanes of a group split the group's row (lane l takes the int4 chunks l,
-// l + 4, ... of each 16-entry block); each lane gathers its entries'
-// positions once and evaluates each of them against all G members, whose
-// positions it holds in registers, so a gathered position serves G pairs
-// and nothing is exchanged between lanes inside the loop.  The entry's cell
-// offset (shared by the members: one cell) is applied to the neighbour,
+// l + G, ... of each 16-entry block); each lane gathers its entries'
+// positions once and evaluates each of them against the members, whose
+// positions it holds in registers, so a gathered position serves up to G
+// pairs and nothing is exchanged between lanes inside the loop.  Each entry
+// carries a byte of member bits from the build (bit k: the entry is in member
+// k's exact Verlet row), so every member sums exactly the pairs of its own
+// row, as with per-atom lists.  The entry's cell offset (shared by the
+// members: one cell) is applied to the neighbour,
 //     d_k = p_k - (p_j + o s),
 // from a 64-entry table of o s per replica.  Each lane keeps a Kahan sum per
 // member over its chunks (four pairs per chunk and member in a plain
 // partial); the G lanes' sums are combined by a fixed butterfly (every lane
 // ends with the same totals), and lane k runs the epilogue of member k.
-// Pairs inside the group: lane l takes member l against the others.
+// Pairs inside the group: lane l takes member l against the members its
+// pair mask names.
 // ---------------------------------------------------------------------------
 template <int G, bool BATCHED, int EPI, bool ENERGY>
 __global__ void __launch_bounds__(256) k_force_mixed_group(Dev d, LJ lj)
@@ -311,7 +315,7 @@ __global__ void __launch_bounds__(256) k_force_mixed_group(Dev d, LJ lj)
             }
         }
     };
-    {   // pairs inside the group: member l against the other members
+    {   // pairs inside the group: member l against the members paired with it
         float px[G], py[G], pz[G], pv[G], pw[G];
 #pragma unroll
         for (int k = 0; k < G; k++) px[k] = py[k] = pz[k] = pv[k] = pw[k] = 0.f;
@@ -319,12 +323,13 @@ __global__ void __launch_bounds__(256) k_force_mixed_group(Dev d, LJ lj)
 #pragma unroll
         for (int k = 0; k < G; k++)
             if (k == l) { jx = qx[k]; jy = qy[k]; jz = qz[k]; }
-        const bool lm = l < m;
+        const uint32_t pairs = (uint32_t)d.gpair[gi] >> (l * G);
 #pragma unroll
         for (int k = 0; k < G; k++) {
-            // k == l would be the self pair (d = 0): moved out of range
+            // k == l would be the self pair (d = 0): moved out of range (its
+            // pair bit is never set)
             const float ox = k == l ? 1.0e4f : 0.f;
-            pair(qx[k] + ox, qy[k], qz[k], jx, jy, jz, lm, px[k], py[k], pz[k], pv[k], pw[k]);
+            pair(qx[k] + ox, qy[k], qz[k], jx, jy, jz, (pairs >> k) & 1u, px[k], py[k], pz[k], pv[k], pw[k]);
         }
         add_partials(px, py, pz, pv, pw);
     }
@@ -333,13 +338,22 @@ __global__ void __launch_bounds__(256) k_force_mixed_group(Dev d, LJ lj)
     // per block: one per lane for G = 4, two for G = 2)
     constexpr int kPer = 4 / G;
     const int nq = ((cnt + 15) >> 4) * kPer;
-    const int4 *nb4 = reinterpret_cast<const int4 *>(d.gnb) + gi * 4 + l;
-    const int64_t bstride = d.ngmax * 4;                   // int4s between 16-entry blocks
-    auto chunk_at = [&](int q) { return nb4 + (int64_t)(q / kPer) * bstride + (q % kPer) * G; };
-    int4 nxt = nq > 0 ? ld_stream(chunk_at(0)) : make_int4(0, 0, 0, 0);
+    // chunk c of the rows as int4 index c; its four member-bit bytes as the
+    // uint32 of the same index
+    const int64_t c0 = gi * 4 + l;
+    const int64_t bstride = d.ngmax * 4;                   // chunks between 16-entry blocks
+    const int4 *nb4 = reinterpret_cast<const int4 *>(d.gnb);
+    const uint32_t *mb4 = reinterpret_cast<const uint32_t *>(d.gmask);
+    auto chunk_at = [&](int q) { return c0 + (int64_t)(q / kPer) * bstride + (q % kPer) * G; };
+    int4 nxt = nq > 0 ? ld_stream(nb4 + chunk_at(0)) : make_int4(0, 0, 0, 0);
+    uint32_t mnxt = nq > 0 ? __ldcs(mb4 + chunk_at(0)) : 0u;
     for (int q = 0; q < nq; q++) {
         const int4 e4 = nxt;
-        if (q + 1 < nq) nxt = ld_stream(chunk_at(q + 1));
+        const uint32_t mw = mnxt;
+        if (q + 1 < nq) {
+            nxt = ld_stream(nb4 + chunk_at(q + 1));
+            mnxt = __ldcs(mb4 + chunk_at(q + 1));
+        }
         const uint32_t es[4] = {(uint32_t)e4.x, (uint32_t)e4.y, (uint32_t)e4.z, (uint32_t)e4.w};
         float4 pj[4], of[4];
 #pragma unroll
@@ -357,7 +371,8 @@ __global__ void __launch_bounds__(256) k_force_mixed_group(Dev d, LJ lj)
             const float jx = pj[u].x + of[u].x, jy = pj[u].y + of[u].y, jz = pj[u].z + of[u].z;
 #pragma unroll
             for (int k = 0; k < G; k++)
-                pair(qx[k], qy[k], qz[k], jx, jy, jz, true, px[k], py[k], pz[k], pv[k], pw[k]);
+                pair(qx[k], qy[k], qz[k], jx, jy, jz, (mw >> (8 * u + k)) & 1u, px[k], py[k], pz[k],
+                     pv[k], pw[k]);
         }
         add_partials(px, py, pz, pv, pw);
     }
@@ -661,7 +676,7 @@ int launch_force_group(const Dev &d, const LJ &lj, int G, int epi, bool energy, 
                        cudaStream_t st, int *nl)
 {
     if (d.n <= 0) return 0;
-    if ((G != 2 && G != 4) || !d.gnb || !d.grp || !d.offtab) return -1;
+    if ((G != 2 && G != 4) || !d.gnb || !d.grp || !d.offtab || !d.gmask || !d.gpair) return -1;
     if (G == 4) {
         if (batched) launch_group_g<4, true>(d, lj, epi, energy, st);
         else launch_group_g<4, false>(d, lj, epi, energy, st);

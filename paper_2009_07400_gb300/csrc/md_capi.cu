@@ -92,6 +92,8 @@ struct md_ctx {
     // for gsz when allocated (ngmax = ceil(n / gsz) + cell ids)
     int32_t *grp = nullptr, *gcnt = nullptr, *gcell_start = nullptr, *gnb = nullptr,
             *gnb_count = nullptr;
+    uint8_t *gmask = nullptr;       // member bits per entry (laid out like gnb)
+    uint16_t *gpair = nullptr;      // member pairs per group
     int64_t ngmax = 0;
     int32_t gcap = 0, gsz = 0;
     double expect_row = 0;          // expected full-list row at the densest replica
@@ -181,6 +183,8 @@ Dev view(const md_ctx *c)
     d.gcell_start = c->gcell_start;
     d.gnb = c->gnb;
     d.gnb_count = c->gnb_count;
+    d.gmask = c->gmask;
+    d.gpair = c->gpair;
     d.ngmax = c->ngmax;
     d.gcap = c->gcap;
     d.offtab = c->offtab_d;
@@ -233,7 +237,7 @@ void free_all(md_ctx *c)
                     c->p32_ref, c->v32[0], c->v32[1], c->adj.ck_x, c->adj.ck_v, c->adj.blk_x,
                     c->adj.xbar, c->adj.wbar, c->adj.blk_p, c->adj.ck_p, c->adj.wbar32,
                     c->adj.ck_id, c->adj.ge, c->adj.gs, c->adj.g2, c->grp, c->gcnt,
-                    c->gcell_start, c->gnb, c->gnb_count, c->offtab_d};
+                    c->gcell_start, c->gnb, c->gnb_count, c->offtab_d, c->gmask, c->gpair};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->own_stream && c->st) cudaStreamDestroy(c->st);
@@ -277,17 +281,23 @@ int alloc_group(md_ctx *c, int g, int32_t cap)
             if (*a) cudaFree(*a);
             *a = nullptr;
         }
+        if (c->gpair) cudaFree(c->gpair);
+        c->gpair = nullptr;
         c->gsz = 0;
         c->ngmax = (c->n + g - 1) / g + c->nids;
         if ((rc = dalloc(c, &c->grp, (size_t)c->ngmax)) || (rc = dalloc(c, &c->gnb_count, (size_t)c->ngmax)) ||
+            (rc = dalloc(c, &c->gpair, (size_t)c->ngmax)) ||
             (rc = dalloc(c, &c->gcnt, (size_t)c->nids)) || (rc = dalloc(c, &c->gcell_start, (size_t)c->nids + 1)))
             return rc;
         c->gsz = g;
     }
     if (c->gnb) cudaFree(c->gnb);
+    if (c->gmask) cudaFree(c->gmask);
     c->gnb = nullptr;
+    c->gmask = nullptr;
     c->gcap = (int32_t)((std::max<int64_t>(cap, 16) + 15) / 16 * 16);
     rc = dalloc(c, &c->gnb, (size_t)c->ngmax * (size_t)c->gcap);
+    if (!rc) rc = dalloc(c, &c->gmask, (size_t)c->ngmax * (size_t)c->gcap);
     for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
     c->graphs.clear();
     return rc;

@@ -181,6 +181,11 @@ struct Dev {
     // group's G lanes reads the int4 chunks l, l + 4, ... of each 16-entry
     // block.  Null when no group list was set up.
     int32_t *grp, *gcnt, *gcell_start, *gnb, *gnb_count;
+    // which members each entry belongs to (bit k: member k's exact row holds
+    // it; one byte per entry, laid out like the entries), and per group the
+    // member pairs inside the list radius (bit a * G + b, both orders)
+    uint8_t *gmask;
+    uint16_t *gpair;
     int64_t ngmax;            // group slots allocated: ceil(n / G) + cells
     int32_t gcap;             // entries per group row (multiple of 16)
     const float4 *offtab;     // per replica 64 codes: (ox s_x, oy s_y, oz s_z) of a
