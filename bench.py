@@ -199,8 +199,9 @@ def algorithmic_bytes_per_atom(mean_nb, list_type, rows_per_atom=1.0):
     """DRAM bytes per atom and time step the dominant kernel must move.
     Full and group lists (force kernel with the fused velocity-Verlet
     epilogue): the 4-byte list entries (mean_nb per atom: row lengths summed
-    over the rows / atoms), 4 bytes of row length per row (and 4 of group
-    table per group row), the FP32 position read and the next step's FP32
+    over the rows / atoms; group lists add a byte of member bits per entry),
+    4 bytes of row length per row (group rows also 4 of group table and 2 of
+    member-pair mask), the FP32 position read and the next step's FP32
     position write (16 + 16), and read + write of FP64 position and velocity
     (24 B each way, 3 doubles).  Half list (force kernel alone): the list
     entries, the row length, the FP32 position read and the final force
@@ -208,8 +209,9 @@ def algorithmic_bytes_per_atom(mean_nb, list_type, rows_per_atom=1.0):
     gathered from L2 and are not counted."""
     if list_type == 1:
         return 4.0 * mean_nb + 4 + 16 + 16
-    per_row = 8.0 if list_type in (2, 4) else 4.0
-    return 4.0 * mean_nb + per_row * rows_per_atom + 16 + 16 + 2 * 24 + 2 * 24
+    if list_type in (2, 4):
+        return 5.0 * mean_nb + 10.0 * rows_per_atom + 16 + 16 + 2 * 24 + 2 * 24
+    return 4.0 * mean_nb + 4.0 * rows_per_atom + 16 + 16 + 2 * 24 + 2 * 24
 
 
 def time_cycles(ctx, steps, warmup, dist, torch, timesteps=TIMESTEPS_PER_STEP):

@@ -388,142 +388,6 @@ __global__ void __launch_bounds__(128, 4) k_build_group(Dev d, LJ lj)
     }
 }
 
-// ---------------------------------------------------------------------------
-// Per-atom full lists built group by group.  The rows are those of k_build
-// (same entries, same order: stencil order, then candidate order), but the
-// candidates of a stencil cell are loaded and offset once for the G atoms of
-// a group: the G lanes take the candidates G * U at a time, test each against
-// every member (FP32 classification, FP64 inside the band) and, per member,
-// append the accepted ones to that member's row with a ballot over the
-// group's lanes.  Loops run the warp's largest trip count (full-warp
-// ballots).
-// ---------------------------------------------------------------------------
-template <int G, bool BATCHED>
-__global__ void __launch_bounds__(128, 4) k_build_rows_grouped(Dev d, LJ lj)
-{
-    if (stopped(d.status)) return;
-    constexpr int U = 2;                                    // candidates per lane per round
-    constexpr unsigned gbits = (1u << G) - 1u;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t gi = t / G;
-    const int l = (int)(t % G);
-    const int lane = threadIdx.x & 31;
-    const int gbase = lane & ~(G - 1);
-    const int32_t ng = d.gcell_start[d.ncells];
-    int32_t a0 = 0;
-    int m = 0;
-    if (gi < ng && MD_CHECK(d, gi < d.ngmax)) {
-        const uint32_t gw = (uint32_t)d.grp[gi];
-        a0 = (int32_t)(gw & kJMask);
-        m = (int)(gw >> kJBits) + 1;
-        if (!MD_CHECK(d, a0 + m <= d.n)) m = 0;
-    }
-    const Rep &R = d.reps[BATCHED && m > 0 ? d.rep_of[a0] : 0];
-    float px[G], py[G], pz[G];
-    uint32_t pack = 0;
-#pragma unroll
-    for (int k = 0; k < G; k++) {
-        const float4 q = k < m ? d.p32[a0 + k] : make_float4(-1.0e4f, -1.0e4f, -1.0e4f, 0.f);
-        px[k] = q.x; py[k] = q.y; pz[k] = q.z;
-        if (k == 0 && m > 0) pack = __float_as_uint(q.w);
-    }
-    const int ci[3] = {(int)(pack & 1023u), (int)((pack >> 10) & 1023u), (int)((pack >> 20) & 1023u)};
-    const int64_t n = d.n;
-    const int32_t cap = d.cap;
-    const float4 *p32 = d.p32;
-    const float lo = lj.rs2f_lo, hi = lj.rs2f_hi;
-    int32_t cnt[G];
-#pragma unroll
-    for (int k = 0; k < G; k++) cnt[k] = 0;
-
-    for (int ox = -1; ox <= 1; ox++) {
-        int ux = ci[0] + ox, kx = 0;
-        if (ux < 0) { ux += R.nc[0]; kx = -1; } else if (ux >= R.nc[0]) { ux -= R.nc[0]; kx = 1; }
-        const float offx = (float)ox * -R.nsf[0];
-        for (int oy = -1; oy <= 1; oy++) {
-            int uy = ci[1] + oy, ky = 0;
-            if (uy < 0) { uy += R.nc[1]; ky = -1; } else if (uy >= R.nc[1]) { uy -= R.nc[1]; ky = 1; }
-            const float offy = (float)oy * -R.nsf[1];
-            const int32_t col = (int32_t)cell_id(R, ux, uy, 0);
-            for (int oz = -1; oz <= 1; oz++) {
-                int uz = ci[2] + oz, kz = 0;
-                if (uz < 0) { uz += R.nc[2]; kz = -1; } else if (uz >= R.nc[2]) { uz -= R.nc[2]; kz = 1; }
-                const float offz = (float)oz * -R.nsf[2];
-                const int32_t cid = cell_id_z(col, uz);
-                int32_t j0 = 0, j1 = 0;
-                if (m > 0 && MD_CHECK(d, cid >= 0 && cid < d.ncells)) {
-                    j0 = d.cell_start[cid];
-                    j1 = d.cell_start[cid + 1];
-                    if (!MD_CHECK(d, j0 >= 0 && j0 <= j1 && j1 <= d.n)) j1 = j0;
-                }
-                const uint32_t tag = offset_code(ox, oy, oz) << kJBits;
-                const int nr = (j1 - j0 + G * U - 1) / (G * U);
-                const int rmax = __reduce_max_sync(0xffffffffu, nr);
-                for (int r = 0; r < rmax; r++) {
-                    uint32_t mk[U];
-                    int32_t jj[U];
-#pragma unroll
-                    for (int u = 0; u < U; u++) {
-                        const int32_t j = j0 + (r * U + u) * G + l;
-                        const bool valid = j < j1;
-                        const float4 pj = __ldg(p32 + (valid ? j : d.n));
-                        const float qx = pj.x + offx, qy = pj.y + offy, qz = pj.z + offz;
-                        uint32_t in = 0, band = 0;
-#pragma unroll
-                        for (int k = 0; k < G; k++) {
-                            const float dx = px[k] - qx, dy = py[k] - qy, dz = pz[k] - qz;
-                            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                            in |= (uint32_t)(r2 < lo) << k;
-                            band |= (uint32_t)((r2 >= lo) & (r2 < hi)) << k;
-                        }
-                        // never the atom itself
-                        const uint32_t self = (uint32_t)(j - a0) < (uint32_t)m ? 1u << (j - a0) : 0u;
-                        in &= ~self;
-                        band &= ~self;
-                        if (!valid) in = band = 0;
-                        if (band) in |= exact_bits<G>(d, lj, R, a0, j, band, kx, ky, kz);
-                        mk[u] = in;
-                        jj[u] = (int32_t)((uint32_t)j | tag);
-                    }
-#pragma unroll
-                    for (int u = 0; u < U; u++) {
-#pragma unroll
-                        for (int k = 0; k < G; k++) {
-                            const bool acc = (mk[u] >> k) & 1u;
-                            const unsigned bal = (__ballot_sync(0xffffffffu, acc) >> gbase) & gbits;
-                            if (acc) {
-                                const int32_t e = cnt[k] + __popc(bal & ((1u << l) - 1u));
-                                if (e < cap) d.nb[((int64_t)(e >> 2) * n + a0 + k) * 4 + (e & 3)] = jj[u];
-                            }
-                            cnt[k] += __popc(bal);
-                        }
-                    }
-                }
-            }
-        }
-    }
-    if (m == 0) return;
-    // lane k pads member k's last chunk and records its row length
-    if (l < m) {
-        int32_t c = 0;
-#pragma unroll
-        for (int k = 0; k < G; k++)
-            if (k == l) c = cnt[k];
-        const int64_t i = a0 + l;
-        if (c < cap) {
-            const int32_t pad = (int32_t)((uint32_t)n | (kZeroOffset << kJBits));
-            for (int32_t e = c; (e & 3) != 0; e++) d.nb[((int64_t)(e >> 2) * n + i) * 4 + (e & 3)] = pad;
-        }
-        d.nb_count[i] = c;
-        atomicMax(&d.status->max_count, c);
-        if (c > cap) {
-            atomicOr(&d.status->flags, FLAG_NL_OVERFLOW);
-            d.status->overflow_at = d.status->rebuild_count;
-            d.status->overflow_step = d.status->dev_step;
-        }
-    }
-}
-
 // Per-atom rows of a group list: member k of group g holds the entries of
 // the group's row with bit k set and the members paired with it; counts and
 // rows in caller order (rows: replica-local ids, at most cap per row; counts
@@ -577,23 +441,6 @@ int launch_decode_group(const Dev &d, const LJ &lj, int G, int32_t *counts, int3
     } else {
         if (b) k_decode_group<2, true><<<g, 128, 0, st>>>(d, lj, counts, rows, cap);
         else k_decode_group<2, false><<<g, 128, 0, st>>>(d, lj, counts, rows, cap);
-    }
-    *nl += 1;
-    return (int)cudaGetLastError();
-}
-
-int launch_build_rows_grouped(const Dev &d, const LJ &lj, int G, cudaStream_t st, int *nl)
-{
-    if (d.n <= 0) return 0;
-    if ((G != 2 && G != 4) || !d.grp || !d.gcell_start) return -1;
-    const bool b = d.nrep > 1;
-    const unsigned g = (unsigned)((d.ngmax * G + 127) / 128);
-    if (G == 4) {
-        if (b) k_build_rows_grouped<4, true><<<g, 128, 0, st>>>(d, lj);
-        else k_build_rows_grouped<4, false><<<g, 128, 0, st>>>(d, lj);
-    } else {
-        if (b) k_build_rows_grouped<2, true><<<g, 128, 0, st>>>(d, lj);
-        else k_build_rows_grouped<2, false><<<g, 128, 0, st>>>(d, lj);
     }
     *nl += 1;
     return (int)cudaGetLastError();

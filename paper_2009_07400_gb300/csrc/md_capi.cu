@@ -271,8 +271,7 @@ int alloc_list(md_ctx *c, int32_t cap)
 
 // Group table for groups of g atoms of a cell: table, per-cell counts and
 // their prefix sums, and the per-group row lengths and member-pair masks of a
-// group list (ngmax = ceil(n / g) + cell ids).  The full per-atom lists are
-// built through it too.
+// group list (ngmax = ceil(n / g) + cell ids).
 int alloc_group_table(md_ctx *c, int g)
 {
     if (c->gsz == g) return MD_OK;
@@ -359,11 +358,11 @@ int enq_bin(md_ctx *c, int *nl)
 // group table of the current binning first).
 int launch_list_build(md_ctx *c, const Dev &d, cudaStream_t st, int *nl)
 {
-    if (is_half(c)) return launch_build(d, c->lj, true, c->nids, st, nl);
-    // full and group lists: the group table of this binning first
-    if (launch_group_table(d, c->gsz, c->nids, c->scan_tmp, c->scan_len, st, nl) != 0) return -1;
-    if (list_g(c)) return launch_build_group(d, c->lj, list_g(c), st, nl);
-    return launch_build_rows_grouped(d, c->lj, c->gsz, st, nl);
+    if (list_g(c)) {
+        if (launch_group_table(d, list_g(c), c->nids, c->scan_tmp, c->scan_len, st, nl) != 0) return -1;
+        return launch_build_group(d, c->lj, list_g(c), st, nl);
+    }
+    return launch_build(d, c->lj, is_half(c), c->nids, st, nl);
 }
 
 int enq_build(md_ctx *c, int *nl)
@@ -1847,7 +1846,6 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
     int64_t cap0 = (int64_t)(1.3 * expect) + 16;
     cap0 = std::min<int64_t>(cap0, maxn + 3);
     if ((rc = alloc_list(c, (int32_t)std::max<int64_t>(cap0, 4)))) return rc;
-    if ((rc = alloc_group_table(c, list_g(c) ? list_g(c) : 4))) return rc;
     if (list_g(c) &&
         (rc = alloc_group(c, list_g(c), (int32_t)std::min<int64_t>(group_cap0(c, list_g(c)), maxn + 16))))
         return rc;

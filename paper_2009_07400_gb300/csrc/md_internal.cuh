@@ -356,9 +356,6 @@ int64_t scan_tmp_elems(int64_t ncells_total);
 int launch_group_table(const Dev &d, int G, int64_t ncells, int32_t *tmp, int64_t tmp_len,
                        cudaStream_t st, int *nlaunch);
 int launch_build_group(const Dev &d, const LJ &lj, int G, cudaStream_t st, int *nlaunch);
-// per-atom full-list rows (the rows of launch_build) built from the group
-// table of groups of G atoms
-int launch_build_rows_grouped(const Dev &d, const LJ &lj, int G, cudaStream_t st, int *nlaunch);
 int launch_force_group(const Dev &d, const LJ &lj, int G, int epi, bool energy, bool batched,
                        cudaStream_t st, int *nlaunch);
 // exact per-atom rows (FP64 criterion) from a group list: counts (n, caller

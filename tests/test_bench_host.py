@@ -23,9 +23,9 @@ def test_algorithmic_bytes_per_atom():
     assert bench.algorithmic_bytes_per_atom(75.0, 0) == 4 * 75 + 4 + 32 + 96
     # half list, force only: entries, row length, p32 in, force out
     assert bench.algorithmic_bytes_per_atom(37.5, 1) == 4 * 37.5 + 4 + 32
-    # group list of 4, fused step: entries per atom, row length and group
-    # table entry per group (0.26 groups per atom)
-    assert bench.algorithmic_bytes_per_atom(35.0, 4, 0.26) == 4 * 35 + 8 * 0.26 + 32 + 96
+    # group list of 4, fused step: entries and their member bytes per atom,
+    # row length, group table entry and pair mask per group (0.27 per atom)
+    assert bench.algorithmic_bytes_per_atom(35.0, 4, 0.27) == 5 * 35 + 10 * 0.27 + 32 + 96
 
 
 def test_parse_tuned():
