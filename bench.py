@@ -42,6 +42,7 @@ WORKLOADS = {
     "fcc80": "fcc80_2048000",      # the paper's single-GPU shape; FP64 leg: full list, 1 lane/atom
     "dem": "dem64_1048576",        # spring-dashpot contacts (Eq. 3), 1,048,576 spheres
     "adjoint": "fcc16_16384",      # differentiable rollout: 200 steps, loss window 50
+    "study": "fcc64_1048576",      # design studies on the benchmark workload (run_study)
 }
 # the contact model's parameters for the dem workload (sigma = sphere diameter)
 DEM_PARAMS = dict(sigma=1.0, cutoff=1.0, skin=0.3, dt=0.001)
@@ -758,6 +759,105 @@ def run_adjoint(args):
     print(json.dumps(line), flush=True)
 
 
+def _study_context(md, s, stream, **kw):
+    ctx = md.MDContext(s.pos, s.vel, s.box, stream=stream, precision=md.MD_MIXED, **kw)
+    ctx.run(STEPS_PER_CYCLE)              # a rebuild cycle: the steady state
+    return ctx
+
+
+def run_cellorder_child(tile):
+    """One cell order (cells numbered in tiles of `tile` cells per edge; the
+    library uses 2): build that library, time the 1M-atom mixed step (per
+    phase with md_profile, and a graph-replayed 200-step run with CUDA
+    events) and print one JSON object."""
+    import torch
+
+    from paper_2009_07400_gb300 import build, md
+    torch.cuda.set_device(0)
+    md.load(build.build(cell_tile=tile))
+    s = inputs.workload(WORKLOAD)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    out = {"cell_tile": tile}
+    with _study_context(md, s, stream.cuda_stream, list_type=0, threads_per_atom=1) as ctx:
+        ctx.run(2 * STEPS_PER_CYCLE)
+        p = ctx.profile(4 * STEPS_PER_CYCLE)
+        out["force_us"] = 1e3 * p.force_ms / p.steps
+        out["neigh_us_per_step"] = 1e3 * p.neigh_ms / p.steps
+        ms, _ = time_cycles(ctx, 3, 1, None, torch)
+        out["step_us"] = 1e3 * ms / (3 * TIMESTEPS_PER_STEP)
+        ids = np.random.default_rng(0).choice(s.n, 512, replace=False)
+        out["force_sample"] = ctx.forces()[ids].tolist()
+    print(json.dumps(out), flush=True)
+
+
+def run_study(args):
+    """Design studies behind the library's choices, on the 1,048,576-atom
+    benchmark workload (mixed path), each against the library's own choice on
+    the same state:
+      * force-kernel variants (md_study_force_variant, full per-atom list,
+        one lane per atom, forces only): gathered-position layouts (AoS, the
+        library's; SoA; AoSoA) and the tile neighbourhood staged in shared
+        memory;
+      * list types: the per-atom full list against lists shared by groups of
+        2 and 4 atoms (md_profile per phase);
+      * cell orders: libraries built with cell tiles of 1 (z fastest), 2 (the
+        library's) and 4 cells per edge, each timed in its own process.
+    Prints one JSON line."""
+    import torch
+
+    from paper_2009_07400_gb300 import build, md
+    torch.cuda.set_device(0)
+    build.build()
+    md.load()
+    s = inputs.workload(WORKLOAD)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    reps = max(5, args.steps)
+    names = {0: "AoS float4 (library)", 1: "SoA", 2: "AoSoA (blocks of 4)",
+             3: "2x2x2-cell tiles, 4x4x4-cell neighbourhood in shared memory"}
+    variants = {}
+    with _study_context(md, s, stream.cuda_stream, list_type=0, threads_per_atom=1) as ctx:
+        F = {}
+        for v in (0, 1, 2, 3):
+            times = [ctx.study_force_variant(v, reps)[0] for _ in range(3)]
+            F[v] = ctx.study_force_variant(v, 1, forces=True)[1]
+            variants[names[v]] = {"us_per_launch": min(times), "runs": times}
+        for v in (1, 2, 3):
+            d = F[v] - F[0]
+            variants[names[v]]["max_abs_force_diff_vs_library"] = float(np.abs(d).max())
+            variants[names[v]]["rms_rel_vs_library"] = float(np.sqrt(np.sum(d ** 2) / np.sum(F[0] ** 2)))
+    lists = {}
+    for lt, nm in ((0, "per-atom full"), (2, "groups of 2"), (4, "groups of 4")):
+        with _study_context(md, s, stream.cuda_stream, list_type=lt, threads_per_atom=1) as ctx:
+            ctx.run(2 * STEPS_PER_CYCLE)
+            p = ctx.profile(4 * STEPS_PER_CYCLE)
+            ms, _ = time_cycles(ctx, 2, 1, None, torch)
+            lists[nm] = {"force_us": 1e3 * p.force_ms / p.steps,
+                         "neigh_us_per_step": 1e3 * p.neigh_ms / p.steps,
+                         "list_entries_per_atom": p.mean_neighbors,
+                         "step_us": 1e3 * ms / (2 * TIMESTEPS_PER_STEP)}
+    orders = {}
+    for tile in (1, 2, 4):
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cellorder-child", str(tile)],
+                           capture_output=True, text=True, timeout=1800)
+        if r.returncode != 0:
+            raise SystemExit(f"cell-order child {tile} failed:\n{r.stderr[-3000:]}")
+        orders[tile] = json.loads([ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1])
+    ref = np.array(orders[2].pop("force_sample"))
+    for tile in (1, 4):
+        f = np.array(orders[tile].pop("force_sample"))
+        orders[tile]["rms_rel_force_vs_tile2"] = float(np.sqrt(np.sum((f - ref) ** 2) / np.sum(ref ** 2)))
+    line = {"study": "design choices of the mixed force path, 1,048,576-atom FCC liquid "
+                     "(rho 0.8442, T 1.44, jitter 0.05), full lists unless stated",
+            "force_kernel_variants": variants, "list_types": lists,
+            "cell_orders": {f"tiles of {t} cells per edge" + (" (library)" if t == 2 else ""): o
+                            for t, o in orders.items()},
+            "timing": "CUDA events on the context's stream; variants: best of 3 runs of "
+                      f"{reps} launches each"}
+    print(json.dumps(line), flush=True)
+
+
 def run_ncu_case(which, pin=None):
     """Create the workload's context and run 2 cycles: 1 first drift, then
     per cycle 19 fused steps, a rebuild (binning kernels + build) and the
@@ -799,14 +899,24 @@ def main():
     ap.add_argument("--tuned", metavar="TPA,HALF,TPA64,HALF64",
                     help="skip the autotuner and use these lanes per atom and list "
                          "types for the mixed and FP64 legs (for profiling commands)")
+    ap.add_argument("--cellorder-child", type=int, choices=[1, 2, 4], help=argparse.SUPPRESS)
     ap.add_argument("--ncu-case", choices=["mixed", "fp64", "dem"],
                     help="only build the workload and run 2 rebuild cycles (a short, "
                          "fixed launch sequence for an ncu capture); prints nothing")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.ncu_case:
+    if args.cellorder_child:
+        run_cellorder_child(args.cellorder_child)
+    elif args.ncu_case:
         run_ncu_case(args.ncu_case, parse_tuned(args.tuned))
+    elif args.workload == "study":
+        if args.impl == "native":
+            run_study(args)
+        else:
+            print(json.dumps({"impl": "reference", "unavailable": "the design studies compare "
+                              "GPU kernels with each other; the oracle arm covers the "
+                              "forward workloads"}), flush=True)
     elif args.workload == "adjoint":
         if args.impl == "native":
             run_adjoint(args)

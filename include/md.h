@@ -337,6 +337,25 @@ int md_adjoint_device(md_ctx *ctx, int64_t nsteps, int64_t window, int32_t ckpt_
  * FP64 pair terms.  Not in the paper.  Errors: MD_ERR_INVAL. */
 int md_set_adjoint_precision(md_ctx *ctx, int32_t precision);
 
+/* Force-kernel studies: variants of the mixed full-list force pass that the
+ * library measured and did not adopt, kept runnable so those measurements can
+ * be repeated on the current state and list (not part of the method).  Runs
+ * one warm-up and `reps` timed launches of variant
+ *   0  the library's kernel (16-byte FP32 cell-relative gathers, offsets
+ *      selected in registers; Sec. 4.2's AoS layout),
+ *   1  SoA gathers (three float arrays), 2  AoSoA gathers (blocks of four
+ *      atoms, x0..x3 y0..y3 z0..z3: Sec. 4.2's clustered layout), both with
+ *      the library's arithmetic in its order (bitwise the same forces),
+ *   3  the 4x4x4-cell neighbourhood of each 2x2x2-cell tile staged in shared
+ *      memory in the tile's frame (one block per tile)
+ * with forces only (no integration), CUDA events on the context's stream;
+ * *us = mean device time per launch in microseconds; forces (may be NULL):
+ * host, n x 3 doubles in caller order.  Needs a single-system mixed LJ
+ * context with full per-atom lists.
+ * Errors: MD_ERR_INVAL, MD_ERR_STATE (wrong kind of context; variant 3: a
+ * neighbourhood above 3008 atoms), MD_ERR_NOMEM, MD_ERR_CUDA. */
+int md_study_force_variant(md_ctx *ctx, int32_t variant, int32_t reps, double *us, double *forces);
+
 /* Chooses threads_per_atom and the list type by timing each candidate for
  * `steps` steps on the context's own state (which it restores), keeps the
  * fastest and reports it in *chosen (may be NULL).  Results are cached per

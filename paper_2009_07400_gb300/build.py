@@ -47,12 +47,22 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, debug: bool = False,
+          cell_tile: int = 2) -> str:
     """Compiles (if needed) and returns the path of libmdgb300.so, or with
-    debug=True of the bounds-checked libmdgb300_debug.so."""
+    debug=True of the bounds-checked libmdgb300_debug.so.  cell_tile (1, 2
+    or 4): the edge of the cell tiles that number the cells (and so order the
+    atoms); the library uses 2, and the others build libmdgb300_tile1.so /
+    libmdgb300_tile4.so for the cell-order study of bench.py."""
+    if cell_tile not in (1, 2, 4) or (debug and cell_tile != 2):
+        raise ValueError("cell_tile must be 1, 2 or 4 (2 for the debug build)")
     nvcc = _nvcc()
     out_dir, lib = (DEBUG_OUT_DIR, DEBUG_LIB) if debug else (OUT_DIR, LIB)
-    flags = NVCC_FLAGS + (["-DMD_DEBUG_CHECKS=1"] if debug else [])
+    if cell_tile != 2:
+        out_dir = os.path.join(HERE, f"_build_tile{cell_tile}")
+        lib = os.path.join(HERE, f"libmdgb300_tile{cell_tile}.so")
+    flags = NVCC_FLAGS + (["-DMD_DEBUG_CHECKS=1"] if debug else []) + (
+        [f"-DMD_CELL_TILE={cell_tile}"] if cell_tile != 2 else [])
     os.makedirs(out_dir, exist_ok=True)
     headers = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(
         os.path.join(os.path.dirname(HERE), "include", "*.h"))

@@ -1545,6 +1545,67 @@ int md_adjoint_device(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt, d
     return adjoint_impl(c, nsteps, window, ckpt, loss, g_eps, g_sigma, g_x0, g_v0, true);
 }
 
+int md_study_force_variant(md_ctx *c, int32_t variant, int32_t reps, double *us, double *forces)
+{
+    if (!c || !us || reps < 1 || variant < 0 || variant > 3) return fail(c, MD_ERR_INVAL, "bad argument");
+    if (!is_mixed(c) || c->p.list_type != MD_LIST_FULL || is_sd(c) || c->nrep != 1)
+        return fail(c, MD_ERR_STATE, "force studies take a single-system mixed LJ context with full lists");
+    if (variant == 3 && kTile != 2)
+        return fail(c, MD_ERR_STATE, "the shared-memory study stages 2x2x2-cell tiles (a build with MD_CELL_TILE = 2)");
+    int rc = ensure_list(c);
+    if (rc) return rc;
+    float4 *fout = nullptr;
+    float *lay = nullptr;
+    if ((rc = dalloc(c, &fout, (size_t)c->n)) || (rc = dalloc(c, &lay, (size_t)study_layout_floats(c->n)))) {
+        cudaFree(fout);
+        return rc;
+    }
+    Dev d = view(c);
+    d.f32 = fout;                                    // the library's kernel writes here too
+    const int64_t ntiles = (int64_t)c->reps_h[0].nt[0] * c->reps_h[0].nt[1] * c->reps_h[0].nt[2];
+    int nl = 0;
+    auto launch = [&]() -> int {
+        if (variant == 0) return launch_force(d, c->lj, MD_MIXED, false, 1, EPI_F, false, false, c->st, &nl);
+        if (variant == 3) return launch_study_tiles(d, c->lj, ntiles, fout, c->st, &nl);
+        return launch_study_force(d, c->lj, variant, lay, fout, c->st, &nl);
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess && launch() != 0) e = cudaErrorLaunchFailure;   // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, c->st);
+    for (int32_t r = 0; e == cudaSuccess && r < reps; r++)
+        if (launch() != 0) e = cudaErrorLaunchFailure;
+    if (e == cudaSuccess) e = cudaEventRecord(e1, c->st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    c->launches += nl;
+    if (e == cudaSuccess) {
+        *us = 1e3 * (double)ms / reps;
+        DevStatus st;
+        if (!(rc = read_status(c, &st)) && (st.flags & FLAG_NL_OVERFLOW)) {
+            CK(cudaMemsetAsync(&c->status->flags, 0, sizeof(int32_t), c->st));
+            rc = fail(c, MD_ERR_STATE, "a tile neighbourhood holds more atoms than the staging array");
+        }
+        if (!rc && forces) {
+            nl = 0;
+            if (launch_gather_out(d, 3, c->io_d, c->st, &nl) != 0) rc = fail(c, MD_ERR_CUDA, "gather failed");
+            c->launches += nl;
+            if (!rc) {
+                e = cudaMemcpyAsync(forces, c->io_d, sizeof(double) * 3 * c->n, cudaMemcpyDeviceToHost, c->st);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+            }
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(fout);
+    cudaFree(lay);
+    if (e != cudaSuccess && !rc) rc = fail(c, MD_ERR_CUDA, std::string("study: ") + cudaGetErrorString(e));
+    return rc;
+}
+
 int md_set_adjoint_precision(md_ctx *c, int32_t precision)
 {
     if (!c || (precision != MD_FP64 && precision != MD_MIXED))
@@ -1706,13 +1767,13 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
             R.invsf[d] = 1.0f / (float)R.s[d];
             vol *= L[d];
         }
-        for (int d = 0; d < 3; d++) R.nt[d] = (R.nc[d] + 1) / 2;
+        for (int d = 0; d < 3; d++) R.nt[d] = (R.nc[d] + kTile - 1) / kTile;
         R.cell_off = ids;
         R.ctr_off = 0;   // set below
         R.atom_off = n;
         R.natoms = counts[r];
         cells += (int64_t)R.nc[0] * R.nc[1] * R.nc[2];
-        ids += (int64_t)R.nt[0] * R.nt[1] * R.nt[2] * 8;
+        ids += (int64_t)R.nt[0] * R.nt[1] * R.nt[2] * kTile3;
         chunk_first.push_back((int64_t)chunk_rep.size() / 2);
         for (int64_t k = 0; k < energy_chunks_of(counts[r]); k++) {
             chunk_rep.push_back(r);

@@ -89,43 +89,50 @@ struct Rep {
     float nsf[3];             // -s in FP32 (stencil offsets of the mixed path)
     float invsf[3];           // fl32(1 / fl32(s)) (binning's quotient estimate)
     int32_t nc[3];
-    int32_t nt[3];            // 2x2x2-cell tiles per dimension, (nc + 1) / 2
+    int32_t nt[3];            // cell tiles per dimension, ceil(nc / MD_CELL_TILE)
     int64_t ctr_off;          // first entry of this replica in Dev::ctr
     int64_t cell_off;         // first global cell id of this replica
     int64_t atom_off;         // first atom slot of this replica
     int64_t natoms;
 };
 
-// Linear cell ids.  Cells are numbered tile by tile: 2x2x2-cell tiles in
-// (tx, ty, tz) order with tz fastest, the 8 cells of a tile in (x, y, z) bit
-// order.  Atoms are sorted by this id, so the 256 consecutive atoms of a
-// thread block form a compact brick of cells instead of a pencil along z,
-// whose neighbourhood (the cells its gathers touch) is about a third smaller.
-// With an odd nc the last tile of a row sticks out of the box; its missing
-// cells get ids but never atoms.
+// Linear cell ids.  Cells are numbered tile by tile: T x T x T-cell tiles
+// (T = MD_CELL_TILE, 2 unless a build sets it) in (tx, ty, tz) order with tz
+// fastest, the cells of a tile in (x, y, z) order with z fastest.  Atoms are
+// sorted by this id, so the 256 consecutive atoms of a thread block form a
+// compact brick of cells instead of a pencil along z (T = 1 is the plain
+// z-fastest order), whose neighbourhood (the cells its gathers touch) is
+// about a third smaller.  When T does not divide nc the last tile of a row
+// sticks out of the box; its missing cells get ids but never atoms.
+#ifndef MD_CELL_TILE
+#define MD_CELL_TILE 2
+#endif
+constexpr int kTile = MD_CELL_TILE;
+static_assert(kTile == 1 || kTile == 2 || kTile == 4, "cell tiles of 1, 2 or 4 cells per edge");
+constexpr int kTile3 = kTile * kTile * kTile;
 __host__ __device__ __forceinline__ int64_t cell_id(const Rep &R, int cx, int cy, int cz)
 {
-    const int64_t tile = ((int64_t)(cx >> 1) * R.nt[1] + (cy >> 1)) * R.nt[2] + (cz >> 1);
-    return R.cell_off + tile * 8 + (((cx & 1) << 2) | ((cy & 1) << 1) | (cz & 1));
+    const int64_t tile = ((int64_t)(cx / kTile) * R.nt[1] + (cy / kTile)) * R.nt[2] + (cz / kTile);
+    return R.cell_off + tile * kTile3 + ((cx % kTile) * kTile + (cy % kTile)) * kTile + (cz % kTile);
 }
 // Id of cell (cx, cy, cz) from the id `col` of (cx, cy, 0) (cell ids are
 // below 2^31).
 __host__ __device__ __forceinline__ int32_t cell_id_z(int32_t col, int cz)
 {
-    return col + ((cz >> 1) << 3) + (cz & 1);
+    return col + (cz / kTile) * kTile3 + (cz % kTile);
 }
 __host__ __device__ __forceinline__ void cell_coords(const Rep &R, int64_t id, int &cx, int &cy,
                                                      int &cz)
 {
     const int64_t local = id - R.cell_off;
-    const int64_t tile = local >> 3;
-    const int l = (int)(local & 7);
+    const int64_t tile = local / kTile3;
+    const int l = (int)(local % kTile3);
     const int tz = (int)(tile % R.nt[2]);
     const int ty = (int)((tile / R.nt[2]) % R.nt[1]);
     const int tx = (int)(tile / ((int64_t)R.nt[2] * R.nt[1]));
-    cx = 2 * tx + ((l >> 2) & 1);
-    cy = 2 * ty + ((l >> 1) & 1);
-    cz = 2 * tz + (l & 1);
+    cx = kTile * tx + l / (kTile * kTile);
+    cy = kTile * ty + (l / kTile) % kTile;
+    cz = kTile * tz + l % kTile;
 }
 
 // LJ constants in both precisions.
@@ -351,6 +358,15 @@ int launch_rebuild_check(const Dev &d, cudaGraphConditionalHandle h, cudaStream_
                          int *nlaunch);
 
 int64_t scan_tmp_elems(int64_t ncells_total);
+
+// Force-kernel studies (k_study.cu): variants 1 (SoA gathers) and 2 (AoSoA
+// gathers) into fout; variant 3 (neighbourhood staged in shared memory, one
+// block per 2x2x2-cell tile).  Single replica, mixed path, full lists.
+int64_t study_layout_floats(int64_t n);
+int launch_study_force(const Dev &d, const LJ &lj, int variant, float *layouts, float4 *fout,
+                       cudaStream_t st, int *nlaunch);
+int launch_study_tiles(const Dev &d, const LJ &lj, int64_t ntiles, float4 *fout, cudaStream_t st,
+                       int *nlaunch);
 
 // Lists shared by groups of G atoms (k_bin.cu, k_build.cu, k_force.cu, k_misc.cu)
 int launch_group_table(const Dev &d, int G, int64_t ncells, int32_t *tmp, int64_t tmp_len,

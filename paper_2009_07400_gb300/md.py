@@ -35,7 +35,7 @@ ABI_SYMBOLS = [
     "md_set_lj", "md_adjoint", "md_energy_sums_static", "md_create_device",
     "md_set_state_device", "md_get_positions_device", "md_get_velocities_device",
     "md_get_forces_device", "md_set_spring_dashpot", "md_set_step",
-    "md_set_adjoint_precision", "md_thermo", "md_adjoint_device",
+    "md_set_adjoint_precision", "md_thermo", "md_adjoint_device", "md_study_force_variant",
 ]
 
 
@@ -138,6 +138,7 @@ def load(path: str | None = None):
                 "md_thermo": [ctx, _D, ctypes.c_int64, ctypes.POINTER(md_thermo_rec)],
                 "md_adjoint_device": [ctx, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, _D,
                                       _D, _D, _P, _P],
+                "md_study_force_variant": [ctx, ctypes.c_int32, ctypes.c_int32, _D, _D],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -444,6 +445,14 @@ class MDContext:
                                                 ctypes.byref(gs), ctypes.c_void_p(g_x0.data_ptr()),
                                                 ctypes.c_void_p(g_v0.data_ptr())))
         return loss.value, ge.value, gs.value, g_x0, g_v0
+
+    def study_force_variant(self, variant, reps=10, forces=False):
+        """md_study_force_variant: (microseconds per launch, forces or None)."""
+        us = ctypes.c_double()
+        F = np.zeros((self.n, 3)) if forces else None
+        self._check(self._lib.md_study_force_variant(self._h, int(variant), int(reps), ctypes.byref(us),
+                                                     F.ctypes.data_as(_D) if forces else None))
+        return us.value, F
 
     def set_adjoint_precision(self, precision):
         """Precision of the reverse sweep's pair terms (MD_FP64 or MD_MIXED)."""
