@@ -1,9 +1,11 @@
 """The bounds-checked build (MD_DEBUG_CHECKS=1) stands in for a memory
 checker: every gathered or stored index of the kernels is checked on the
 device, and a bad one raises an error flag (MD_ERR_STATE) instead of
-touching memory.  Here it runs the main paths with no check firing and must
-agree bit for bit with the normal build on every deterministic path (the
-half-list paths add forces with atomics, so only their completion counts)."""
+touching memory.  Here it runs the main paths (per-atom and group lists,
+replicas, the contact model, the adjoint, the force-kernel studies) with no
+check firing and must agree bit for bit with the normal build on every
+deterministic path (the half-list paths add forces with atomics, so only
+their completion counts)."""
 import os
 import subprocess
 import sys
@@ -55,6 +57,20 @@ for prec in (md.MD_FP64, md.MD_MIXED):
         c.set_spring_dashpot(200.0, 2.0)
         c.run(60)
         out.append(h(c.positions(), c.velocities()))
+# lists shared by groups of atoms (their own build, force kernel and row
+# decode), a batch of replicas with them, and the force-kernel studies
+for g in (2, 4):
+    with md.MDContext(s.pos, s.vel, s.box, precision=md.MD_MIXED, list_type=g) as c:
+        E = c.run(60, energy_every=20)
+        cnt, rows = c.neighbors_raw()
+        out.append(h(c.positions(), c.velocities(), c.forces(), E, cnt))
+with md.MDContext(pos, vel, [r.box for r in reps], counts=[r.n for r in reps],
+                  precision=md.MD_MIXED, list_type=4) as c:
+    c.run(40)
+    out.append(h(c.positions()))
+with md.MDContext(s.pos, s.vel, s.box, precision=md.MD_MIXED, threads_per_atom=1) as c:
+    c.run(20)
+    out.append(h(*[c.study_force_variant(v, 1, forces=True)[1] for v in range(4)]))
 s4 = inputs.fcc_system(4, jitter=0.05, seed=2)
 with md.MDContext(s4.pos, s4.vel, s4.box, precision=md.MD_FP64) as c:
     loss, ge, gs, gx, gv = c.adjoint(20, 10, 10)
@@ -74,5 +90,5 @@ def test_debug_build_agrees_and_stays_silent():
                            timeout=900)
         assert r.returncode == 0, f"{name}: {r.stderr[-3000:]}"
         res[name] = r.stdout.split()
-    assert len(res["release"]) == 10
+    assert len(res["release"]) == 14
     assert res["debug"] == res["release"]
