@@ -347,13 +347,17 @@ int md_set_adjoint_precision(md_ctx *ctx, int32_t precision);
  *      atoms, x0..x3 y0..y3 z0..z3: Sec. 4.2's clustered layout), both with
  *      the library's arithmetic in its order (bitwise the same forces),
  *   3  the 4x4x4-cell neighbourhood of each 2x2x2-cell tile staged in shared
- *      memory in the tile's frame (one block per tile)
+ *      memory in the tile's frame (one block per tile), 4  the same staged by
+ *      TMA bulk copies (one per cell: cells are contiguous ranges of the
+ *      position array) completing on an mbarrier (bitwise variant 3's forces)
  * with forces only (no integration), CUDA events on the context's stream;
  * *us = mean device time per launch in microseconds; forces (may be NULL):
  * host, n x 3 doubles in caller order.  Needs a single-system mixed LJ
  * context with full per-atom lists.
- * Errors: MD_ERR_INVAL, MD_ERR_STATE (wrong kind of context; variant 3: a
- * neighbourhood above 3008 atoms), MD_ERR_NOMEM, MD_ERR_CUDA. */
+ * Errors: MD_ERR_INVAL, MD_ERR_STATE (wrong kind of context; variants 3, 4:
+ * a neighbourhood above 3008 atoms), MD_ERR_TIMEOUT (variant 4: a bulk copy
+ * did not complete within ~10 ms; the kernel returns), MD_ERR_NOMEM,
+ * MD_ERR_CUDA. */
 int md_study_force_variant(md_ctx *ctx, int32_t variant, int32_t reps, double *us, double *forces);
 
 /* Chooses threads_per_atom and the list type by timing each candidate for

@@ -13,6 +13,11 @@
 //      the positions of the tile's 4x4x4-cell neighbourhood in the tile's
 //      frame, and every pair reads its neighbour from there (the entry's
 //      cell offset picks the staged cell; no per-pair offset select).
+//   4  The same with the staging done by the TMA: each staged cell is a
+//      contiguous, 16-byte aligned range of the position array, copied by
+//      one bulk copy (cp.async.bulk) that completes on a shared-memory
+//      mbarrier; the block then shifts the staged positions into the tile
+//      frame in place.  Its forces are bitwise those of variant 3.
 //
 // Variants 1 and 2 evaluate every pair with the library kernel's arithmetic
 // in the same order, so their forces are bitwise those of the library.
@@ -120,18 +125,23 @@ __global__ void __launch_bounds__(256) k_study_gather(Dev d, LJ lj, const float 
 
 constexpr int kTileSlots = 3008;   // staged atoms per block (47 KiB of float4; static shared
                                    // memory stays below 48 KiB with the tables)
+constexpr long long kWaitCycles = 20000000;   // bulk-copy wait limit (~10 ms at 2 GHz)
 
-// Variant 3: block b = 2x2x2-cell tile b of the (single) replica.  Staged
-// cell L = (lx, ly, lz) in [0, 4)^3 is the cell at (2 t + l - 1) per
+// Variants 3 and 4: block b = 2x2x2-cell tile b of the (single) replica.
+// Staged cell L = (lx, ly, lz) in [0, 4)^3 is the cell at (2 t + l - 1) per
 // dimension (periodic), its atoms shifted into the tile frame (origin at the
 // tile's centre): p + (l - 1.5) s.  A pair's staged slot is off[L] + j with
 // L = (the atom's local cell) + (the entry's cell offset).  Returns with the
-// overflow flag raised if a neighbourhood holds more than kTileSlots atoms.
+// overflow flag raised if a neighbourhood holds more than kTileSlots atoms,
+// and (TMA) with the timeout flag if the bulk copies do not complete within
+// kWaitCycles (the block then waits once more, bounded, before it leaves).
+template <bool TMA>
 __global__ void __launch_bounds__(256) k_study_tiles(Dev d, LJ lj, float4 *fout)
 {
-    __shared__ float4 pos[kTileSlots];
+    __shared__ __align__(128) float4 pos[kTileSlots];
     __shared__ int32_t off[64];
     __shared__ int32_t base[65];
+    __shared__ __align__(8) uint64_t bar;
     const Rep &R = d.reps[0];
     const int64_t tile = blockIdx.x;
     const int tz = (int)(tile % R.nt[2]);
@@ -173,14 +183,59 @@ __global__ void __launch_bounds__(256) k_study_tiles(Dev d, LJ lj, float4 *fout)
         if (threadIdx.x == 0) atomicOr(&d.status->flags, FLAG_NL_OVERFLOW);
         return;
     }
-    // stage: every staged slot from its cell, shifted into the tile frame
-    for (int32_t k = threadIdx.x; k < total; k += blockDim.x) {
-        int L = 0;
-        while (base[L + 1] <= k) L++;
-        const int32_t j = off[L] + (k - base[L]);
-        const float4 p = d.p32[j];
-        pos[k] = make_float4(p.x + ((float)(L >> 4) - 1.5f) * s[0], p.y + ((float)((L >> 2) & 3) - 1.5f) * s[1],
-                             p.z + ((float)(L & 3) - 1.5f) * s[2], 0.f);
+    if (TMA) {
+        // one bulk copy per non-empty cell (16-byte aligned source and
+        // destination, 16 bytes per atom), completing on the mbarrier; the
+        // expected byte count is registered before any copy is issued
+        const uint32_t bar_a = (uint32_t)__cvta_generic_to_shared(&bar);
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a),
+                         "r"((uint32_t)total * 16u) : "memory");
+        }
+        __syncthreads();
+        if (threadIdx.x < 64) {
+            const int32_t cnt = base[threadIdx.x + 1] - base[threadIdx.x];
+            if (cnt > 0) {
+                const uint32_t dst = (uint32_t)__cvta_generic_to_shared(pos + base[threadIdx.x]);
+                const float4 *src = d.p32 + off[threadIdx.x];
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                    "l"(src), "r"((uint32_t)cnt * 16u), "r"(bar_a) : "memory");
+            }
+        }
+        auto wait = [&]() {
+            const long long t0 = clock64();
+            uint32_t ok = 0;
+            while (!ok && clock64() - t0 < kWaitCycles)
+                asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+                             : "=r"(ok) : "r"(bar_a) : "memory");
+            return ok != 0;
+        };
+        // every thread waits; the block leaves together if any gave up
+        if (__syncthreads_or(!wait())) {
+            if (threadIdx.x == 0) atomicOr(&d.status->flags, FLAG_TIMEOUT);
+            __syncthreads_or(!wait());      // the copies of this block, once more
+            return;
+        }
+        for (int32_t k = threadIdx.x; k < total; k += blockDim.x) {
+            int L = 0;
+            while (base[L + 1] <= k) L++;
+            const float4 p = pos[k];
+            pos[k] = make_float4(p.x + ((float)(L >> 4) - 1.5f) * s[0], p.y + ((float)((L >> 2) & 3) - 1.5f) * s[1],
+                                 p.z + ((float)(L & 3) - 1.5f) * s[2], 0.f);
+        }
+    } else {
+        // stage: every staged slot from its cell, shifted into the tile frame
+        for (int32_t k = threadIdx.x; k < total; k += blockDim.x) {
+            int L = 0;
+            while (base[L + 1] <= k) L++;
+            const int32_t j = off[L] + (k - base[L]);
+            const float4 p = d.p32[j];
+            pos[k] = make_float4(p.x + ((float)(L >> 4) - 1.5f) * s[0], p.y + ((float)((L >> 2) & 3) - 1.5f) * s[1],
+                                 p.z + ((float)(L & 3) - 1.5f) * s[2], 0.f);
+        }
     }
     __syncthreads();
     if (threadIdx.x < 64) off[threadIdx.x] = base[threadIdx.x] - off[threadIdx.x];   // slot = off[L] + j
@@ -260,11 +315,12 @@ int launch_study_force(const Dev &d, const LJ &lj, int variant, float *layouts, 
     return (int)cudaGetLastError();
 }
 
-int launch_study_tiles(const Dev &d, const LJ &lj, int64_t ntiles, float4 *fout, cudaStream_t st,
-                       int *nl)
+int launch_study_tiles(const Dev &d, const LJ &lj, int64_t ntiles, bool tma, float4 *fout,
+                       cudaStream_t st, int *nl)
 {
     if (d.n <= 0 || d.nrep != 1 || ntiles <= 0) return -1;
-    k_study_tiles<<<(unsigned)ntiles, 256, 0, st>>>(d, lj, fout);
+    if (tma) k_study_tiles<true><<<(unsigned)ntiles, 256, 0, st>>>(d, lj, fout);
+    else k_study_tiles<false><<<(unsigned)ntiles, 256, 0, st>>>(d, lj, fout);
     *nl += 1;
     return (int)cudaGetLastError();
 }

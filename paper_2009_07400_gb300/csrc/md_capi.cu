@@ -1547,10 +1547,10 @@ int md_adjoint_device(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt, d
 
 int md_study_force_variant(md_ctx *c, int32_t variant, int32_t reps, double *us, double *forces)
 {
-    if (!c || !us || reps < 1 || variant < 0 || variant > 3) return fail(c, MD_ERR_INVAL, "bad argument");
+    if (!c || !us || reps < 1 || variant < 0 || variant > 4) return fail(c, MD_ERR_INVAL, "bad argument");
     if (!is_mixed(c) || c->p.list_type != MD_LIST_FULL || is_sd(c) || c->nrep != 1)
         return fail(c, MD_ERR_STATE, "force studies take a single-system mixed LJ context with full lists");
-    if (variant == 3 && kTile != 2)
+    if (variant >= 3 && kTile != 2)
         return fail(c, MD_ERR_STATE, "the shared-memory study stages 2x2x2-cell tiles (a build with MD_CELL_TILE = 2)");
     int rc = ensure_list(c);
     if (rc) return rc;
@@ -1566,7 +1566,7 @@ int md_study_force_variant(md_ctx *c, int32_t variant, int32_t reps, double *us,
     int nl = 0;
     auto launch = [&]() -> int {
         if (variant == 0) return launch_force(d, c->lj, MD_MIXED, false, 1, EPI_F, false, false, c->st, &nl);
-        if (variant == 3) return launch_study_tiles(d, c->lj, ntiles, fout, c->st, &nl);
+        if (variant >= 3) return launch_study_tiles(d, c->lj, ntiles, variant == 4, fout, c->st, &nl);
         return launch_study_force(d, c->lj, variant, lay, fout, c->st, &nl);
     };
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1584,9 +1584,11 @@ int md_study_force_variant(md_ctx *c, int32_t variant, int32_t reps, double *us,
     if (e == cudaSuccess) {
         *us = 1e3 * (double)ms / reps;
         DevStatus st;
-        if (!(rc = read_status(c, &st)) && (st.flags & FLAG_NL_OVERFLOW)) {
+        if (!(rc = read_status(c, &st)) && (st.flags & (FLAG_NL_OVERFLOW | FLAG_TIMEOUT))) {
             CK(cudaMemsetAsync(&c->status->flags, 0, sizeof(int32_t), c->st));
-            rc = fail(c, MD_ERR_STATE, "a tile neighbourhood holds more atoms than the staging array");
+            rc = (st.flags & FLAG_TIMEOUT)
+                     ? fail(c, MD_ERR_TIMEOUT, "a bulk copy into shared memory did not complete in time")
+                     : fail(c, MD_ERR_STATE, "a tile neighbourhood holds more atoms than the staging array");
         }
         if (!rc && forces) {
             nl = 0;

@@ -53,7 +53,10 @@ constexpr int kMaxNc = 1023;        // cell coordinates are packed in 10 bits ea
 
 // Bits of the device error word.  Every kernel returns immediately while it
 // is non-zero, so the state freezes at the first failure.
-enum : int32_t { FLAG_NL_OVERFLOW = 1, FLAG_NONFINITE = 2, FLAG_BADPOS = 4, FLAG_BOUNDS = 8 };
+enum : int32_t {
+    FLAG_NL_OVERFLOW = 1, FLAG_NONFINITE = 2, FLAG_BADPOS = 4, FLAG_BOUNDS = 8,
+    FLAG_TIMEOUT = 16   // a bounded device wait gave up
+};
 
 // Bounds checks of the debug build (MD_DEBUG_CHECKS=1): MD_CHECK(d, cond) is
 // true when cond holds; otherwise it raises FLAG_BOUNDS and is false, and
@@ -360,13 +363,14 @@ int launch_rebuild_check(const Dev &d, cudaGraphConditionalHandle h, cudaStream_
 int64_t scan_tmp_elems(int64_t ncells_total);
 
 // Force-kernel studies (k_study.cu): variants 1 (SoA gathers) and 2 (AoSoA
-// gathers) into fout; variant 3 (neighbourhood staged in shared memory, one
-// block per 2x2x2-cell tile).  Single replica, mixed path, full lists.
+// gathers) into fout; variants 3 and 4 (neighbourhood staged in shared
+// memory by plain loads / by TMA bulk copies, one block per 2x2x2-cell
+// tile).  Single replica, mixed path, full lists.
 int64_t study_layout_floats(int64_t n);
 int launch_study_force(const Dev &d, const LJ &lj, int variant, float *layouts, float4 *fout,
                        cudaStream_t st, int *nlaunch);
-int launch_study_tiles(const Dev &d, const LJ &lj, int64_t ntiles, float4 *fout, cudaStream_t st,
-                       int *nlaunch);
+int launch_study_tiles(const Dev &d, const LJ &lj, int64_t ntiles, bool tma, float4 *fout,
+                       cudaStream_t st, int *nlaunch);
 
 // Lists shared by groups of G atoms (k_bin.cu, k_build.cu, k_force.cu, k_misc.cu)
 int launch_group_table(const Dev &d, int G, int64_t ncells, int32_t *tmp, int64_t tmp_len,

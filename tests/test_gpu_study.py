@@ -2,7 +2,8 @@
 compare with the library's kernel compute the same forces.  SoA and AoSoA
 gathers run the library's arithmetic in its order (bitwise equal forces); the
 shared-memory tile variant rounds differently (tile frame) and is held to
-the mixed path's tolerance against the oracle."""
+the mixed path's tolerance against the oracle; staged by TMA bulk copies
+instead of loads it gives the same bits."""
 import numpy as np
 import pytest
 
@@ -52,6 +53,8 @@ def test_study_variants_agree(md, orc, case):
             assert us > 0 and np.array_equal(F, F0)
         _, F3 = ctx.study_force_variant(3, 2, forces=True)
         assert rms_rel(F3, Fr) <= 1e-5
+        _, F4 = ctx.study_force_variant(4, 2, forces=True)      # staged by TMA bulk copies
+        assert np.array_equal(F4, F3)
         assert np.array_equal(ctx.forces(), F_lib)        # the context's state is untouched
 
 
@@ -67,5 +70,5 @@ def test_study_rejects_other_contexts(md, orc):
         assert e.value.code == md.MD_ERR_STATE
     with md.MDContext(s.pos, s.vel, s.box, precision=md.MD_MIXED) as ctx:
         with pytest.raises(md.MDError) as e:
-            ctx.study_force_variant(4, 1)
+            ctx.study_force_variant(5, 1)
         assert e.value.code == md.MD_ERR_INVAL
