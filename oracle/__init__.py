@@ -85,6 +85,9 @@ def _load():
                 "orc_energy_list": (None, [ctypes.c_int64, _D, _D, ctypes.c_int32, _I32, _I32, P,
                                            _D, _D, _D]),
                 "orc_kinetic": (ctypes.c_double, [ctypes.c_int64, _D, ctypes.c_double]),
+                "orc_neighbors_sample": (ctypes.c_int32, [ctypes.c_int64, _D, _D, _I32, _I32, _I32,
+                                                          _I32, ctypes.c_double, ctypes.c_int64,
+                                                          _I64, ctypes.c_int32, _I32, _I32]),
                 "orc_thermo": (None, [ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_int64, ctypes.c_double, _D]),
                 "orc_forces_sd_list": (None, [ctypes.c_int64, _D, _D, _D, ctypes.c_int32, _I32,
@@ -231,6 +234,23 @@ def neighbors_cells_raw(x, L, r, half=False, cap=128):
         if m <= cap:
             return counts, lst.reshape(n, cap)
         cap = m + 16
+
+
+def neighbors_sample(x, L, r, ids, cap=256):
+    """(counts[m], rows[m, cap]) of the full Verlet rows of the atoms `ids`
+    (x is wrapped first), by the cell list of neighbors_cells."""
+    xw = wrap(x, L)
+    cell_of, start, atoms = bin_cells(xw, L, r)
+    nc, _ = cell_grid(L, r)
+    ids = np.ascontiguousarray(ids, dtype=np.int64)
+    counts = np.zeros(ids.shape[0], np.int32)
+    rows = np.zeros((ids.shape[0], cap), np.int32)
+    m = _load().orc_neighbors_sample(xw.shape[0], _dp(xw), _dp(_box(L)), _ip(nc), _ip(cell_of),
+                                     _ip(start), _ip(atoms), float(r), ids.shape[0],
+                                     ids.ctypes.data_as(_I64), cap, _ip(counts), _ip(rows))
+    if m > cap:
+        raise RuntimeError(f"a row of {m} exceeds cap {cap}")
+    return counts, rows
 
 
 def _pack(rows):

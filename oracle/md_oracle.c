@@ -281,6 +281,45 @@ int32_t orc_neighbors_cells(int64_t n, const double *x, const double L[3], const
     return maxc;
 }
 
+/* Full Verlet rows of the m atoms ids[] only (the criterion and candidate
+ * order of orc_neighbors_cells), for checks on systems too large to list
+ * whole: counts[q] and list[q * cap ...] for atom ids[q]; returns the
+ * longest row. */
+int32_t orc_neighbors_sample(int64_t n, const double *x, const double L[3], const int32_t nc[3],
+                             const int32_t *cell_of, const int32_t *cell_start,
+                             const int32_t *cell_atoms, double r, int64_t m, const int64_t *ids,
+                             int32_t cap, int32_t *counts, int32_t *list)
+{
+    double r2 = r * r;
+    int32_t maxc = 0;
+    (void)n;
+#pragma omp parallel for schedule(dynamic, 16) reduction(max : maxc)
+    for (int64_t q = 0; q < m; q++) {
+        int64_t i = ids[q];
+        int32_t ci = cell_of[i];
+        int32_t cz = ci % nc[2];
+        int32_t cy = (ci / nc[2]) % nc[1];
+        int32_t cx = ci / (nc[2] * nc[1]);
+        int64_t cells[27];
+        int mc = neighbour_cells(cx, cy, cz, nc, cells);
+        int32_t k = 0;
+        for (int c = 0; c < mc; c++)
+            for (int32_t t = cell_start[cells[c]]; t < cell_start[cells[c] + 1]; t++) {
+                int64_t j = cell_atoms[t];
+                if (j == i) continue;
+                double del[3];
+                displacement(x, i, j, L, del);
+                if (norm2(del) < r2) {
+                    if (k < cap) list[q * cap + k] = (int32_t)j;
+                    k++;
+                }
+            }
+        counts[q] = k;
+        if (k > maxc) maxc = k;
+    }
+    return maxc;
+}
+
 /* ---------------------------------------------------------------------------
  * Pair terms (Sec. 3.2 Eq. 2 in the operation order of the Sec. 4.2 kernel).
  * ------------------------------------------------------------------------- */

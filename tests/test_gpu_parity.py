@@ -402,6 +402,31 @@ def test_full_size(md, orc, precision):
             assert rms_rel(F, Fr) <= 1e-5
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_sizing_8m(md, orc, precision):
+    """The largest workload (FCC 128^3, 8,388,608 atoms, the sizing run),
+    after one graph-replayed rebuild cycle: the rows of 4096 sampled atoms
+    bit-exact against the oracle's cell list, their forces within the
+    path's tolerance, and every row length equal to the oracle's for those
+    atoms."""
+    s = inputs.workload("fcc128_8388608")
+    prec = md.MD_FP64 if precision == "fp64" else md.MD_MIXED
+    with ctx_of(md, s, precision=prec) as ctx:
+        ctx.run(20)
+        x = ctx.positions()
+        counts, rows = ctx.neighbors_raw()
+        F = ctx.forces()
+    ids = np.random.default_rng(8).choice(s.n, 4096, replace=False)
+    c_o, r_o = orc.neighbors_sample(x, s.box, RC + SKIN, ids, cap=rows.shape[1])
+    assert np.array_equal(counts[ids], c_o)
+    assert np.array_equal(sorted_rows(counts[ids], rows[ids]), sorted_rows(c_o, r_o))
+    Fr = orc.forces_sample(x, s.box, ids)
+    if prec == md.MD_FP64:
+        assert fp64_force_ok(F[ids], Fr) <= 1e-10
+    else:
+        assert rms_rel(F[ids], Fr) <= 1e-5
+
+
 def test_paper_gpu_shape_80(md, orc):
     """The paper's single-GPU workload shape (Sec. 6: FCC 80^3 unit cells,
     2,048,000 atoms, FP64, full lists, one thread per atom), after one

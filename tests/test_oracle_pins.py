@@ -198,6 +198,20 @@ def test_cells_equal_brute(orc, L, n, half):
         assert set(pairs_half) == pairs_full
 
 
+def test_neighbors_sample_equals_full_rows(orc):
+    """The sampled rows are the full cell-list rows of those atoms, in the
+    same order (nc = 2 de-duplication included)."""
+    for L, n in (((5.7, 5.7, 5.7), 150), ((12.0, 8.5, 11.3), 700)):
+        s = inputs.uniform_box(n, L, seed=11)
+        x = orc.wrap(s.pos, s.box)
+        c_all, r_all = orc.neighbors_cells_raw(x, s.box, RC + SKIN)
+        ids = np.random.default_rng(2).choice(n, 40, replace=False)
+        c_s, r_s = orc.neighbors_sample(x, s.box, RC + SKIN, ids, cap=r_all.shape[1])
+        assert np.array_equal(c_s, c_all[ids])
+        for q, i in enumerate(ids):
+            assert np.array_equal(r_s[q, :c_s[q]], r_all[i, :c_all[i]])
+
+
 def test_binning(orc):
     L = np.array([9.0, 11.0, 13.0])
     s = inputs.uniform_box(600, L, seed=2)
