@@ -277,6 +277,7 @@ def run_gpu(args):
             tuned = ctx.autotune(STEPS_PER_CYCLE)
             res["tuned"] = {"threads_per_atom": tuned.threads_per_atom,
                             "list_type": int(tuned.list_type)}
+        res["tuned"]["cell_split"] = int(ctx.info().cell_split)
         with ClockSampler(local) as clk:
             ms, launches = time_cycles(ctx, args.steps, args.warmup, dist, torch)
         res["mixed_ms"] = ms
@@ -289,6 +290,7 @@ def run_gpu(args):
     with make(precision=md.MD_MIXED, rebuild_every=0,
               threads_per_atom=res["tuned"]["threads_per_atom"],
               list_type=res["tuned"]["list_type"]) as ctx:
+        ctx.set_cell_split(res["tuned"]["cell_split"])
         disp_cycles = max(1, min(args.steps, 5))
         r0 = ctx.info().rebuilds
         ms_d, _ = time_cycles(ctx, disp_cycles, 1, dist, torch, timesteps=STEPS_PER_CYCLE)
@@ -802,7 +804,11 @@ def run_study(args):
       * list types: the per-atom full list against lists shared by groups of
         2 and 4 atoms (md_profile per phase);
       * cell orders: libraries built with cell tiles of 1 (z fastest), 2 (the
-        library's) and 4 cells per edge, each timed in its own process.
+        library's) and 4 cells per edge, each timed in its own process;
+      * cell size of the list build: whole cells (the library's default)
+        against cells split into octants (md_set_cell_split), on this
+        workload and on the 256-replica ensemble (small boxes, cells up to
+        ~1.3 rc + skin).
     Prints one JSON line."""
     import torch
 
@@ -838,6 +844,24 @@ def run_study(args):
                          "neigh_us_per_step": 1e3 * p.neigh_ms / p.steps,
                          "list_entries_per_atom": p.mean_neighbors,
                          "step_us": 1e3 * ms / (2 * TIMESTEPS_PER_STEP)}
+    splits = {}
+    ens = inputs.replica_ensemble(256, seed=1004)
+    systems = {WORKLOAD: (s.pos, s.vel, s.box, None),
+               "ensemble256": (np.concatenate([r.pos for r in ens]), np.concatenate([r.vel for r in ens]),
+                               [r.box for r in ens], [r.n for r in ens])}
+    for wname, (pos, vel, box, counts) in systems.items():
+        splits[wname] = {}
+        with md.MDContext(pos, vel, box, counts=counts, stream=stream.cuda_stream,
+                          precision=md.MD_MIXED, list_type=0, threads_per_atom=1) as ctx:
+            for split in (0, 1):
+                ctx.set_cell_split(split)
+                ctx.run(2 * STEPS_PER_CYCLE)
+                p = ctx.profile(4 * STEPS_PER_CYCLE)
+                ms, _ = time_cycles(ctx, 2, 1, None, torch)
+                splits[wname]["octants" if split else "whole cells (library)"] = {
+                    "neigh_us_per_step": 1e3 * p.neigh_ms / p.steps,
+                    "force_us": 1e3 * p.force_ms / p.steps,
+                    "step_us": 1e3 * ms / (2 * TIMESTEPS_PER_STEP)}
     orders = {}
     for tile in (1, 2, 4):
         r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cellorder-child", str(tile)],
@@ -854,6 +878,7 @@ def run_study(args):
             "force_kernel_variants": variants, "list_types": lists,
             "cell_orders": {f"tiles of {t} cells per edge" + (" (library)" if t == 2 else ""): o
                             for t, o in orders.items()},
+            "cell_split": splits,
             "timing": "CUDA events on the context's stream; variants: best of 3 runs of "
                       f"{reps} launches each"}
     print(json.dumps(line), flush=True)

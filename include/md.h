@@ -115,6 +115,8 @@ typedef struct {
     int64_t step;            /* steps taken by md_run / md_integrate(2)             */
     int64_t kernel_launches; /* kernels this context launched (graph nodes counted) */
     int64_t rebuilds;        /* list builds done                                    */
+    int32_t cell_split;      /* 1: the list build scans half-size cells (see
+                                md_set_cell_split)                              */
 } md_info;
 
 /* Per-phase device time of md_profile (Force / Neigh / Other, the
@@ -361,10 +363,30 @@ int md_set_adjoint_precision(md_ctx *ctx, int32_t precision);
 int md_study_force_variant(md_ctx *ctx, int32_t variant, int32_t reps, double *us, double *forces);
 
 /* Chooses threads_per_atom and the list type by timing each candidate for
- * `steps` steps on the context's own state (which it restores), keeps the
- * fastest and reports it in *chosen (may be NULL).  Results are cached per
- * (precision, atoms-per-replica bucket) for the life of the process. */
+ * `steps` steps on the context's own state (which it restores), then the
+ * winner with the other cell split (md_set_cell_split), keeps the fastest and
+ * reports it in *chosen (may be NULL; the split in md_info.cell_split).
+ * Results are cached per (precision, atoms-per-replica bucket) for the life
+ * of the process. */
 int md_autotune(md_ctx *ctx, int32_t steps, md_params *chosen);
+
+/* Cell size of the list build (Sec. 3.2, Fig. 1: cells of side at least
+ * rc + skin; smaller cells with a wider stencil also find every pair).
+ * split = 1: the binning orders each cell's atoms by octant, i.e. by the
+ * half-size cells, and the build scans, in each of the 27 neighbour cells,
+ * only the octants that can hold a pair within rc + skin of the atom: the far
+ * half of a face-adjacent cell lies at least s beyond the near side of the
+ * atom's own cell (s >= rc + skin), so it is skipped for atoms on that near
+ * side (with a margin of 1e-3 s for the FP32 half decisions).  The lists hold
+ * the same pairs with either split (only the order of a cell's entries, and
+ * so the rounding of the force sums, changes).  split = 0: whole cells.
+ * Default: 0 (on the 1M-atom LJ liquid split cells take 63 against 44 us of
+ * neighbour work per step: lanes of a warp keep different octants, and the
+ * warp scans the union of their runs).  A change rebins, rebuilds the list
+ * and recomputes the forces of the current state.
+ * Not in the paper as an option; its cells are the split = 0 ones.
+ * Errors: MD_ERR_INVAL (split not 0 or 1), MD_ERR_CUDA. */
+int md_set_cell_split(md_ctx *ctx, int32_t split);
 
 /* Allocation-free FP64 totals: out3[0] = sum pe_atom, out3[1] = 1/2 mass
  * sum |v|^2, out3[2] = sum w_atom, for callers that cannot allocate device

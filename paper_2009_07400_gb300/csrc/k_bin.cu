@@ -5,18 +5,22 @@
 //   1. k_bin_assign   one thread per atom: wrap x into the box (one
 //                     conditional +/-L per component, written back only
 //                     when it changed), cell = (int)(x/s) clamped to nc-1,
-//                     histogram with one atomicAdd per distinct cell of a
-//                     warp.
+//                     and with split cells the octant of the atom in its
+//                     cell (which half along each axis: the half-size cells
+//                     of Sec. 3.2, which the list build scans); histogram of
+//                     the keys (cell, or cell and octant) with one atomicAdd
+//                     per distinct key of a warp.
 //   2. scan           exclusive prefix sum of the histogram (three kernels,
 //                     4096 cells per 1024-thread block, warp shuffles).
 //   3. k_bin_scatter  one thread per atom: slot = start + count - 1 - rank,
 //                     count taken down by one atomicSub per distinct cell of
 //                     a warp (leaves the histogram at zero for the next
 //                     binning).
-//   4. k_sort_gather  a group of 32, 16, 8 or 4 lanes per cell (from the
-//                     mean occupancy): rank the cell's members by caller
-//                     id (so the order is the stable (cell, id) order,
-//                     independent of atomic arrival order) and gather x, v,
+//   4. k_sort_gather  a group of 32, 16, 8 or 4 lanes per key (from the
+//                     mean occupancy): rank the key's members by caller
+//                     id (so the order is the stable (cell, id) order, or
+//                     (cell, octant, id) with split cells, independent of
+//                     atomic arrival order) and gather x, v,
 //                     id into the reordered buffers; also writes the
 //                     cell-relative FP32 position p = fl32(x - C_cell) and
 //                     the packed cell coordinates used by the mixed path.
@@ -44,6 +48,7 @@ __global__ void __launch_bounds__(256) k_bin_assign(Dev d)
     const dvec4 x = d.x[a];
     double c[3] = {x.x, x.y, x.z};
     int32_t k[3];
+    uint32_t oct = 0;
     int32_t bad = 0;
     bool moved = false;
     for (int q = 0; q < 3; q++) {
@@ -76,14 +81,19 @@ __global__ void __launch_bounds__(256) k_bin_assign(Dev d)
         const float fr = y - (float)kk;
         if (fr < 1e-3f || fr > 1.0f - 1e-3f) kk = (int32_t)(u / R.s[q]);
         k[q] = kk >= R.nc[q] ? R.nc[q] - 1 : kk;
+        // octant bit: the upper half of the cell along q.  y - k is the
+        // position in the cell in cell units, within 2e-4 of u/s - k (the
+        // list build allows 1e-3 for it); for the last cell it can reach 1
+        oct = (oct << 1) | (uint32_t)(y - (float)k[q] >= 0.5f);
     }
     if (bad) atomicOr(&d.status->flags, bad);
     if (moved) d.x[a] = mk_dvec4(c[0], c[1], c[2], 0.0);
-    int32_t key = (int32_t)cell_id(R, k[0], k[1], k[2]);
-    if (!MD_CHECK(d, key >= 0 && key < d.ncells)) return;
+    int32_t key = (int32_t)key_of(d, cell_id(R, k[0], k[1], k[2]));
+    if (d.split) key |= (int32_t)oct;
+    if (!MD_CHECK(d, key >= 0 && key < nkeys(d))) return;
     d.cell_key[a] = key;
-    // atoms arrive roughly in cell order, so lanes of a warp share cells:
-    // one atomic per distinct cell of the warp
+    // atoms arrive roughly in cell order, so lanes of a warp share keys:
+    // one atomic per distinct key of the warp
     const unsigned same = __match_any_sync(__activemask(), key);
     if ((threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&d.cell_count[key], __popc(same));
 }
@@ -178,10 +188,10 @@ __global__ void __launch_bounds__(256) k_bin_scatter(Dev d)
     int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= d.n) return;
     int32_t key = d.cell_key[a];
-    if (!MD_CHECK(d, key >= 0 && key < d.ncells)) return;
-    // one atomic per distinct cell of the warp (atoms arrive roughly in cell
-    // order); the slots inside a cell are re-ranked by id afterwards, so
-    // their order here does not matter
+    if (!MD_CHECK(d, key >= 0 && key < nkeys(d))) return;
+    // one atomic per distinct key of the warp (atoms arrive roughly in cell
+    // order); the slots of a key are re-ranked by id afterwards, so their
+    // order here does not matter
     const unsigned same = __match_any_sync(__activemask(), key);
     const int leader = __ffs(same) - 1;
     int32_t top = 0;
@@ -193,21 +203,21 @@ __global__ void __launch_bounds__(256) k_bin_scatter(Dev d)
     d.perm[pos] = (int32_t)a;
 }
 
-// G lanes per cell (G = 32, 16, 8 or 4, chosen from the mean cell
+// G lanes per key (G = 32, 16, 8 or 4, chosen from the mean key
 // occupancy, so that small cells do not leave most of a warp idle): rank
-// each cell's members by caller id with shuffles inside the group, gather
+// each key's members by caller id with shuffles inside the group, gather
 // into the new order.  All 32 lanes run the same number of loop trips (the
-// warp's largest cell), so every shuffle has the whole warp converged.
+// warp's largest key), so every shuffle has the whole warp converged.
 template <int G, bool BATCHED>
-__global__ void __launch_bounds__(256) k_sort_gather(Dev d, int64_t ncells)
+__global__ void __launch_bounds__(256) k_sort_gather(Dev d, int64_t nk)
 {
     if (stopped(d.status)) return;
     const int gl = threadIdx.x % G;
-    const int64_t cell = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int64_t key = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
     int32_t start = 0, m = 0;
-    if (cell < ncells) {
-        start = d.cell_start[cell];
-        m = d.cell_start[cell + 1] - start;
+    if (key < nk) {
+        start = d.cell_start[key];
+        m = d.cell_start[key + 1] - start;
         if (!MD_CHECK(d, start >= 0 && m >= 0 && start + m <= d.n)) m = 0;
     }
     int32_t mmax = m;
@@ -235,7 +245,7 @@ __global__ void __launch_bounds__(256) k_sort_gather(Dev d, int64_t ncells)
         if (d.v32) d.v32[ns] = make_float4(f32_of_f64(v.x), f32_of_f64(v.y), f32_of_f64(v.z), 0.f);
         const Rep &R = d.reps[BATCHED ? d.rep_of[ns] : 0];
         int cx, cy, cz;
-        cell_coords(R, cell, cx, cy, cz);
+        cell_coords(R, key >> (3 * d.split), cx, cy, cz);
         // centres (c + 0.5) s from the table the force epilogue uses, so
         // both compute p = fl32(x - C) from the same C
         const double *ct = d.ctr + R.ctr_off;
@@ -254,7 +264,7 @@ __global__ void __launch_bounds__(256) k_group_count(Dev d, int64_t ncells, int 
     if (stopped(d.status)) return;
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncells) return;
-    const int32_t m = d.cell_start[c + 1] - d.cell_start[c];
+    const int32_t m = d.cell_start[key_of(d, c + 1)] - d.cell_start[key_of(d, c)];
     d.gcnt[c] = (m + G - 1) / G;
 }
 
@@ -266,8 +276,8 @@ __global__ void __launch_bounds__(256) k_group_fill(Dev d, int64_t ncells, int G
     if (stopped(d.status)) return;
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncells) return;
-    const int32_t start = d.cell_start[c];
-    const int32_t m = d.cell_start[c + 1] - start;
+    const int32_t start = d.cell_start[key_of(d, c)];
+    const int32_t m = d.cell_start[key_of(d, c + 1)] - start;
     const int32_t g0 = d.gcell_start[c];
     for (int32_t k = 0; k * G < m; k++) {
         const int32_t size = min(G, m - k * G);
@@ -277,45 +287,46 @@ __global__ void __launch_bounds__(256) k_group_fill(Dev d, int64_t ncells, int G
 }
 
 template <int G>
-void launch_sort_gather(const Dev &d, int64_t ncells, cudaStream_t st)
+void launch_sort_gather(const Dev &d, int64_t nk, cudaStream_t st)
 {
-    const unsigned gs = (unsigned)((ncells * G + 255) / 256);
-    if (d.nrep > 1) k_sort_gather<G, true><<<gs, 256, 0, st>>>(d, ncells);
-    else k_sort_gather<G, false><<<gs, 256, 0, st>>>(d, ncells);
+    const unsigned gs = (unsigned)((nk * G + 255) / 256);
+    if (d.nrep > 1) k_sort_gather<G, true><<<gs, 256, 0, st>>>(d, nk);
+    else k_sort_gather<G, false><<<gs, 256, 0, st>>>(d, nk);
 }
 
 inline unsigned blocks_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
 
 }  // namespace
 
-int64_t scan_tmp_elems(int64_t ncells_total)
+int64_t scan_tmp_elems(int64_t nkeys_total)
 {
-    return (ncells_total + kScanPer - 1) / kScanPer + 1;
+    return (nkeys_total + kScanPer - 1) / kScanPer + 1;
 }
 
 // Bins the atoms of d (all replicas).  On return the reordered state is in
 // d.x_alt / d.v_alt / d.id_alt and d.p32 (the caller swaps the pointers).
-int launch_bin(const Dev &d, int64_t ncells, int32_t *tmp, int64_t tmp_len, cudaStream_t st,
-               int *nl)
+int launch_bin(const Dev &d, int32_t *tmp, int64_t tmp_len, cudaStream_t st, int *nl)
 {
     if (d.n <= 0) return 0;
     const bool batched = d.nrep > 1;
+    const int64_t nk = nkeys(d);
     unsigned gb = blocks_for(d.n, 256);
     if (batched) k_bin_assign<true><<<gb, 256, 0, st>>>(d);
     else k_bin_assign<false><<<gb, 256, 0, st>>>(d);
-    int64_t nb = (ncells + kScanPer - 1) / kScanPer;
+    int64_t nb = (nk + kScanPer - 1) / kScanPer;
     if (nb + 1 > tmp_len) return -1;
-    k_scan_block<<<(unsigned)nb, 1024, 0, st>>>(d.cell_count, d.cell_start, ncells, tmp);
-    k_scan_tops<<<1, 1024, 0, st>>>(tmp, nb, d.cell_start, ncells);
-    k_scan_add<<<(unsigned)nb, 1024, 0, st>>>(d.cell_start, ncells, tmp);
+    k_scan_block<<<(unsigned)nb, 1024, 0, st>>>(d.cell_count, d.cell_start, nk, tmp);
+    k_scan_tops<<<1, 1024, 0, st>>>(tmp, nb, d.cell_start, nk);
+    k_scan_add<<<(unsigned)nb, 1024, 0, st>>>(d.cell_start, nk, tmp);
     k_bin_scatter<<<gb, 256, 0, st>>>(d);
-    // lanes per cell from the mean occupancy (about 19 atoms at the LJ
-    // benchmark's density, about 3 for dense granular packings)
-    const int64_t mean = d.n / (ncells > 0 ? ncells : 1);
-    if (mean >= 12) launch_sort_gather<32>(d, ncells, st);
-    else if (mean >= 6) launch_sort_gather<16>(d, ncells, st);
-    else if (mean >= 3) launch_sort_gather<8>(d, ncells, st);
-    else launch_sort_gather<4>(d, ncells, st);
+    // lanes per key from the mean occupancy (about 19 atoms per cell at the
+    // LJ benchmark's density, 2.4 per octant; about 3 per cell for dense
+    // granular packings)
+    const int64_t mean = d.n / (nk > 0 ? nk : 1);
+    if (mean >= 12) launch_sort_gather<32>(d, nk, st);
+    else if (mean >= 6) launch_sort_gather<16>(d, nk, st);
+    else if (mean >= 3) launch_sort_gather<8>(d, nk, st);
+    else launch_sort_gather<4>(d, nk, st);
     *nl += 6;
     return (int)cudaGetLastError();
 }

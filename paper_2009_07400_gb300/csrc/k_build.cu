@@ -76,8 +76,9 @@ __device__ __forceinline__ bool owns(const Dev &d, const LJ &lj, int64_t i, int3
 }
 
 // Builds row i; returns its length (rows longer than the capacity are
-// counted in full but stored only up to the capacity).
-template <bool BATCHED, bool HALF>
+// counted in full but stored only up to the capacity).  SPLIT: the binning
+// ordered each cell's atoms by octant (the context's cell split).
+template <bool BATCHED, bool HALF, bool SPLIT>
 __device__ __forceinline__ int32_t build_row(const Dev &d, const LJ &lj, int64_t i)
 {
     const Rep &R = d.reps[BATCHED ? d.rep_of[i] : 0];
@@ -96,24 +97,46 @@ __device__ __forceinline__ int32_t build_row(const Dev &d, const LJ &lj, int64_t
     const int64_t wstep = 4 * n - 3;      // from entry 4q+3 to entry 4q+4
     bool have_xi = false;
     dvec4 xi = mk_dvec4(0, 0, 0, 0);
+    // Split cells: the octants of neighbour cell o that can hold a neighbour
+    // (octant bits 4 hx + 2 hy + hz).  Along an axis with o = +1 the upper
+    // half lies at least s (1 - 2e-4) - p beyond the atom (binned halves are
+    // exact to 2e-4 cell units), so it is skipped when p <= s - rs - 1e-3 s;
+    // likewise the lower half of the o = -1 cell when p >= -(s - rs - 1e-3 s).
+    // far: bit 2a set = skip the upper half of the o = +1 cell along axis a,
+    // bit 2a + 1 = skip the lower half of the o = -1 cell.
+    uint32_t far = 0;
+    {
+        const float pc[3] = {pi.x, pi.y, pi.z};
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+            far |= ((uint32_t)(pc[a] <= R.splitf[a]) << (2 * a)) |
+                   ((uint32_t)(pc[a] >= -R.splitf[a]) << (2 * a + 1));
+    }
+    // octants kept along axis a (lower-half octants `lo`) in neighbour cell o
+    auto keep = [&](int a, int o, uint32_t lo) -> uint32_t {
+        const uint32_t up = 0xFFu & ~lo;
+        if (o > 0) return lo | (((far >> (2 * a)) & 1u) ? 0u : up);
+        if (o < 0) return up | (((far >> (2 * a + 1)) & 1u) ? 0u : lo);
+        return 0xFFu;
+    };
 
     for (int ox = -1; ox <= 1; ox++) {
         int ux = ci[0] + ox, kx = 0;
         if (ux < 0) { ux += R.nc[0]; kx = -1; } else if (ux >= R.nc[0]) { ux -= R.nc[0]; kx = 1; }
         const float qx = pi.x + (float)ox * R.nsf[0];
+        const uint32_t kx8 = keep(0, ox, 0x0Fu);
         for (int oy = -1; oy <= 1; oy++) {
             int uy = ci[1] + oy, ky = 0;
             if (uy < 0) { uy += R.nc[1]; ky = -1; } else if (uy >= R.nc[1]) { uy -= R.nc[1]; ky = 1; }
             const float qy = pi.y + (float)oy * R.nsf[1];
             const int32_t col = (int32_t)cell_id(R, ux, uy, 0);
+            const uint32_t kxy8 = kx8 & keep(1, oy, 0x33u);
             for (int oz = -1; oz <= 1; oz++) {
                 int uz = ci[2] + oz, kz = 0;
                 if (uz < 0) { uz += R.nc[2]; kz = -1; } else if (uz >= R.nc[2]) { uz -= R.nc[2]; kz = 1; }
                 const float qz = pi.z + (float)oz * R.nsf[2];
                 const int32_t cid = cell_id_z(col, uz);
                 if (!MD_CHECK(d, cid >= 0 && cid < d.ncells)) continue;
-                const int32_t j0 = d.cell_start[cid], j1 = d.cell_start[cid + 1];
-                if (!MD_CHECK(d, j0 >= 0 && j0 <= j1 && j1 <= d.n)) continue;
                 if (HALF && oz < 0 && kz == 0) continue;        // entirely below
                 const bool test_sign = HALF && (oz == 0 || kz != 0);
                 const uint32_t tag = offset_code(ox, oy, oz) << kJBits;
@@ -136,48 +159,65 @@ __device__ __forceinline__ int32_t build_row(const Dev &d, const LJ &lj, int64_t
                     wp += ((cnt & 3) == 3) ? wstep : 1;
                     cnt++;
                 };
-                // hot loop, 32 candidates at a time: a candidate clearly
-                // inside (FP32 r^2 below the band) is appended at once by a
-                // predicated store, so the lanes of a warp stay converged;
-                // the few in the band (and, in half lists, those whose
-                // ownership the FP32 sign cannot decide) are marked and go
-                // through accept() after the chunk
-                for (int32_t jb = j0; jb < j1; jb += 32) {
-                    const int m = min(32, (int)(j1 - jb));
-                    uint32_t slow = 0;
-                    // CAP: the row may reach its capacity within this chunk
-                    // (the per-candidate test costs ~7 % of the build, so it
-                    // is compiled in only where it can matter)
-                    auto scan = [&](auto CAP) {
+                // candidates j0 .. j1 - 1 of this cell
+                auto range = [&](int32_t j0, int32_t j1) {
+                    if (!MD_CHECK(d, j0 >= 0 && j0 <= j1 && j1 <= d.n)) return;
+                    // hot loop, 32 candidates at a time: a candidate clearly
+                    // inside (FP32 r^2 below the band) is appended at once by a
+                    // predicated store, so the lanes of a warp stay converged;
+                    // the few in the band (and, in half lists, those whose
+                    // ownership the FP32 sign cannot decide) are marked and go
+                    // through accept() after the chunk
+                    for (int32_t jb = j0; jb < j1; jb += 32) {
+                        const int m = min(32, (int)(j1 - jb));
+                        uint32_t slow = 0;
+                        // CAP: the row may reach its capacity within this chunk
+                        // (the per-candidate test costs ~7 % of the build, so it
+                        // is compiled in only where it can matter)
+                        auto scan = [&](auto CAP) {
 #pragma unroll 4
-                        for (int t = 0; t < m; t++) {
+                            for (int t = 0; t < m; t++) {
+                                const int32_t j = jb + t;
+                                const float4 pj = __ldg(p32 + j);
+                                const float dx = qx - pj.x, dy = qy - pj.y, dz = qz - pj.z;
+                                const float r2f = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                                bool in = (r2f < lo) & (j != (int32_t)i);
+                                bool sl = (r2f >= lo) & (r2f < hi);
+                                if (HALF && test_sign) {
+                                    const bool amb = fabsf(dz) <= 1e-4f;
+                                    sl |= amb & (r2f < lo);
+                                    in &= !amb & (dz < 0.f);
+                                }
+                                if (CAP.value ? (in & (cnt < cap)) : in) *wp = (int32_t)((uint32_t)j | tag);
+                                wp += in ? (((cnt & 3) == 3) ? wstep : 1) : 0;
+                                cnt += in;
+                                slow |= (uint32_t)sl << t;
+                            }
+                        };
+                        if (cnt + m <= cap) scan(std::false_type{});
+                        else scan(std::true_type{});
+                        while (slow) {
+                            const int t = __ffs(slow) - 1;
+                            slow &= slow - 1;
                             const int32_t j = jb + t;
                             const float4 pj = __ldg(p32 + j);
                             const float dx = qx - pj.x, dy = qy - pj.y, dz = qz - pj.z;
-                            const float r2f = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                            bool in = (r2f < lo) & (j != (int32_t)i);
-                            bool sl = (r2f >= lo) & (r2f < hi);
-                            if (HALF && test_sign) {
-                                const bool amb = fabsf(dz) <= 1e-4f;
-                                sl |= amb & (r2f < lo);
-                                in &= !amb & (dz < 0.f);
-                            }
-                            if (CAP.value ? (in & (cnt < cap)) : in) *wp = (int32_t)((uint32_t)j | tag);
-                            wp += in ? (((cnt & 3) == 3) ? wstep : 1) : 0;
-                            cnt += in;
-                            slow |= (uint32_t)sl << t;
+                            accept(j, dx, dy, dz, fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
                         }
-                    };
-                    if (cnt + m <= cap) scan(std::false_type{});
-                    else scan(std::true_type{});
-                    while (slow) {
-                        const int t = __ffs(slow) - 1;
-                        slow &= slow - 1;
-                        const int32_t j = jb + t;
-                        const float4 pj = __ldg(p32 + j);
-                        const float dx = qx - pj.x, dy = qy - pj.y, dz = qz - pj.z;
-                        accept(j, dx, dy, dz, fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
                     }
+                };
+                if (SPLIT) {
+                    // the kept octants of this cell as runs of consecutive keys
+                    const int64_t kb = key_of(d, cid);
+                    uint32_t runs = kxy8 & keep(2, oz, 0x55u);
+                    while (runs) {
+                        const int q0 = __ffs(runs) - 1;
+                        const int len = __ffs(~(runs >> q0)) - 1;
+                        runs &= ~(((1u << len) - 1u) << q0);
+                        range(d.cell_start[kb + q0], d.cell_start[kb + q0 + len]);
+                    }
+                } else {
+                    range(d.cell_start[cid], d.cell_start[cid + 1]);
                 }
             }
         }
@@ -193,12 +233,12 @@ __device__ __forceinline__ int32_t build_row(const Dev &d, const LJ &lj, int64_t
 // The explicit minimum of one block per SM matters: with the bare block size
 // ptxas capped the full-list instance at 56 registers and spilled; with it
 // the kernel takes 72 registers (7 blocks of 4 warps per SM) and no spills.
-template <bool BATCHED, bool HALF>
+template <bool BATCHED, bool HALF, bool SPLIT>
 __global__ void __launch_bounds__(128, 1) k_build(Dev d, LJ lj)
 {
     if (stopped(d.status)) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int32_t cnt = i < d.n ? build_row<BATCHED, HALF>(d, lj, i) : 0;
+    const int32_t cnt = i < d.n ? build_row<BATCHED, HALF, SPLIT>(d, lj, i) : 0;
     // every lane of the warp reaches this point: reduce the row lengths
     const int32_t wmax = __reduce_max_sync(0xffffffffu, cnt);
     if ((threadIdx.x & 31) == 0) atomicMax(&d.status->max_count, wmax);
@@ -304,8 +344,8 @@ __global__ void __launch_bounds__(128, 4) k_build_group(Dev d, LJ lj)
                 const int32_t cid = cell_id_z(col, uz);
                 int32_t j0 = 0, j1 = 0;
                 if (m > 0 && MD_CHECK(d, cid >= 0 && cid < d.ncells)) {
-                    j0 = d.cell_start[cid];
-                    j1 = d.cell_start[cid + 1];
+                    j0 = d.cell_start[key_of(d, cid)];
+                    j1 = d.cell_start[key_of(d, cid + 1)];
                     if (!MD_CHECK(d, j0 >= 0 && j0 <= j1 && j1 <= d.n)) j1 = j0;
                 }
                 const uint32_t tag = offset_code(ox, oy, oz) << kJBits;
@@ -472,10 +512,17 @@ int launch_build(const Dev &d, const LJ &lj, bool half, int64_t ncells, cudaStre
     if (d.n <= 0) return 0;
     const bool b = d.nrep > 1;
     const unsigned g = (unsigned)((d.n + 127) / 128);
-    if (b && half) k_build<true, true><<<g, 128, 0, st>>>(d, lj);
-    else if (b) k_build<true, false><<<g, 128, 0, st>>>(d, lj);
-    else if (half) k_build<false, true><<<g, 128, 0, st>>>(d, lj);
-    else k_build<false, false><<<g, 128, 0, st>>>(d, lj);
+    if (d.split) {
+        if (b && half) k_build<true, true, true><<<g, 128, 0, st>>>(d, lj);
+        else if (b) k_build<true, false, true><<<g, 128, 0, st>>>(d, lj);
+        else if (half) k_build<false, true, true><<<g, 128, 0, st>>>(d, lj);
+        else k_build<false, false, true><<<g, 128, 0, st>>>(d, lj);
+    } else {
+        if (b && half) k_build<true, true, false><<<g, 128, 0, st>>>(d, lj);
+        else if (b) k_build<true, false, false><<<g, 128, 0, st>>>(d, lj);
+        else if (half) k_build<false, true, false><<<g, 128, 0, st>>>(d, lj);
+        else k_build<false, false, false><<<g, 128, 0, st>>>(d, lj);
+    }
     *nl += 1;
     return (int)cudaGetLastError();
 }

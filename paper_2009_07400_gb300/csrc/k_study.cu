@@ -161,8 +161,8 @@ __global__ void __launch_bounds__(256) k_study_tiles(Dev d, LJ lj, float4 *fout)
         int32_t j0 = 0, j1 = 0;
         if (g[0] < R.nc[0] && g[1] < R.nc[1] && g[2] < R.nc[2]) {   // (nc < 2 never occurs)
             const int64_t cid = cell_id(R, g[0], g[1], g[2]);
-            j0 = d.cell_start[cid];
-            j1 = d.cell_start[cid + 1];
+            j0 = d.cell_start[key_of(d, cid)];
+            j1 = d.cell_start[key_of(d, cid + 1)];
         }
         base[threadIdx.x] = j1 - j0;        // counts, summed below
         off[threadIdx.x] = j0;              // first atom, for now
@@ -241,7 +241,8 @@ __global__ void __launch_bounds__(256) k_study_tiles(Dev d, LJ lj, float4 *fout)
     if (threadIdx.x < 64) off[threadIdx.x] = base[threadIdx.x] - off[threadIdx.x];   // slot = off[L] + j
     __syncthreads();
     // the tile's own atoms: cells 8 tile .. 8 tile + 7 are consecutive
-    const int32_t a0 = d.cell_start[R.cell_off + tile * 8], a1 = d.cell_start[R.cell_off + tile * 8 + 8];
+    const int32_t a0 = d.cell_start[key_of(d, R.cell_off + tile * 8)],
+                  a1 = d.cell_start[key_of(d, R.cell_off + tile * 8 + 8)];
     const int4 *nb4 = reinterpret_cast<const int4 *>(d.nb);
     const int64_t n = d.n;
     for (int32_t i = a0 + (int32_t)threadIdx.x; i < a1; i += blockDim.x) {

@@ -65,6 +65,7 @@ struct md_ctx {
     bool own_stream = false;
     int device = 0;
     int tpa = 1;
+    int32_t split = 0;      // cells split into octants for the list build (keys 8 per cell)
     int adj_prec = -1;      // md_set_adjoint_precision: pair terms of the reverse
                             // sweep in MD_FP64 / MD_MIXED; -1 = the context's
 
@@ -148,6 +149,7 @@ Dev view(const md_ctx *c)
     Dev d{};
     d.n = c->n;
     d.ncells = c->nids;
+    d.split = c->split;
     d.nrep = c->nrep;
     d.cap = c->cap;
     d.reps = c->reps_d;
@@ -337,7 +339,7 @@ int realloc_active(md_ctx *c, int32_t cap)
 int enq_bin(md_ctx *c, int *nl)
 {
     Dev d = view(c);
-    if (launch_bin(d, c->nids, c->scan_tmp, c->scan_len, c->st, nl) != 0)
+    if (launch_bin(d, c->scan_tmp, c->scan_len, c->st, nl) != 0)
         return fail(c, MD_ERR_CUDA, "binning launch failed");
     if (d.v32) c->v32_fresh = true;   // the gather writes v32 in the new order
     if (c->disp) {
@@ -473,7 +475,7 @@ int enq_cond_rebuild(md_ctx *c, int *nl)
     cudaGraph_t body = np.conditional.phGraph_out[0];
     CK(cudaStreamBeginCaptureToGraph(c->side, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     int bl = 0, rc = MD_OK;
-    if (launch_bin(d, c->nids, c->scan_tmp, c->scan_len, c->side, &bl) != 0 ||
+    if (launch_bin(d, c->scan_tmp, c->scan_len, c->side, &bl) != 0 ||
         launch_copy_back(d, c->side, &bl) != 0 || launch_list_build(c, d, c->side, &bl) != 0)
         rc = fail(c, MD_ERR_CUDA, "rebuild body launch failed");
     cudaGraph_t out = nullptr;
@@ -740,10 +742,13 @@ void set_lj_constants(md_ctx *c)
 }
 
 // Process-wide autotuner cache: (precision, log2 atoms per replica, batched)
-// -> (threads per atom, half list).
-std::map<std::string, std::pair<int, int>> &tune_cache()
+// -> (threads per atom, list type, cell split).
+struct Tuning {
+    int tpa, lt, split;
+};
+std::map<std::string, Tuning> &tune_cache()
 {
-    static std::map<std::string, std::pair<int, int>> m;
+    static std::map<std::string, Tuning> m;
     return m;
 }
 
@@ -753,10 +758,12 @@ std::mutex &tune_mutex()
     return m;
 }
 
-// Switches lanes-per-atom / list type; a list-type change rebuilds the list.
-int apply_tuning(md_ctx *c, int tpa, int lt)
+// Switches lanes-per-atom / list type / cell split; a list-type or split
+// change rebins and rebuilds the list.
+int apply_tuning(md_ctx *c, int tpa, int lt, int split)
 {
-    const bool relist = (lt != c->p.list_type);
+    const bool relist = lt != c->p.list_type || split != c->split;
+    c->split = split;
     c->tpa = tpa;
     c->p.threads_per_atom = tpa;
     c->p.list_type = lt;
@@ -1107,11 +1114,13 @@ int md_get_forces_device(md_ctx *c, double *out)
 int md_get_cells(md_ctx *c, int32_t *cell_start, int32_t *cell_atoms)
 {
     if (!c || !cell_start || !cell_atoms) return fail(c, MD_ERR_INVAL, "null argument");
-    std::vector<int32_t> cs((size_t)c->nids + 1), ids((size_t)c->n);
+    const int sh = 3 * c->split;
+    std::vector<int32_t> cs(((size_t)c->nids << sh) + 1), ids((size_t)c->n);
     CK(cudaMemcpyAsync(cs.data(), c->cell_start, sizeof(int32_t) * cs.size(), cudaMemcpyDeviceToHost, c->st));
     CK(cudaMemcpyAsync(ids.data(), c->id[c->vp], sizeof(int32_t) * ids.size(), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
-    // device cells are numbered by tiles; report them in (cx, cy, cz) order
+    // device cells are numbered by tiles; report them in (cx, cy, cz) order,
+    // each cell's atoms by caller id (split cells hold them by octant first)
     int64_t o = 0;
     for (int32_t r = 0; r < c->nrep; r++) {
         const Rep &R = c->reps_h[r];
@@ -1121,7 +1130,10 @@ int md_get_cells(md_ctx *c, int32_t *cell_start, int32_t *cell_atoms)
                 for (int cz = 0; cz < R.nc[2]; cz++) {
                     const int64_t id = cell_id(R, cx, cy, cz);
                     cell_start[o++] = (int32_t)(at - R.atom_off);
-                    for (int32_t a = cs[id]; a < cs[id + 1]; a++) cell_atoms[at++] = (int32_t)(ids[a] - R.atom_off);
+                    const int64_t first = at;
+                    for (int32_t a = cs[id << sh]; a < cs[(id + 1) << sh]; a++)
+                        cell_atoms[at++] = (int32_t)(ids[a] - R.atom_off);
+                    std::sort(cell_atoms + first, cell_atoms + at);
                 }
         cell_start[o++] = (int32_t)(at - R.atom_off);
     }
@@ -1191,7 +1203,23 @@ int md_get_info(md_ctx *c, md_info *info)
     info->step = c->step;
     info->kernel_launches = c->launches;
     info->rebuilds = c->rebuilds;
+    info->cell_split = c->split;
     return MD_OK;
+}
+
+int md_set_cell_split(md_ctx *c, int32_t split)
+{
+    if (!c || (split != 0 && split != 1)) return fail(c, MD_ERR_INVAL, "split must be 0 or 1");
+    if (split == c->split) return MD_OK;
+    CK(cudaStreamSynchronize(c->st));
+    c->split = split;
+    // new binning keys: rebin and rebuild (the rows hold the same pairs; the
+    // order of a cell's entries, and so the force sums' rounding, changes)
+    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+    c->graphs.clear();
+    c->list_valid = false;
+    c->forces_valid = false;
+    return ensure_forces(c);
 }
 
 int md_set_step(md_ctx *c, int64_t step)
@@ -1335,7 +1363,7 @@ int md_set_spring_dashpot(md_ctx *c, double k_spring, double gamma)
     }
     c->v32_fresh = false;
     // contacts use full per-atom lists
-    if (c->p.list_type != MD_LIST_FULL && (rc = apply_tuning(c, 1, MD_LIST_FULL))) return rc;
+    if (c->p.list_type != MD_LIST_FULL && (rc = apply_tuning(c, 1, MD_LIST_FULL, c->split))) return rc;
     c->lj.pot = 1;
     c->lj.sd_k = k_spring;
     c->lj.sd_g = gamma;
@@ -1367,7 +1395,7 @@ static int adjoint_impl(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt,
     const int lt0 = c->p.list_type, tpa0 = c->tpa;
     int rc = MD_OK;
     // the adjoint walks full per-atom lists
-    if (lt0 != MD_LIST_FULL && (rc = apply_tuning(c, tpa0, MD_LIST_FULL))) return rc;
+    if (lt0 != MD_LIST_FULL && (rc = apply_tuning(c, tpa0, MD_LIST_FULL, c->split))) return rc;
 
     // workspace: reused between calls, grown when a call needs more
     auto &W = c->adj;
@@ -1529,7 +1557,7 @@ static int adjoint_impl(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt,
     }
     c->launches += nl;
     c->forces_valid = false;
-    if (!rc && lt0 != MD_LIST_FULL) rc = apply_tuning(c, tpa0, lt0);
+    if (!rc && lt0 != MD_LIST_FULL) rc = apply_tuning(c, tpa0, lt0, c->split);
     return rc;
 }
 
@@ -1632,7 +1660,7 @@ int md_autotune(md_ctx *c, int32_t steps, md_params *chosen)
         std::lock_guard<std::mutex> g(tune_mutex());
         auto it = tune_cache().find(key);
         if (it != tune_cache().end()) {
-            int rc = apply_tuning(c, it->second.first, it->second.second);
+            int rc = apply_tuning(c, it->second.tpa, it->second.lt, it->second.split);
             if (rc) return rc;
             if (chosen) { *chosen = c->p; chosen->threads_per_atom = c->tpa; }
             return MD_OK;
@@ -1671,32 +1699,47 @@ int md_autotune(md_ctx *c, int32_t steps, md_params *chosen)
                              {8, MD_LIST_FULL},   {1, MD_LIST_HALF}, {1, MD_LIST_GROUP4},
                              {1, MD_LIST_GROUP2}};
     float best = 1e30f;
-    int best_k = 0;
+    int best_k = 0, best_split = c->split;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    const int ncand = is_mixed(c) ? 7 : 5;
-    for (int k = 0; k < ncand && !rc; k++) {
-        if ((rc = apply_tuning(c, cands[k][0], cands[k][1]))) break;
-        if ((rc = md_run(c, steps, 0, nullptr))) break;  // warm-up (graph capture)
-        if ((rc = restore())) break;
+    // times `steps` steps of one configuration from the saved state
+    auto time_one = [&](int k, int split, float *ms) -> int {
+        int r;
+        if ((r = apply_tuning(c, cands[k][0], cands[k][1], split))) return r;
+        if ((r = md_run(c, steps, 0, nullptr))) return r;  // warm-up (graph capture)
+        if ((r = restore())) return r;
         CK(cudaEventRecord(e0, c->st));
-        if ((rc = md_run(c, steps, 0, nullptr))) break;
+        if ((r = md_run(c, steps, 0, nullptr))) return r;
         CK(cudaEventRecord(e1, c->st));
         CK(cudaEventSynchronize(e1));
+        CK(cudaEventElapsedTime(ms, e0, e1));
+        return restore();
+    };
+    // lanes per atom and list type at the current cell split, then the
+    // winner with the other split (the cell size of the list build)
+    const int ncand = is_mixed(c) ? 7 : 5;
+    const int split0 = c->split;
+    for (int k = 0; k < ncand && !rc; k++) {
         float ms = 0;
-        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if ((rc = time_one(k, split0, &ms))) break;
         if (ms < best) { best = ms; best_k = k; }
-        if ((rc = restore())) break;
+    }
+    if (!rc) {
+        float ms = 0;
+        if (!(rc = time_one(best_k, 1 - split0, &ms)) && ms < best) {
+            best = ms;
+            best_split = 1 - split0;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(xb); cudaFree(vb); cudaFree(ib);
     if (rc) return rc;
-    if ((rc = apply_tuning(c, cands[best_k][0], cands[best_k][1]))) return rc;
+    if ((rc = apply_tuning(c, cands[best_k][0], cands[best_k][1], best_split))) return rc;
     {
         std::lock_guard<std::mutex> g(tune_mutex());
-        tune_cache()[key] = {cands[best_k][0], cands[best_k][1]};
+        tune_cache()[key] = {cands[best_k][0], cands[best_k][1], best_split};
     }
     if (chosen) { *chosen = c->p; chosen->threads_per_atom = c->tpa; }
     return MD_OK;
@@ -1767,6 +1810,10 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
             R.s[d] = L[d] / (double)R.nc[d];
             R.nsf[d] = -(float)R.s[d];
             R.invsf[d] = 1.0f / (float)R.s[d];
+            // the split build's threshold s - rs - 1e-3 s, rounded down
+            const double t = R.s[d] - rs - 1e-3 * R.s[d];
+            R.splitf[d] = (float)t;
+            if ((double)R.splitf[d] > t) R.splitf[d] = std::nextafter(R.splitf[d], -INFINITY);
             vol *= L[d];
         }
         for (int d = 0; d < 3; d++) R.nt[d] = (R.nc[d] + kTile - 1) / kTile;
@@ -1809,6 +1856,10 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
             c->tpa = n <= 8192 ? 8 : (n <= 393216 ? 4 : (n <= 3000000 ? 2 : 1));
     }
     c->ncells = cells;
+    // whole cells: the split build (half-size cells) measured slower on the
+    // LJ liquids (its lanes' octant runs diverge); md_set_cell_split and
+    // md_autotune change it
+    c->split = 0;
     c->nids = ids;
     c->nchunks = (int64_t)chunk_rep.size() / 2;
 
@@ -1846,10 +1897,12 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
     }
     if ((rc = dalloc(c, &c->f64, N))) return rc;
     if ((rc = dalloc(c, &c->cell_key, N))) return rc;
-    if ((rc = dalloc(c, &c->cell_count, (size_t)ids))) return rc;
-    if ((rc = dalloc(c, &c->cell_start, (size_t)ids + 1))) return rc;
+    // binning keys: 8 per cell id (cells split into octants) or 1; the
+    // arrays hold the split layout either way, so the split can change
+    if ((rc = dalloc(c, &c->cell_count, (size_t)ids * 8))) return rc;
+    if ((rc = dalloc(c, &c->cell_start, (size_t)ids * 8 + 1))) return rc;
     if ((rc = dalloc(c, &c->perm, N))) return rc;
-    c->scan_len = scan_tmp_elems(ids);
+    c->scan_len = scan_tmp_elems(ids * 8);
     if ((rc = dalloc(c, &c->scan_tmp, (size_t)c->scan_len))) return rc;
     if ((rc = dalloc(c, &c->nb_count, N))) return rc;
     if ((rc = dalloc(c, &c->pe_atom, N))) return rc;
@@ -1896,7 +1949,7 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
     CK(cudaMemcpyAsync(c->rep_of_d, rep_of.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, c->st));
     CK(cudaMemcpyAsync(c->chunk_rep_d, chunk_rep.data(), sizeof(int64_t) * chunk_rep.size(), cudaMemcpyHostToDevice, c->st));
     CK(cudaMemcpyAsync(c->chunk_first_d, chunk_first.data(), sizeof(int64_t) * chunk_first.size(), cudaMemcpyHostToDevice, c->st));
-    CK(cudaMemsetAsync(c->cell_count, 0, sizeof(int32_t) * (size_t)ids, c->st));
+    CK(cudaMemsetAsync(c->cell_count, 0, sizeof(int32_t) * (size_t)ids * 8, c->st));
     CK(cudaMemsetAsync(c->status, 0, sizeof(DevStatus), c->st));
     CK(cudaMemsetAsync(c->f32, 0, sizeof(float4) * N, c->st));
     CK(cudaMemsetAsync(c->f64, 0, sizeof(dvec4) * N, c->st));

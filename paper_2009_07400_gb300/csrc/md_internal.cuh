@@ -91,6 +91,9 @@ struct Rep {
     double s[3];              // cell side L / nc (FP64)
     float nsf[3];             // -s in FP32 (stencil offsets of the mixed path)
     float invsf[3];           // fl32(1 / fl32(s)) (binning's quotient estimate)
+    float splitf[3];          // split cells: s - rs - 1e-3 s in FP32, rounded down (the
+                              // build skips the far half of a neighbour cell for atoms
+                              // at least this far on the near side of their own centre)
     int32_t nc[3];
     int32_t nt[3];            // cell tiles per dimension, ceil(nc / MD_CELL_TILE)
     int64_t ctr_off;          // first entry of this replica in Dev::ctr
@@ -156,6 +159,10 @@ struct LJ {
 struct Dev {
     int64_t n;
     int64_t ncells;           // cell ids over all replicas, tile padding included
+    int32_t split;            // 1: each cell's atoms are ordered by octant (the
+                              // half-size cells of Sec. 3.2), cell_start holds 8
+                              // entries per cell; 0: one entry per cell
+    int32_t split_pad_;
     int32_t nrep;
     int32_t cap;              // list capacity (multiple of 4)
     const Rep *reps;
@@ -171,9 +178,12 @@ struct Dev {
     float disp2_thr;          // squared trigger distance (FP32, below (skin/2)^2)
     float4 *f32;              // mixed-path forces
     dvec4 *f64;             // FP64-path forces
-    int32_t *cell_key;        // global cell of each slot (binning scratch)
-    int32_t *cell_count;      // per global cell (returns to zero after scatter)
-    int32_t *cell_start;      // per global cell + 1
+    // Binning keys: the global cell id, times 8 plus the octant when split
+    // (octant = 4 hx + 2 hy + hz, h = 1 for the upper half of the cell along
+    // that axis), so a cell's atoms are cell_start[key(c)] .. cell_start[key(c + 1)]
+    int32_t *cell_key;        // binning key of each slot (binning scratch)
+    int32_t *cell_count;      // per key (returns to zero after scatter)
+    int32_t *cell_start;      // per key + 1
     int32_t *perm;            // scatter target: slot -> old slot
     int32_t *nb;              // list: int4 chunks, chunk q of atom i at ((q*n)+i)*4
     int32_t *nb_count;
@@ -201,6 +211,16 @@ struct Dev {
     const float4 *offtab;     // per replica 64 codes: (ox s_x, oy s_y, oz s_z) of a
                               // list entry's 6-bit cell-offset code
 };
+
+// Binning keys of cell c: its first key, and its atom range.
+__host__ __device__ __forceinline__ int64_t key_of(const Dev &d, int64_t c)
+{
+    return c << (3 * d.split);
+}
+__host__ __device__ __forceinline__ int64_t nkeys(const Dev &d)
+{
+    return d.ncells << (3 * d.split);
+}
 
 #ifdef __CUDACC__
 // Bit casts on host and device (the host side serves the conversion tests).
@@ -317,8 +337,8 @@ __device__ __forceinline__ void check_displacement(const Dev &d, int64_t i, cons
 // ---------------------------------------------------------------------------
 // Kernel launchers (defined in the k_*.cu files).
 // ---------------------------------------------------------------------------
-int launch_bin(const Dev &d, int64_t ncells_total, int32_t *scan_tmp, int64_t scan_tmp_len,
-               cudaStream_t st, int *nlaunch);
+int launch_bin(const Dev &d, int32_t *scan_tmp, int64_t scan_tmp_len, cudaStream_t st,
+               int *nlaunch);
 int launch_build(const Dev &d, const LJ &lj, bool half, int64_t ncells, cudaStream_t st,
                  int *nlaunch);
 
@@ -360,7 +380,7 @@ int launch_copy_back(const Dev &d, cudaStream_t st, int *nlaunch);
 int launch_rebuild_check(const Dev &d, cudaGraphConditionalHandle h, cudaStream_t st,
                          int *nlaunch);
 
-int64_t scan_tmp_elems(int64_t ncells_total);
+int64_t scan_tmp_elems(int64_t nkeys_total);
 
 // Force-kernel studies (k_study.cu): variants 1 (SoA gathers) and 2 (AoSoA
 // gathers) into fout; variants 3 and 4 (neighbourhood staged in shared

@@ -36,6 +36,7 @@ ABI_SYMBOLS = [
     "md_set_state_device", "md_get_positions_device", "md_get_velocities_device",
     "md_get_forces_device", "md_set_spring_dashpot", "md_set_step",
     "md_set_adjoint_precision", "md_thermo", "md_adjoint_device", "md_study_force_variant",
+    "md_set_cell_split",
 ]
 
 
@@ -77,7 +78,7 @@ class md_info(ctypes.Structure):
                 ("threads_per_atom", ctypes.c_int32), ("list_capacity", ctypes.c_int32),
                 ("max_neighbors", ctypes.c_int32), ("ncells", ctypes.c_int64),
                 ("step", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
-                ("rebuilds", ctypes.c_int64)]
+                ("rebuilds", ctypes.c_int64), ("cell_split", ctypes.c_int32)]
 
 
 _lib = None
@@ -139,6 +140,7 @@ def load(path: str | None = None):
                 "md_adjoint_device": [ctx, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, _D,
                                       _D, _D, _P, _P],
                 "md_study_force_variant": [ctx, ctypes.c_int32, ctypes.c_int32, _D, _D],
+                "md_set_cell_split": [ctx, ctypes.c_int32],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -457,6 +459,11 @@ class MDContext:
     def set_adjoint_precision(self, precision):
         """Precision of the reverse sweep's pair terms (MD_FP64 or MD_MIXED)."""
         self._check(self._lib.md_set_adjoint_precision(self._h, int(precision)))
+
+    def set_cell_split(self, split):
+        """1: the list build scans half-size cells (each cell's atoms ordered
+        by octant); 0: whole cells.  Rebins and rebuilds."""
+        self._check(self._lib.md_set_cell_split(self._h, int(split)))
 
     def set_capacity(self, cap):
         self._check(self._lib.md_set_capacity(self._h, int(cap)))

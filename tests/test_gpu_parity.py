@@ -91,9 +91,10 @@ def band_system(seed=5, L=(30.0, 31.0, 29.0)):
 def edge_coordinates(seed=6, L=(9.0, 10.0, 11.0)):
     """Coordinates on the edges of the wrap and the binning: -0.0, 0, L,
     the doubles next to 0 and L, -1e-300 (wraps to exactly L, so into the
-    last cell), -L, one box length above, and the cell faces k s and their
+    last cell), -L, one box length above, the cell faces k s and their
     neighbouring doubles (where the quotient estimate must defer to the
-    exact division)."""
+    exact division), and the mid-planes (k + 1/2) s of the cells with their
+    neighbouring doubles (the octant boundaries of split cells)."""
     rng = np.random.default_rng(seed)
     L = np.array(L)
     pos = rng.uniform(0, 1, (240, 3)) * L
@@ -105,6 +106,9 @@ def edge_coordinates(seed=6, L=(9.0, 10.0, 11.0)):
                 -L[d], 2 * L[d] - 1e-9, L[d] + 1e-12, np.nextafter(-0.0, -1.0)]
         for f in faces:
             vals += [f, np.nextafter(f, 0.0), np.nextafter(f, np.inf), f - L[d], f + L[d]]
+        for k in range(int(round(L[d] / s))):
+            m = (k + 0.5) * s
+            vals += [m, np.nextafter(m, 0.0), np.nextafter(m, np.inf)]
         for v in vals:
             pos[row, d] = v
             row += 1
@@ -139,8 +143,11 @@ def test_bin_parity(md, orc, case):
 # --------------------------------------------------------------------------
 
 @pytest.mark.parametrize("half", [False, True])
-@pytest.mark.parametrize("case", ["fcc8", "jitter7", "nc2", "aniso", "band", "band_wide", "liquid"])
+@pytest.mark.parametrize("case", ["fcc8", "jitter7", "nc2", "aniso", "band", "band_wide", "liquid",
+                                  "edges", "s_eq_rs"])
 def test_list_parity(md, orc, case, half):
+    """Rows equal the oracle's as sets, in both precisions, with the build
+    scanning whole cells and half-size cells (md_set_cell_split 0 and 1)."""
     if case == "fcc8":
         s = inputs.fcc_system(8, seed=1001)
     elif case == "jitter7":
@@ -153,11 +160,18 @@ def test_list_parity(md, orc, case, half):
         s = band_system()
     elif case == "band_wide":
         s = band_system(seed=6, L=(8.39, 5.75, 30.0))
+    elif case == "edges":
+        s = edge_coordinates()
+    elif case == "s_eq_rs":      # cell sides equal to rc + skin (2, 3 and 4 cells)
+        s = inputs.uniform_box(1500, (5.6, 8.4, 11.2), seed=13)
     else:
         s = liquid(orc)
     for precision in (md.MD_FP64, md.MD_MIXED):
         with ctx_of(md, s, half_list=half, precision=precision) as ctx:
-            assert_lists_equal(orc, ctx, s.pos, s.box, half)
+            for split in (1 - ctx.info().cell_split, ctx.info().cell_split):
+                ctx.set_cell_split(split)
+                assert ctx.info().cell_split == split
+                assert_lists_equal(orc, ctx, s.pos, s.box, half)
 
 
 # --------------------------------------------------------------------------
@@ -175,10 +189,13 @@ def test_force_parity(md, orc, case, half, tpa):
         s = inputs.replica_system(2999, 0.82, 1.3, seed=12)
     xw = orc.wrap(s.pos, s.box)
     Fr = orc.forces_list(xw, s.box, orc.neighbors_cells(xw, s.box, RC + SKIN))
-    with ctx_of(md, s, half_list=half, threads_per_atom=tpa, precision=md.MD_FP64) as ctx:
-        assert fp64_force_ok(ctx.forces(), Fr) <= 1e-10
-    with ctx_of(md, s, half_list=half, threads_per_atom=tpa, precision=md.MD_MIXED) as ctx:
-        assert rms_rel(ctx.forces(), Fr) <= 1e-5
+    for split in (0, 1):
+        with ctx_of(md, s, half_list=half, threads_per_atom=tpa, precision=md.MD_FP64) as ctx:
+            ctx.set_cell_split(split)
+            assert fp64_force_ok(ctx.forces(), Fr) <= 1e-10
+        with ctx_of(md, s, half_list=half, threads_per_atom=tpa, precision=md.MD_MIXED) as ctx:
+            ctx.set_cell_split(split)
+            assert rms_rel(ctx.forces(), Fr) <= 1e-5
 
 
 def test_force_params(md, orc):
@@ -456,6 +473,7 @@ def test_autotune_keeps_state(md, orc):
             x0, v0 = ctx.positions(), ctx.velocities()
             chosen = ctx.autotune(steps=20)
             assert chosen.threads_per_atom in (1, 2, 4, 8) and chosen.list_type in (0, 1, 2, 4)
+            assert ctx.info().cell_split in (0, 1)
             assert ctx.info().step == 0
             assert np.array_equal(ctx.positions(), x0)
             assert np.array_equal(ctx.velocities(), v0)
@@ -464,6 +482,29 @@ def test_autotune_keeps_state(md, orc):
                 assert fp64_force_ok(F, Fr) <= 1e-10
             else:
                 assert rms_rel(F, Fr) <= 1e-5
+
+
+def test_cell_split_switch(md, orc):
+    """md_set_cell_split: whole cells by default, a change keeps the state
+    (up to the wrap of atoms that left the box) and the run goes on, and
+    values other than 0 and 1 are rejected."""
+    s = liquid(orc, n_cells=6)
+    with ctx_of(md, s, precision=md.MD_MIXED) as ctx:
+        assert ctx.info().cell_split == 0
+        ctx.run(10)
+        x, v = ctx.positions(), ctx.velocities()
+        ctx.set_cell_split(1)
+        assert ctx.info().cell_split == 1
+        # the rebinning wraps atoms that left the box by one box length
+        dx = ctx.positions() - x
+        assert np.all(np.abs(dx - s.box * np.round(dx / s.box)) <= 1e-12)
+        assert np.array_equal(ctx.velocities(), v)
+        ctx.run(10)
+        assert ctx.info().step == 20
+        for bad in (-1, 2):
+            with pytest.raises(md.MDError) as e:
+                ctx.set_cell_split(bad)
+            assert e.value.code == md.MD_ERR_INVAL
 
 
 def test_ensemble_256_sampled(md, orc):
