@@ -799,8 +799,8 @@ def run_study(args):
     the same state:
       * force-kernel variants (md_study_force_variant, full per-atom list,
         one lane per atom, forces only): gathered-position layouts (AoS, the
-        library's; SoA; AoSoA) and the tile neighbourhood staged in shared
-        memory;
+        library's; SoA; AoSoA), the tile neighbourhood staged in shared
+        memory, and gathers through the texture path;
       * list types: the per-atom full list against lists shared by groups of
         2 and 4 atoms (md_profile per phase);
       * cell orders: libraries built with cell tiles of 1 (z fastest), 2 (the
@@ -822,15 +822,17 @@ def run_study(args):
     reps = max(5, args.steps)
     names = {0: "AoS float4 (library)", 1: "SoA", 2: "AoSoA (blocks of 4)",
              3: "2x2x2-cell tiles, 4x4x4-cell neighbourhood in shared memory",
-             4: "the same staged by TMA bulk copies (one per cell)"}
+             4: "the same staged by TMA bulk copies (one per cell)",
+             5: "AoS float4 gathers through the texture path",
+             6: "half of the gathers through the texture path"}
     variants = {}
     with _study_context(md, s, stream.cuda_stream, list_type=0, threads_per_atom=1) as ctx:
         F = {}
-        for v in (0, 1, 2, 3, 4):
+        for v in (0, 1, 2, 3, 4, 5, 6):
             times = [ctx.study_force_variant(v, reps)[0] for _ in range(3)]
             F[v] = ctx.study_force_variant(v, 1, forces=True)[1]
             variants[names[v]] = {"us_per_launch": min(times), "runs": times}
-        for v in (1, 2, 3, 4):
+        for v in (1, 2, 3, 4, 5, 6):
             d = F[v] - F[0]
             variants[names[v]]["max_abs_force_diff_vs_library"] = float(np.abs(d).max())
             variants[names[v]]["rms_rel_vs_library"] = float(np.sqrt(np.sum(d ** 2) / np.sum(F[0] ** 2)))

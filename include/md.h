@@ -351,13 +351,18 @@ int md_set_adjoint_precision(md_ctx *ctx, int32_t precision);
  *   3  the 4x4x4-cell neighbourhood of each 2x2x2-cell tile staged in shared
  *      memory in the tile's frame (one block per tile), 4  the same staged by
  *      TMA bulk copies (one per cell: cells are contiguous ranges of the
- *      position array) completing on an mbarrier (bitwise variant 3's forces)
+ *      position array) completing on an mbarrier (bitwise variant 3's forces),
+ *   5  the library's gathers through the texture path (tex1Dfetch on a
+ *      texture object over the positions), 6  half of them (the pairs of a
+ *      list chunk alternate between the two paths), both bitwise the
+ *      library's forces,
  * with forces only (no integration), CUDA events on the context's stream;
  * *us = mean device time per launch in microseconds; forces (may be NULL):
  * host, n x 3 doubles in caller order.  Needs a single-system mixed LJ
  * context with full per-atom lists.
  * Errors: MD_ERR_INVAL, MD_ERR_STATE (wrong kind of context; variants 3, 4:
- * a neighbourhood above 3008 atoms), MD_ERR_TIMEOUT (variant 4: a bulk copy
+ * a neighbourhood above 3008 atoms; variants 5, 6: more atoms than a linear
+ * texture holds), MD_ERR_TIMEOUT (variant 4: a bulk copy
  * did not complete within ~10 ms; the kernel returns), MD_ERR_NOMEM,
  * MD_ERR_CUDA. */
 int md_study_force_variant(md_ctx *ctx, int32_t variant, int32_t reps, double *us, double *forces);

@@ -18,9 +18,15 @@
 //      one bulk copy (cp.async.bulk) that completes on a shared-memory
 //      mbarrier; the block then shifts the staged positions into the tile
 //      frame in place.  Its forces are bitwise those of variant 3.
+//   5  The library's AoS float4 gathers through the texture path
+//      (tex1Dfetch on a texture object over the position array) instead of
+//      the load/store unit's global loads.
+//   6  Half of the gathers through each path: the pairs of a list chunk
+//      alternate between a global load and a texture fetch.
 //
-// Variants 1 and 2 evaluate every pair with the library kernel's arithmetic
-// in the same order, so their forces are bitwise those of the library.
+// Variants 1, 2, 5 and 6 evaluate every pair with the library kernel's
+// arithmetic in the same order, so their forces are bitwise those of the
+// library.
 // Variant 3 forms displacements in the tile frame (coordinates up to two
 // cells from its centre), so its FP32 rounding differs.
 #include "md_internal.cuh"
@@ -61,12 +67,13 @@ __global__ void __launch_bounds__(256) k_study_layouts(const float4 *p32, int64_
     b[8] = p.z;
 }
 
-// Variants 1 and 2: the library's pair loop (one lane per atom, int4 list
-// chunks, offsets selected in registers, four pairs per Kahan step) with the
-// gather replaced.
+// Variants 1, 2, 5 and 6: the library's pair loop (one lane per atom, int4
+// list chunks, offsets selected in registers, four pairs per Kahan step) with
+// the gather replaced.
 template <int LAYOUT>
 __global__ void __launch_bounds__(256) k_study_gather(Dev d, LJ lj, const float *soa,
-                                                      const float *aosoa, int64_t n1, float4 *fout)
+                                                      const float *aosoa, int64_t n1,
+                                                      cudaTextureObject_t tex, float4 *fout)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n) return;
@@ -81,10 +88,15 @@ __global__ void __launch_bounds__(256) k_study_gather(Dev d, LJ lj, const float 
     const float qx0 = pi.x - nsx, qx2 = pi.x + nsx;
     const float qy0 = pi.y - nsy, qy2 = pi.y + nsy;
     const float qz0 = pi.z - nsz, qz2 = pi.z + nsz;
-    auto pair = [&](uint32_t e, float &px, float &py, float &pz) {
+    auto pair = [&](uint32_t e, bool via_tex, float &px, float &py, float &pz) {
         const uint32_t j = e & kJMask;
         float jx, jy, jz;
-        if (LAYOUT == 1) {
+        if (LAYOUT == 5 || LAYOUT == 6) {
+            const float4 p = via_tex ? tex1Dfetch<float4>(tex, (int)j) : __ldg(d.p32 + j);
+            jx = p.x;
+            jy = p.y;
+            jz = p.z;
+        } else if (LAYOUT == 1) {
             jx = __ldg(soa + j);
             jy = __ldg(soa + n1 + j);
             jz = __ldg(soa + 2 * n1 + j);
@@ -112,10 +124,10 @@ __global__ void __launch_bounds__(256) k_study_gather(Dev d, LJ lj, const float 
         const int4 e = nxt;
         if (q + 1 < nq) nxt = __ldcs(nb4 + (int64_t)(q + 1) * n + i);
         float px = 0.f, py = 0.f, pz = 0.f;
-        pair((uint32_t)e.x, px, py, pz);
-        pair((uint32_t)e.y, px, py, pz);
-        pair((uint32_t)e.z, px, py, pz);
-        pair((uint32_t)e.w, px, py, pz);
+        pair((uint32_t)e.x, LAYOUT == 5, px, py, pz);
+        pair((uint32_t)e.y, LAYOUT >= 5, px, py, pz);
+        pair((uint32_t)e.z, LAYOUT == 5, px, py, pz);
+        pair((uint32_t)e.w, LAYOUT >= 5, px, py, pz);
         kahan(sx, cx, px);
         kahan(sy, cy, py);
         kahan(sz, cz, pz);
@@ -296,22 +308,27 @@ __global__ void __launch_bounds__(256) k_study_tiles(Dev d, LJ lj, float4 *fout)
 
 int64_t study_layout_floats(int64_t n) { return 3 * (n + 1) + 12 * ((n + 1 + 3) / 4); }
 
-// Variants 1-3 into fout (n float4, cell order).  layouts: device scratch of
-// study_layout_floats(n) floats (variants 1 and 2 fill it on every call).
-int launch_study_force(const Dev &d, const LJ &lj, int variant, float *layouts, float4 *fout,
-                       cudaStream_t st, int *nl)
+// Variants 1, 2, 5 and 6 into fout (n float4, cell order).  layouts: device
+// scratch of study_layout_floats(n) floats (variants 1 and 2 fill it on every
+// call); tex: a texture object over d.p32 (n + 1 float4; variants 5 and 6).
+int launch_study_force(const Dev &d, const LJ &lj, int variant, float *layouts,
+                       cudaTextureObject_t tex, float4 *fout, cudaStream_t st, int *nl)
 {
     if (d.n <= 0 || d.nrep != 1) return -1;
     const int64_t n1 = d.n + 1;
     const unsigned g = (unsigned)((d.n + 255) / 256);
+    float *soa = layouts, *aosoa = layouts + 3 * n1;
     if (variant == 1 || variant == 2) {
-        float *soa = layouts, *aosoa = layouts + 3 * n1;
         k_study_layouts<<<(unsigned)((n1 + 255) / 256), 256, 0, st>>>(d.p32, n1, soa, aosoa);
-        if (variant == 1) k_study_gather<1><<<g, 256, 0, st>>>(d, lj, soa, aosoa, n1, fout);
-        else k_study_gather<2><<<g, 256, 0, st>>>(d, lj, soa, aosoa, n1, fout);
+        if (variant == 1) k_study_gather<1><<<g, 256, 0, st>>>(d, lj, soa, aosoa, n1, tex, fout);
+        else k_study_gather<2><<<g, 256, 0, st>>>(d, lj, soa, aosoa, n1, tex, fout);
         *nl += 2;
+    } else if (variant == 5 || variant == 6) {
+        if (variant == 5) k_study_gather<5><<<g, 256, 0, st>>>(d, lj, soa, aosoa, n1, tex, fout);
+        else k_study_gather<6><<<g, 256, 0, st>>>(d, lj, soa, aosoa, n1, tex, fout);
+        *nl += 1;
     } else {
-        return -1;   // variant 3: launch_study_tiles
+        return -1;   // variants 3 and 4: launch_study_tiles
     }
     return (int)cudaGetLastError();
 }

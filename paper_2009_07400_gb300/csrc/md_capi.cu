@@ -1575,10 +1575,10 @@ int md_adjoint_device(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt, d
 
 int md_study_force_variant(md_ctx *c, int32_t variant, int32_t reps, double *us, double *forces)
 {
-    if (!c || !us || reps < 1 || variant < 0 || variant > 4) return fail(c, MD_ERR_INVAL, "bad argument");
+    if (!c || !us || reps < 1 || variant < 0 || variant > 6) return fail(c, MD_ERR_INVAL, "bad argument");
     if (!is_mixed(c) || c->p.list_type != MD_LIST_FULL || is_sd(c) || c->nrep != 1)
         return fail(c, MD_ERR_STATE, "force studies take a single-system mixed LJ context with full lists");
-    if (variant >= 3 && kTile != 2)
+    if ((variant == 3 || variant == 4) && kTile != 2)
         return fail(c, MD_ERR_STATE, "the shared-memory study stages 2x2x2-cell tiles (a build with MD_CELL_TILE = 2)");
     int rc = ensure_list(c);
     if (rc) return rc;
@@ -1591,11 +1591,38 @@ int md_study_force_variant(md_ctx *c, int32_t variant, int32_t reps, double *us,
     Dev d = view(c);
     d.f32 = fout;                                    // the library's kernel writes here too
     const int64_t ntiles = (int64_t)c->reps_h[0].nt[0] * c->reps_h[0].nt[1] * c->reps_h[0].nt[2];
+    // variants 5 and 6: a texture object over the current FP32 positions
+    cudaTextureObject_t tex = 0;
+    if (variant >= 5) {
+        int maxw = 0;
+        cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxTexture1DLinearWidth, c->device);
+        if ((int64_t)c->n + 1 > (int64_t)maxw) {
+            cudaFree(fout);
+            cudaFree(lay);
+            return fail(c, MD_ERR_STATE, "more atoms than a linear texture holds");
+        }
+        cudaResourceDesc rd{};
+        rd.resType = cudaResourceTypeLinear;
+        rd.res.linear.devPtr = d.p32;
+        rd.res.linear.desc = cudaCreateChannelDesc<float4>();
+        rd.res.linear.sizeInBytes = sizeof(float4) * ((size_t)c->n + 1);
+        cudaTextureDesc td{};
+        td.addressMode[0] = cudaAddressModeClamp;
+        td.filterMode = cudaFilterModePoint;
+        td.readMode = cudaReadModeElementType;
+        if (cudaCreateTextureObject(&tex, &rd, &td, nullptr) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(fout);
+            cudaFree(lay);
+            return fail(c, MD_ERR_CUDA, "cudaCreateTextureObject failed");
+        }
+    }
     int nl = 0;
     auto launch = [&]() -> int {
         if (variant == 0) return launch_force(d, c->lj, MD_MIXED, false, 1, EPI_F, false, false, c->st, &nl);
-        if (variant >= 3) return launch_study_tiles(d, c->lj, ntiles, variant == 4, fout, c->st, &nl);
-        return launch_study_force(d, c->lj, variant, lay, fout, c->st, &nl);
+        if (variant == 3 || variant == 4)
+            return launch_study_tiles(d, c->lj, ntiles, variant == 4, fout, c->st, &nl);
+        return launch_study_force(d, c->lj, variant, lay, tex, fout, c->st, &nl);
     };
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaEventCreate(&e0);
@@ -1630,6 +1657,7 @@ int md_study_force_variant(md_ctx *c, int32_t variant, int32_t reps, double *us,
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
+    if (tex) cudaDestroyTextureObject(tex);
     cudaFree(fout);
     cudaFree(lay);
     if (e != cudaSuccess && !rc) rc = fail(c, MD_ERR_CUDA, std::string("study: ") + cudaGetErrorString(e));

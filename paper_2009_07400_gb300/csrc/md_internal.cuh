@@ -382,13 +382,14 @@ int launch_rebuild_check(const Dev &d, cudaGraphConditionalHandle h, cudaStream_
 
 int64_t scan_tmp_elems(int64_t nkeys_total);
 
-// Force-kernel studies (k_study.cu): variants 1 (SoA gathers) and 2 (AoSoA
-// gathers) into fout; variants 3 and 4 (neighbourhood staged in shared
-// memory by plain loads / by TMA bulk copies, one block per 2x2x2-cell
-// tile).  Single replica, mixed path, full lists.
+// Force-kernel studies (k_study.cu): variants 1 (SoA gathers), 2 (AoSoA
+// gathers), 5 (gathers through the texture path) and 6 (half of them) into
+// fout; variants 3 and 4 (neighbourhood staged in shared memory by plain
+// loads / by TMA bulk copies, one block per 2x2x2-cell tile).  Single
+// replica, mixed path, full lists.
 int64_t study_layout_floats(int64_t n);
-int launch_study_force(const Dev &d, const LJ &lj, int variant, float *layouts, float4 *fout,
-                       cudaStream_t st, int *nlaunch);
+int launch_study_force(const Dev &d, const LJ &lj, int variant, float *layouts,
+                       cudaTextureObject_t tex, float4 *fout, cudaStream_t st, int *nlaunch);
 int launch_study_tiles(const Dev &d, const LJ &lj, int64_t ntiles, bool tma, float4 *fout,
                        cudaStream_t st, int *nlaunch);
 

@@ -75,7 +75,7 @@ with md.MDContext(s.pos, s.vel, s.box, precision=md.MD_MIXED) as c:
     out.append(h(c.positions(), c.velocities(), c.forces(), E, cnt))
 with md.MDContext(s.pos, s.vel, s.box, precision=md.MD_MIXED, threads_per_atom=1) as c:
     c.run(20)
-    out.append(h(*[c.study_force_variant(v, 1, forces=True)[1] for v in range(5)]))
+    out.append(h(*[c.study_force_variant(v, 1, forces=True)[1] for v in range(7)]))
 s4 = inputs.fcc_system(4, jitter=0.05, seed=2)
 with md.MDContext(s4.pos, s4.vel, s4.box, precision=md.MD_FP64) as c:
     loss, ge, gs, gx, gv = c.adjoint(20, 10, 10)

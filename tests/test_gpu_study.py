@@ -1,6 +1,7 @@
 """md_study_force_variant: the force-kernel variants that the design notes
 compare with the library's kernel compute the same forces.  SoA and AoSoA
-gathers run the library's arithmetic in its order (bitwise equal forces); the
+gathers, and gathers through the texture path, run the library's arithmetic
+in its order (bitwise equal forces); the
 shared-memory tile variant rounds differently (tile frame) and is held to
 the mixed path's tolerance against the oracle; staged by TMA bulk copies
 instead of loads it gives the same bits."""
@@ -48,7 +49,7 @@ def test_study_variants_agree(md, orc, case):
         F_lib = ctx.forces()
         us0, F0 = ctx.study_force_variant(0, 2, forces=True)
         assert us0 > 0 and np.array_equal(F0, F_lib)
-        for v in (1, 2):
+        for v in (1, 2, 5, 6):                   # layouts, texture-path gathers
             us, F = ctx.study_force_variant(v, 2, forces=True)
             assert us > 0 and np.array_equal(F, F0)
         _, F3 = ctx.study_force_variant(3, 2, forces=True)
@@ -70,5 +71,5 @@ def test_study_rejects_other_contexts(md, orc):
         assert e.value.code == md.MD_ERR_STATE
     with md.MDContext(s.pos, s.vel, s.box, precision=md.MD_MIXED) as ctx:
         with pytest.raises(md.MDError) as e:
-            ctx.study_force_variant(5, 1)
+            ctx.study_force_variant(7, 1)
         assert e.value.code == md.MD_ERR_INVAL
