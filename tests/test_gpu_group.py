@@ -101,10 +101,12 @@ def system_of(orc, case):
 def test_group_rows_exact(md, orc, case, g):
     """Exact per-atom rows from a group list: cells with 1..G members in their
     last group, boxes with 2 cells per edge (each periodic image visited
-    once), pairs on the edge of the list radius."""
+    once), pairs on the edge of the list radius; with whole and split cells."""
     s = system_of(orc, case)
     with md.MDContext(s.pos, s.vel, s.box, precision=md.MD_MIXED, list_type=g) as ctx:
         assert ctx.info().list_type == g
+        assert_rows_exact(orc, ctx, s.pos, s.box)
+        ctx.set_cell_split(1)          # groups then follow the octant order of a cell
         assert_rows_exact(orc, ctx, s.pos, s.box)
 
 

@@ -359,7 +359,8 @@ def test_overflow_recovery(md, orc):
 # Batched replicas (independent systems advanced together).
 # --------------------------------------------------------------------------
 
-def test_batched_replicas(md, orc):
+@pytest.mark.parametrize("split", [0, 1])
+def test_batched_replicas(md, orc, split):
     reps = inputs.replica_ensemble(6, seed=77, n_min=500, n_max=3000)
     pos = np.concatenate([r.pos for r in reps])
     vel = np.concatenate([r.vel for r in reps])
@@ -367,6 +368,7 @@ def test_batched_replicas(md, orc):
     boxes = [r.box for r in reps]
     for precision in (md.MD_FP64, md.MD_MIXED):
         with md.MDContext(pos, vel, boxes, counts=counts, precision=precision) as ctx:
+            ctx.set_cell_split(split)
             c_g, r_g = ctx.neighbors_raw()
             F = ctx.forces()
             o = 0
