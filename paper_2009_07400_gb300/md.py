@@ -394,9 +394,11 @@ class MDContext:
                                                rows.ctypes.data_as(_I32), cap))
         return [rows[i * cap:i * cap + counts[i]].copy() for i in range(self.n)]
 
-    def neighbors_raw(self):
-        """(counts[n], rows[n, cap]) of the current list, caller order."""
-        cap = self._row_cap()
+    def neighbors_raw(self, cap=None):
+        """(counts[n], rows[n, cap]) of the current list, caller order; cap
+        defaults to one that holds every row (MD_ERR_INVAL if a row exceeds a
+        given cap)."""
+        cap = cap or self._row_cap()
         counts = np.zeros(self.n, np.int32)
         rows = np.zeros((self.n, cap), np.int32)
         self._check(self._lib.md_get_neighbors(self._h, counts.ctypes.data_as(_I32),

@@ -446,6 +446,27 @@ def test_sizing_8m(md, orc, precision):
         assert rms_rel(F[ids], Fr) <= 1e-5
 
 
+def test_sizing_8m_wide_offsets(md, orc):
+    """The sizing workload with rows of capacity 520: capacity x atoms is
+    above 2^32, so the list build writes through 64-bit addresses (below it
+    uses 32-bit offsets from the row), and every reader of the list indexes
+    past 2^32 entries.  Sampled rows bit-exact and mixed forces within 1e-5
+    after one graph-replayed rebuild cycle."""
+    s = inputs.workload("fcc128_8388608")
+    with ctx_of(md, s, precision=md.MD_MIXED) as ctx:
+        ctx.set_capacity(520)
+        assert ctx.info().list_capacity * s.n >= 2 ** 32
+        ctx.run(20)
+        x = ctx.positions()
+        counts, rows = ctx.neighbors_raw(cap=ctx.info().max_neighbors + 8)
+        F = ctx.forces()
+    ids = np.random.default_rng(9).choice(s.n, 4096, replace=False)
+    c_o, r_o = orc.neighbors_sample(x, s.box, RC + SKIN, ids, cap=rows.shape[1])
+    assert np.array_equal(counts[ids], c_o)
+    assert np.array_equal(sorted_rows(counts[ids], rows[ids]), sorted_rows(c_o, r_o))
+    assert rms_rel(F[ids], orc.forces_sample(x, s.box, ids)) <= 1e-5
+
+
 def test_paper_gpu_shape_80(md, orc):
     """The paper's single-GPU workload shape (Sec. 6: FCC 80^3 unit cells,
     2,048,000 atoms, FP64, full lists, one thread per atom), after one
