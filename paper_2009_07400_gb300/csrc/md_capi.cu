@@ -758,6 +758,16 @@ std::mutex &tune_mutex()
     return m;
 }
 
+// Lanes per atom of the full-list force kernels from the atom count: the
+// choices md_autotune measured on GB300 for FCC liquids (mixed: 8 at 4k
+// atoms, 4 at ~16k, 2 at ~55k, 1 from 131k; FP64, bound by its FP64 pipe: 8
+// at 4k, 4 up to ~256k, 2 up to ~2M, 1 at 4M).
+int default_lanes(int64_t n, int32_t precision)
+{
+    if (precision == MD_MIXED) return n <= 8192 ? 8 : (n <= 32768 ? 4 : (n <= 98304 ? 2 : 1));
+    return n <= 8192 ? 8 : (n <= 393216 ? 4 : (n <= 3000000 ? 2 : 1));
+}
+
 // Switches lanes-per-atom / list type / cell split; a list-type or split
 // change rebins and rebuilds the list.
 int apply_tuning(md_ctx *c, int tpa, int lt, int split)
@@ -1394,8 +1404,12 @@ static int adjoint_impl(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt,
     const bool mixed = c->adj_prec < 0 ? is_mixed(c) : c->adj_prec == MD_MIXED;
     const int lt0 = c->p.list_type, tpa0 = c->tpa;
     int rc = MD_OK;
-    // the adjoint walks full per-atom lists
-    if (lt0 != MD_LIST_FULL && (rc = apply_tuning(c, tpa0, MD_LIST_FULL, c->split))) return rc;
+    // the adjoint walks full per-atom lists (with the default lanes per atom
+    // for the atom count when the context runs another list type, whose
+    // tuned lanes belong to that type: the group lists run one per atom)
+    if (lt0 != MD_LIST_FULL &&
+        (rc = apply_tuning(c, default_lanes(c->n, c->p.precision), MD_LIST_FULL, c->split)))
+        return rc;
 
     // workspace: reused between calls, grown when a call needs more
     auto &W = c->adj;
@@ -1445,12 +1459,21 @@ static int adjoint_impl(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt,
             cudaMemcpyAsync(c->p32[c->pb], ck_p + k * n, sizeof(float4) * n, cudaMemcpyDeviceToDevice, c->st);
     };
     // state at force point cb: the list of its epoch (built from the epoch's
-    // start positions, which re-binning reproduces bit for bit), then x, v
-    auto restore = [&](int64_t cb) -> int {
+    // start positions, which re-binning reproduces bit for bit), then x, v.
+    // check: the rebuild reads the device status back (overflow repair);
+    // else it is only enqueued (the forward sweep already built every list of
+    // the run with this capacity, so the same positions cannot overflow it;
+    // the status is read once after the reverse sweep).
+    auto restore = [&](int64_t cb, bool check) -> int {
         const int64_t e = cb - cb % every;
         load_ck(e / ckpt, true);
         c->moved_since_bin = true;
-        int r = rebuild_now(c, true);
+        int r;
+        if (check) {
+            r = rebuild_now(c, true);
+        } else if (!(r = enq_bin(c, &nl)) && !(r = enq_build(c, &nl))) {
+            c->rebuilds++;
+        }
         if (r) return r;
         if (e != cb) load_ck(cb / ckpt, false);
         return MD_OK;
@@ -1463,29 +1486,36 @@ static int adjoint_impl(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt,
     };
 
     // ---- forward, with checkpoints ---------------------------------------
-    if ((rc = rebuild_now(c, true))) return rc;
-    if ((rc = enq_force(c, EPI_F, false, &nl))) return rc;
-    save_ck(0);
-    CK(cudaMemsetAsync(&c->status->elog_cursor, 0, sizeof(int64_t), c->st));
-    for (int64_t s = 1; s <= nsteps && !rc; s++) {
-        if ((rc = kick_drift())) break;
-        if (s % every == 0) {
-            c->moved_since_bin = true;
-            if ((rc = rebuild_now(c, true))) break;
-        }
-        const bool en = s > nsteps - window;
-        if ((rc = enq_force(c, EPI_FK, en, &nl))) break;
-        if (en && (rc = enq_energy(c, true, nullptr, &nl))) break;
-        if (s % ckpt == 0) save_ck(s / ckpt);
-    }
+    // md_run's path: spans of fused steps replayed from the context's cached
+    // graphs (the same trajectory bit for bit as separate kick-drift and
+    // force launches), a span ending at every checkpoint and where the loss
+    // window starts (energies logged on every step inside it).  The status is
+    // read once at the end: a rebuild that overflowed stops every later
+    // kernel, and the forward then reruns from step 0 with a larger list.
     std::vector<double> elog((size_t)window * 3);
-    if (!rc) {
+    const int64_t w0 = nsteps - window;      // steps after w0 are in the loss window
+    for (int attempt = 0;; attempt++) {
+        if (attempt == 8) return fail(c, MD_ERR_NL_OVERFLOW, "neighbour list kept overflowing");
+        if ((rc = attempt == 0 ? rebuild_now(c, true) : restore(0, true))) return rc;
+        if ((rc = enq_force(c, EPI_F, false, &nl))) return rc;
+        save_ck(0);
+        CK(cudaMemsetAsync(&c->status->elog_cursor, 0, sizeof(int64_t), c->st));
+        std::vector<PlannedRebuild> planned;
+        for (int64_t s = 0; s < nsteps;) {
+            int64_t last = std::min<int64_t>((s / ckpt + 1) * ckpt, nsteps);
+            if (s < w0 && last > w0) last = w0;
+            if ((rc = run_span(c, s, s + 1, last, true, s >= w0 ? 1 : 0, &planned))) return rc;
+            s = last;
+            if (s % ckpt == 0) save_ck(s / ckpt);
+        }
         CK(cudaMemcpyAsync(elog.data(), c->elog_d, sizeof(double) * elog.size(), cudaMemcpyDeviceToHost, c->st));
-        CK(cudaStreamSynchronize(c->st));
         DevStatus st;
-        if (!(rc = read_status(c, &st))) rc = check_flags(c, st);
+        if ((rc = read_status(c, &st)) || (rc = check_flags(c, st))) return rc;
+        c->last_max = st.max_count;
+        if (!(st.flags & FLAG_NL_OVERFLOW)) break;
+        CK(cudaMemsetAsync(&c->status->flags, 0, sizeof(int32_t), c->st));
+        if ((rc = grow_list(c, st.max_count))) return rc;
     }
-    if (rc) return rc;
     double acc = 0;
     for (int64_t k = 0; k < window; k++) acc += elog[3 * k];
     *loss = acc / (double)window;
@@ -1500,7 +1530,7 @@ static int adjoint_impl(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt,
     for (int64_t b = nck - 1; b >= 0 && !rc; b--) {
         const int64_t cb = b * ckpt;
         const int64_t npts = (b == nck - 1) ? 1 : ckpt;
-        if ((rc = restore(cb))) break;
+        if ((rc = restore(cb, false))) break;
         if ((rc = enq_force(c, EPI_F, false, &nl))) break;
         for (int64_t m = 0; m < npts && !rc; m++) {
             if (m > 0) {
@@ -1530,6 +1560,12 @@ static int adjoint_impl(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt,
         }
     }
     if (!rc && launch_sum2(n, ge, gs, g2, c->st, &nl)) rc = fail(c, MD_ERR_CUDA, "sum launch failed");
+    if (!rc) {
+        // the reverse sweep's rebuilds and kernels, checked once
+        DevStatus st;
+        if (!(rc = read_status(c, &st)) && !(rc = check_flags(c, st)) && (st.flags & FLAG_NL_OVERFLOW))
+            rc = fail(c, MD_ERR_NL_OVERFLOW, "a recomputed list overflowed");
+    }
     if (!rc && on_device) {
         // gradients straight into the caller's device buffers (n x 3)
         if ((g_x0 && launch_unpad3(n, xbar, g_x0, c->st, &nl)) ||
@@ -1553,7 +1589,7 @@ static int adjoint_impl(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt,
             if (g_x0) { g_x0[3 * a] = hx[a].x; g_x0[3 * a + 1] = hx[a].y; g_x0[3 * a + 2] = hx[a].z; }
             if (g_v0) { g_v0[3 * a] = hw[a].x; g_v0[3 * a + 1] = hw[a].y; g_v0[3 * a + 2] = hw[a].z; }
         }
-        rc = restore(0);            // leave the context at the initial state
+        rc = restore(0, true);      // leave the context at the initial state
     }
     c->launches += nl;
     c->forces_valid = false;
@@ -1873,16 +1909,7 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
                 return fail(c, MD_ERR_NONFINITE, "non-finite input");
     }
     c->n = n;
-    if (q.threads_per_atom == 0) {
-        // lanes per atom of the full-list force kernels from the atom count:
-        // the choices md_autotune measured on GB300 for FCC liquids (mixed: 8
-        // at 4k atoms, 4 at ~16k, 2 at ~55k, 1 from 131k; FP64, bound by its
-        // FP64 pipe: 8 at 4k, 4 up to ~256k, 2 up to ~2M, 1 at 4M)
-        if (q.precision == MD_MIXED)
-            c->tpa = n <= 8192 ? 8 : (n <= 32768 ? 4 : (n <= 98304 ? 2 : 1));
-        else
-            c->tpa = n <= 8192 ? 8 : (n <= 393216 ? 4 : (n <= 3000000 ? 2 : 1));
-    }
+    if (q.threads_per_atom == 0) c->tpa = default_lanes(n, q.precision);
     c->ncells = cells;
     // whole cells: the split build (half-size cells) measured slower on the
     // LJ liquids (its lanes' octant runs diverge); md_set_cell_split and
