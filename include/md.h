@@ -385,7 +385,7 @@ int md_autotune(md_ctx *ctx, int32_t steps, md_params *chosen);
  * side (with a margin of 1e-3 s for the FP32 half decisions).  The lists hold
  * the same pairs with either split (only the order of a cell's entries, and
  * so the rounding of the force sums, changes).  split = 0: whole cells.
- * Default: 0 (on the 1M-atom LJ liquid split cells take 63 against 44 us of
+ * Default: 0 (on the 1M-atom LJ liquid split cells take 61 against 37 us of
  * neighbour work per step: lanes of a warp keep different octants, and the
  * warp scans the union of their runs).  A change rebins, rebuilds the list
  * and recomputes the forces of the current state.
