@@ -44,8 +44,17 @@ __device__ __forceinline__ double rcp64(double a)
     return fma(r, fma(-a, r, 1.0), r);
 }
 
+// FP32 reciprocal on the special-function unit (relative error below 2^-22,
+// as in the mixed force kernel).
+__device__ __forceinline__ float rcp_approx(float a)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+
 struct AdjArgs {
-    const float4 *wbar32; // FP32 copy of wbar (mixed path)
+    const float4 *wbar32; // FP32 copy of wbar in slot order (mixed path)
     const dvec4 *wbar;   // dloss/dw (caller order)
     dvec4 *xbar;         // dloss/dx carry (caller order), updated
     double *g_eps;       // per-atom accumulators (caller order)
@@ -154,9 +163,11 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs(Dev d, LJ lj, AdjArgs a)
 }
 
 // Mixed path: the same pair terms in FP32 (geometry from the cell-relative
-// FP32 positions, the neighbour's adjoint from an FP32 copy), summed per atom
-// in FP32 and added to the FP64 adjoint state once per atom.  The FP64 pipe
-// then only sees the per-atom updates.
+// FP32 positions, the neighbour's adjoint from an FP32 copy that the axpy
+// kernel writes in slot order, so it is gathered like the positions: one
+// local 16-byte load per pair instead of the caller id and a scattered
+// load), summed per atom in FP32 and added to the FP64 adjoint state once
+// per atom.  The FP64 pipe then only sees the per-atom updates.
 template <bool WINDOW, int TPA>
 __global__ void __launch_bounds__(128) k_adjoint_pairs_f32(Dev d, LJ lj, AdjArgs a)
 {
@@ -170,7 +181,7 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs_f32(Dev d, LJ lj, AdjArgs
     const Rep &R = d.reps[0];
     const int32_t idi = d.id[i];
     const float4 pi = d.p32[i];
-    const float4 ui = a.wbar32[idi];
+    const float4 ui = a.wbar32[i];
     const int cnt = valid && MD_CHECK(d, d.nb_count[i] <= d.cap) ? d.nb_count[i] : 0;
     const int4 *nb4 = reinterpret_cast<const int4 *>(d.nb);
     const float eps = (float)lj.eps, sig6 = lj.sigma6f;
@@ -188,18 +199,18 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs_f32(Dev d, LJ lj, AdjArgs
         const uint32_t e = (uint32_t)es[t4];
         const uint32_t c = e >> kJBits;
         const int32_t j = (int32_t)(e & kJMask);
-        if (!MD_CHECK(d, j <= d.n)) continue;
+        if (!MD_CHECK(d, j < d.n)) continue;
         const float4 pj = d.p32[j];
         const float dx = ((c & 2u) ? qx2 : ((c & 1u) ? pi.x : qx0)) - pj.x;
         const float dy = ((c & 8u) ? qy2 : ((c & 4u) ? pi.y : qy0)) - pj.y;
         const float dz = ((c & 32u) ? qz2 : ((c & 16u) ? pi.z : qz0)) - pj.z;
         const float rsq = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
         if (!(rsq < lj.rc2f)) continue;
-        const float sr2 = 1.0f / rsq;
+        const float sr2 = rcp_approx(rsq);
         const float t = sr2 * sr2 * sr2 * sig6;
         const float f = 48.0f * eps * t * (t - 0.5f) * sr2;
         const float fp = 48.0f * eps * sr2 * sr2 * t * (2.0f - 7.0f * t);
-        const float4 uj = a.wbar32[d.id[j]];
+        const float4 uj = a.wbar32[j];
         const float dux = ui.x - uj.x, duy = ui.y - uj.y, duz = ui.z - uj.z;
         const float ddu = fmaf(dz, duz, fmaf(dy, duy, dx * dux));
         jx += f * dux + 2.0f * fp * dx * ddu;
@@ -244,18 +255,22 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs_f32(Dev d, LJ lj, AdjArgs
     a.g_sig[idi] += a.k * (double)gs + a.lw * (double)pe_s;
 }
 
+// wbar += dt xbar (caller order) for the atom in slot s, and the FP32 copy
+// of the result into slot s (the current slot order, id: slot -> caller id).
 __global__ void __launch_bounds__(256) k_adjoint_axpy(int64_t n, double dt, const dvec4 *xbar,
-                                                      dvec4 *wbar, float4 *wbar32)
+                                                      dvec4 *wbar, float4 *wbar32,
+                                                      const int32_t *id)
 {
-    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= n) return;
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int64_t a = id[s];
     dvec4 w = wbar[a];
     const dvec4 x = xbar[a];
     w.x = fma(dt, x.x, w.x);
     w.y = fma(dt, x.y, w.y);
     w.z = fma(dt, x.z, w.z);
     wbar[a] = w;
-    if (wbar32) wbar32[a] = make_float4((float)w.x, (float)w.y, (float)w.z, 0.f);
+    if (wbar32) wbar32[s] = make_float4((float)w.x, (float)w.y, (float)w.z, 0.f);
 }
 
 // out (n x 3 doubles) <- a (padded FP64 3-vectors), same atom order.
@@ -320,9 +335,9 @@ int launch_adjoint_pairs(const Dev &d, const LJ &lj, bool mixed, int lanes, cons
 }
 
 int launch_adjoint_axpy(int64_t n, double dt, const dvec4 *xbar, dvec4 *wbar, float4 *wbar32,
-                        cudaStream_t st, int *nl)
+                        const int32_t *id, cudaStream_t st, int *nl)
 {
-    k_adjoint_axpy<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, dt, xbar, wbar, wbar32);
+    k_adjoint_axpy<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, dt, xbar, wbar, wbar32, id);
     *nl += 1;
     return (int)cudaGetLastError();
 }

@@ -1542,7 +1542,8 @@ static int adjoint_impl(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt,
         }
         for (int64_t m = npts - 1; m >= 0 && !rc; m--) {
             const int64_t pt = cb + m;
-            if (pt < nsteps && launch_adjoint_axpy(n, c->lj.dt, xbar, wbar, wbar32, c->st, &nl)) {
+            if (pt < nsteps &&
+                launch_adjoint_axpy(n, c->lj.dt, xbar, wbar, wbar32, c->id[c->vp], c->st, &nl)) {
                 rc = fail(c, MD_ERR_CUDA, "adjoint launch failed");
                 break;
             }

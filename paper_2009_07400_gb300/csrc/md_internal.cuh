@@ -405,15 +405,17 @@ int launch_decode_group(const Dev &d, const LJ &lj, int G, int32_t *counts_dev, 
                         int32_t cap, cudaStream_t st, int *nlaunch);
 
 // Adjoint (k_adjoint.cu)
-// mixed: FP32 pair terms reading wbar32 (an FP32 copy of wbar kept by the
-// axpy kernel); FP64 path: wbar32 may be null.
+// mixed: FP32 pair terms reading wbar32 (an FP32 copy of wbar in slot order
+// kept by the axpy kernel); FP64 path: wbar32 may be null.
 // lanes: 1, 2, 4 or 8 lanes per atom (the context's lanes per atom: several
 // lanes keep small systems from leaving SMs idle)
 int launch_adjoint_pairs(const Dev &d, const LJ &lj, bool mixed, int lanes, const dvec4 *wbar,
                          const float4 *wbar32, dvec4 *xbar, double *g_eps, double *g_sig,
                          double k, double lw, cudaStream_t st, int *nlaunch);
+// wbar += dt xbar (caller order); wbar32 (may be null) <- its FP32 copy in
+// the slot order of id (slot -> caller id)
 int launch_adjoint_axpy(int64_t n, double dt, const dvec4 *xbar, dvec4 *wbar, float4 *wbar32,
-                        cudaStream_t st, int *nlaunch);
+                        const int32_t *id, cudaStream_t st, int *nlaunch);
 int launch_sum2(int64_t n, const double *a, const double *b, double *out, cudaStream_t st,
                 int *nlaunch);
 int launch_unpad3(int64_t n, const dvec4 *a, double *out, cudaStream_t st, int *nlaunch);
