@@ -1537,8 +1537,13 @@ static int adjoint_impl(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt,
                 if ((rc = kick_drift())) break;
                 if ((rc = enq_force(c, EPI_FK, false, &nl))) break;
             }
-            cudaMemcpyAsync(blk_x + m * n, c->x[c->xp], sizeof(dvec4) * n, cudaMemcpyDeviceToDevice, c->st);
-            cudaMemcpyAsync(blk_p + m * n, c->p32[c->pb], sizeof(float4) * n, cudaMemcpyDeviceToDevice, c->st);
+            // the snapshot the pair terms read: FP32 cell-relative positions
+            // (mixed pair terms) or FP64 positions (FP64 pair terms, which
+            // take only the cell coordinates from p32: fixed for the epoch)
+            if (mixed)
+                cudaMemcpyAsync(blk_p + m * n, c->p32[c->pb], sizeof(float4) * n, cudaMemcpyDeviceToDevice, c->st);
+            else
+                cudaMemcpyAsync(blk_x + m * n, c->x[c->xp], sizeof(dvec4) * n, cudaMemcpyDeviceToDevice, c->st);
         }
         for (int64_t m = npts - 1; m >= 0 && !rc; m--) {
             const int64_t pt = cb + m;
@@ -1552,8 +1557,8 @@ static int adjoint_impl(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt,
             // the pair terms read the recomputed snapshot of force point pt
             // in place (same atom order and list as the whole block)
             Dev dv = view(c);
-            dv.x = blk_x + m * n;
-            dv.p32 = blk_p + m * n;
+            if (mixed) dv.p32 = blk_p + m * n;
+            else dv.x = blk_x + m * n;
             if (launch_adjoint_pairs(dv, c->lj, mixed, c->tpa, wbar, wbar32, xbar, ge, gs, k, lw, c->st, &nl)) {
                 rc = fail(c, MD_ERR_CUDA, "adjoint launch failed");
                 break;
