@@ -1533,10 +1533,13 @@ static int adjoint_impl(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt,
         if ((rc = restore(cb, false))) break;
         if ((rc = enq_force(c, EPI_F, false, &nl))) break;
         for (int64_t m = 0; m < npts && !rc; m++) {
-            if (m > 0) {
-                if ((rc = kick_drift())) break;
-                if ((rc = enq_force(c, EPI_FK, false, &nl))) break;
-            }
+            // the state at point cb + m, by the forward's own launches: a
+            // kick-drift with the forces of cb for the first step of the block,
+            // then one fused step per point (force at the previous point, both
+            // half kicks, drift), so the recompute is the forward bit for bit
+            if (m == 1) rc = kick_drift();
+            else if (m > 1) rc = enq_force(c, EPI_FKKD, false, &nl);
+            if (rc) break;
             // the snapshot the pair terms read: FP32 cell-relative positions
             // (mixed pair terms) or FP64 positions (FP64 pair terms, which
             // take only the cell coordinates from p32: fixed for the epoch)
