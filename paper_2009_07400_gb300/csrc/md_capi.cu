@@ -1464,8 +1464,17 @@ static int adjoint_impl(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt,
     // else it is only enqueued (the forward sweep already built every list of
     // the run with this capacity, so the same positions cannot overflow it;
     // the status is read once after the reverse sweep).
+    // list_epoch: the epoch whose list (and slot order) the context holds, or
+    // -1.  A block of an epoch whose list is built only loads its checkpoint
+    // (saved in that slot order): x, v and the FP32 positions.
+    int64_t list_epoch = -1;
     auto restore = [&](int64_t cb, bool check) -> int {
         const int64_t e = cb - cb % every;
+        if (!check && e == list_epoch) {
+            load_ck(cb / ckpt, false);
+            c->forces_valid = false;
+            return MD_OK;
+        }
         load_ck(e / ckpt, true);
         c->moved_since_bin = true;
         int r;
@@ -1475,6 +1484,7 @@ static int adjoint_impl(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt,
             c->rebuilds++;
         }
         if (r) return r;
+        list_epoch = check ? -1 : e;
         if (e != cb) load_ck(cb / ckpt, false);
         return MD_OK;
     };
@@ -1521,6 +1531,8 @@ static int adjoint_impl(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt,
     *loss = acc / (double)window;
 
     // ---- reverse sweep ------------------------------------------------------
+    // the forward ended on the list of its last epoch, in that slot order
+    list_epoch = nsteps - nsteps % every;
     CK(cudaMemsetAsync(xbar, 0, sizeof(dvec4) * n, c->st));
     CK(cudaMemsetAsync(wbar, 0, sizeof(dvec4) * n, c->st));
     if (wbar32) CK(cudaMemsetAsync(wbar32, 0, sizeof(float4) * n, c->st));
