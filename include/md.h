@@ -389,8 +389,10 @@ int md_autotune(md_ctx *ctx, int32_t steps, md_params *chosen);
  * neighbour work per step: lanes of a warp keep different octants, and the
  * warp scans the union of their runs).  A change rebins, rebuilds the list
  * and recomputes the forces of the current state.
+ * The cell arrays grow to 8 entries per cell the first time cells are split.
  * Not in the paper as an option; its cells are the split = 0 ones.
- * Errors: MD_ERR_INVAL (split not 0 or 1), MD_ERR_CUDA. */
+ * Errors: MD_ERR_INVAL (split not 0 or 1; split = 1 on boxes of 2^28 or more
+ * cells, whose keys would not fit 31 bits), MD_ERR_NOMEM, MD_ERR_CUDA. */
 int md_set_cell_split(md_ctx *ctx, int32_t split);
 
 /* Allocation-free FP64 totals: out3[0] = sum pe_atom, out3[1] = 1/2 mass

@@ -86,6 +86,7 @@ struct md_ctx {
     int32_t *cell_key = nullptr, *cell_count = nullptr, *cell_start = nullptr, *perm = nullptr;
     int32_t *scan_tmp = nullptr;
     int64_t scan_len = 0;
+    int64_t key_cap = 0;    // binning keys the cell arrays hold (nids, or 8 nids once split)
     int32_t *nb = nullptr, *nb_count = nullptr;
     int32_t cap = 0;
     // list shared by groups of gsz atoms (list types 2 and 4): group table,
@@ -768,11 +769,44 @@ int default_lanes(int64_t n, int32_t precision)
     return n <= 8192 ? 8 : (n <= 393216 ? 4 : (n <= 3000000 ? 2 : 1));
 }
 
+// Cell arrays large enough for the binning keys of `split` (8 per cell id
+// when split; keys 8 c + octant must stay below 2^31).  Synchronises.
+int ensure_key_arrays(md_ctx *c, int split)
+{
+    const int64_t want = split ? c->nids * 8 : c->nids;
+    if (split && want >= ((int64_t)1 << 31)) return fail(c, MD_ERR_INVAL, "too many cells to split");
+    if (want <= c->key_cap) return MD_OK;
+    CK(cudaStreamSynchronize(c->st));
+    int32_t *cnt = nullptr, *start = nullptr, *tmp = nullptr;
+    const int64_t tlen = scan_tmp_elems(want);
+    int rc;
+    if ((rc = dalloc(c, &cnt, (size_t)want)) || (rc = dalloc(c, &start, (size_t)want + 1)) ||
+        (rc = dalloc(c, &tmp, (size_t)tlen))) {
+        cudaFree(cnt); cudaFree(start); cudaFree(tmp);
+        return rc;
+    }
+    CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)want, c->st));
+    cudaFree(c->cell_count); cudaFree(c->cell_start); cudaFree(c->scan_tmp);
+    c->cell_count = cnt;
+    c->cell_start = start;
+    c->scan_tmp = tmp;
+    c->scan_len = tlen;
+    c->key_cap = want;
+    // captured graphs hold the old arrays
+    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+    c->graphs.clear();
+    return MD_OK;
+}
+
 // Switches lanes-per-atom / list type / cell split; a list-type or split
 // change rebins and rebuilds the list.
 int apply_tuning(md_ctx *c, int tpa, int lt, int split)
 {
     const bool relist = lt != c->p.list_type || split != c->split;
+    if (split != c->split) {
+        const int rc = ensure_key_arrays(c, split);
+        if (rc) return rc;
+    }
     c->split = split;
     c->tpa = tpa;
     c->p.threads_per_atom = tpa;
@@ -1222,6 +1256,8 @@ int md_set_cell_split(md_ctx *c, int32_t split)
     if (!c || (split != 0 && split != 1)) return fail(c, MD_ERR_INVAL, "split must be 0 or 1");
     if (split == c->split) return MD_OK;
     CK(cudaStreamSynchronize(c->st));
+    int rc = ensure_key_arrays(c, split);
+    if (rc) return rc;
     c->split = split;
     // new binning keys: rebin and rebuild (the rows hold the same pairs; the
     // order of a cell's entries, and so the force sums' rounding, changes)
@@ -1810,7 +1846,8 @@ int md_autotune(md_ctx *c, int32_t steps, md_params *chosen)
         if ((rc = time_one(k, split0, &ms))) break;
         if (ms < best) { best = ms; best_k = k; }
     }
-    if (!rc) {
+    // (split cells need their binning keys 8 c + octant below 2^31)
+    if (!rc && (split0 == 1 || c->nids * 8 < ((int64_t)1 << 31))) {
         float ms = 0;
         if (!(rc = time_one(best_k, 1 - split0, &ms)) && ms < best) {
             best = ms;
@@ -1973,13 +2010,14 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
     }
     if ((rc = dalloc(c, &c->f64, N))) return rc;
     if ((rc = dalloc(c, &c->cell_key, N))) return rc;
-    // binning keys: 8 per cell id (cells split into octants) or 1; the
-    // arrays hold the split layout either way, so the split can change
-    if ((rc = dalloc(c, &c->cell_count, (size_t)ids * 8))) return rc;
-    if ((rc = dalloc(c, &c->cell_start, (size_t)ids * 8 + 1))) return rc;
+    // binning keys: one per cell id (whole cells); md_set_cell_split grows
+    // the arrays to 8 per cell id when cells are split
+    if ((rc = dalloc(c, &c->cell_count, (size_t)ids))) return rc;
+    if ((rc = dalloc(c, &c->cell_start, (size_t)ids + 1))) return rc;
     if ((rc = dalloc(c, &c->perm, N))) return rc;
-    c->scan_len = scan_tmp_elems(ids * 8);
+    c->scan_len = scan_tmp_elems(ids);
     if ((rc = dalloc(c, &c->scan_tmp, (size_t)c->scan_len))) return rc;
+    c->key_cap = ids;
     if ((rc = dalloc(c, &c->nb_count, N))) return rc;
     if ((rc = dalloc(c, &c->pe_atom, N))) return rc;
     if ((rc = dalloc(c, &c->w_atom, N))) return rc;
@@ -2025,7 +2063,7 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
     CK(cudaMemcpyAsync(c->rep_of_d, rep_of.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, c->st));
     CK(cudaMemcpyAsync(c->chunk_rep_d, chunk_rep.data(), sizeof(int64_t) * chunk_rep.size(), cudaMemcpyHostToDevice, c->st));
     CK(cudaMemcpyAsync(c->chunk_first_d, chunk_first.data(), sizeof(int64_t) * chunk_first.size(), cudaMemcpyHostToDevice, c->st));
-    CK(cudaMemsetAsync(c->cell_count, 0, sizeof(int32_t) * (size_t)ids * 8, c->st));
+    CK(cudaMemsetAsync(c->cell_count, 0, sizeof(int32_t) * (size_t)ids, c->st));
     CK(cudaMemsetAsync(c->status, 0, sizeof(DevStatus), c->st));
     CK(cudaMemsetAsync(c->f32, 0, sizeof(float4) * N, c->st));
     CK(cudaMemsetAsync(c->f64, 0, sizeof(dvec4) * N, c->st));

@@ -530,6 +530,21 @@ def test_cell_split_switch(md, orc):
             assert e.value.code == md.MD_ERR_INVAL
 
 
+def test_cell_split_refused_on_huge_boxes(md, orc):
+    """Split binning keys are 8 c + octant in 31 bits: a box of 645 cells per
+    edge (646^3 >= 2^28 cell ids with the 2-cell tiles) refuses split cells
+    with MD_ERR_INVAL and keeps running with whole cells."""
+    L = np.full(3, 645 * (RC + SKIN) + 1.0)
+    pos = np.array([[10.0, 10.0, 10.0], [11.2, 10.0, 10.0]])
+    with md.MDContext(pos, np.zeros_like(pos), L) as ctx:
+        with pytest.raises(md.MDError) as e:
+            ctx.set_cell_split(1)
+        assert e.value.code == md.MD_ERR_INVAL
+        assert ctx.info().cell_split == 0
+        ctx.run(5)
+        assert np.isfinite(ctx.positions()).all()
+
+
 def test_ensemble_256_sampled(md, orc):
     """The 256-replica ensemble (about 1.4 M atoms in one context, the
     batched benchmark workload) after one graph-replayed rebuild cycle:
