@@ -263,3 +263,26 @@ def test_adjoint_workspace_reuse(md, small):
             ref = run(ctx, a)
         assert got[0] == ref[0] and got[1] == ref[1] and got[2] == ref[2]
         assert np.array_equal(got[3], ref[3]) and np.array_equal(got[4], ref[4])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_adjoint_list_overflow_reruns(md, orc, precision):
+    """A list that overflows during the forward sweep is found after the
+    sweep, which reruns from step 0 with a larger list: loss and gradients
+    bit for bit those of a context with room to spare (the capacity changes
+    neither the rows nor their order).  A perfect FCC lattice has rows of
+    exactly 78 (capacity 80); its sixth shell (2.909 sigma) lies just
+    outside rc + skin, so once the atoms move the rows built at step 20
+    outgrow it."""
+    s = inputs.fcc_system(5, jitter=0.0, seed=43)         # 500 atoms, T 1.44
+    x0, v0, L = s.pos, s.vel, s.box
+    prec = md.MD_FP64 if precision == "fp64" else md.MD_MIXED
+    with md.MDContext(x0, v0, L, precision=prec, rebuild_every=20) as ref:
+        want = ref.adjoint(100, 20, 10)
+    with md.MDContext(x0, v0, L, precision=prec, rebuild_every=20) as ctx:
+        ctx.set_capacity(ctx.info().max_neighbors)
+        cap0 = ctx.info().list_capacity
+        got = ctx.adjoint(100, 20, 10)
+        assert ctx.info().list_capacity > cap0          # the sweep overflowed and grew it
+    assert got[0] == want[0] and got[1] == want[1] and got[2] == want[2]
+    assert np.array_equal(got[3], want[3]) and np.array_equal(got[4], want[4])
