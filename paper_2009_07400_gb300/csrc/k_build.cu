@@ -30,6 +30,12 @@
 // cells per dimension need no de-duplication: at most one image of an atom
 // lies within rs < L/2.
 //
+// Split cells (optional, md_set_cell_split): the binning orders each cell's
+// atoms by octant, and a neighbour cell is scanned as the runs of its
+// octants that can hold a pair (the half-size cells of Sec. 3.2's footnote
+// with their wider stencil); the rows hold the same pairs as with whole
+// cells.
+//
 // Layout: entries of atom i are int4 chunks, chunk q at int4 index q*n + i;
 // the last chunk of a row is padded with entries pointing at the far-away
 // sentinel slot n.  Rows longer than the capacity are counted but not stored
