@@ -79,11 +79,16 @@ def test_trajectory_fp64(md, orc, every):
     assert E[2, 0, 0] + E[2, 0, 1] < 0.8 * (E[0, 0, 0] + E[0, 0, 1])   # the gas cools
 
 
-def test_trajectory_mixed(md, orc):
+@pytest.mark.parametrize("split", [0, 1])
+def test_trajectory_mixed(md, orc, split):
+    """Mixed path against the oracle's run; also with split cells (the
+    binning then orders each cell's spheres by octant and reorders the FP32
+    velocity copies with them)."""
     x, v, L = dense(seed=9, n=400)
     kw = dict(k_spring=200.0, gamma=2.0, sigma=SIG, cutoff=SIG, skin=SKIN, dt=0.001)
     xr, vr, _, Er = orc.vv_run(x, v, L, 200, energies=True, potential=1, **kw)
     with sd_ctx(md, x, v, L, 200.0, 2.0, precision=md.MD_MIXED, dt=0.001) as ctx:
+        ctx.set_cell_split(split)
         E = ctx.run(200, energy_every=200)
         d = np.mod(ctx.positions() - xr + L / 2, L) - L / 2
         assert np.abs(d).max() < 1e-4
