@@ -286,3 +286,20 @@ def test_adjoint_list_overflow_reruns(md, orc, precision):
         assert ctx.info().list_capacity > cap0          # the sweep overflowed and grew it
     assert got[0] == want[0] and got[1] == want[1] and got[2] == want[2]
     assert np.array_equal(got[3], want[3]) and np.array_equal(got[4], want[4])
+
+
+def test_adjoint_with_split_cells(md, orc, small):
+    """FP64 adjoint on a context whose build scans split cells (its checkpoint
+    restores rebin by octant): the same loss and gradients as with whole
+    cells, up to the summation order of the rows (round-off)."""
+    x0, v0, L = small
+    out = []
+    for split in (0, 1):
+        with md.MDContext(x0, v0, L, precision=md.MD_FP64, rebuild_every=20) as ctx:
+            ctx.set_cell_split(split)
+            out.append(ctx.adjoint(60, 20, 10))
+    (l0, e0, s0, gx0, gv0), (l1, e1, s1, gx1, gv1) = out
+    assert l1 == pytest.approx(l0, rel=1e-12)
+    assert e1 == pytest.approx(e0, rel=1e-10) and s1 == pytest.approx(s0, rel=1e-10)
+    assert np.linalg.norm(gx1 - gx0) <= 1e-9 * np.linalg.norm(gx0)
+    assert np.linalg.norm(gv1 - gv0) <= 1e-9 * np.linalg.norm(gv0)
