@@ -667,12 +667,15 @@ def _mi(d, L):
     return np.mod(d + L / 2, L) - L / 2
 
 
-@pytest.mark.parametrize("half", [False, True])
-def test_displacement_trigger_fp64(md, orc, half):
-    """FP64 path, the 2,048-atom FCC workload at T = 1.44, 200 steps."""
+@pytest.mark.parametrize("half,split", [(False, 0), (True, 0), (False, 1)])
+def test_displacement_trigger_fp64(md, orc, half, split):
+    """FP64 path, the 2,048-atom FCC workload at T = 1.44, 200 steps; with
+    split cells the conditional rebuilds inside the step graphs bin by
+    octant."""
     s = inputs.workload("fcc8_2048")
     x_ref, v_ref, F_ref = orc.vv_run(s.pos, s.vel, s.box, 200, rebuild_every=1)
     with ctx_of(md, s, precision=md.MD_FP64, half_list=half, rebuild_every=0) as ctx:
+        ctx.set_cell_split(split)
         r0 = ctx.info().rebuilds
         ctx.run(200)
         nreb = ctx.info().rebuilds - r0
