@@ -92,7 +92,7 @@ __global__ void k_rebuild_check(DevStatus *st, cudaGraphConditionalHandle h)
     cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
-constexpr int kChunk = 4096;   // atoms per reduction chunk
+constexpr int kChunk = 1024;   // atoms per reduction chunk (1024: a 16k-atom system still fills 16 blocks)
 
 // Per-chunk FP64 partial sums of (PE, KE, W).  Chunks never straddle
 // replicas: chunk c of replica r covers atoms [off_r + c*kChunk, ...).
