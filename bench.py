@@ -316,6 +316,21 @@ def run_gpu(args):
         res["fp64_ms"] = ms64 / fp64_cycles
         res["prof64"] = ctx.profile(STEPS_PER_CYCLE)
         res["fp64_state"] = (ctx.positions(), ctx.forces())
+    # double-word pair arithmetic (MD_DW): FP64-class forces on the FP32 pipe;
+    # full per-atom lists, lanes per atom from the autotuner (one lane on the
+    # paper-shaped workload, as its FP64 leg)
+    dw_kw = dict(threads_per_atom=1) if paper_shaped else {}
+    with make(precision=md.MD_DW, **dw_kw) as ctx:
+        if paper_shaped:
+            res["tuned_dw"] = {"threads_per_atom": 1, "list_type": 0, "paper_shaped": True}
+        else:
+            tdw = ctx.autotune(STEPS_PER_CYCLE)
+            res["tuned_dw"] = {"threads_per_atom": tdw.threads_per_atom,
+                               "list_type": int(tdw.list_type)}
+        msdw, _ = time_cycles(ctx, fp64_cycles, 1, dist, torch, timesteps=STEPS_PER_CYCLE)
+        res["dw_ms"] = msdw / fp64_cycles
+        res["prof_dw"] = ctx.profile(STEPS_PER_CYCLE)
+        res["dw_state"] = (ctx.positions(), ctx.forces())
     # end to end through the C ABI with host buffers, every step: the state
     # (positions and velocities) from pinned host memory -> md_set_state ->
     # one benchmark step (200 time steps) -> positions and velocities back
@@ -349,8 +364,9 @@ def run_gpu(args):
             dist.barrier()
     nrep = 1 if counts is None else len(counts)
 
-    mixed_ms, fp64_ms, e2e_s = mdist.max_over_ranks(
-        [res["mixed_ms"], res["fp64_ms"], e2e_s], dist, device="cuda" if dist else None)
+    mixed_ms, fp64_ms, dw_ms, e2e_s = mdist.max_over_ranks(
+        [res["mixed_ms"], res["fp64_ms"], res["dw_ms"], e2e_s], dist,
+        device="cuda" if dist else None)
     n_total = n * world
     if dist and sharded:     # the ranks hold different parts of the ensemble
         t = torch.tensor([n], dtype=torch.int64, device="cuda")
@@ -358,6 +374,7 @@ def run_gpu(args):
         n_total = int(t.item())
     value = n_total * TIMESTEPS_PER_STEP * args.steps / (mixed_ms / 1e3)
     fp64_value = n_total * STEPS_PER_CYCLE / (fp64_ms / 1e3)
+    dw_value = n_total * STEPS_PER_CYCLE / (dw_ms / 1e3)
     e2e_value = n_total * TIMESTEPS_PER_STEP * e_steps / e2e_s
     if rank == 0:
         prof = res["prof"]
@@ -399,7 +416,16 @@ def run_gpu(args):
                               "force": res["prof64"].force_ms / res["prof64"].steps,
                               "neigh": res["prof64"].neigh_ms / res["prof64"].steps,
                               "other": res["prof64"].other_ms / res["prof64"].steps}},
+            "dw_path": {"value": dw_value, "ms_per_step": dw_ms, "tuned": res["tuned_dw"],
+                        "note": "MD_DW: pair arithmetic in double word (two FP32 numbers per "
+                                "quantity) on the FP32 pipe, FP64 integration; forces within "
+                                "1e-11 of the FP64 oracle (force_error.dw_max_rel)",
+                        "phases_ms_per_timestep": {
+                            "force": res["prof_dw"].force_ms / res["prof_dw"].steps,
+                            "neigh": res["prof_dw"].neigh_ms / res["prof_dw"].steps,
+                            "other": res["prof_dw"].other_ms / res["prof_dw"].steps}},
             "speedup_mixed_over_fp64": value / fp64_value,
+            "speedup_dw_over_fp64": dw_value / fp64_value,
             "displacement_trigger": {
                 "value": n_total * STEPS_PER_CYCLE / (res["disp_ms"] / 1e3), "unit": UNIT,
                 "rebuilds_per_100_steps": 100.0 * res["disp_rebuilds"],
@@ -484,7 +510,8 @@ def cpu_baseline_leg(pos, vel, box, counts, res):
                                   f"{t_step1:.3f} s per step"}}}
     rng = np.random.default_rng(0)
     errs = {}
-    for key, name in (("mixed_state", "mixed_rms_rel"), ("fp64_state", "fp64_max_rel")):
+    for key, name in (("mixed_state", "mixed_rms_rel"), ("fp64_state", "fp64_max_rel"),
+                      ("dw_state", "dw_max_rel")):
         x, F = res[key]
         Fg, Fr = [], []
         per = 2048 // len(systems[:4])
@@ -906,8 +933,8 @@ def run_ncu_case(which, pin=None):
         torch.cuda.synchronize()
         return
     s = inputs.workload(WORKLOAD)
-    prec = md.MD_MIXED if which == "mixed" else md.MD_FP64
-    kw = (pin[0] if which == "mixed" else pin[1]) if pin else {}
+    prec = {"mixed": md.MD_MIXED, "fp64": md.MD_FP64, "dw": md.MD_DW}[which]
+    kw = ((pin[0] if which == "mixed" else pin[1]) if pin and which != "dw" else {})
     with md.MDContext(s.pos, s.vel, s.box, precision=prec, **kw) as ctx:
         ctx.run(2 * STEPS_PER_CYCLE)
     torch.cuda.synchronize()
@@ -929,7 +956,7 @@ def main():
                     help="skip the autotuner and use these lanes per atom and list "
                          "types for the mixed and FP64 legs (for profiling commands)")
     ap.add_argument("--cellorder-child", type=int, choices=[1, 2, 4], help=argparse.SUPPRESS)
-    ap.add_argument("--ncu-case", choices=["mixed", "fp64", "dem"],
+    ap.add_argument("--ncu-case", choices=["mixed", "fp64", "dw", "dem"],
                     help="only build the workload and run 2 rebuild cycles (a short, "
                          "fixed launch sequence for an ncu capture); prints nothing")
     args = ap.parse_args()

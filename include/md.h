@@ -55,6 +55,14 @@ extern "C" {
 
 #define MD_FP64 0   /* every arithmetic step in FP64 */
 #define MD_MIXED 1  /* FP32 pair arithmetic with Kahan sums; FP64 integration and reductions */
+#define MD_DW 2     /* pair arithmetic (Eq. 2) in double word: each quantity an unevaluated
+                       sum of two FP32 numbers (~48 significant bits), on the FP32 pipe;
+                       forces agree with FP64 to ~1e-13; FP64 integration and reductions.
+                       Positions relative to the cell centre are split into a high part
+                       on a power-of-two grid and a low part at each binning and step;
+                       an atom that moves more than a cell side beyond its cell between
+                       binnings stops the run with MD_ERR_BADPOS.  Full per-atom lists
+                       only (MD_LIST_FULL); no contact model, no md_adjoint.          */
 
 /* Verlet-list layouts (md_params.list_type).  All hold every pair with
  * r^2 < (rc + skin)^2 at the build (Sec. 3.2, Fig. 1); md_get_neighbors
@@ -87,7 +95,7 @@ typedef struct {
                                 pairs inside rc; checked on the device each step,
                                 the rebuild is a conditional node of the captured
                                 step graph (no host round trip)                   */
-    int32_t precision;       /* MD_FP64 or MD_MIXED                                 */
+    int32_t precision;       /* MD_FP64, MD_MIXED or MD_DW                          */
     int32_t list_type;       /* MD_LIST_FULL, MD_LIST_HALF (pair (i,j) stored
                                 with i iff j's nearest image is in i's upper
                                 half-space: del = x_i - x_j has del.z < 0, ties
@@ -296,8 +304,8 @@ int md_set_lj(md_ctx *ctx, double epsilon, double sigma);
  * sum of x_ij . F_ij.  Full lists are used (a half-list context switches and
  * rebuilds); md_set_lj switches back to Lennard-Jones.  K = gamma = 0 is the
  * paper's static setting (no force).
- * Errors: MD_ERR_INVAL (negative or non-finite K or gamma, cutoff < sigma),
- * MD_ERR_CUDA. */
+ * Errors: MD_ERR_INVAL (negative or non-finite K or gamma, cutoff < sigma,
+ * an MD_DW context), MD_ERR_CUDA. */
 int md_set_spring_dashpot(md_ctx *ctx, double k_spring, double gamma);
 
 /* Differentiable rollout (not in the paper; it differentiates the Sec. 3.2
@@ -316,8 +324,8 @@ int md_set_spring_dashpot(md_ctx *ctx, double k_spring, double gamma);
  * for later calls, grown when a call needs more, and is freed by md_destroy;
  * if growing it fails the whole workspace is released and MD_ERR_NOMEM
  * returned.
- * Errors: MD_ERR_INVAL (nrep != 1; rebuild_every == 0; spring-dashpot model; window not in
- * [1, nsteps]; ckpt_every not dividing both rebuild_every and nsteps),
+ * Errors: MD_ERR_INVAL (nrep != 1; rebuild_every == 0; spring-dashpot model; an MD_DW
+ * context; window not in [1, nsteps]; ckpt_every not dividing both rebuild_every and nsteps),
  * MD_ERR_NOMEM, MD_ERR_CUDA and those of md_run. */
 int md_adjoint(md_ctx *ctx, int64_t nsteps, int64_t window, int32_t ckpt_every, double *loss,
                double *g_eps, double *g_sigma, double *g_x0, double *g_v0);
@@ -371,6 +379,7 @@ int md_study_force_variant(md_ctx *ctx, int32_t variant, int32_t reps, double *u
  * `steps` steps on the context's own state (which it restores), then the
  * winner with the other cell split (md_set_cell_split), keeps the fastest and
  * reports it in *chosen (may be NULL; the split in md_info.cell_split).
+ * MD_DW contexts try full lists with 1, 2, 4 and 8 lanes per atom.
  * Results are cached per (precision, atoms-per-replica bucket) for the life
  * of the process. */
 int md_autotune(md_ctx *ctx, int32_t steps, md_params *chosen);

@@ -252,8 +252,8 @@ __global__ void __launch_bounds__(256) k_sort_gather(Dev d, int64_t nk)
         const double px = x.x - __ldg(ct + cx);
         const double py = x.y - __ldg(ct + R.nc[0] + cy);
         const double pz = x.z - __ldg(ct + R.nc[0] + R.nc[1] + cz);
-        uint32_t pack = (uint32_t)cx | ((uint32_t)cy << 10) | ((uint32_t)cz << 20);
-        d.p32[ns] = make_float4(f32_of_f64(px), f32_of_f64(py), f32_of_f64(pz), __uint_as_float(pack));
+        const uint32_t pack = (uint32_t)cx | ((uint32_t)cy << 10) | ((uint32_t)cz << 20);
+        store_cell_pos(d, R, d.p32, d.plo, ns, px, py, pz, pack);
     }
 }
 

@@ -1,0 +1,290 @@
+// LJ 12-6 forces over the Verlet list (tinyMD Sec. 3.2, Eq. 2) in
+// double-word arithmetic: every quantity of the pair kernel is an unevaluated
+// sum h + l of two FP32 numbers, which carries about 48 significant bits, so
+// the forces agree with an FP64 evaluation to ~1e-13 while every operation
+// runs on the FP32 pipe.  GB300's FP64 pipe is about 1/64 of its FP32 rate
+// and bounds the FP64 path (17 FP64 operations per pair); the double-word
+// pair takes about 150 FP32 operations instead.  Precision MD_DW.
+//
+// Building blocks, written from the published error-free transformations:
+//   two_sum      s + e = a + b exactly (Knuth, TAOCP vol. 2, Sec. 4.2.2);
+//   fast_two_sum the same for |a| >= |b| in three operations (Dekker 1971);
+//   two_prod     p + e = a b exactly, e = fma(a, b, -p);
+//   dw_mul       product of double words: the exact product of the high
+//                parts plus the two cross terms (the low x low term is below
+//                2^-46 of the product), as in the double-word multiplication
+//                of Joldes, Muller and Popescu (ACM TOMS 2017);
+//   dw_add       exact sum of the high parts plus the low parts.
+// Intermediate results are not renormalised (their low parts stay within a
+// few ulps of the high parts, which the multiplication tolerates); r^2 is
+// renormalised before the cut-off compare and the reciprocal, and the
+// per-atom sums once per list chunk.  All arithmetic uses the _rn
+// intrinsics so that nothing is contracted or reassociated.
+//
+// Positions: p32 holds the high parts of the cell-relative positions, on a
+// grid of step g = 2^k with 2^24 g >= 2.5 cell sides, plo the low parts
+// (dw_split).  The displacement of a listed pair,
+//     d = (p_i - o s) - p_j,
+// then has an exact FP32 high part (p_ih -+ s_h - p_jh: multiples of g below
+// 2^24 g) and a low part (p_il -+ s_l) - p_jl rounded once, so the
+// cancellation of nearby positions loses nothing; d is good to ~2^-45.
+//
+// Reciprocal: 1/r^2 from the hardware approximation refined by one FP32
+// Newton step (within ~1 ulp), then one Newton step in double word,
+// y (1 + e) with e = 1 - r^2 y: relative error ~2^-46.
+//
+// Epilogue: the FP64 velocity-Verlet update of the mixed path (x and v
+// updated in place), with the force F = (double)h + (double)l; the next
+// positions' split goes to the other p32 / plo buffers.
+#include "md_internal.cuh"
+
+namespace mdk {
+
+namespace {
+
+__device__ __forceinline__ bool stopped(const DevStatus *st)
+{
+    return *((volatile const int32_t *)&st->flags) != 0;
+}
+
+struct dw {
+    float h, l;
+};
+
+__device__ __forceinline__ dw two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bv = __fsub_rn(s, a);
+    const float av = __fsub_rn(s, bv);
+    return {s, __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv))};
+}
+
+__device__ __forceinline__ dw fast_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ dw two_prod(float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ dw dw_mul(dw x, dw y)
+{
+    dw p = two_prod(x.h, y.h);
+    p.l = __fmaf_rn(x.h, y.l, __fmaf_rn(x.l, y.h, p.l));
+    return p;
+}
+
+__device__ __forceinline__ dw dw_add(dw x, dw y)
+{
+    dw s = two_sum(x.h, y.h);
+    s.l = __fadd_rn(s.l, __fadd_rn(x.l, y.l));
+    return s;
+}
+
+// (h + l)^2 for an exact high part h and a small low part l:
+// h^2 exactly, plus (2h + l) l
+__device__ __forceinline__ dw dw_sq_of(float h, float l)
+{
+    dw p = two_prod(h, h);
+    p.l = __fmaf_rn(__fmaf_rn(2.f, h, l), l, p.l);
+    return p;
+}
+
+__device__ __forceinline__ float rcp_approx(float a)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+
+__device__ __forceinline__ double to_f64(dw a)
+{
+    return f64_of_f32(a.h) + f64_of_f32(a.l);
+}
+
+__device__ __forceinline__ dw dw_const(const float c[2])
+{
+    return {c[0], c[1]};
+}
+
+// FP64 epilogue (velocity Verlet, Sec. 3.2 Eq. 1, as the mixed path: x and v
+// in place with streaming accesses), the next split positions into
+// p32_nxt / plo_nxt.
+template <int EPI, bool ENERGY>
+__device__ __forceinline__ void dw_epilogue(const Dev &d, const LJ &lj, const Rep &R, int64_t i,
+                                            double fx, double fy, double fz, uint32_t pack)
+{
+    if (EPI == EPI_F || EPI == EPI_FK) d.f64[i] = mk_dvec4(fx, fy, fz, 0.0);
+    if (EPI == EPI_F) return;
+    dvec4 v = ld_cs_dvec4(d.v + i);
+    v.x = fma(lj.half_dt_m, fx, v.x);
+    v.y = fma(lj.half_dt_m, fy, v.y);
+    v.z = fma(lj.half_dt_m, fz, v.z);
+    if (ENERGY) d.ke_atom64[i] = 0.5 * lj.mass * fma(v.x, v.x, fma(v.y, v.y, v.z * v.z));
+    if (EPI == EPI_FKKD) {
+        v.x = fma(lj.half_dt_m, fx, v.x);
+        v.y = fma(lj.half_dt_m, fy, v.y);
+        v.z = fma(lj.half_dt_m, fz, v.z);
+        dvec4 x = ld_cs_dvec4(d.x + i);
+        x.x = fma(lj.dt, v.x, x.x);
+        x.y = fma(lj.dt, v.y, x.y);
+        x.z = fma(lj.dt, v.z, x.z);
+        st_cs_dvec4(d.x + i, x);
+        const double *ct = d.ctr + R.ctr_off;
+        const double cx = __ldg(ct + (pack & 1023u));
+        const double cy = __ldg(ct + R.nc[0] + ((pack >> 10) & 1023u));
+        const double cz = __ldg(ct + R.nc[0] + R.nc[1] + ((pack >> 20) & 1023u));
+        store_cell_pos(d, R, d.p32_nxt, d.plo_nxt, i, x.x - cx, x.y - cy, x.z - cz, pack);
+        if (d.p32_ref) check_displacement(d, i, d.p32_nxt[i]);
+    }
+    st_cs_dvec4(d.v + i, v);
+}
+
+// One atom (TPA lanes) over its full list.
+template <int TPA, bool BATCHED, int EPI, bool ENERGY>
+__global__ void __launch_bounds__(256) k_force_dw_full(Dev d, LJ lj)
+{
+    if (stopped(d.status)) return;
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i0 = gt / TPA;
+    const int sub = (int)(gt % TPA);
+    const bool valid = i0 < d.n;
+    if (TPA == 1 && !valid) return;
+    const int64_t i = valid ? i0 : d.n - 1;
+    const int64_t n = d.n;
+    const Rep &R = d.reps[BATCHED ? d.rep_of[i] : 0];
+    const float4 hi = d.p32[i], li = d.plo[i];
+    const int cnt = valid && MD_CHECK(d, d.nb_count[i] <= d.cap) ? d.nb_count[i] : 0;
+    const int nq = (cnt + 3) >> 2;
+    const int4 *nb4 = reinterpret_cast<const int4 *>(d.nb);
+    const float4 *p32 = d.p32, *plo = d.plo;
+
+    // p_i - o s for o = -1 (field 0) and o = +1 (field 2): high parts exact
+    const float qhx0 = __fadd_rn(hi.x, R.dw_sh[0]), qhx2 = __fsub_rn(hi.x, R.dw_sh[0]);
+    const float qhy0 = __fadd_rn(hi.y, R.dw_sh[1]), qhy2 = __fsub_rn(hi.y, R.dw_sh[1]);
+    const float qhz0 = __fadd_rn(hi.z, R.dw_sh[2]), qhz2 = __fsub_rn(hi.z, R.dw_sh[2]);
+    const float qlx0 = __fadd_rn(li.x, R.dw_sl[0]), qlx2 = __fsub_rn(li.x, R.dw_sl[0]);
+    const float qly0 = __fadd_rn(li.y, R.dw_sl[1]), qly2 = __fsub_rn(li.y, R.dw_sl[1]);
+    const float qlz0 = __fadd_rn(li.z, R.dw_sl[2]), qlz2 = __fsub_rn(li.z, R.dw_sl[2]);
+    const dw rc2 = dw_const(lj.dw_rc2), sig6 = dw_const(lj.dw_sig6), c48 = dw_const(lj.dw_c48);
+    const dw c24n = {-lj.dw_c24[0], -lj.dw_c24[1]};
+
+    dw ax = {0.f, 0.f}, ay = {0.f, 0.f}, az = {0.f, 0.f}, ape = {0.f, 0.f}, aw = {0.f, 0.f};
+
+    auto pair = [&](uint32_t e) {
+        if (!MD_CHECK(d, (e & kJMask) <= (uint32_t)d.n)) return;
+        const uint32_t j = e & kJMask;
+        const float4 hj = __ldg(p32 + j);
+        const float4 lj4 = __ldg(plo + j);
+        const uint32_t c = e >> kJBits;
+        const bool x2 = c & 2u, x1 = c & 1u, y2 = c & 8u, y1 = c & 4u, z2 = c & 32u, z1 = c & 16u;
+        const float dxh = __fsub_rn(x2 ? qhx2 : (x1 ? hi.x : qhx0), hj.x);
+        const float dyh = __fsub_rn(y2 ? qhy2 : (y1 ? hi.y : qhy0), hj.y);
+        const float dzh = __fsub_rn(z2 ? qhz2 : (z1 ? hi.z : qhz0), hj.z);
+        const float dxl = __fsub_rn(x2 ? qlx2 : (x1 ? li.x : qlx0), lj4.x);
+        const float dyl = __fsub_rn(y2 ? qly2 : (y1 ? li.y : qly0), lj4.y);
+        const float dzl = __fsub_rn(z2 ? qlz2 : (z1 ? li.z : qlz0), lj4.z);
+        dw r2 = dw_add(dw_add(dw_sq_of(dxh, dxl), dw_sq_of(dyh, dyl)), dw_sq_of(dzh, dzl));
+        r2 = fast_two_sum(r2.h, r2.l);
+        const bool in = r2.h < rc2.h || (r2.h == rc2.h && r2.l < rc2.l);
+        // 1 / r^2
+        float y = rcp_approx(r2.h);
+        y = __fmaf_rn(y, __fmaf_rn(-r2.h, y, 1.f), y);
+        const float er = __fmaf_rn(-r2.l, y, __fmaf_rn(-r2.h, y, 1.f));
+        const dw sr2 = {y, __fmul_rn(y, er)};
+        // t = sr2^3 sigma^6 (the paper's sr6); f = sr2 t (48 eps t - 24 eps)
+        const dw t = dw_mul(dw_mul(dw_mul(sr2, sr2), sr2), sig6);
+        dw f = dw_mul(dw_mul(sr2, t), dw_add(dw_mul(c48, t), c24n));
+        f.h = in ? f.h : 0.f;
+        f.l = in ? f.l : 0.f;
+        ax = dw_add(ax, dw_mul(f, dw{dxh, dxl}));
+        ay = dw_add(ay, dw_mul(f, dw{dyh, dyl}));
+        az = dw_add(az, dw_mul(f, dw{dzh, dzl}));
+        if (ENERGY) {
+            dw v = dw_mul(dw_mul(dw_const(lj.dw_c4), t), dw_add(t, dw{-1.f, 0.f}));
+            v.h = in ? v.h : 0.f;
+            v.l = in ? v.l : 0.f;
+            ape = dw_add(ape, v);
+            aw = dw_add(aw, dw_mul(f, r2));
+        }
+    };
+
+    int q = sub;
+    int4 nxt = q < nq ? __ldcs(nb4 + (int64_t)q * n + i) : make_int4(0, 0, 0, 0);
+    for (; q < nq; q += TPA) {
+        const int4 e = nxt;
+        if (q + TPA < nq) nxt = __ldcs(nb4 + (int64_t)(q + TPA) * n + i);
+        pair((uint32_t)e.x);
+        pair((uint32_t)e.y);
+        pair((uint32_t)e.z);
+        pair((uint32_t)e.w);
+        // keep the low parts of the sums near an ulp of the high parts
+        ax = fast_two_sum(ax.h, ax.l);
+        ay = fast_two_sum(ay.h, ay.l);
+        az = fast_two_sum(az.h, az.l);
+        if (ENERGY) {
+            ape = fast_two_sum(ape.h, ape.l);
+            aw = fast_two_sum(aw.h, aw.l);
+        }
+    }
+    if (TPA > 1) {
+        // butterfly: two_sum is symmetric, so every lane ends with the same sums
+#pragma unroll
+        for (int o = TPA / 2; o > 0; o >>= 1) {
+            ax = dw_add(ax, dw{__shfl_xor_sync(0xffffffffu, ax.h, o), __shfl_xor_sync(0xffffffffu, ax.l, o)});
+            ay = dw_add(ay, dw{__shfl_xor_sync(0xffffffffu, ay.h, o), __shfl_xor_sync(0xffffffffu, ay.l, o)});
+            az = dw_add(az, dw{__shfl_xor_sync(0xffffffffu, az.h, o), __shfl_xor_sync(0xffffffffu, az.l, o)});
+            if (ENERGY) {
+                ape = dw_add(ape, dw{__shfl_xor_sync(0xffffffffu, ape.h, o),
+                                     __shfl_xor_sync(0xffffffffu, ape.l, o)});
+                aw = dw_add(aw, dw{__shfl_xor_sync(0xffffffffu, aw.h, o),
+                                   __shfl_xor_sync(0xffffffffu, aw.l, o)});
+            }
+        }
+        if (sub != 0 || !valid) return;
+    }
+    if (ENERGY) {
+        d.pe_atom64[i] = 0.5 * to_f64(ape);
+        d.w_atom64[i] = 0.5 * to_f64(aw);
+    }
+    dw_epilogue<EPI, ENERGY>(d, lj, R, i, to_f64(ax), to_f64(ay), to_f64(az), __float_as_uint(hi.w));
+}
+
+template <int TPA, bool B>
+void launch_dw(const Dev &d, const LJ &lj, int epi, bool energy, cudaStream_t st)
+{
+    const unsigned g = (unsigned)((d.n * TPA + 255) / 256);
+#define MD_DW_K(EP, EN) k_force_dw_full<TPA, B, EP, EN><<<g, 256, 0, st>>>(d, lj)
+    if (epi == EPI_F) { if (energy) MD_DW_K(EPI_F, true); else MD_DW_K(EPI_F, false); }
+    else if (epi == EPI_FK) { if (energy) MD_DW_K(EPI_FK, true); else MD_DW_K(EPI_FK, false); }
+    else { if (energy) MD_DW_K(EPI_FKKD, true); else MD_DW_K(EPI_FKKD, false); }
+#undef MD_DW_K
+}
+
+}  // namespace
+
+int launch_force_dw(const Dev &d, const LJ &lj, int tpa, int epi, bool energy, bool batched,
+                    cudaStream_t st, int *nl)
+{
+    if (d.n <= 0) return 0;
+    if (!d.plo || !d.plo_nxt) return -1;
+    if (batched) {
+        if (tpa == 8) launch_dw<8, true>(d, lj, epi, energy, st);
+        else if (tpa == 4) launch_dw<4, true>(d, lj, epi, energy, st);
+        else if (tpa == 2) launch_dw<2, true>(d, lj, epi, energy, st);
+        else launch_dw<1, true>(d, lj, epi, energy, st);
+    } else {
+        if (tpa == 8) launch_dw<8, false>(d, lj, epi, energy, st);
+        else if (tpa == 4) launch_dw<4, false>(d, lj, epi, energy, st);
+        else if (tpa == 2) launch_dw<2, false>(d, lj, epi, energy, st);
+        else launch_dw<1, false>(d, lj, epi, energy, st);
+    }
+    *nl += 1;
+    return (int)cudaGetLastError();
+}
+
+}  // namespace mdk

@@ -15,8 +15,9 @@ __device__ __forceinline__ bool stopped(const DevStatus *st)
 // phase 1: v += c F; x += dt v            (c = dt / (2m))
 // phase 2: v += c F
 // phase 3: v += c F (full step; KE when asked); v += c F; x += dt v
-// Positions change in place, so the FP32 cell-relative copy is refreshed in
-// place too (no other kernel reads it concurrently).
+// Positions change in place, so the FP32 cell-relative copy (on the
+// double-word path its high and low parts) is refreshed in place too (no
+// other kernel reads it concurrently).
 template <bool BATCHED, bool MIXED>
 __global__ void __launch_bounds__(256) k_integrate(Dev d, LJ lj, int phase, int want_ke)
 {
@@ -58,9 +59,8 @@ __global__ void __launch_bounds__(256) k_integrate(Dev d, LJ lj, int phase, int 
     const double cx = __ldg(ct + (pack & 1023u));
     const double cy = __ldg(ct + R.nc[0] + ((pack >> 10) & 1023u));
     const double cz = __ldg(ct + R.nc[0] + R.nc[1] + ((pack >> 20) & 1023u));
-    const float4 pn = make_float4(f32_of_f64(x.x - cx), f32_of_f64(x.y - cy), f32_of_f64(x.z - cz), p.w);
-    d.p32[i] = pn;
-    check_displacement(d, i, pn);
+    store_cell_pos(d, R, d.p32, d.plo, i, x.x - cx, x.y - cy, x.z - cz, pack);
+    check_displacement(d, i, d.p32[i]);
 }
 
 // After a binning with the displacement trigger: the reordered state goes

@@ -75,6 +75,8 @@ struct md_ctx {
     int32_t *id[2] = {nullptr, nullptr};
     float4 *p32[2] = {nullptr, nullptr};
     float4 *p32_ref = nullptr;      // displacement trigger: p32 at the last binning
+    float4 *plo[2] = {nullptr, nullptr};   // double-word path: low parts of the split
+                                    // positions, same parity as p32 (else null)
     float4 *v32[2] = {nullptr, nullptr};   // contact model, mixed path: FP32 velocity
                                     // copies, same parity as p32
     bool v32_fresh = false;         // v32[pb] == fl32(v) (else regenerated before a force)
@@ -165,6 +167,8 @@ Dev view(const md_ctx *c)
     d.p32 = c->p32[c->pb];
     d.p32_nxt = c->p32[1 - c->pb];
     d.p32_ref = c->p32_ref;
+    d.plo = c->plo[c->pb];
+    d.plo_nxt = c->plo[1 - c->pb];
     d.disp2_thr = c->disp2_thr;
     d.f32 = c->f32;
     d.f64 = c->f64;
@@ -240,7 +244,8 @@ void free_all(md_ctx *c)
                     c->p32_ref, c->v32[0], c->v32[1], c->adj.ck_x, c->adj.ck_v, c->adj.blk_x,
                     c->adj.xbar, c->adj.wbar, c->adj.blk_p, c->adj.ck_p, c->adj.wbar32,
                     c->adj.ck_id, c->adj.ge, c->adj.gs, c->adj.g2, c->grp, c->gcnt,
-                    c->gcell_start, c->gnb, c->gnb_count, c->offtab_d, c->gmask, c->gpair};
+                    c->gcell_start, c->gnb, c->gnb_count, c->offtab_d, c->gmask, c->gpair,
+                    c->plo[0], c->plo[1]};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->own_stream && c->st) cudaStreamDestroy(c->st);
@@ -248,6 +253,11 @@ void free_all(md_ctx *c)
 }
 
 bool is_mixed(const md_ctx *c) { return c->p.precision == MD_MIXED; }
+// double-word pair arithmetic (FP32 pipe); state handled as on the mixed path
+bool is_dw(const md_ctx *c) { return c->p.precision == MD_DW; }
+// the FP64 path gathers x itself: its fused step writes the next x into the
+// other buffer; the mixed and double-word paths update x in place
+bool x_flips(const md_ctx *c) { return c->p.precision == MD_FP64; }
 bool is_half(const md_ctx *c) { return c->p.list_type == MD_LIST_HALF; }
 // group size of a list shared by groups of atoms (list types 2 and 4), else 0
 int list_g(const md_ctx *c)
@@ -433,13 +443,14 @@ int enq_force(md_ctx *c, int epi, bool energy, int *nl, cudaEvent_t *ev = nullpt
     } else {
         if (ev) CK(cudaEventRecord(ev[0], c->st));
         const int rc = list_g(c) ? launch_force_group(d, c->lj, list_g(c), epi, energy, batched(c), c->st, nl)
-                                 : launch_force(d, c->lj, c->p.precision, false, c->tpa, epi, energy,
-                                                batched(c), c->st, nl);
+                       : is_dw(c) ? launch_force_dw(d, c->lj, c->tpa, epi, energy, batched(c), c->st, nl)
+                                  : launch_force(d, c->lj, c->p.precision, false, c->tpa, epi, energy,
+                                                 batched(c), c->st, nl);
         if (rc) return fail(c, MD_ERR_CUDA, "force launch failed");
         if (ev) CK(cudaEventRecord(ev[1], c->st));
         if (epi == EPI_FKKD) {
             c->pb = 1 - c->pb;
-            if (!is_mixed(c)) c->xp = 1 - c->xp;
+            if (x_flips(c)) c->xp = 1 - c->xp;
         }
     }
     if (epi == EPI_FKKD) c->moved_since_bin = true;
@@ -602,6 +613,9 @@ int check_flags(md_ctx *c, const DevStatus &s)
     if (s.flags & FLAG_NONFINITE) return fail(c, MD_ERR_NONFINITE, "non-finite position or velocity");
     if (s.flags & FLAG_BADPOS) return fail(c, MD_ERR_BADPOS, "an atom moved more than one box length between wraps");
     if (s.flags & FLAG_BOUNDS) return fail(c, MD_ERR_STATE, "a device bounds check failed (debug build)");
+    if (s.flags & FLAG_DWRANGE)
+        return fail(c, MD_ERR_BADPOS, "double-word path: an atom moved more than a cell side beyond "
+                                      "its cell since the last binning");
     return MD_OK;
 }
 
@@ -732,6 +746,16 @@ void set_lj_constants(md_ctx *c)
     lj.half_dt_m = 0.5 * q.dt / q.mass;
     lj.dt = q.dt;
     lj.mass = q.mass;
+    // double-word constants: high part fl32(c), low part fl32(c - high)
+    auto split2 = [](double v, float out[2]) {
+        out[0] = (float)v;
+        out[1] = (float)(v - (double)out[0]);
+    };
+    split2(lj.rc2, lj.dw_rc2);
+    split2(lj.sigma6, lj.dw_sig6);
+    split2(lj.c48e, lj.dw_c48);
+    split2(lj.c24e, lj.dw_c24);
+    split2(lj.c4e, lj.dw_c4);
     lj.rs2f_lo = (float)(lj.rs2 * (1.0 - 2.5e-4));
     lj.rs2f_hi = (float)(lj.rs2 * (1.0 + 2.5e-4));
     // spring-dashpot constants (pot, sd_k, sd_g are set by md_set_spring_dashpot)
@@ -765,7 +789,8 @@ std::mutex &tune_mutex()
 // at 4k, 4 up to ~256k, 2 up to ~2M, 1 at 4M).
 int default_lanes(int64_t n, int32_t precision)
 {
-    if (precision == MD_MIXED) return n <= 8192 ? 8 : (n <= 32768 ? 4 : (n <= 98304 ? 2 : 1));
+    if (precision == MD_MIXED || precision == MD_DW)
+        return n <= 8192 ? 8 : (n <= 32768 ? 4 : (n <= 98304 ? 2 : 1));
     return n <= 8192 ? 8 : (n <= 393216 ? 4 : (n <= 3000000 ? 2 : 1));
 }
 
@@ -1039,7 +1064,7 @@ int md_run(md_ctx *c, int64_t nsteps, int32_t energy_every, double *energies)
                 return fail(c, MD_ERR_NL_OVERFLOW, "list overflow at an unknown step");
             const int64_t done = n_fail - first;
             c->pb = pb0 ^ (int)(done & 1);
-            c->xp = is_mixed(c) ? xp0 : (xp0 ^ (int)(done & 1));
+            c->xp = x_flips(c) ? (xp0 ^ (int)(done & 1)) : xp0;
             c->moved_since_bin = false;
             c->list_valid = false;
             c->forces_valid = false;
@@ -1399,6 +1424,7 @@ int md_set_spring_dashpot(md_ctx *c, double k_spring, double gamma)
         return fail(c, MD_ERR_INVAL, "bad argument");
     if (!(c->p.cutoff >= c->p.sigma))
         return fail(c, MD_ERR_INVAL, "cutoff must be >= sigma (the sphere diameter) so lists hold every contact");
+    if (is_dw(c)) return fail(c, MD_ERR_INVAL, "the contact model runs on MD_FP64 or MD_MIXED contexts");
     CK(cudaStreamSynchronize(c->st));
     int rc = MD_OK;
     for (int b = 0; b < 2; b++) {
@@ -1431,6 +1457,7 @@ static int adjoint_impl(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt,
     if (c->disp)
         return fail(c, MD_ERR_INVAL, "md_adjoint needs the fixed rebuild schedule (rebuild_every > 0)");
     if (is_sd(c)) return fail(c, MD_ERR_INVAL, "md_adjoint differentiates the Lennard-Jones force only");
+    if (is_dw(c)) return fail(c, MD_ERR_INVAL, "md_adjoint runs on MD_FP64 or MD_MIXED contexts");
     const int64_t every = c->p.rebuild_every;
     if (every % ckpt != 0 || nsteps % ckpt != 0)
         return fail(c, MD_ERR_INVAL, "ckpt_every must divide rebuild_every and nsteps");
@@ -1839,7 +1866,8 @@ int md_autotune(md_ctx *c, int32_t steps, md_params *chosen)
     };
     // lanes per atom and list type at the current cell split, then the
     // winner with the other split (the cell size of the list build)
-    const int ncand = is_mixed(c) ? 7 : 5;
+    // (the double-word path runs full lists only)
+    const int ncand = is_mixed(c) ? 7 : (is_dw(c) ? 4 : 5);
     const int split0 = c->split;
     for (int k = 0; k < ncand && !rc; k++) {
         float ms = 0;
@@ -1892,7 +1920,8 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
         return fail(c, MD_ERR_INVAL, "null argument or nrep <= 0");
     const md_params &q = *p;
     if (!(q.epsilon > 0) || !(q.sigma > 0) || !(q.mass > 0) || !(q.cutoff > 0) || !(q.skin >= 0) ||
-        !(q.dt > 0) || q.rebuild_every < 0 || (q.precision != MD_FP64 && q.precision != MD_MIXED) ||
+        !(q.dt > 0) || q.rebuild_every < 0 ||
+        (q.precision != MD_FP64 && q.precision != MD_MIXED && q.precision != MD_DW) ||
         (q.list_type != MD_LIST_FULL && q.list_type != MD_LIST_HALF &&
          q.list_type != MD_LIST_GROUP2 && q.list_type != MD_LIST_GROUP4) ||
         !(q.threads_per_atom == 0 || q.threads_per_atom == 1 || q.threads_per_atom == 2 ||
@@ -1900,6 +1929,8 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
         return fail(c, MD_ERR_INVAL, "invalid md_params");
     if ((q.list_type == MD_LIST_GROUP2 || q.list_type == MD_LIST_GROUP4) && q.precision != MD_MIXED)
         return fail(c, MD_ERR_INVAL, "lists shared by groups of atoms need the mixed path");
+    if (q.precision == MD_DW && q.list_type != MD_LIST_FULL)
+        return fail(c, MD_ERR_INVAL, "the double-word path runs full per-atom lists");
     c->p = q;
     c->nrep = nrep;
     c->disp = q.rebuild_every == 0;
@@ -1939,6 +1970,23 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
             vol *= L[d];
         }
         for (int d = 0; d < 3; d++) R.nt[d] = (R.nc[d] + kTile - 1) / kTile;
+        {
+            // double-word positions: grid step g = 2^k, the least with
+            // 2^24 g >= 2.5 max(s); s = s_h + s_l with s_h a multiple of g
+            const double smax = std::max(R.s[0], std::max(R.s[1], R.s[2]));
+            double g = std::ldexp(1.0, (int)std::floor(std::log2(2.5 * smax)) - 26);
+            while (std::ldexp(g, 24) < 2.5 * smax) g *= 2.0;
+            R.dw_magic = 1.5 * std::ldexp(g, 52);
+            for (int d = 0; d < 3; d++) {
+                const double sh = std::nearbyint(R.s[d] / g) * g;
+                R.dw_sh[d] = (float)sh;
+                R.dw_sl[d] = (float)(R.s[d] - sh);
+            }
+            // |p_h| + s_h <= 2^24 g keeps p_h +- s_h exact (one step g of margin)
+            const double lim = std::ldexp(g, 24) - smax - g;
+            R.dw_lim = (float)lim;
+            if ((double)R.dw_lim > lim) R.dw_lim = std::nextafter(R.dw_lim, 0.0f);
+        }
         R.cell_off = ids;
         R.ctr_off = 0;   // set below
         R.atom_off = n;
@@ -2004,6 +2052,13 @@ int make_context(md_ctx *c, const md_box *boxes, const md_params *p, const int64
         CK(cudaMemcpy(c->p32[b] + N, &far32, sizeof(float4), cudaMemcpyHostToDevice));
     }
     if ((rc = dalloc(c, &c->f32, N))) return rc;
+    if (q.precision == MD_DW) {
+        // low parts of the split positions; slot n (the sentinel) stays zero
+        for (int b = 0; b < 2; b++) {
+            if ((rc = dalloc(c, &c->plo[b], N + 1))) return rc;
+            CK(cudaMemsetAsync(c->plo[b], 0, sizeof(float4) * (N + 1), c->st));
+        }
+    }
     if (c->disp) {
         if ((rc = dalloc(c, &c->p32_ref, N))) return rc;
         CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));

@@ -55,7 +55,9 @@ constexpr int kMaxNc = 1023;        // cell coordinates are packed in 10 bits ea
 // is non-zero, so the state freezes at the first failure.
 enum : int32_t {
     FLAG_NL_OVERFLOW = 1, FLAG_NONFINITE = 2, FLAG_BADPOS = 4, FLAG_BOUNDS = 8,
-    FLAG_TIMEOUT = 16   // a bounded device wait gave up
+    FLAG_TIMEOUT = 16,  // a bounded device wait gave up
+    FLAG_DWRANGE = 32   // double-word path: an atom left the range its split
+                        // position keeps exact (see dw_split)
 };
 
 // Bounds checks of the debug build (MD_DEBUG_CHECKS=1): MD_CHECK(d, cond) is
@@ -96,6 +98,15 @@ struct Rep {
                               // at least this far on the near side of their own centre)
     int32_t nc[3];
     int32_t nt[3];            // cell tiles per dimension, ceil(nc / MD_CELL_TILE)
+    // double-word positions (precision MD_DW): grid step g = 2^k of the high
+    // parts (the least power of two with 2^24 g >= 2.5 max(s)), the constant
+    // 1.5 * 2^52 * g that rounds an FP64 number to a multiple of g, the cell
+    // side split into s_h (a multiple of g) and s_l = fl32(s - s_h), and the
+    // largest |high part| for which p_h +- s_h stays exact (2^24 g - max s)
+    double dw_magic;
+    float dw_sh[3], dw_sl[3];
+    float dw_lim;
+    int32_t dw_pad_;
     int64_t ctr_off;          // first entry of this replica in Dev::ctr
     int64_t cell_off;         // first global cell id of this replica
     int64_t atom_off;         // first atom slot of this replica
@@ -149,6 +160,8 @@ struct LJ {
     double dt;
     double mass;
     float rs2f_lo, rs2f_hi;   // FP32 prefilter band around rs^2 (exact FP64 test inside)
+    // double-word constants (precision MD_DW): {fl32(c), fl32(c - fl32(c))}
+    float dw_rc2[2], dw_sig6[2], dw_c48[2], dw_c24[2], dw_c4[2];
     // spring-dashpot contact (Eq. 3; pot == 1): K, gamma, sigma^2 (sigma = diameter)
     int32_t pot;
     double sd_k, sd_g, sd_sig2;
@@ -175,6 +188,8 @@ struct Dev {
     int32_t *id, *id_alt;     // caller id of each slot
     float4 *p32, *p32_nxt;    // cell-relative FP32 positions; .w = packed cell coords
     float4 *p32_ref;          // p32 at the last binning (displacement trigger only, else null)
+    float4 *plo, *plo_nxt;    // precision MD_DW: low parts of the split positions (p32
+                              // then holds the high parts); null on the other paths
     float disp2_thr;          // squared trigger distance (FP32, below (skin/2)^2)
     float4 *f32;              // mixed-path forces
     dvec4 *f64;             // FP64-path forces
@@ -332,6 +347,39 @@ __device__ __forceinline__ void check_displacement(const Dev &d, int64_t i, cons
     const float dx = p.x - r.x, dy = p.y - r.y, dz = p.z - r.z;
     if (fmaf(dz, dz, fmaf(dy, dy, dx * dx)) > d.disp2_thr) d.status->need_rebuild = 1;
 }
+
+// Double-word positions (precision MD_DW): the cell-relative FP64 position p
+// as h + l, h = p rounded to a multiple of the replica's grid step g (two
+// FP64 additions of 1.5 * 2^52 * g), l = fl32(p - h) (p - h is exact).  h has
+// at most 24 significant bits while |p| < 2^24 g, so it is an FP32 number,
+// and sums and differences of such numbers below 2^24 g are exact in FP32:
+// the force kernel forms the high part of each displacement without
+// rounding.  l carries p to 2^-25 g.  Returns false (the caller raises
+// FLAG_DWRANGE) when |h| exceeds R.dw_lim, past which h +- s_h could round.
+__device__ __forceinline__ bool dw_split(const Rep &R, double p, float &h, float &l)
+{
+    const double hd = __dsub_rn(__dadd_rn(p, R.dw_magic), R.dw_magic);
+    h = f32_of_f64(hd);
+    l = f32_of_f64(__dsub_rn(p, hd));
+    return fabsf(h) <= R.dw_lim;
+}
+
+// p32 / plo entries of slot i from the cell-relative FP64 position (px, py,
+// pz): on the double-word path the split above, else p32 = fl32(p).
+__device__ __forceinline__ void store_cell_pos(const Dev &d, const Rep &R, float4 *p32,
+                                               float4 *plo, int64_t i, double px, double py,
+                                               double pz, uint32_t pack)
+{
+    if (plo) {
+        float hx, hy, hz, lx, ly, lz;
+        const bool ok = dw_split(R, px, hx, lx) & dw_split(R, py, hy, ly) & dw_split(R, pz, hz, lz);
+        if (!ok) atomicOr(&d.status->flags, FLAG_DWRANGE);
+        p32[i] = make_float4(hx, hy, hz, __uint_as_float(pack));
+        plo[i] = make_float4(lx, ly, lz, 0.f);
+    } else {
+        p32[i] = make_float4(f32_of_f64(px), f32_of_f64(py), f32_of_f64(pz), __uint_as_float(pack));
+    }
+}
 #endif
 
 // ---------------------------------------------------------------------------
@@ -347,6 +395,11 @@ int launch_force(const Dev &d, const LJ &lj, int precision, bool half, int tpa, 
                  bool energy, bool batched, cudaStream_t st, int *nlaunch);
 int launch_integrate(const Dev &d, const LJ &lj, int precision, int phase, bool batched,
                      cudaStream_t st, int *nlaunch);
+// Double-word path (precision MD_DW, k_force_dw.cu): full per-atom lists,
+// 1/2/4/8 lanes per atom, epilogues as the other full-list kernels; forces
+// in d.f64, per-atom PE / W in d.pe_atom64 / d.w_atom64.
+int launch_force_dw(const Dev &d, const LJ &lj, int tpa, int epi, bool energy, bool batched,
+                    cudaStream_t st, int *nlaunch);
 // Spring-dashpot forces (full list).  Mixed path: one kernel with the
 // epilogue epi (EPI_F / EPI_FK / EPI_FKKD, as the LJ kernels), gathering the
 // neighbours' FP32 velocities from d.v32 and, for EPI_FKKD, writing the next

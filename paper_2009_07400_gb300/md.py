@@ -21,7 +21,7 @@ ERRORS = {
     -5: "MD_ERR_NL_OVERFLOW", -6: "MD_ERR_TIMEOUT", -7: "MD_ERR_NONFINITE",
     -8: "MD_ERR_BADPOS", -9: "MD_ERR_STATE",
 }
-MD_FP64, MD_MIXED = 0, 1
+MD_FP64, MD_MIXED, MD_DW = 0, 1, 2
 MD_LIST_FULL, MD_LIST_HALF, MD_LIST_GROUP2, MD_LIST_GROUP4 = 0, 1, 2, 4
 (MD_ERR_INVAL, MD_ERR_BOX_TOO_SMALL, MD_ERR_NOMEM, MD_ERR_CUDA, MD_ERR_NL_OVERFLOW,
  MD_ERR_TIMEOUT, MD_ERR_NONFINITE, MD_ERR_BADPOS, MD_ERR_STATE) = range(-1, -10, -1)

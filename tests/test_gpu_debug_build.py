@@ -3,7 +3,7 @@ checker: every gathered or stored index of the kernels is checked on the
 device, and a bad one raises an error flag (MD_ERR_STATE) instead of
 touching memory.  Here it runs the main paths (per-atom and group lists,
 replicas, the contact model, the adjoint, the force-kernel studies, the
-split-cell build) with no check firing and must agree bit for bit with the
+split-cell build, the double-word path) with no check firing and must agree bit for bit with the
 normal build on every deterministic path (the half-list paths add forces
 with atomics, so only their completion counts)."""
 import os
@@ -73,6 +73,9 @@ with md.MDContext(s.pos, s.vel, s.box, precision=md.MD_MIXED) as c:
     E = c.run(60, energy_every=20)
     cnt, rows = c.neighbors_raw()
     out.append(h(c.positions(), c.velocities(), c.forces(), E, cnt))
+with md.MDContext(s.pos, s.vel, s.box, precision=md.MD_DW) as c:   # double-word pairs
+    E = c.run(60, energy_every=20)
+    out.append(h(c.positions(), c.velocities(), c.forces(), E))
 with md.MDContext(s.pos, s.vel, s.box, precision=md.MD_MIXED, threads_per_atom=1) as c:
     c.run(20)
     out.append(h(*[c.study_force_variant(v, 1, forces=True)[1] for v in range(7)]))
@@ -95,5 +98,5 @@ def test_debug_build_agrees_and_stays_silent():
                            timeout=900)
         assert r.returncode == 0, f"{name}: {r.stderr[-3000:]}"
         res[name] = r.stdout.split()
-    assert len(res["release"]) == 15
+    assert len(res["release"]) == 16
     assert res["debug"] == res["release"]

@@ -1,0 +1,264 @@
+"""Double-word path (precision MD_DW) vs the FP64 oracle, through the C ABI.
+
+The pair arithmetic runs in unevaluated sums of two FP32 numbers (~48
+significant bits): forces must meet the FP64 path's bar and a tighter one,
+|dF_i| <= 1e-11 max(|F_i|, F_rms) per atom (the arithmetic's own error is
+~1e-13 of the pair terms; the positions are represented to ~2^-46 absolute,
+next to FP64's ~1e-14 at box coordinates), and trajectories, energies and
+lists follow the FP64 oracle as the FP64 path does.
+"""
+import numpy as np
+import pytest
+
+from paper_2009_07400_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+RC, SKIN = 2.5, 0.3
+DW_TOL = 1e-11
+
+
+@pytest.fixture(scope="module")
+def md():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2009_07400_gb300 import build
+    build.build()
+    from paper_2009_07400_gb300 import md as m
+    m.load()
+    return m
+
+
+def force_err(F, Fr):
+    frms = np.sqrt(np.mean(np.sum(Fr ** 2, axis=1)))
+    scale = np.maximum(np.linalg.norm(Fr, axis=1), frms)
+    return np.max(np.linalg.norm(F - Fr, axis=1) / scale)
+
+
+def sorted_rows(counts, rows):
+    big = np.iinfo(np.int32).max
+    width = max(1, int(counts.max()))
+    out = np.full((counts.shape[0], width), big, np.int64)
+    mask = np.arange(width)[None, :] < counts[:, None]
+    out[mask] = rows[:, :width][mask]
+    out.sort(axis=1)
+    return out
+
+
+def mi(d, L):
+    return np.mod(d + L / 2, L) - L / 2
+
+
+def liquid(orc, n_cells=7, steps=60, seed=3):
+    s = inputs.fcc_system(n_cells, jitter=0.05, seed=seed)
+    x, v, _ = orc.vv_run(s.pos, s.vel, s.box, steps)
+    return inputs.System(x, v, s.box, seed)
+
+
+def dw_ctx(md, s, **kw):
+    return md.MDContext(s.pos, s.vel, s.box, precision=md.MD_DW, **kw)
+
+
+@pytest.mark.parametrize("tpa", [1, 2, 4, 8])
+@pytest.mark.parametrize("case", ["jitter7", "liquid", "ragged", "aniso"])
+def test_dw_force_parity(md, orc, case, tpa):
+    """Per-atom forces of the first evaluation, with whole and split cells
+    (the order of a cell's entries changes the rounding, not the bar)."""
+    if case == "jitter7":
+        s = inputs.fcc_system(7, jitter=0.1, seed=8)
+    elif case == "liquid":
+        s = liquid(orc)
+    elif case == "aniso":
+        s = inputs.fcc_system(6, jitter=0.1, seed=21)
+        s = inputs.System(s.pos * [1.0, 1.3, 0.8], s.vel, s.box * [1.0, 1.3, 0.8], 21)
+    else:
+        s = inputs.replica_system(2999, 0.82, 1.3, seed=12)
+    xw = orc.wrap(s.pos, s.box)
+    Fr = orc.forces_list(xw, s.box, orc.neighbors_cells(xw, s.box, RC + SKIN))
+    for split in (0, 1):
+        with dw_ctx(md, s, threads_per_atom=tpa) as ctx:
+            ctx.set_cell_split(split)
+            err = force_err(ctx.forces(), Fr)
+            print(case, tpa, split, "max |dF| / max(|F|, F_rms):", err)
+            assert err <= DW_TOL
+
+
+def test_dw_force_params(md, orc):
+    s = liquid(orc, n_cells=6)
+    kw = dict(epsilon=1.7, sigma=0.93, cutoff=2.2, skin=0.4)
+    xw = orc.wrap(s.pos, s.box)
+    Fr = orc.forces_list(xw, s.box, orc.neighbors_cells(xw, s.box, 2.6), epsilon=1.7,
+                         sigma=0.93, cutoff=2.2, skin=0.4)
+    with dw_ctx(md, s, **kw) as ctx:
+        assert force_err(ctx.forces(), Fr) <= DW_TOL
+        # md_set_lj changes the double-word constants too
+        ctx.set_lj(1.0, 1.0)
+        Fr1 = orc.forces_list(xw, s.box, orc.neighbors_cells(xw, s.box, 2.6), epsilon=1.0,
+                              sigma=1.0, cutoff=2.2, skin=0.4)
+        assert force_err(ctx.forces(), Fr1) <= DW_TOL
+
+
+def test_dw_lists_and_energy(md, orc):
+    """Lists (built from the high parts of the split positions) equal the
+    oracle's rows; PE, KE and W at the FP64 path's tolerances."""
+    s = liquid(orc)
+    xw = orc.wrap(s.pos, s.box)
+    pe, w = orc.energy_list(xw, s.box, orc.neighbors_cells(xw, s.box, RC + SKIN, half=True),
+                            half=True)
+    ke = orc.kinetic(s.vel)
+    with dw_ctx(md, s) as ctx:
+        c_g, r_g = ctx.neighbors_raw()
+        c_o, r_o = orc.neighbors_cells_raw(xw, s.box, RC + SKIN)
+        assert np.array_equal(c_g, c_o)
+        assert np.array_equal(sorted_rows(c_g, r_g), sorted_rows(c_o, r_o))
+        gpe, gke, gw = ctx.energy()
+        assert gpe[0] == pytest.approx(pe, rel=1e-12)
+        assert gke[0] == pytest.approx(ke, rel=1e-13)
+        assert gw[0] == pytest.approx(w, rel=1e-11)
+
+
+@pytest.mark.parametrize("tpa", [1, 4])
+def test_dw_run_matches_oracle(md, orc, tpa):
+    """100 steps of the 2,048-atom FCC workload (rebuild every 20): the FP64
+    path's trajectory bar."""
+    s = inputs.workload("fcc8_2048")
+    x_ref, v_ref, _, E_ref = orc.vv_run(s.pos, s.vel, s.box, 100, energies=True)
+    with dw_ctx(md, s, threads_per_atom=tpa) as ctx:
+        E = ctx.run(100, energy_every=20)
+        assert np.abs(mi(ctx.positions() - x_ref, s.box)).max() < 1e-9
+        assert np.abs(ctx.velocities() - v_ref).max() < 1e-8
+        for k in range(5):
+            pe, ke, w = E[k, 0]
+            assert pe == pytest.approx(E_ref[20 * k + 19, 0], rel=1e-10)
+            assert ke == pytest.approx(E_ref[20 * k + 19, 1], rel=1e-10)
+            assert w == pytest.approx(E_ref[20 * k + 19, 2], rel=1e-9)
+
+
+def test_dw_chunks_equal_one_run(md, orc):
+    """A run split into calls (graphs of other shapes) is bitwise the same."""
+    s = liquid(orc, n_cells=6)
+    with dw_ctx(md, s) as a, dw_ctx(md, s) as b:
+        a.run(57)
+        b.run(13)
+        b.run(20)
+        b.run(24)
+        assert np.array_equal(a.positions(), b.positions())
+        assert np.array_equal(a.velocities(), b.velocities())
+
+
+def test_dw_131k_energy(md, orc):
+    """The paper's CPU workload size (131,072 atoms): total energy after 100
+    steps within 1e-10 relative of the oracle, as the FP64 path."""
+    s = inputs.workload("fcc32_131072")
+    x_ref, v_ref, _ = orc.vv_run(s.pos, s.vel, s.box, 100)
+    e_ref = orc.energy(x_ref, s.box)[0] + orc.kinetic(v_ref)
+    with dw_ctx(md, s) as ctx:
+        E = ctx.run(100, energy_every=100)
+    assert E[-1, 0, 0] + E[-1, 0, 1] == pytest.approx(e_ref, rel=1e-10)
+
+
+def test_dw_full_size(md, orc):
+    """1,048,576 atoms after a graph-replayed rebuild cycle: rows equal the
+    oracle's, forces of 4,096 sampled atoms within the bar."""
+    s = inputs.workload("fcc64_1048576")
+    with dw_ctx(md, s) as ctx:
+        ctx.run(20)
+        x = ctx.positions()
+        c_g, r_g = ctx.neighbors_raw()
+        c_o, r_o = orc.neighbors_cells_raw(orc.wrap(x, s.box), s.box, RC + SKIN)
+        assert np.array_equal(c_g, c_o)
+        assert np.array_equal(sorted_rows(c_g, r_g), sorted_rows(c_o, r_o))
+        ids = np.random.default_rng(0).choice(s.n, 4096, replace=False)
+        Fr = orc.forces_sample(x, s.box, ids)
+        assert force_err(ctx.forces()[ids], Fr) <= DW_TOL
+
+
+def test_dw_batched_replicas(md, orc):
+    reps = inputs.replica_ensemble(6, seed=77, n_min=500, n_max=3000)
+    pos = np.concatenate([r.pos for r in reps])
+    vel = np.concatenate([r.vel for r in reps])
+    counts = [r.n for r in reps]
+    with md.MDContext(pos, vel, [r.box for r in reps], counts=counts, precision=md.MD_DW) as ctx:
+        F = ctx.forces()
+        o = 0
+        for r in reps:
+            xw = orc.wrap(r.pos, r.box)
+            Fr = orc.forces_list(xw, r.box, orc.neighbors_cells(xw, r.box, RC + SKIN))
+            assert force_err(F[o:o + r.n], Fr) <= DW_TOL
+            o += r.n
+        E = ctx.run(40, energy_every=40)
+        X = ctx.positions()
+        o = 0
+        for k, r in enumerate(reps):
+            x_ref, _, _, E_ref = orc.vv_run(r.pos, r.vel, r.box, 40, energies=True)
+            assert np.abs(mi(X[o:o + r.n] - x_ref, r.box)).max() < 1e-9
+            assert E[0, k, 0] == pytest.approx(E_ref[-1, 0], rel=1e-10)
+            o += r.n
+
+
+def test_dw_displacement_trigger(md, orc):
+    """rebuild_every = 0 on the double-word path follows the oracle's
+    fresh-list run (the trigger reads the high parts of the positions)."""
+    s = inputs.workload("fcc8_2048")
+    x_ref, v_ref, F_ref = orc.vv_run(s.pos, s.vel, s.box, 200, rebuild_every=1)
+    with dw_ctx(md, s, rebuild_every=0) as ctx:
+        ctx.run(200)
+        assert np.abs(mi(ctx.positions() - x_ref, s.box)).max() < 1e-9
+        assert np.abs(ctx.velocities() - v_ref).max() < 1e-8
+        assert force_err(ctx.forces(), F_ref) <= 1e-10
+
+
+def test_dw_autotune(md, orc):
+    """The autotuner tries full lists with 1, 2, 4 and 8 lanes and keeps the state."""
+    s = liquid(orc, n_cells=6)
+    with dw_ctx(md, s) as ctx:
+        x0 = ctx.positions()
+        chosen = ctx.autotune(20)
+        assert chosen.list_type == md.MD_LIST_FULL
+        assert chosen.threads_per_atom in (1, 2, 4, 8)
+        assert np.array_equal(ctx.positions(), x0)
+
+
+def test_dw_refusals(md, orc):
+    """What the double-word path does not run is refused with MD_ERR_INVAL."""
+    s = inputs.fcc_system(5, jitter=0.05, seed=4)
+    for lt in (md.MD_LIST_HALF, md.MD_LIST_GROUP2, md.MD_LIST_GROUP4):
+        with pytest.raises(md.MDError) as e:
+            dw_ctx(md, s, list_type=lt)
+        assert e.value.code == -1
+    with dw_ctx(md, s) as ctx:
+        with pytest.raises(md.MDError) as e:
+            ctx.adjoint(20, 10, 10)
+        assert e.value.code == -1
+        with pytest.raises(md.MDError) as e:
+            ctx.set_spring_dashpot(100.0, 1.0)
+        assert e.value.code == -1
+        with pytest.raises(md.MDError) as e:
+            ctx.study_force_variant(0, 1)
+        assert e.value.code in (-1, -9)
+        ctx.run(10)                      # the context still runs
+
+
+def test_dw_range_guard(md, orc):
+    """An atom that runs more than a cell side beyond its cell between
+    binnings (no interactions: a dilute lattice, one fast atom, binning only
+    at the start) stops the double-word run with MD_ERR_BADPOS instead of
+    losing the exactness of its split position; the other paths run on."""
+    L = np.full(3, 30.0)                             # 10 cells of side 3 per edge
+    g = (np.arange(4) * 7.5 + 1.0)
+    pos = np.array([[a, b, c] for a in g for b in g for c in g])
+    pos = np.concatenate([pos, [[2.0, 4.75, 4.75]]])   # 5.3 from every lattice line
+    vel = np.zeros_like(pos)
+    vel[-1] = [20.0, 0.0, 0.0]
+    kw = dict(rebuild_every=100000)
+    with md.MDContext(pos, vel, L, precision=md.MD_DW, **kw) as ctx:
+        ctx.run(20)                                  # 2 units: still in range
+        with pytest.raises(md.MDError) as e:
+            ctx.run(200)
+        assert e.value.code == -8
+        assert "double-word" in str(e.value)
+    for prec in (md.MD_FP64, md.MD_MIXED):
+        with md.MDContext(pos, vel, L, precision=prec, **kw) as ctx:
+            ctx.run(220)
+            assert ctx.positions()[-1, 0] == pytest.approx(2.0 + 220 * 0.005 * 20.0, rel=1e-12)
