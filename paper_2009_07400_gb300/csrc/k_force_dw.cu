@@ -4,7 +4,9 @@
 // the forces agree with an FP64 evaluation to ~1e-13 while every operation
 // runs on the FP32 pipe.  GB300's FP64 pipe is about 1/64 of its FP32 rate
 // and bounds the FP64 path (17 FP64 operations per pair); the double-word
-// pair takes about 150 FP32 operations instead.  Precision MD_DW.
+// pair takes about 160 FP32-pipe instructions instead (ncu: 418 M warp
+// instructions for 78.6 M listed pairs before the constant folding below).
+// Precision MD_DW.
 //
 // Building blocks, written from the published error-free transformations:
 //   two_sum      s + e = a + b exactly (Knuth, TAOCP vol. 2, Sec. 4.2.2);
@@ -16,10 +18,14 @@
 //                of Joldes, Muller and Popescu (ACM TOMS 2017);
 //   dw_add       exact sum of the high parts plus the low parts.
 // Intermediate results are not renormalised (their low parts stay within a
-// few ulps of the high parts, which the multiplication tolerates); r^2 is
-// renormalised before the cut-off compare and the reciprocal, and the
-// per-atom sums once per list chunk.  All arithmetic uses the _rn
-// intrinsics so that nothing is contracted or reassociated.
+// few ulps of the high parts, which the multiplication tolerates); the
+// per-atom sums are renormalised once per list chunk.  The cut-off test
+// takes the sign of (r2_h - rc2_h) + (r2_l - rc2_l): the first difference is
+// exact near rc^2 (Sterbenz), so the sign is that of r^2 - rc^2 unless they
+// differ by less than ~2^-47 rc^2.  All arithmetic uses the _rn intrinsics
+// so that nothing is contracted or reassociated.  (Renormalising r^2 first
+// measured 13 % slower together with the unfolded constants below: 73
+// instead of 64 registers.)
 //
 // Positions: p32 holds the high parts of the cell-relative positions, on a
 // grid of step g = 2^k with 2^24 g >= 2.5 cell sides, plo the low parts
@@ -29,9 +35,16 @@
 // 2^24 g) and a low part (p_il -+ s_l) - p_jl rounded once, so the
 // cancellation of nearby positions loses nothing; d is good to ~2^-45.
 //
-// Reciprocal: 1/r^2 from the hardware approximation refined by one FP32
-// Newton step (within ~1 ulp), then one Newton step in double word,
-// y (1 + e) with e = 1 - r^2 y: relative error ~2^-46.
+// Reciprocal: 1/r^2 from the hardware approximation of 1/fl(r2_h + r2_l)
+// refined by one FP32 Newton step (within ~1 ulp), then one Newton step in
+// double word, y (1 + e) with e = 1 - r^2 y: relative error ~2^-46.
+//
+// Pair arithmetic as executed, with sigma and epsilon folded into double-word
+// constants (A12 = 48 eps sigma^12, A6 = 24 eps sigma^6, B12 = 4 eps
+// sigma^12, B6 = 4 eps sigma^6): sr6 = sr2^3,
+//     f = sr2 sr6 (A12 sr6 - A6),   V = sr6 (B12 sr6 - B6),
+// the paper's f = 48 eps sr6' (sr6' - 1/2) sr2 and 4 eps sr6' (sr6' - 1)
+// with sr6' = sigma^6 sr6, regrouped.
 //
 // Epilogue: the FP64 velocity-Verlet update of the mixed path (x and v
 // updated in place), with the force F = (double)h + (double)l; the next
@@ -170,8 +183,8 @@ __global__ void __launch_bounds__(256) k_force_dw_full(Dev d, LJ lj)
     const float qlx0 = __fadd_rn(li.x, R.dw_sl[0]), qlx2 = __fsub_rn(li.x, R.dw_sl[0]);
     const float qly0 = __fadd_rn(li.y, R.dw_sl[1]), qly2 = __fsub_rn(li.y, R.dw_sl[1]);
     const float qlz0 = __fadd_rn(li.z, R.dw_sl[2]), qlz2 = __fsub_rn(li.z, R.dw_sl[2]);
-    const dw rc2 = dw_const(lj.dw_rc2), sig6 = dw_const(lj.dw_sig6), c48 = dw_const(lj.dw_c48);
-    const dw c24n = {-lj.dw_c24[0], -lj.dw_c24[1]};
+    const dw rc2 = dw_const(lj.dw_rc2);
+    const dw a12 = dw_const(lj.dw_a12), a6n = {-lj.dw_a6[0], -lj.dw_a6[1]};
 
     dw ax = {0.f, 0.f}, ay = {0.f, 0.f}, az = {0.f, 0.f}, ape = {0.f, 0.f}, aw = {0.f, 0.f};
 
@@ -189,23 +202,22 @@ __global__ void __launch_bounds__(256) k_force_dw_full(Dev d, LJ lj)
         const float dyl = __fsub_rn(y2 ? qly2 : (y1 ? li.y : qly0), lj4.y);
         const float dzl = __fsub_rn(z2 ? qlz2 : (z1 ? li.z : qlz0), lj4.z);
         dw r2 = dw_add(dw_add(dw_sq_of(dxh, dxl), dw_sq_of(dyh, dyl)), dw_sq_of(dzh, dzl));
-        r2 = fast_two_sum(r2.h, r2.l);
-        const bool in = r2.h < rc2.h || (r2.h == rc2.h && r2.l < rc2.l);
+        const bool in = __fadd_rn(__fsub_rn(r2.h, rc2.h), __fsub_rn(r2.l, rc2.l)) < 0.f;
         // 1 / r^2
-        float y = rcp_approx(r2.h);
-        y = __fmaf_rn(y, __fmaf_rn(-r2.h, y, 1.f), y);
+        const float rf = __fadd_rn(r2.h, r2.l);
+        float y = rcp_approx(rf);
+        y = __fmaf_rn(y, __fmaf_rn(-rf, y, 1.f), y);
         const float er = __fmaf_rn(-r2.l, y, __fmaf_rn(-r2.h, y, 1.f));
         const dw sr2 = {y, __fmul_rn(y, er)};
-        // t = sr2^3 sigma^6 (the paper's sr6); f = sr2 t (48 eps t - 24 eps)
-        const dw t = dw_mul(dw_mul(dw_mul(sr2, sr2), sr2), sig6);
-        dw f = dw_mul(dw_mul(sr2, t), dw_add(dw_mul(c48, t), c24n));
+        const dw sr6 = dw_mul(dw_mul(sr2, sr2), sr2);
+        dw f = dw_mul(dw_mul(sr2, sr6), dw_add(dw_mul(a12, sr6), a6n));
         f.h = in ? f.h : 0.f;
         f.l = in ? f.l : 0.f;
         ax = dw_add(ax, dw_mul(f, dw{dxh, dxl}));
         ay = dw_add(ay, dw_mul(f, dw{dyh, dyl}));
         az = dw_add(az, dw_mul(f, dw{dzh, dzl}));
         if (ENERGY) {
-            dw v = dw_mul(dw_mul(dw_const(lj.dw_c4), t), dw_add(t, dw{-1.f, 0.f}));
+            dw v = dw_mul(sr6, dw_add(dw_mul(dw_const(lj.dw_b12), sr6), dw{-lj.dw_b6[0], -lj.dw_b6[1]}));
             v.h = in ? v.h : 0.f;
             v.l = in ? v.l : 0.f;
             ape = dw_add(ape, v);

@@ -752,10 +752,11 @@ void set_lj_constants(md_ctx *c)
         out[1] = (float)(v - (double)out[0]);
     };
     split2(lj.rc2, lj.dw_rc2);
-    split2(lj.sigma6, lj.dw_sig6);
-    split2(lj.c48e, lj.dw_c48);
-    split2(lj.c24e, lj.dw_c24);
-    split2(lj.c4e, lj.dw_c4);
+    const double s6 = lj.sigma6, s12 = lj.sigma6 * lj.sigma6;
+    split2(48.0 * q.epsilon * s12, lj.dw_a12);
+    split2(24.0 * q.epsilon * s6, lj.dw_a6);
+    split2(4.0 * q.epsilon * s12, lj.dw_b12);
+    split2(4.0 * q.epsilon * s6, lj.dw_b6);
     lj.rs2f_lo = (float)(lj.rs2 * (1.0 - 2.5e-4));
     lj.rs2f_hi = (float)(lj.rs2 * (1.0 + 2.5e-4));
     // spring-dashpot constants (pot, sd_k, sd_g are set by md_set_spring_dashpot)

@@ -160,8 +160,9 @@ struct LJ {
     double dt;
     double mass;
     float rs2f_lo, rs2f_hi;   // FP32 prefilter band around rs^2 (exact FP64 test inside)
-    // double-word constants (precision MD_DW): {fl32(c), fl32(c - fl32(c))}
-    float dw_rc2[2], dw_sig6[2], dw_c48[2], dw_c24[2], dw_c4[2];
+    // double-word constants (precision MD_DW) as {fl32(c), fl32(c - fl32(c))}:
+    // rc^2, 48 eps sigma^12, 24 eps sigma^6, 4 eps sigma^12, 4 eps sigma^6
+    float dw_rc2[2], dw_a12[2], dw_a6[2], dw_b12[2], dw_b6[2];
     // spring-dashpot contact (Eq. 3; pot == 1): K, gamma, sigma^2 (sigma = diameter)
     int32_t pot;
     double sd_k, sd_g, sd_sig2;
