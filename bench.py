@@ -180,20 +180,22 @@ def ncu_traffic(list_type=0):
 
 
 def parse_tuned(text):
-    """--tuned "TPA,LIST,TPA64,LIST64" -> ({mixed kwargs}, {FP64 kwargs}) or
-    None (LIST: 0 full, 1 half, 2 / 4 group lists).  Skips the autotuner:
+    """--tuned "TPA,LIST,TPA64,LIST64[,TPADW]" -> ({mixed kwargs}, {FP64
+    kwargs}, {double-word kwargs or None}) or None (LIST: 0 full, 1 half, 2 / 4
+    group lists; the double-word path runs full lists).  Skips the autotuner:
     under a profiler its timings include the profiler's per-launch overhead
     and it may choose another candidate than the timed run did, so profiling
     commands pin the timed run's choice."""
     if not text:
         return None
     v = [int(x) for x in text.split(",")]
-    if (len(v) != 4 or v[0] not in (1, 2, 4, 8) or v[2] not in (1, 2, 4, 8)
-            or v[1] not in LIST_NAMES or v[3] not in (0, 1)):
-        raise SystemExit("--tuned wants TPA,LIST,TPA64,LIST64 with TPA in {1,2,4,8}, "
+    if (len(v) not in (4, 5) or v[0] not in (1, 2, 4, 8) or v[2] not in (1, 2, 4, 8)
+            or v[1] not in LIST_NAMES or v[3] not in (0, 1) or (len(v) == 5 and v[4] not in (1, 2, 4, 8))):
+        raise SystemExit("--tuned wants TPA,LIST,TPA64,LIST64[,TPADW] with TPA in {1,2,4,8}, "
                          "LIST in {0,1,2,4} (FP64: {0,1})")
     return (dict(threads_per_atom=v[0], list_type=v[1]),
-            dict(threads_per_atom=v[2], list_type=v[3]))
+            dict(threads_per_atom=v[2], list_type=v[3]),
+            dict(threads_per_atom=v[4], list_type=0) if len(v) == 5 else None)
 
 
 def algorithmic_bytes_per_atom(mean_nb, list_type, rows_per_atom=1.0):
@@ -320,9 +322,13 @@ def run_gpu(args):
     # full per-atom lists, lanes per atom from the autotuner (one lane on the
     # paper-shaped workload, as its FP64 leg)
     dw_kw = dict(threads_per_atom=1) if paper_shaped else {}
+    if pin and pin[2] and not paper_shaped:
+        dw_kw = pin[2]
     with make(precision=md.MD_DW, **dw_kw) as ctx:
         if paper_shaped:
             res["tuned_dw"] = {"threads_per_atom": 1, "list_type": 0, "paper_shaped": True}
+        elif pin and pin[2]:
+            res["tuned_dw"] = dict(pin[2], pinned=True)
         else:
             tdw = ctx.autotune(STEPS_PER_CYCLE)
             res["tuned_dw"] = {"threads_per_atom": tdw.threads_per_atom,
@@ -952,7 +958,7 @@ def main():
                          "8,388,608-atom sizing run; ensemble: 256 replicas; fcc80: the "
                          "paper's 2,048,000-atom GPU shape; dem: 1,048,576 spheres with "
                          "the contact model of Eq. 3")
-    ap.add_argument("--tuned", metavar="TPA,HALF,TPA64,HALF64",
+    ap.add_argument("--tuned", metavar="TPA,LIST,TPA64,LIST64[,TPADW]",
                     help="skip the autotuner and use these lanes per atom and list "
                          "types for the mixed and FP64 legs (for profiling commands)")
     ap.add_argument("--cellorder-child", type=int, choices=[1, 2, 4], help=argparse.SUPPRESS)

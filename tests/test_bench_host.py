@@ -31,11 +31,14 @@ def test_algorithmic_bytes_per_atom():
 def test_parse_tuned():
     assert bench.parse_tuned(None) is None
     assert bench.parse_tuned("") is None
-    mixed, fp64 = bench.parse_tuned("1,0,2,1")
+    mixed, fp64, dw = bench.parse_tuned("1,0,2,1")
     assert mixed == {"threads_per_atom": 1, "list_type": 0}
     assert fp64 == {"threads_per_atom": 2, "list_type": 1}
+    assert dw is None
     assert bench.parse_tuned("1,4,2,0")[0] == {"threads_per_atom": 1, "list_type": 4}
-    for bad in ("3,0,1,0", "1,0,1", "1,0,16,0", "1,3,1,0", "1,0,1,4"):
+    assert bench.parse_tuned("1,0,2,0,4")[2] == {"threads_per_atom": 4, "list_type": 0}
+    for bad in ("3,0,1,0", "1,0,1", "1,0,16,0", "1,3,1,0", "1,0,1,4", "1,0,1,0,3",
+                "1,0,1,0,1,1"):
         with pytest.raises(SystemExit):
             bench.parse_tuned(bad)
 
