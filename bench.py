@@ -731,7 +731,7 @@ def run_adjoint(args):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     res = {}
-    for label, prec in (("mixed", md.MD_MIXED), ("fp64", md.MD_FP64)):
+    for label, prec in (("mixed", md.MD_MIXED), ("fp64", md.MD_FP64), ("dw", md.MD_DW)):
         with md.MDContext(s.pos, s.vel, s.box, stream=stream.cuda_stream, precision=prec) as ctx:
             # lanes per atom of the force kernels tuned as in the main bench
             # (md_adjoint walks full per-atom lists: another choice falls back)
@@ -770,6 +770,7 @@ def run_adjoint(args):
 
     out_m, t_m, f_m, tune_m = res["mixed"]
     out_d, t_d, f_d, tune_d = res["fp64"]
+    out_w, t_w, f_w, tune_w = res["dw"]
     rate = lambda t: n * nsteps / t                          # noqa: E731
     line = {
         "metric": "atom-timesteps/s of the differentiated LJ rollout (forward + reverse sweep)",
@@ -781,10 +782,12 @@ def run_adjoint(args):
                                f"loss = mean PE over the last {window}, checkpoints every {ckpt}, "
                                "gradients w.r.t. epsilon, sigma, x0, v0", "atoms": n,
                    "timesteps_per_step": nsteps, "seed": inputs.WORKLOADS[name]["seed"],
-                   "tuned": {"mixed": tune_m, "fp64": tune_d}},
-        "adjoint_over_forward": {"mixed": t_m / f_m, "fp64": t_d / f_d},
+                   "tuned": {"mixed": tune_m, "fp64": tune_d, "dw": tune_w}},
+        "adjoint_over_forward": {"mixed": t_m / f_m, "fp64": t_d / f_d, "dw": t_w / f_w},
         "fp64_path": {"value": rate(t_d), "ms_per_step": t_d * 1e3},
-        "gradient_error_vs_oracle": {"mixed": errs(out_m), "fp64": errs(out_d)},
+        "dw_path": {"value": rate(t_w), "ms_per_step": t_w * 1e3,
+                    "note": "double-word forward and recompute, FP64 reverse pair terms"},
+        "gradient_error_vs_oracle": {"mixed": errs(out_m), "fp64": errs(out_d), "dw": errs(out_w)},
         "cpu_baseline": {"value": rate(t_orc), "unit": UNIT, "cores": oracle.num_threads(),
                          "kind": "oracle",
                          "sample": f"the oracle's FP64 reverse sweep of the same rollout "

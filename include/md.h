@@ -62,7 +62,8 @@ extern "C" {
                        on a power-of-two grid and a low part at each binning and step;
                        an atom that moves more than a cell side beyond its cell between
                        binnings stops the run with MD_ERR_BADPOS.  Full per-atom lists
-                       only (MD_LIST_FULL); no contact model, no md_adjoint.          */
+                       only (MD_LIST_FULL); no contact model.  md_adjoint runs the
+                       forward in double word and the reverse pair terms in FP64.   */
 
 /* Verlet-list layouts (md_params.list_type).  All hold every pair with
  * r^2 < (rc + skin)^2 at the build (Sec. 3.2, Fig. 1); md_get_neighbors
@@ -324,8 +325,8 @@ int md_set_spring_dashpot(md_ctx *ctx, double k_spring, double gamma);
  * for later calls, grown when a call needs more, and is freed by md_destroy;
  * if growing it fails the whole workspace is released and MD_ERR_NOMEM
  * returned.
- * Errors: MD_ERR_INVAL (nrep != 1; rebuild_every == 0; spring-dashpot model; an MD_DW
- * context; window not in [1, nsteps]; ckpt_every not dividing both rebuild_every and nsteps),
+ * Errors: MD_ERR_INVAL (nrep != 1; rebuild_every == 0; spring-dashpot model; window not in
+ * [1, nsteps]; ckpt_every not dividing both rebuild_every and nsteps),
  * MD_ERR_NOMEM, MD_ERR_CUDA and those of md_run. */
 int md_adjoint(md_ctx *ctx, int64_t nsteps, int64_t window, int32_t ckpt_every, double *loss,
                double *g_eps, double *g_sigma, double *g_x0, double *g_v0);
@@ -342,9 +343,10 @@ int md_adjoint_device(md_ctx *ctx, int64_t nsteps, int64_t window, int32_t ckpt_
  * vector products and the parameter derivatives): MD_MIXED evaluates them in
  * FP32 from the cell-relative FP32 positions (the default of a mixed
  * context), MD_FP64 in FP64 from the FP64 positions (the default of an FP64
- * context).  The forward run keeps the context's precision, so a mixed
- * context with MD_FP64 here differentiates its own mixed trajectory with
- * FP64 pair terms.  Not in the paper.  Errors: MD_ERR_INVAL. */
+ * context, and of an MD_DW context).  The forward run keeps the context's
+ * precision, so a mixed context with MD_FP64 here differentiates its own
+ * mixed trajectory with FP64 pair terms.  Not in the paper.
+ * Errors: MD_ERR_INVAL. */
 int md_set_adjoint_precision(md_ctx *ctx, int32_t precision);
 
 /* Force-kernel studies: variants of the mixed full-list force pass that the

@@ -126,6 +126,7 @@ struct md_ctx {
         int64_t nck = 0, ckpt = 0;
         dvec4 *ck_x = nullptr, *ck_v = nullptr, *blk_x = nullptr, *xbar = nullptr, *wbar = nullptr;
         float4 *blk_p = nullptr, *ck_p = nullptr, *wbar32 = nullptr;
+        float4 *ck_plo = nullptr;   // double-word path: the low parts beside ck_p
         int32_t *ck_id = nullptr;
         double *ge = nullptr, *gs = nullptr, *g2 = nullptr;
     } adj;
@@ -242,7 +243,7 @@ void free_all(md_ctx *c)
                     c->w_atom, c->pe64, c->w64, c->ke64, c->status, c->chunk_rep_d,
                     c->chunk_first_d, c->partials_d, c->eout_d, c->elog_d, c->io_d, c->ctr_d,
                     c->p32_ref, c->v32[0], c->v32[1], c->adj.ck_x, c->adj.ck_v, c->adj.blk_x,
-                    c->adj.xbar, c->adj.wbar, c->adj.blk_p, c->adj.ck_p, c->adj.wbar32,
+                    c->adj.xbar, c->adj.wbar, c->adj.blk_p, c->adj.ck_p, c->adj.wbar32, c->adj.ck_plo,
                     c->adj.ck_id, c->adj.ge, c->adj.gs, c->adj.g2, c->grp, c->gcnt,
                     c->gcell_start, c->gnb, c->gnb_count, c->offtab_d, c->gmask, c->gpair,
                     c->plo[0], c->plo[1]};
@@ -1458,14 +1459,15 @@ static int adjoint_impl(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt,
     if (c->disp)
         return fail(c, MD_ERR_INVAL, "md_adjoint needs the fixed rebuild schedule (rebuild_every > 0)");
     if (is_sd(c)) return fail(c, MD_ERR_INVAL, "md_adjoint differentiates the Lennard-Jones force only");
-    if (is_dw(c)) return fail(c, MD_ERR_INVAL, "md_adjoint runs on MD_FP64 or MD_MIXED contexts");
     const int64_t every = c->p.rebuild_every;
     if (every % ckpt != 0 || nsteps % ckpt != 0)
         return fail(c, MD_ERR_INVAL, "ckpt_every must divide rebuild_every and nsteps");
     const int64_t n = c->n, nck = nsteps / ckpt + 1;
     // precision of the reverse sweep's pair terms (the forward run always
-    // uses the context's precision)
+    // uses the context's precision; a double-word context takes FP64 pair
+    // terms unless md_set_adjoint_precision chose MD_MIXED)
     const bool mixed = c->adj_prec < 0 ? is_mixed(c) : c->adj_prec == MD_MIXED;
+    const bool dw = is_dw(c);
     const int lt0 = c->p.list_type, tpa0 = c->tpa;
     int rc = MD_OK;
     // the adjoint walks full per-atom lists (with the default lanes per atom
@@ -1478,7 +1480,7 @@ static int adjoint_impl(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt,
     // workspace: reused between calls, grown when a call needs more
     auto &W = c->adj;
     auto drop = [](auto *&p) { if (p) cudaFree(p); p = nullptr; };
-    if (nck > W.nck) { drop(W.ck_x); drop(W.ck_v); drop(W.ck_id); drop(W.ck_p); W.nck = 0; }
+    if (nck > W.nck) { drop(W.ck_x); drop(W.ck_v); drop(W.ck_id); drop(W.ck_p); drop(W.ck_plo); W.nck = 0; }
     if (ckpt > W.ckpt) { drop(W.blk_x); drop(W.blk_p); W.ckpt = 0; }
     if ((!W.ck_x && ((rc = dalloc(c, &W.ck_x, (size_t)(nck * n))) || (rc = dalloc(c, &W.ck_v, (size_t)(nck * n))) ||
                      (rc = dalloc(c, &W.ck_id, (size_t)(nck * n))) || (rc = dalloc(c, &W.ck_p, (size_t)(nck * n))))) ||
@@ -1486,9 +1488,10 @@ static int adjoint_impl(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt,
         (!W.xbar && ((rc = dalloc(c, &W.xbar, (size_t)n)) || (rc = dalloc(c, &W.wbar, (size_t)n)) ||
                      (rc = dalloc(c, &W.ge, (size_t)n)) || (rc = dalloc(c, &W.gs, (size_t)n)) ||
                      (rc = dalloc(c, &W.g2, 2)))) ||
-        (mixed && !W.wbar32 && (rc = dalloc(c, &W.wbar32, (size_t)n)))) {
+        (mixed && !W.wbar32 && (rc = dalloc(c, &W.wbar32, (size_t)n))) ||
+        (dw && !W.ck_plo && (rc = dalloc(c, &W.ck_plo, (size_t)(W.nck ? W.nck * n : nck * n))))) {
         // release the whole workspace: a later call starts from scratch
-        drop(W.ck_x); drop(W.ck_v); drop(W.ck_id); drop(W.ck_p); drop(W.blk_x); drop(W.blk_p);
+        drop(W.ck_x); drop(W.ck_v); drop(W.ck_id); drop(W.ck_p); drop(W.ck_plo); drop(W.blk_x); drop(W.blk_p);
         drop(W.xbar); drop(W.wbar); drop(W.wbar32); drop(W.ge); drop(W.gs); drop(W.g2);
         W.nck = W.ckpt = 0;
         return rc;
@@ -1497,6 +1500,7 @@ static int adjoint_impl(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt,
     W.ckpt = std::max<int64_t>(W.ckpt, ckpt);
     dvec4 *ck_x = W.ck_x, *ck_v = W.ck_v, *blk_x = W.blk_x, *xbar = W.xbar, *wbar = W.wbar;
     float4 *blk_p = W.blk_p, *ck_p = W.ck_p, *wbar32 = mixed ? W.wbar32 : nullptr;
+    float4 *ck_plo = dw ? W.ck_plo : nullptr;
     int32_t *ck_id = W.ck_id;
     double *ge = W.ge, *gs = W.gs, *g2 = W.g2;
     if (window > c->elog_cap) {
@@ -1513,14 +1517,19 @@ static int adjoint_impl(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt,
         cudaMemcpyAsync(ck_v + k * n, c->v[c->vp], sizeof(dvec4) * n, cudaMemcpyDeviceToDevice, c->st);
         cudaMemcpyAsync(ck_id + k * n, c->id[c->vp], sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, c->st);
         cudaMemcpyAsync(ck_p + k * n, c->p32[c->pb], sizeof(float4) * n, cudaMemcpyDeviceToDevice, c->st);
+        if (ck_plo)
+            cudaMemcpyAsync(ck_plo + k * n, c->plo[c->pb], sizeof(float4) * n, cudaMemcpyDeviceToDevice, c->st);
     };
     auto load_ck = [&](int64_t k, bool with_id) {
         cudaMemcpyAsync(c->x[c->xp], ck_x + k * n, sizeof(dvec4) * n, cudaMemcpyDeviceToDevice, c->st);
         cudaMemcpyAsync(c->v[c->vp], ck_v + k * n, sizeof(dvec4) * n, cudaMemcpyDeviceToDevice, c->st);
         if (with_id)
             cudaMemcpyAsync(c->id[c->vp], ck_id + k * n, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, c->st);
-        else  // mid-epoch: the FP32 cell-relative copy of the same step
+        else {  // mid-epoch: the FP32 cell-relative copy of the same step
             cudaMemcpyAsync(c->p32[c->pb], ck_p + k * n, sizeof(float4) * n, cudaMemcpyDeviceToDevice, c->st);
+            if (ck_plo)   // and on the double-word path its low parts
+                cudaMemcpyAsync(c->plo[c->pb], ck_plo + k * n, sizeof(float4) * n, cudaMemcpyDeviceToDevice, c->st);
+        }
     };
     // state at force point cb: the list of its epoch (built from the epoch's
     // start positions, which re-binning reproduces bit for bit), then x, v.

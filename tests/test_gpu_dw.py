@@ -229,9 +229,6 @@ def test_dw_refusals(md, orc):
         assert e.value.code == -1
     with dw_ctx(md, s) as ctx:
         with pytest.raises(md.MDError) as e:
-            ctx.adjoint(20, 10, 10)
-        assert e.value.code == -1
-        with pytest.raises(md.MDError) as e:
             ctx.set_spring_dashpot(100.0, 1.0)
         assert e.value.code == -1
         with pytest.raises(md.MDError) as e:
@@ -262,3 +259,45 @@ def test_dw_range_guard(md, orc):
         with md.MDContext(pos, vel, L, precision=prec, **kw) as ctx:
             ctx.run(220)
             assert ctx.positions()[-1, 0] == pytest.approx(2.0 + 220 * 0.005 * 20.0, rel=1e-12)
+
+
+def rel(a, b):
+    return abs(a - b) / abs(b)
+
+
+@pytest.mark.parametrize("nsteps,window,every,ckpt,lanes", [(40, 10, 20, 10, 1), (60, 25, 20, 20, 2),
+                                                            (30, 30, 10, 5, 4)])
+def test_dw_adjoint_matches_oracle(md, orc, nsteps, window, every, ckpt, lanes):
+    """md_adjoint on a double-word context (double-word forward and
+    recompute, FP64 reverse pair terms) against the oracle's FP64 reverse
+    sweep: the loss and every gradient far inside the FP64 path's bar."""
+    s = inputs.fcc_system(5, jitter=0.05, seed=41)        # 500 atoms
+    x, v, _ = orc.vv_run(s.pos, s.vel, s.box, 40)
+    x0, v0, L = orc.wrap(x, s.box), v, s.box
+    loss_o, ge_o, gs_o, gx_o, gv_o = orc.adjoint(x0, v0, L, nsteps, window, rebuild_every=every)
+    with md.MDContext(x0, v0, L, precision=md.MD_DW, rebuild_every=every,
+                      threads_per_atom=lanes) as ctx:
+        loss, ge, gs, gx, gv = ctx.adjoint(nsteps, window, ckpt)
+        again = ctx.adjoint(nsteps, window, ckpt)          # the workspace is reused
+        xa = ctx.positions()
+    e = [rel(loss, loss_o), rel(ge, ge_o), rel(gs, gs_o),
+         np.linalg.norm(gx - gx_o) / np.linalg.norm(gx_o),
+         np.linalg.norm(gv - gv_o) / np.linalg.norm(gv_o)]
+    print("double-word adjoint errors (loss, eps, sigma, x0, v0):", e)
+    assert e[0] < 1e-11 and max(e[1:]) < 1e-8
+    assert again[0] == loss and np.array_equal(again[3], gx)
+    assert np.array_equal(xa, x0) or np.abs(mi(xa - x0, L)).max() == 0.0
+
+
+def test_dw_adjoint_full_config(md, orc):
+    """16,384 atoms, 200 steps, window 50, checkpoints every 10: the FP64
+    path's bar (1e-6 per scalar and in relative norm)."""
+    s = inputs.workload("fcc16_16384")
+    loss_o, ge_o, gs_o, gx_o, gv_o = orc.adjoint(s.pos, s.vel, s.box, 200, 50)
+    with dw_ctx(md, s) as ctx:
+        loss, ge, gs, gx, gv = ctx.adjoint(200, 50, 10)
+    e = [rel(loss, loss_o), rel(ge, ge_o), rel(gs, gs_o),
+         np.linalg.norm(gx - gx_o) / np.linalg.norm(gx_o),
+         np.linalg.norm(gv - gv_o) / np.linalg.norm(gv_o)]
+    print("double-word adjoint, full config (loss, eps, sigma, x0, v0):", e)
+    assert e[0] < 1e-12 and max(e[1:]) < 1e-6
