@@ -786,7 +786,7 @@ def run_adjoint(args):
         "adjoint_over_forward": {"mixed": t_m / f_m, "fp64": t_d / f_d, "dw": t_w / f_w},
         "fp64_path": {"value": rate(t_d), "ms_per_step": t_d * 1e3},
         "dw_path": {"value": rate(t_w), "ms_per_step": t_w * 1e3,
-                    "note": "double-word forward and recompute, FP64 reverse pair terms"},
+                    "note": "double-word forward, recompute and reverse pair terms"},
         "gradient_error_vs_oracle": {"mixed": errs(out_m), "fp64": errs(out_d), "dw": errs(out_w)},
         "cpu_baseline": {"value": rate(t_orc), "unit": UNIT, "cores": oracle.num_threads(),
                          "kind": "oracle",

@@ -63,7 +63,8 @@ extern "C" {
                        an atom that moves more than a cell side beyond its cell between
                        binnings stops the run with MD_ERR_BADPOS.  Full per-atom lists
                        only (MD_LIST_FULL); no contact model.  md_adjoint runs the
-                       forward in double word and the reverse pair terms in FP64.   */
+                       forward and, by default, the reverse pair terms in double
+                       word (md_set_adjoint_precision).                             */
 
 /* Verlet-list layouts (md_params.list_type).  All hold every pair with
  * r^2 < (rc + skin)^2 at the build (Sec. 3.2, Fig. 1); md_get_neighbors
@@ -343,10 +344,12 @@ int md_adjoint_device(md_ctx *ctx, int64_t nsteps, int64_t window, int32_t ckpt_
  * vector products and the parameter derivatives): MD_MIXED evaluates them in
  * FP32 from the cell-relative FP32 positions (the default of a mixed
  * context), MD_FP64 in FP64 from the FP64 positions (the default of an FP64
- * context, and of an MD_DW context).  The forward run keeps the context's
+ * context), MD_DW in double word from the split positions (the default of an
+ * MD_DW context, and only there).  The forward run keeps the context's
  * precision, so a mixed context with MD_FP64 here differentiates its own
  * mixed trajectory with FP64 pair terms.  Not in the paper.
- * Errors: MD_ERR_INVAL. */
+ * Errors: MD_ERR_INVAL (another value; MD_DW on a context of another
+ * precision). */
 int md_set_adjoint_precision(md_ctx *ctx, int32_t precision);
 
 /* Force-kernel studies: variants of the mixed full-list force pass that the

@@ -256,10 +256,11 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs_f32(Dev d, LJ lj, AdjArgs
 }
 
 // wbar += dt xbar (caller order) for the atom in slot s, and the FP32 copy
-// of the result into slot s (the current slot order, id: slot -> caller id).
+// of the result into slot s (the current slot order, id: slot -> caller id);
+// with wbar_lo also the low parts fl32(w - fl32(w)) (a double-word copy).
 __global__ void __launch_bounds__(256) k_adjoint_axpy(int64_t n, double dt, const dvec4 *xbar,
                                                       dvec4 *wbar, float4 *wbar32,
-                                                      const int32_t *id)
+                                                      float4 *wbar_lo, const int32_t *id)
 {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
@@ -270,7 +271,13 @@ __global__ void __launch_bounds__(256) k_adjoint_axpy(int64_t n, double dt, cons
     w.y = fma(dt, x.y, w.y);
     w.z = fma(dt, x.z, w.z);
     wbar[a] = w;
-    if (wbar32) wbar32[s] = make_float4((float)w.x, (float)w.y, (float)w.z, 0.f);
+    if (wbar32) {
+        const float hx = (float)w.x, hy = (float)w.y, hz = (float)w.z;
+        wbar32[s] = make_float4(hx, hy, hz, 0.f);
+        if (wbar_lo)
+            wbar_lo[s] = make_float4((float)(w.x - (double)hx), (float)(w.y - (double)hy),
+                                     (float)(w.z - (double)hz), 0.f);
+    }
 }
 
 // out (n x 3 doubles) <- a (padded FP64 3-vectors), same atom order.
@@ -335,9 +342,10 @@ int launch_adjoint_pairs(const Dev &d, const LJ &lj, bool mixed, int lanes, cons
 }
 
 int launch_adjoint_axpy(int64_t n, double dt, const dvec4 *xbar, dvec4 *wbar, float4 *wbar32,
-                        const int32_t *id, cudaStream_t st, int *nl)
+                        float4 *wbar_lo, const int32_t *id, cudaStream_t st, int *nl)
 {
-    k_adjoint_axpy<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, dt, xbar, wbar, wbar32, id);
+    if (wbar_lo && !wbar32) return -1;
+    k_adjoint_axpy<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, dt, xbar, wbar, wbar32, wbar_lo, id);
     *nl += 1;
     return (int)cudaGetLastError();
 }

@@ -277,6 +277,142 @@ void launch_dw(const Dev &d, const LJ &lj, int epi, bool energy, cudaStream_t st
 #undef MD_DW_K
 }
 
+
+// ---------------------------------------------------------------------------
+// Adjoint pair terms in double word (md_adjoint on an MD_DW context, pair
+// precision MD_DW): the Jacobian-vector product J(x) w and the parameter
+// derivatives of k_adjoint.cu's FP64 kernel, term for term, with sigma and
+// epsilon folded into double-word constants (s = sigma, sr8 = sr2 sr6,
+// sr10 = sr8 sr2):
+//   f            = sr8 (A12 sr6 - A6)        A12 = 48 eps s^12, A6 = 24 eps s^6
+//   2 f'         = sr10 (D6 - D12 sr6)       D6 = 192 eps s^6, D12 = 672 eps s^12
+//   f / eps      = sr8 (E12 sr6 - E6)        E12 = 48 s^12, E6 = 24 s^6
+//   df / dsigma  = sr8 (S12 sr6 - S6)        S12 = 576 eps s^11, S6 = 144 eps s^5
+//   dV/deps / 2  = sr6 (P12 sr6 - P6)        P12 = 2 s^12, P6 = 2 s^6
+//   dV/dsigma / 2 = sr6 (Q12 sr6 - Q6)       Q12 = 24 eps s^11, Q6 = 12 eps s^5
+// (f' = df/d(r^2)).  Per pair, with u the adjoint w and du = u_i - u_j:
+//   (J u)_i += f du + 2 f' d (d . du),  g_eps += (f / eps)(d . u_i),
+//   g_sigma += (df / dsigma)(d . u_i), and inside the loss window F_i and the
+//   PE derivatives.  Geometry from the high and low parts of the positions
+// (snapshots in p32 / plo), the neighbour's u from double-word copies in slot
+// order (wbar_h, wbar_l, written by the axpy kernel); per-atom sums in double
+// word, added to the FP64 adjoint state (caller order) once per atom.
+struct DwAdjArgs {
+    const float4 *wh, *wl;   // u in slot order: high and low parts
+    dvec4 *xbar;             // caller order, updated
+    double *g_eps, *g_sig;   // caller order, updated
+    double k, lw;
+};
+
+__device__ __forceinline__ dw dw_axb(dw a, dw x, dw b)   // a x - b
+{
+    return dw_add(dw_mul(a, x), dw{-b.h, -b.l});
+}
+
+template <bool WINDOW, int TPA>
+__global__ void __launch_bounds__(128) k_adjoint_pairs_dw(Dev d, LJ lj, DwAdjArgs a)
+{
+    if (stopped(d.status)) return;
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i0 = gt / TPA;
+    const int sub = (int)(gt % TPA);
+    const bool valid = i0 < d.n;
+    if (TPA == 1 && !valid) return;
+    const int64_t i = valid ? i0 : d.n - 1;   // idle lanes still join the shuffles
+    const Rep &R = d.reps[0];
+    const int32_t idi = d.id[i];
+    const float4 hi = d.p32[i], li = d.plo[i];
+    const float4 uih = a.wh[i], uil = a.wl[i];
+    const dw uix = {uih.x, uil.x}, uiy = {uih.y, uil.y}, uiz = {uih.z, uil.z};
+    const int cnt = valid && MD_CHECK(d, d.nb_count[i] <= d.cap) ? d.nb_count[i] : 0;
+    const int4 *nb4 = reinterpret_cast<const int4 *>(d.nb);
+    const float qhx0 = __fadd_rn(hi.x, R.dw_sh[0]), qhx2 = __fsub_rn(hi.x, R.dw_sh[0]);
+    const float qhy0 = __fadd_rn(hi.y, R.dw_sh[1]), qhy2 = __fsub_rn(hi.y, R.dw_sh[1]);
+    const float qhz0 = __fadd_rn(hi.z, R.dw_sh[2]), qhz2 = __fsub_rn(hi.z, R.dw_sh[2]);
+    const float qlx0 = __fadd_rn(li.x, R.dw_sl[0]), qlx2 = __fsub_rn(li.x, R.dw_sl[0]);
+    const float qly0 = __fadd_rn(li.y, R.dw_sl[1]), qly2 = __fsub_rn(li.y, R.dw_sl[1]);
+    const float qlz0 = __fadd_rn(li.z, R.dw_sl[2]), qlz2 = __fsub_rn(li.z, R.dw_sl[2]);
+    const dw rc2 = dw_const(lj.dw_rc2);
+    const dw zero = {0.f, 0.f};
+    dw jx = zero, jy = zero, jz = zero, ge = zero, gs = zero;
+    dw fx = zero, fy = zero, fz = zero, pe_e = zero, pe_s = zero;
+    for (int q = sub; 4 * q < cnt; q += TPA) {
+      const int4 e4 = __ldcs(nb4 + (int64_t)q * d.n + i);
+      const uint32_t es[4] = {(uint32_t)e4.x, (uint32_t)e4.y, (uint32_t)e4.z, (uint32_t)e4.w};
+#pragma unroll
+      for (int t4 = 0; t4 < 4; t4++) {
+        if (4 * q + t4 >= cnt) break;
+        const uint32_t e = es[t4];
+        const uint32_t j = e & kJMask;
+        if (!MD_CHECK(d, j < (uint32_t)d.n)) continue;
+        const float4 hj = __ldg(d.p32 + j), lj4 = __ldg(d.plo + j);
+        const uint32_t c = e >> kJBits;
+        const bool x2 = c & 2u, x1 = c & 1u, y2 = c & 8u, y1 = c & 4u, z2 = c & 32u, z1 = c & 16u;
+        const float dxh = __fsub_rn(x2 ? qhx2 : (x1 ? hi.x : qhx0), hj.x);
+        const float dyh = __fsub_rn(y2 ? qhy2 : (y1 ? hi.y : qhy0), hj.y);
+        const float dzh = __fsub_rn(z2 ? qhz2 : (z1 ? hi.z : qhz0), hj.z);
+        const float dxl = __fsub_rn(x2 ? qlx2 : (x1 ? li.x : qlx0), lj4.x);
+        const float dyl = __fsub_rn(y2 ? qly2 : (y1 ? li.y : qly0), lj4.y);
+        const float dzl = __fsub_rn(z2 ? qlz2 : (z1 ? li.z : qlz0), lj4.z);
+        const dw r2 = dw_add(dw_add(dw_sq_of(dxh, dxl), dw_sq_of(dyh, dyl)), dw_sq_of(dzh, dzl));
+        if (!(__fadd_rn(__fsub_rn(r2.h, rc2.h), __fsub_rn(r2.l, rc2.l)) < 0.f)) continue;
+        const float rf = __fadd_rn(r2.h, r2.l);
+        float y = rcp_approx(rf);
+        y = __fmaf_rn(y, __fmaf_rn(-rf, y, 1.f), y);
+        const float er = __fmaf_rn(-r2.l, y, __fmaf_rn(-r2.h, y, 1.f));
+        const dw sr2 = {y, __fmul_rn(y, er)};
+        const dw sr6 = dw_mul(dw_mul(sr2, sr2), sr2);
+        const dw sr8 = dw_mul(sr2, sr6);
+        const dw f = dw_mul(sr8, dw_axb(dw_const(lj.dw_a12), sr6, dw_const(lj.dw_a6)));
+        // 2 f' = sr10 (D6 - D12 sr6)
+        const dw fp2 = dw_mul(dw_mul(sr8, sr2), dw_add(dw_const(lj.dw_adj[0]),
+                                                       dw_mul(dw{-lj.dw_adj[1][0], -lj.dw_adj[1][1]}, sr6)));
+        const dw dx = {dxh, dxl}, dy = {dyh, dyl}, dz = {dzh, dzl};
+        const float4 ujh = __ldg(a.wh + j), ujl = __ldg(a.wl + j);
+        const dw dux = dw_add(uix, dw{-ujh.x, -ujl.x});
+        const dw duy = dw_add(uiy, dw{-ujh.y, -ujl.y});
+        const dw duz = dw_add(uiz, dw{-ujh.z, -ujl.z});
+        const dw g = dw_mul(fp2, dw_add(dw_add(dw_mul(dx, dux), dw_mul(dy, duy)), dw_mul(dz, duz)));
+        jx = dw_add(jx, dw_add(dw_mul(f, dux), dw_mul(g, dx)));
+        jy = dw_add(jy, dw_add(dw_mul(f, duy), dw_mul(g, dy)));
+        jz = dw_add(jz, dw_add(dw_mul(f, duz), dw_mul(g, dz)));
+        const dw dui = dw_add(dw_add(dw_mul(dx, uix), dw_mul(dy, uiy)), dw_mul(dz, uiz));
+        ge = dw_add(ge, dw_mul(dw_mul(sr8, dw_axb(dw_const(lj.dw_adj[2]), sr6, dw_const(lj.dw_adj[3]))), dui));
+        gs = dw_add(gs, dw_mul(dw_mul(sr8, dw_axb(dw_const(lj.dw_adj[4]), sr6, dw_const(lj.dw_adj[5]))), dui));
+        if (WINDOW) {   // -F/W and dPE/dtheta: only inside the loss window
+            fx = dw_add(fx, dw_mul(f, dx));
+            fy = dw_add(fy, dw_mul(f, dy));
+            fz = dw_add(fz, dw_mul(f, dz));
+            pe_e = dw_add(pe_e, dw_mul(sr6, dw_axb(dw_const(lj.dw_adj[6]), sr6, dw_const(lj.dw_adj[7]))));
+            pe_s = dw_add(pe_s, dw_mul(sr6, dw_axb(dw_const(lj.dw_adj[8]), sr6, dw_const(lj.dw_adj[9]))));
+        }
+      }
+      jx = fast_two_sum(jx.h, jx.l);
+      jy = fast_two_sum(jy.h, jy.l);
+      jz = fast_two_sum(jz.h, jz.l);
+      ge = fast_two_sum(ge.h, ge.l);
+      gs = fast_two_sum(gs.h, gs.l);
+    }
+    if (TPA > 1) {
+        auto red = [](dw &v, int o) {
+            v = dw_add(v, dw{__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)});
+        };
+#pragma unroll
+        for (int o = TPA / 2; o > 0; o >>= 1) {
+            red(jx, o); red(jy, o); red(jz, o); red(ge, o); red(gs, o);
+            if (WINDOW) { red(fx, o); red(fy, o); red(fz, o); red(pe_e, o); red(pe_s, o); }
+        }
+        if (sub != 0 || !valid) return;
+    }
+    dvec4 xb = a.xbar[idi];
+    xb.x += a.k * to_f64(jx) - a.lw * to_f64(fx);
+    xb.y += a.k * to_f64(jy) - a.lw * to_f64(fy);
+    xb.z += a.k * to_f64(jz) - a.lw * to_f64(fz);
+    a.xbar[idi] = xb;
+    a.g_eps[idi] += a.k * to_f64(ge) + a.lw * to_f64(pe_e);
+    a.g_sig[idi] += a.k * to_f64(gs) + a.lw * to_f64(pe_s);
+}
+
 }  // namespace
 
 int launch_force_dw(const Dev &d, const LJ &lj, int tpa, int epi, bool energy, bool batched,
@@ -295,6 +431,34 @@ int launch_force_dw(const Dev &d, const LJ &lj, int tpa, int epi, bool energy, b
         else if (tpa == 2) launch_dw<2, false>(d, lj, epi, energy, st);
         else launch_dw<1, false>(d, lj, epi, energy, st);
     }
+    *nl += 1;
+    return (int)cudaGetLastError();
+}
+
+}  // namespace mdk
+
+namespace mdk {
+
+int launch_adjoint_pairs_dw(const Dev &d, const LJ &lj, int lanes, const float4 *wh,
+                            const float4 *wl, dvec4 *xbar, double *g_eps, double *g_sig, double k,
+                            double lw, cudaStream_t st, int *nl)
+{
+    if (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8) return -1;
+    if (!wh || !wl || !d.plo) return -1;
+    if (d.n <= 0) return 0;
+    DwAdjArgs a{wh, wl, xbar, g_eps, g_sig, k, lw};
+    const unsigned g = (unsigned)((d.n * lanes + 127) / 128);
+    const bool win = lw != 0.0;
+#define MD_ADJDW(W)                                                                   \
+    do {                                                                              \
+        if (lanes == 8) k_adjoint_pairs_dw<W, 8><<<g, 128, 0, st>>>(d, lj, a);        \
+        else if (lanes == 4) k_adjoint_pairs_dw<W, 4><<<g, 128, 0, st>>>(d, lj, a);   \
+        else if (lanes == 2) k_adjoint_pairs_dw<W, 2><<<g, 128, 0, st>>>(d, lj, a);   \
+        else k_adjoint_pairs_dw<W, 1><<<g, 128, 0, st>>>(d, lj, a);                   \
+    } while (0)
+    if (win) MD_ADJDW(true);
+    else MD_ADJDW(false);
+#undef MD_ADJDW
     *nl += 1;
     return (int)cudaGetLastError();
 }

@@ -127,6 +127,7 @@ struct md_ctx {
         dvec4 *ck_x = nullptr, *ck_v = nullptr, *blk_x = nullptr, *xbar = nullptr, *wbar = nullptr;
         float4 *blk_p = nullptr, *ck_p = nullptr, *wbar32 = nullptr;
         float4 *ck_plo = nullptr;   // double-word path: the low parts beside ck_p
+        float4 *blk_plo = nullptr, *wbar_lo = nullptr;   // double-word pair terms
         int32_t *ck_id = nullptr;
         double *ge = nullptr, *gs = nullptr, *g2 = nullptr;
     } adj;
@@ -244,6 +245,7 @@ void free_all(md_ctx *c)
                     c->chunk_first_d, c->partials_d, c->eout_d, c->elog_d, c->io_d, c->ctr_d,
                     c->p32_ref, c->v32[0], c->v32[1], c->adj.ck_x, c->adj.ck_v, c->adj.blk_x,
                     c->adj.xbar, c->adj.wbar, c->adj.blk_p, c->adj.ck_p, c->adj.wbar32, c->adj.ck_plo,
+                    c->adj.blk_plo, c->adj.wbar_lo,
                     c->adj.ck_id, c->adj.ge, c->adj.gs, c->adj.g2, c->grp, c->gcnt,
                     c->gcell_start, c->gnb, c->gnb_count, c->offtab_d, c->gmask, c->gpair,
                     c->plo[0], c->plo[1]};
@@ -758,6 +760,13 @@ void set_lj_constants(md_ctx *c)
     split2(24.0 * q.epsilon * s6, lj.dw_a6);
     split2(4.0 * q.epsilon * s12, lj.dw_b12);
     split2(4.0 * q.epsilon * s6, lj.dw_b6);
+    {
+        const double e = q.epsilon, sg = q.sigma, s5 = s6 / sg, s11 = s12 / sg;
+        const double adj[10] = {192.0 * e * s6, 672.0 * e * s12, 48.0 * s12, 24.0 * s6,
+                                576.0 * e * s11, 144.0 * e * s5, 2.0 * s12, 2.0 * s6,
+                                24.0 * e * s11, 12.0 * e * s5};
+        for (int k = 0; k < 10; k++) split2(adj[k], lj.dw_adj[k]);
+    }
     lj.rs2f_lo = (float)(lj.rs2 * (1.0 - 2.5e-4));
     lj.rs2f_hi = (float)(lj.rs2 * (1.0 + 2.5e-4));
     // spring-dashpot constants (pot, sd_k, sd_g are set by md_set_spring_dashpot)
@@ -1464,10 +1473,12 @@ static int adjoint_impl(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt,
         return fail(c, MD_ERR_INVAL, "ckpt_every must divide rebuild_every and nsteps");
     const int64_t n = c->n, nck = nsteps / ckpt + 1;
     // precision of the reverse sweep's pair terms (the forward run always
-    // uses the context's precision; a double-word context takes FP64 pair
-    // terms unless md_set_adjoint_precision chose MD_MIXED)
-    const bool mixed = c->adj_prec < 0 ? is_mixed(c) : c->adj_prec == MD_MIXED;
+    // uses the context's precision): by default the context's own
+    const int pp = c->adj_prec < 0 ? c->p.precision : c->adj_prec;
+    const bool mixed = pp == MD_MIXED;
     const bool dw = is_dw(c);
+    const bool dwp = pp == MD_DW;
+    if (dwp && !dw) return fail(c, MD_ERR_INVAL, "double-word pair terms need an MD_DW context");
     const int lt0 = c->p.list_type, tpa0 = c->tpa;
     int rc = MD_OK;
     // the adjoint walks full per-atom lists (with the default lanes per atom
@@ -1481,17 +1492,20 @@ static int adjoint_impl(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt,
     auto &W = c->adj;
     auto drop = [](auto *&p) { if (p) cudaFree(p); p = nullptr; };
     if (nck > W.nck) { drop(W.ck_x); drop(W.ck_v); drop(W.ck_id); drop(W.ck_p); drop(W.ck_plo); W.nck = 0; }
-    if (ckpt > W.ckpt) { drop(W.blk_x); drop(W.blk_p); W.ckpt = 0; }
+    if (ckpt > W.ckpt) { drop(W.blk_x); drop(W.blk_p); drop(W.blk_plo); W.ckpt = 0; }
     if ((!W.ck_x && ((rc = dalloc(c, &W.ck_x, (size_t)(nck * n))) || (rc = dalloc(c, &W.ck_v, (size_t)(nck * n))) ||
                      (rc = dalloc(c, &W.ck_id, (size_t)(nck * n))) || (rc = dalloc(c, &W.ck_p, (size_t)(nck * n))))) ||
         (!W.blk_x && ((rc = dalloc(c, &W.blk_x, (size_t)(ckpt * n))) || (rc = dalloc(c, &W.blk_p, (size_t)(ckpt * n))))) ||
         (!W.xbar && ((rc = dalloc(c, &W.xbar, (size_t)n)) || (rc = dalloc(c, &W.wbar, (size_t)n)) ||
                      (rc = dalloc(c, &W.ge, (size_t)n)) || (rc = dalloc(c, &W.gs, (size_t)n)) ||
                      (rc = dalloc(c, &W.g2, 2)))) ||
-        (mixed && !W.wbar32 && (rc = dalloc(c, &W.wbar32, (size_t)n))) ||
+        ((mixed || dwp) && !W.wbar32 && (rc = dalloc(c, &W.wbar32, (size_t)n))) ||
+        (dwp && !W.wbar_lo && (rc = dalloc(c, &W.wbar_lo, (size_t)n))) ||
+        (dwp && !W.blk_plo && (rc = dalloc(c, &W.blk_plo, (size_t)(W.ckpt ? W.ckpt * n : ckpt * n)))) ||
         (dw && !W.ck_plo && (rc = dalloc(c, &W.ck_plo, (size_t)(W.nck ? W.nck * n : nck * n))))) {
         // release the whole workspace: a later call starts from scratch
         drop(W.ck_x); drop(W.ck_v); drop(W.ck_id); drop(W.ck_p); drop(W.ck_plo); drop(W.blk_x); drop(W.blk_p);
+        drop(W.blk_plo); drop(W.wbar_lo);
         drop(W.xbar); drop(W.wbar); drop(W.wbar32); drop(W.ge); drop(W.gs); drop(W.g2);
         W.nck = W.ckpt = 0;
         return rc;
@@ -1499,8 +1513,9 @@ static int adjoint_impl(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt,
     W.nck = std::max<int64_t>(W.nck, nck);
     W.ckpt = std::max<int64_t>(W.ckpt, ckpt);
     dvec4 *ck_x = W.ck_x, *ck_v = W.ck_v, *blk_x = W.blk_x, *xbar = W.xbar, *wbar = W.wbar;
-    float4 *blk_p = W.blk_p, *ck_p = W.ck_p, *wbar32 = mixed ? W.wbar32 : nullptr;
+    float4 *blk_p = W.blk_p, *ck_p = W.ck_p, *wbar32 = (mixed || dwp) ? W.wbar32 : nullptr;
     float4 *ck_plo = dw ? W.ck_plo : nullptr;
+    float4 *blk_plo = dwp ? W.blk_plo : nullptr, *wbar_lo = dwp ? W.wbar_lo : nullptr;
     int32_t *ck_id = W.ck_id;
     double *ge = W.ge, *gs = W.gs, *g2 = W.g2;
     if (window > c->elog_cap) {
@@ -1609,6 +1624,7 @@ static int adjoint_impl(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt,
     CK(cudaMemsetAsync(xbar, 0, sizeof(dvec4) * n, c->st));
     CK(cudaMemsetAsync(wbar, 0, sizeof(dvec4) * n, c->st));
     if (wbar32) CK(cudaMemsetAsync(wbar32, 0, sizeof(float4) * n, c->st));
+    if (wbar_lo) CK(cudaMemsetAsync(wbar_lo, 0, sizeof(float4) * n, c->st));
     CK(cudaMemsetAsync(ge, 0, sizeof(double) * n, c->st));
     CK(cudaMemsetAsync(gs, 0, sizeof(double) * n, c->st));
     const double cdt = c->lj.half_dt_m;
@@ -1628,15 +1644,18 @@ static int adjoint_impl(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt,
             // the snapshot the pair terms read: FP32 cell-relative positions
             // (mixed pair terms) or FP64 positions (FP64 pair terms, which
             // take only the cell coordinates from p32: fixed for the epoch)
-            if (mixed)
+            // (double-word pair terms: the high and low parts of the split positions)
+            if (mixed || dwp)
                 cudaMemcpyAsync(blk_p + m * n, c->p32[c->pb], sizeof(float4) * n, cudaMemcpyDeviceToDevice, c->st);
             else
                 cudaMemcpyAsync(blk_x + m * n, c->x[c->xp], sizeof(dvec4) * n, cudaMemcpyDeviceToDevice, c->st);
+            if (dwp)
+                cudaMemcpyAsync(blk_plo + m * n, c->plo[c->pb], sizeof(float4) * n, cudaMemcpyDeviceToDevice, c->st);
         }
         for (int64_t m = npts - 1; m >= 0 && !rc; m--) {
             const int64_t pt = cb + m;
             if (pt < nsteps &&
-                launch_adjoint_axpy(n, c->lj.dt, xbar, wbar, wbar32, c->id[c->vp], c->st, &nl)) {
+                launch_adjoint_axpy(n, c->lj.dt, xbar, wbar, wbar32, wbar_lo, c->id[c->vp], c->st, &nl)) {
                 rc = fail(c, MD_ERR_CUDA, "adjoint launch failed");
                 break;
             }
@@ -1645,9 +1664,11 @@ static int adjoint_impl(md_ctx *c, int64_t nsteps, int64_t window, int32_t ckpt,
             // the pair terms read the recomputed snapshot of force point pt
             // in place (same atom order and list as the whole block)
             Dev dv = view(c);
-            if (mixed) dv.p32 = blk_p + m * n;
+            if (mixed || dwp) dv.p32 = blk_p + m * n;
             else dv.x = blk_x + m * n;
-            if (launch_adjoint_pairs(dv, c->lj, mixed, c->tpa, wbar, wbar32, xbar, ge, gs, k, lw, c->st, &nl)) {
+            if (dwp) dv.plo = blk_plo + m * n;
+            if (dwp ? launch_adjoint_pairs_dw(dv, c->lj, c->tpa, wbar32, wbar_lo, xbar, ge, gs, k, lw, c->st, &nl)
+                    : launch_adjoint_pairs(dv, c->lj, mixed, c->tpa, wbar, wbar32, xbar, ge, gs, k, lw, c->st, &nl)) {
                 rc = fail(c, MD_ERR_CUDA, "adjoint launch failed");
                 break;
             }
@@ -1796,8 +1817,10 @@ int md_study_force_variant(md_ctx *c, int32_t variant, int32_t reps, double *us,
 
 int md_set_adjoint_precision(md_ctx *c, int32_t precision)
 {
-    if (!c || (precision != MD_FP64 && precision != MD_MIXED))
-        return fail(c, MD_ERR_INVAL, "precision must be MD_FP64 or MD_MIXED");
+    if (!c || (precision != MD_FP64 && precision != MD_MIXED && precision != MD_DW))
+        return fail(c, MD_ERR_INVAL, "precision must be MD_FP64, MD_MIXED or MD_DW");
+    if (precision == MD_DW && !is_dw(c))
+        return fail(c, MD_ERR_INVAL, "double-word pair terms need an MD_DW context");
     c->adj_prec = precision;
     return MD_OK;
 }

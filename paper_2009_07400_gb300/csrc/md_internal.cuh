@@ -163,6 +163,10 @@ struct LJ {
     // double-word constants (precision MD_DW) as {fl32(c), fl32(c - fl32(c))}:
     // rc^2, 48 eps sigma^12, 24 eps sigma^6, 4 eps sigma^12, 4 eps sigma^6
     float dw_rc2[2], dw_a12[2], dw_a6[2], dw_b12[2], dw_b6[2];
+    // adjoint pair terms in double word (s = sigma): 192 eps s^6, 672 eps s^12
+    // (2 f'), 48 s^12, 24 s^6 (f / eps), 576 eps s^11, 144 eps s^5 (df/dsigma),
+    // 2 s^12, 2 s^6 (dV/deps / 2), 24 eps s^11, 12 eps s^5 (dV/dsigma / 2)
+    float dw_adj[10][2];
     // spring-dashpot contact (Eq. 3; pot == 1): K, gamma, sigma^2 (sigma = diameter)
     int32_t pot;
     double sd_k, sd_g, sd_sig2;
@@ -468,8 +472,16 @@ int launch_adjoint_pairs(const Dev &d, const LJ &lj, bool mixed, int lanes, cons
                          double k, double lw, cudaStream_t st, int *nlaunch);
 // wbar += dt xbar (caller order); wbar32 (may be null) <- its FP32 copy in
 // the slot order of id (slot -> caller id)
+// wbar_lo (may be null): the low parts fl32(w - fl32(w)) beside wbar32 (the
+// double-word pair terms read both)
 int launch_adjoint_axpy(int64_t n, double dt, const dvec4 *xbar, dvec4 *wbar, float4 *wbar32,
-                        const int32_t *id, cudaStream_t st, int *nlaunch);
+                        float4 *wbar_lo, const int32_t *id, cudaStream_t st, int *nlaunch);
+// Adjoint pair terms in double word (k_force_dw.cu): d.p32 / d.plo the high
+// and low parts of the snapshot's positions, wh / wl those of the adjoint w
+// in slot order; full lists, single replica.
+int launch_adjoint_pairs_dw(const Dev &d, const LJ &lj, int lanes, const float4 *wh,
+                            const float4 *wl, dvec4 *xbar, double *g_eps, double *g_sig, double k,
+                            double lw, cudaStream_t st, int *nlaunch);
 int launch_sum2(int64_t n, const double *a, const double *b, double *out, cudaStream_t st,
                 int *nlaunch);
 int launch_unpad3(int64_t n, const dvec4 *a, double *out, cudaStream_t st, int *nlaunch);

@@ -459,7 +459,8 @@ class MDContext:
         return us.value, F
 
     def set_adjoint_precision(self, precision):
-        """Precision of the reverse sweep's pair terms (MD_FP64 or MD_MIXED)."""
+        """Precision of the reverse sweep's pair terms (MD_FP64, MD_MIXED, or
+        MD_DW on a double-word context)."""
         self._check(self._lib.md_set_adjoint_precision(self._h, int(precision)))
 
     def set_cell_split(self, split):

@@ -265,33 +265,37 @@ def rel(a, b):
     return abs(a - b) / abs(b)
 
 
+@pytest.mark.parametrize("pair", ["dw", "fp64"])
 @pytest.mark.parametrize("nsteps,window,every,ckpt,lanes", [(40, 10, 20, 10, 1), (60, 25, 20, 20, 2),
                                                             (30, 30, 10, 5, 4)])
-def test_dw_adjoint_matches_oracle(md, orc, nsteps, window, every, ckpt, lanes):
+def test_dw_adjoint_matches_oracle(md, orc, nsteps, window, every, ckpt, lanes, pair):
     """md_adjoint on a double-word context (double-word forward and
-    recompute, FP64 reverse pair terms) against the oracle's FP64 reverse
-    sweep: the loss and every gradient far inside the FP64 path's bar."""
+    recompute; reverse pair terms in double word, the default, or in FP64)
+    against the oracle's FP64 reverse sweep: the loss and every gradient far
+    inside the FP64 path's bar."""
     s = inputs.fcc_system(5, jitter=0.05, seed=41)        # 500 atoms
     x, v, _ = orc.vv_run(s.pos, s.vel, s.box, 40)
     x0, v0, L = orc.wrap(x, s.box), v, s.box
     loss_o, ge_o, gs_o, gx_o, gv_o = orc.adjoint(x0, v0, L, nsteps, window, rebuild_every=every)
     with md.MDContext(x0, v0, L, precision=md.MD_DW, rebuild_every=every,
                       threads_per_atom=lanes) as ctx:
+        if pair == "fp64":
+            ctx.set_adjoint_precision(md.MD_FP64)
         loss, ge, gs, gx, gv = ctx.adjoint(nsteps, window, ckpt)
         again = ctx.adjoint(nsteps, window, ckpt)          # the workspace is reused
         xa = ctx.positions()
     e = [rel(loss, loss_o), rel(ge, ge_o), rel(gs, gs_o),
          np.linalg.norm(gx - gx_o) / np.linalg.norm(gx_o),
          np.linalg.norm(gv - gv_o) / np.linalg.norm(gv_o)]
-    print("double-word adjoint errors (loss, eps, sigma, x0, v0):", e)
+    print(f"double-word adjoint, {pair} pair terms, errors (loss, eps, sigma, x0, v0):", e)
     assert e[0] < 1e-11 and max(e[1:]) < 1e-8
     assert again[0] == loss and np.array_equal(again[3], gx)
     assert np.array_equal(xa, x0) or np.abs(mi(xa - x0, L)).max() == 0.0
 
 
 def test_dw_adjoint_full_config(md, orc):
-    """16,384 atoms, 200 steps, window 50, checkpoints every 10: the FP64
-    path's bar (1e-6 per scalar and in relative norm)."""
+    """16,384 atoms, 200 steps, window 50, checkpoints every 10, double-word
+    pair terms: the FP64 path's bar (1e-6 per scalar and in relative norm)."""
     s = inputs.workload("fcc16_16384")
     loss_o, ge_o, gs_o, gx_o, gv_o = orc.adjoint(s.pos, s.vel, s.box, 200, 50)
     with dw_ctx(md, s) as ctx:
@@ -301,3 +305,18 @@ def test_dw_adjoint_full_config(md, orc):
          np.linalg.norm(gv - gv_o) / np.linalg.norm(gv_o)]
     print("double-word adjoint, full config (loss, eps, sigma, x0, v0):", e)
     assert e[0] < 1e-12 and max(e[1:]) < 1e-6
+
+
+def test_dw_adjoint_precision_refusals(md, orc):
+    """MD_DW pair terms need a double-word context (split positions)."""
+    s = inputs.fcc_system(4, jitter=0.05, seed=2)
+    for prec in (md.MD_FP64, md.MD_MIXED):
+        with md.MDContext(s.pos, s.vel, s.box, precision=prec) as ctx:
+            with pytest.raises(md.MDError) as e:
+                ctx.set_adjoint_precision(md.MD_DW)
+            assert e.value.code == -1
+    with dw_ctx(md, s) as ctx:
+        for p in (md.MD_DW, md.MD_FP64, md.MD_MIXED):
+            ctx.set_adjoint_precision(p)
+        with pytest.raises(md.MDError):
+            ctx.set_adjoint_precision(5)
