@@ -61,7 +61,9 @@ extern "C" {
                        Positions relative to the cell centre are split into a high part
                        on a power-of-two grid and a low part at each binning and step;
                        an atom that moves more than a cell side beyond its cell between
-                       binnings stops the run with MD_ERR_BADPOS.  Full per-atom lists
+                       binnings stops the run with MD_ERR_BADPOS.  The exponent range is
+                       FP32's: pairs closer than ~2e-3 sigma overflow the pair terms
+                       (MD_ERR_NONFINITE at the next binning).  Full per-atom lists
                        only (MD_LIST_FULL); no contact model.  md_adjoint runs the
                        forward and, by default, the reverse pair terms in double
                        word (md_set_adjoint_precision).                             */
