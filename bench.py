@@ -588,9 +588,9 @@ def run_reference(args):
 
 def run_dem(args):
     """The contact model of Eq. 3 on a dense granular packing of 1,048,576
-    spheres (mixed and FP64 paths, rebuild every 20 steps), with the force
-    error of both paths against the oracle on the full final state and the
-    oracle's own rate on the host cores."""
+    spheres (mixed, double-word and FP64 paths, rebuild every 20 steps), with
+    the force error of each path against the oracle on the full final state
+    and the oracle's own rate on the host cores."""
     import torch
 
     import oracle
@@ -628,6 +628,12 @@ def run_dem(args):
         prof64 = ctx.profile(STEPS_PER_CYCLE)
         ctx.set_state(x, v)
         F_64 = ctx.forces()
+    with make(md.MD_DW) as ctx:
+        cdw = max(1, min(args.steps, 3))
+        msdw, _ = time_cycles(ctx, cdw, 1, None, torch)
+        profdw = ctx.profile(STEPS_PER_CYCLE)
+        ctx.set_state(x, v)
+        F_dw = ctx.forces()
     # end to end: state from pinned host memory, one cycle, energies back
     pin_x = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
     pin_v = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
@@ -693,9 +699,15 @@ def run_dem(args):
                       "phases_ms_per_timestep": {"force": prof64.force_ms / prof64.steps,
                                                  "neigh": prof64.neigh_ms / prof64.steps,
                                                  "other": prof64.other_ms / prof64.steps}},
+        "dw_path": {"value": n * TIMESTEPS_PER_STEP * cdw / (msdw / 1e3),
+                    "note": "double-word contact arithmetic on the FP32 pipe, FP64 integration",
+                    "phases_ms_per_timestep": {"force": profdw.force_ms / profdw.steps,
+                                               "neigh": profdw.neigh_ms / profdw.steps,
+                                               "other": profdw.other_ms / profdw.steps}},
         "force_error": {
             "mixed_rms_rel": float(np.sqrt(np.sum((F_mix - Fr) ** 2) / np.sum(Fr ** 2))),
             "fp64_max_rel": float(np.max(np.linalg.norm(F_64 - Fr, axis=1) / sc)),
+            "dw_max_rel": float(np.max(np.linalg.norm(F_dw - Fr, axis=1) / sc)),
             "sample": "every sphere, the packing after one 20-step cycle of the mixed path, "
                       "oracle list forces"},
         "e2e": {"value": n * STEPS_PER_CYCLE * e_steps / e2e_s, "unit": UNIT,

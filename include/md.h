@@ -64,7 +64,7 @@ extern "C" {
                        binnings stops the run with MD_ERR_BADPOS.  The exponent range is
                        FP32's: pairs closer than ~2e-3 sigma overflow the pair terms
                        (MD_ERR_NONFINITE at the next binning).  Full per-atom lists
-                       only (MD_LIST_FULL); no contact model.  md_adjoint runs the
+                       only (MD_LIST_FULL).  md_adjoint runs the
                        forward and, by default, the reverse pair terms in double
                        word (md_set_adjoint_precision).                             */
 
@@ -308,8 +308,8 @@ int md_set_lj(md_ctx *ctx, double epsilon, double sigma);
  * sum of x_ij . F_ij.  Full lists are used (a half-list context switches and
  * rebuilds); md_set_lj switches back to Lennard-Jones.  K = gamma = 0 is the
  * paper's static setting (no force).
- * Errors: MD_ERR_INVAL (negative or non-finite K or gamma, cutoff < sigma,
- * an MD_DW context), MD_ERR_CUDA. */
+ * Errors: MD_ERR_INVAL (negative or non-finite K or gamma, cutoff < sigma),
+ * MD_ERR_CUDA. */
 int md_set_spring_dashpot(md_ctx *ctx, double k_spring, double gamma);
 
 /* Differentiable rollout (not in the paper; it differentiates the Sec. 3.2

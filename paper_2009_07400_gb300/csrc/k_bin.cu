@@ -241,8 +241,8 @@ __global__ void __launch_bounds__(256) k_sort_gather(Dev d, int64_t nk)
         d.x_alt[ns] = x;
         d.v_alt[ns] = v;
         d.id_alt[ns] = my_id;
-        // contact model, mixed path: the FP32 velocity copies in the new order
-        if (d.v32) d.v32[ns] = make_float4(f32_of_f64(v.x), f32_of_f64(v.y), f32_of_f64(v.z), 0.f);
+        // contact model: the velocity copies in the new order
+        if (d.v32) store_vel_copy(d.v32, d.vlo, ns, v);
         const Rep &R = d.reps[BATCHED ? d.rep_of[ns] : 0];
         int cx, cy, cz;
         cell_coords(R, key >> (3 * d.split), cx, cy, cz);

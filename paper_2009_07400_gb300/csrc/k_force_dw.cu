@@ -413,6 +413,153 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs_dw(Dev d, LJ lj, DwAdjArg
     a.g_sig[idi] += a.k * to_f64(gs) + a.lw * to_f64(pe_s);
 }
 
+
+// ---------------------------------------------------------------------------
+// Spring-dashpot contact forces (Sec. 3.2, Eq. 3) in double word: the mixed
+// contact kernel's mapping (one thread per sphere over its full row, the
+// velocity-Verlet update fused into the epilogue) with every pair quantity a
+// double word.  Spheres touch when r^2 < sigma^2 (strict; the sign test of
+// the LJ kernel); then
+//     F_i += x_ij [K (sigma - r) - gamma (x_ij . v_ij) / r] / r.
+// 1/r: the hardware reciprocal square root of fl(r2_h + r2_l), one FP32
+// Newton step y (3 - a y^2) / 2, then one double-word step y (1 + e / 2) with
+// e = 1 - r^2 y^2 (y^2 exact by two_prod): relative error ~2^-47; r = r^2 / r.
+// sigma - r cancels for touching spheres; its high parts are subtracted
+// exactly (two_sum).  The neighbours' velocities come from double-word
+// copies (v32: high parts, vlo: low parts) that the binning, the velocity
+// copy kernel and this epilogue keep, like the positions.
+__device__ __forceinline__ float rsqrt_approx(float a)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+
+template <int EPI, bool ENERGY>
+__device__ __forceinline__ void dw_sd_epilogue(const Dev &d, const LJ &lj, const Rep &R, int64_t i,
+                                               double fx, double fy, double fz, uint32_t pack)
+{
+    if (EPI == EPI_F || EPI == EPI_FK) d.f64[i] = mk_dvec4(fx, fy, fz, 0.0);
+    if (EPI == EPI_F) return;
+    dvec4 v = ld_cs_dvec4(d.v + i);
+    v.x = fma(lj.half_dt_m, fx, v.x);
+    v.y = fma(lj.half_dt_m, fy, v.y);
+    v.z = fma(lj.half_dt_m, fz, v.z);
+    if (ENERGY) d.ke_atom64[i] = 0.5 * lj.mass * fma(v.x, v.x, fma(v.y, v.y, v.z * v.z));
+    if (EPI == EPI_FKKD) {
+        v.x = fma(lj.half_dt_m, fx, v.x);
+        v.y = fma(lj.half_dt_m, fy, v.y);
+        v.z = fma(lj.half_dt_m, fz, v.z);
+        dvec4 x = ld_cs_dvec4(d.x + i);
+        x.x = fma(lj.dt, v.x, x.x);
+        x.y = fma(lj.dt, v.y, x.y);
+        x.z = fma(lj.dt, v.z, x.z);
+        st_cs_dvec4(d.x + i, x);
+        const double *ct = d.ctr + R.ctr_off;
+        const double cx = __ldg(ct + (pack & 1023u));
+        const double cy = __ldg(ct + R.nc[0] + ((pack >> 10) & 1023u));
+        const double cz = __ldg(ct + R.nc[0] + R.nc[1] + ((pack >> 20) & 1023u));
+        store_cell_pos(d, R, d.p32_nxt, d.plo_nxt, i, x.x - cx, x.y - cy, x.z - cz, pack);
+        if (d.p32_ref) check_displacement(d, i, d.p32_nxt[i]);
+        store_vel_copy(d.v32_nxt, d.vlo_nxt, i, v);
+    }
+    st_cs_dvec4(d.v + i, v);
+}
+
+template <bool BATCHED, bool ENERGY, int EPI>
+__global__ void __launch_bounds__(256) k_force_sd_dw(Dev d, LJ lj)
+{
+    if (stopped(d.status)) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.n) return;
+    const int64_t n = d.n;
+    const Rep &R = d.reps[BATCHED ? d.rep_of[i] : 0];
+    const float4 hi = d.p32[i], li = d.plo[i];
+    const float4 vih = d.v32[i], vil = d.vlo[i];
+    const float qhx0 = __fadd_rn(hi.x, R.dw_sh[0]), qhx2 = __fsub_rn(hi.x, R.dw_sh[0]);
+    const float qhy0 = __fadd_rn(hi.y, R.dw_sh[1]), qhy2 = __fsub_rn(hi.y, R.dw_sh[1]);
+    const float qhz0 = __fadd_rn(hi.z, R.dw_sh[2]), qhz2 = __fsub_rn(hi.z, R.dw_sh[2]);
+    const float qlx0 = __fadd_rn(li.x, R.dw_sl[0]), qlx2 = __fsub_rn(li.x, R.dw_sl[0]);
+    const float qly0 = __fadd_rn(li.y, R.dw_sl[1]), qly2 = __fsub_rn(li.y, R.dw_sl[1]);
+    const float qlz0 = __fadd_rn(li.z, R.dw_sl[2]), qlz2 = __fsub_rn(li.z, R.dw_sl[2]);
+    const dw sig2 = dw_const(lj.dw_sd_sig2), sig = dw_const(lj.dw_sd_sig);
+    const dw kk = dw_const(lj.dw_sd_k), gn = {-lj.dw_sd_g[0], -lj.dw_sd_g[1]};
+    const int cnt = MD_CHECK(d, d.nb_count[i] <= d.cap) ? d.nb_count[i] : 0;
+    const int nq = (cnt + 3) >> 2;
+    const int4 *nb4 = reinterpret_cast<const int4 *>(d.nb);
+    const dw zero = {0.f, 0.f};
+    dw ax = zero, ay = zero, az = zero, ape = zero, aw = zero;
+    for (int q = 0; q < nq; q++) {
+        const int4 e4 = __ldcs(nb4 + (int64_t)q * n + i);
+        const uint32_t es[4] = {(uint32_t)e4.x, (uint32_t)e4.y, (uint32_t)e4.z, (uint32_t)e4.w};
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            const uint32_t e = es[t];
+            const uint32_t j = MD_CHECK(d, (e & kJMask) <= (uint32_t)d.n) ? (e & kJMask) : (uint32_t)d.n;
+            const float4 hj = __ldg(d.p32 + j), lj4 = __ldg(d.plo + j);
+            const uint32_t c = e >> kJBits;
+            const bool x2 = c & 2u, x1 = c & 1u, y2 = c & 8u, y1 = c & 4u, z2 = c & 32u, z1 = c & 16u;
+            const float dxh = __fsub_rn(x2 ? qhx2 : (x1 ? hi.x : qhx0), hj.x);
+            const float dyh = __fsub_rn(y2 ? qhy2 : (y1 ? hi.y : qhy0), hj.y);
+            const float dzh = __fsub_rn(z2 ? qhz2 : (z1 ? hi.z : qhz0), hj.z);
+            const float dxl = __fsub_rn(x2 ? qlx2 : (x1 ? li.x : qlx0), lj4.x);
+            const float dyl = __fsub_rn(y2 ? qly2 : (y1 ? li.y : qly0), lj4.y);
+            const float dzl = __fsub_rn(z2 ? qlz2 : (z1 ? li.z : qlz0), lj4.z);
+            const dw r2 = dw_add(dw_add(dw_sq_of(dxh, dxl), dw_sq_of(dyh, dyl)), dw_sq_of(dzh, dzl));
+            if (!(__fadd_rn(__fsub_rn(r2.h, sig2.h), __fsub_rn(r2.l, sig2.l)) < 0.f)) continue;
+            const float4 vjh = __ldg(d.v32 + j), vjl = __ldg(d.vlo + j);
+            // 1/r and r
+            const float af = __fadd_rn(r2.h, r2.l);
+            float y = rsqrt_approx(af);
+            y = __fmul_rn(y, __fmaf_rn(-0.5f * __fmul_rn(af, y), y, 1.5f));
+            const dw p = dw_mul(r2, two_prod(y, y));
+            const float ee = __fsub_rn(__fsub_rn(1.f, p.h), p.l);
+            const dw ir = {y, __fmul_rn(y, 0.5f * ee)};
+            const dw r = dw_mul(r2, ir);
+            const dw dx = {dxh, dxl}, dy = {dyh, dyl}, dz = {dzh, dzl};
+            const dw vx = dw_add(dw{vih.x, vil.x}, dw{-vjh.x, -vjl.x});
+            const dw vy = dw_add(dw{vih.y, vil.y}, dw{-vjh.y, -vjl.y});
+            const dw vz = dw_add(dw{vih.z, vil.z}, dw{-vjh.z, -vjl.z});
+            const dw vn = dw_mul(dw_add(dw_add(dw_mul(dx, vx), dw_mul(dy, vy)), dw_mul(dz, vz)), ir);
+            const dw ov = dw_add(sig, dw{-r.h, -r.l});
+            const dw fo = dw_mul(dw_add(dw_mul(kk, ov), dw_mul(gn, vn)), ir);
+            ax = dw_add(ax, dw_mul(fo, dx));
+            ay = dw_add(ay, dw_mul(fo, dy));
+            az = dw_add(az, dw_mul(fo, dz));
+            if (ENERGY) {
+                ape = dw_add(ape, dw_mul(dw_const(lj.dw_sd_hk), dw_mul(ov, ov)));
+                aw = dw_add(aw, dw_mul(fo, r2));
+            }
+        }
+        ax = fast_two_sum(ax.h, ax.l);
+        ay = fast_two_sum(ay.h, ay.l);
+        az = fast_two_sum(az.h, az.l);
+    }
+    if (ENERGY) {
+        d.pe_atom64[i] = 0.5 * to_f64(ape);
+        d.w_atom64[i] = 0.5 * to_f64(aw);
+    }
+    dw_sd_epilogue<EPI, ENERGY>(d, lj, R, i, to_f64(ax), to_f64(ay), to_f64(az), __float_as_uint(hi.w));
+}
+
+// Double-word velocity copies (v32: high parts, vlo: low parts) for the
+// contact kernel, where something other than its fused step changed v.
+__global__ void __launch_bounds__(256) k_velocity_dw(Dev d)
+{
+    if (stopped(d.status)) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > d.n) return;                     // slot n: the sentinel (zero velocity)
+    store_vel_copy(d.v32, d.vlo, i, d.v[i]);
+}
+
+template <bool B, bool EN>
+void launch_sd_dw(const Dev &d, const LJ &lj, int epi, unsigned g, cudaStream_t st)
+{
+    if (epi == EPI_F) k_force_sd_dw<B, EN, EPI_F><<<g, 256, 0, st>>>(d, lj);
+    else if (epi == EPI_FK) k_force_sd_dw<B, EN, EPI_FK><<<g, 256, 0, st>>>(d, lj);
+    else k_force_sd_dw<B, EN, EPI_FKKD><<<g, 256, 0, st>>>(d, lj);
+}
+
 }  // namespace
 
 int launch_force_dw(const Dev &d, const LJ &lj, int tpa, int epi, bool energy, bool batched,
@@ -459,6 +606,33 @@ int launch_adjoint_pairs_dw(const Dev &d, const LJ &lj, int lanes, const float4 
     if (win) MD_ADJDW(true);
     else MD_ADJDW(false);
 #undef MD_ADJDW
+    *nl += 1;
+    return (int)cudaGetLastError();
+}
+
+}  // namespace mdk
+
+namespace mdk {
+
+int launch_velocity_dw(const Dev &d, cudaStream_t st, int *nl)
+{
+    if (d.n <= 0) return 0;
+    if (!d.v32 || !d.vlo) return -1;
+    k_velocity_dw<<<(unsigned)((d.n + 256) / 256), 256, 0, st>>>(d);
+    *nl += 1;
+    return (int)cudaGetLastError();
+}
+
+int launch_force_sd_dw(const Dev &d, const LJ &lj, int epi, bool energy, cudaStream_t st, int *nl)
+{
+    if (d.n <= 0) return 0;
+    if (!d.plo || !d.plo_nxt || !d.v32 || !d.v32_nxt || !d.vlo || !d.vlo_nxt) return -1;
+    const unsigned g = (unsigned)((d.n + 255) / 256);
+    const bool b = d.nrep > 1;
+    if (b && energy) launch_sd_dw<true, true>(d, lj, epi, g, st);
+    else if (b) launch_sd_dw<true, false>(d, lj, epi, g, st);
+    else if (energy) launch_sd_dw<false, true>(d, lj, epi, g, st);
+    else launch_sd_dw<false, false>(d, lj, epi, g, st);
     *nl += 1;
     return (int)cudaGetLastError();
 }

@@ -77,6 +77,7 @@ struct md_ctx {
     float4 *p32_ref = nullptr;      // displacement trigger: p32 at the last binning
     float4 *plo[2] = {nullptr, nullptr};   // double-word path: low parts of the split
                                     // positions, same parity as p32 (else null)
+    float4 *vlo[2] = {nullptr, nullptr};   // contact model, double-word path: low parts
     float4 *v32[2] = {nullptr, nullptr};   // contact model, mixed path: FP32 velocity
                                     // copies, same parity as p32
     bool v32_fresh = false;         // v32[pb] == fl32(v) (else regenerated before a force)
@@ -197,9 +198,12 @@ Dev view(const md_ctx *c)
     d.ngmax = c->ngmax;
     d.gcap = c->gcap;
     d.offtab = c->offtab_d;
-    if (c->lj.pot == 1 && c->p.precision == MD_MIXED) {   // contact model, mixed path
+    if (c->lj.pot == 1 && (c->p.precision == MD_MIXED || c->p.precision == MD_DW)) {
+        // contact model: velocity copies (and, double word, their low parts)
         d.v32 = c->v32[c->pb];
         d.v32_nxt = c->v32[1 - c->pb];
+        d.vlo = c->vlo[c->pb];
+        d.vlo_nxt = c->vlo[1 - c->pb];
     }
     return d;
 }
@@ -248,7 +252,7 @@ void free_all(md_ctx *c)
                     c->adj.blk_plo, c->adj.wbar_lo,
                     c->adj.ck_id, c->adj.ge, c->adj.gs, c->adj.g2, c->grp, c->gcnt,
                     c->gcell_start, c->gnb, c->gnb_count, c->offtab_d, c->gmask, c->gpair,
-                    c->plo[0], c->plo[1]};
+                    c->plo[0], c->plo[1], c->vlo[0], c->vlo[1]};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->own_stream && c->st) cudaStreamDestroy(c->st);
@@ -269,8 +273,12 @@ int list_g(const md_ctx *c)
 }
 bool is_sd(const md_ctx *c) { return c->lj.pot == 1; }
 bool batched(const md_ctx *c) { return c->nrep > 1; }
-// the contact model's mixed path keeps FP32 velocity copies (v32)
-bool uses_v32(const md_ctx *c) { return c->lj.pot == 1 && c->p.precision == MD_MIXED; }
+// the contact model's mixed and double-word paths keep velocity copies (v32,
+// and on the double-word path their low parts)
+bool uses_v32(const md_ctx *c)
+{
+    return c->lj.pot == 1 && (c->p.precision == MD_MIXED || c->p.precision == MD_DW);
+}
 
 int32_t round4(int64_t v) { return (int32_t)((v + 3) / 4 * 4); }
 
@@ -408,16 +416,18 @@ int enq_energy(md_ctx *c, bool ke_from_v, double *out3, int *nl)
 int enq_force(md_ctx *c, int epi, bool energy, int *nl, cudaEvent_t *ev = nullptr)
 {
     Dev d = view(c);
-    if (is_sd(c) && is_mixed(c)) {
-        // contact model, mixed path: one fused kernel; the FP32 velocity
-        // copies are regenerated only when something other than the fused
-        // step or a binning changed v since they were made
+    if (is_sd(c) && (is_mixed(c) || is_dw(c))) {
+        // contact model, mixed and double-word paths: one fused kernel; the
+        // velocity copies are regenerated only when something other than the
+        // fused step or a binning changed v since they were made
         if (ev) CK(cudaEventRecord(ev[0], c->st));
         if (!c->v32_fresh) {
-            if (launch_velocity_f32(d, c->st, nl)) return fail(c, MD_ERR_CUDA, "velocity copy launch failed");
+            if (is_dw(c) ? launch_velocity_dw(d, c->st, nl) : launch_velocity_f32(d, c->st, nl))
+                return fail(c, MD_ERR_CUDA, "velocity copy launch failed");
             c->v32_fresh = true;
         }
-        if (launch_force_sd(d, c->lj, true, epi, energy, c->st, nl))
+        if (is_dw(c) ? launch_force_sd_dw(d, c->lj, epi, energy, c->st, nl)
+                     : launch_force_sd(d, c->lj, true, epi, energy, c->st, nl))
             return fail(c, MD_ERR_CUDA, "force launch failed");
         if (ev) CK(cudaEventRecord(ev[1], c->st));
         if (epi == EPI_FKKD) c->pb = 1 - c->pb;      // next p32 and v32 written
@@ -775,6 +785,11 @@ void set_lj_constants(md_ctx *c)
     lj.sd_sig2f = (float)lj.sd_sig2;
     lj.sd_kf = (float)lj.sd_k;
     lj.sd_gf = (float)lj.sd_g;
+    split2(lj.sd_sig2, lj.dw_sd_sig2);
+    split2(q.sigma, lj.dw_sd_sig);
+    split2(lj.sd_k, lj.dw_sd_k);
+    split2(lj.sd_g, lj.dw_sd_g);
+    split2(0.5 * lj.sd_k, lj.dw_sd_hk);
 }
 
 // Process-wide autotuner cache: (precision, log2 atoms per replica, batched)
@@ -1435,14 +1450,18 @@ int md_set_spring_dashpot(md_ctx *c, double k_spring, double gamma)
         return fail(c, MD_ERR_INVAL, "bad argument");
     if (!(c->p.cutoff >= c->p.sigma))
         return fail(c, MD_ERR_INVAL, "cutoff must be >= sigma (the sphere diameter) so lists hold every contact");
-    if (is_dw(c)) return fail(c, MD_ERR_INVAL, "the contact model runs on MD_FP64 or MD_MIXED contexts");
     CK(cudaStreamSynchronize(c->st));
     int rc = MD_OK;
     for (int b = 0; b < 2; b++) {
-        if (c->v32[b]) continue;
-        if ((rc = dalloc(c, &c->v32[b], (size_t)c->n + 1))) return rc;
-        // slot n (the sentinel) stays zero: the fused step writes slots < n
-        CK(cudaMemsetAsync(c->v32[b], 0, sizeof(float4) * ((size_t)c->n + 1), c->st));
+        if (!c->v32[b]) {
+            if ((rc = dalloc(c, &c->v32[b], (size_t)c->n + 1))) return rc;
+            // slot n (the sentinel) stays zero: the fused step writes slots < n
+            CK(cudaMemsetAsync(c->v32[b], 0, sizeof(float4) * ((size_t)c->n + 1), c->st));
+        }
+        if (is_dw(c) && !c->vlo[b]) {
+            if ((rc = dalloc(c, &c->vlo[b], (size_t)c->n + 1))) return rc;
+            CK(cudaMemsetAsync(c->vlo[b], 0, sizeof(float4) * ((size_t)c->n + 1), c->st));
+        }
     }
     c->v32_fresh = false;
     // contacts use full per-atom lists

@@ -167,6 +167,8 @@ struct LJ {
     // (2 f'), 48 s^12, 24 s^6 (f / eps), 576 eps s^11, 144 eps s^5 (df/dsigma),
     // 2 s^12, 2 s^6 (dV/deps / 2), 24 eps s^11, 12 eps s^5 (dV/dsigma / 2)
     float dw_adj[10][2];
+    // contact model in double word: sigma^2, sigma, K, gamma, K / 2
+    float dw_sd_sig2[2], dw_sd_sig[2], dw_sd_k[2], dw_sd_g[2], dw_sd_hk[2];
     // spring-dashpot contact (Eq. 3; pot == 1): K, gamma, sigma^2 (sigma = diameter)
     int32_t pot;
     double sd_k, sd_g, sd_sig2;
@@ -213,7 +215,9 @@ struct Dev {
     const double *ctr;        // cell-centre coordinates (c + 0.5) s: per replica
                               // nc_x, then nc_y, then nc_z values
     float4 *v32, *v32_nxt;    // contact model, mixed path: FP32 velocity copies
-                              // (n + 1 each, slot n zero; flip with p32), else null
+                              // (n + 1 each, slot n zero; flip with p32), else null;
+                              // double-word path: the high parts of the copies
+    float4 *vlo, *vlo_nxt;    // contact model, double-word path: their low parts
     // Lists shared by groups of G atoms of one cell (list types 2 and 4):
     // group table, per-cell group counts and their prefix sums (the number of
     // groups at gcell_start[ncells]), rows and row lengths.  Entry k of group
@@ -369,6 +373,17 @@ __device__ __forceinline__ bool dw_split(const Rep &R, double p, float &h, float
     return fabsf(h) <= R.dw_lim;
 }
 
+// Velocity copies of slot i for the contact kernels: fl32(v) into vh and,
+// on the double-word path, fl32(v - fl32(v)) into vl.
+__device__ __forceinline__ void store_vel_copy(float4 *vh, float4 *vl, int64_t i, const dvec4 &v)
+{
+    const float hx = f32_of_f64(v.x), hy = f32_of_f64(v.y), hz = f32_of_f64(v.z);
+    vh[i] = make_float4(hx, hy, hz, 0.f);
+    if (vl)
+        vl[i] = make_float4(f32_of_f64(v.x - f64_of_f32(hx)), f32_of_f64(v.y - f64_of_f32(hy)),
+                            f32_of_f64(v.z - f64_of_f32(hz)), 0.f);
+}
+
 // p32 / plo entries of slot i from the cell-relative FP64 position (px, py,
 // pz): on the double-word path the split above, else p32 = fl32(p).
 __device__ __forceinline__ void store_cell_pos(const Dev &d, const Rep &R, float4 *p32,
@@ -412,7 +427,15 @@ int launch_force_dw(const Dev &d, const LJ &lj, int tpa, int epi, bool energy, b
 // ignored; the update runs in launch_integrate).
 int launch_force_sd(const Dev &d, const LJ &lj, bool mixed, int epi, bool energy,
                     cudaStream_t st, int *nlaunch);
-// d.v32[i] = fl32(d.v[i]) for i <= n (slot n: the sentinel's zero velocity).
+// The same in double word (k_force_dw.cu): one fused kernel with the
+// epilogue epi, gathering the neighbours' velocities from d.v32 / d.vlo and,
+// for EPI_FKKD, writing the next p32 / plo and v32 / vlo.
+int launch_force_sd_dw(const Dev &d, const LJ &lj, int epi, bool energy, cudaStream_t st,
+                       int *nlaunch);
+// d.v32 / d.vlo <- the double-word split of d.v for i <= n.
+int launch_velocity_dw(const Dev &d, cudaStream_t st, int *nlaunch);
+// d.v32[i] = fl32(d.v[i]) for i <= n (slot n: the sentinel's zero velocity);
+// with d.vlo also the low parts.
 int launch_velocity_f32(const Dev &d, cudaStream_t st, int *nlaunch);
 // out3 != NULL: write (PE, KE, W) per replica there; otherwise append one
 // record to log_base at status->elog_cursor and advance the cursor.

@@ -229,9 +229,6 @@ def test_dw_refusals(md, orc):
         assert e.value.code == -1
     with dw_ctx(md, s) as ctx:
         with pytest.raises(md.MDError) as e:
-            ctx.set_spring_dashpot(100.0, 1.0)
-        assert e.value.code == -1
-        with pytest.raises(md.MDError) as e:
             ctx.study_force_variant(0, 1)
         assert e.value.code in (-1, -9)
         ctx.run(10)                      # the context still runs
