@@ -3,7 +3,7 @@ checker: every gathered or stored index of the kernels is checked on the
 device, and a bad one raises an error flag (MD_ERR_STATE) instead of
 touching memory.  Here it runs the main paths (per-atom and group lists,
 replicas, the contact model, the adjoint, the force-kernel studies, the
-split-cell build, the double-word path) with no check firing and must agree bit for bit with the
+split-cell build, the double-word path with its contact model and adjoint) with no check firing and must agree bit for bit with the
 normal build on every deterministic path (the half-list paths add forces
 with atomics, so only their completion counts)."""
 import os
@@ -52,7 +52,7 @@ rng = np.random.default_rng(3)
 L = np.array([8.0, 8.5, 9.0])
 x = rng.uniform(0, 1, (600, 3)) * L
 v = rng.normal(size=(600, 3))
-for prec in (md.MD_FP64, md.MD_MIXED):
+for prec in (md.MD_FP64, md.MD_MIXED, md.MD_DW):
     with md.MDContext(x, v, L, sigma=1.0, cutoff=1.0, skin=0.3, dt=0.001, precision=prec) as c:
         c.set_spring_dashpot(200.0, 2.0)
         c.run(60)
@@ -80,9 +80,10 @@ with md.MDContext(s.pos, s.vel, s.box, precision=md.MD_MIXED, threads_per_atom=1
     c.run(20)
     out.append(h(*[c.study_force_variant(v, 1, forces=True)[1] for v in range(7)]))
 s4 = inputs.fcc_system(4, jitter=0.05, seed=2)
-with md.MDContext(s4.pos, s4.vel, s4.box, precision=md.MD_FP64) as c:
-    loss, ge, gs, gx, gv = c.adjoint(20, 10, 10)
-    out.append(h(np.array([loss, ge, gs]), gx, gv))
+for prec in (md.MD_FP64, md.MD_DW):
+    with md.MDContext(s4.pos, s4.vel, s4.box, precision=prec) as c:
+        loss, ge, gs, gx, gv = c.adjoint(20, 10, 10)
+        out.append(h(np.array([loss, ge, gs]), gx, gv))
 print(" ".join(out))
 """
 
@@ -98,5 +99,5 @@ def test_debug_build_agrees_and_stays_silent():
                            timeout=900)
         assert r.returncode == 0, f"{name}: {r.stderr[-3000:]}"
         res[name] = r.stdout.split()
-    assert len(res["release"]) == 16
+    assert len(res["release"]) == 18
     assert res["debug"] == res["release"]
