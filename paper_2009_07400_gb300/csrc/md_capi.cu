@@ -811,12 +811,13 @@ std::mutex &tune_mutex()
 
 // Lanes per atom of the full-list force kernels from the atom count: the
 // choices md_autotune measured on GB300 for FCC liquids (mixed: 8 at 4k
-// atoms, 4 at ~16k, 2 at ~55k, 1 from 131k; FP64, bound by its FP64 pipe: 8
-// at 4k, 4 up to ~256k, 2 up to ~2M, 1 at 4M).
+// atoms, 4 at ~16k, 2 at ~55k, 1 from 131k; double word: 8 at 4k, 4 at ~16k,
+// 2 from ~55k to ~442k (64 against 72 us per step at 131k), 1 at 1M; FP64,
+// bound by its FP64 pipe: 8 at 4k, 4 up to ~256k, 2 up to ~2M, 1 at 4M).
 int default_lanes(int64_t n, int32_t precision)
 {
-    if (precision == MD_MIXED || precision == MD_DW)
-        return n <= 8192 ? 8 : (n <= 32768 ? 4 : (n <= 98304 ? 2 : 1));
+    if (precision == MD_MIXED) return n <= 8192 ? 8 : (n <= 32768 ? 4 : (n <= 98304 ? 2 : 1));
+    if (precision == MD_DW) return n <= 8192 ? 8 : (n <= 32768 ? 4 : (n <= 600000 ? 2 : 1));
     return n <= 8192 ? 8 : (n <= 393216 ? 4 : (n <= 3000000 ? 2 : 1));
 }
 
