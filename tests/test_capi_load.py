@@ -80,6 +80,14 @@ def test_host_validation_without_gpu(lib):
     pos[2, 1] = np.nan
     rc, _ = _create(lib, (20.0, 20.0, 20.0), p, pos=pos)
     assert rc == -7
+    # precisions: MD_FP64, MD_MIXED, MD_DW; the double-word path runs full
+    # per-atom lists only, the group lists the mixed path only
+    rc, _ = _create(lib, (20.0, 20.0, 20.0), md.make_params(precision=3))
+    assert rc == -1
+    for lt in (md.MD_LIST_HALF, md.MD_LIST_GROUP2, md.MD_LIST_GROUP4):
+        rc, _ = _create(lib, (20.0, 20.0, 20.0), md.make_params(precision=md.MD_DW, list_type=lt))
+        assert rc == -1
+    assert b"full per-atom lists" in lib.md_last_error(None) or b"mixed path" in lib.md_last_error(None)
 
 
 def _create_batch(lib, boxes, counts, params, pos=None):
