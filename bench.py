@@ -946,9 +946,10 @@ def run_ncu_case(which, pin=None):
     from paper_2009_07400_gb300 import build, md
     torch.cuda.set_device(0)
     build.build()
-    if which == "dem":
+    if which in ("dem", "dem_dw"):
         s = inputs.workload(WORKLOADS["dem"])
-        with md.MDContext(s.pos, s.vel, s.box, precision=md.MD_MIXED, **DEM_PARAMS) as ctx:
+        prec = md.MD_MIXED if which == "dem" else md.MD_DW
+        with md.MDContext(s.pos, s.vel, s.box, precision=prec, **DEM_PARAMS) as ctx:
             ctx.set_spring_dashpot(DEM_K, DEM_GAMMA)
             ctx.run(2 * STEPS_PER_CYCLE)
         torch.cuda.synchronize()
@@ -977,7 +978,7 @@ def main():
                     help="skip the autotuner and use these lanes per atom and list "
                          "types for the mixed and FP64 legs (for profiling commands)")
     ap.add_argument("--cellorder-child", type=int, choices=[1, 2, 4], help=argparse.SUPPRESS)
-    ap.add_argument("--ncu-case", choices=["mixed", "fp64", "dw", "dem"],
+    ap.add_argument("--ncu-case", choices=["mixed", "fp64", "dw", "dem", "dem_dw"],
                     help="only build the workload and run 2 rebuild cycles (a short, "
                          "fixed launch sequence for an ncu capture); prints nothing")
     args = ap.parse_args()
