@@ -49,6 +49,10 @@
 // Epilogue: the FP64 velocity-Verlet update of the mixed path (x and v
 // updated in place), with the force F = (double)h + (double)l; the next
 // positions' split goes to the other p32 / plo buffers.
+//
+// The file also holds the double-word adjoint pair terms (md_adjoint on an
+// MD_DW context) and the double-word spring-dashpot contact step (Eq. 3),
+// which share these building blocks.
 #include "md_internal.cuh"
 
 namespace mdk {
