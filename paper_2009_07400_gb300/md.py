@@ -181,7 +181,9 @@ def _f64(a, n):
 def make_params(epsilon=1.0, sigma=1.0, mass=1.0, cutoff=2.5, skin=0.3, dt=0.005,
                 rebuild_every=20, precision=MD_FP64, half_list=False, threads_per_atom=0,
                 list_type=None):
-    """md_params; list_type (MD_LIST_*) wins over the older half_list flag."""
+    """md_params; list_type (MD_LIST_*) wins over the older half_list flag.
+    precision: MD_FP64, MD_MIXED (FP32 pairs) or MD_DW (pairs in double word,
+    full lists only)."""
     lt = int(list_type) if list_type is not None else (MD_LIST_HALF if half_list else MD_LIST_FULL)
     return md_params(epsilon, sigma, mass, cutoff, skin, dt, int(rebuild_every), int(precision),
                      lt, int(threads_per_atom))
