@@ -409,3 +409,29 @@ def test_dw_random_geometry_sweep(md, orc):
             worst = max(worst, err)
             assert err <= 1e-10, case
     print("double-word random geometries, worst force error:", worst)
+
+
+def test_dw_autograd_function_device(md, orc):
+    """torch.autograd through the adjoint of a double-word context with CUDA
+    tensors in and out: loss and gradients at the FP64 path's bar."""
+    torch = pytest.importorskip("torch")
+    from paper_2009_07400_gb300.autodiff import rollout_loss
+    s = inputs.fcc_system(5, jitter=0.05, seed=41)
+    x, v, _ = orc.vv_run(s.pos, s.vel, s.box, 40)
+    x0, v0, L = orc.wrap(x, s.box), v, s.box
+    eps = torch.tensor(1.0, dtype=torch.float64, device="cuda", requires_grad=True)
+    sig = torch.tensor(1.0, dtype=torch.float64, device="cuda", requires_grad=True)
+    xt = torch.tensor(x0, dtype=torch.float64, device="cuda", requires_grad=True)
+    vt = torch.tensor(v0, dtype=torch.float64, device="cuda", requires_grad=True)
+    with md.MDContext(x0, v0, L, precision=md.MD_DW) as ctx:
+        loss = rollout_loss(ctx, eps, sig, xt, vt, nsteps=20, window=10, ckpt_every=10)
+        (3.0 * loss).backward()
+    assert xt.grad.is_cuda and vt.grad.is_cuda
+    loss_o, ge_o, gs_o, gx_o, gv_o = orc.adjoint(x0, v0, L, 20, 10)
+    assert rel(loss.item(), loss_o) < 1e-11
+    assert rel(eps.grad.item(), 3 * ge_o) < 1e-9
+    assert rel(sig.grad.item(), 3 * gs_o) < 1e-9
+    gx = xt.grad.cpu().numpy()
+    gv = vt.grad.cpu().numpy()
+    assert np.linalg.norm(gx - 3 * gx_o) < 1e-9 * np.linalg.norm(3 * gx_o)
+    assert np.linalg.norm(gv - 3 * gv_o) < 1e-9 * np.linalg.norm(3 * gv_o)
