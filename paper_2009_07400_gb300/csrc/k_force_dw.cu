@@ -8,15 +8,10 @@
 // instructions for 78.6 M listed pairs before the constant folding below).
 // Precision MD_DW.
 //
-// Building blocks, written from the published error-free transformations:
-//   two_sum      s + e = a + b exactly (Knuth, TAOCP vol. 2, Sec. 4.2.2);
-//   fast_two_sum the same for |a| >= |b| in three operations (Dekker 1971);
-//   two_prod     p + e = a b exactly, e = fma(a, b, -p);
-//   dw_mul       product of double words: the exact product of the high
-//                parts plus the two cross terms (the low x low term is below
-//                2^-46 of the product), as in the double-word multiplication
-//                of Joldes, Muller and Popescu (ACM TOMS 2017);
-//   dw_add       exact sum of the high parts plus the low parts.
+// Building blocks (dw_arith.cuh, with their CPU check of exactness and
+// error bounds in the tests): TwoSum, Fast2Sum, the FMA exact product, the
+// double-word product and sum, and the Newton-refined reciprocal and
+// reciprocal square root.
 // Intermediate results are not renormalised (their low parts stay within a
 // few ulps of the high parts, which the multiplication tolerates); the
 // per-atom sums are renormalised once per list chunk.  The cut-off test
@@ -54,6 +49,7 @@
 // MD_DW context) and the double-word spring-dashpot contact step (Eq. 3),
 // which share these building blocks.
 #include "md_internal.cuh"
+#include "dw_arith.cuh"
 
 namespace mdk {
 
@@ -64,52 +60,7 @@ __device__ __forceinline__ bool stopped(const DevStatus *st)
     return *((volatile const int32_t *)&st->flags) != 0;
 }
 
-struct dw {
-    float h, l;
-};
-
-__device__ __forceinline__ dw two_sum(float a, float b)
-{
-    const float s = __fadd_rn(a, b);
-    const float bv = __fsub_rn(s, a);
-    const float av = __fsub_rn(s, bv);
-    return {s, __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv))};
-}
-
-__device__ __forceinline__ dw fast_two_sum(float a, float b)
-{
-    const float s = __fadd_rn(a, b);
-    return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-
-__device__ __forceinline__ dw two_prod(float a, float b)
-{
-    const float p = __fmul_rn(a, b);
-    return {p, __fmaf_rn(a, b, -p)};
-}
-
-__device__ __forceinline__ dw dw_mul(dw x, dw y)
-{
-    dw p = two_prod(x.h, y.h);
-    p.l = __fmaf_rn(x.h, y.l, __fmaf_rn(x.l, y.h, p.l));
-    return p;
-}
-
-__device__ __forceinline__ dw dw_add(dw x, dw y)
-{
-    dw s = two_sum(x.h, y.h);
-    s.l = __fadd_rn(s.l, __fadd_rn(x.l, y.l));
-    return s;
-}
-
-// (h + l)^2 for an exact high part h and a small low part l:
-// h^2 exactly, plus (2h + l) l
-__device__ __forceinline__ dw dw_sq_of(float h, float l)
-{
-    dw p = two_prod(h, h);
-    p.l = __fmaf_rn(__fmaf_rn(2.f, h, l), l, p.l);
-    return p;
-}
+using namespace dwa;
 
 __device__ __forceinline__ float rcp_approx(float a)
 {
@@ -209,10 +160,7 @@ __global__ void __launch_bounds__(256) k_force_dw_full(Dev d, LJ lj)
         const bool in = __fadd_rn(__fsub_rn(r2.h, rc2.h), __fsub_rn(r2.l, rc2.l)) < 0.f;
         // 1 / r^2
         const float rf = __fadd_rn(r2.h, r2.l);
-        float y = rcp_approx(rf);
-        y = __fmaf_rn(y, __fmaf_rn(-rf, y, 1.f), y);
-        const float er = __fmaf_rn(-r2.l, y, __fmaf_rn(-r2.h, y, 1.f));
-        const dw sr2 = {y, __fmul_rn(y, er)};
+        const dw sr2 = dw_recip(r2, rf, rcp_approx(rf));
         const dw sr6 = dw_mul(dw_mul(sr2, sr2), sr2);
         dw f = dw_mul(dw_mul(sr2, sr6), dw_add(dw_mul(a12, sr6), a6n));
         f.h = in ? f.h : 0.f;
@@ -361,10 +309,7 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs_dw(Dev d, LJ lj, DwAdjArg
         const dw r2 = dw_add(dw_add(dw_sq_of(dxh, dxl), dw_sq_of(dyh, dyl)), dw_sq_of(dzh, dzl));
         if (!(__fadd_rn(__fsub_rn(r2.h, rc2.h), __fsub_rn(r2.l, rc2.l)) < 0.f)) continue;
         const float rf = __fadd_rn(r2.h, r2.l);
-        float y = rcp_approx(rf);
-        y = __fmaf_rn(y, __fmaf_rn(-rf, y, 1.f), y);
-        const float er = __fmaf_rn(-r2.l, y, __fmaf_rn(-r2.h, y, 1.f));
-        const dw sr2 = {y, __fmul_rn(y, er)};
+        const dw sr2 = dw_recip(r2, rf, rcp_approx(rf));
         const dw sr6 = dw_mul(dw_mul(sr2, sr2), sr2);
         const dw sr8 = dw_mul(sr2, sr6);
         const dw f = dw_mul(sr8, dw_axb(dw_const(lj.dw_a12), sr6, dw_const(lj.dw_a6)));
@@ -514,11 +459,7 @@ __global__ void __launch_bounds__(256) k_force_sd_dw(Dev d, LJ lj)
             const float4 vjh = __ldg(d.v32 + j), vjl = __ldg(d.vlo + j);
             // 1/r and r
             const float af = __fadd_rn(r2.h, r2.l);
-            float y = rsqrt_approx(af);
-            y = __fmul_rn(y, __fmaf_rn(-0.5f * __fmul_rn(af, y), y, 1.5f));
-            const dw p = dw_mul(r2, two_prod(y, y));
-            const float ee = __fsub_rn(__fsub_rn(1.f, p.h), p.l);
-            const dw ir = {y, __fmul_rn(y, 0.5f * ee)};
+            const dw ir = dw_rsqrt(r2, af, rsqrt_approx(af));
             const dw r = dw_mul(r2, ir);
             const dw dx = {dxh, dxl}, dy = {dyh, dyl}, dz = {dzh, dzl};
             const dw vx = dw_add(dw{vih.x, vil.x}, dw{-vjh.x, -vjl.x});

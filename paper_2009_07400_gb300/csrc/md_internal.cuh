@@ -365,11 +365,16 @@ __device__ __forceinline__ void check_displacement(const Dev &d, int64_t i, cons
 // the force kernel forms the high part of each displacement without
 // rounding.  l carries p to 2^-25 g.  Returns false (the caller raises
 // FLAG_DWRANGE) when |h| exceeds R.dw_lim, past which h +- s_h could round.
-__device__ __forceinline__ bool dw_split(const Rep &R, double p, float &h, float &l)
+__host__ __device__ __forceinline__ bool dw_split(const Rep &R, double p, float &h, float &l)
 {
+#ifdef __CUDA_ARCH__
     const double hd = __dsub_rn(__dadd_rn(p, R.dw_magic), R.dw_magic);
-    h = f32_of_f64(hd);
     l = f32_of_f64(__dsub_rn(p, hd));
+#else
+    const double hd = (p + R.dw_magic) - R.dw_magic;   // (the CPU check of the split)
+    l = f32_of_f64(p - hd);
+#endif
+    h = f32_of_f64(hd);
     return fabsf(h) <= R.dw_lim;
 }
 
